@@ -1,0 +1,1017 @@
+/*
+ * FP64 oracle for the per-layer Kalman-filter step of mkFit-style track fitting
+ * and finding ("Parallelized and Vectorized Tracking Using Kalman Filters with
+ * CMS Detector Geometry and Events", sec. 1 and 2.1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+ * CUDA path is checked against.  Only the tests, the smoke check and the CPU
+ * baseline leg of the bench may load it.  It shares no code, header or constant
+ * table with the CUDA library.
+ *
+ * The paper prints no equations: it names the Kalman filter (Fruhwirth), the
+ * propagation of tracks to barrel and endcap layers (sec. 1), the selection of
+ * the best chi2 extensions before the final Kalman updates (sec. 1, the "clone
+ * engine"), per-layer hit search windows and layer plans (sec. 2.1) and a
+ * constant field (sec. 2.1, sec. 3).  What follows writes out the textbook
+ * definitions behind those words:
+ *
+ *  - state p = (x, y, z, q/pT, phi, theta), phi = azimuth of the momentum;
+ *  - uniform field Bz: turning rate h = -(q/pT) * K * Bz per unit transverse path s,
+ *    x(s) = x + (sin(phi + h s) - sin(phi)) / h,  y(s) = y - (cos(phi + h s) - cos(phi)) / h,
+ *    z(s) = z + s cot(theta),  phi(s) = phi + h s  (straight line for h = 0);
+ *  - propagation to a layer = the smallest s > 0 (less than half a turn) that puts
+ *    the helix on the layer surface (cylinder r = R, or disk z = Z);
+ *  - Jacobian of that map, J = dF/dp + (dF/ds)(ds/dp), ds/dp from the surface
+ *    constraint; covariance transport C' = J C J^T;
+ *  - 2-D measurement on the surface (r-phi and z on cylinders, r-phi and r on
+ *    disks), Kalman gain update and chi2 of the predicted residual;
+ *  - seeds from the circle through three hits;
+ *  - finding: layer by layer, every hit of the layer is tested (no binning);
+ *    candidates are ranked by score = chi2_cut * n_hits - chi2_total, the best
+ *    N children are kept and only they receive the Kalman update.
+ *
+ * Covariances are full 6x6 row-major arrays here.  Interfaces that exchange the
+ * 21-value packed lower triangle use index i(i+1)/2 + j for i >= j.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_K 0.0029979245800 /* GeV / (T cm) */
+#define OR_MAXL 64
+#define OR_MAXR 16
+#define OR_PI 3.14159265358979323846
+
+/* per-track status bits */
+#define OR_ST_UNREACHABLE 1u   /* a requested layer could not be reached (fit) */
+#define OR_ST_BADSEED 2u       /* seed hits degenerate */
+#define OR_ST_NONFINITE 4u     /* a non-finite number appeared */
+#define OR_ST_BADS 8u          /* residual covariance not positive definite */
+#define OR_ST_MISSSTOP 16u     /* finding stopped by consecutive misses */
+#define OR_ST_TRUNC 32u        /* output hit list truncated */
+
+#define OR_HIT_MISS (-2)
+#define OR_HIT_PASS (-3)
+
+typedef struct {
+    int n;
+    int kind[OR_MAXL];
+    double rz[OR_MAXL], lo[OR_MAXL], hi[OR_MAXL], su[OR_MAXL], sv[OR_MAXL];
+    double bz;
+    int n_regions;
+    double edges[OR_MAXR];
+    uint64_t mask[OR_MAXR];
+} geom_t;
+
+static int geom_init(geom_t *g, int n_layers, const int32_t *kind, const double *rz, const double *lo,
+                     const double *hi, const double *su, const double *sv, double bz, int n_regions,
+                     const double *edges, const uint64_t *masks) {
+    if (n_layers < 1 || n_layers > OR_MAXL) return -1;
+    if (n_regions < 1 || n_regions > OR_MAXR) return -1;
+    g->n = n_layers;
+    for (int i = 0; i < n_layers; ++i) {
+        g->kind[i] = kind[i];
+        g->rz[i] = rz[i];
+        g->lo[i] = lo[i];
+        g->hi[i] = hi[i];
+        g->su[i] = su[i];
+        g->sv[i] = sv[i];
+    }
+    g->bz = bz;
+    g->n_regions = n_regions;
+    for (int r = 0; r + 1 < n_regions; ++r) g->edges[r] = edges[r];
+    for (int r = 0; r < n_regions; ++r) {
+        uint64_t all = (n_layers == 64) ? ~0ull : ((1ull << n_layers) - 1ull);
+        g->mask[r] = masks ? (masks[r] & all) : all;
+    }
+    return 0;
+}
+
+static double wrap_pi(double a) {
+    a = fmod(a + OR_PI, 2.0 * OR_PI);
+    if (a < 0) a += 2.0 * OR_PI;
+    return a - OR_PI;
+}
+
+static double cot_of(double theta) { return cos(theta) / sin(theta); }
+
+/* ------------------------------------------------------------------------- */
+/* Helix and propagation                                                     */
+/* ------------------------------------------------------------------------- */
+
+static double turn_rate(const geom_t *g, double w) { return -w * OR_K * g->bz; }
+
+/* Move state p along the helix by transverse path s (closed form). */
+static void helix_move(const double p[6], double h, double s, double q[6]) {
+    double phi = p[4], dx, dy;
+    if (h == 0.0) {
+        dx = s * cos(phi);
+        dy = s * sin(phi);
+    } else {
+        dx = (sin(phi + h * s) - sin(phi)) / h;
+        dy = -(cos(phi + h * s) - cos(phi)) / h;
+    }
+    q[0] = p[0] + dx;
+    q[1] = p[1] + dy;
+    q[2] = p[2] + s * cot_of(p[5]);
+    q[3] = p[3];
+    q[4] = wrap_pi(phi + h * s);
+    q[5] = p[5];
+}
+
+/* Smallest s > 0 (and below half a turn) with x(s)^2 + y(s)^2 = R^2.
+ * Circle of the track (centre C, radius 1/|h|) intersected with the layer circle. */
+static int cyl_path(double x, double y, double phi, double h, double R, double *s_out) {
+    double best = INFINITY;
+    if (h == 0.0) {
+        double b = x * cos(phi) + y * sin(phi);
+        double c = x * x + y * y - R * R;
+        double disc = b * b - c;
+        if (disc < 0) return 0;
+        double sq = sqrt(disc);
+        double r1 = -b - sq, r2 = -b + sq;
+        if (r1 > 0) best = r1;
+        if (r2 > 0 && r2 < best) best = r2;
+    } else {
+        double rho = 1.0 / fabs(h);
+        double cx = x - sin(phi) / h, cy = y + cos(phi) / h;
+        double d = hypot(cx, cy);
+        if (d == 0.0 || d > R + rho || d < fabs(R - rho)) return 0;
+        double a = (R * R - rho * rho + d * d) / (2.0 * d);
+        double hc2 = R * R - a * a;
+        double hc = hc2 > 0 ? sqrt(hc2) : 0.0;
+        double ux = cx / d, uy = cy / d;
+        for (int k = -1; k <= 1; k += 2) {
+            double X = a * ux - k * hc * uy, Y = a * uy + k * hc * ux;
+            double ax = x - cx, ay = y - cy, bx = X - cx, by = Y - cy;
+            double ang = atan2(ax * by - ay * bx, ax * bx + ay * by);
+            double s = ang / h;
+            if (s > 0 && s < best) best = s;
+        }
+    }
+    if (!(best < INFINITY)) return 0;
+    *s_out = best;
+    return 1;
+}
+
+/* Path to the surface of layer l, or 0 if the helix does not reach it going
+ * forward within half a turn.  No extent check. */
+static int path_to_layer(const geom_t *g, const double p[6], int l, double *s) {
+    double h = turn_rate(g, p[3]);
+    if (g->kind[l] == 0) return cyl_path(p[0], p[1], p[4], h, g->rz[l], s);
+    double ct = cot_of(p[5]);
+    if (ct == 0.0) return 0;
+    double sd = (g->rz[l] - p[2]) / ct;
+    if (!(sd > 0)) return 0;
+    if (h != 0.0 && fabs(h) * sd >= OR_PI) return 0;
+    *s = sd;
+    return 1;
+}
+
+/* J = dF/dp + (dF/ds) (ds/dp), 6x6 row-major, for the move by s onto layer l. */
+static void prop_jacobian(const geom_t *g, const double p[6], int l, double s, const double q[6],
+                          double J[36]) {
+    double A[36];
+    memset(A, 0, sizeof(A));
+    double h = turn_rate(g, p[3]);
+    double dhdw = -OR_K * g->bz;
+    double phi = p[4], phis = phi + h * s;
+    double dx = q[0] - p[0], dy = q[1] - p[1];
+    double dxdh, dydh;
+    if (h == 0.0) {
+        dxdh = -0.5 * s * s * sin(phi);
+        dydh = 0.5 * s * s * cos(phi);
+    } else {
+        dxdh = (s * cos(phis) - dx) / h;
+        dydh = (s * sin(phis) - dy) / h;
+    }
+    double st = sin(p[5]);
+    for (int i = 0; i < 6; ++i) A[i * 6 + i] = 1.0;
+    A[0 * 6 + 3] = dxdh * dhdw;
+    A[0 * 6 + 4] = -dy;
+    A[1 * 6 + 3] = dydh * dhdw;
+    A[1 * 6 + 4] = dx;
+    A[2 * 6 + 5] = -s / (st * st);
+    A[4 * 6 + 3] = s * dhdw;
+    double d[6] = {cos(phis), sin(phis), cot_of(p[5]), 0.0, h, 0.0};
+    double dsdp[6];
+    if (g->kind[l] == 0) {
+        double den = q[0] * d[0] + q[1] * d[1];
+        for (int j = 0; j < 6; ++j) dsdp[j] = -(q[0] * A[0 * 6 + j] + q[1] * A[1 * 6 + j]) / den;
+    } else {
+        for (int j = 0; j < 6; ++j) dsdp[j] = -A[2 * 6 + j] / d[2];
+    }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) J[i * 6 + j] = A[i * 6 + j] + d[i] * dsdp[j];
+}
+
+/* C' = J C J^T (full matrices), symmetrised. */
+static void transport(const double J[36], const double C[36], double Co[36]) {
+    double M[36];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double a = 0;
+            for (int k = 0; k < 6; ++k) a += J[i * 6 + k] * C[k * 6 + j];
+            M[i * 6 + j] = a;
+        }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double a = 0;
+            for (int k = 0; k < 6; ++k) a += M[i * 6 + k] * J[j * 6 + k];
+            Co[i * 6 + j] = a;
+        }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < i; ++j) {
+            double m = 0.5 * (Co[i * 6 + j] + Co[j * 6 + i]);
+            Co[i * 6 + j] = Co[j * 6 + i] = m;
+        }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Measurement and update                                                    */
+/* ------------------------------------------------------------------------- */
+
+/* Residual (u, v) of hit (xh, yh, zh) against a state on layer l's surface and
+ * the 2x6 projection H. */
+static void residual(const geom_t *g, int l, const double p[6], double xh, double yh, double zh,
+                     double r[2], double H[12]) {
+    double phip = atan2(p[1], p[0]);
+    double phih = atan2(yh, xh);
+    double sp = sin(phip), cp = cos(phip);
+    memset(H, 0, 12 * sizeof(double));
+    H[0] = -sp;
+    H[1] = cp;
+    if (g->kind[l] == 0) {
+        r[0] = g->rz[l] * wrap_pi(phih - phip);
+        r[1] = zh - p[2];
+        H[6 + 2] = 1.0;
+    } else {
+        double rt = hypot(p[0], p[1]);
+        r[0] = rt * wrap_pi(phih - phip);
+        r[1] = hypot(xh, yh) - rt;
+        H[6 + 0] = cp;
+        H[6 + 1] = sp;
+    }
+}
+
+/* S = H C H^T + V and its inverse; returns 0 if S is not positive definite. */
+static int residual_cov(const geom_t *g, int l, const double C[36], const double H[12], double S[4],
+                        double Si[4], double HC[12]) {
+    for (int a = 0; a < 2; ++a)
+        for (int j = 0; j < 6; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 6; ++k) acc += H[a * 6 + k] * C[k * 6 + j];
+            HC[a * 6 + j] = acc;
+        }
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            double acc = 0;
+            for (int k = 0; k < 6; ++k) acc += HC[a * 6 + k] * H[b * 6 + k];
+            S[a * 2 + b] = acc;
+        }
+    S[0] += g->su[l] * g->su[l];
+    S[3] += g->sv[l] * g->sv[l];
+    double sym = 0.5 * (S[1] + S[2]);
+    S[1] = S[2] = sym;
+    double det = S[0] * S[3] - S[1] * S[2];
+    if (!(S[0] > 0 && det > 0)) return 0;
+    Si[0] = S[3] / det;
+    Si[3] = S[0] / det;
+    Si[1] = Si[2] = -S[1] / det;
+    return 1;
+}
+
+static double chi2_of(const double r[2], const double Si[4]) {
+    return r[0] * (Si[0] * r[0] + Si[1] * r[1]) + r[1] * (Si[2] * r[0] + Si[3] * r[1]);
+}
+
+/* Kalman update of (p, C) with residual r: K = C H^T S^-1, p += K r,
+ * C -= K H C (symmetrised).  Returns chi2 of the predicted residual. */
+static double kf_update(const double HC[12], const double Si[4], const double r[2], double p[6],
+                        double C[36]) {
+    double K[12]; /* 6x2 */
+    for (int i = 0; i < 6; ++i)
+        for (int b = 0; b < 2; ++b) K[i * 2 + b] = HC[0 * 6 + i] * Si[0 * 2 + b] + HC[1 * 6 + i] * Si[1 * 2 + b];
+    for (int i = 0; i < 6; ++i) p[i] += K[i * 2 + 0] * r[0] + K[i * 2 + 1] * r[1];
+    p[4] = wrap_pi(p[4]);
+    double Cn[36];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) Cn[i * 6 + j] = C[i * 6 + j] - (K[i * 2 + 0] * HC[0 * 6 + j] + K[i * 2 + 1] * HC[1 * 6 + j]);
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double m = 0.5 * (Cn[i * 6 + j] + Cn[j * 6 + i]);
+            C[i * 6 + j] = C[j * 6 + i] = m;
+        }
+    return chi2_of(r, Si);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Seeds                                                                      */
+/* ------------------------------------------------------------------------- */
+
+/* State at hit 1 from the circle through three hits (x-y) and the straight line
+ * through hits 1 and 3 in (arc length, z); diagonal prior covariance. */
+static int seed_state(const geom_t *g, const double *h1, const double *h2, const double *h3, int layer1,
+                      double p[6], double C[36]) {
+    double ax = h2[0] - h1[0], ay = h2[1] - h1[1];
+    double bx = h3[0] - h1[0], by = h3[1] - h1[1];
+    double cx = h3[0] - h2[0], cy = h3[1] - h2[1];
+    double la = hypot(ax, ay), lb = hypot(bx, by), lc = hypot(cx, cy);
+    if (!(la > 0 && lb > 0 && lc > 0)) return 0;
+    double kappa = 2.0 * (ax * by - ay * bx) / (la * lb * lc); /* signed curvature = h */
+    double h = kappa;
+    double w = (g->bz != 0.0) ? -h / (OR_K * g->bz) : 0.0;
+    if (g->bz == 0.0) h = 0.0;
+    double a12 = (h == 0.0) ? 0.0 : asin(fmax(-1.0, fmin(1.0, 0.5 * h * la)));
+    double phi0 = atan2(ay, ax) - a12;
+    double s13 = (h == 0.0) ? lb : 2.0 * asin(fmax(-1.0, fmin(1.0, 0.5 * h * lb))) / h;
+    double cot = (h3[2] - h1[2]) / s13;
+    p[0] = h1[0];
+    p[1] = h1[1];
+    p[2] = h1[2];
+    p[3] = w;
+    p[4] = wrap_pi(phi0);
+    p[5] = atan2(1.0, cot);
+    /* position prior lies in the surface of hit 1's layer (no variance along its
+     * normal), so the state has 5 free parameters and ndf = 2 n_hits - 5 */
+    double sig = 10.0 * fmax(g->su[layer1], g->sv[layer1]);
+    double s2 = sig * sig;
+    memset(C, 0, 36 * sizeof(double));
+    if (g->kind[layer1] == 0) {
+        double ph = atan2(h1[1], h1[0]), sp = sin(ph), cp = cos(ph);
+        C[0] = s2 * sp * sp;
+        C[1] = C[6] = -s2 * sp * cp;
+        C[7] = s2 * cp * cp;
+        C[14] = s2;
+    } else {
+        C[0] = C[7] = s2;
+    }
+    C[21] = (0.1 * w) * (0.1 * w) + 0.01 * 0.01;
+    C[28] = 0.01 * 0.01;
+    C[35] = 0.01 * 0.01;
+    return 1;
+}
+
+static int finite6(const double p[6]) {
+    for (int i = 0; i < 6; ++i)
+        if (!isfinite(p[i])) return 0;
+    return 1;
+}
+
+static void pack21(const double C[36], double *out, int64_t stride) {
+    int k = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) out[(int64_t)(k++) * stride] = C[i * 6 + j];
+}
+
+static void unpack21(const double *in, int64_t stride, double C[36]) {
+    int k = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double v = in[(int64_t)(k++) * stride];
+            C[i * 6 + j] = C[j * 6 + i] = v;
+        }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exported single-step entry points (used by the pin tests)                  */
+/* ------------------------------------------------------------------------- */
+
+#define GEOM_ARGS                                                                                     \
+    int n_layers, const int32_t *kind, const double *rz, const double *lo, const double *hi,        \
+        const double *su, const double *sv, double bz, int n_regions, const double *edges,           \
+        const uint64_t *masks
+#define GEOM_PASS n_layers, kind, rz, lo, hi, su, sv, bz, n_regions, edges, masks
+
+/* Propagate p to layer l: writes q, J (6x6 row-major) and s.  Returns 1 on
+ * success, 0 if unreachable, -1 on bad arguments. */
+int or_propagate(GEOM_ARGS, const double *p, int l, double *q, double *J, double *s) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS) || l < 0 || l >= g.n) return -1;
+    double ss;
+    if (!path_to_layer(&g, p, l, &ss)) return 0;
+    helix_move(p, turn_rate(&g, p[3]), ss, q);
+    prop_jacobian(&g, p, l, ss, q, J);
+    *s = ss;
+    return 1;
+}
+
+/* Move p by transverse path s (closed-form helix). */
+int or_helix_move(GEOM_ARGS, const double *p, double s, double *q) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS)) return -1;
+    helix_move(p, turn_rate(&g, p[3]), s, q);
+    return 1;
+}
+
+void or_transport(const double *J, const double *C, double *Co) { transport(J, C, Co); }
+
+/* One Kalman update on layer l with hit (xh, yh, zh).  Writes updated p, C,
+ * the residual r[2], S[4], and returns chi2 (NaN if S is not positive definite).
+ * Also writes the Joseph-form covariance into Cj for comparison. */
+double or_update(GEOM_ARGS, int l, const double *hit, double *p, double *C, double *r_out, double *S_out,
+                 double *Cj) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS)) return NAN;
+    double H[12], r[2], S[4], Si[4], HC[12];
+    residual(&g, l, p, hit[0], hit[1], hit[2], r, H);
+    if (!residual_cov(&g, l, C, H, S, Si, HC)) return NAN;
+    double C0[36];
+    memcpy(C0, C, sizeof(C0));
+    double chi2 = kf_update(HC, Si, r, p, C);
+    if (Cj) {
+        /* Joseph form: (I - K H) C0 (I - K H)^T + K V K^T */
+        double K[12], IKH[36], T[36];
+        for (int i = 0; i < 6; ++i)
+            for (int b = 0; b < 2; ++b) K[i * 2 + b] = HC[i] * Si[b] + HC[6 + i] * Si[2 + b];
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) IKH[i * 6 + j] = (i == j) - (K[i * 2] * H[j] + K[i * 2 + 1] * H[6 + j]);
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double a = 0;
+                for (int k = 0; k < 6; ++k) a += IKH[i * 6 + k] * C0[k * 6 + j];
+                T[i * 6 + j] = a;
+            }
+        double V0 = g.su[l] * g.su[l], V1 = g.sv[l] * g.sv[l];
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double a = 0;
+                for (int k = 0; k < 6; ++k) a += T[i * 6 + k] * IKH[j * 6 + k];
+                Cj[i * 6 + j] = a + K[i * 2] * V0 * K[j * 2] + K[i * 2 + 1] * V1 * K[j * 2 + 1];
+            }
+    }
+    if (r_out) { r_out[0] = r[0]; r_out[1] = r[1]; }
+    if (S_out) memcpy(S_out, S, sizeof(S));
+    return chi2;
+}
+
+/* Seed state and prior covariance (6x6) from three hits; returns 1 or 0. */
+int or_seed(GEOM_ARGS, const double *h1, const double *h2, const double *h3, int layer1, double *p, double *C) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS)) return -1;
+    return seed_state(&g, h1, h2, h3, layer1, p, C);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fit: Kalman filter along fixed hit lists                                   */
+/* ------------------------------------------------------------------------- */
+
+/* xyz: [3][n_hits] SoA; hit_layer[n_hits]; hit_idx: [max_hits][n] (-1 = none,
+ * hits in path order); seed_par [6][n] and seed_cov [21][n] (packed) or NULL to
+ * seed from the first three hits.  Outputs: par [6][n], cov [21][n] (packed),
+ * chi2[n], ndf[n], status[n].  The state is reported on the surface of the last
+ * hit used. */
+int or_fit(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_layer, const int32_t *hit_idx,
+           int max_hits, int64_t n, const double *seed_par, const double *seed_cov, double *out_par,
+           double *out_cov, double *out_chi2, int32_t *out_ndf, uint32_t *out_status) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS)) return -1;
+    const double *X = xyz, *Y = xyz + n_hits, *Z = xyz + 2 * n_hits;
+    for (int64_t t = 0; t < n; ++t) {
+        double p[6], C[36];
+        uint32_t st = 0;
+        int idx[OR_MAXL + 8];
+        int nh = 0;
+        for (int k = 0; k < max_hits && k < OR_MAXL + 8; ++k) {
+            int32_t hi_ = hit_idx[(int64_t)k * n + t];
+            if (hi_ >= 0 && hi_ < n_hits) idx[nh++] = hi_;
+        }
+        double chi2 = 0;
+        int used = 0;
+        if (nh < 3) st |= OR_ST_BADSEED;
+        if (!(st & OR_ST_BADSEED)) {
+            if (seed_par) {
+                for (int i = 0; i < 6; ++i) p[i] = seed_par[(int64_t)i * n + t];
+                unpack21(seed_cov + t, n, C);
+            } else {
+                double a[3] = {X[idx[0]], Y[idx[0]], Z[idx[0]]};
+                double b[3] = {X[idx[1]], Y[idx[1]], Z[idx[1]]};
+                double c[3] = {X[idx[2]], Y[idx[2]], Z[idx[2]]};
+                if (!seed_state(&g, a, b, c, hit_layer[idx[0]], p, C)) st |= OR_ST_BADSEED;
+            }
+        }
+        if (!(st & OR_ST_BADSEED)) {
+            for (int k = 0; k < nh; ++k) {
+                int hid = idx[k], l = hit_layer[hid];
+                if (k > 0) {
+                    double s, q[6], J[36], Cn[36];
+                    if (!path_to_layer(&g, p, l, &s)) { st |= OR_ST_UNREACHABLE; continue; }
+                    helix_move(p, turn_rate(&g, p[3]), s, q);
+                    prop_jacobian(&g, p, l, s, q, J);
+                    transport(J, C, Cn);
+                    memcpy(p, q, sizeof(q));
+                    memcpy(C, Cn, sizeof(Cn));
+                }
+                double H[12], r[2], S[4], Si[4], HC[12];
+                residual(&g, l, p, X[hid], Y[hid], Z[hid], r, H);
+                if (!residual_cov(&g, l, C, H, S, Si, HC)) { st |= OR_ST_BADS; continue; }
+                chi2 += kf_update(HC, Si, r, p, C);
+                used++;
+            }
+        }
+        if (!finite6(p) || !isfinite(chi2)) st |= OR_ST_NONFINITE;
+        for (int i = 0; i < 6; ++i) out_par[(int64_t)i * n + t] = (st & OR_ST_BADSEED) ? NAN : p[i];
+        if (st & OR_ST_BADSEED) {
+            for (int k = 0; k < 21; ++k) out_cov[(int64_t)k * n + t] = NAN;
+        } else {
+            pack21(C, out_cov + t, n);
+        }
+        out_chi2[t] = chi2;
+        /* five free parameters on a surface; without a field q/pT is not measured */
+        out_ndf[t] = 2 * used - (g.bz != 0.0 ? 5 : 4);
+        out_status[t] = st;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Finding                                                                    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    double p[6], C[36];
+    double chi2, score;
+    int n_hits, n_miss, consec;
+    int next_cyl, next_dsk; /* positions in the sorted cylinder / disk lists, -1 = none */
+    int dir;                /* +1 / -1 along z for disks */
+    int done;
+    int path;               /* index of this candidate's last record in the history */
+} cand_t;
+
+typedef struct {
+    int parent;   /* rank of the parent candidate */
+    int hit;      /* global hit index, OR_HIT_MISS or OR_HIT_PASS */
+    double chi2;  /* chi2 of the hit */
+    double score;
+    int layer;
+} child_t;
+
+typedef struct {
+    int prev;     /* previous record, -1 at the seed */
+    int hit;
+} hrec_t;
+
+typedef struct {
+    const geom_t *g;
+    const double *X, *Y, *Z, *PHI, *RH;
+    const int32_t *HL;        /* layer of each hit */
+    const int32_t *lay_start; /* [n_events * n_layers + 1] into lay_hits */
+    const int32_t *lay_hits;
+    int cyl_sorted[OR_MAXL], n_cyl;
+    int dsk_sorted[OR_MAXL], n_dsk;
+    double cut;
+    int max_consec;
+    int n_best;
+} find_ctx_t;
+
+static int cmp_child(const child_t *a, const child_t *b) {
+    if (a->score != b->score) return a->score > b->score ? -1 : 1;
+    if (a->parent != b->parent) return a->parent < b->parent ? -1 : 1;
+    unsigned ha = a->hit < 0 ? 0xFFFFFFFFu : (unsigned)a->hit;
+    unsigned hb = b->hit < 0 ? 0xFFFFFFFFu : (unsigned)b->hit;
+    if (ha != hb) return ha < hb ? -1 : 1;
+    return 0;
+}
+
+static int cmp_child_q(const void *a, const void *b) { return cmp_child((const child_t *)a, (const child_t *)b); }
+
+/* chi2 total of the candidate a child would become */
+static double child_chi2_total(const cand_t *parents, const child_t *ch) {
+    return parents[ch->parent].chi2 + (ch->hit >= 0 ? ch->chi2 : 0.0);
+}
+
+static void upd_min(double *m, double v) {
+    if (v < *m) *m = v;
+}
+
+/* Next layer of a candidate: the nearer (in path length) of the next cylinder
+ * and the next disk allowed by the region mask.  Layers crossed outside their
+ * extent are passed over (pointer advanced, no measurement, state unchanged).
+ * Returns the layer id (and its path s) or -1 when no layer is left. */
+static int next_layer(const find_ctx_t *f, cand_t *c, uint64_t mask, double *s_out, double *mgeo) {
+    const geom_t *g = f->g;
+    for (int guard = 0; guard < 2 * OR_MAXL + 2; ++guard) {
+        while (c->next_cyl >= 0 && c->next_cyl < f->n_cyl && !((mask >> f->cyl_sorted[c->next_cyl]) & 1ull))
+            c->next_cyl++;
+        if (c->next_cyl >= f->n_cyl) c->next_cyl = -1;
+        while (c->next_dsk >= 0 && c->next_dsk < f->n_dsk && !((mask >> f->dsk_sorted[c->next_dsk]) & 1ull))
+            c->next_dsk += c->dir;
+        if (c->next_dsk >= f->n_dsk) c->next_dsk = -1;
+        double sc = INFINITY, sd = INFINITY;
+        int lc = -1, ld = -1;
+        if (c->next_cyl >= 0) {
+            lc = f->cyl_sorted[c->next_cyl];
+            if (!path_to_layer(g, c->p, lc, &sc)) { c->next_cyl = -1; sc = INFINITY; lc = -1; }
+        }
+        if (c->next_dsk >= 0) {
+            ld = f->dsk_sorted[c->next_dsk];
+            if (!path_to_layer(g, c->p, ld, &sd)) { c->next_dsk = -1; sd = INFINITY; ld = -1; }
+        }
+        if (lc < 0 && ld < 0) return -1;
+        int use_cyl = (sc <= sd);
+        if (lc >= 0 && ld >= 0) upd_min(mgeo, fabs(sc - sd) / fmax(sc, sd));
+        int l = use_cyl ? lc : ld;
+        double s = use_cyl ? sc : sd;
+        double q[6];
+        helix_move(c->p, turn_rate(g, c->p[3]), s, q);
+        double coord = (g->kind[l] == 0) ? q[2] : hypot(q[0], q[1]);
+        double span = g->hi[l] - g->lo[l];
+        upd_min(mgeo, fmin(fabs(coord - g->lo[l]), fabs(coord - g->hi[l])) / span);
+        int inside = coord >= g->lo[l] && coord <= g->hi[l];
+        if (use_cyl) c->next_cyl++;
+        else c->next_dsk += c->dir;
+        if (c->next_dsk >= f->n_dsk) c->next_dsk = -1;
+        if (inside) {
+            *s_out = s;
+            return l;
+        }
+    }
+    return -1;
+}
+
+/* Position of the first entry > v in a sorted list of values (or count). */
+static int first_cyl_beyond(const find_ctx_t *f, double r) {
+    for (int i = 0; i < f->n_cyl; ++i)
+        if (f->g->rz[f->cyl_sorted[i]] > r) return i;
+    return -1;
+}
+
+static int first_dsk_beyond(const find_ctx_t *f, double z, int dir) {
+    if (dir > 0) {
+        for (int i = 0; i < f->n_dsk; ++i)
+            if (f->g->rz[f->dsk_sorted[i]] > z) return i;
+    } else {
+        for (int i = f->n_dsk - 1; i >= 0; --i)
+            if (f->g->rz[f->dsk_sorted[i]] < z) return i;
+    }
+    return -1;
+}
+
+typedef struct {
+    child_t *v;
+    int n, cap;
+} childvec_t;
+
+static int push_child(childvec_t *cv, child_t c) {
+    if (cv->n == cv->cap) {
+        int nc = cv->cap ? 2 * cv->cap : 64;
+        child_t *nv = (child_t *)realloc(cv->v, sizeof(child_t) * nc);
+        if (!nv) return 0;
+        cv->v = nv;
+        cv->cap = nc;
+    }
+    cv->v[cv->n++] = c;
+    return 1;
+}
+
+typedef struct {
+    hrec_t *v;
+    int n, cap;
+} histvec_t;
+
+static int push_hist(histvec_t *hv, int prev, int hit) {
+    if (hv->n == hv->cap) {
+        int nc = hv->cap ? 2 * hv->cap : 256;
+        hrec_t *nv = (hrec_t *)realloc(hv->v, sizeof(hrec_t) * nc);
+        if (!nv) return -1;
+        hv->v = nv;
+        hv->cap = nc;
+    }
+    hv->v[hv->n].prev = prev;
+    hv->v[hv->n].hit = hit;
+    return hv->n++;
+}
+
+/* Find one seed.  Returns 0, or -1 on allocation failure. */
+static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *outp, double *outC,
+                    double *out_chi2, int32_t *out_nhits, int32_t *out_hits, int max_out, uint32_t *out_status,
+                    int64_t cnt[3], double marg[3]) {
+    const geom_t *g = f->g;
+    const int L = g->n;
+    uint32_t st = 0;
+    cnt[0] = cnt[1] = cnt[2] = 0;
+    marg[0] = marg[1] = marg[2] = INFINITY;
+    cand_t *cands = (cand_t *)calloc((size_t)f->n_best, sizeof(cand_t));
+    cand_t *nextc = (cand_t *)calloc((size_t)f->n_best, sizeof(cand_t));
+    childvec_t cv = {0, 0, 0};
+    histvec_t hv = {0, 0, 0};
+    if (!cands || !nextc) { free(cands); free(nextc); return -1; }
+
+    /* seed state + seed fit over the three seed hits */
+    cand_t c0;
+    memset(&c0, 0, sizeof(c0));
+    double a[3] = {f->X[sh[0]], f->Y[sh[0]], f->Z[sh[0]]};
+    double b[3] = {f->X[sh[1]], f->Y[sh[1]], f->Z[sh[1]]};
+    double cc[3] = {f->X[sh[2]], f->Y[sh[2]], f->Z[sh[2]]};
+    int seed_layer[3] = {f->HL[sh[0]], f->HL[sh[1]], f->HL[sh[2]]};
+    int ok = 1;
+    for (int k = 0; k < 3; ++k)
+        if (seed_layer[k] < 0 || seed_layer[k] >= L) ok = 0;
+    ok = ok && seed_state(g, a, b, cc, seed_layer[0], c0.p, c0.C);
+    double eta = 0;
+    if (ok) eta = asinh(cot_of(c0.p[5]));
+    if (ok) {
+        for (int k = 0; k < 3; ++k) {
+            int l = seed_layer[k];
+            int hid = sh[k];
+            if (k > 0) {
+                double s, q[6], J[36], Cn[36];
+                if (!path_to_layer(g, c0.p, l, &s)) { ok = 0; break; }
+                helix_move(c0.p, turn_rate(g, c0.p[3]), s, q);
+                prop_jacobian(g, c0.p, l, s, q, J);
+                transport(J, c0.C, Cn);
+                memcpy(c0.p, q, sizeof(q));
+                memcpy(c0.C, Cn, sizeof(Cn));
+            }
+            double H[12], r[2], S[4], Si[4], HC[12];
+            residual(g, l, c0.p, f->X[hid], f->Y[hid], f->Z[hid], r, H);
+            if (!residual_cov(g, l, c0.C, H, S, Si, HC)) { ok = 0; break; }
+            c0.chi2 += kf_update(HC, Si, r, c0.p, c0.C);
+        }
+    }
+    if (!ok || !finite6(c0.p)) {
+        st |= OR_ST_BADSEED;
+        for (int i = 0; i < 6; ++i) outp[i] = NAN;
+        for (int i = 0; i < 36; ++i) outC[i] = NAN;
+        *out_chi2 = NAN;
+        *out_nhits = 0;
+        for (int k = 0; k < max_out; ++k) out_hits[k] = -1;
+        *out_status = st;
+        free(cands); free(nextc);
+        return 0;
+    }
+    c0.n_hits = 3;
+    c0.score = f->cut * 3 - c0.chi2;
+    c0.dir = cot_of(c0.p[5]) >= 0 ? 1 : -1;
+    {
+        int l3 = seed_layer[2];
+        double r3 = hypot(f->X[sh[2]], f->Y[sh[2]]), z3 = f->Z[sh[2]];
+        if (g->kind[l3] == 0) {
+            int pos = -1;
+            for (int i = 0; i < f->n_cyl; ++i)
+                if (f->cyl_sorted[i] == l3) pos = i;
+            c0.next_cyl = (pos + 1 < f->n_cyl) ? pos + 1 : -1;
+        } else {
+            c0.next_cyl = first_cyl_beyond(f, r3);
+        }
+        if (g->kind[l3] == 1) {
+            int pos = -1;
+            for (int i = 0; i < f->n_dsk; ++i)
+                if (f->dsk_sorted[i] == l3) pos = i;
+            int nx = pos + c0.dir;
+            c0.next_dsk = (nx >= 0 && nx < f->n_dsk) ? nx : -1;
+        } else {
+            c0.next_dsk = first_dsk_beyond(f, z3, c0.dir);
+        }
+    }
+    /* tracking region from the seed's eta */
+    int region = 0;
+    while (region + 1 < g->n_regions && eta >= g->edges[region]) region++;
+    uint64_t mask = g->mask[region];
+
+    c0.path = -1;
+    int nc = 1;
+    double last_gap = INFINITY;
+    cands[0] = c0;
+    for (int step = 0; step < 4 * OR_MAXL; ++step) {
+        int any = 0;
+        for (int r = 0; r < nc; ++r)
+            if (!cands[r].done) any = 1;
+        if (!any) break;
+        cv.n = 0;
+        for (int r = 0; r < nc; ++r) {
+            cand_t *c = &cands[r];
+            child_t ch;
+            ch.parent = r;
+            ch.chi2 = 0;
+            ch.layer = -1;
+            if (c->done) {
+                ch.hit = OR_HIT_PASS;
+                ch.score = c->score;
+                if (!push_child(&cv, ch)) goto oom;
+                continue;
+            }
+            double s;
+            int l = next_layer(f, c, mask, &s, &marg[2]);
+            if (l < 0) {
+                c->done = 1;
+                ch.hit = OR_HIT_PASS;
+                ch.score = c->score;
+                if (!push_child(&cv, ch)) goto oom;
+                continue;
+            }
+            /* propagate the parent in place: its children start from here */
+            double q[6], J[36], Cn[36];
+            helix_move(c->p, turn_rate(g, c->p[3]), s, q);
+            prop_jacobian(g, c->p, l, s, q, J);
+            transport(J, c->C, Cn);
+            memcpy(c->p, q, sizeof(q));
+            memcpy(c->C, Cn, sizeof(Cn));
+            cnt[0]++;
+            /* window half-widths from S at the predicted state */
+            double H[12], rr[2], S[4], Si[4], HC[12];
+            residual(g, l, c->p, c->p[0], c->p[1], c->p[2], rr, H);
+            int sok = residual_cov(g, l, c->C, H, S, Si, HC);
+            if (sok) {
+                double wu = sqrt(f->cut * S[0]), wv = sqrt(f->cut * S[3]);
+                int32_t b0 = f->lay_start[(int64_t)ev * L + l], b1 = f->lay_start[(int64_t)ev * L + l + 1];
+                for (int32_t j = b0; j < b1; ++j) {
+                    int hid = f->lay_hits[j];
+                    double u, v;
+                    if (g->kind[l] == 0) {
+                        u = g->rz[l] * wrap_pi(f->PHI[hid] - atan2(c->p[1], c->p[0]));
+                        v = f->Z[hid] - c->p[2];
+                    } else {
+                        double rt = hypot(c->p[0], c->p[1]);
+                        u = rt * wrap_pi(f->PHI[hid] - atan2(c->p[1], c->p[0]));
+                        v = f->RH[hid] - rt;
+                    }
+                    if (fabs(u) > wu || fabs(v) > wv) continue;
+                    cnt[1]++;
+                    double rv[2] = {u, v};
+                    double x2 = chi2_of(rv, Si);
+                    upd_min(&marg[1], fabs(x2 - f->cut) / f->cut);
+                    if (x2 < f->cut) {
+                        ch.hit = hid;
+                        ch.chi2 = x2;
+                        ch.score = c->score + f->cut - x2;
+                        ch.layer = l;
+                        if (!push_child(&cv, ch)) goto oom;
+                    }
+                }
+            } else {
+                st |= OR_ST_BADS;
+            }
+            ch.hit = OR_HIT_MISS;
+            ch.chi2 = 0;
+            ch.score = c->score;
+            ch.layer = l;
+            if (!push_child(&cv, ch)) goto oom;
+        }
+        qsort(cv.v, (size_t)cv.n, sizeof(child_t), cmp_child_q);
+        int keep = cv.n < f->n_best ? cv.n : f->n_best;
+        /* ranking margins on the chi2 scale: the keep/drop boundary of this step,
+         * and (kept until the end) the order of the two best */
+        if (cv.n > f->n_best) {
+            const child_t *u = &cv.v[f->n_best - 1], *w = &cv.v[f->n_best];
+            upd_min(&marg[0], fabs(u->score - w->score) / fmax(1.0, child_chi2_total(cands, u)));
+        }
+        last_gap = INFINITY;
+        if (cv.n > 1) last_gap = fabs(cv.v[0].score - cv.v[1].score) / fmax(1.0, child_chi2_total(cands, &cv.v[0]));
+        for (int i = 0; i < keep; ++i) {
+            const child_t *ch = &cv.v[i];
+            cand_t n = cands[ch->parent];
+            if (ch->hit >= 0) {
+                int l = ch->layer;
+                double H[12], r[2], S[4], Si[4], HC[12];
+                residual(g, l, n.p, f->X[ch->hit], f->Y[ch->hit], f->Z[ch->hit], r, H);
+                residual_cov(g, l, n.C, H, S, Si, HC);
+                double x2 = kf_update(HC, Si, r, n.p, n.C);
+                n.chi2 += x2;
+                n.n_hits++;
+                n.consec = 0;
+                n.score = f->cut * n.n_hits - n.chi2;
+                cnt[2]++;
+            } else if (ch->hit == OR_HIT_MISS) {
+                n.n_miss++;
+                n.consec++;
+                if (n.consec >= f->max_consec) n.done = 2;
+            }
+            if (ch->hit != OR_HIT_PASS) {
+                int id = push_hist(&hv, n.path, ch->hit);
+                if (id < 0) goto oom;
+                n.path = id;
+            }
+            nextc[i] = n;
+        }
+        cand_t *tmp = cands;
+        cands = nextc;
+        nextc = tmp;
+        nc = keep;
+    }
+    upd_min(&marg[0], last_gap);
+    {
+        const cand_t *best = &cands[0];
+        /* walk the history of the best candidate back to the seed */
+        int tmp[4 * OR_MAXL + 8];
+        int nt = 0;
+        for (int id = best->path; id >= 0 && nt < 4 * OR_MAXL; id = hv.v[id].prev)
+            if (hv.v[id].hit >= 0) tmp[nt++] = hv.v[id].hit;
+        int nh = 0;
+        for (int k = 0; k < 3; ++k)
+            if (nh < max_out) out_hits[nh++] = sh[k];
+        for (int k = nt - 1; k >= 0; --k) {
+            if (nh < max_out) out_hits[nh++] = tmp[k];
+            else st |= OR_ST_TRUNC;
+        }
+        for (int k = nh; k < max_out; ++k) out_hits[k] = -1;
+        memcpy(outp, best->p, sizeof(best->p));
+        memcpy(outC, best->C, sizeof(best->C));
+        *out_chi2 = best->chi2;
+        *out_nhits = best->n_hits;
+        if (best->done == 2) st |= OR_ST_MISSSTOP;
+        if (!finite6(best->p)) st |= OR_ST_NONFINITE;
+        *out_status = st;
+    }
+    free(cands); free(nextc); free(cv.v); free(hv.v);
+    return 0;
+oom:
+    free(cands); free(nextc); free(cv.v); free(hv.v);
+    return -1;
+}
+
+/* Track finding over a batch of events.
+ * xyz [3][n_hits] (global hit index), hit_layer[n_hits], event_offsets[n_events+1];
+ * seed_hits [3][n_seeds] (global hit indices, in path order), seed_event[n_seeds].
+ * n_best = 1 is best-hit finding, n_best > 1 keeps the N best candidates.
+ * Outputs per seed: par [6][n], cov [21][n] (packed), chi2, n_hits,
+ * hits [max_out][n] (-1 padded), status, counters [3][n] (candidate-layers,
+ * hits inside the window rectangle, Kalman updates), margins [3][n]
+ * (closest score gap at a ranking decision, closest |chi2 - cut| / cut, closest
+ * geometric decision).  seed_list (or NULL for all) selects which seeds to run;
+ * outputs are indexed by position in seed_list. */
+int or_find(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_layer, const int32_t *event_offsets,
+            int n_events, const int32_t *seed_hits, const int32_t *seed_event, int64_t n_seeds,
+            const int64_t *seed_list, int64_t n_list, int n_best, double chi2_cut, int max_consec,
+            double *out_par, double *out_cov, double *out_chi2, int32_t *out_nhits, int32_t *out_hits, int max_out,
+            uint32_t *out_status, int64_t *out_counters, double *out_margins) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS)) return -1;
+    if (n_best < 1 || max_out < 3 || max_consec < 1) return -1;
+    const int L = g.n;
+    find_ctx_t f;
+    memset(&f, 0, sizeof(f));
+    f.g = &g;
+    f.X = xyz;
+    f.Y = xyz + n_hits;
+    f.Z = xyz + 2 * n_hits;
+    f.cut = chi2_cut;
+    f.max_consec = max_consec;
+    f.n_best = n_best;
+    /* sorted layer lists */
+    for (int l = 0; l < L; ++l) {
+        if (g.kind[l] == 0) f.cyl_sorted[f.n_cyl++] = l;
+        else f.dsk_sorted[f.n_dsk++] = l;
+    }
+    for (int i = 1; i < f.n_cyl; ++i)
+        for (int j = i; j > 0 && g.rz[f.cyl_sorted[j - 1]] > g.rz[f.cyl_sorted[j]]; --j) {
+            int t = f.cyl_sorted[j]; f.cyl_sorted[j] = f.cyl_sorted[j - 1]; f.cyl_sorted[j - 1] = t;
+        }
+    for (int i = 1; i < f.n_dsk; ++i)
+        for (int j = i; j > 0 && g.rz[f.dsk_sorted[j - 1]] > g.rz[f.dsk_sorted[j]]; --j) {
+            int t = f.dsk_sorted[j]; f.dsk_sorted[j] = f.dsk_sorted[j - 1]; f.dsk_sorted[j - 1] = t;
+        }
+    /* per-hit azimuth and radius; per (event, layer) hit lists */
+    double *PHI = (double *)malloc(sizeof(double) * (size_t)(n_hits > 0 ? n_hits : 1));
+    double *RH = (double *)malloc(sizeof(double) * (size_t)(n_hits > 0 ? n_hits : 1));
+    int32_t *start = (int32_t *)calloc((size_t)n_events * L + 1, sizeof(int32_t));
+    int32_t *fill = (int32_t *)calloc((size_t)n_events * L + 1, sizeof(int32_t));
+    int32_t *lh = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_hits > 0 ? n_hits : 1));
+    if (!PHI || !RH || !start || !fill || !lh) { free(PHI); free(RH); free(start); free(fill); free(lh); return -2; }
+    for (int64_t i = 0; i < n_hits; ++i) {
+        PHI[i] = atan2(f.Y[i], f.X[i]);
+        RH[i] = hypot(f.X[i], f.Y[i]);
+    }
+    for (int e = 0; e < n_events; ++e)
+        for (int32_t i = event_offsets[e]; i < event_offsets[e + 1]; ++i) start[(int64_t)e * L + hit_layer[i] + 1]++;
+    for (int64_t k = 0; k < (int64_t)n_events * L; ++k) start[k + 1] += start[k];
+    for (int e = 0; e < n_events; ++e)
+        for (int32_t i = event_offsets[e]; i < event_offsets[e + 1]; ++i) {
+            int64_t key = (int64_t)e * L + hit_layer[i];
+            lh[start[key] + fill[key]++] = i;
+        }
+    f.PHI = PHI;
+    f.RH = RH;
+    f.lay_start = start;
+    f.lay_hits = lh;
+    f.HL = hit_layer;
+    int64_t nl = seed_list ? n_list : n_seeds;
+    int rc = 0;
+    for (int64_t k = 0; k < nl && rc == 0; ++k) {
+        int64_t sidx = seed_list ? seed_list[k] : k;
+        int32_t sh[3] = {seed_hits[sidx], seed_hits[n_seeds + sidx], seed_hits[2 * n_seeds + sidx]};
+        double p[6], C[36], chi2, marg[3];
+        int32_t nh, hits[4 * OR_MAXL + 8];
+        uint32_t st;
+        int64_t cnt[3];
+        int mo = max_out < 4 * OR_MAXL ? max_out : 4 * OR_MAXL;
+        int ev = seed_event[sidx];
+        if (ev < 0 || ev >= n_events || sh[0] < 0 || sh[1] < 0 || sh[2] < 0 || sh[0] >= n_hits || sh[1] >= n_hits ||
+            sh[2] >= n_hits) {
+            rc = -3;
+            break;
+        }
+        if (find_one(&f, ev, sh, p, C, &chi2, &nh, hits, mo, &st, cnt, marg)) { rc = -2; break; }
+        for (int i = 0; i < 6; ++i) out_par[(int64_t)i * nl + k] = p[i];
+        pack21(C, out_cov + k, nl);
+        out_chi2[k] = chi2;
+        out_nhits[k] = nh;
+        for (int j = 0; j < max_out; ++j) out_hits[(int64_t)j * nl + k] = j < mo ? hits[j] : -1;
+        out_status[k] = st;
+        for (int j = 0; j < 3; ++j) out_counters[(int64_t)j * nl + k] = cnt[j];
+        for (int j = 0; j < 3; ++j) out_margins[(int64_t)j * nl + k] = marg[j];
+    }
+    free(PHI); free(RH); free(start); free(fill); free(lh);
+    return rc;
+}

@@ -1,0 +1,273 @@
+"""Seeded synthetic events: particles, layer crossings, smeared hits, noise, truth seeds.
+
+Every random number comes from a counter-based Philox stream keyed by
+(base seed 181104141, config id, event index), so an event is reproducible from
+its three integers alone.
+
+Particle motion (physics, not the fitting method): a particle of charge q and
+transverse momentum pT in a uniform field Bz turns at the rate
+h = -q * K_FIELD * Bz / pT per unit transverse path length s.  From the vertex
+(0, 0, z0) with azimuth phi0 and polar angle theta,
+    x(s) = (sin(phi0 + h s) - sin(phi0)) / h,  y(s) = -(cos(phi0 + h s) - cos(phi0)) / h,
+    z(s) = z0 + s cot(theta),  with the straight line as the h = 0 case.
+Hits are made only on the outward half-turn (0 < h s < pi), at most one per layer.
+Cylinder crossings are located by bisection on the transverse radius, which grows
+monotonically along the outward half-turn.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .configs import CONFIG_IDS, K_FIELD, get_config
+
+BASE_SEED = 181104141
+_S_MAX_STRAIGHT = 5000.0  # cm; path limit for a straight (B = 0) track
+
+
+def _rng(config: str, event: int, base_seed: int = BASE_SEED) -> np.random.Generator:
+    key = (int(base_seed) << 64) | (CONFIG_IDS[config] << 32) | (int(event) & 0xFFFFFFFF)
+    return np.random.Generator(np.random.Philox(key=key))
+
+
+def _helix_xy(h, phi0, s):
+    """Transverse position after path s from the origin (vectorised, float64)."""
+    h = np.asarray(h, dtype=np.float64)
+    straight = h == 0.0
+    hs = np.where(straight, 1.0, h)
+    x = np.where(straight, s * np.cos(phi0), (np.sin(phi0 + h * s) - np.sin(phi0)) / hs)
+    y = np.where(straight, s * np.sin(phi0), -(np.cos(phi0 + h * s) - np.cos(phi0)) / hs)
+    return x, y
+
+
+def _cylinder_crossings(h, phi0, radii, s_max):
+    """Path length of each particle's outward crossing of each radius (NaN if none)."""
+    P, L = h.shape[0], radii.shape[0]
+    hh = np.repeat(h[:, None], L, axis=1)
+    pp = np.repeat(phi0[:, None], L, axis=1)
+    R = np.broadcast_to(radii[None, :], (P, L))
+    hi = np.repeat(s_max[:, None], L, axis=1).copy()
+    xe, ye = _helix_xy(hh, pp, hi)
+    reach = np.hypot(xe, ye) >= R
+    lo = np.zeros_like(hi)
+    for _ in range(90):
+        mid = 0.5 * (lo + hi)
+        xm, ym = _helix_xy(hh, pp, mid)
+        inside = np.hypot(xm, ym) < R
+        lo = np.where(inside, mid, lo)
+        hi = np.where(inside, hi, mid)
+    s = 0.5 * (lo + hi)
+    return np.where(reach, s, np.nan)
+
+
+@dataclass
+class Batch:
+    """A batch of events, hit arrays concatenated event after event.
+
+    Hit arrays are indexed by the global hit index; `event_offsets[e]` is the first
+    hit of event e.  Seeds are the first three hits (in path order) of every
+    particle with at least three hits, in particle order.
+    """
+    config: str
+    layers: list
+    bz: float
+    xyz: np.ndarray            # float32 [3, n_hits] SoA (the canonical input)
+    xyz64: np.ndarray          # float64 [3, n_hits], values before rounding to float32
+    layer: np.ndarray          # int32 [n_hits]
+    hit_particle: np.ndarray   # int32 [n_hits], global particle id, -1 for noise
+    event_offsets: np.ndarray  # int32 [n_events + 1]
+    true_state: np.ndarray     # float64 [6, n_hits]: (x, y, z, q/pT, phi, theta) at the hit, NaN for noise
+    true_xyz: np.ndarray       # float64 [3, n_hits]: unsmeared crossing point, NaN for noise
+    seed_hits: np.ndarray      # int32 [3, n_seeds]
+    seed_event: np.ndarray     # int32 [n_seeds]
+    seed_particle: np.ndarray  # int32 [n_seeds]
+    track_hits: np.ndarray     # int32 [max_hits, n_seeds], the particle's hits in path order, -1 padded
+    particle_nhits: np.ndarray  # int32 [n_particles]
+    particle_event: np.ndarray  # int32 [n_particles]
+    particle_par: np.ndarray   # float64 [6, n_particles]: state at the vertex
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_hits(self) -> int:
+        return int(self.layer.shape[0])
+
+    @property
+    def n_events(self) -> int:
+        return int(self.event_offsets.shape[0] - 1)
+
+    @property
+    def n_seeds(self) -> int:
+        return int(self.seed_event.shape[0])
+
+    def hit_bytes(self) -> int:
+        return int(self.xyz.nbytes + self.layer.nbytes + self.event_offsets.nbytes)
+
+
+def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: int | None = None,
+               base_seed: int = BASE_SEED, ineff: float | None = None, noise_scale: float = 1.0,
+               eta_max: float | None = None, smear: bool = True):
+    """One event as a dict of per-event arrays (local hit and particle indices)."""
+    cfg = get_config(config)
+    layers = cfg["layers"]
+    rng = _rng(config, event, base_seed)
+    P = int(cfg["n_tracks"] if n_tracks is None else n_tracks)
+    eta_max = float(cfg["eta_max"] if eta_max is None else eta_max)
+    ineff = float(cfg["ineff"] if ineff is None else ineff)
+    bz = float(cfg["bz"])
+
+    # Particle kinematics, drawn in a fixed order from the event's stream.
+    u_pt = rng.random(P)
+    if cfg["pt_spectrum"] == "flat":
+        pt = cfg["pt_min"] + (cfg["pt_max"] - cfg["pt_min"]) * u_pt
+    else:  # density ~ pT^-3 on [pt_min, pt_max], inverse CDF
+        a, b = cfg["pt_min"] ** -2, cfg["pt_max"] ** -2
+        pt = (a - u_pt * (a - b)) ** -0.5
+    q = np.where(rng.random(P) < 0.5, -1.0, 1.0)
+    phi0 = -np.pi + 2.0 * np.pi * rng.random(P)
+    eta = -eta_max + 2.0 * eta_max * rng.random(P)
+    z0 = -cfg["z0_half"] + 2.0 * cfg["z0_half"] * rng.random(P)
+    theta = 2.0 * np.arctan(np.exp(-eta))
+    cot = np.sinh(eta)
+    h = -q * K_FIELD * bz / pt
+    s_max = np.where(h == 0.0, _S_MAX_STRAIGHT, np.pi / np.where(h == 0.0, 1.0, np.abs(h)))
+
+    kinds = np.array([d["kind"] for d in layers])
+    rz = np.array([d["r_or_z"] for d in layers], dtype=np.float64)
+    lo = np.array([d["lo"] for d in layers], dtype=np.float64)
+    hi = np.array([d["hi"] for d in layers], dtype=np.float64)
+    su = np.array([d["sigma_u"] for d in layers], dtype=np.float64)
+    sv = np.array([d["sigma_v"] for d in layers], dtype=np.float64)
+    L = len(layers)
+
+    # Path length of each (particle, layer) crossing, NaN where there is none.
+    S = np.full((P, L), np.nan)
+    cyl = np.where(kinds == 0)[0]
+    dsk = np.where(kinds == 1)[0]
+    if cyl.size:
+        S[:, cyl] = _cylinder_crossings(h, phi0, rz[cyl], s_max)
+    if dsk.size:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            sd = (rz[dsk][None, :] - z0[:, None]) / cot[:, None]
+        ok = np.isfinite(sd) & (sd > 0) & (sd < s_max[:, None])
+        S[:, dsk] = np.where(ok, sd, np.nan)
+    Sf = np.where(np.isnan(S), 1.0, S)
+    X, Y = _helix_xy(np.repeat(h[:, None], L, 1), np.repeat(phi0[:, None], L, 1), Sf)
+    Z = z0[:, None] + Sf * cot[:, None]
+    Rt = np.hypot(X, Y)
+    in_ext = np.where(kinds[None, :] == 0, (Z >= lo[None, :]) & (Z <= hi[None, :]),
+                      (Rt >= lo[None, :]) & (Rt <= hi[None, :]))
+    crossed = ~np.isnan(S) & in_ext
+    # Inefficiency: one uniform per (particle, layer), drawn for every pair.
+    kept = crossed & (rng.random((P, L)) >= ineff)
+
+    # Gaussian smearing: two normals per (particle, layer), drawn for every pair.
+    g = rng.standard_normal((P, L, 2)) if smear else np.zeros((P, L, 2))
+    phit = np.arctan2(Y, X)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ph_s = phit + g[:, :, 0] * su[None, :] / np.where(Rt > 0, Rt, 1.0)
+    is_cyl = kinds[None, :] == 0
+    r_s = np.where(is_cyl, rz[None, :], Rt + g[:, :, 1] * sv[None, :])
+    z_s = np.where(is_cyl, Z + g[:, :, 1] * sv[None, :], rz[None, :])
+    xs, ys = r_s * np.cos(ph_s), r_s * np.sin(ph_s)
+
+    # Signal hits in particle order, then path order within a particle.
+    pid_l, lay_l = np.nonzero(kept)
+    order = np.lexsort((np.where(kept, S, np.inf)[pid_l, lay_l], pid_l))
+    pid_l, lay_l = pid_l[order], lay_l[order]
+    sig_xyz = np.stack([xs[pid_l, lay_l], ys[pid_l, lay_l], z_s[pid_l, lay_l]])
+    sig_true_xyz = np.stack([X[pid_l, lay_l], Y[pid_l, lay_l], Z[pid_l, lay_l]])
+    ss = S[pid_l, lay_l]
+    sig_state = np.stack([X[pid_l, lay_l], Y[pid_l, lay_l], Z[pid_l, lay_l],
+                          (q / pt)[pid_l], phi0[pid_l] + h[pid_l] * ss, theta[pid_l]])
+    sig_state[4] = np.arctan2(np.sin(sig_state[4]), np.cos(sig_state[4]))
+
+    # Noise hits, uniform in (phi, z) on cylinders and uniform in area on disks.
+    if cfg["noise_mode"] == "none" and n_noise is None:
+        n_per_layer = np.zeros(L, dtype=np.int64)
+    elif n_noise is not None or cfg["noise_mode"] == "total":
+        tot = int(cfg["noise"] if n_noise is None else n_noise)
+        tot = int(round(tot * noise_scale))
+        n_per_layer = np.full(L, tot // L, dtype=np.int64)
+        n_per_layer[0] += tot - int(n_per_layer.sum())
+    else:
+        n_sig = np.bincount(lay_l, minlength=L)
+        n_per_layer = np.round(cfg["noise"] * noise_scale * n_sig).astype(np.int64)
+    nz_layer = np.repeat(np.arange(L), n_per_layer)
+    un = rng.random((nz_layer.size, 2))
+    nph = -np.pi + 2.0 * np.pi * un[:, 0]
+    k = kinds[nz_layer]
+    nr = np.where(k == 0, rz[nz_layer], np.sqrt(lo[nz_layer] ** 2 + un[:, 1] * (hi[nz_layer] ** 2 - lo[nz_layer] ** 2)))
+    nzc = np.where(k == 0, lo[nz_layer] + un[:, 1] * (hi[nz_layer] - lo[nz_layer]), rz[nz_layer])
+    noise_xyz = np.stack([nr * np.cos(nph), nr * np.sin(nph), nzc])
+
+    n_sig_hits = pid_l.size
+    xyz64 = np.concatenate([sig_xyz, noise_xyz], axis=1)
+    layer = np.concatenate([lay_l, nz_layer]).astype(np.int32)
+    particle = np.concatenate([pid_l, np.full(nz_layer.size, -1)]).astype(np.int32)
+    true_state = np.concatenate([sig_state, np.full((6, nz_layer.size), np.nan)], axis=1)
+    true_xyz = np.concatenate([sig_true_xyz, np.full((3, nz_layer.size), np.nan)], axis=1)
+    nhits_p = np.bincount(pid_l, minlength=P).astype(np.int32)
+    first = np.concatenate([[0], np.cumsum(nhits_p)[:-1]]).astype(np.int64)
+    return dict(xyz64=xyz64, layer=layer, particle=particle, true_state=true_state,
+                true_xyz=true_xyz, nhits_p=nhits_p, first_hit_p=first, n_signal=n_sig_hits,
+                par0=np.stack([np.zeros(P), np.zeros(P), z0, q / pt, phi0, theta]))
+
+
+def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int = BASE_SEED,
+               min_seed_hits: int = 3, **kw) -> Batch:
+    """Concatenate events.  `n_tracks` / `n_noise` may be scalars or per-event lists."""
+    cfg = get_config(config)
+    events = list(events)
+    E = len(events)
+
+    def per_event(v, i):
+        if v is None or np.isscalar(v):
+            return v
+        return v[i]
+
+    parts = [make_event(config, ev, per_event(n_tracks, i), per_event(n_noise, i), base_seed, **kw)
+             for i, ev in enumerate(events)]
+    max_hits = max([1] + [int(p["nhits_p"].max(initial=0)) for p in parts])
+    offs = np.zeros(E + 1, dtype=np.int64)
+    xyz64, layer, hp, ts, tx = [], [], [], [], []
+    seed_hits, seed_event, seed_part, track_hits = [], [], [], []
+    p_nh, p_ev, p_par = [], [], []
+    pbase = 0
+    for i, p in enumerate(parts):
+        base = offs[i]
+        n = p["layer"].shape[0]
+        offs[i + 1] = base + n
+        xyz64.append(p["xyz64"]); layer.append(p["layer"]); ts.append(p["true_state"]); tx.append(p["true_xyz"])
+        hp.append(np.where(p["particle"] >= 0, p["particle"] + pbase, -1).astype(np.int32))
+        P = p["nhits_p"].shape[0]
+        ok = np.nonzero(p["nhits_p"] >= min_seed_hits)[0]
+        f = p["first_hit_p"][ok]
+        seed_hits.append(np.stack([f, f + 1, f + 2]) + base)
+        seed_event.append(np.full(ok.size, i))
+        seed_part.append(ok + pbase)
+        th = np.full((max_hits, ok.size), -1, dtype=np.int64)
+        for j in range(max_hits):
+            valid = j < p["nhits_p"][ok]
+            th[j, valid] = f[valid] + j + base
+        track_hits.append(th)
+        p_nh.append(p["nhits_p"]); p_ev.append(np.full(P, i)); p_par.append(p["par0"])
+        pbase += P
+    if offs[-1] >= (1 << 28) - 2:
+        raise ValueError("too many hits for 28-bit hit indices")
+    xyz64 = np.concatenate(xyz64, axis=1)
+    return Batch(
+        config=config, layers=[dict(d) for d in cfg["layers"]], bz=float(cfg["bz"]),
+        xyz=np.ascontiguousarray(xyz64.astype(np.float32)), xyz64=xyz64,
+        layer=np.concatenate(layer).astype(np.int32), hit_particle=np.concatenate(hp).astype(np.int32),
+        event_offsets=offs.astype(np.int32), true_state=np.concatenate(ts, axis=1),
+        true_xyz=np.concatenate(tx, axis=1),
+        seed_hits=np.ascontiguousarray(np.concatenate(seed_hits, axis=1).astype(np.int32)),
+        seed_event=np.concatenate(seed_event).astype(np.int32),
+        seed_particle=np.concatenate(seed_part).astype(np.int32),
+        track_hits=np.ascontiguousarray(np.concatenate(track_hits, axis=1).astype(np.int32)),
+        particle_nhits=np.concatenate(p_nh).astype(np.int32),
+        particle_event=np.concatenate(p_ev).astype(np.int32),
+        particle_par=np.concatenate(p_par, axis=1),
+        meta=dict(events=events, base_seed=base_seed),
+    )
