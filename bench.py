@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the Kalman-filter finding step on GB300 (one JSON line on stdout).
+
+A step is one pass of the whole finding path over one batch: hit binning
+(mkf_hits_bin) and seeded N-best finding (mkf_find: seed state and seed fit,
+per-layer propagation, covariance transport, window search, chi2, N-best
+selection, Kalman updates, output).  Workload: 20 synthetic events x 2000
+tracks, 10 barrel cylinders + 2 x 5 endcap disks in 3.8 T, |eta| < 2.4, 2 %
+hit inefficiency, uniform noise at 5x each layer's signal hits, N = 10 best
+candidates kept per seed, chi2 cut 30.  Metric: KF candidate-layer updates/s
+(one unit = one candidate propagated to one layer and searched).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank processes its own 20 events (weak scaling, no
+collective on the data path); rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "KF candidate-layer updates/s"
+UNIT = "candidate-layer updates/s"
+CONFIG = "find20"
+EVENTS = 20
+N_BEST = 10
+CHI2_CUT = 30.0
+MAX_CONSEC = 3
+WORKLOAD = ("KF track finding, 20 events x 2000 tracks: 10 barrel cylinders r=4..100 cm + 2x5 endcap disks "
+            "|z|=120..270 cm, 3.8 T, |eta|<2.4, pT 0.5-10 GeV, 2% hit inefficiency, uniform noise 5x signal "
+            "per layer; N=10 best candidates per seed, chi2 cut 30")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def allreduce_max(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+def oracle_rate(batch, target_s: float):
+    """Candidate-layer updates/s of the oracle on a sample of seeds of `batch`,
+    sized to take about target_s seconds on one host core."""
+    import oracle as O
+    geo = O.geometry_for(batch)
+    xyz = batch.xyz.astype(np.float64)
+    rng = np.random.default_rng(7)
+    order = rng.permutation(batch.n_seeds)
+    done, units, t_used = 0, 0, 0.0
+    n = 20
+    while t_used < target_s and done < batch.n_seeds:
+        sel = np.sort(order[done:done + n])
+        t0 = time.perf_counter()
+        r = O.find(geo, xyz, batch.layer, batch.event_offsets, batch.seed_hits, batch.seed_event, n_best=N_BEST,
+                   chi2_cut=CHI2_CUT, max_consec=MAX_CONSEC, seed_list=sel)
+        t_used += time.perf_counter() - t0
+        units += int(r["counters"][0].sum())
+        done += sel.size
+        rate = max(t_used, 1e-6) / done
+        n = int(min(max(20, (target_s - t_used) / rate), batch.n_seeds - done))
+        if n <= 0:
+            break
+    return units / t_used, done, t_used
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    from paper_1811_04141_gb300 import Context, build, flops
+    from synth import make_batch
+
+    if local == 0 or world == 1:
+        build.build()
+    barrier(pg)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    events = list(range(rank * EVENTS, (rank + 1) * EVENTS))
+    batch = make_batch(CONFIG, events)
+    ctx = Context(local, torch.cuda.current_stream(dev))
+    ctx.geometry_load(batch.layers, batch.bz)
+    to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    xyz, layer = to(batch.xyz, torch.float32), to(batch.layer, torch.int32)
+    evo, sh, se = to(batch.event_offsets, torch.int32), to(batch.seed_hits, torch.int32), to(batch.seed_event,
+                                                                                             torch.int32)
+    max_out = len(batch.layers) + 3
+    bins = ctx.hits_bin(xyz, layer, evo)
+    out = ctx.find(bins, sh, se, n_best=N_BEST, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.hits_bin(xyz, layer, evo, bins)
+        ctx.find(bins, sh, se, n_best=N_BEST, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=out)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    ctx.sync()
+    cl = int(out["counters"][0].sum().item())
+    ht = int(out["counters"][1].sum().item())
+    up = int(out["counters"][2].sum().item())
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(pg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stream = torch.cuda.current_stream(dev)
+    for i in range(K):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        ctx.hits_bin(xyz, layer, evo, bins)
+        ev[i][1].record(stream)
+        ctx.find(bins, sh, se, n_best=N_BEST, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out,
+                 out=out)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ctx.sync()
+    step_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in ev]))
+    find_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    bin_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    step_ms_max = allreduce_max(pg, step_ms)
+    units_all = allreduce_sum(pg, cl)
+    value = units_all / (step_ms_max * 1e-3)
+
+    # roofline of the dominant kernel (find): FP32 ALU bound
+    fl = flops.find_flops(cl, ht, up)
+    achieved = fl / (find_ms * 1e-3) / 1e12
+    peak_mhz = 2070.0
+    peak = flops.fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count, peak_mhz)
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "find_kernel", "kernel_ms": round(find_ms, 4),
+                "flops_per_launch": fl, "peak_basis": f"{peak_mhz:.0f} MHz x SMs x 128 FP32 lanes x 2 (derived)"}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+        h_xyz, h_layer, h_evo = pin(batch.xyz), pin(batch.layer), pin(batch.event_offsets)
+        h_sh, h_se = pin(batch.seed_hits), pin(batch.seed_event)
+        outs_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items() if v is not None}
+        d_xyz, d_layer, d_evo = torch.empty_like(xyz), torch.empty_like(layer), torch.empty_like(evo)
+        d_sh, d_se = torch.empty_like(sh), torch.empty_like(se)
+        h2d = sum(t.numel() * t.element_size() for t in (h_xyz, h_layer, h_evo, h_sh, h_se))
+        d2h = sum(t.numel() * t.element_size() for t in outs_h.values())
+
+        def e2e_step():
+            d_xyz.copy_(h_xyz, non_blocking=True)
+            d_layer.copy_(h_layer, non_blocking=True)
+            d_evo.copy_(h_evo, non_blocking=True)
+            d_sh.copy_(h_sh, non_blocking=True)
+            d_se.copy_(h_se, non_blocking=True)
+            ctx.hits_bin(d_xyz, d_layer, d_evo, bins)
+            ctx.find(bins, d_sh, d_se, n_best=N_BEST, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out,
+                     out=out)
+            for k, v in outs_h.items():
+                v.copy_(out[k], non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for i in range(K):
+            flush.fill_(float(i))
+            es[i][0].record(stream)
+            e2e_step()
+            es[i][1].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = allreduce_max(pg, float(np.mean([a.elapsed_time(b) for a, b in es])))
+        e2e = {"value": units_all / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, nseeds, secs = oracle_rate(batch, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nseeds} randomly chosen seeds of the {batch.n_seeds} in the workload (all hits of "
+                         f"their events), {secs:.1f} s on one host core, FP64"}
+
+    launches_per_step = 7  # bin_keys, scan_tiles, scan_blocksums, scan_write, scatter, bin_sort, find
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(step_ms_max, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events_per_gpu": EVENTS, "tracks_per_event": 2000, "n_best": N_BEST,
+                   "chi2_cut": CHI2_CUT, "hits_per_gpu": batch.n_hits, "seeds_per_gpu": batch.n_seeds,
+                   "cand_layers_per_step_per_gpu": cl, "hits_tested_per_step_per_gpu": ht,
+                   "updates_per_step_per_gpu": up, "bin_ms": round(bin_ms, 4), "find_ms": round(find_ms, 4),
+                   "l2": "flushed between steps (256 MiB write, outside the per-step CUDA events)",
+                   "wall_s_timed_region": round(wall, 3), "parallelism": f"events sharded, {world} GPU(s)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "gpu_launches": launches_per_step * K,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_reference(args, world, rank, local, pg):
+    """The FP64 oracle on the host cores, same metric and workload (a bounded
+    sample of seeds per step)."""
+    if rank != 0:
+        return
+    from synth import make_batch
+    batch = make_batch(CONFIG, list(range(EVENTS)))
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup) * 2)
+    for _ in range(args.warmup):
+        oracle_rate(batch, per_step / 4)
+    rates, seeds, secs = [], 0, 0.0
+    for _ in range(args.steps):
+        r, n, s = oracle_rate(batch, per_step)
+        rates.append(r)
+        seeds += n
+        secs += s
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events": EVENTS, "tracks_per_event": 2000, "n_best": N_BEST,
+                       "chi2_cut": CHI2_CUT},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{seeds} seeds sampled over {args.steps} steps of about {per_step:.1f} s"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local, pg)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * mkf.h -- C ABI of the GB300 (sm_103a) Kalman-filter track fitting and finding
+ * library (libmkf.so).
+ *
+ * Method: "Parallelized and Vectorized Tracking Using Kalman Filters with CMS
+ * Detector Geometry and Events" (mkFit).  The library runs the data-parallel
+ * per-layer step of that method on every track candidate at once: helix
+ * propagation in a uniform solenoid field to a barrel cylinder or an endcap
+ * disk (Sec. 1, extension of the Kalman-filter and propagation equations to
+ * the endcap case), transport of the 6x6 symmetric covariance, a hit search in
+ * per-layer windows (Sec. 2.1, hit search windows in the layer description),
+ * chi2 of each compatible hit, best-hit or N-best branching where only the
+ * selected extensions receive the final Kalman update (Sec. 1, the selection of
+ * the best chi2 extensions before the Kalman update), and the Kalman update.
+ * The same update along fixed hit lists is the track fit (Sec. 1, vectorised
+ * fitting).  Hits and seeds are provided by the caller and found tracks are
+ * copied back to the caller (Sec. 2.2).
+ *
+ * Conventions (all entry points):
+ *  - Every pointer documented as "device" is caller-owned CUDA device memory on
+ *    the context's device; the library only borrows it for the duration of the
+ *    work it enqueues.  "Host" pointers are read before the call returns.
+ *  - Work is enqueued asynchronously on the context's stream; outputs are valid
+ *    once that stream has been synchronised (mkf_sync does that and also reports
+ *    faults that kernels recorded on the device).
+ *  - Track state p = (x, y, z, q/pT, phi, theta) in cm, cm, cm, c/GeV, rad, rad:
+ *    global position on the current layer surface, azimuth phi of the momentum,
+ *    polar angle theta.  Arrays of states are structure-of-arrays with the track
+ *    index fastest: par[i * n + t] for i in 0..5; covariances are the 21-value
+ *    packed lower triangle, cov[k * n + t] with k = i (i + 1) / 2 + j, i >= j.
+ *  - Errors: a negative mkf_status; nothing aborts, traps or prints.  Per-track
+ *    problems are MKF_ST_* status bits, not call errors.
+ */
+#ifndef MKF_H
+#define MKF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mkf_status;
+
+#define MKF_OK 0
+#define MKF_ERR_ARG (-1)          /* invalid argument (NULL, negative size, bad parameter) */
+#define MKF_ERR_GEOMETRY (-2)     /* invalid geometry, or no geometry loaded, or bins built for another geometry */
+#define MKF_ERR_CAPACITY (-3)     /* a size exceeds a documented maximum */
+#define MKF_ERR_CUDA (-4)         /* a CUDA runtime call failed (allocation, launch, copy) */
+#define MKF_ERR_DEVICE_CHECK (-5) /* a kernel found an invalid value in device input (see mkf_sync) */
+
+/* Per-track status bits (outputs of mkf_fit / mkf_find). */
+#define MKF_ST_UNREACHABLE 1u /* fit: a hit's layer could not be reached; the hit was skipped */
+#define MKF_ST_BADSEED 2u     /* the three seed hits do not define a track; outputs are NaN */
+#define MKF_ST_NONFINITE 4u   /* a non-finite value appeared in the state */
+#define MKF_ST_BADS 8u        /* a residual covariance was not positive definite; that update was skipped */
+#define MKF_ST_MISSSTOP 16u   /* find: the best candidate stopped after max_consec_miss misses in a row */
+#define MKF_ST_TRUNC 32u      /* find: the hit list did not fit into max_out entries */
+
+#define MKF_MAX_LAYERS 64
+#define MKF_MAX_REGIONS 16
+#define MKF_MAX_NBEST 16
+#define MKF_MAX_HITS ((1 << 28) - 2) /* hit indices are carried in 28 bits */
+
+typedef struct mkf_ctx mkf_ctx;         /* opaque, library-owned */
+typedef struct mkf_hitbins mkf_hitbins; /* opaque, library-owned device storage */
+
+/* Create a context on CUDA device `cuda_device`, enqueueing work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * *out receives the context.  Errors: MKF_ERR_ARG, MKF_ERR_CUDA. */
+mkf_status mkf_create(mkf_ctx **out, int32_t cuda_device, void *cuda_stream);
+
+/* Release the context and its scratch memory (after synchronising its stream). */
+void mkf_destroy(mkf_ctx *ctx);
+
+/* Change the stream later calls enqueue on. */
+mkf_status mkf_set_stream(mkf_ctx *ctx, void *cuda_stream);
+
+/* Synchronise the context's stream and report any fault a kernel recorded in
+ * device memory since the last mkf_sync (MKF_ERR_DEVICE_CHECK; the record is
+ * then cleared) or a CUDA error (MKF_ERR_CUDA). */
+mkf_status mkf_sync(mkf_ctx *ctx);
+
+/* Human-readable name of a status code (static string). */
+const char *mkf_status_string(mkf_status s);
+
+/* ------------------------------------------------------------------------ */
+/* Geometry (Sec. 2.1: a vector of per-layer descriptions with dimensions,   */
+/* hit-search parameters and type; per-region layer plans)                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t kind;      /* 0 = barrel cylinder, 1 = endcap disk */
+    float r_or_z;      /* cylinder radius R > 0, or disk position Z (signed), cm */
+    float lo, hi;      /* extent: z range (cylinder) or r range (disk), cm, lo < hi */
+    float sigma_u;     /* hit resolution along r-phi, cm (> 0) */
+    float sigma_v;     /* hit resolution along z (cylinder) or r (disk), cm (> 0) */
+    int32_t n_phi_bins; /* hit bins in phi, 1..4096 */
+    int32_t n_zr_bins;  /* hit bins in z (cylinder) or r (disk), 1..4096 */
+} mkf_layer;
+
+typedef struct {
+    int32_t n_layers;         /* number of entries in layer_ids */
+    const int32_t *layer_ids; /* host; the layers this region's candidates may visit */
+} mkf_plan;
+
+/* Load the detector description (host arrays, copied).
+ *  layers[n_layers], 1 <= n_layers <= MKF_MAX_LAYERS.
+ *  plans[n_plans]: tracking regions (Sec. 2.1: steering parameters per region;
+ *  the paper uses five eta regions).  A seed belongs to region r when
+ *  region_eta_edges[r-1] <= eta < region_eta_edges[r] (eta of the three-hit seed
+ *  estimate); region_eta_edges has n_plans - 1 ascending entries.  Within its
+ *  region a candidate visits only the plan's layers, in the order its helix
+ *  reaches them.  n_plans = 0 (plans and edges may be NULL) is one region with
+ *  every layer.
+ *  bz_tesla: uniform solenoid field (0 allowed: straight tracks).
+ * Errors: MKF_ERR_ARG, MKF_ERR_GEOMETRY, MKF_ERR_CAPACITY. */
+mkf_status mkf_geometry_load(mkf_ctx *ctx, const mkf_layer *layers, int32_t n_layers, const mkf_plan *plans,
+                             int32_t n_plans, const float *region_eta_edges, float bz_tesla);
+
+/* ------------------------------------------------------------------------ */
+/* Hit binning (per event and layer, phi x z or phi x r bins)               */
+/* ------------------------------------------------------------------------ */
+
+/* Sort hits into per-(event, layer) bins of the loaded geometry: phi x z on
+ * cylinders, phi x r on disks (the acceleration structure behind Sec. 2.1's hit
+ * search windows).
+ *  xyz:           device float [3][n_hits], SoA global coordinates.
+ *  layer:         device int32 [n_hits], layer id of each hit.
+ *  event_offsets: device int32 [n_events + 1], first hit of each event,
+ *                 ascending, event_offsets[0] = 0, event_offsets[n_events] = n_hits.
+ * *inout: NULL to allocate a new bin store, or a store from an earlier call to
+ * refill (its device memory is reused, grown only when too small).  Hits with
+ * an invalid layer id are dropped and recorded as a device fault (mkf_sync).
+ * The order of hits within one bin is ascending original index.
+ * Errors: MKF_ERR_ARG, MKF_ERR_GEOMETRY (no geometry), MKF_ERR_CAPACITY
+ * (n_hits > MKF_MAX_HITS), MKF_ERR_CUDA. */
+mkf_status mkf_hits_bin(mkf_ctx *ctx, const float *xyz, const int32_t *layer, const int32_t *event_offsets,
+                        int32_t n_events, int32_t n_hits, mkf_hitbins **inout);
+
+/* Free a bin store (after the work that uses it has completed). */
+void mkf_hitbins_free(mkf_hitbins *bins);
+
+/* Sizes of a bin store: hits, events, bins (n_events * bins_per_event).
+ * Errors: MKF_ERR_ARG. */
+mkf_status mkf_hitbins_info(const mkf_hitbins *bins, int32_t *n_hits, int32_t *n_events, int64_t *n_bins);
+
+/* Copy a bin store into caller-owned device buffers (asynchronous, on the
+ * context's stream; any pointer may be NULL to skip that array):
+ *  rec [n_hits][4] float: binned hits (x, y, z on cylinders or r on disks, the
+ *      original index as int32 bits), grouped by bin, ascending original index
+ *      within a bin;
+ *  inv [n_hits] int32: binned position of each original hit (-1 if dropped);
+ *  offsets [n_bins + 1] int32: CSR offsets; bin id = event * bins_per_event +
+ *      layer_base + phi_bin * n_zr_bins + zr_bin, with layer_base the sum of
+ *      n_phi_bins * n_zr_bins over lower layer ids, phi_bin =
+ *      floor((phi + pi) * n_phi_bins / 2pi), zr_bin = floor((zr - lo) *
+ *      n_zr_bins / (hi - lo)), both clamped into range.
+ * Errors: MKF_ERR_ARG, MKF_ERR_CUDA. */
+mkf_status mkf_hitbins_export(mkf_ctx *ctx, const mkf_hitbins *bins, float *rec, int32_t *inv, int32_t *offsets);
+
+/* ------------------------------------------------------------------------ */
+/* Fit (Sec. 1: Kalman-filter fitting along known hits)                      */
+/* ------------------------------------------------------------------------ */
+
+/* Kalman fit of n tracks along fixed hit lists.
+ *  xyz [3][n_hits], hit_layer [n_hits]: device, as for mkf_hits_bin.
+ *  hit_idx: device int32 [max_hits][n] (track fastest), the track's hits in
+ *           path order; -1 entries are skipped.  1 <= max_hits <= 64.
+ *  seed_par [6][n], seed_cov [21][n]: device, the starting state on the surface
+ *           of the first hit; both NULL = seed each track from its first three
+ *           hits (circle through three points, straight line in arc length-z).
+ *  The first hit is applied without propagation; every later hit is reached by
+ *  propagating to its layer's surface.
+ *  Outputs (device, caller-owned): out_par [6][n], out_cov [21][n] -- state on
+ *  the surface of the last hit used; chi2 [n] -- sum of the predicted-residual
+ *  chi2 of all updates; ndf [n] = 2 * hits used - 5 (- 4 at zero field);
+ *  status [n] -- MKF_ST_* bits.
+ * Errors: MKF_ERR_ARG, MKF_ERR_GEOMETRY, MKF_ERR_CAPACITY, MKF_ERR_CUDA. */
+mkf_status mkf_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit_layer, int32_t n_hits, const int32_t *hit_idx,
+                   int32_t max_hits, int32_t n, const float *seed_par, const float *seed_cov, float *out_par,
+                   float *out_cov, float *chi2, int32_t *ndf, uint32_t *status);
+
+/* ------------------------------------------------------------------------ */
+/* Finding (Sec. 1: layer-by-layer finding with selection of the best chi2   */
+/* extensions before the final Kalman updates)                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t n_best;          /* candidates kept per seed: 1 = best hit, 2..MKF_MAX_NBEST = N best */
+    float chi2_cut;          /* a hit is compatible when its chi2 < chi2_cut (> 0) */
+    int32_t max_consec_miss; /* a candidate stops after this many misses in a row (1..15) */
+    int32_t block_threads;   /* CUDA block size, multiple of 32 in 32..256; 0 = default (128) */
+} mkf_find_params;
+
+/* Find tracks from seeds.
+ *  bins: from mkf_hits_bin with the current geometry.
+ *  seed_hits: device int32 [3][n_seeds], three hit indices per seed (path order).
+ *  seed_event: device int32 [n_seeds], event of each seed.
+ * Each seed is fitted through its three hits and then extended layer by layer:
+ * a candidate goes to the next layer its helix reaches (the nearer of the next
+ * cylinder and the next disk), every hit of that layer with chi2 < chi2_cut is
+ * a child, plus one child without a hit; children are ranked by
+ * score = chi2_cut * n_hits - chi2 (ties: lower parent rank, then lower hit
+ * index, the child without a hit last) and the best n_best are kept; only kept
+ * children receive the Kalman update.
+ * Outputs (device, caller-owned): out_par [6][n_seeds], out_cov [21][n_seeds]
+ * (best candidate's state at its last visited layer), chi2 [n_seeds],
+ * n_hits [n_seeds], hit_idx [max_out][n_seeds] (hit indices in path order,
+ * seed hits first, -1 padded; max_out >= 3), status [n_seeds],
+ * counters [3][n_seeds] or NULL: candidate-layer steps, hits inside the chi2
+ * window rectangle, Kalman updates.
+ * Errors: MKF_ERR_ARG, MKF_ERR_GEOMETRY, MKF_ERR_CAPACITY, MKF_ERR_CUDA. */
+mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int32_t *seed_hits, const int32_t *seed_event,
+                    int32_t n_seeds, const mkf_find_params *params, float *out_par, float *out_cov, float *chi2,
+                    int32_t *n_hits, int32_t *hit_idx, int32_t max_out, uint32_t *status, int32_t *counters);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MKF_H */

@@ -1,0 +1,217 @@
+"""Python binding of the C ABI with the same names (mkf_create, mkf_geometry_load,
+mkf_hits_bin, mkf_fit, mkf_find, mkf_sync, mkf_destroy), plus a small Context
+class.  PyTorch supplies device memory and streams; this module only checks
+tensor shapes, dtypes and devices and passes raw pointers to libmkf.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _native as N
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _need(t, name, dtype, shape=None, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the context on cuda:{device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+def mkf_create(device: int = 0, stream=None):
+    """Create a library context on `device` enqueueing on `stream` (a
+    torch.cuda.Stream, a raw cudaStream_t int, or None = torch's current stream)."""
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    h = C.c_void_p()
+    N.check("mkf_create", N.lib().mkf_create(C.byref(h), int(device), C.c_void_p(raw)))
+    return h
+
+
+def mkf_destroy(ctx) -> None:
+    N.lib().mkf_destroy(ctx)
+
+
+def mkf_set_stream(ctx, stream) -> None:
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    N.check("mkf_set_stream", N.lib().mkf_set_stream(ctx, C.c_void_p(raw)))
+
+
+def mkf_sync(ctx) -> None:
+    N.check("mkf_sync", N.lib().mkf_sync(ctx))
+
+
+def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None) -> None:
+    """layers: list of dicts (kind, r_or_z, lo, hi, sigma_u, sigma_v, n_phi, n_zr);
+    plans: list of layer-id lists, one per region (None = one region, all layers)."""
+    arr = (N.MkfLayer * len(layers))()
+    for i, d in enumerate(layers):
+        arr[i] = N.MkfLayer(int(d["kind"]), float(d["r_or_z"]), float(d["lo"]), float(d["hi"]),
+                            float(d["sigma_u"]), float(d["sigma_v"]), int(d.get("n_phi", 64)), int(d.get("n_zr", 8)))
+    n_plans = 0 if plans is None else len(plans)
+    parr, keep, edges = None, [], None
+    if n_plans:
+        parr = (N.MkfPlan * n_plans)()
+        for r, ids in enumerate(plans):
+            a = (C.c_int32 * max(1, len(ids)))(*[int(x) for x in ids])
+            keep.append(a)
+            parr[r] = N.MkfPlan(len(ids), C.cast(a, C.POINTER(C.c_int32)))
+        e = list(region_eta_edges or [])
+        if len(e) != n_plans - 1:
+            raise ValueError("need n_plans - 1 region edges")
+        edges = (C.c_float * max(1, len(e)))(*[float(x) for x in e])
+    N.check("mkf_geometry_load", N.lib().mkf_geometry_load(
+        ctx, arr, len(layers), parr, n_plans, edges, float(bz)))
+
+
+class HitBins:
+    """Library-owned bin store; freed with the object (or explicitly)."""
+
+    def __init__(self):
+        self.handle = C.c_void_p()
+
+    def info(self) -> dict:
+        nh, ne, nb = C.c_int32(), C.c_int32(), C.c_int64()
+        N.check("mkf_hitbins_info", N.lib().mkf_hitbins_info(self.handle, C.byref(nh), C.byref(ne), C.byref(nb)))
+        return dict(n_hits=nh.value, n_events=ne.value, n_bins=nb.value)
+
+    def export(self, ctx, device="cuda") -> dict:
+        """Copies of the store's arrays: rec [n_hits, 4] float32, inv [n_hits] int32,
+        offsets [n_bins + 1] int32 (on the context's stream)."""
+        i = self.info()
+        rec = torch.empty(i["n_hits"], 4, dtype=torch.float32, device=device)
+        inv = torch.empty(i["n_hits"], dtype=torch.int32, device=device)
+        off = torch.empty(i["n_bins"] + 1, dtype=torch.int32, device=device)
+        h = ctx.handle if hasattr(ctx, "handle") else ctx
+        N.check("mkf_hitbins_export", N.lib().mkf_hitbins_export(h, self.handle, _ptr(rec), _ptr(inv), _ptr(off)))
+        return dict(rec=rec, inv=inv, offsets=off, **i)
+
+    def free(self):
+        if self.handle:
+            N.lib().mkf_hitbins_free(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mkf_hits_bin(ctx, xyz, layer, event_offsets, bins: HitBins | None = None, device: int | None = None) -> HitBins:
+    n = xyz.shape[1]
+    _need(xyz, "xyz", torch.float32, (3, n), device)
+    _need(layer, "layer", torch.int32, (n,), device)
+    _need(event_offsets, "event_offsets", torch.int32, None, device)
+    n_events = event_offsets.shape[0] - 1
+    bins = bins or HitBins()
+    N.check("mkf_hits_bin", N.lib().mkf_hits_bin(ctx, _ptr(xyz), _ptr(layer), _ptr(event_offsets), n_events, n,
+                                                 C.byref(bins.handle)))
+    return bins
+
+
+def mkf_fit(ctx, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, out=None, device: int | None = None):
+    """Fit along fixed hit lists; returns dict(par [6,n], cov [21,n], chi2, ndf, status)."""
+    n_hits = xyz.shape[1]
+    _need(xyz, "xyz", torch.float32, (3, n_hits), device)
+    _need(hit_layer, "hit_layer", torch.int32, (n_hits,), device)
+    max_hits, n = hit_idx.shape
+    _need(hit_idx, "hit_idx", torch.int32, (max_hits, n), device)
+    if (seed_par is None) != (seed_cov is None):
+        raise ValueError("give both seed_par and seed_cov or neither")
+    if seed_par is not None:
+        _need(seed_par, "seed_par", torch.float32, (6, n), device)
+        _need(seed_cov, "seed_cov", torch.float32, (21, n), device)
+    dev = xyz.device
+    if out is None:
+        out = dict(par=torch.empty(6, n, device=dev), cov=torch.empty(21, n, device=dev),
+                   chi2=torch.empty(n, device=dev), ndf=torch.empty(n, dtype=torch.int32, device=dev),
+                   status=torch.empty(n, dtype=torch.int32, device=dev))
+    N.check("mkf_fit", N.lib().mkf_fit(ctx, _ptr(xyz), _ptr(hit_layer), n_hits, _ptr(hit_idx), max_hits, n,
+                                       _ptr(seed_par), _ptr(seed_cov), _ptr(out["par"]), _ptr(out["cov"]),
+                                       _ptr(out["chi2"]), _ptr(out["ndf"]), _ptr(out["status"])))
+    return out
+
+
+def find_params(n_best=10, chi2_cut=30.0, max_consec_miss=3, block_threads=0) -> N.MkfFindParams:
+    return N.MkfFindParams(int(n_best), float(chi2_cut), int(max_consec_miss), int(block_threads))
+
+
+def mkf_find(ctx, bins: HitBins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
+             n_layers=None, out=None, counters=True, block_threads=0, device: int | None = None):
+    """Find tracks; returns dict(par, cov, chi2, n_hits, hits [max_out, n], status, counters [3, n])."""
+    n = seed_hits.shape[1]
+    _need(seed_hits, "seed_hits", torch.int32, (3, n), device)
+    _need(seed_event, "seed_event", torch.int32, (n,), device)
+    if max_out is None:
+        max_out = (n_layers or N.MAX_LAYERS) + 3
+    dev = seed_hits.device
+    if out is None:
+        out = dict(par=torch.empty(6, n, device=dev), cov=torch.empty(21, n, device=dev),
+                   chi2=torch.empty(n, device=dev), n_hits=torch.empty(n, dtype=torch.int32, device=dev),
+                   hits=torch.empty(max_out, n, dtype=torch.int32, device=dev),
+                   status=torch.empty(n, dtype=torch.int32, device=dev),
+                   counters=torch.empty(3, n, dtype=torch.int32, device=dev) if counters else None)
+    prm = find_params(n_best, chi2_cut, max_consec_miss, block_threads)
+    N.check("mkf_find", N.lib().mkf_find(ctx, bins.handle, _ptr(seed_hits), _ptr(seed_event), n, C.byref(prm),
+                                         _ptr(out["par"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out["n_hits"]),
+                                         _ptr(out["hits"]), int(out["hits"].shape[0]), _ptr(out["status"]),
+                                         _ptr(out.get("counters"))))
+    return out
+
+
+class Context:
+    """Convenience wrapper: one library context on one device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.device = int(device)
+        self.handle = mkf_create(self.device, stream)
+        self.layers = None
+
+    def close(self):
+        if self.handle:
+            mkf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        mkf_set_stream(self.handle, stream)
+
+    def sync(self):
+        mkf_sync(self.handle)
+
+    def geometry_load(self, layers, bz, plans=None, region_eta_edges=None):
+        mkf_geometry_load(self.handle, layers, bz, plans, region_eta_edges)
+        self.layers = [dict(d) for d in layers]
+
+    def hits_bin(self, xyz, layer, event_offsets, bins=None):
+        return mkf_hits_bin(self.handle, xyz, layer, event_offsets, bins, self.device)
+
+    def fit(self, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, out=None):
+        return mkf_fit(self.handle, xyz, hit_layer, hit_idx, seed_par, seed_cov, out, self.device)
+
+    def find(self, bins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
+             out=None, counters=True, block_threads=0):
+        nl = len(self.layers) if self.layers else None
+        return mkf_find(self.handle, bins, seed_hits, seed_event, n_best, chi2_cut, max_consec_miss, max_out, nl, out,
+                        counters, block_threads, self.device)

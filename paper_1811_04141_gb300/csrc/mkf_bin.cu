@@ -1,0 +1,338 @@
+// Hit binning: counting sort of hits into per-(event, layer) phi x z (cylinder)
+// or phi x r (disk) bins, CSR offsets, binned SoA records.  The bins are the
+// acceleration structure behind the per-layer hit search windows (Sec. 2.1);
+// they are a superset test only, the chi2 cut decides.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "mkf_internal.h"
+
+namespace {
+
+using namespace mkf;
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = 4;
+constexpr int kScanTile = kScanThreads * kScanPerThread;
+
+struct BinArgs {
+    Geom G;
+    const float *X, *Y, *Z;
+    const int32_t *layer;
+    const int32_t *event_offsets;
+    int32_t n_events, n_hits;
+    int32_t *key;
+    uint8_t *layer8;
+    float *zhit;
+    int32_t *counts;
+    mkf_fault *fault;
+};
+
+__device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) {
+    if (atomicCAS(&f->code, 0, code) == 0) f->where = where;
+}
+
+__global__ void __launch_bounds__(256) bin_keys_kernel(const __grid_constant__ BinArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n_hits) return;
+    // event of hit i: first e with event_offsets[e + 1] > i
+    int lo = 0, hi = A.n_events;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (A.event_offsets[mid + 1] <= i) lo = mid + 1;
+        else hi = mid;
+    }
+    const int ev = lo;
+    const int l = A.layer[i];
+    if (ev >= A.n_events || i < A.event_offsets[0]) {
+        record_fault(A.fault, kFaultBadEvent, i);
+        A.key[i] = -1;
+        A.layer8[i] = 255;
+        return;
+    }
+    if (l < 0 || l >= A.G.n_layers) {
+        record_fault(A.fault, kFaultBadLayer, i);
+        A.key[i] = -1;
+        A.layer8[i] = 255;
+        return;
+    }
+    const LayerDesc &Ld = A.G.L[l];
+    const float x = A.X[i], y = A.Y[i], z = A.Z[i];
+    A.zhit[i] = z;
+    const float phi = atan2f(y, x);
+    const float zr = Ld.kind == 0 ? z : sqrtf(fmaf(x, x, y * y));
+    int pb = static_cast<int>(floorf((phi + kPi) * Ld.phi_scale));
+    pb = min(max(pb, 0), Ld.nphi - 1);
+    int zb = static_cast<int>(floorf((zr - Ld.lo) * Ld.zr_scale));
+    zb = min(max(zb, 0), Ld.nzr - 1);
+    const int k = ev * A.G.bins_per_event + Ld.bin_base + pb * Ld.nzr + zb;
+    A.key[i] = k;
+    A.layer8[i] = static_cast<uint8_t>(l);
+    atomicAdd(&A.counts[k], 1);
+}
+
+// Block-wide exclusive scan of kScanTile elements; returns the block total.
+__device__ int block_scan_tile(const int32_t *in, int64_t n, int64_t base, int vals[kScanPerThread]) {
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        int64_t idx = base + (int64_t)tid * kScanPerThread + k;
+        int v = idx < n ? in[idx] : 0;
+        vals[k] = s;
+        s += v;
+    }
+    int incl = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int o = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += o;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;  // exclusive
+    }
+    __syncthreads();
+    const int excl = warp_tot[wid] + incl - s;
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) vals[k] += excl;
+    __shared__ int total;
+    if (tid == kScanThreads - 1) total = excl + s;
+    __syncthreads();
+    int t = total;
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int32_t *counts, int64_t n, int32_t *blocksums) {
+    int vals[kScanPerThread];
+    int t = block_scan_tile(counts, n, (int64_t)blockIdx.x * kScanTile, vals);
+    if (threadIdx.x == 0) blocksums[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_blocksums_kernel(int32_t *blocksums, int64_t nb, int32_t *offsets,
+                                                                    int64_t n) {
+    int carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanTile) {
+        int vals[kScanPerThread];
+        int t = block_scan_tile(blocksums, nb, base, vals);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanPerThread; ++k) {
+            int64_t idx = base + (int64_t)threadIdx.x * kScanPerThread + k;
+            if (idx < nb) blocksums[idx] = vals[k] + carry;
+        }
+        carry += t;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) offsets[n] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const int32_t *counts, int64_t n,
+                                                                const int32_t *blocksums, int32_t *offsets) {
+    int vals[kScanPerThread];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    block_scan_tile(counts, n, base, vals);
+    const int add = blocksums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) {
+        int64_t idx = base + (int64_t)threadIdx.x * kScanPerThread + k;
+        if (idx < n) offsets[idx] = vals[k] + add;
+    }
+}
+
+__global__ void __launch_bounds__(256) scatter_kernel(const float *X, const float *Y, const float *Z, const int32_t *key,
+                                                      const uint8_t *layer8, int32_t n_hits,
+                                                      unsigned long long disk_mask, const int32_t *offsets,
+                                                      int32_t *counts, float4 *rec, int32_t *inv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_hits) return;
+    const int k = key[i];
+    if (k < 0) {
+        inv[i] = -1;
+        return;
+    }
+    const int pos = offsets[k] + atomicSub(&counts[k], 1) - 1;
+    const float x = X[i], y = Y[i], z = Z[i];
+    const float zr = ((disk_mask >> layer8[i]) & 1ull) == 0 ? z : sqrtf(fmaf(x, x, y * y));
+    rec[pos] = make_float4(x, y, zr, __int_as_float(i));
+    inv[i] = pos;
+}
+
+// Order the hits of each bin by original index (the scatter's atomics leave an
+// arbitrary order), and rebuild the inverse map.
+__global__ void __launch_bounds__(256) bin_sort_kernel(const int32_t *offsets, int64_t n_bins, float4 *rec, int32_t *inv) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bins) return;
+    const int s = offsets[b], e = offsets[b + 1];
+    for (int i = s + 1; i < e; ++i) {
+        float4 v = rec[i];
+        int key = __float_as_int(v.w);
+        int j = i - 1;
+        while (j >= s && __float_as_int(rec[j].w) > key) {
+            rec[j + 1] = rec[j];
+            --j;
+        }
+        rec[j + 1] = v;
+    }
+    for (int i = s; i < e; ++i) inv[__float_as_int(rec[i].w)] = i;
+}
+
+mkf_status grow(mkf_hitbins *b, int64_t n_hits, int64_t n_bins) {
+    if (n_hits > b->cap_hits) {
+        cudaFree(b->rec);
+        cudaFree(b->inv);
+        cudaFree(b->layer);
+        cudaFree(b->key);
+        cudaFree(b->zhit);
+        b->zhit = nullptr;
+        b->rec = nullptr;
+        b->inv = b->key = nullptr;
+        b->layer = nullptr;
+        b->cap_hits = 0;
+        int64_t c = std::max<int64_t>(n_hits, 1024);
+        MKF_CUDA_TRY(cudaMalloc(&b->rec, c * sizeof(float4)));
+        MKF_CUDA_TRY(cudaMalloc(&b->inv, c * sizeof(int32_t)));
+        MKF_CUDA_TRY(cudaMalloc(&b->key, c * sizeof(int32_t)));
+        MKF_CUDA_TRY(cudaMalloc(&b->layer, c * sizeof(uint8_t)));
+        MKF_CUDA_TRY(cudaMalloc(&b->zhit, c * sizeof(float)));
+        b->cap_hits = c;
+    }
+    const int64_t nblk = (n_bins + kScanTile - 1) / kScanTile;
+    if (n_bins > b->cap_bins || nblk > b->cap_blocks) {
+        cudaFree(b->offsets);
+        cudaFree(b->counts);
+        cudaFree(b->blocksums);
+        b->offsets = b->counts = b->blocksums = nullptr;
+        b->cap_bins = b->cap_blocks = 0;
+        int64_t c = std::max<int64_t>(n_bins, 1024);
+        int64_t cb = std::max<int64_t>((c + kScanTile - 1) / kScanTile, 1);
+        MKF_CUDA_TRY(cudaMalloc(&b->offsets, (c + 1) * sizeof(int32_t)));
+        MKF_CUDA_TRY(cudaMalloc(&b->counts, c * sizeof(int32_t)));
+        MKF_CUDA_TRY(cudaMalloc(&b->blocksums, cb * sizeof(int32_t)));
+        b->cap_bins = c;
+        b->cap_blocks = cb;
+    }
+    return MKF_OK;
+}
+
+}  // namespace
+
+extern "C" void mkf_hitbins_free(mkf_hitbins *b) {
+    if (!b) return;
+    DeviceGuard g(b->device);
+    cudaFree(b->rec);
+    cudaFree(b->inv);
+    cudaFree(b->layer);
+    cudaFree(b->key);
+    cudaFree(b->zhit);
+    cudaFree(b->offsets);
+    cudaFree(b->counts);
+    cudaFree(b->blocksums);
+    delete b;
+}
+
+extern "C" mkf_status mkf_hitbins_info(const mkf_hitbins *b, int32_t *n_hits, int32_t *n_events, int64_t *n_bins) {
+    if (!b) return MKF_ERR_ARG;
+    if (n_hits) *n_hits = b->n_hits;
+    if (n_events) *n_events = b->n_events;
+    if (n_bins) *n_bins = b->n_bins;
+    return MKF_OK;
+}
+
+extern "C" mkf_status mkf_hitbins_export(mkf_ctx *ctx, const mkf_hitbins *b, float *rec, int32_t *inv,
+                                         int32_t *offsets) {
+    if (!ctx || !b || b->device != ctx->device) return MKF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return MKF_ERR_CUDA;
+    cudaStream_t s = ctx->stream;
+    if (rec && b->n_hits)
+        MKF_CUDA_TRY(cudaMemcpyAsync(rec, b->rec, sizeof(float4) * b->n_hits, cudaMemcpyDeviceToDevice, s));
+    if (inv && b->n_hits)
+        MKF_CUDA_TRY(cudaMemcpyAsync(inv, b->inv, sizeof(int32_t) * b->n_hits, cudaMemcpyDeviceToDevice, s));
+    if (offsets)
+        MKF_CUDA_TRY(cudaMemcpyAsync(offsets, b->offsets, sizeof(int32_t) * (b->n_bins + 1), cudaMemcpyDeviceToDevice, s));
+    return MKF_OK;
+}
+
+extern "C" mkf_status mkf_hits_bin(mkf_ctx *ctx, const float *xyz, const int32_t *layer, const int32_t *event_offsets,
+                                   int32_t n_events, int32_t n_hits, mkf_hitbins **inout) {
+    if (!ctx || !inout) return MKF_ERR_ARG;
+    if (!ctx->has_geom) return MKF_ERR_GEOMETRY;
+    if (n_events < 1 || n_hits < 0) return MKF_ERR_ARG;
+    if (n_hits > MKF_MAX_HITS) return MKF_ERR_CAPACITY;
+    if (n_hits > 0 && (!xyz || !layer)) return MKF_ERR_ARG;
+    if (!event_offsets) return MKF_ERR_ARG;
+    const int64_t n_bins = (int64_t)n_events * ctx->geom.bins_per_event;
+    if (n_bins >= (int64_t(1) << 31) - 1) return MKF_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return MKF_ERR_CUDA;
+    mkf_hitbins *b = *inout;
+    bool fresh = false;
+    if (!b) {
+        b = new mkf_hitbins();
+        b->device = ctx->device;
+        fresh = true;
+    } else if (b->device != ctx->device) {
+        return MKF_ERR_ARG;
+    }
+    mkf_status st = grow(b, n_hits, n_bins);
+    if (st != MKF_OK) {
+        if (fresh) mkf_hitbins_free(b);
+        return st;
+    }
+    b->geom_version = ctx->geom_version;
+    b->n_hits = n_hits;
+    b->n_events = n_events;
+    b->n_bins = n_bins;
+    cudaStream_t s = ctx->stream;
+    MKF_CUDA_TRY(cudaMemsetAsync(b->counts, 0, n_bins * sizeof(int32_t), s));
+    if (n_hits > 0) {
+        BinArgs A;
+        A.G = ctx->geom;
+        A.X = xyz;
+        A.Y = xyz + n_hits;
+        A.Z = xyz + 2 * (int64_t)n_hits;
+        A.layer = layer;
+        A.event_offsets = event_offsets;
+        A.n_events = n_events;
+        A.n_hits = n_hits;
+        A.key = b->key;
+        A.layer8 = b->layer;
+        A.zhit = b->zhit;
+        A.counts = b->counts;
+        A.fault = ctx->fault;
+        bin_keys_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(A);
+        MKF_CUDA_TRY(cudaGetLastError());
+    }
+    const int64_t nblk = (n_bins + kScanTile - 1) / kScanTile;
+    scan_tiles_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(b->counts, n_bins, b->blocksums);
+    MKF_CUDA_TRY(cudaGetLastError());
+    scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(b->blocksums, nblk, b->offsets, n_bins);
+    MKF_CUDA_TRY(cudaGetLastError());
+    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(b->counts, n_bins, b->blocksums, b->offsets);
+    MKF_CUDA_TRY(cudaGetLastError());
+    if (n_hits > 0) {
+        unsigned long long disk_mask = 0;
+        for (int l = 0; l < ctx->geom.n_layers; ++l)
+            if (ctx->geom.L[l].kind == 1) disk_mask |= 1ull << l;
+        scatter_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(xyz, xyz + n_hits, xyz + 2 * (int64_t)n_hits, b->key,
+                                                           b->layer, n_hits, disk_mask, b->offsets, b->counts, b->rec,
+                                                           b->inv);
+        MKF_CUDA_TRY(cudaGetLastError());
+        bin_sort_kernel<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(b->offsets, n_bins, b->rec, b->inv);
+        MKF_CUDA_TRY(cudaGetLastError());
+    }
+    *inout = b;
+    return MKF_OK;
+}

@@ -1,0 +1,618 @@
+// Track finding: per-layer propagation, hit search in phi x z / phi x r bins,
+// chi2 of compatible hits, best-hit or N-best branching and the Kalman update
+// of the kept children only (Sec. 1: selection of the best chi2 extensions
+// before the final Kalman updates; Sec. 2.1: layer plans per tracking region).
+//
+// GPU mapping: one lane per candidate; the N candidates of a seed occupy N
+// consecutive lanes of a warp (32 / N seeds per warp).  A step of the layer loop
+// is warp-synchronous:
+//   1. every live candidate lane goes to its next layer, propagates, transports
+//      its covariance and scans the bins of its chi2 window, keeping its best N
+//      compatible hits in a shared-memory list sorted by (chi2, hit index);
+//   2. the seed's N lanes pick the N best children in N rounds of a segmented
+//      max over 64-bit keys (score, parent rank, hit index) exchanged by shuffles;
+//   3. each lane becomes one child: it pulls its parent's propagated state by
+//      shuffles and applies the Kalman update with its hit;
+//   4. each lane records (parent rank, hit) in a per-step history in shared
+//      memory, walked back at the end to produce the best candidate's hit list.
+// No candidate state goes through global memory between layers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "mkf_internal.h"
+
+namespace {
+
+using namespace mkf;
+
+constexpr uint32_t kHitMask = 0x0FFFFFFFu;
+constexpr uint32_t kCodeMiss = 0x0FFFFFFEu;
+constexpr uint32_t kCodePass = 0x0FFFFFFFu;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct FindArgs {
+    Geom G;
+    const float4 *rec;
+    const int32_t *inv;
+    const uint8_t *layer8;
+    const float *zhit;
+    const int32_t *offsets;
+    int32_t n_hits, n_events;
+    const int32_t *seed_hits;
+    const int32_t *seed_event;
+    int32_t n_seeds;
+    int32_t n_best;
+    float cut;
+    int32_t max_consec;
+    int32_t max_steps;
+    float *out_par, *out_cov, *out_chi2;
+    int32_t *out_nhits, *out_hits;
+    int32_t max_out;
+    uint32_t *out_status;
+    int32_t *counters;
+    mkf_fault *fault;
+};
+
+__device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) {
+    if (atomicCAS(&f->code, 0, code) == 0) f->where = where;
+}
+
+// Order-preserving map of a float to uint32 (larger float -> larger integer).
+__device__ __forceinline__ uint32_t ord_float(float f) {
+    if (!isfinite(f)) f = -3.0e38f;
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Child key: larger = better.  (score desc, parent rank asc, hit index asc,
+// the child without a hit last).
+__device__ __forceinline__ unsigned long long child_key(float score, int prank, uint32_t code) {
+    uint32_t lo = (static_cast<uint32_t>(15 - prank) << 28) | (kHitMask - code);
+    return (static_cast<unsigned long long>(ord_float(score)) << 32) | lo;
+}
+
+// Candidate bookkeeping packed into one word for the lane-to-lane transfer.
+struct Book {
+    int nh, consec, ncyl, ndsk;
+    bool done, missstop;
+};
+
+__device__ __forceinline__ uint32_t pack_book(const Book &b) {
+    return static_cast<uint32_t>(b.nh & 0xFF) | (static_cast<uint32_t>(b.consec & 0xF) << 8) |
+           (static_cast<uint32_t>((b.ncyl + 1) & 0x7F) << 12) | (static_cast<uint32_t>((b.ndsk + 1) & 0x7F) << 19) |
+           (b.done ? (1u << 26) : 0u) | (b.missstop ? (1u << 27) : 0u);
+}
+
+__device__ __forceinline__ Book unpack_book(uint32_t w) {
+    Book b;
+    b.nh = w & 0xFF;
+    b.consec = (w >> 8) & 0xF;
+    b.ncyl = static_cast<int>((w >> 12) & 0x7F) - 1;
+    b.ndsk = static_cast<int>((w >> 19) & 0x7F) - 1;
+    b.done = (w >> 26) & 1u;
+    b.missstop = (w >> 27) & 1u;
+    return b;
+}
+
+// Next layer of a candidate (the nearer of its next cylinder and next disk in
+// path length, within the region's layer mask); layers crossed outside their
+// extent are passed over.  Returns the layer id and the path, or -1.
+__device__ __forceinline__ int next_layer(const Geom &G, unsigned long long mask, const float p[6], const Lo &lo,
+                                          float sphi, float cphi, float cot, int dir, int &ncyl, int &ndsk,
+                                          float &s_out) {
+    const float h = -p[3] * G.kb;
+    for (int guard = 0; guard < 2 * kMaxLayers + 2; ++guard) {
+        while (ncyl >= 0 && ncyl < G.n_cyl && !((mask >> G.cyl[ncyl]) & 1ull)) ++ncyl;
+        if (ncyl >= G.n_cyl) ncyl = -1;
+        while (ndsk >= 0 && ndsk < G.n_dsk && !((mask >> G.dsk[ndsk]) & 1ull)) ndsk += dir;
+        if (ndsk >= G.n_dsk) ndsk = -1;
+        const float inf = __int_as_float(0x7f800000);
+        float sc = inf, sd = inf;
+        int lc = -1, ld = -1;
+        if (ncyl >= 0) {
+            lc = G.cyl[ncyl];
+            if (!path_to_layer(G.L[lc], G.kb, p, lo, sphi, cphi, cot, sc)) {
+                ncyl = -1;
+                lc = -1;
+                sc = inf;
+            }
+        }
+        if (ndsk >= 0) {
+            ld = G.dsk[ndsk];
+            if (!path_to_layer(G.L[ld], G.kb, p, lo, sphi, cphi, cot, sd)) {
+                ndsk = -1;
+                ld = -1;
+                sd = inf;
+            }
+        }
+        if (lc < 0 && ld < 0) return -1;
+        const bool use_cyl = sc <= sd;
+        const int l = use_cyl ? lc : ld;
+        const float s = use_cyl ? sc : sd;
+        float x, y, z;
+        helix_point(p, sphi, cphi, cot, h, s, x, y, z);
+        const LayerDesc &Ld = G.L[l];
+        const float coord = Ld.kind == 0 ? z : sqrtf(fmaf(x, x, y * y));
+        const bool inside = coord >= Ld.lo && coord <= Ld.hi;
+        if (use_cyl) ++ncyl;
+        else ndsk += dir;
+        if (ndsk >= G.n_dsk) ndsk = -1;
+        if (inside) {
+            s_out = s;
+            return l;
+        }
+    }
+    return -1;
+}
+
+// Segmented reductions over the N lanes [base, base + N) of a seed.
+__device__ __forceinline__ unsigned long long seg_max(unsigned long long v, int rank, int N, int base) {
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        unsigned long long o = __shfl_down_sync(kFull, v, off);
+        if (rank + off < N && o > v) v = o;
+    }
+    return __shfl_sync(kFull, v, base & 31);
+}
+
+__device__ __forceinline__ int seg_sum(int v, int rank, int N) {
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        int o = __shfl_down_sync(kFull, v, off);
+        if (rank + off < N) v += o;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t seg_or(uint32_t v, int rank, int N) {
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        uint32_t o = __shfl_down_sync(kFull, v, off);
+        if (rank + off < N) v |= o;
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ FindArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Geom SG;
+    {
+        const int *src = reinterpret_cast<const int *>(&A.G);
+        int *dst = reinterpret_cast<int *>(&SG);
+        for (int i = threadIdx.x; i < static_cast<int>(sizeof(Geom) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const Geom &G = SG;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int N = A.n_best;
+    const int spw = 32 / N;
+    const int slot = lane / N, rank = lane - slot * N;
+    const int base = slot * N;
+    const bool lane_used = slot < spw;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int seed = gwarp * spw + slot;
+    const bool has_seed = lane_used && seed < A.n_seeds;
+    const int nwarps = blockDim.x >> 5;
+
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem) + warp * (A.max_steps * 32);
+    float *lchi = reinterpret_cast<float *>(reinterpret_cast<uint32_t *>(smem) + nwarps * A.max_steps * 32) +
+                  warp * (N * 32 * 3);
+    int *lorig = reinterpret_cast<int *>(lchi) + N * 32;
+    int *lbin = lorig + N * 32;
+
+    const float cut = A.cut;
+    float p[6], C[21];
+    Lo lo{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) p[i] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 21; ++k) C[k] = 0.f;
+    float chi2 = 0.f;
+    Book bk{0, 0, -1, -1, true, false};
+    bool live = false;
+    uint32_t status = 0;
+    int c_cl = 0, c_ht = 0, c_up = 0;
+    int dir = 1, ev = 0;
+    unsigned long long mask = 0;
+    int sh[3] = {-1, -1, -1};
+
+    // ---- seed: state from three hits, then the Kalman fit through them (rank-0 lane)
+    if (has_seed && rank == 0) {
+        ev = A.seed_event[seed];
+        bool ok = ev >= 0 && ev < A.n_events;
+        float hx[3], hy[3], hz[3];
+        int hl[3];
+        for (int k = 0; k < 3 && ok; ++k) {
+            sh[k] = A.seed_hits[(int64_t)k * A.n_seeds + seed];
+            if (sh[k] < 0 || sh[k] >= A.n_hits) {
+                record_fault(A.fault, kFaultBadSeedHit, seed);
+                ok = false;
+                break;
+            }
+            const int pos = A.inv[sh[k]];
+            hl[k] = A.layer8[sh[k]];
+            if (pos < 0 || hl[k] >= G.n_layers) {
+                ok = false;
+                break;
+            }
+            const float4 r = A.rec[pos];
+            hx[k] = r.x;
+            hy[k] = r.y;
+            hz[k] = A.zhit[sh[k]];
+        }
+        float eta = 0.f;
+        if (ok) {
+            float h1[3] = {hx[0], hy[0], hz[0]}, h2[3] = {hx[1], hy[1], hz[1]}, h3[3] = {hx[2], hy[2], hz[2]};
+            ok = seed_state(G.L[hl[0]], G.kb, h1, h2, h3, p, C, eta);
+        }
+        for (int k = 0; k < 3 && ok; ++k) {
+            const LayerDesc &Ld = G.L[hl[k]];
+            if (k > 0) {
+                float sphi, cphi, s;
+                sincos_pair(p[4], lo.phi, sphi, cphi);
+                const float cot = cot_of(p[5]);
+                if (!path_to_layer(Ld, G.kb, p, lo, sphi, cphi, cot, s)) {
+                    ok = false;
+                    break;
+                }
+                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+            }
+            const Frame f = frame_of(p);
+            Innov I;
+            if (!innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
+                ok = false;
+                break;
+            }
+            float u, v;
+            const float zr = Ld.kind == 0 ? hz[k] : sqrtf(fmaf(hx[k], hx[k], hy[k] * hy[k]));
+            residual(Ld.kind, Ld.rz, p, lo, f, hx[k], hy[k], zr, u, v);
+            chi2 += chi2_of(I, u, v);
+            kf_apply(I, u, v, p, lo, C);
+        }
+        ok = ok && finite_state(p);
+        if (ok) {
+            int region = 0;
+            while (region + 1 < G.n_regions && eta >= G.edges[region]) ++region;
+            mask = G.mask[region];
+            const float cot = cot_of(p[5]);
+            dir = cot >= 0.f ? 1 : -1;
+            const int l3 = hl[2];
+            const float r3 = sqrtf(fmaf(hx[2], hx[2], hy[2] * hy[2])), z3 = hz[2];
+            if (G.L[l3].kind == 0) {
+                const int pos = G.cyl_pos[l3] + 1;
+                bk.ncyl = pos < G.n_cyl ? pos : -1;
+            } else {
+                bk.ncyl = -1;
+                for (int i = 0; i < G.n_cyl; ++i)
+                    if (G.L[G.cyl[i]].rz > r3) {
+                        bk.ncyl = i;
+                        break;
+                    }
+            }
+            if (G.L[l3].kind == 1) {
+                const int nx = G.dsk_pos[l3] + dir;
+                bk.ndsk = (nx >= 0 && nx < G.n_dsk) ? nx : -1;
+            } else {
+                bk.ndsk = -1;
+                if (dir > 0) {
+                    for (int i = 0; i < G.n_dsk; ++i)
+                        if (G.L[G.dsk[i]].rz > z3) {
+                            bk.ndsk = i;
+                            break;
+                        }
+                } else {
+                    for (int i = G.n_dsk - 1; i >= 0; --i)
+                        if (G.L[G.dsk[i]].rz < z3) {
+                            bk.ndsk = i;
+                            break;
+                        }
+                }
+            }
+            bk.nh = 3;
+            bk.consec = 0;
+            bk.done = false;
+            bk.missstop = false;
+            live = true;
+        } else {
+            status |= MKF_ST_BADSEED;
+        }
+    }
+    // every lane of a seed needs the seed's event, direction and region mask
+    {
+        const int src = lane_used ? base : lane;
+        ev = __shfl_sync(kFull, ev, src);
+        dir = __shfl_sync(kFull, dir, src);
+        mask = __shfl_sync(kFull, mask, src);
+    }
+
+    int step = 0;
+    while (true) {
+        const bool active = live && !bk.done;
+        if (!__any_sync(kFull, active)) break;  // every candidate of the warp has finished
+        // ---- 1. expansion
+        int nlist = 0;
+        bool searched = false;
+        if (active) {
+            float sphi, cphi;
+            sincos_pair(p[4], lo.phi, sphi, cphi);
+            const float cot = cot_of(p[5]);
+            float s;
+            const int l =
+                finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
+            if (l == -2) status |= MKF_ST_NONFINITE;
+            if (l < 0) {
+                bk.done = true;
+            } else {
+                const LayerDesc &Ld = G.L[l];
+                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+                searched = true;
+                ++c_cl;
+                const Frame f = frame_of(p);
+                Innov I;
+                if (innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
+                    const float wu = sqrtf(cut * I.Suu), wv = sqrtf(cut * I.Svv);
+                    const float wu_m = wu * 1.0001f, wv_m = wv * 1.0001f;
+                    const float lever = Ld.kind == 0 ? Ld.rz : f.rt;
+                    const float dphiw = wu_m / lever + 2e-6f;
+                    const float zc = Ld.kind == 0 ? p[2] : f.rt;
+                    const float wz = wv_m + 1e-5f;
+                    const float phic = atan2f(p[1], p[0]);
+                    int pb_lo, nphib;
+                    if (dphiw >= kPi) {
+                        pb_lo = 0;
+                        nphib = Ld.nphi;
+                    } else {
+                        pb_lo = static_cast<int>(floorf((phic - dphiw + kPi) * Ld.phi_scale));
+                        const int pb_hi = static_cast<int>(floorf((phic + dphiw + kPi) * Ld.phi_scale));
+                        nphib = min(pb_hi - pb_lo + 1, Ld.nphi);
+                    }
+                    const float zlo_f = fminf(fmaxf(floorf((zc - wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
+                    const float zhi_f = fminf(fmaxf(floorf((zc + wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
+                    const int zb_lo = static_cast<int>(zlo_f), zb_hi = static_cast<int>(zhi_f);
+                    const int ebase = ev * G.bins_per_event + Ld.bin_base;
+                    for (int i = 0; i < nphib; ++i) {
+                        int pb = (pb_lo + i) % Ld.nphi;
+                        if (pb < 0) pb += Ld.nphi;
+                        const int bin = ebase + pb * Ld.nzr;
+                        const int k0 = A.offsets[bin + zb_lo], k1 = A.offsets[bin + zb_hi + 1];
+                        for (int k = k0; k < k1; ++k) {
+                            const float4 hr = A.rec[k];
+                            float u, v;
+                            if (fabsf(hr.z - zc) > wv_m) continue;
+                            residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
+                            if (fabsf(u) > wu_m) continue;
+                            if (fabsf(u) <= wu && fabsf(v) <= wv) ++c_ht;
+                            const float x2 = chi2_of(I, u, v);
+                            if (!(x2 < cut)) continue;
+                            const int orig = __float_as_int(hr.w);
+                            // insert into the lane's list, sorted by (chi2, orig), at most N
+                            if (nlist == N) {
+                                const float wc = lchi[(N - 1) * 32 + lane];
+                                const int wo = lorig[(N - 1) * 32 + lane];
+                                if (!(x2 < wc || (x2 == wc && orig < wo))) continue;
+                            }
+                            int j = nlist < N ? nlist : N - 1;
+                            while (j > 0) {
+                                const float pc = lchi[(j - 1) * 32 + lane];
+                                const int po = lorig[(j - 1) * 32 + lane];
+                                if (pc > x2 || (pc == x2 && po > orig)) {
+                                    lchi[j * 32 + lane] = pc;
+                                    lorig[j * 32 + lane] = po;
+                                    lbin[j * 32 + lane] = lbin[(j - 1) * 32 + lane];
+                                    --j;
+                                } else {
+                                    break;
+                                }
+                            }
+                            lchi[j * 32 + lane] = x2;
+                            lorig[j * 32 + lane] = orig;
+                            lbin[j * 32 + lane] = k;
+                            if (nlist < N) ++nlist;
+                        }
+                    }
+                } else {
+                    status |= MKF_ST_BADS;
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- 2. selection of the N best children of each seed
+        const float score = cut * static_cast<float>(bk.nh) - chi2;
+        const int n_children = live ? (searched ? nlist + 1 : 1) : 0;
+        int head = 0;
+        unsigned long long mine = 0;
+        for (int j = 0; j < N; ++j) {
+            unsigned long long k = 0;
+            if (head < n_children) {
+                if (head < nlist) {
+                    const float x2 = lchi[head * 32 + lane];
+                    k = child_key(score + cut - x2, rank, static_cast<uint32_t>(lorig[head * 32 + lane]));
+                } else {
+                    k = child_key(score, rank, searched ? kCodeMiss : kCodePass);
+                }
+            }
+            const unsigned long long m = seg_max(k, rank, N, base);
+            if (m != 0ull) {
+                const int wr = 15 - static_cast<int>((m >> 28) & 15ull);
+                if (wr == rank) ++head;
+                if (j == rank) mine = m;
+            }
+        }
+
+        // ---- 3. each lane becomes one child: state from its parent lane
+        const int prank = mine ? 15 - static_cast<int>((mine >> 28) & 15ull) : rank;
+        const int src = lane_used ? base + prank : lane;
+        uint32_t bw = pack_book(bk);
+        bw = __shfl_sync(kFull, bw, src);
+        chi2 = __shfl_sync(kFull, chi2, src);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) p[i] = __shfl_sync(kFull, p[i], src);
+#pragma unroll
+        for (int k = 0; k < 21; ++k) C[k] = __shfl_sync(kFull, C[k], src);
+        lo.x = __shfl_sync(kFull, lo.x, src);
+        lo.y = __shfl_sync(kFull, lo.y, src);
+        lo.z = __shfl_sync(kFull, lo.z, src);
+        lo.phi = __shfl_sync(kFull, lo.phi, src);
+        bk = unpack_book(bw);
+        live = lane_used && mine != 0ull;
+        if (live) {
+            const uint32_t code = kHitMask - static_cast<uint32_t>(mine & kHitMask);
+            if (code < kCodeMiss) {
+                // the hit's binned position from the parent's list
+                int kbin = -1;
+                for (int j = 0; j < N; ++j)
+                    if (lorig[j * 32 + src] == static_cast<int>(code)) {
+                        kbin = lbin[j * 32 + src];
+                        break;
+                    }
+                const int hl = A.layer8[code];
+                const LayerDesc &Ld = G.L[hl];
+                const float4 hr = A.rec[kbin >= 0 ? kbin : A.inv[code]];
+                const Frame f = frame_of(p);
+                Innov I;
+                innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I);
+                float u, v;
+                residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
+                chi2 += chi2_of(I, u, v);
+                kf_apply(I, u, v, p, lo, C);
+                bk.nh += 1;
+                bk.consec = 0;
+                ++c_up;
+            } else if (code == kCodeMiss) {
+                bk.consec += 1;
+                if (bk.consec >= A.max_consec) {
+                    bk.done = true;
+                    bk.missstop = true;
+                }
+            }
+            if (step < A.max_steps) hist[step * 32 + lane] = (static_cast<uint32_t>(prank) << 28) | code;
+        }
+        ++step;
+        if (step >= A.max_steps) {
+            if (lane == 0) record_fault(A.fault, kFaultHistOverflow, gwarp);
+            break;
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+
+    // ---- output: rank 0 of each seed holds the best candidate
+    c_cl = seg_sum(c_cl, rank, N);
+    c_ht = seg_sum(c_ht, rank, N);
+    c_up = seg_sum(c_up, rank, N);
+    status = seg_or(status, rank, N);
+    if (has_seed && rank == 0) {
+        const int n = A.n_seeds;
+        const bool ok = !(status & MKF_ST_BADSEED);
+        int nout = 0;
+        if (ok) {
+            for (int k = 0; k < 3 && nout < A.max_out; ++k) A.out_hits[(int64_t)(nout++) * n + seed] = sh[k];
+            // walk the history back from the best candidate, then write forwards
+            int r = 0, cnt = 0;
+            for (int st = step - 1; st >= 0; --st) {
+                const uint32_t rec = hist[st * 32 + base + r];
+                if ((rec & kHitMask) < kCodeMiss) ++cnt;
+                r = static_cast<int>(rec >> 28);
+            }
+            int pos = nout + cnt - 1;
+            r = 0;
+            for (int st = step - 1; st >= 0; --st) {
+                const uint32_t rec = hist[st * 32 + base + r];
+                const uint32_t code = rec & kHitMask;
+                if (code < kCodeMiss) {
+                    if (pos < A.max_out) A.out_hits[(int64_t)pos * n + seed] = static_cast<int>(code);
+                    --pos;
+                }
+                r = static_cast<int>(rec >> 28);
+            }
+            if (nout + cnt > A.max_out) status |= MKF_ST_TRUNC;
+            nout = min(nout + cnt, A.max_out);
+            if (bk.missstop) status |= MKF_ST_MISSSTOP;
+            if (!finite_state(p) || !isfinite(chi2)) status |= MKF_ST_NONFINITE;
+        }
+        for (int k = nout; k < A.max_out; ++k) A.out_hits[(int64_t)k * n + seed] = -1;
+        const float nanv = __int_as_float(0x7fc00000);
+        p[0] += lo.x;
+        p[1] += lo.y;
+        p[2] += lo.z;
+        p[4] += lo.phi;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) A.out_par[(int64_t)i * n + seed] = ok ? p[i] : nanv;
+#pragma unroll
+        for (int k = 0; k < 21; ++k) A.out_cov[(int64_t)k * n + seed] = ok ? C[k] : nanv;
+        A.out_chi2[seed] = ok ? chi2 : nanv;
+        A.out_nhits[seed] = ok ? bk.nh : 0;
+        A.out_status[seed] = status;
+        if (A.counters) {
+            A.counters[seed] = c_cl;
+            A.counters[(int64_t)n + seed] = c_ht;
+            A.counters[2 * (int64_t)n + seed] = c_up;
+        }
+    }
+}
+
+}  // namespace
+
+static size_t find_smem_bytes(int n_layers, int n_best, int threads) {
+    const int nwarps = threads / 32;
+    const int max_steps = n_layers + 2;
+    return static_cast<size_t>(nwarps) * (max_steps * 32 * 4 + n_best * 32 * 12);
+}
+
+extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int32_t *seed_hits,
+                               const int32_t *seed_event, int32_t n_seeds, const mkf_find_params *params,
+                               float *out_par, float *out_cov, float *chi2, int32_t *n_hits, int32_t *hit_idx,
+                               int32_t max_out, uint32_t *status, int32_t *counters) {
+    if (!ctx || !bins || !params) return MKF_ERR_ARG;
+    if (!ctx->has_geom || bins->geom_version != ctx->geom_version) return MKF_ERR_GEOMETRY;
+    if (bins->device != ctx->device) return MKF_ERR_ARG;
+    if (n_seeds < 0 || max_out < 3) return MKF_ERR_ARG;
+    const int N = params->n_best;
+    if (N < 1) return MKF_ERR_ARG;
+    if (N > MKF_MAX_NBEST) return MKF_ERR_CAPACITY;
+    if (!(params->chi2_cut > 0.f) || !(params->chi2_cut < 3.0e38f)) return MKF_ERR_ARG;
+    if (params->max_consec_miss < 1 || params->max_consec_miss > 15) return MKF_ERR_ARG;
+    int threads = params->block_threads ? params->block_threads : 128;
+    if (threads < 32 || threads > 256 || threads % 32) return MKF_ERR_ARG;
+    if (n_seeds == 0) return MKF_OK;
+    if (!seed_hits || !seed_event || !out_par || !out_cov || !chi2 || !n_hits || !hit_idx || !status) return MKF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return MKF_ERR_CUDA;
+    FindArgs A;
+    A.G = ctx->geom;
+    A.rec = bins->rec;
+    A.inv = bins->inv;
+    A.layer8 = bins->layer;
+    A.zhit = bins->zhit;
+    A.offsets = bins->offsets;
+    A.n_hits = bins->n_hits;
+    A.n_events = bins->n_events;
+    A.seed_hits = seed_hits;
+    A.seed_event = seed_event;
+    A.n_seeds = n_seeds;
+    A.n_best = N;
+    A.cut = params->chi2_cut;
+    A.max_consec = params->max_consec_miss;
+    A.max_steps = ctx->geom.n_layers + 2;
+    A.out_par = out_par;
+    A.out_cov = out_cov;
+    A.out_chi2 = chi2;
+    A.out_nhits = n_hits;
+    A.out_hits = hit_idx;
+    A.max_out = max_out;
+    A.out_status = status;
+    A.counters = counters;
+    A.fault = ctx->fault;
+    const size_t smem = find_smem_bytes(ctx->geom.n_layers, N, threads);
+    if (smem > 200 * 1024) return MKF_ERR_CAPACITY;
+    MKF_CUDA_TRY(cudaFuncSetAttribute(find_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(std::max<size_t>(smem, 48 * 1024))));
+    const int spw = 32 / N;
+    const int seeds_per_block = spw * (threads / 32);
+    const int blocks = (n_seeds + seeds_per_block - 1) / seeds_per_block;
+    find_kernel<<<blocks, threads, smem, ctx->stream>>>(A);
+    MKF_CUDA_TRY(cudaGetLastError());
+    return MKF_OK;
+}

@@ -1,0 +1,163 @@
+// Track fit along fixed hit lists: one thread per track, state and covariance in
+// registers for the whole hit list (Sec. 1: Kalman-filter fitting).
+#include <cuda_runtime.h>
+
+#include "mkf_internal.h"
+
+namespace {
+
+using namespace mkf;
+
+struct FitArgs {
+    Geom G;
+    const float *X, *Y, *Z;
+    const int32_t *hit_layer;
+    int32_t n_hits;
+    const int32_t *hit_idx;
+    int32_t max_hits, n;
+    const float *seed_par, *seed_cov;
+    float *out_par, *out_cov, *chi2;
+    int32_t *ndf;
+    uint32_t *status;
+    mkf_fault *fault;
+};
+
+__device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) {
+    if (atomicCAS(&f->code, 0, code) == 0) f->where = where;
+}
+
+__global__ void __launch_bounds__(128) fit_kernel(const __grid_constant__ FitArgs A) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.n) return;
+    const Geom &G = A.G;
+    float p[6], C[21];
+    Lo lo{0.f, 0.f, 0.f, 0.f};
+    uint32_t st = 0;
+    float chi2 = 0.f;
+    int used = 0;
+
+    // first three valid hits (seed) and validity of all indices
+    int first[3] = {-1, -1, -1}, nfirst = 0;
+    for (int k = 0; k < A.max_hits; ++k) {
+        int h = A.hit_idx[(int64_t)k * A.n + t];
+        if (h < 0) continue;
+        if (h >= A.n_hits) {
+            record_fault(A.fault, kFaultBadHitIndex, t);
+            continue;
+        }
+        if (nfirst < 3) first[nfirst++] = h;
+    }
+    bool ok = nfirst >= 3;
+    if (ok) {
+        int l0 = A.hit_layer[first[0]];
+        if (l0 < 0 || l0 >= G.n_layers) {
+            record_fault(A.fault, kFaultBadLayer, first[0]);
+            ok = false;
+        } else if (A.seed_par) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) p[i] = A.seed_par[(int64_t)i * A.n + t];
+#pragma unroll
+            for (int k = 0; k < 21; ++k) C[k] = A.seed_cov[(int64_t)k * A.n + t];
+        } else {
+            float h1[3], h2[3], h3[3], eta;
+            h1[0] = A.X[first[0]]; h1[1] = A.Y[first[0]]; h1[2] = A.Z[first[0]];
+            h2[0] = A.X[first[1]]; h2[1] = A.Y[first[1]]; h2[2] = A.Z[first[1]];
+            h3[0] = A.X[first[2]]; h3[1] = A.Y[first[2]]; h3[2] = A.Z[first[2]];
+            ok = seed_state(G.L[l0], G.kb, h1, h2, h3, p, C, eta);
+        }
+    }
+    if (!ok) st |= MKF_ST_BADSEED;
+
+    if (ok) {
+        bool firsthit = true;
+        for (int k = 0; k < A.max_hits; ++k) {
+            const int h = A.hit_idx[(int64_t)k * A.n + t];
+            if (h < 0 || h >= A.n_hits) continue;
+            const int l = A.hit_layer[h];
+            if (l < 0 || l >= G.n_layers) {
+                record_fault(A.fault, kFaultBadLayer, h);
+                continue;
+            }
+            const LayerDesc &Ld = G.L[l];
+            const float xh = A.X[h], yh = A.Y[h], zh = A.Z[h];
+            if (!firsthit) {
+                float sphi, cphi;
+                sincos_pair(p[4], lo.phi, sphi, cphi);
+                const float cot = cot_of(p[5]);
+                float s;
+                if (!path_to_layer(Ld, G.kb, p, lo, sphi, cphi, cot, s)) {
+                    st |= MKF_ST_UNREACHABLE;
+                    continue;
+                }
+                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+            }
+            firsthit = false;
+            const Frame f = frame_of(p);
+            Innov I;
+            if (!innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
+                st |= MKF_ST_BADS;
+                continue;
+            }
+            float u, v;
+            const float zr = Ld.kind == 0 ? zh : sqrtf(fmaf(xh, xh, yh * yh));
+            residual(Ld.kind, Ld.rz, p, lo, f, xh, yh, zr, u, v);
+            chi2 += chi2_of(I, u, v);
+            kf_apply(I, u, v, p, lo, C);
+            ++used;
+        }
+        if (!finite_state(p) || !isfinite(chi2)) st |= MKF_ST_NONFINITE;
+    }
+    const float nanv = __int_as_float(0x7fc00000);
+    p[0] += lo.x;
+    p[1] += lo.y;
+    p[2] += lo.z;
+    p[4] += lo.phi;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) A.out_par[(int64_t)i * A.n + t] = ok ? p[i] : nanv;
+#pragma unroll
+    for (int k = 0; k < 21; ++k) A.out_cov[(int64_t)k * A.n + t] = ok ? C[k] : nanv;
+    A.chi2[t] = chi2;
+    A.ndf[t] = 2 * used - (G.kb != 0.f ? 5 : 4);
+    A.status[t] = st;
+}
+
+}  // namespace
+
+extern "C" mkf_status mkf_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit_layer, int32_t n_hits,
+                              const int32_t *hit_idx, int32_t max_hits, int32_t n, const float *seed_par,
+                              const float *seed_cov, float *out_par, float *out_cov, float *chi2, int32_t *ndf,
+                              uint32_t *status) {
+    if (!ctx) return MKF_ERR_ARG;
+    if (!ctx->has_geom) return MKF_ERR_GEOMETRY;
+    if (n < 0 || n_hits < 0 || max_hits < 1) return MKF_ERR_ARG;
+    if (max_hits > MKF_MAX_LAYERS) return MKF_ERR_CAPACITY;
+    if (n_hits > MKF_MAX_HITS) return MKF_ERR_CAPACITY;
+    if ((seed_par == nullptr) != (seed_cov == nullptr)) return MKF_ERR_ARG;
+    if (n == 0) return MKF_OK;
+    if (!xyz || !hit_layer || !hit_idx || !out_par || !out_cov || !chi2 || !ndf || !status) return MKF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return MKF_ERR_CUDA;
+    FitArgs A;
+    A.G = ctx->geom;
+    A.X = xyz;
+    A.Y = xyz + n_hits;
+    A.Z = xyz + 2 * (int64_t)n_hits;
+    A.hit_layer = hit_layer;
+    A.n_hits = n_hits;
+    A.hit_idx = hit_idx;
+    A.max_hits = max_hits;
+    A.n = n;
+    A.seed_par = seed_par;
+    A.seed_cov = seed_cov;
+    A.out_par = out_par;
+    A.out_cov = out_cov;
+    A.chi2 = chi2;
+    A.ndf = ndf;
+    A.status = status;
+    A.fault = ctx->fault;
+    const int threads = 128;
+    const int blocks = (n + threads - 1) / threads;
+    fit_kernel<<<blocks, threads, 0, ctx->stream>>>(A);
+    MKF_CUDA_TRY(cudaGetLastError());
+    return MKF_OK;
+}

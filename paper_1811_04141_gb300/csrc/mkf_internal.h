@@ -1,0 +1,79 @@
+// Host-side internals of libmkf: context, bin store, error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "mkf.h"
+#include "mkf_math.cuh"
+
+// Device fault record written by kernels (bounds and input checks); read and
+// cleared by mkf_sync.
+struct mkf_fault {
+    int code;   // 0 = none, else a kernel-specific code
+    int where;  // index of the offending element
+};
+
+enum : int {
+    kFaultBadLayer = 1,       // hit with a layer id outside the geometry
+    kFaultBadEvent = 2,       // hit outside the event offsets
+    kFaultBadSeedHit = 3,     // seed hit index out of range
+    kFaultHistOverflow = 4,   // candidate history longer than reserved
+    kFaultBadHitIndex = 5,    // fit hit index out of range
+};
+
+struct mkf_ctx {
+    int device;
+    cudaStream_t stream;
+    int has_geom;
+    uint32_t geom_version;
+    mkf::Geom geom;
+    mkf_fault *fault;  // device, one record
+    // reusable scratch owned by the context
+    void *scratch;
+    size_t scratch_bytes;
+    int num_sms;
+};
+
+struct mkf_hitbins {
+    int device;
+    uint32_t geom_version;
+    int32_t n_hits, n_events;
+    int64_t n_bins;
+    // capacities
+    int64_t cap_hits, cap_bins;
+    float4 *rec;        // [n_hits] binned hits: x, y, z-or-r, original index (int bits)
+    int32_t *inv;       // [n_hits] original index -> binned position
+    uint8_t *layer;     // [n_hits] layer of each original hit
+    float *zhit;        // [n_hits] z of each original hit (seeds on disks need it)
+    int32_t *key;       // [n_hits] bin of each original hit (-1 if dropped)
+    int32_t *offsets;   // [n_bins + 1] CSR offsets of the bins
+    int32_t *counts;    // [n_bins] scratch histogram
+    int32_t *blocksums; // scan scratch
+    int64_t cap_blocks;
+};
+
+#define MKF_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return MKF_ERR_CUDA;         \
+    } while (0)
+
+// Make the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Context scratch of at least `bytes` (grown with cudaMalloc, never shrunk).
+mkf_status mkf_scratch(mkf_ctx *ctx, size_t bytes, void **out);

@@ -1,0 +1,463 @@
+// Device-side Kalman-filter math for one track candidate, FP32, register
+// resident.  Shared by the fit and find kernels of libmkf.
+//
+// State p = (x, y, z, w = q/pT, phi, theta); covariance C packed lower triangle,
+// C[i (i + 1) / 2 + j], i >= j.  Uniform field Bz: a track turns at the rate
+// h = -w K Bz per unit transverse path s (Sec. 1 of the paper names helix
+// propagation to barrel and endcap layers; the formulas are the textbook helix).
+//
+// Formulation chosen for FP32 on sm_103a:
+//  * the helix step is written with the half turning angle a = h s / 2 and the
+//    chord L = s sinc(a) in the direction phi + a, which stays exact as h -> 0;
+//  * the crossing with a cylinder r = R is the root of a quadratic in
+//    tau = tan(h s / 2) / h (half-angle substitution), solved in the
+//    cancellation-free form, s = 2 tau atan(h tau) / (h tau);
+//  * the Jacobian of the propagate-to-surface map is J = A + d g^T, with A the
+//    fixed-path Jacobian (identity plus six entries), d = dF/ds and g = ds/dp
+//    from the surface constraint; C' = J C J^T is evaluated from that structure
+//    (about 150 FMAs instead of 432 for dense 6x6 products);
+//  * the r-phi residual is R atan2(P x H, P . H) from the difference vector, so
+//    no large angle is subtracted;
+//  * position (x, y, z) and phi are carried as unevaluated float pairs
+//    (hi + lo): an FP32 coordinate at r ~ 100 cm is only good to 7.6e-6 cm, a
+//    few thousandths of a 20 um resolution, so moves, updates, R^2 - r^2 and
+//    the residuals are formed with exact two-sum / two-product steps instead.
+#pragma once
+
+#include <cstdint>
+
+namespace mkf {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kField = 0.0029979245800f;  // GeV / (T cm)
+constexpr int kMaxLayers = 64;
+constexpr int kMaxRegions = 16;
+
+struct LayerDesc {
+    int kind;         // 0 cylinder, 1 disk
+    float rz;         // R or Z
+    float lo, hi;     // extent: z (cylinder) or r (disk)
+    float su2, sv2;   // measurement variances
+    float seed_sig2;  // seed position variance for a first hit on this layer
+    int nphi, nzr;    // bin grid
+    int bin_base;     // first bin of this layer inside an event's bin block
+    float phi_scale;  // nphi / (2 pi)
+    float zr_scale;   // nzr / (hi - lo)
+};
+
+struct Geom {
+    int n_layers;
+    float kb;  // K * Bz
+    int n_cyl, n_dsk;
+    int bins_per_event;
+    int n_regions;
+    LayerDesc L[kMaxLayers];
+    int8_t cyl[kMaxLayers];      // cylinder ids sorted by radius
+    int8_t dsk[kMaxLayers];      // disk ids sorted by z
+    int8_t cyl_pos[kMaxLayers];  // layer id -> position in cyl[] (-1 if a disk)
+    int8_t dsk_pos[kMaxLayers];  // layer id -> position in dsk[] (-1 if a cylinder)
+    float edges[kMaxRegions];
+    unsigned long long mask[kMaxRegions];
+};
+
+__host__ __device__ constexpr int sym(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+__device__ __forceinline__ float wrap_pi(float a) {
+    if (a > kPi) a -= kTwoPi;
+    else if (a < -kPi) a += kTwoPi;
+    return a;
+}
+
+// Error-free transformations (Knuth two-sum, FMA two-product).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// (hi, lo) += d, renormalised.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float d) {
+    float s, e;
+    two_sum(hi, d, s, e);
+    e += lo;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+// phi pair wrapped into [-pi, pi] with 2 pi as a float pair (a plain float 2 pi
+// is off by 1.7e-7 rad).
+__device__ __forceinline__ void df_wrap_pi(float &hi, float &lo) {
+    constexpr float kTwoPiHi = 6.28318548202514648438f;
+    constexpr float kTwoPiLo = -1.74845553146951e-7f;
+    if (hi > kPi) {
+        df_add(hi, lo, -kTwoPiHi);
+        df_add(hi, lo, -kTwoPiLo);
+    } else if (hi < -kPi) {
+        df_add(hi, lo, kTwoPiHi);
+        df_add(hi, lo, kTwoPiLo);
+    }
+}
+
+// a^2 + b^2 - c^2 - d^2 for floats a, b, c, d (exact products, compensated sum).
+__device__ __forceinline__ float diff_sq2(float a, float b, float c, float d) {
+    float pa, ea, pb, eb, pc, ec, pd, ed;
+    two_prod(a, a, pa, ea);
+    two_prod(b, b, pb, eb);
+    two_prod(c, c, pc, ec);
+    two_prod(d, d, pd, ed);
+    float s1, e1, s2, e2, s3, e3;
+    two_sum(pa, pb, s1, e1);
+    two_sum(pc, pd, s2, e2);
+    two_sum(s1, -s2, s3, e3);
+    return s3 + (e3 + ((e1 - e2) + ((ea + eb) - (ec + ed))));
+}
+
+// Position pair: (x, y, z) = hi + lo per coordinate; phi = hi + lo.
+struct Lo {
+    float x, y, z, phi;
+};
+
+// sin(a)/a and its derivative (a cos a - sin a)/a^2, series near 0.
+__device__ __forceinline__ void sinc_and_deriv(float a, float sa, float ca, float& sn, float& dsn) {
+    float a2 = a * a;
+    if (fabsf(a) < 0.25f) {
+        sn = 1.f - a2 * (1.f / 6.f) * (1.f - a2 * (1.f / 20.f) * (1.f - a2 * (1.f / 42.f) * (1.f - a2 * (1.f / 72.f))));
+        dsn = a * (-1.f / 3.f + a2 * (1.f / 30.f + a2 * (-1.f / 840.f + a2 * (1.f / 45360.f - a2 * (1.f / 3991680.f)))));
+    } else {
+        sn = sa / a;
+        dsn = (a * ca - sa) / a2;
+    }
+}
+
+// atan(x)/x, series near 0.
+__device__ __forceinline__ float atanc(float x) {
+    float x2 = x * x;
+    if (fabsf(x) < 0.125f) return 1.f - x2 * (1.f / 3.f - x2 * (1.f / 5.f - x2 * (1.f / 7.f - x2 * (1.f / 9.f))));
+    return atanf(x) / x;
+}
+
+// asin(x)/x, series near 0.
+__device__ __forceinline__ float asinc(float x) {
+    x = fminf(1.f, fmaxf(-1.f, x));
+    float x2 = x * x;
+    if (fabsf(x) < 0.125f)
+        return 1.f + x2 * (1.f / 6.f + x2 * (3.f / 40.f + x2 * (5.f / 112.f + x2 * (35.f / 1152.f))));
+    return asinf(x) / x;
+}
+
+__device__ __forceinline__ float cot_of(float theta) {
+    float st, ct;
+    sincosf(theta, &st, &ct);
+    return ct / st;
+}
+
+// Smallest s in (0, pi/|h|) (or s > 0 when h = 0) with |P(s)| = R.
+// D = R^2 - |P|^2 is formed from the position pair without cancellation.
+__device__ __forceinline__ bool path_cyl(float x, float y, const Lo &lo, float sphi, float cphi, float h, float R,
+                                         float &s_out) {
+    const float b = fmaf(x, cphi, y * sphi);   // P0 . u
+    const float nn = fmaf(y, cphi, -x * sphi); // P0 . n
+    const float D = diff_sq2(R, 0.f, x, y) - 2.f * fmaf(x, lo.x, y * lo.y);
+    const float a2 = 2.f + 2.f * h * nn - 0.5f * h * h * D;
+    const float disc = fmaf(b, b, 0.5f * a2 * D);
+    if (!(disc >= 0.f)) return false;
+    const float sq = sqrtf(disc);
+    const float qq = -(b + copysignf(sq, b));
+    float best = __int_as_float(0x7f800000);
+    if (qq != 0.f) {
+        const float t = (-0.5f * D) / qq;
+        const float st = 2.f * t * atanc(h * t);
+        if (st > 0.f) best = st;
+    }
+    if (a2 != 0.f) {
+        const float t = qq / a2;
+        const float st = 2.f * t * atanc(h * t);
+        if (st > 0.f && st < best) best = st;
+    }
+    if (!(best < __int_as_float(0x7f800000))) return false;
+    s_out = best;
+    return true;
+}
+
+// Path from state p to the surface of layer l (no extent check).
+__device__ __forceinline__ bool path_to_layer(const LayerDesc& Ld, float kb, const float p[6], const Lo& lo, float sphi,
+                                              float cphi, float cot, float& s) {
+    float h = -p[3] * kb;
+    if (Ld.kind == 0) return path_cyl(p[0], p[1], lo, sphi, cphi, h, Ld.rz, s);
+    if (cot == 0.f) return false;
+    float sd = ((Ld.rz - p[2]) - lo.z) / cot;
+    if (!(sd > 0.f)) return false;
+    if (h != 0.f && fabsf(h) * sd >= kPi) return false;
+    s = sd;
+    return true;
+}
+
+// Position after a move by s (chord form), without touching the state.
+__device__ __forceinline__ void helix_point(const float p[6], float sphi, float cphi, float cot, float h, float s,
+                                            float& x, float& y, float& z) {
+    float a = 0.5f * h * s, sa, ca, sn, dsn;
+    sincosf(a, &sa, &ca);
+    sinc_and_deriv(a, sa, ca, sn, dsn);
+    float L = s * sn;
+    float cm = cphi * ca - sphi * sa, sm = sphi * ca + cphi * sa;
+    x = fmaf(L, cm, p[0]);
+    y = fmaf(L, sm, p[1]);
+    z = fmaf(s, cot, p[2]);
+}
+
+// Move state p by path s onto the surface of layer Ld and transport C with the
+// surface-constrained Jacobian J = A + d g^T.
+__device__ __forceinline__ void propagate_transport(const LayerDesc& Ld, float kb, float p[6], Lo& lo, float C[21],
+                                                   float sphi, float cphi, float cot, float s) {
+    const float h = -p[3] * kb;
+    const float a = 0.5f * h * s;
+    float sa, ca, sn, dsn;
+    sincosf(a, &sa, &ca);
+    sinc_and_deriv(a, sa, ca, sn, dsn);
+    const float L = s * sn;
+    const float cm = cphi * ca - sphi * sa, sm = sphi * ca + cphi * sa;  // direction phi + a
+    const float dx = L * cm, dy = L * sm;
+    const float c2a = 1.f - 2.f * sa * sa, s2a = 2.f * sa * ca;
+    const float cpe = cphi * c2a - sphi * s2a, spe = sphi * c2a + cphi * s2a;  // direction at the end
+    const float st = sinf(p[5]);
+    const float xe = p[0] + dx, ye = p[1] + dy;
+
+    // fixed-path Jacobian entries
+    const float dxdh = 0.5f * s * fmaf(s * dsn, cm, -dy);
+    const float dydh = 0.5f * s * fmaf(s * dsn, sm, dx);
+    const float Axw = -kb * dxdh, Ayw = -kb * dydh;
+    const float Axf = -dy, Ayf = dx;
+    const float Azt = -s / (st * st);
+    const float Afw = -kb * s;
+    // d = dF/ds
+    const float d0 = cpe, d1 = spe, d2 = cot, d4 = h;
+    // g = ds/dp (only the nonzero entries)
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f;
+    if (Ld.kind == 0) {
+        const float inv = -1.f / fmaf(xe, cpe, ye * spe);
+        g0 = xe * inv;
+        g1 = ye * inv;
+        g3 = fmaf(xe, Axw, ye * Ayw) * inv;
+        g4 = fmaf(xe, Axf, ye * Ayf) * inv;
+    } else {
+        const float inv = -1.f / cot;
+        g2 = inv;
+        g5 = Azt * inv;
+    }
+
+    // full symmetric C in registers
+    float Cf[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) Cf[i][j] = C[sym(i, j)];
+
+    // M = A C
+    float M[6][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        M[0][j] = fmaf(Axw, Cf[3][j], fmaf(Axf, Cf[4][j], Cf[0][j]));
+        M[1][j] = fmaf(Ayw, Cf[3][j], fmaf(Ayf, Cf[4][j], Cf[1][j]));
+        M[2][j] = fmaf(Azt, Cf[5][j], Cf[2][j]);
+        M[3][j] = Cf[3][j];
+        M[4][j] = fmaf(Afw, Cf[3][j], Cf[4][j]);
+        M[5][j] = Cf[5][j];
+    }
+    // M += d (g^T C)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        float v;
+        if (Ld.kind == 0) v = fmaf(g0, Cf[0][j], fmaf(g1, Cf[1][j], fmaf(g3, Cf[3][j], g4 * Cf[4][j])));
+        else v = fmaf(g2, Cf[2][j], g5 * Cf[5][j]);
+        M[0][j] = fmaf(d0, v, M[0][j]);
+        M[1][j] = fmaf(d1, v, M[1][j]);
+        M[2][j] = fmaf(d2, v, M[2][j]);
+        M[4][j] = fmaf(d4, v, M[4][j]);
+    }
+    // C' = M A^T + (M g) d^T, lower triangle
+    float u[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (Ld.kind == 0) u[i] = fmaf(g0, M[i][0], fmaf(g1, M[i][1], fmaf(g3, M[i][3], g4 * M[i][4])));
+        else u[i] = fmaf(g2, M[i][2], g5 * M[i][5]);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        C[sym(i, 0)] = fmaf(u[i], d0, fmaf(Axw, M[i][3], fmaf(Axf, M[i][4], M[i][0])));
+        if (i >= 1) C[sym(i, 1)] = fmaf(u[i], d1, fmaf(Ayw, M[i][3], fmaf(Ayf, M[i][4], M[i][1])));
+        if (i >= 2) C[sym(i, 2)] = fmaf(u[i], d2, fmaf(Azt, M[i][5], M[i][2]));
+        if (i >= 3) C[sym(i, 3)] = M[i][3];
+        if (i >= 4) C[sym(i, 4)] = fmaf(u[i], d4, fmaf(Afw, M[i][3], M[i][4]));
+        if (i >= 5) C[sym(i, 5)] = M[i][5];
+    }
+
+    df_add(p[0], lo.x, dx);
+    df_add(p[1], lo.y, dy);
+    if (Ld.kind == 1) {
+        p[2] = Ld.rz;  // on the disk by construction
+        lo.z = 0.f;
+    } else {
+        df_add(p[2], lo.z, s * cot);
+    }
+    df_add(p[4], lo.phi, 2.f * a);
+    df_wrap_pi(p[4], lo.phi);
+}
+
+// Measurement frame at the state's position: unit radial vector (cp, sp), radius.
+struct Frame {
+    float cp, sp, rt, r2;
+};
+
+__device__ __forceinline__ Frame frame_of(const float p[6]) {
+    Frame f;
+    f.r2 = fmaf(p[0], p[0], p[1] * p[1]);
+    f.rt = sqrtf(f.r2);
+    float inv = 1.f / f.rt;
+    f.cp = p[0] * inv;
+    f.sp = p[1] * inv;
+    return f;
+}
+
+// S = H C H^T + V (2x2), its inverse and H C (two rows); false if S is not
+// positive definite.  H_u = (-sin, cos, 0...) of the position azimuth;
+// H_v = (0, 0, 1, ...) on cylinders, (cos, sin, 0, ...) on disks.
+struct Innov {
+    float HCu[6], HCv[6];
+    float Suu, Suv, Svv;
+    float Iuu, Iuv, Ivv;
+};
+
+__device__ __forceinline__ bool innovation(int kind, float su2, float sv2, const Frame& f, const float C[21], Innov& I) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        I.HCu[j] = fmaf(-f.sp, C[sym(0, j)], f.cp * C[sym(1, j)]);
+        I.HCv[j] = kind == 0 ? C[sym(2, j)] : fmaf(f.cp, C[sym(0, j)], f.sp * C[sym(1, j)]);
+    }
+    I.Suu = fmaf(-f.sp, I.HCu[0], f.cp * I.HCu[1]) + su2;
+    if (kind == 0) {
+        I.Suv = I.HCu[2];
+        I.Svv = I.HCv[2] + sv2;
+    } else {
+        I.Suv = fmaf(f.cp, I.HCu[0], f.sp * I.HCu[1]);
+        I.Svv = fmaf(f.cp, I.HCv[0], f.sp * I.HCv[1]) + sv2;
+    }
+    float det = fmaf(I.Suu, I.Svv, -I.Suv * I.Suv);
+    if (!(I.Suu > 0.f && det > 0.f)) return false;
+    float id = 1.f / det;
+    I.Iuu = I.Svv * id;
+    I.Ivv = I.Suu * id;
+    I.Iuv = -I.Suv * id;
+    return true;
+}
+
+// Residual (u, v) of a hit against the state on the layer surface.
+// zr_hit = z (cylinder) or r of the hit (disk; recomputed here from x, y).
+__device__ __forceinline__ void residual(int kind, float R, const float p[6], const Lo& lo, const Frame& f, float xh,
+                                         float yh, float zr_hit, float& u, float& v) {
+    const float dx = (xh - p[0]) - lo.x, dy = (yh - p[1]) - lo.y;
+    const float cross = fmaf(p[0], dy, -p[1] * dx);
+    const float dot = fmaf(p[0], dx, fmaf(p[1], dy, f.r2));
+    const float dphi = atan2f(cross, dot);
+    if (kind == 0) {
+        u = R * dphi;
+        v = (zr_hit - p[2]) - lo.z;
+    } else {
+        u = f.rt * dphi;
+        // r_hit - r = (|H|^2 - |P|^2) / (r_hit + r), numerator without cancellation
+        const float num = diff_sq2(xh, yh, p[0], p[1]) - 2.f * fmaf(p[0], lo.x, p[1] * lo.y);
+        v = num / (sqrtf(fmaf(xh, xh, yh * yh)) + f.rt);
+    }
+}
+
+__device__ __forceinline__ float chi2_of(const Innov& I, float u, float v) {
+    return fmaf(u, fmaf(I.Iuu, u, I.Iuv * v), v * fmaf(I.Iuv, u, I.Ivv * v));
+}
+
+// Kalman update: K = C H^T S^-1, p += K r, C -= K (H C).
+__device__ __forceinline__ void kf_apply(const Innov& I, float u, float v, float p[6], Lo& lo, float C[21]) {
+    float K0[6], K1[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        K0[i] = fmaf(I.HCu[i], I.Iuu, I.HCv[i] * I.Iuv);
+        K1[i] = fmaf(I.HCu[i], I.Iuv, I.HCv[i] * I.Ivv);
+    }
+    df_add(p[0], lo.x, fmaf(K0[0], u, K1[0] * v));
+    df_add(p[1], lo.y, fmaf(K0[1], u, K1[1] * v));
+    df_add(p[2], lo.z, fmaf(K0[2], u, K1[2] * v));
+    p[3] = fmaf(K0[3], u, fmaf(K1[3], v, p[3]));
+    df_add(p[4], lo.phi, fmaf(K0[4], u, K1[4] * v));
+    df_wrap_pi(p[4], lo.phi);
+    p[5] = fmaf(K0[5], u, fmaf(K1[5], v, p[5]));
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) C[sym(i, j)] = C[sym(i, j)] - fmaf(K0[i], I.HCu[j], K1[i] * I.HCv[j]);
+}
+
+// Seed state at hit 1 from three hits (circle in x-y, line in arc length-z),
+// with a prior covariance whose position part lies in the first layer's surface.
+// Returns false for degenerate hits.  Also returns eta of the estimate.
+__device__ __forceinline__ bool seed_state(const LayerDesc& L1, float kb, const float h1[3], const float h2[3],
+                                           const float h3[3], float p[6], float C[21], float& eta) {
+    float ax = h2[0] - h1[0], ay = h2[1] - h1[1];
+    float bx = h3[0] - h1[0], by = h3[1] - h1[1];
+    float cx = h3[0] - h2[0], cy = h3[1] - h2[1];
+    float la = sqrtf(fmaf(ax, ax, ay * ay)), lb = sqrtf(fmaf(bx, bx, by * by)), lc = sqrtf(fmaf(cx, cx, cy * cy));
+    if (!(la > 0.f && lb > 0.f && lc > 0.f)) return false;
+    float h = 2.f * fmaf(ax, by, -ay * bx) / (la * lb * lc);
+    float w = 0.f;
+    if (kb != 0.f) w = -h / kb;
+    else h = 0.f;
+    float xa = 0.5f * h * la, xb = 0.5f * h * lb;
+    float phi0 = atan2f(ay, ax) - xa * asinc(xa);
+    float s13 = lb * asinc(xb);
+    float cot = (h3[2] - h1[2]) / s13;
+    p[0] = h1[0];
+    p[1] = h1[1];
+    p[2] = h1[2];
+    p[3] = w;
+    p[4] = wrap_pi(phi0);
+    p[5] = atan2f(1.f, cot);
+    eta = asinhf(cot);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) C[k] = 0.f;
+    float s2 = L1.seed_sig2;
+    if (L1.kind == 0) {
+        float r = sqrtf(fmaf(h1[0], h1[0], h1[1] * h1[1]));
+        float sp = h1[1] / r, cp = h1[0] / r;
+        C[sym(0, 0)] = s2 * sp * sp;
+        C[sym(1, 0)] = -s2 * sp * cp;
+        C[sym(1, 1)] = s2 * cp * cp;
+        C[sym(2, 2)] = s2;
+    } else {
+        C[sym(0, 0)] = s2;
+        C[sym(1, 1)] = s2;
+    }
+    C[sym(3, 3)] = (0.1f * w) * (0.1f * w) + 1e-4f;
+    C[sym(4, 4)] = 1e-4f;
+    C[sym(5, 5)] = 1e-4f;
+    return true;
+}
+
+// sin and cos of the phi pair (first-order correction for the low part).
+__device__ __forceinline__ void sincos_pair(float hi, float lo, float& s, float& c) {
+    float s0, c0;
+    sincosf(hi, &s0, &c0);
+    s = fmaf(c0, lo, s0);
+    c = fmaf(-s0, lo, c0);
+}
+
+__device__ __forceinline__ bool finite_state(const float p[6]) {
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ok = ok && isfinite(p[i]);
+    return ok;
+}
+
+}  // namespace mkf

@@ -4,9 +4,9 @@ This package simulates the detector: particles on exact helices in a uniform
 solenoid field, their crossings with barrel cylinders and endcap disks, Gaussian
 hit smearing, hit inefficiency and uniform noise.  It contains none of the
 Kalman-filter method (no propagation-to-surface solver, no Jacobian, no update):
-layer crossings are found by bisection on the helix position, which is a
-different computation from the analytic surface solves of either implementation
-of the method.
+particles start on the beam line, where the crossing of a cylinder has a closed
+form; neither implementation of the method uses it (both solve crossings from
+arbitrary points on the track).
 
 The paper ("Parallelized and Vectorized Tracking Using Kalman Filters with CMS
 Detector Geometry and Events", sec. 2.1-2.2 and 3) runs on CMSSW ttbar + PU70

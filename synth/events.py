@@ -11,8 +11,9 @@ h = -q * K_FIELD * Bz / pT per unit transverse path length s.  From the vertex
     x(s) = (sin(phi0 + h s) - sin(phi0)) / h,  y(s) = -(cos(phi0 + h s) - cos(phi0)) / h,
     z(s) = z0 + s cot(theta),  with the straight line as the h = 0 case.
 Hits are made only on the outward half-turn (0 < h s < pi), at most one per layer.
-Cylinder crossings are located by bisection on the transverse radius, which grows
-monotonically along the outward half-turn.
+Cylinder crossings use the closed form from the beam line (the transverse
+distance grows as |2 sin(h s / 2) / h|), which is a special case that neither
+implementation of the method uses: both solve crossings from arbitrary points.
 """
 from __future__ import annotations
 
@@ -42,23 +43,25 @@ def _helix_xy(h, phi0, s):
 
 
 def _cylinder_crossings(h, phi0, radii, s_max):
-    """Path length of each particle's outward crossing of each radius (NaN if none)."""
-    P, L = h.shape[0], radii.shape[0]
-    hh = np.repeat(h[:, None], L, axis=1)
-    pp = np.repeat(phi0[:, None], L, axis=1)
-    R = np.broadcast_to(radii[None, :], (P, L))
-    hi = np.repeat(s_max[:, None], L, axis=1).copy()
-    xe, ye = _helix_xy(hh, pp, hi)
-    reach = np.hypot(xe, ye) >= R
-    lo = np.zeros_like(hi)
-    for _ in range(90):
-        mid = 0.5 * (lo + hi)
-        xm, ym = _helix_xy(hh, pp, mid)
-        inside = np.hypot(xm, ym) < R
-        lo = np.where(inside, mid, lo)
-        hi = np.where(inside, hi, mid)
-    s = 0.5 * (lo + hi)
-    return np.where(reach, s, np.nan)
+    """Path length of each particle's outward crossing of each radius (NaN if none).
+
+    From the beam line the transverse distance after path s is
+    |2 sin(h s / 2) / h|, so the crossing of radius R is s = 2 asin(R |h| / 2) / |h|
+    (s = R for a straight track), provided R <= 2 / |h|."""
+    R = radii[None, :]
+    ah = np.abs(h)[:, None]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        x = R * ah / 2.0
+        s = np.where(ah == 0.0, R, 2.0 * np.arcsin(np.minimum(x, 1.0)) / np.where(ah == 0.0, 1.0, ah))
+    s = np.where((ah == 0.0) | (x <= 1.0), s, np.nan)
+    s = np.where(s < s_max[:, None], s, np.nan)
+    # the crossing point must lie on the cylinder
+    ok = ~np.isnan(s)
+    if ok.any():
+        hh = np.broadcast_to(h[:, None], s.shape)[ok]
+        xx, yy = _helix_xy(hh, np.broadcast_to(phi0[:, None], s.shape)[ok], s[ok])
+        assert np.allclose(np.hypot(xx, yy), np.broadcast_to(R, s.shape)[ok], rtol=1e-9, atol=1e-9)
+    return s
 
 
 @dataclass
@@ -172,15 +175,24 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
     xs, ys = r_s * np.cos(ph_s), r_s * np.sin(ph_s)
 
     # Signal hits in particle order, then path order within a particle.
-    pid_l, lay_l = np.nonzero(kept)
-    order = np.lexsort((np.where(kept, S, np.inf)[pid_l, lay_l], pid_l))
-    pid_l, lay_l = pid_l[order], lay_l[order]
-    sig_xyz = np.stack([xs[pid_l, lay_l], ys[pid_l, lay_l], z_s[pid_l, lay_l]])
-    sig_true_xyz = np.stack([X[pid_l, lay_l], Y[pid_l, lay_l], Z[pid_l, lay_l]])
-    ss = S[pid_l, lay_l]
-    sig_state = np.stack([X[pid_l, lay_l], Y[pid_l, lay_l], Z[pid_l, lay_l],
-                          (q / pt)[pid_l], phi0[pid_l] + h[pid_l] * ss, theta[pid_l]])
-    sig_state[4] = np.arctan2(np.sin(sig_state[4]), np.cos(sig_state[4]))
+    flat = np.flatnonzero(kept)
+    Sflat = S.ravel()[flat]
+    order = np.lexsort((Sflat, flat // L))
+    flat = flat[order]
+    pid_l, lay_l = flat // L, flat % L
+    ss = Sflat[order]
+    n_sig = flat.size
+    sig_xyz = np.empty((3, n_sig))
+    sig_true_xyz = np.empty((3, n_sig))
+    for k_, arr in enumerate((xs, ys, z_s)):
+        sig_xyz[k_] = arr.ravel()[flat]
+    for k_, arr in enumerate((X, Y, Z)):
+        sig_true_xyz[k_] = arr.ravel()[flat]
+    sig_state = np.empty((6, n_sig))
+    sig_state[:3] = sig_true_xyz
+    sig_state[3] = (q / pt)[pid_l]
+    sig_state[4] = np.arctan2(np.sin(phi0[pid_l] + h[pid_l] * ss), np.cos(phi0[pid_l] + h[pid_l] * ss))
+    sig_state[5] = theta[pid_l]
 
     # Noise hits, uniform in (phi, z) on cylinders and uniform in area on disks.
     if cfg["noise_mode"] == "none" and n_noise is None:

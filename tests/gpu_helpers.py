@@ -1,0 +1,68 @@
+"""Shared helpers of the GPU parity tests: device upload of synthetic batches,
+oracle runs on the same inputs, and the parity tolerances."""
+import numpy as np
+
+import oracle as O
+
+# Track-parameter tolerance: relative 1e-4 with per-component floors
+# (x, y, z: 1e-4 cm; q/pT: 1e-6 c/GeV; phi, theta: 1e-5 rad).
+PAR_REL = 1e-4
+PAR_FLOOR = np.array([1e-4, 1e-4, 1e-4, 1e-6, 1e-5, 1e-5])
+# chi2: relative 1e-3 of max(chi2, ndf) on >= 98 % of tracks and 3e-3 on all.
+# The FP32 rounding of a residual is a fixed fraction of the hit resolution, so
+# its effect on chi2 scales with the number of measurements, not with chi2 itself
+# (which can be ~0 by chance).  The FP64 oracle with only its state rounded to
+# FP32 after every step already differs by up to 0.9e-3 max(chi2, ndf), and a
+# disk crossing's path (Z - z) / cot(theta) carries the ~1e-7 relative error of
+# an FP32 sine/cosine, a few 1e-6 cm: a few 1e-3 of a 20 um resolution.
+CHI2_REL = 1e-3
+CHI2_QUANTILE = 0.98
+CHI2_MAX = 3.0  # in units of CHI2_REL
+
+
+def wrap(a):
+    return (a + np.pi) % (2 * np.pi) - np.pi
+
+
+def par_errors(gpu, ref):
+    """|gpu - ref| / (rel * |ref| + floor), per component; <= 1 passes."""
+    d = np.abs(gpu - ref)
+    d[4] = np.abs(wrap(gpu[4] - ref[4]))
+    return d / (PAR_REL * np.abs(ref) + PAR_FLOOR[:, None])
+
+
+def chi2_errors(gpu, ref, ndf):
+    """|gpu - ref| in units of CHI2_REL * max(chi2, ndf, 1)."""
+    return np.abs(gpu - ref) / (CHI2_REL * np.maximum(np.maximum(np.abs(ref), ndf), 1.0))
+
+
+def chi2_ok(gpu, ref, ndf) -> bool:
+    c = chi2_errors(gpu, ref, ndf)
+    if c.size == 0:
+        return True
+    return bool(np.quantile(c, CHI2_QUANTILE) <= 1.0 and c.max() <= CHI2_MAX)
+
+
+def upload(batch, device="cuda"):
+    import torch
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+    return dict(xyz=t(batch.xyz, torch.float32), layer=t(batch.layer, torch.int32),
+                event_offsets=t(batch.event_offsets, torch.int32), seed_hits=t(batch.seed_hits, torch.int32),
+                seed_event=t(batch.seed_event, torch.int32), track_hits=t(batch.track_hits, torch.int32))
+
+
+def make_ctx(batch, plans=None, edges=None):
+    from paper_1811_04141_gb300 import Context, build
+    build.build()
+    ctx = Context(0)
+    ctx.geometry_load(batch.layers, batch.bz, plans, edges)
+    return ctx
+
+
+def oracle_fit(batch, hit_idx=None):
+    geo = O.geometry_for(batch)
+    return O.fit(geo, batch.xyz.astype(np.float64), batch.layer, batch.track_hits if hit_idx is None else hit_idx)
+
+
+def to_np(d):
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in d.items() if v is not None}

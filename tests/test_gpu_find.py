@@ -1,0 +1,153 @@
+"""GPU track finding (mkf_find) against the FP64 oracle on the same FP32 hits.
+
+Hit lists must be identical on >= 99.9 % of tracks; a track whose list differs
+must show an oracle-logged near-tie (a ranking decision, the chi2 cut or a
+geometric decision within FP32 reach).  Tracks with identical lists must agree
+on parameters, chi2, hit count and the candidate-layer and update counters."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synth import make_batch
+from tests.gpu_helpers import chi2_errors, chi2_ok, make_ctx, par_errors, to_np, upload
+
+pytestmark = pytest.mark.gpu
+
+# near-tie thresholds on the oracle's margins (see oracle.find)
+TIE_SCORE = 5e-3   # score gap / max(1, chi2) at a keep/drop or final-order decision
+TIE_CUT = 2e-3     # |chi2 - cut| / cut of a tested hit
+TIE_GEO = 1e-4     # relative gap of a layer-order or extent decision
+
+
+def run_gpu(b, n_best, plans=None, edges=None, max_out=None, block_threads=0):
+    ctx = make_ctx(b, plans, edges)
+    d = upload(b)
+    bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
+    out = ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=n_best, max_out=max_out,
+                   block_threads=block_threads)
+    ctx.sync()
+    return to_np(out)
+
+
+def run_oracle(b, n_best, seed_list=None, geo=None, max_out=None):
+    geo = geo or O.geometry_for(b)
+    return O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+                  n_best=n_best, seed_list=seed_list, max_out=max_out or len(b.layers) + 3)
+
+
+def compare(out, ref, sel=None, min_same=0.999):
+    if sel is None:
+        sel = np.arange(ref["hits"].shape[1])
+    gh = out["hits"][:, sel]
+    same = (gh == ref["hits"]).all(axis=0)
+    diff = np.nonzero(~same)[0]
+    m = ref["margins"]
+    for k in diff:
+        near = m[0, k] < TIE_SCORE or m[1, k] < TIE_CUT or m[2, k] < TIE_GEO
+        assert near, (int(sel[k]), m[:, k], gh[:, k], ref["hits"][:, k])
+    n_allowed = max(1, int(np.floor((1 - min_same) * sel.size + 1e-9)))
+    assert diff.size <= n_allowed, (diff.size, sel.size)
+    ok = same & (ref["status"] & O.ST_BADSEED == 0)
+    assert (out["n_hits"][sel][ok] == ref["n_hits"][ok]).all()
+    assert par_errors(out["par"][:, sel][:, ok], ref["par"][:, ok]).max() <= 1.0
+    ndf = 2 * ref["n_hits"][ok] - 5
+    assert chi2_ok(out["chi2"][sel][ok], ref["chi2"][ok], ndf)
+    assert (out["counters"][0, sel][ok] == ref["counters"][0, ok]).all()
+    assert (out["counters"][2, sel][ok] == ref["counters"][2, ok]).all()
+    # hits inside the window rectangle: FP32 and FP64 may disagree at its edge
+    assert np.abs(out["counters"][1, sel][ok] - ref["counters"][1, ok]).max() <= 2
+    st_mask = O.ST_BADSEED | O.ST_MISSSTOP | O.ST_TRUNC
+    assert ((out["status"][sel][ok] & st_mask) == (ref["status"][ok] & st_mask)).all()
+    return same.mean()
+
+
+@pytest.mark.parametrize("n_best", [1, 10])
+def test_find_parity_small(n_best):
+    b = make_batch("find20", [21], n_tracks=600)
+    out = run_gpu(b, n_best)
+    ref = run_oracle(b, n_best)
+    compare(out, ref)
+
+
+@pytest.mark.parametrize("n_best", [1, 4, 16])
+def test_find_parity_other_widths(n_best):
+    b = make_batch("find20", [22, 23], n_tracks=200)
+    compare(run_gpu(b, n_best), run_oracle(b, n_best))
+
+
+def test_find_parity_dense_sampled():
+    b = make_batch("dense45", [24], n_tracks=1500, n_noise=50000)
+    out = run_gpu(b, 10)
+    sel = np.arange(0, b.n_seeds, 7)
+    ref = run_oracle(b, 10, seed_list=sel)
+    compare(out, ref, sel)
+
+
+def test_find_full_size_sampled():
+    """The finding workload the bench times (20 events x 2000 tracks, N = 10),
+    checked on sampled seeds against the oracle."""
+    b = make_batch("find20", list(range(20)))
+    out = run_gpu(b, 10)
+    rng = np.random.default_rng(1)
+    sel = np.sort(rng.choice(b.n_seeds, 120, replace=False))
+    ref = run_oracle(b, 10, seed_list=sel)
+    compare(out, ref, sel)
+    # every seed produced a finite track with at least its seed hits
+    assert (out["n_hits"] >= 3).all() and np.isfinite(out["par"]).all()
+
+
+def test_find_clean_events_recover_truth():
+    """No noise, no inefficiency: every found track is exactly its particle's hits."""
+    b = make_batch("find20", [25], n_tracks=500, ineff=0.0, noise_scale=0.0)
+    out = run_gpu(b, 10)
+    for t in range(b.n_seeds):
+        want = sorted(b.track_hits[:, t][b.track_hits[:, t] >= 0])
+        got = sorted(out["hits"][:, t][out["hits"][:, t] >= 0])
+        assert got == want
+
+
+def test_find_edge_cases():
+    b = make_batch("find20", [26], n_tracks=100)
+    # truncated output lists
+    out = run_gpu(b, 10, max_out=5)
+    ref = run_oracle(b, 10, max_out=5)
+    assert ((out["status"] & O.ST_TRUNC) > 0).sum() == ((ref["status"] & O.ST_TRUNC) > 0).sum()
+    assert (out["hits"] == ref["hits"]).mean() > 0.99
+    # a degenerate seed (three identical hits) and an empty seed list
+    sh = b.seed_hits.copy()
+    sh[1, 0] = sh[0, 0]
+    sh[2, 0] = sh[0, 0]
+    b.seed_hits = sh
+    out = run_gpu(b, 10)
+    assert out["status"][0] & O.ST_BADSEED and np.isnan(out["par"][:, 0]).all()
+    assert (out["hits"][:, 0] == -1).all()
+    ctx = make_ctx(b)
+    d = upload(b)
+    bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
+    e = ctx.find(bins, torch.zeros(3, 0, dtype=torch.int32, device="cuda"),
+                 torch.zeros(0, dtype=torch.int32, device="cuda"))
+    ctx.sync()
+    assert e["par"].shape == (6, 0)
+
+
+def test_find_block_sizes_agree():
+    b = make_batch("find20", [27], n_tracks=300)
+    ref = run_gpu(b, 10)
+    for bt in (32, 64, 256):
+        out = run_gpu(b, 10, block_threads=bt)
+        assert (out["hits"] == ref["hits"]).all()
+        assert np.array_equal(out["par"], ref["par"])
+
+
+def test_find_region_plans():
+    b = make_batch("find20", [28], n_tracks=400)
+    n = len(b.layers)
+    odd_cyl = [l for l in range(n) if b.layers[l]["kind"] == 0 and l % 2 == 1]
+    plans = [list(range(n)), [l for l in range(n) if l not in odd_cyl], list(range(n))]
+    edges = [-0.9, 0.9]
+    out = run_gpu(b, 10, plans=plans, edges=edges)
+    masks = [sum(1 << l for l in p) for p in plans]
+    geo = O.Geometry(b.layers, b.bz, edges, masks)
+    ref = run_oracle(b, 10, geo=geo)
+    compare(out, ref)

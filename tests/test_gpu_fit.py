@@ -1,0 +1,97 @@
+"""GPU fit (mkf_fit) against the FP64 oracle on the same FP32 hits."""
+import numpy as np
+import pytest
+import torch
+
+from synth import make_batch
+from tests.gpu_helpers import chi2_errors, chi2_ok, make_ctx, oracle_fit, par_errors, to_np, upload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("cfg,tracks", [("fit10", 1000), ("fit10_b0", 1000), ("find20", 700), ("dense45", 500)])
+def test_fit_parity(cfg, tracks):
+    b = make_batch(cfg, [11], n_tracks=tracks)
+    ctx = make_ctx(b)
+    d = upload(b)
+    out = to_np(ctx.fit(d["xyz"], d["layer"], d["track_hits"]))
+    ctx.sync()
+    ref = oracle_fit(b)
+    assert (out["status"] == ref["status"]).all()
+    assert (out["ndf"] == ref["ndf"]).all()
+    ok = ref["status"] == 0
+    e = par_errors(out["par"][:, ok], ref["par"][:, ok])
+    assert e.max() <= 1.0, e.max(axis=1)
+    c = chi2_errors(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
+    assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok]), (np.quantile(c, 0.98), c.max())
+    # covariance diagonal: relative 1e-3
+    for k in (0, 2, 5, 9, 14, 20):
+        r = np.abs(out["cov"][k, ok] - ref["cov"][k, ok]) / np.abs(ref["cov"][k, ok])
+        assert r.max() < 1e-3, (k, r.max())
+
+
+def test_fit_given_seed_states_and_ragged_lists():
+    """Caller-provided seeds, -1 gaps inside the hit lists, a ragged tail of
+    tracks (n not a multiple of the block), and tracks with < 3 hits."""
+    b = make_batch("find20", [12], n_tracks=333)
+    hidx = b.track_hits.copy()
+    hidx[4, ::3] = -1          # gaps
+    hidx[3:, 7] = -1           # short track: 3 hits
+    hidx[2:, 8] = -1           # too short: 2 hits -> bad seed
+    ctx = make_ctx(b)
+    d = upload(b)
+    ht = torch.as_tensor(hidx, device="cuda")
+    out = to_np(ctx.fit(d["xyz"], d["layer"], ht))
+    ref = oracle_fit(b, hidx)
+    assert out["status"][8] & 2 and ref["status"][8] & 2
+    ok = ref["status"] == 0
+    assert (out["status"] == ref["status"]).all()
+    assert par_errors(out["par"][:, ok], ref["par"][:, ok]).max() <= 1.0
+    # seeds given explicitly: the oracle's own seed state (FP32-rounded)
+    import oracle as O
+    geo = O.geometry_for(b)
+    sp, sc = [], []
+    for t in range(b.n_seeds):
+        h = [x for x in hidx[:, t] if x >= 0][:3]
+        if len(h) < 3:
+            sp.append(np.zeros(6)); sc.append(np.eye(6))
+            continue
+        p, Cm = O.seed(geo, *[b.xyz[:, i].astype(np.float64) for i in h], b.layer[h[0]])
+        sp.append(p); sc.append(Cm)
+    sp = np.array(sp).T.astype(np.float32)
+    sc = O.pack21(np.array(sc)).astype(np.float32)
+    out2 = to_np(ctx.fit(d["xyz"], d["layer"], ht, torch.as_tensor(sp, device="cuda"),
+                         torch.as_tensor(sc, device="cuda")))
+    ref2 = O.fit(geo, b.xyz.astype(np.float64), b.layer, hidx, sp.astype(np.float64), sc.astype(np.float64))
+    ok2 = ref2["status"] == 0
+    assert par_errors(out2["par"][:, ok2], ref2["par"][:, ok2]).max() <= 1.0
+
+
+def test_fit_empty_and_errors():
+    b = make_batch("fit10", [13], n_tracks=10)
+    ctx = make_ctx(b)
+    d = upload(b)
+    empty = torch.empty(10, 0, dtype=torch.int32, device="cuda")
+    out = ctx.fit(d["xyz"], d["layer"], empty)
+    assert out["par"].shape == (6, 0)
+    from paper_1811_04141_gb300._native import MkfError
+    with pytest.raises(MkfError):
+        ctx.fit(d["xyz"], d["layer"], torch.zeros(65, 4, dtype=torch.int32, device="cuda"))
+
+
+def test_fit_full_size_sampled():
+    """The 10^6-track fit workload (as timed by the bench), checked on a sample of
+    tracks against the oracle."""
+    from tests.gpu_helpers import O
+    b = make_batch("fit10", list(range(1000)))
+    ctx = make_ctx(b)
+    d = upload(b)
+    out = to_np(ctx.fit(d["xyz"], d["layer"], d["track_hits"]))
+    ctx.sync()
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(b.n_seeds, 2000, replace=False))
+    ref = oracle_fit(b, np.ascontiguousarray(b.track_hits[:, sel]))
+    ok = ref["status"] == 0
+    assert par_errors(out["par"][:, sel][:, ok], ref["par"][:, ok]).max() <= 1.0
+    assert chi2_ok(out["chi2"][sel][ok], ref["chi2"][ok], ref["ndf"][ok])
+    assert np.isfinite(out["par"]).all()

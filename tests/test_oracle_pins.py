@@ -1,7 +1,7 @@
 """Pins of the FP64 oracle against facts fixed outside it (CPU only).
 
 Each test checks an oracle function against something the oracle does not
-compute itself: the generator's crossings (bisection on the helix position),
+compute itself: the generator's crossings (closed form from the beam line),
 closed forms from the origin, finite differences, the composition law of
 Jacobians, limits of the Kalman update, the information form, the Joseph form,
 an independent global least-squares helix fit (scipy), brute-force enumeration
@@ -37,7 +37,7 @@ def find20():
 @pytest.mark.parametrize("cfg", ["find20", "fit10_b0", "dense45"])
 def test_propagation_lands_on_generator_crossings(cfg):
     """Propagating the true state at hit k to the layer of hit k+1 reproduces the
-    generator's crossing (found there by bisection) and its true direction."""
+    generator's crossing (closed form from the beam line) and its true direction."""
     b = make_batch(cfg, [3], n_tracks=300, smear=False)
     geo = O.geometry_for(b)
     worst_pos, worst_phi, n = 0.0, 0.0, 0
