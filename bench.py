@@ -46,12 +46,14 @@ WORKLOAD = ("KF track finding, 20 events x 2000 tracks: 10 barrel cylinders r=4.
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--events", type=int, default=EVENTS, help="events per GPU (profiling runs only)")
+    ap.add_argument("--n-best", type=int, default=N_BEST, help="candidates kept per seed (profiling runs only)")
     return ap.parse_args()
 
 
@@ -115,7 +117,7 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -196,7 +198,8 @@ def run_ours(args, world, rank, local, pg):
     barrier(pg)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    events = list(range(rank * EVENTS, (rank + 1) * EVENTS))
+    E, NB = args.events, args.n_best
+    events = list(range(rank * E, (rank + 1) * E))
     batch = make_batch(CONFIG, events)
     ctx = Context(local, torch.cuda.current_stream(dev))
     ctx.geometry_load(batch.layers, batch.bz)
@@ -206,13 +209,13 @@ def run_ours(args, world, rank, local, pg):
                                                                                              torch.int32)
     max_out = len(batch.layers) + 3
     bins = ctx.hits_bin(xyz, layer, evo)
-    out = ctx.find(bins, sh, se, n_best=N_BEST, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
+    out = ctx.find(bins, sh, se, n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
     torch.cuda.synchronize()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
         ctx.hits_bin(xyz, layer, evo, bins)
-        ctx.find(bins, sh, se, n_best=N_BEST, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=out)
+        ctx.find(bins, sh, se, n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=out)
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -235,7 +238,7 @@ def run_ours(args, world, rank, local, pg):
         ev[i][0].record(stream)
         ctx.hits_bin(xyz, layer, evo, bins)
         ev[i][1].record(stream)
-        ctx.find(bins, sh, se, n_best=N_BEST, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out,
+        ctx.find(bins, sh, se, n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out,
                  out=out)
         ev[i][2].record(stream)
     torch.cuda.synchronize()
@@ -279,7 +282,7 @@ def run_ours(args, world, rank, local, pg):
             d_sh.copy_(h_sh, non_blocking=True)
             d_se.copy_(h_se, non_blocking=True)
             ctx.hits_bin(d_xyz, d_layer, d_evo, bins)
-            ctx.find(bins, d_sh, d_se, n_best=N_BEST, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out,
+            ctx.find(bins, d_sh, d_se, n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out,
                      out=out)
             for k, v in outs_h.items():
                 v.copy_(out[k], non_blocking=True)
@@ -310,7 +313,9 @@ def run_ours(args, world, rank, local, pg):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(step_ms_max, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events_per_gpu": EVENTS, "tracks_per_event": 2000, "n_best": N_BEST,
+        "config": {"workload": WORKLOAD if (E, NB) == (EVENTS, N_BEST) else f"{WORKLOAD} [profiling variant: "
+                                                                                 f"{E} events, N={NB}]",
+                   "events_per_gpu": E, "tracks_per_event": 2000, "n_best": NB,
                    "chi2_cut": CHI2_CUT, "hits_per_gpu": batch.n_hits, "seeds_per_gpu": batch.n_seeds,
                    "cand_layers_per_step_per_gpu": cl, "hits_tested_per_step_per_gpu": ht,
                    "updates_per_step_per_gpu": up, "bin_ms": round(bin_ms, 4), "find_ms": round(find_ms, 4),

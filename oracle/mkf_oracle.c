@@ -587,15 +587,23 @@ static void upd_min(double *m, double v) {
 
 /* Next layer of a candidate: the nearer (in path length) of the next cylinder
  * and the next disk allowed by the region mask.  Layers crossed outside their
- * extent are passed over (pointer advanced, no measurement, state unchanged).
- * Returns the layer id (and its path s) or -1 when no layer is left. */
+ * extent are passed over (pointer advanced, no measurement, state unchanged),
+ * and so are layers already behind the candidate.  Returns the layer id (and
+ * its path s) or -1 when no layer is left. */
 static int next_layer(const find_ctx_t *f, cand_t *c, uint64_t mask, double *s_out, double *mgeo) {
     const geom_t *g = f->g;
+    const double rcur = hypot(c->p[0], c->p[1]), zcur = c->p[2];
     for (int guard = 0; guard < 2 * OR_MAXL + 2; ++guard) {
-        while (c->next_cyl >= 0 && c->next_cyl < f->n_cyl && !((mask >> f->cyl_sorted[c->next_cyl]) & 1ull))
+        /* layers outside the region's plan, and layers already behind the
+         * candidate (a cylinder not beyond its radius, a disk not ahead in z),
+         * are passed over */
+        while (c->next_cyl >= 0 && c->next_cyl < f->n_cyl &&
+               (!((mask >> f->cyl_sorted[c->next_cyl]) & 1ull) || g->rz[f->cyl_sorted[c->next_cyl]] <= rcur))
             c->next_cyl++;
         if (c->next_cyl >= f->n_cyl) c->next_cyl = -1;
-        while (c->next_dsk >= 0 && c->next_dsk < f->n_dsk && !((mask >> f->dsk_sorted[c->next_dsk]) & 1ull))
+        while (c->next_dsk >= 0 && c->next_dsk < f->n_dsk &&
+               (!((mask >> f->dsk_sorted[c->next_dsk]) & 1ull) ||
+                c->dir * (g->rz[f->dsk_sorted[c->next_dsk]] - zcur) <= 0))
             c->next_dsk += c->dir;
         if (c->next_dsk >= f->n_dsk) c->next_dsk = -1;
         double sc = INFINITY, sd = INFINITY;

@@ -156,6 +156,11 @@ extern "C" mkf_status mkf_geometry_load(mkf_ctx *ctx, const mkf_layer *layers, i
         G.dsk[i] = static_cast<int8_t>(dsk[i]);
         G.dsk_pos[dsk[i]] = static_cast<int8_t>(i);
     }
+    for (int i = nc - 1; i >= 0; --i) {
+        const float hi = layers[cyl[i]].hi, lo = layers[cyl[i]].lo;
+        G.cyl_hi_beyond[i] = (i == nc - 1) ? hi : std::max(hi, G.cyl_hi_beyond[i + 1]);
+        G.cyl_lo_beyond[i] = (i == nc - 1) ? lo : std::min(lo, G.cyl_lo_beyond[i + 1]);
+    }
     // regions
     unsigned long long all = n_layers == 64 ? ~0ull : ((1ull << n_layers) - 1ull);
     if (n_plans == 0) {

@@ -15,7 +15,11 @@
 //      shuffles and applies the Kalman update with its hit;
 //   4. each lane records (parent rank, hit) in a per-step history in shared
 //      memory, walked back at the end to produce the best candidate's hit list.
-// No candidate state goes through global memory between layers.
+// The seed fit runs as the first three steps of the same loop with the seed
+// hits forced, so each heavy routine (propagation, transport, S, residual,
+// update) appears once in the kernel; a child reuses its parent's S^-1, H C and
+// hit residual instead of recomputing them.  No candidate state goes through
+// global memory between layers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -97,15 +101,21 @@ __device__ __forceinline__ Book unpack_book(uint32_t w) {
 
 // Next layer of a candidate (the nearer of its next cylinder and next disk in
 // path length, within the region's layer mask); layers crossed outside their
-// extent are passed over.  Returns the layer id and the path, or -1.
+// extent, and layers already behind the candidate, are passed over.  Returns
+// the layer id and the path, or -1.
 __device__ __forceinline__ int next_layer(const Geom &G, unsigned long long mask, const float p[6], const Lo &lo,
                                           float sphi, float cphi, float cot, int dir, int &ncyl, int &ndsk,
                                           float &s_out) {
     const float h = -p[3] * G.kb;
+    const float rcur = sqrtf(fmaf(p[0], p[0], p[1] * p[1])), zcur = p[2] + lo.z;
     for (int guard = 0; guard < 2 * kMaxLayers + 2; ++guard) {
-        while (ncyl >= 0 && ncyl < G.n_cyl && !((mask >> G.cyl[ncyl]) & 1ull)) ++ncyl;
+        // layers outside the region's plan, and layers already behind the
+        // candidate (a cylinder not beyond its radius, a disk not ahead in z)
+        while (ncyl >= 0 && ncyl < G.n_cyl && (!((mask >> G.cyl[ncyl]) & 1ull) || G.L[G.cyl[ncyl]].rz <= rcur)) ++ncyl;
         if (ncyl >= G.n_cyl) ncyl = -1;
-        while (ndsk >= 0 && ndsk < G.n_dsk && !((mask >> G.dsk[ndsk]) & 1ull)) ndsk += dir;
+        while (ndsk >= 0 && ndsk < G.n_dsk &&
+               (!((mask >> G.dsk[ndsk]) & 1ull) || dir * (G.L[G.dsk[ndsk]].rz - zcur) <= 0.f))
+            ndsk += dir;
         if (ndsk >= G.n_dsk) ndsk = -1;
         const float inf = __int_as_float(0x7f800000);
         float sc = inf, sd = inf;
@@ -130,13 +140,27 @@ __device__ __forceinline__ int next_layer(const Geom &G, unsigned long long mask
         const bool use_cyl = sc <= sd;
         const int l = use_cyl ? lc : ld;
         const float s = use_cyl ? sc : sd;
-        float x, y, z;
-        helix_point(p, sphi, cphi, cot, h, s, x, y, z);
         const LayerDesc &Ld = G.L[l];
-        const float coord = Ld.kind == 0 ? z : sqrtf(fmaf(x, x, y * y));
+        float coord;
+        if (use_cyl) {
+            coord = fmaf(s, cot, zcur);  // z along the helix
+        } else {
+            float x, y, z;
+            helix_point(p, sphi, cphi, cot, h, s, x, y, z);
+            coord = sqrtf(fmaf(x, x, y * y));
+        }
         const bool inside = coord >= Ld.lo && coord <= Ld.hi;
-        if (use_cyl) ++ncyl;
-        else ndsk += dir;
+        if (use_cyl) {
+            // z changes monotonically along the helix and larger cylinders are
+            // reached later: past the z-extent of every remaining cylinder, none
+            // of them can be crossed inside its extent
+            if ((cot > 0.f && coord > G.cyl_hi_beyond[ncyl]) || (cot < 0.f && coord < G.cyl_lo_beyond[ncyl]))
+                ncyl = -1;
+            else
+                ++ncyl;
+        } else {
+            ndsk += dir;
+        }
         if (ndsk >= G.n_dsk) ndsk = -1;
         if (inside) {
             s_out = s;
@@ -147,10 +171,10 @@ __device__ __forceinline__ int next_layer(const Geom &G, unsigned long long mask
 }
 
 // Segmented reductions over the N lanes [base, base + N) of a seed.
-__device__ __forceinline__ unsigned long long seg_max(unsigned long long v, int rank, int N, int base) {
+__device__ __forceinline__ uint32_t seg_max32(uint32_t v, int rank, int N, int base) {
 #pragma unroll
     for (int off = 1; off < 16; off <<= 1) {
-        unsigned long long o = __shfl_down_sync(kFull, v, off);
+        const uint32_t o = __shfl_down_sync(kFull, v, off);
         if (rank + off < N && o > v) v = o;
     }
     return __shfl_sync(kFull, v, base & 31);
@@ -195,11 +219,13 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     const bool has_seed = lane_used && seed < A.n_seeds;
     const int nwarps = blockDim.x >> 5;
 
+    // shared memory: per-step history, then the per-lane child lists
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem) + warp * (A.max_steps * 32);
     float *lchi = reinterpret_cast<float *>(reinterpret_cast<uint32_t *>(smem) + nwarps * A.max_steps * 32) +
-                  warp * (N * 32 * 3);
+                  warp * (N * 32 * 4);
     int *lorig = reinterpret_cast<int *>(lchi) + N * 32;
-    int *lbin = lorig + N * 32;
+    float *lu = lchi + 2 * N * 32;
+    float *lv = lchi + 3 * N * 32;
 
     const float cut = A.cut;
     float p[6], C[21];
@@ -208,6 +234,10 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     for (int i = 0; i < 6; ++i) p[i] = 0.f;
 #pragma unroll
     for (int k = 0; k < 21; ++k) C[k] = 0.f;
+    Innov I;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) I.HCu[k] = I.HCv[k] = 0.f;
+    I.Suu = I.Suv = I.Svv = I.Iuu = I.Iuv = I.Ivv = 0.f;
     float chi2 = 0.f;
     Book bk{0, 0, -1, -1, true, false};
     bool live = false;
@@ -215,114 +245,62 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     int c_cl = 0, c_ht = 0, c_up = 0;
     int dir = 1, ev = 0;
     unsigned long long mask = 0;
-    int sh[3] = {-1, -1, -1};
+    // seed hits (rank-0 lane): index, layer, position
+    int sh0 = -1, sh1 = -1, sh2 = -1, sl0 = 0, sl1 = 0, sl2 = 0;
+    float r3 = 0.f, z3 = 0.f;
 
-    // ---- seed: state from three hits, then the Kalman fit through them (rank-0 lane)
+    // ---- seed state from three hits (rank-0 lane); the seed fit runs as the
+    // first three steps of the layer loop, with the seed hits forced
     if (has_seed && rank == 0) {
         ev = A.seed_event[seed];
         bool ok = ev >= 0 && ev < A.n_events;
         float hx[3], hy[3], hz[3];
-        int hl[3];
-        for (int k = 0; k < 3 && ok; ++k) {
-            sh[k] = A.seed_hits[(int64_t)k * A.n_seeds + seed];
-            if (sh[k] < 0 || sh[k] >= A.n_hits) {
+        int hidx[3], hl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            hidx[k] = A.seed_hits[(int64_t)k * A.n_seeds + seed];
+            hl[k] = 0;
+            hx[k] = hy[k] = hz[k] = 0.f;
+            if (!ok) continue;
+            if (hidx[k] < 0 || hidx[k] >= A.n_hits) {
                 record_fault(A.fault, kFaultBadSeedHit, seed);
                 ok = false;
-                break;
+                continue;
             }
-            const int pos = A.inv[sh[k]];
-            hl[k] = A.layer8[sh[k]];
+            const int pos = A.inv[hidx[k]];
+            hl[k] = A.layer8[hidx[k]];
             if (pos < 0 || hl[k] >= G.n_layers) {
                 ok = false;
-                break;
+                continue;
             }
             const float4 r = A.rec[pos];
             hx[k] = r.x;
             hy[k] = r.y;
-            hz[k] = A.zhit[sh[k]];
+            hz[k] = A.zhit[hidx[k]];
         }
         float eta = 0.f;
         if (ok) {
             float h1[3] = {hx[0], hy[0], hz[0]}, h2[3] = {hx[1], hy[1], hz[1]}, h3[3] = {hx[2], hy[2], hz[2]};
             ok = seed_state(G.L[hl[0]], G.kb, h1, h2, h3, p, C, eta);
         }
-        for (int k = 0; k < 3 && ok; ++k) {
-            const LayerDesc &Ld = G.L[hl[k]];
-            if (k > 0) {
-                float sphi, cphi, s;
-                sincos_pair(p[4], lo.phi, sphi, cphi);
-                const float cot = cot_of(p[5]);
-                if (!path_to_layer(Ld, G.kb, p, lo, sphi, cphi, cot, s)) {
-                    ok = false;
-                    break;
-                }
-                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-            }
-            const Frame f = frame_of(p);
-            Innov I;
-            if (!innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
-                ok = false;
-                break;
-            }
-            float u, v;
-            const float zr = Ld.kind == 0 ? hz[k] : sqrtf(fmaf(hx[k], hx[k], hy[k] * hy[k]));
-            residual(Ld.kind, Ld.rz, p, lo, f, hx[k], hy[k], zr, u, v);
-            chi2 += chi2_of(I, u, v);
-            kf_apply(I, u, v, p, lo, C);
-        }
-        ok = ok && finite_state(p);
         if (ok) {
             int region = 0;
             while (region + 1 < G.n_regions && eta >= G.edges[region]) ++region;
             mask = G.mask[region];
-            const float cot = cot_of(p[5]);
-            dir = cot >= 0.f ? 1 : -1;
-            const int l3 = hl[2];
-            const float r3 = sqrtf(fmaf(hx[2], hx[2], hy[2] * hy[2])), z3 = hz[2];
-            if (G.L[l3].kind == 0) {
-                const int pos = G.cyl_pos[l3] + 1;
-                bk.ncyl = pos < G.n_cyl ? pos : -1;
-            } else {
-                bk.ncyl = -1;
-                for (int i = 0; i < G.n_cyl; ++i)
-                    if (G.L[G.cyl[i]].rz > r3) {
-                        bk.ncyl = i;
-                        break;
-                    }
-            }
-            if (G.L[l3].kind == 1) {
-                const int nx = G.dsk_pos[l3] + dir;
-                bk.ndsk = (nx >= 0 && nx < G.n_dsk) ? nx : -1;
-            } else {
-                bk.ndsk = -1;
-                if (dir > 0) {
-                    for (int i = 0; i < G.n_dsk; ++i)
-                        if (G.L[G.dsk[i]].rz > z3) {
-                            bk.ndsk = i;
-                            break;
-                        }
-                } else {
-                    for (int i = G.n_dsk - 1; i >= 0; --i)
-                        if (G.L[G.dsk[i]].rz < z3) {
-                            bk.ndsk = i;
-                            break;
-                        }
-                }
-            }
-            bk.nh = 3;
-            bk.consec = 0;
+            sh0 = hidx[0]; sh1 = hidx[1]; sh2 = hidx[2];
+            sl0 = hl[0]; sl1 = hl[1]; sl2 = hl[2];
+            r3 = sqrtf(fmaf(hx[2], hx[2], hy[2] * hy[2]));
+            z3 = hz[2];
+            bk.nh = 0;
             bk.done = false;
-            bk.missstop = false;
             live = true;
         } else {
             status |= MKF_ST_BADSEED;
         }
     }
-    // every lane of a seed needs the seed's event, direction and region mask
     {
         const int src = lane_used ? base : lane;
         ev = __shfl_sync(kFull, ev, src);
-        dir = __shfl_sync(kFull, dir, src);
         mask = __shfl_sync(kFull, mask, src);
     }
 
@@ -330,118 +308,170 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     while (true) {
         const bool active = live && !bk.done;
         if (!__any_sync(kFull, active)) break;  // every candidate of the warp has finished
-        // ---- 1. expansion
+        const bool seeding = step < 3;          // warp-uniform
+        // ---- 1. expansion: next layer, propagation, window search
         int nlist = 0;
         bool searched = false;
         if (active) {
             float sphi, cphi;
             sincos_pair(p[4], lo.phi, sphi, cphi);
             const float cot = cot_of(p[5]);
-            float s;
-            const int l =
-                finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
+            float s = 0.f;
+            int l;
+            if (seeding) {
+                l = step == 0 ? sl0 : (step == 1 ? sl1 : sl2);
+                if (step > 0 && !path_to_layer(G.L[l], G.kb, p, lo, sphi, cphi, cot, s)) l = -3;
+            } else {
+                l = finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
+            }
             if (l == -2) status |= MKF_ST_NONFINITE;
-            if (l < 0) {
+            if (l == -3) {
+                status |= MKF_ST_BADSEED;
+                live = false;
+            } else if (l < 0) {
                 bk.done = true;
             } else {
                 const LayerDesc &Ld = G.L[l];
-                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-                searched = true;
-                ++c_cl;
+                if (!(seeding && step == 0)) propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+                if (!seeding) {
+                    searched = true;
+                    ++c_cl;
+                }
                 const Frame f = frame_of(p);
-                Innov I;
                 if (innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
-                    const float wu = sqrtf(cut * I.Suu), wv = sqrtf(cut * I.Svv);
-                    const float wu_m = wu * 1.0001f, wv_m = wv * 1.0001f;
-                    const float lever = Ld.kind == 0 ? Ld.rz : f.rt;
-                    const float dphiw = wu_m / lever + 2e-6f;
-                    const float zc = Ld.kind == 0 ? p[2] : f.rt;
-                    const float wz = wv_m + 1e-5f;
-                    const float phic = atan2f(p[1], p[0]);
-                    int pb_lo, nphib;
-                    if (dphiw >= kPi) {
-                        pb_lo = 0;
-                        nphib = Ld.nphi;
+                    if (seeding) {
+                        // the seed hit, accepted whatever its chi2
+                        const int h = step == 0 ? sh0 : (step == 1 ? sh1 : sh2);
+                        const float4 hr = A.rec[A.inv[h]];
+                        float u, v;
+                        residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
+                        lchi[lane] = chi2_of(I, u, v);
+                        lorig[lane] = h;
+                        lu[lane] = u;
+                        lv[lane] = v;
+                        nlist = 1;
                     } else {
-                        pb_lo = static_cast<int>(floorf((phic - dphiw + kPi) * Ld.phi_scale));
-                        const int pb_hi = static_cast<int>(floorf((phic + dphiw + kPi) * Ld.phi_scale));
-                        nphib = min(pb_hi - pb_lo + 1, Ld.nphi);
-                    }
-                    const float zlo_f = fminf(fmaxf(floorf((zc - wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
-                    const float zhi_f = fminf(fmaxf(floorf((zc + wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
-                    const int zb_lo = static_cast<int>(zlo_f), zb_hi = static_cast<int>(zhi_f);
-                    const int ebase = ev * G.bins_per_event + Ld.bin_base;
-                    for (int i = 0; i < nphib; ++i) {
-                        int pb = (pb_lo + i) % Ld.nphi;
-                        if (pb < 0) pb += Ld.nphi;
-                        const int bin = ebase + pb * Ld.nzr;
-                        const int k0 = A.offsets[bin + zb_lo], k1 = A.offsets[bin + zb_hi + 1];
-                        for (int k = k0; k < k1; ++k) {
-                            const float4 hr = A.rec[k];
-                            float u, v;
-                            if (fabsf(hr.z - zc) > wv_m) continue;
-                            residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
-                            if (fabsf(u) > wu_m) continue;
-                            if (fabsf(u) <= wu && fabsf(v) <= wv) ++c_ht;
-                            const float x2 = chi2_of(I, u, v);
-                            if (!(x2 < cut)) continue;
-                            const int orig = __float_as_int(hr.w);
-                            // insert into the lane's list, sorted by (chi2, orig), at most N
-                            if (nlist == N) {
-                                const float wc = lchi[(N - 1) * 32 + lane];
-                                const int wo = lorig[(N - 1) * 32 + lane];
-                                if (!(x2 < wc || (x2 == wc && orig < wo))) continue;
-                            }
-                            int j = nlist < N ? nlist : N - 1;
-                            while (j > 0) {
-                                const float pc = lchi[(j - 1) * 32 + lane];
-                                const int po = lorig[(j - 1) * 32 + lane];
-                                if (pc > x2 || (pc == x2 && po > orig)) {
-                                    lchi[j * 32 + lane] = pc;
-                                    lorig[j * 32 + lane] = po;
-                                    lbin[j * 32 + lane] = lbin[(j - 1) * 32 + lane];
-                                    --j;
-                                } else {
-                                    break;
+                        const float wu = sqrtf(cut * I.Suu), wv = sqrtf(cut * I.Svv);
+                        const float wu_m = wu * 1.0001f, wv_m = wv * 1.0001f;
+                        const float lever = Ld.kind == 0 ? Ld.rz : f.rt;
+                        const float dphiw = wu_m / lever + 2e-6f;
+                        const float zc = Ld.kind == 0 ? p[2] : f.rt;
+                        const float wz = wv_m + 1e-5f;
+                        const float phic = atan2f(p[1], p[0]);
+                        int pb_lo, nphib;
+                        if (dphiw >= kPi) {
+                            pb_lo = 0;
+                            nphib = Ld.nphi;
+                        } else {
+                            pb_lo = static_cast<int>(floorf((phic - dphiw + kPi) * Ld.phi_scale));
+                            const int pb_hi = static_cast<int>(floorf((phic + dphiw + kPi) * Ld.phi_scale));
+                            nphib = min(pb_hi - pb_lo + 1, Ld.nphi);
+                        }
+                        const float zlo_f = fminf(fmaxf(floorf((zc - wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
+                        const float zhi_f = fminf(fmaxf(floorf((zc + wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
+                        const int zb_lo = static_cast<int>(zlo_f), zb_hi = static_cast<int>(zhi_f);
+                        const int ebase = ev * G.bins_per_event + Ld.bin_base;
+                        for (int i = 0; i < nphib; ++i) {
+                            int pb = (pb_lo + i) % Ld.nphi;
+                            if (pb < 0) pb += Ld.nphi;
+                            const int bin = ebase + pb * Ld.nzr;
+                            const int k0 = A.offsets[bin + zb_lo], k1 = A.offsets[bin + zb_hi + 1];
+                            for (int k = k0; k < k1; ++k) {
+                                const float4 hr = A.rec[k];
+                                if (fabsf(hr.z - zc) > wv_m) continue;
+                                float u, v;
+                                residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
+                                if (fabsf(u) > wu_m) continue;
+                                if (fabsf(u) <= wu && fabsf(v) <= wv) ++c_ht;
+                                const float x2 = chi2_of(I, u, v);
+                                if (!(x2 < cut)) continue;
+                                const int orig = __float_as_int(hr.w);
+                                // insert into the lane's list, sorted by (chi2, orig), at most N
+                                if (nlist == N) {
+                                    const float wc = lchi[(N - 1) * 32 + lane];
+                                    const int wo = lorig[(N - 1) * 32 + lane];
+                                    if (!(x2 < wc || (x2 == wc && orig < wo))) continue;
                                 }
+                                int j = nlist < N ? nlist : N - 1;
+                                while (j > 0) {
+                                    const float pc = lchi[(j - 1) * 32 + lane];
+                                    const int po = lorig[(j - 1) * 32 + lane];
+                                    if (pc > x2 || (pc == x2 && po > orig)) {
+                                        lchi[j * 32 + lane] = pc;
+                                        lorig[j * 32 + lane] = po;
+                                        lu[j * 32 + lane] = lu[(j - 1) * 32 + lane];
+                                        lv[j * 32 + lane] = lv[(j - 1) * 32 + lane];
+                                        --j;
+                                    } else {
+                                        break;
+                                    }
+                                }
+                                lchi[j * 32 + lane] = x2;
+                                lorig[j * 32 + lane] = orig;
+                                lu[j * 32 + lane] = u;
+                                lv[j * 32 + lane] = v;
+                                if (nlist < N) ++nlist;
                             }
-                            lchi[j * 32 + lane] = x2;
-                            lorig[j * 32 + lane] = orig;
-                            lbin[j * 32 + lane] = k;
-                            if (nlist < N) ++nlist;
                         }
                     }
                 } else {
                     status |= MKF_ST_BADS;
+                    if (seeding) {
+                        status |= MKF_ST_BADSEED;
+                        live = false;
+                    }
                 }
             }
         }
         __syncwarp();
 
-        // ---- 2. selection of the N best children of each seed
+        // ---- 2. selection of the N best children of each seed: N rounds of a
+        // segmented max over the lanes' best remaining child.  The score is
+        // compared as an order-preserving 32-bit integer; exact score ties (rare)
+        // are resolved by a second reduction on (parent rank, hit index).
         const float score = cut * static_cast<float>(bk.nh) - chi2;
-        const int n_children = live ? (searched ? nlist + 1 : 1) : 0;
+        const int n_children = live ? (seeding ? nlist : (searched ? nlist + 1 : 1)) : 0;
         int head = 0;
         unsigned long long mine = 0;
-        for (int j = 0; j < N; ++j) {
-            unsigned long long k = 0;
-            if (head < n_children) {
-                if (head < nlist) {
-                    const float x2 = lchi[head * 32 + lane];
-                    k = child_key(score + cut - x2, rank, static_cast<uint32_t>(lorig[head * 32 + lane]));
-                } else {
-                    k = child_key(score, rank, searched ? kCodeMiss : kCodePass);
-                }
+        if (N == 1) {
+            if (n_children > 0) {
+                mine = head < nlist ? child_key(score + cut - lchi[lane], 0, static_cast<uint32_t>(lorig[lane]))
+                                    : child_key(score, 0, searched ? kCodeMiss : kCodePass);
             }
-            const unsigned long long m = seg_max(k, rank, N, base);
-            if (m != 0ull) {
-                const int wr = 15 - static_cast<int>((m >> 28) & 15ull);
-                if (wr == rank) ++head;
-                if (j == rank) mine = m;
+        } else {
+            for (int j = 0; j < N; ++j) {
+                const bool has = head < n_children;
+                if (!__any_sync(kFull, has)) break;
+                uint32_t k32 = 0, lo32 = 0;
+                if (has) {
+                    const bool is_hit = head < nlist;
+                    const float sc = is_hit ? score + cut - lchi[head * 32 + lane] : score;
+                    const uint32_t code = is_hit ? static_cast<uint32_t>(lorig[head * 32 + lane])
+                                                 : (searched ? kCodeMiss : kCodePass);
+                    k32 = ord_float(sc);
+                    lo32 = (static_cast<uint32_t>(15 - rank) << 28) | (kHitMask - code);
+                }
+                const uint32_t m32 = seg_max32(k32, rank, N, base);
+                const bool cand = has && k32 == m32;
+                // the lanes of my segment holding the maximum score
+                const unsigned seg_bits = (N == 32 ? kFull : ((1u << N) - 1u)) << (base & 31);
+                const unsigned tied = __ballot_sync(kFull, cand) & seg_bits;
+                uint32_t mlo;
+                if (__any_sync(kFull, lane_used && __popc(tied) > 1)) {
+                    mlo = seg_max32(cand ? lo32 : 0u, rank, N, base);
+                } else {
+                    mlo = __shfl_sync(kFull, lo32, tied ? (__ffs(tied) - 1) : lane);
+                }
+                if (m32 != 0u && lane_used) {
+                    const int wr = 15 - static_cast<int>(mlo >> 28);
+                    if (wr == rank) ++head;
+                    if (j == rank) mine = (static_cast<unsigned long long>(m32) << 32) | mlo;
+                }
             }
         }
 
-        // ---- 3. each lane becomes one child: state from its parent lane
+        // ---- 3. each lane becomes one child: its parent's propagated state,
+        // and the parent's S^-1 and H C, by shuffles
         const int prank = mine ? 15 - static_cast<int>((mine >> 28) & 15ull) : rank;
         const int src = lane_used ? base + prank : lane;
         uint32_t bw = pack_book(bk);
@@ -455,31 +485,68 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
         lo.y = __shfl_sync(kFull, lo.y, src);
         lo.z = __shfl_sync(kFull, lo.z, src);
         lo.phi = __shfl_sync(kFull, lo.phi, src);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            I.HCu[k] = __shfl_sync(kFull, I.HCu[k], src);
+            I.HCv[k] = __shfl_sync(kFull, I.HCv[k], src);
+        }
+        I.Iuu = __shfl_sync(kFull, I.Iuu, src);
+        I.Iuv = __shfl_sync(kFull, I.Iuv, src);
+        I.Ivv = __shfl_sync(kFull, I.Ivv, src);
         bk = unpack_book(bw);
         live = lane_used && mine != 0ull;
         if (live) {
             const uint32_t code = kHitMask - static_cast<uint32_t>(mine & kHitMask);
             if (code < kCodeMiss) {
-                // the hit's binned position from the parent's list
-                int kbin = -1;
+                // the hit's residual and chi2 from the parent's list
+                float u = 0.f, v = 0.f, x2 = 0.f;
                 for (int j = 0; j < N; ++j)
                     if (lorig[j * 32 + src] == static_cast<int>(code)) {
-                        kbin = lbin[j * 32 + src];
+                        u = lu[j * 32 + src];
+                        v = lv[j * 32 + src];
+                        x2 = lchi[j * 32 + src];
                         break;
                     }
-                const int hl = A.layer8[code];
-                const LayerDesc &Ld = G.L[hl];
-                const float4 hr = A.rec[kbin >= 0 ? kbin : A.inv[code]];
-                const Frame f = frame_of(p);
-                Innov I;
-                innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I);
-                float u, v;
-                residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
-                chi2 += chi2_of(I, u, v);
+                chi2 += x2;
                 kf_apply(I, u, v, p, lo, C);
                 bk.nh += 1;
                 bk.consec = 0;
-                ++c_up;
+                if (!seeding) ++c_up;
+                if (seeding && step == 2) {
+                    // direction along z and the first layers beyond the seed
+                    const float cot = cot_of(p[5]);
+                    dir = cot >= 0.f ? 1 : -1;
+                    if (G.L[sl2].kind == 0) {
+                        const int pos = G.cyl_pos[sl2] + 1;
+                        bk.ncyl = pos < G.n_cyl ? pos : -1;
+                    } else {
+                        bk.ncyl = -1;
+                        for (int i = 0; i < G.n_cyl; ++i)
+                            if (G.L[G.cyl[i]].rz > r3) {
+                                bk.ncyl = i;
+                                break;
+                            }
+                    }
+                    if (G.L[sl2].kind == 1) {
+                        const int nx = G.dsk_pos[sl2] + dir;
+                        bk.ndsk = (nx >= 0 && nx < G.n_dsk) ? nx : -1;
+                    } else {
+                        bk.ndsk = -1;
+                        if (dir > 0) {
+                            for (int i = 0; i < G.n_dsk; ++i)
+                                if (G.L[G.dsk[i]].rz > z3) {
+                                    bk.ndsk = i;
+                                    break;
+                                }
+                        } else {
+                            for (int i = G.n_dsk - 1; i >= 0; --i)
+                                if (G.L[G.dsk[i]].rz < z3) {
+                                    bk.ndsk = i;
+                                    break;
+                                }
+                        }
+                    }
+                }
             } else if (code == kCodeMiss) {
                 bk.consec += 1;
                 if (bk.consec >= A.max_consec) {
@@ -487,7 +554,11 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                     bk.missstop = true;
                 }
             }
-            if (step < A.max_steps) hist[step * 32 + lane] = (static_cast<uint32_t>(prank) << 28) | code;
+            hist[step * 32 + lane] = (static_cast<uint32_t>(prank) << 28) | code;
+        }
+        if (seeding && step == 2) {
+            // the seed fit is over: the direction is shared by the seed's lanes
+            dir = __shfl_sync(kFull, dir, lane_used ? base : lane);
         }
         ++step;
         if (step >= A.max_steps) {
@@ -505,10 +576,9 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     status = seg_or(status, rank, N);
     if (has_seed && rank == 0) {
         const int n = A.n_seeds;
-        const bool ok = !(status & MKF_ST_BADSEED);
+        const bool ok = !(status & MKF_ST_BADSEED) && live;
         int nout = 0;
         if (ok) {
-            for (int k = 0; k < 3 && nout < A.max_out; ++k) A.out_hits[(int64_t)(nout++) * n + seed] = sh[k];
             // walk the history back from the best candidate, then write forwards
             int r = 0, cnt = 0;
             for (int st = step - 1; st >= 0; --st) {
@@ -516,7 +586,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                 if ((rec & kHitMask) < kCodeMiss) ++cnt;
                 r = static_cast<int>(rec >> 28);
             }
-            int pos = nout + cnt - 1;
+            int pos = cnt - 1;
             r = 0;
             for (int st = step - 1; st >= 0; --st) {
                 const uint32_t rec = hist[st * 32 + base + r];
@@ -527,8 +597,8 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                 }
                 r = static_cast<int>(rec >> 28);
             }
-            if (nout + cnt > A.max_out) status |= MKF_ST_TRUNC;
-            nout = min(nout + cnt, A.max_out);
+            if (cnt > A.max_out) status |= MKF_ST_TRUNC;
+            nout = min(cnt, A.max_out);
             if (bk.missstop) status |= MKF_ST_MISSSTOP;
             if (!finite_state(p) || !isfinite(chi2)) status |= MKF_ST_NONFINITE;
         }
@@ -555,10 +625,12 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
 
 }  // namespace
 
+// steps: 3 seed steps + at most one per layer + one final step with no layer left
+static int find_max_steps(int n_layers) { return n_layers + 5; }
+
 static size_t find_smem_bytes(int n_layers, int n_best, int threads) {
     const int nwarps = threads / 32;
-    const int max_steps = n_layers + 2;
-    return static_cast<size_t>(nwarps) * (max_steps * 32 * 4 + n_best * 32 * 12);
+    return static_cast<size_t>(nwarps) * (find_max_steps(n_layers) * 32 * 4 + n_best * 32 * 16);
 }
 
 extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int32_t *seed_hits,
@@ -595,7 +667,7 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     A.n_best = N;
     A.cut = params->chi2_cut;
     A.max_consec = params->max_consec_miss;
-    A.max_steps = ctx->geom.n_layers + 2;
+    A.max_steps = find_max_steps(ctx->geom.n_layers);
     A.out_par = out_par;
     A.out_cov = out_cov;
     A.out_chi2 = chi2;

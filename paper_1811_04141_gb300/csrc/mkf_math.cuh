@@ -48,6 +48,8 @@ struct LayerDesc {
 
 struct Geom {
     int n_layers;
+    float cyl_hi_beyond[kMaxLayers];  // max z-extent end of the cylinders at and after each sorted position
+    float cyl_lo_beyond[kMaxLayers];  // min z-extent start of the same
     float kb;  // K * Bz
     int n_cyl, n_dsk;
     int bins_per_event;
@@ -169,16 +171,19 @@ __device__ __forceinline__ bool path_cyl(float x, float y, const Lo &lo, float s
     if (!(disc >= 0.f)) return false;
     const float sq = sqrtf(disc);
     const float qq = -(b + copysignf(sq, b));
+    // s = 2 tau atan(h tau) / (h tau) has the sign of tau: only positive roots
+    // are converted
     float best = __int_as_float(0x7f800000);
     if (qq != 0.f) {
         const float t = (-0.5f * D) / qq;
-        const float st = 2.f * t * atanc(h * t);
-        if (st > 0.f) best = st;
+        if (t > 0.f) best = 2.f * t * atanc(h * t);
     }
     if (a2 != 0.f) {
         const float t = qq / a2;
-        const float st = 2.f * t * atanc(h * t);
-        if (st > 0.f && st < best) best = st;
+        if (t > 0.f) {
+            const float st = 2.f * t * atanc(h * t);
+            if (st > 0.f && st < best) best = st;
+        }
     }
     if (!(best < __int_as_float(0x7f800000))) return false;
     s_out = best;

