@@ -159,6 +159,37 @@ mkf_status mkf_hitbins_info(const mkf_hitbins *bins, int32_t *n_hits, int32_t *n
  * Errors: MKF_ERR_ARG, MKF_ERR_CUDA. */
 mkf_status mkf_hitbins_export(mkf_ctx *ctx, const mkf_hitbins *bins, float *rec, int32_t *inv, int32_t *offsets);
 
+/* Largest input mkf_hits_bin_static accepts. */
+#define MKF_STATIC_MAX_HITS (1 << 22)
+#define MKF_STATIC_MAX_BINS (1 << 22) /* n_events * bins per event */
+
+/* Hit binning for callers that cannot allocate GPU memory: the paper has no
+ * counterpart; this is a deployment variant of mkf_hits_bin.
+ *
+ * Some callers cannot call cudaMalloc at all -- code that runs inside another
+ * framework's memory pool or a real-time trigger process whose memory is fixed
+ * at start-up, or a process that must not grow its footprint.  This entry point
+ * allocates nothing: it writes the same arrays mkf_hitbins_export copies out of
+ * a bin store straight into caller-owned buffers, and keeps its working memory
+ * (histogram, scan partial sums, per-hit bin keys) in one statically sized
+ * device array inside libmkf.  That array (about 52 MB) is reserved on every GPU
+ * that loads the library, for as long as the library stays loaded.
+ *
+ *  xyz, layer, event_offsets, n_events, n_hits: as for mkf_hits_bin.
+ *  rec [n_hits][4] float, inv [n_hits] int32, offsets [n_bins + 1] int32:
+ *      device, caller-owned outputs, same layout and contents as
+ *      mkf_hitbins_export (n_bins = n_events * bins per event of the geometry).
+ * Limits: n_hits <= MKF_STATIC_MAX_HITS and n_bins <= MKF_STATIC_MAX_BINS, else
+ * MKF_ERR_CAPACITY and nothing is enqueued.
+ * The first call on a device looks up the device address of the working array
+ * (a runtime call, no allocation); make that first call before capturing the
+ * stream into a CUDA graph.  All calls on a device share the one working array:
+ * two calls whose work overlaps on the GPU (different streams or contexts
+ * without ordering between them) race and corrupt each other's results.
+ * Errors: MKF_ERR_ARG, MKF_ERR_GEOMETRY, MKF_ERR_CAPACITY, MKF_ERR_CUDA. */
+mkf_status mkf_hits_bin_static(mkf_ctx *ctx, const float *xyz, const int32_t *layer, const int32_t *event_offsets,
+                               int32_t n_events, int32_t n_hits, float *rec, int32_t *inv, int32_t *offsets);
+
 /* ------------------------------------------------------------------------ */
 /* Fit (Sec. 1: Kalman-filter fitting along known hits)                      */
 /* ------------------------------------------------------------------------ */

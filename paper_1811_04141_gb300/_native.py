@@ -28,11 +28,13 @@ ST_MISSSTOP = 16
 ST_TRUNC = 32
 
 MAX_LAYERS = 64
+STATIC_MAX_HITS = 1 << 22
+STATIC_MAX_BINS = 1 << 22
 MAX_NBEST = 16
 
 # Symbols declared in include/mkf.h (checked by the ABI test).
 EXPORTS = ("mkf_create", "mkf_destroy", "mkf_set_stream", "mkf_sync", "mkf_status_string", "mkf_geometry_load",
-           "mkf_hits_bin", "mkf_hitbins_free", "mkf_hitbins_info", "mkf_hitbins_export", "mkf_fit", "mkf_find")
+           "mkf_hits_bin", "mkf_hitbins_free", "mkf_hitbins_info", "mkf_hitbins_export", "mkf_hits_bin_static", "mkf_fit", "mkf_find")
 
 
 class MkfLayer(C.Structure):
@@ -89,6 +91,8 @@ def lib():
             L.mkf_hitbins_info.restype = i32
             L.mkf_hitbins_export.argtypes = [vp, vp, vp, vp, vp]
             L.mkf_hitbins_export.restype = i32
+            L.mkf_hits_bin_static.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp]
+            L.mkf_hits_bin_static.restype = i32
             L.mkf_fit.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
             L.mkf_fit.restype = i32
             L.mkf_find.argtypes = [vp, vp, vp, vp, i32, C.POINTER(MkfFindParams), vp, vp, vp, vp, vp, i32, vp, vp]

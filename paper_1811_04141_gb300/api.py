@@ -125,6 +125,23 @@ def mkf_hits_bin(ctx, xyz, layer, event_offsets, bins: HitBins | None = None, de
     return bins
 
 
+def mkf_hits_bin_static(ctx, xyz, layer, event_offsets, rec, inv, offsets, device: int | None = None) -> None:
+    """Binning into caller-owned buffers with no GPU allocation (for callers that
+    cannot allocate device memory); rec [n_hits, 4] float32, inv [n_hits] int32,
+    offsets [n_bins + 1] int32, filled like HitBins.export()."""
+    n = xyz.shape[1]
+    _need(xyz, "xyz", torch.float32, (3, n), device)
+    _need(layer, "layer", torch.int32, (n,), device)
+    _need(event_offsets, "event_offsets", torch.int32, None, device)
+    _need(rec, "rec", torch.float32, (n, 4), device)
+    _need(inv, "inv", torch.int32, (n,), device)
+    _need(offsets, "offsets", torch.int32, None, device)
+    h = ctx.handle if hasattr(ctx, "handle") else ctx
+    N.check("mkf_hits_bin_static", N.lib().mkf_hits_bin_static(
+        h, _ptr(xyz), _ptr(layer), _ptr(event_offsets), event_offsets.shape[0] - 1, n, _ptr(rec), _ptr(inv),
+        _ptr(offsets)))
+
+
 def mkf_fit(ctx, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, out=None, device: int | None = None):
     """Fit along fixed hit lists; returns dict(par [6,n], cov [21,n], chi2, ndf, status)."""
     n_hits = xyz.shape[1]

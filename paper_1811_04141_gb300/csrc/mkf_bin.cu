@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "mkf_internal.h"
 
@@ -334,5 +335,107 @@ extern "C" mkf_status mkf_hits_bin(mkf_ctx *ctx, const float *xyz, const int32_t
         MKF_CUDA_TRY(cudaGetLastError());
     }
     *inout = b;
+    return MKF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Binning without allocation: working memory in one file-scope device array.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr int64_t kStaticHits = MKF_STATIC_MAX_HITS;
+constexpr int64_t kStaticBins = MKF_STATIC_MAX_BINS;
+constexpr int64_t kStaticBlocks = (kStaticBins + kScanTile - 1) / kScanTile;
+constexpr size_t kOffCounts = 0;
+constexpr size_t kOffBlocks = align256(kOffCounts + sizeof(int32_t) * kStaticBins);
+constexpr size_t kOffKey = align256(kOffBlocks + sizeof(int32_t) * kStaticBlocks);
+constexpr size_t kOffZ = align256(kOffKey + sizeof(int32_t) * kStaticHits);
+constexpr size_t kOffLayer = align256(kOffZ + sizeof(float) * kStaticHits);
+constexpr size_t kStaticBytes = align256(kOffLayer + sizeof(uint8_t) * kStaticHits);
+
+// Reserved on every device that loads the library.  In host code this name is
+// only a stand-in: the device address comes from cudaGetSymbolAddress.
+__device__ __align__(256) unsigned char g_bin_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+unsigned char *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_bin_scratch on `device` (which must be current).
+mkf_status static_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= kMaxDevices) return MKF_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[device]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_bin_scratch) != cudaSuccess || !ptr) return MKF_ERR_CUDA;
+        g_scratch_addr[device] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_scratch_addr[device];
+    return MKF_OK;
+}
+
+}  // namespace
+
+extern "C" mkf_status mkf_hits_bin_static(mkf_ctx *ctx, const float *xyz, const int32_t *layer,
+                                          const int32_t *event_offsets, int32_t n_events, int32_t n_hits, float *rec,
+                                          int32_t *inv, int32_t *offsets) {
+    if (!ctx) return MKF_ERR_ARG;
+    if (!ctx->has_geom) return MKF_ERR_GEOMETRY;
+    if (n_events < 1 || n_hits < 0) return MKF_ERR_ARG;
+    if (!event_offsets || !offsets) return MKF_ERR_ARG;
+    if (n_hits > 0 && (!xyz || !layer || !rec || !inv)) return MKF_ERR_ARG;
+    const int64_t n_bins = (int64_t)n_events * ctx->geom.bins_per_event;
+    if (n_hits > kStaticHits || n_bins > kStaticBins) return MKF_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return MKF_ERR_CUDA;
+    unsigned char *base = nullptr;
+    mkf_status st = static_scratch(ctx->device, &base);
+    if (st != MKF_OK) return st;
+    int32_t *counts = reinterpret_cast<int32_t *>(base + kOffCounts);
+    int32_t *blocksums = reinterpret_cast<int32_t *>(base + kOffBlocks);
+    int32_t *key = reinterpret_cast<int32_t *>(base + kOffKey);
+    float *zhit = reinterpret_cast<float *>(base + kOffZ);
+    uint8_t *layer8 = base + kOffLayer;
+    float4 *rec4 = reinterpret_cast<float4 *>(rec);
+    cudaStream_t s = ctx->stream;
+    // the histogram starts at zero on every call (the array keeps the last call's contents)
+    MKF_CUDA_TRY(cudaMemsetAsync(counts, 0, n_bins * sizeof(int32_t), s));
+    if (n_hits > 0) {
+        BinArgs A;
+        A.G = ctx->geom;
+        A.X = xyz;
+        A.Y = xyz + n_hits;
+        A.Z = xyz + 2 * (int64_t)n_hits;
+        A.layer = layer;
+        A.event_offsets = event_offsets;
+        A.n_events = n_events;
+        A.n_hits = n_hits;
+        A.key = key;
+        A.layer8 = layer8;
+        A.zhit = zhit;
+        A.counts = counts;
+        A.fault = ctx->fault;
+        bin_keys_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(A);
+        MKF_CUDA_TRY(cudaGetLastError());
+    }
+    const int64_t nblk = (n_bins + kScanTile - 1) / kScanTile;
+    scan_tiles_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n_bins, blocksums);
+    MKF_CUDA_TRY(cudaGetLastError());
+    scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(blocksums, nblk, offsets, n_bins);
+    MKF_CUDA_TRY(cudaGetLastError());
+    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n_bins, blocksums, offsets);
+    MKF_CUDA_TRY(cudaGetLastError());
+    if (n_hits > 0) {
+        unsigned long long disk_mask = 0;
+        for (int l = 0; l < ctx->geom.n_layers; ++l)
+            if (ctx->geom.L[l].kind == 1) disk_mask |= 1ull << l;
+        scatter_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(xyz, xyz + n_hits, xyz + 2 * (int64_t)n_hits, key, layer8,
+                                                           n_hits, disk_mask, offsets, counts, rec4, inv);
+        MKF_CUDA_TRY(cudaGetLastError());
+        bin_sort_kernel<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(offsets, n_bins, rec4, inv);
+        MKF_CUDA_TRY(cudaGetLastError());
+    }
     return MKF_OK;
 }
