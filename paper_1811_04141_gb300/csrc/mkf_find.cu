@@ -15,11 +15,10 @@
 //      shuffles and applies the Kalman update with its hit;
 //   4. each lane records (parent rank, hit) in a per-step history in shared
 //      memory, walked back at the end to produce the best candidate's hit list.
-// The seed fit runs as the first three steps of the same loop with the seed
-// hits forced, so each heavy routine (propagation, transport, S, residual,
-// update) appears once in the kernel; a child reuses its parent's S^-1, H C and
-// hit residual instead of recomputing them.  No candidate state goes through
-// global memory between layers.
+// The seed fit runs before, in its own kernel with one thread per seed (in the
+// layer loop it would keep 9 of every 10 lanes idle for three steps).  A child
+// reuses its parent's S^-1, H C and hit residual instead of recomputing them.
+// No candidate state goes through global memory between layers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +55,13 @@ struct FindArgs {
     uint32_t *out_status;
     int32_t *counters;
     mkf_fault *fault;
+    float *seedbuf;  // [kSeedFields][n_seeds] fitted seeds (written by seed_kernel)
+};
+
+// Fitted-seed record, structure of arrays over seeds.
+enum {
+    SF_P = 0, SF_LO = 6, SF_C = 10, SF_CHI2 = 31, SF_BOOK = 32, SF_MASK_LO = 33, SF_MASK_HI = 34, SF_DIR = 35,
+    SF_STATUS = 36, SF_HITS = 37, kSeedFields = 40
 };
 
 __device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) {
@@ -198,6 +204,127 @@ __device__ __forceinline__ uint32_t seg_or(uint32_t v, int rank, int N) {
     return v;
 }
 
+// Seed fit, one thread per seed: state from the three hits (circle + line),
+// then the Kalman fit through them (the first hit without propagation), the
+// tracking region from the seed's eta, the direction along z and the first
+// layers beyond the third hit.
+__global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindArgs A) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.n_seeds) return;
+    const Geom &G = A.G;
+    const int n = A.n_seeds;
+    float *B = A.seedbuf;
+    const int ev = A.seed_event[t];
+    bool ok = ev >= 0 && ev < A.n_events;
+    float hx[3] = {0.f, 0.f, 0.f}, hy[3] = {0.f, 0.f, 0.f}, hz[3] = {0.f, 0.f, 0.f};
+    int hidx[3] = {-1, -1, -1}, hl[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        hidx[k] = A.seed_hits[(int64_t)k * n + t];
+        if (!ok) continue;
+        if (hidx[k] < 0 || hidx[k] >= A.n_hits) {
+            record_fault(A.fault, kFaultBadSeedHit, t);
+            ok = false;
+            continue;
+        }
+        const int pos = A.inv[hidx[k]];
+        hl[k] = A.layer8[hidx[k]];
+        if (pos < 0 || hl[k] >= G.n_layers) {
+            ok = false;
+            continue;
+        }
+        const float4 r = A.rec[pos];
+        hx[k] = r.x;
+        hy[k] = r.y;
+        hz[k] = A.zhit[hidx[k]];
+    }
+    float p[6], C[21], eta = 0.f, chi2 = 0.f;
+    Lo lo{0.f, 0.f, 0.f, 0.f};
+    if (ok) {
+        const float h1[3] = {hx[0], hy[0], hz[0]}, h2[3] = {hx[1], hy[1], hz[1]}, h3[3] = {hx[2], hy[2], hz[2]};
+        ok = seed_state(G.L[hl[0]], G.kb, h1, h2, h3, p, C, eta);
+    }
+    for (int k = 0; k < 3 && ok; ++k) {
+        const LayerDesc &Ld = G.L[hl[k]];
+        if (k > 0) {
+            float sphi, cphi, s;
+            sincos_pair(p[4], lo.phi, sphi, cphi);
+            const float cot = cot_of(p[5]);
+            if (!path_to_layer(Ld, G.kb, p, lo, sphi, cphi, cot, s)) {
+                ok = false;
+                break;
+            }
+            propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+        }
+        const Frame f = frame_of(p);
+        Innov I;
+        if (!innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
+            ok = false;
+            break;
+        }
+        float u, v;
+        const float zr = Ld.kind == 0 ? hz[k] : sqrtf(fmaf(hx[k], hx[k], hy[k] * hy[k]));
+        residual(Ld.kind, Ld.rz, p, lo, f, hx[k], hy[k], zr, u, v);
+        chi2 += chi2_of(I, u, v);
+        kf_apply(I, u, v, p, lo, C);
+    }
+    ok = ok && finite_state(p);
+    uint32_t status = ok ? 0u : MKF_ST_BADSEED;
+    unsigned long long mask = 0;
+    int dir = 1;
+    Book bk{3, 0, -1, -1, false, false};
+    if (ok) {
+        int region = 0;
+        while (region + 1 < G.n_regions && eta >= G.edges[region]) ++region;
+        mask = G.mask[region];
+        dir = cot_of(p[5]) >= 0.f ? 1 : -1;
+        const int l3 = hl[2];
+        const float r3 = sqrtf(fmaf(hx[2], hx[2], hy[2] * hy[2])), z3 = hz[2];
+        if (G.L[l3].kind == 0) {
+            const int pos = G.cyl_pos[l3] + 1;
+            bk.ncyl = pos < G.n_cyl ? pos : -1;
+        } else {
+            for (int i = 0; i < G.n_cyl; ++i)
+                if (G.L[G.cyl[i]].rz > r3) {
+                    bk.ncyl = i;
+                    break;
+                }
+        }
+        if (G.L[l3].kind == 1) {
+            const int nx = G.dsk_pos[l3] + dir;
+            bk.ndsk = (nx >= 0 && nx < G.n_dsk) ? nx : -1;
+        } else if (dir > 0) {
+            for (int i = 0; i < G.n_dsk; ++i)
+                if (G.L[G.dsk[i]].rz > z3) {
+                    bk.ndsk = i;
+                    break;
+                }
+        } else {
+            for (int i = G.n_dsk - 1; i >= 0; --i)
+                if (G.L[G.dsk[i]].rz < z3) {
+                    bk.ndsk = i;
+                    break;
+                }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) B[(SF_P + i) * (int64_t)n + t] = p[i];
+    B[(SF_LO + 0) * (int64_t)n + t] = lo.x;
+    B[(SF_LO + 1) * (int64_t)n + t] = lo.y;
+    B[(SF_LO + 2) * (int64_t)n + t] = lo.z;
+    B[(SF_LO + 3) * (int64_t)n + t] = lo.phi;
+#pragma unroll
+    for (int k = 0; k < 21; ++k) B[(SF_C + k) * (int64_t)n + t] = C[k];
+    B[SF_CHI2 * (int64_t)n + t] = chi2;
+    B[SF_BOOK * (int64_t)n + t] = __uint_as_float(pack_book(bk));
+    B[SF_MASK_LO * (int64_t)n + t] = __uint_as_float(static_cast<uint32_t>(mask));
+    B[SF_MASK_HI * (int64_t)n + t] = __uint_as_float(static_cast<uint32_t>(mask >> 32));
+    B[SF_DIR * (int64_t)n + t] = __int_as_float(dir);
+    B[SF_STATUS * (int64_t)n + t] = __uint_as_float(status);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) B[(SF_HITS + k) * (int64_t)n + t] = __int_as_float(hidx[k]);
+}
+
 __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ FindArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Geom SG;
@@ -245,70 +372,45 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     int c_cl = 0, c_ht = 0, c_up = 0;
     int dir = 1, ev = 0;
     unsigned long long mask = 0;
-    // seed hits (rank-0 lane): index, layer, position
-    int sh0 = -1, sh1 = -1, sh2 = -1, sl0 = 0, sl1 = 0, sl2 = 0;
-    float r3 = 0.f, z3 = 0.f;
+    int sh0 = -1, sh1 = -1, sh2 = -1;
 
-    // ---- seed state from three hits (rank-0 lane); the seed fit runs as the
-    // first three steps of the layer loop, with the seed hits forced
+    // ---- the fitted seed (rank-0 lane), from seed_kernel
     if (has_seed && rank == 0) {
+        const float *Bs = A.seedbuf;
+        const int64_t n = A.n_seeds;
+        status = __float_as_uint(Bs[SF_STATUS * n + seed]);
         ev = A.seed_event[seed];
-        bool ok = ev >= 0 && ev < A.n_events;
-        float hx[3], hy[3], hz[3];
-        int hidx[3], hl[3];
+        if (!(status & MKF_ST_BADSEED)) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            hidx[k] = A.seed_hits[(int64_t)k * A.n_seeds + seed];
-            hl[k] = 0;
-            hx[k] = hy[k] = hz[k] = 0.f;
-            if (!ok) continue;
-            if (hidx[k] < 0 || hidx[k] >= A.n_hits) {
-                record_fault(A.fault, kFaultBadSeedHit, seed);
-                ok = false;
-                continue;
-            }
-            const int pos = A.inv[hidx[k]];
-            hl[k] = A.layer8[hidx[k]];
-            if (pos < 0 || hl[k] >= G.n_layers) {
-                ok = false;
-                continue;
-            }
-            const float4 r = A.rec[pos];
-            hx[k] = r.x;
-            hy[k] = r.y;
-            hz[k] = A.zhit[hidx[k]];
-        }
-        float eta = 0.f;
-        if (ok) {
-            float h1[3] = {hx[0], hy[0], hz[0]}, h2[3] = {hx[1], hy[1], hz[1]}, h3[3] = {hx[2], hy[2], hz[2]};
-            ok = seed_state(G.L[hl[0]], G.kb, h1, h2, h3, p, C, eta);
-        }
-        if (ok) {
-            int region = 0;
-            while (region + 1 < G.n_regions && eta >= G.edges[region]) ++region;
-            mask = G.mask[region];
-            sh0 = hidx[0]; sh1 = hidx[1]; sh2 = hidx[2];
-            sl0 = hl[0]; sl1 = hl[1]; sl2 = hl[2];
-            r3 = sqrtf(fmaf(hx[2], hx[2], hy[2] * hy[2]));
-            z3 = hz[2];
-            bk.nh = 0;
-            bk.done = false;
+            for (int i = 0; i < 6; ++i) p[i] = Bs[(SF_P + i) * n + seed];
+            lo.x = Bs[(SF_LO + 0) * n + seed];
+            lo.y = Bs[(SF_LO + 1) * n + seed];
+            lo.z = Bs[(SF_LO + 2) * n + seed];
+            lo.phi = Bs[(SF_LO + 3) * n + seed];
+#pragma unroll
+            for (int k = 0; k < 21; ++k) C[k] = Bs[(SF_C + k) * n + seed];
+            chi2 = Bs[SF_CHI2 * n + seed];
+            bk = unpack_book(__float_as_uint(Bs[SF_BOOK * n + seed]));
+            mask = static_cast<unsigned long long>(__float_as_uint(Bs[SF_MASK_LO * n + seed])) |
+                   (static_cast<unsigned long long>(__float_as_uint(Bs[SF_MASK_HI * n + seed])) << 32);
+            dir = __float_as_int(Bs[SF_DIR * n + seed]);
+            sh0 = __float_as_int(Bs[(SF_HITS + 0) * n + seed]);
+            sh1 = __float_as_int(Bs[(SF_HITS + 1) * n + seed]);
+            sh2 = __float_as_int(Bs[(SF_HITS + 2) * n + seed]);
             live = true;
-        } else {
-            status |= MKF_ST_BADSEED;
         }
     }
     {
         const int src = lane_used ? base : lane;
         ev = __shfl_sync(kFull, ev, src);
         mask = __shfl_sync(kFull, mask, src);
+        dir = __shfl_sync(kFull, dir, src);
     }
 
     int step = 0;
     while (true) {
         const bool active = live && !bk.done;
         if (!__any_sync(kFull, active)) break;  // every candidate of the warp has finished
-        const bool seeding = step < 3;          // warp-uniform
         // ---- 1. expansion: next layer, propagation, window search
         int nlist = 0;
         bool searched = false;
@@ -317,40 +419,19 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             sincos_pair(p[4], lo.phi, sphi, cphi);
             const float cot = cot_of(p[5]);
             float s = 0.f;
-            int l;
-            if (seeding) {
-                l = step == 0 ? sl0 : (step == 1 ? sl1 : sl2);
-                if (step > 0 && !path_to_layer(G.L[l], G.kb, p, lo, sphi, cphi, cot, s)) l = -3;
-            } else {
-                l = finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
-            }
+            const int l =
+                finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
             if (l == -2) status |= MKF_ST_NONFINITE;
-            if (l == -3) {
-                status |= MKF_ST_BADSEED;
-                live = false;
-            } else if (l < 0) {
+            if (l < 0) {
                 bk.done = true;
             } else {
                 const LayerDesc &Ld = G.L[l];
-                if (!(seeding && step == 0)) propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-                if (!seeding) {
-                    searched = true;
-                    ++c_cl;
-                }
+                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+                searched = true;
+                ++c_cl;
                 const Frame f = frame_of(p);
                 if (innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
-                    if (seeding) {
-                        // the seed hit, accepted whatever its chi2
-                        const int h = step == 0 ? sh0 : (step == 1 ? sh1 : sh2);
-                        const float4 hr = A.rec[A.inv[h]];
-                        float u, v;
-                        residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
-                        lchi[lane] = chi2_of(I, u, v);
-                        lorig[lane] = h;
-                        lu[lane] = u;
-                        lv[lane] = v;
-                        nlist = 1;
-                    } else {
+                    {
                         const float wu = sqrtf(cut * I.Suu), wv = sqrtf(cut * I.Svv);
                         const float wu_m = wu * 1.0001f, wv_m = wv * 1.0001f;
                         const float lever = Ld.kind == 0 ? Ld.rz : f.rt;
@@ -416,10 +497,6 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                     }
                 } else {
                     status |= MKF_ST_BADS;
-                    if (seeding) {
-                        status |= MKF_ST_BADSEED;
-                        live = false;
-                    }
                 }
             }
         }
@@ -430,7 +507,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
         // compared as an order-preserving 32-bit integer; exact score ties (rare)
         // are resolved by a second reduction on (parent rank, hit index).
         const float score = cut * static_cast<float>(bk.nh) - chi2;
-        const int n_children = live ? (seeding ? nlist : (searched ? nlist + 1 : 1)) : 0;
+        const int n_children = live ? (searched ? nlist + 1 : 1) : 0;
         int head = 0;
         unsigned long long mine = 0;
         if (N == 1) {
@@ -511,42 +588,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                 kf_apply(I, u, v, p, lo, C);
                 bk.nh += 1;
                 bk.consec = 0;
-                if (!seeding) ++c_up;
-                if (seeding && step == 2) {
-                    // direction along z and the first layers beyond the seed
-                    const float cot = cot_of(p[5]);
-                    dir = cot >= 0.f ? 1 : -1;
-                    if (G.L[sl2].kind == 0) {
-                        const int pos = G.cyl_pos[sl2] + 1;
-                        bk.ncyl = pos < G.n_cyl ? pos : -1;
-                    } else {
-                        bk.ncyl = -1;
-                        for (int i = 0; i < G.n_cyl; ++i)
-                            if (G.L[G.cyl[i]].rz > r3) {
-                                bk.ncyl = i;
-                                break;
-                            }
-                    }
-                    if (G.L[sl2].kind == 1) {
-                        const int nx = G.dsk_pos[sl2] + dir;
-                        bk.ndsk = (nx >= 0 && nx < G.n_dsk) ? nx : -1;
-                    } else {
-                        bk.ndsk = -1;
-                        if (dir > 0) {
-                            for (int i = 0; i < G.n_dsk; ++i)
-                                if (G.L[G.dsk[i]].rz > z3) {
-                                    bk.ndsk = i;
-                                    break;
-                                }
-                        } else {
-                            for (int i = G.n_dsk - 1; i >= 0; --i)
-                                if (G.L[G.dsk[i]].rz < z3) {
-                                    bk.ndsk = i;
-                                    break;
-                                }
-                        }
-                    }
-                }
+                ++c_up;
             } else if (code == kCodeMiss) {
                 bk.consec += 1;
                 if (bk.consec >= A.max_consec) {
@@ -555,10 +597,6 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                 }
             }
             hist[step * 32 + lane] = (static_cast<uint32_t>(prank) << 28) | code;
-        }
-        if (seeding && step == 2) {
-            // the seed fit is over: the direction is shared by the seed's lanes
-            dir = __shfl_sync(kFull, dir, lane_used ? base : lane);
         }
         ++step;
         if (step >= A.max_steps) {
@@ -579,6 +617,8 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
         const bool ok = !(status & MKF_ST_BADSEED) && live;
         int nout = 0;
         if (ok) {
+            const int shs[3] = {sh0, sh1, sh2};
+            for (int k = 0; k < 3 && nout < A.max_out; ++k) A.out_hits[(int64_t)(nout++) * n + seed] = shs[k];
             // walk the history back from the best candidate, then write forwards
             int r = 0, cnt = 0;
             for (int st = step - 1; st >= 0; --st) {
@@ -586,7 +626,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                 if ((rec & kHitMask) < kCodeMiss) ++cnt;
                 r = static_cast<int>(rec >> 28);
             }
-            int pos = cnt - 1;
+            int pos = nout + cnt - 1;
             r = 0;
             for (int st = step - 1; st >= 0; --st) {
                 const uint32_t rec = hist[st * 32 + base + r];
@@ -597,8 +637,8 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                 }
                 r = static_cast<int>(rec >> 28);
             }
-            if (cnt > A.max_out) status |= MKF_ST_TRUNC;
-            nout = min(cnt, A.max_out);
+            if (nout + cnt > A.max_out) status |= MKF_ST_TRUNC;
+            nout = min(nout + cnt, A.max_out);
             if (bk.missstop) status |= MKF_ST_MISSSTOP;
             if (!finite_state(p) || !isfinite(chi2)) status |= MKF_ST_NONFINITE;
         }
@@ -625,8 +665,8 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
 
 }  // namespace
 
-// steps: 3 seed steps + at most one per layer + one final step with no layer left
-static int find_max_steps(int n_layers) { return n_layers + 5; }
+// steps: at most one per layer + one final step with no layer left
+static int find_max_steps(int n_layers) { return n_layers + 2; }
 
 static size_t find_smem_bytes(int n_layers, int n_best, int threads) {
     const int nwarps = threads / 32;
@@ -681,6 +721,12 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     if (smem > 200 * 1024) return MKF_ERR_CAPACITY;
     MKF_CUDA_TRY(cudaFuncSetAttribute(find_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(std::max<size_t>(smem, 48 * 1024))));
+    void *scratch = nullptr;
+    mkf_status st = mkf_scratch(ctx, sizeof(float) * (size_t)kSeedFields * n_seeds, &scratch);
+    if (st != MKF_OK) return st;
+    A.seedbuf = static_cast<float *>(scratch);
+    seed_kernel<<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A);
+    MKF_CUDA_TRY(cudaGetLastError());
     const int spw = 32 / N;
     const int seeds_per_block = spw * (threads / 32);
     const int blocks = (n_seeds + seeds_per_block - 1) / seeds_per_block;
