@@ -308,7 +308,7 @@ def run_ours(args, world, rank, local, pg):
                "sample": f"{nseeds} randomly chosen seeds of the {batch.n_seeds} in the workload (all hits of "
                          f"their events), {secs:.1f} s on one host core, FP64"}
 
-    launches_per_step = 7  # bin_keys, scan_tiles, scan_blocksums, scan_write, scatter, bin_sort, find
+    launches_per_step = 8  # bin_keys, scan_tiles, scan_blocksums, scan_write, scatter, bin_sort, seed, find
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(step_ms_max, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
