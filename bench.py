@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline sample")
     ap.add_argument("--events", type=int, default=EVENTS, help="events per GPU (profiling runs only)")
     ap.add_argument("--n-best", type=int, default=N_BEST, help="candidates kept per seed (profiling runs only)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-pruning comparison")
     return ap.parse_args()
 
 
@@ -184,6 +185,89 @@ def oracle_rate(batch, target_s: float):
 
 
 # ---------------------------------------------------------------------------
+# learned pruning: events/s of the MLP-pruned finder vs the plain finder
+# ---------------------------------------------------------------------------
+
+def learned_leg(dev, reps: int = 30):
+    """Dense events (17 cylinders + 2 x 14 disks, 6000 tracks + 200k noise hits
+    per event): train the MLP on features the plain finder dumps on 10 training
+    events (labels from truth), take the largest threshold whose efficiency stays
+    within 0.5 points of the plain finder on those events, then time both finders
+    (binning + finding) on 10 held-out events."""
+    import torch
+
+    from paper_1811_04141_gb300 import Context
+    from paper_1811_04141_gb300 import learned as L
+    from synth import make_batch
+    tr = make_batch("dense45", list(range(1000, 1010)))
+    ev = make_batch("dense45", list(range(10)))
+    ctx = Context(dev.index, torch.cuda.current_stream(dev))
+    ctx.geometry_load(tr.layers, tr.bz)
+
+    def prep(b):
+        to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        d = dict(xyz=to(b.xyz, torch.float32), layer=to(b.layer, torch.int32), evo=to(b.event_offsets, torch.int32),
+                 sh=to(b.seed_hits, torch.int32), se=to(b.seed_event, torch.int32),
+                 hp=to(b.hit_particle, torch.int32), sp=to(b.seed_particle, torch.int32))
+        d["bins"] = ctx.hits_bin(d["xyz"], d["layer"], d["evo"])
+        return d
+
+    dt, de = prep(tr), prep(ev)
+    feat, ref = L.collect_features(ctx, dt["bins"], dt["sh"], dt["se"], 8_000_000, n_best=N_BEST)
+    lab = L.label_pairs(ref, dt["hp"], dt["sp"])
+    st = L.train(ctx, feat, lab, steps=1500, batch=4096, lr=2e-3)
+    max_out = len(tr.layers) + 3
+
+    def run(d, tau=None):
+        kw = dict(n_best=N_BEST, max_out=max_out)
+        if tau is not None:
+            kw.update(mlp_bf16=st["w_bf16"], mlp_tau=tau)
+        out = ctx.find(d["bins"], d["sh"], d["se"], **kw)
+        ctx.sync()
+        e, f = L.efficiency(out["hits"], d["hp"], d["sp"])
+        return e, f, out["counters"].sum(dim=1).cpu().numpy()
+
+    e0, f0, _ = run(dt)
+    best = L.choose_tau(lambda t: run(dt, t)[:2], e0, [-4.0, -2.0, -1.0, 0.0, 1.0, 2.0, 3.0])
+    tau = best[0] if best else None
+
+    def timed(tau_):
+        kw = dict(n_best=N_BEST, max_out=max_out)
+        if tau_ is not None:
+            kw.update(mlp_bf16=st["w_bf16"], mlp_tau=tau_)
+        out = ctx.find(de["bins"], de["sh"], de["se"], **kw)
+        for _ in range(3):
+            ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
+            ctx.find(de["bins"], de["sh"], de["se"], out=out, **kw)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
+            ctx.find(de["bins"], de["sh"], de["se"], out=out, **kw)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_plain = timed(None)
+    ms_pruned = timed(tau) if tau is not None else None
+    ep, fp, cp = run(de)
+    res = {"workload": "dense45: 17 cylinders + 2x14 disks, 6000 tracks (pT^-3 from 0.5 GeV) + 200k noise hits "
+                       "per event; trained on 10 events, evaluated on 10 held-out events; N=10",
+           "metric": "events/s (hit binning + finding)", "train_pairs": int(feat.shape[0]),
+           "train_loss_first_last": [st["losses"][0], st["losses"][-1]] if st["losses"] else None,
+           "plain": {"events_per_s": 10 / (ms_plain * 1e-3), "ms": ms_plain, "efficiency": ep, "fake_rate": fp,
+                     "cand_layers": int(cp[0]), "updates": int(cp[2])}}
+    if tau is not None:
+        el, fl, cl = run(de, tau)
+        res["pruned"] = {"tau": tau, "events_per_s": 10 / (ms_pruned * 1e-3), "ms": ms_pruned, "efficiency": el,
+                         "fake_rate": fl, "cand_layers": int(cl[0]), "updates": int(cl[2])}
+        res["pruned_over_plain_events_per_s"] = ms_plain / ms_pruned
+    ctx.close()
+    return res
+
+
+# ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
 
@@ -308,6 +392,10 @@ def run_ours(args, world, rank, local, pg):
                "sample": f"{nseeds} randomly chosen seeds of the {batch.n_seeds} in the workload (all hits of "
                          f"their events), {secs:.1f} s on one host core, FP64"}
 
+    learned = None
+    if rank == 0 and world == 1 and not args.no_learned:
+        learned = learned_leg(dev)
+
     launches_per_step = 8  # bin_keys, scan_tiles, scan_blocksums, scan_write, scatter, bin_sort, seed, find
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -321,7 +409,7 @@ def run_ours(args, world, rank, local, pg):
                    "updates_per_step_per_gpu": up, "bin_ms": round(bin_ms, 4), "find_ms": round(find_ms, 4),
                    "l2": "flushed between steps (256 MiB write, outside the per-step CUDA events)",
                    "wall_s_timed_region": round(wall, 3), "parallelism": f"events sharded, {world} GPU(s)"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "learned": learned,
         "gpu_launches": launches_per_step * K,
     }
     if rank == 0:

@@ -222,6 +222,27 @@ typedef struct {
     float chi2_cut;          /* a hit is compatible when its chi2 < chi2_cut (> 0) */
     int32_t max_consec_miss; /* a candidate stops after this many misses in a row (1..15) */
     int32_t block_threads;   /* CUDA block size, multiple of 32 in 32..256; 0 = default (128) */
+    /* Learned pruning (not in the paper): when mlp_bf16 is not NULL and a
+     * candidate has two or more compatible hits on a layer, each of its N best
+     * compatible hits (by chi2) is scored by the MLP (device, MKF_MLP_PARAMS
+     * bfloat16 weights) and dropped when its logit < mlp_tau; the child without
+     * a hit is never dropped.  Features of a (candidate, hit) pair, in order:
+     * u/sqrt(S_uu), v/sqrt(S_vv), chi2/chi2_cut, chi2_total/max(1, 2 n_hits - 5),
+     * n_hits/10, n_miss/5, layer/n_layers, is_disk, q/pT, eta/3,
+     * log10 sqrt(S_uu), log10 sqrt(S_vv) -- candidate quantities before the hit. */
+    const uint16_t *mlp_bf16;
+    float mlp_tau;
+    /* Feature dump (training data): when feat_out is not NULL, the features of
+     * each candidate's N best compatible hits (before any pruning) go to
+     * feat_out [feat_cap][12] (device) with (seed index, hit index, number of
+     * compatible hits of the candidate on that layer) in feat_ref [feat_cap][3];
+     * the device counter *feat_count (caller zeroes it) ends at the number of
+     * pairs seen, of which min(count, feat_cap) were written, in no particular
+     * order. */
+    float *feat_out;
+    int32_t *feat_ref;
+    int32_t *feat_count;
+    int32_t feat_cap;
 } mkf_find_params;
 
 /* Find tracks from seeds.
@@ -245,6 +266,46 @@ typedef struct {
 mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int32_t *seed_hits, const int32_t *seed_event,
                     int32_t n_seeds, const mkf_find_params *params, float *out_par, float *out_cov, float *chi2,
                     int32_t *n_hits, int32_t *hit_idx, int32_t max_out, uint32_t *status, int32_t *counters);
+
+/* ------------------------------------------------------------------------ */
+/* Learned hit ranking (not in the paper: a small MLP that scores a          */
+/* (candidate, compatible hit) pair so that branching can be pruned before   */
+/* the Kalman update; trained here by these kernels)                         */
+/* ------------------------------------------------------------------------ */
+
+#define MKF_MLP_IN 12
+#define MKF_MLP_HIDDEN 64
+#define MKF_MLP_PARAMS (MKF_MLP_IN * MKF_MLP_HIDDEN + 2 * MKF_MLP_HIDDEN + 1) /* 897 */
+/* Parameter layout: W1[64][12] (row = hidden unit), b1[64], w2[64], b2.
+ * logit = w2 . relu(W1 x + b1) + b2, computed in FP32 with the weights rounded
+ * to bfloat16 (round to nearest, ties to even). */
+
+typedef struct {
+    float lr, beta1, beta2, eps; /* Adam hyper-parameters (e.g. 1e-3, 0.9, 0.999, 1e-8) */
+} mkf_adam;
+
+/* FP32 -> bfloat16 (uint16 bit patterns), n values, device arrays.
+ * Errors: MKF_ERR_ARG, MKF_ERR_CUDA. */
+mkf_status mkf_mlp_to_bf16(mkf_ctx *ctx, const float *w, uint16_t *w_bf16, int32_t n);
+
+/* Logits of n feature rows.  w_bf16 [MKF_MLP_PARAMS], feat [n][12], logit [n]:
+ * device.  Errors: MKF_ERR_ARG, MKF_ERR_CUDA. */
+mkf_status mkf_mlp_forward(mkf_ctx *ctx, const uint16_t *w_bf16, const float *feat, int32_t n, float *logit);
+
+/* Mean binary cross-entropy of the logits against labels (0 or 1) and its
+ * gradient with respect to the (bfloat16-rounded) weights.  feat [n][12],
+ * label [n], grad [MKF_MLP_PARAMS], loss [1]: device.  The batch sum runs in a
+ * fixed order: the result does not depend on scheduling.
+ * Errors: MKF_ERR_ARG, MKF_ERR_CUDA. */
+mkf_status mkf_mlp_grad(mkf_ctx *ctx, const uint16_t *w_bf16, const float *feat, const float *label, int32_t n,
+                        float *grad, float *loss);
+
+/* One Adam training step: gradient as mkf_mlp_grad with the weights w rounded
+ * to bfloat16, then m, v and the FP32 master weights w updated in place (t is
+ * the 1-based step number) and w_bf16 refreshed.  loss may be NULL.
+ * Errors: MKF_ERR_ARG, MKF_ERR_CUDA. */
+mkf_status mkf_mlp_train_step(mkf_ctx *ctx, const float *feat, const float *label, int32_t n, float *w, float *m,
+                              float *v, int32_t t, const mkf_adam *hp, uint16_t *w_bf16, float *loss);
 
 #ifdef __cplusplus
 }

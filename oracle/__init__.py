@@ -63,7 +63,8 @@ def _load():
             lib.or_fit.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, d, d, d, i32, u32]
             lib.or_fit.restype = C.c_int
             lib.or_find.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, i32, i32, C.c_int64, i64, C.c_int64,
-                                           C.c_int, C.c_double, C.c_int, d, d, d, i32, i32, C.c_int, u32, i64, d]
+                                           C.c_int, C.c_double, C.c_int, d, d, d, i32, i32, C.c_int, u32, i64, d,
+                                           d, C.c_double, d, i32, i64, C.c_int64]
             lib.or_find.restype = C.c_int
             _lib = lib
     return _lib
@@ -194,8 +195,10 @@ def fit(geo: Geometry, xyz, hit_layer, hit_idx, seed_par=None, seed_cov21=None):
 
 
 def find(geo: Geometry, xyz, hit_layer, event_offsets, seed_hits, seed_event, n_best=10, chi2_cut=30.0,
-         max_consec=3, seed_list=None, max_out=None):
-    """Track finding (n_best = 1: best hit; > 1: N best candidates per seed)."""
+         max_consec=3, seed_list=None, max_out=None, mlp_w=None, mlp_tau=0.0, dump_cap=0):
+    """Track finding (n_best = 1: best hit; > 1: N best candidates per seed).
+    mlp_w: 897 MLP weights (use the bfloat16-rounded values) turns on pruning at
+    mlp_tau; dump_cap > 0 returns the features of compatible hits."""
     lib = _load()
     xyz = _f64(xyz)
     n_hits = xyz.shape[1]
@@ -213,16 +216,25 @@ def find(geo: Geometry, xyz, hit_layer, event_offsets, seed_hits, seed_event, n_
     hits = np.zeros((max_out, nl), dtype=np.int32)
     st = np.zeros(nl, dtype=np.uint32)
     cnt = np.zeros((3, nl), dtype=np.int64)
-    marg = np.zeros((3, nl))
+    marg = np.zeros((4, nl))
+    mw = None if mlp_w is None else _f64(mlp_w)
+    feat = np.zeros((max(1, dump_cap), 12)) if dump_cap else None
+    fref = np.zeros((max(1, dump_cap), 3), dtype=np.int32) if dump_cap else None
+    fcnt = np.zeros(1, dtype=np.int64)
     rc = lib.or_find(*geo.args(), _p(xyz, C.c_double), n_hits, _p(hit_layer, C.c_int32),
                      _p(event_offsets, C.c_int32), event_offsets.shape[0] - 1, _p(seed_hits, C.c_int32),
                      _p(seed_event, C.c_int32), n_seeds, _p(sl, C.c_int64), nl, int(n_best), float(chi2_cut),
                      int(max_consec), _p(par, C.c_double), _p(cov, C.c_double), _p(chi2, C.c_double),
                      _p(nh, C.c_int32), _p(hits, C.c_int32), int(max_out), _p(st, C.c_uint32), _p(cnt, C.c_int64),
-                     _p(marg, C.c_double))
+                     _p(marg, C.c_double), _p(mw, C.c_double), float(mlp_tau), _p(feat, C.c_double),
+                     _p(fref, C.c_int32), _p(fcnt, C.c_int64), int(dump_cap))
     if rc != 0:
         raise RuntimeError(f"or_find failed: {rc}")
-    return dict(par=par, cov=cov, chi2=chi2, n_hits=nh, hits=hits, status=st, counters=cnt, margins=marg)
+    out = dict(par=par, cov=cov, chi2=chi2, n_hits=nh, hits=hits, status=st, counters=cnt, margins=marg)
+    if dump_cap:
+        k = int(min(fcnt[0], dump_cap))
+        out.update(feat=feat[:k], feat_ref=fref[:k], feat_count=int(fcnt[0]))
+    return out
 
 
 def geometry_for(batch, region_edges=None, region_masks=None) -> Geometry:

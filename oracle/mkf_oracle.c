@@ -545,6 +545,7 @@ typedef struct {
     double chi2;  /* chi2 of the hit */
     double score;
     int layer;
+    double u, v;  /* residual of the hit */
 } child_t;
 
 typedef struct {
@@ -563,6 +564,13 @@ typedef struct {
     double cut;
     int max_consec;
     int n_best;
+    const double *mlp;   /* 897 weights (bfloat16 values) or NULL */
+    double tau;
+    double *feat;        /* [cap][12] or NULL */
+    int32_t *feat_ref;   /* [cap][2] */
+    int64_t *feat_n;
+    int64_t feat_cap;
+    int seed_index;
 } find_ctx_t;
 
 static int cmp_child(const child_t *a, const child_t *b) {
@@ -572,6 +580,12 @@ static int cmp_child(const child_t *a, const child_t *b) {
     unsigned hb = b->hit < 0 ? 0xFFFFFFFFu : (unsigned)b->hit;
     if (ha != hb) return ha < hb ? -1 : 1;
     return 0;
+}
+
+/* order of one parent's hit children: chi2, then hit index */
+static int cmp_hit_child(const child_t *a, const child_t *b) {
+    if (a->chi2 != b->chi2) return a->chi2 < b->chi2 ? -1 : 1;
+    return a->hit < b->hit ? -1 : (a->hit > b->hit ? 1 : 0);
 }
 
 static int cmp_child_q(const void *a, const void *b) { return cmp_child((const child_t *)a, (const child_t *)b); }
@@ -691,15 +705,50 @@ static int push_hist(histvec_t *hv, int prev, int hit) {
     return hv->n++;
 }
 
+/* Features of a (candidate, compatible hit) pair: residual pulls, chi2 of the
+ * hit over the cut, the candidate's chi2 per degree of freedom, hit and miss
+ * counts, layer, layer kind, q/pT, eta, and the log widths of the residual
+ * covariance.  The miss count saturates at 15. */
+static void pair_features(const find_ctx_t *f, const cand_t *c, int l, const double r[2], const double S[4], double x2,
+                          double fe[12]) {
+    const geom_t *g = f->g;
+    double su = sqrt(S[0]), sv = sqrt(S[3]);
+    int nm = c->n_miss < 15 ? c->n_miss : 15;
+    int ndf = 2 * c->n_hits - 5;
+    fe[0] = r[0] / su;
+    fe[1] = r[1] / sv;
+    fe[2] = x2 / f->cut;
+    fe[3] = c->chi2 / (ndf > 1 ? ndf : 1);
+    fe[4] = c->n_hits * 0.1;
+    fe[5] = nm * 0.2;
+    fe[6] = (double)l / g->n;
+    fe[7] = g->kind[l] == 1 ? 1.0 : 0.0;
+    fe[8] = c->p[3];
+    fe[9] = asinh(cot_of(c->p[5])) / 3.0;
+    fe[10] = log10(su);
+    fe[11] = log10(sv);
+}
+
+/* 12 -> 64 ReLU -> 1; weights W1[64][12], b1[64], w2[64], b2. */
+static double mlp_logit(const double *w, const double fe[12]) {
+    double z = w[896];
+    for (int j = 0; j < 64; ++j) {
+        double a = w[768 + j];
+        for (int k = 0; k < 12; ++k) a += w[j * 12 + k] * fe[k];
+        z += w[832 + j] * (a > 0 ? a : 0.0);
+    }
+    return z;
+}
+
 /* Find one seed.  Returns 0, or -1 on allocation failure. */
 static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *outp, double *outC,
                     double *out_chi2, int32_t *out_nhits, int32_t *out_hits, int max_out, uint32_t *out_status,
-                    int64_t cnt[3], double marg[3]) {
+                    int64_t cnt[3], double marg[4]) {
     const geom_t *g = f->g;
     const int L = g->n;
     uint32_t st = 0;
     cnt[0] = cnt[1] = cnt[2] = 0;
-    marg[0] = marg[1] = marg[2] = INFINITY;
+    marg[0] = marg[1] = marg[2] = marg[3] = INFINITY;
     cand_t *cands = (cand_t *)calloc((size_t)f->n_best, sizeof(cand_t));
     cand_t *nextc = (cand_t *)calloc((size_t)f->n_best, sizeof(cand_t));
     childvec_t cv = {0, 0, 0};
@@ -794,6 +843,7 @@ static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *ou
             ch.parent = r;
             ch.chi2 = 0;
             ch.layer = -1;
+            ch.u = ch.v = 0;
             if (c->done) {
                 ch.hit = OR_HIT_PASS;
                 ch.score = c->score;
@@ -823,6 +873,7 @@ static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *ou
             int sok = residual_cov(g, l, c->C, H, S, Si, HC);
             if (sok) {
                 double wu = sqrt(f->cut * S[0]), wv = sqrt(f->cut * S[3]);
+                int n_pend = 0;
                 int32_t b0 = f->lay_start[(int64_t)ev * L + l], b1 = f->lay_start[(int64_t)ev * L + l + 1];
                 for (int32_t j = b0; j < b1; ++j) {
                     int hid = f->lay_hits[j];
@@ -845,9 +896,46 @@ static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *ou
                         ch.chi2 = x2;
                         ch.score = c->score + f->cut - x2;
                         ch.layer = l;
+                        ch.u = rv[0];
+                        ch.v = rv[1];
                         if (!push_child(&cv, ch)) goto oom;
+                        n_pend++;
                     }
                 }
+                /* the parent's children: its N best compatible hits (by chi2, then
+                 * hit index); with the MLP on and two or more compatible hits, those
+                 * whose logit is below tau are dropped */
+                int first = cv.n - n_pend;
+                for (int i = first + 1; i < cv.n; ++i)
+                    for (int j = i; j > first && cmp_hit_child(&cv.v[j - 1], &cv.v[j]) > 0; --j) {
+                        child_t t = cv.v[j]; cv.v[j] = cv.v[j - 1]; cv.v[j - 1] = t;
+                    }
+                int n_compat = n_pend;
+                if (n_pend > f->n_best) cv.n = first + f->n_best;
+                int kept = first;
+                for (int i = first; i < cv.n; ++i) {
+                    int drop = 0;
+                    if (f->feat || (f->mlp && n_compat >= 2)) {
+                        double fe[12], rr2[2] = {cv.v[i].u, cv.v[i].v};
+                        pair_features(f, c, l, rr2, S, cv.v[i].chi2, fe);
+                        if (f->feat) {
+                            int64_t at = (*f->feat_n)++;
+                            if (at < f->feat_cap) {
+                                for (int q = 0; q < 12; ++q) f->feat[at * 12 + q] = fe[q];
+                                f->feat_ref[at * 3] = f->seed_index;
+                                f->feat_ref[at * 3 + 1] = cv.v[i].hit;
+                                f->feat_ref[at * 3 + 2] = n_compat;
+                            }
+                        }
+                        if (f->mlp && n_compat >= 2) {
+                            double z = mlp_logit(f->mlp, fe);
+                            upd_min(&marg[3], fabs(z - f->tau));
+                            if (z < f->tau) drop = 1;
+                        }
+                    }
+                    if (!drop) cv.v[kept++] = cv.v[i];
+                }
+                cv.n = kept;
             } else {
                 st |= OR_ST_BADS;
             }
@@ -935,15 +1023,20 @@ oom:
  * n_best = 1 is best-hit finding, n_best > 1 keeps the N best candidates.
  * Outputs per seed: par [6][n], cov [21][n] (packed), chi2, n_hits,
  * hits [max_out][n] (-1 padded), status, counters [3][n] (candidate-layers,
- * hits inside the window rectangle, Kalman updates), margins [3][n]
+ * hits inside the window rectangle, Kalman updates), margins [4][n]
  * (closest score gap at a ranking decision, closest |chi2 - cut| / cut, closest
- * geometric decision).  seed_list (or NULL for all) selects which seeds to run;
+ * geometric decision, closest |logit - tau| of the pruning MLP).  mlp_w (897
+ * values, or NULL) turns on learned pruning: a compatible hit whose logit is
+ * below mlp_tau gives no child.  feat_out (or NULL) receives the 12 features of
+ * every compatible hit, with (seed, hit) in feat_ref and the running count in
+ * *feat_count (rows beyond feat_cap are counted, not written).  seed_list (or NULL for all) selects which seeds to run;
  * outputs are indexed by position in seed_list. */
 int or_find(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_layer, const int32_t *event_offsets,
             int n_events, const int32_t *seed_hits, const int32_t *seed_event, int64_t n_seeds,
             const int64_t *seed_list, int64_t n_list, int n_best, double chi2_cut, int max_consec,
             double *out_par, double *out_cov, double *out_chi2, int32_t *out_nhits, int32_t *out_hits, int max_out,
-            uint32_t *out_status, int64_t *out_counters, double *out_margins) {
+            uint32_t *out_status, int64_t *out_counters, double *out_margins, const double *mlp_w, double mlp_tau,
+            double *feat_out, int32_t *feat_ref, int64_t *feat_count, int64_t feat_cap) {
     geom_t g;
     if (geom_init(&g, GEOM_PASS)) return -1;
     if (n_best < 1 || max_out < 3 || max_consec < 1) return -1;
@@ -957,6 +1050,13 @@ int or_find(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_lay
     f.cut = chi2_cut;
     f.max_consec = max_consec;
     f.n_best = n_best;
+    f.mlp = mlp_w;
+    f.tau = mlp_tau;
+    f.feat = feat_out;
+    f.feat_ref = feat_ref;
+    f.feat_n = feat_count;
+    f.feat_cap = feat_cap;
+    if (feat_out && (!feat_ref || !feat_count)) return -1;
     /* sorted layer lists */
     for (int l = 0; l < L; ++l) {
         if (g.kind[l] == 0) f.cyl_sorted[f.n_cyl++] = l;
@@ -999,7 +1099,7 @@ int or_find(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_lay
     for (int64_t k = 0; k < nl && rc == 0; ++k) {
         int64_t sidx = seed_list ? seed_list[k] : k;
         int32_t sh[3] = {seed_hits[sidx], seed_hits[n_seeds + sidx], seed_hits[2 * n_seeds + sidx]};
-        double p[6], C[36], chi2, marg[3];
+        double p[6], C[36], chi2, marg[4];
         int32_t nh, hits[4 * OR_MAXL + 8];
         uint32_t st;
         int64_t cnt[3];
@@ -1010,6 +1110,7 @@ int or_find(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_lay
             rc = -3;
             break;
         }
+        f.seed_index = (int)sidx;
         if (find_one(&f, ev, sh, p, C, &chi2, &nh, hits, mo, &st, cnt, marg)) { rc = -2; break; }
         for (int i = 0; i < 6; ++i) out_par[(int64_t)i * nl + k] = p[i];
         pack21(C, out_cov + k, nl);
@@ -1018,7 +1119,7 @@ int or_find(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_lay
         for (int j = 0; j < max_out; ++j) out_hits[(int64_t)j * nl + k] = j < mo ? hits[j] : -1;
         out_status[k] = st;
         for (int j = 0; j < 3; ++j) out_counters[(int64_t)j * nl + k] = cnt[j];
-        for (int j = 0; j < 3; ++j) out_margins[(int64_t)j * nl + k] = marg[j];
+        for (int j = 0; j < 4; ++j) out_margins[(int64_t)j * nl + k] = marg[j];
     }
     free(PHI); free(RH); free(start); free(fill); free(lh);
     return rc;

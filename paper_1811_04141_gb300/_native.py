@@ -34,7 +34,8 @@ MAX_NBEST = 16
 
 # Symbols declared in include/mkf.h (checked by the ABI test).
 EXPORTS = ("mkf_create", "mkf_destroy", "mkf_set_stream", "mkf_sync", "mkf_status_string", "mkf_geometry_load",
-           "mkf_hits_bin", "mkf_hitbins_free", "mkf_hitbins_info", "mkf_hitbins_export", "mkf_hits_bin_static", "mkf_fit", "mkf_find")
+           "mkf_hits_bin", "mkf_hitbins_free", "mkf_hitbins_info", "mkf_hitbins_export", "mkf_hits_bin_static", "mkf_fit", "mkf_find", "mkf_mlp_to_bf16",
+           "mkf_mlp_forward", "mkf_mlp_grad", "mkf_mlp_train_step")
 
 
 class MkfLayer(C.Structure):
@@ -48,7 +49,18 @@ class MkfPlan(C.Structure):
 
 class MkfFindParams(C.Structure):
     _fields_ = [("n_best", C.c_int32), ("chi2_cut", C.c_float), ("max_consec_miss", C.c_int32),
-                ("block_threads", C.c_int32)]
+                ("block_threads", C.c_int32), ("mlp_bf16", C.c_void_p), ("mlp_tau", C.c_float),
+                ("feat_out", C.c_void_p), ("feat_ref", C.c_void_p), ("feat_count", C.c_void_p),
+                ("feat_cap", C.c_int32)]
+
+
+MLP_IN = 12
+MLP_HIDDEN = 64
+MLP_PARAMS = MLP_IN * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
+
+
+class MkfAdam(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
 class MkfError(RuntimeError):
@@ -93,6 +105,14 @@ def lib():
             L.mkf_hitbins_export.restype = i32
             L.mkf_hits_bin_static.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp]
             L.mkf_hits_bin_static.restype = i32
+            L.mkf_mlp_to_bf16.argtypes = [vp, vp, vp, i32]
+            L.mkf_mlp_to_bf16.restype = i32
+            L.mkf_mlp_forward.argtypes = [vp, vp, vp, i32, vp]
+            L.mkf_mlp_forward.restype = i32
+            L.mkf_mlp_grad.argtypes = [vp, vp, vp, vp, i32, vp, vp]
+            L.mkf_mlp_grad.restype = i32
+            L.mkf_mlp_train_step.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, C.POINTER(MkfAdam), vp, vp]
+            L.mkf_mlp_train_step.restype = i32
             L.mkf_fit.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
             L.mkf_fit.restype = i32
             L.mkf_find.argtypes = [vp, vp, vp, vp, i32, C.POINTER(MkfFindParams), vp, vp, vp, vp, vp, i32, vp, vp]

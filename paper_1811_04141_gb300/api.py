@@ -165,16 +165,41 @@ def mkf_fit(ctx, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, out=None
     return out
 
 
-def find_params(n_best=10, chi2_cut=30.0, max_consec_miss=3, block_threads=0) -> N.MkfFindParams:
-    return N.MkfFindParams(int(n_best), float(chi2_cut), int(max_consec_miss), int(block_threads))
+def find_params(n_best=10, chi2_cut=30.0, max_consec_miss=3, block_threads=0, mlp_bf16=None, mlp_tau=0.0,
+                feat=None) -> N.MkfFindParams:
+    prm = N.MkfFindParams(int(n_best), float(chi2_cut), int(max_consec_miss), int(block_threads))
+    if mlp_bf16 is not None:
+        prm.mlp_bf16 = mlp_bf16.data_ptr()
+        prm.mlp_tau = float(mlp_tau)
+    if feat is not None:
+        prm.feat_out = feat["feat"].data_ptr()
+        prm.feat_ref = feat["ref"].data_ptr()
+        prm.feat_count = feat["count"].data_ptr()
+        prm.feat_cap = int(feat["feat"].shape[0])
+    return prm
+
+
+def feature_buffer(cap: int, device="cuda") -> dict:
+    """Device buffers for the finder's feature dump (counter zeroed)."""
+    return dict(feat=torch.empty(cap, N.MLP_IN, device=device), ref=torch.empty(cap, 3, dtype=torch.int32, device=device),
+                count=torch.zeros(1, dtype=torch.int32, device=device))
 
 
 def mkf_find(ctx, bins: HitBins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
-             n_layers=None, out=None, counters=True, block_threads=0, device: int | None = None):
-    """Find tracks; returns dict(par, cov, chi2, n_hits, hits [max_out, n], status, counters [3, n])."""
+             n_layers=None, out=None, counters=True, block_threads=0, device: int | None = None, mlp_bf16=None,
+             mlp_tau=0.0, feat=None):
+    """Find tracks; returns dict(par, cov, chi2, n_hits, hits [max_out, n], status, counters [3, n]).
+    mlp_bf16 (int16 tensor of MLP_PARAMS bfloat16 patterns) turns on learned pruning at mlp_tau;
+    feat (from feature_buffer) receives the features of every compatible hit."""
     n = seed_hits.shape[1]
     _need(seed_hits, "seed_hits", torch.int32, (3, n), device)
     _need(seed_event, "seed_event", torch.int32, (n,), device)
+    if mlp_bf16 is not None:
+        _need(mlp_bf16, "mlp_bf16", torch.int16, (N.MLP_PARAMS,), device)
+    if feat is not None:
+        _need(feat["feat"], "feat", torch.float32, None, device)
+        _need(feat["ref"], "feat ref", torch.int32, None, device)
+        _need(feat["count"], "feat count", torch.int32, (1,), device)
     if max_out is None:
         max_out = (n_layers or N.MAX_LAYERS) + 3
     dev = seed_hits.device
@@ -184,12 +209,59 @@ def mkf_find(ctx, bins: HitBins, seed_hits, seed_event, n_best=10, chi2_cut=30.0
                    hits=torch.empty(max_out, n, dtype=torch.int32, device=dev),
                    status=torch.empty(n, dtype=torch.int32, device=dev),
                    counters=torch.empty(3, n, dtype=torch.int32, device=dev) if counters else None)
-    prm = find_params(n_best, chi2_cut, max_consec_miss, block_threads)
-    N.check("mkf_find", N.lib().mkf_find(ctx, bins.handle, _ptr(seed_hits), _ptr(seed_event), n, C.byref(prm),
+    prm = find_params(n_best, chi2_cut, max_consec_miss, block_threads, mlp_bf16, mlp_tau, feat)
+    N.check("mkf_find", N.lib().mkf_find(_h(ctx), bins.handle, _ptr(seed_hits), _ptr(seed_event), n, C.byref(prm),
                                          _ptr(out["par"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out["n_hits"]),
                                          _ptr(out["hits"]), int(out["hits"].shape[0]), _ptr(out["status"]),
                                          _ptr(out.get("counters"))))
     return out
+
+
+def _h(ctx):
+    return ctx.handle if hasattr(ctx, "handle") else ctx
+
+
+def mkf_mlp_to_bf16(ctx, w, out=None):
+    """FP32 weights -> bfloat16 bit patterns (int16 tensor)."""
+    _need(w, "w", torch.float32)
+    out = torch.empty(w.shape, dtype=torch.int16, device=w.device) if out is None else out
+    N.check("mkf_mlp_to_bf16", N.lib().mkf_mlp_to_bf16(_h(ctx), _ptr(w), _ptr(out), w.numel()))
+    return out
+
+
+def mkf_mlp_forward(ctx, w_bf16, feat, out=None):
+    n = feat.shape[0]
+    _need(w_bf16, "w_bf16", torch.int16, (N.MLP_PARAMS,))
+    _need(feat, "feat", torch.float32, (n, N.MLP_IN))
+    out = torch.empty(n, device=feat.device) if out is None else out
+    N.check("mkf_mlp_forward", N.lib().mkf_mlp_forward(_h(ctx), _ptr(w_bf16), _ptr(feat), n, _ptr(out)))
+    return out
+
+
+def mkf_mlp_grad(ctx, w_bf16, feat, label):
+    n = feat.shape[0]
+    _need(w_bf16, "w_bf16", torch.int16, (N.MLP_PARAMS,))
+    _need(feat, "feat", torch.float32, (n, N.MLP_IN))
+    _need(label, "label", torch.float32, (n,))
+    grad = torch.empty(N.MLP_PARAMS, device=feat.device)
+    loss = torch.empty(1, device=feat.device)
+    N.check("mkf_mlp_grad", N.lib().mkf_mlp_grad(_h(ctx), _ptr(w_bf16), _ptr(feat), _ptr(label), n, _ptr(grad),
+                                                 _ptr(loss)))
+    return grad, loss
+
+
+def mkf_mlp_train_step(ctx, feat, label, w, m, v, t, w_bf16, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, loss=None):
+    """One Adam step on the batch (w, m, v, w_bf16 updated in place)."""
+    n = feat.shape[0]
+    _need(feat, "feat", torch.float32, (n, N.MLP_IN))
+    _need(label, "label", torch.float32, (n,))
+    for name, t_ in (("w", w), ("m", m), ("v", v)):
+        _need(t_, name, torch.float32, (N.MLP_PARAMS,))
+    _need(w_bf16, "w_bf16", torch.int16, (N.MLP_PARAMS,))
+    hp = N.MkfAdam(lr, beta1, beta2, eps)
+    N.check("mkf_mlp_train_step", N.lib().mkf_mlp_train_step(
+        _h(ctx), _ptr(feat), _ptr(label), n, _ptr(w), _ptr(m), _ptr(v), int(t), C.byref(hp), _ptr(w_bf16),
+        _ptr(loss)))
 
 
 class Context:
@@ -228,7 +300,7 @@ class Context:
         return mkf_fit(self.handle, xyz, hit_layer, hit_idx, seed_par, seed_cov, out, self.device)
 
     def find(self, bins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
-             out=None, counters=True, block_threads=0):
+             out=None, counters=True, block_threads=0, mlp_bf16=None, mlp_tau=0.0, feat=None):
         nl = len(self.layers) if self.layers else None
         return mkf_find(self.handle, bins, seed_hits, seed_event, n_best, chi2_cut, max_consec_miss, max_out, nl, out,
-                        counters, block_threads, self.device)
+                        counters, block_threads, self.device, mlp_bf16, mlp_tau, feat)

@@ -56,6 +56,12 @@ struct FindArgs {
     int32_t *counters;
     mkf_fault *fault;
     float *seedbuf;  // [kSeedFields][n_seeds] fitted seeds (written by seed_kernel)
+    const uint16_t *mlp;  // bfloat16 weights or nullptr
+    float mlp_tau;
+    float *feat_out;
+    int32_t *feat_ref;
+    int32_t *feat_count;
+    int32_t feat_cap;
 };
 
 // Fitted-seed record, structure of arrays over seeds.
@@ -86,12 +92,14 @@ __device__ __forceinline__ unsigned long long child_key(float score, int prank, 
 struct Book {
     int nh, consec, ncyl, ndsk;
     bool done, missstop;
+    int nmiss;  // misses so far (saturates at 15)
 };
 
 __device__ __forceinline__ uint32_t pack_book(const Book &b) {
     return static_cast<uint32_t>(b.nh & 0xFF) | (static_cast<uint32_t>(b.consec & 0xF) << 8) |
            (static_cast<uint32_t>((b.ncyl + 1) & 0x7F) << 12) | (static_cast<uint32_t>((b.ndsk + 1) & 0x7F) << 19) |
-           (b.done ? (1u << 26) : 0u) | (b.missstop ? (1u << 27) : 0u);
+           (b.done ? (1u << 26) : 0u) | (b.missstop ? (1u << 27) : 0u) |
+           (static_cast<uint32_t>(min(b.nmiss, 15)) << 28);
 }
 
 __device__ __forceinline__ Book unpack_book(uint32_t w) {
@@ -102,6 +110,7 @@ __device__ __forceinline__ Book unpack_book(uint32_t w) {
     b.ndsk = static_cast<int>((w >> 19) & 0x7F) - 1;
     b.done = (w >> 26) & 1u;
     b.missstop = (w >> 27) & 1u;
+    b.nmiss = static_cast<int>(w >> 28);
     return b;
 }
 
@@ -204,6 +213,37 @@ __device__ __forceinline__ uint32_t seg_or(uint32_t v, int rank, int N) {
     return v;
 }
 
+// Features of a (candidate, compatible hit) pair (see mkf_find_params).
+__device__ __forceinline__ void pair_features(float u, float v, const Innov &I, float x2, float cut, float chi2_tot,
+                                              const Book &bk, int layer, int n_layers, int kind, const float p[6],
+                                              float cot, float f[12]) {
+    const float su = sqrtf(I.Suu), sv = sqrtf(I.Svv);
+    f[0] = u / su;
+    f[1] = v / sv;
+    f[2] = x2 / cut;
+    f[3] = chi2_tot / fmaxf(1.f, static_cast<float>(2 * bk.nh - 5));
+    f[4] = static_cast<float>(bk.nh) * 0.1f;
+    f[5] = static_cast<float>(bk.nmiss) * 0.2f;
+    f[6] = static_cast<float>(layer) / static_cast<float>(n_layers);
+    f[7] = kind == 1 ? 1.f : 0.f;
+    f[8] = p[3];
+    f[9] = asinhf(cot) * (1.f / 3.f);
+    f[10] = log10f(su);
+    f[11] = log10f(sv);
+}
+
+// MLP logit with FP32 weights in shared memory (layout of mkf.h).
+__device__ __forceinline__ float mlp_logit(const float *ws, const float f[12]) {
+    float z = ws[MKF_MLP_PARAMS - 1];
+    for (int j = 0; j < MKF_MLP_HIDDEN; ++j) {
+        float a = ws[MKF_MLP_IN * MKF_MLP_HIDDEN + j];
+#pragma unroll
+        for (int k = 0; k < MKF_MLP_IN; ++k) a = fmaf(ws[j * MKF_MLP_IN + k], f[k], a);
+        z = fmaf(ws[MKF_MLP_IN * MKF_MLP_HIDDEN + MKF_MLP_HIDDEN + j], fmaxf(a, 0.f), z);
+    }
+    return z;
+}
+
 // Seed fit, one thread per seed: state from the three hits (circle + line),
 // then the Kalman fit through them (the first hit without propagation), the
 // tracking region from the seed's eta, the direction along z and the first
@@ -272,7 +312,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
     uint32_t status = ok ? 0u : MKF_ST_BADSEED;
     unsigned long long mask = 0;
     int dir = 1;
-    Book bk{3, 0, -1, -1, false, false};
+    Book bk{3, 0, -1, -1, false, false, 0};
     if (ok) {
         int region = 0;
         while (region + 1 < G.n_regions && eta >= G.edges[region]) ++region;
@@ -328,10 +368,14 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
 __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ FindArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Geom SG;
+    __shared__ float WS[MKF_MLP_PARAMS];
     {
         const int *src = reinterpret_cast<const int *>(&A.G);
         int *dst = reinterpret_cast<int *>(&SG);
         for (int i = threadIdx.x; i < static_cast<int>(sizeof(Geom) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        if (A.mlp)
+            for (int i = threadIdx.x; i < MKF_MLP_PARAMS; i += blockDim.x)
+                WS[i] = __uint_as_float(static_cast<uint32_t>(A.mlp[i]) << 16);
     }
     __syncthreads();
     const Geom &G = SG;
@@ -366,7 +410,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     for (int k = 0; k < 6; ++k) I.HCu[k] = I.HCv[k] = 0.f;
     I.Suu = I.Suv = I.Svv = I.Iuu = I.Iuv = I.Ivv = 0.f;
     float chi2 = 0.f;
-    Book bk{0, 0, -1, -1, true, false};
+    Book bk{0, 0, -1, -1, true, false, 0};
     bool live = false;
     uint32_t status = 0;
     int c_cl = 0, c_ht = 0, c_up = 0;
@@ -452,6 +496,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                         const float zhi_f = fminf(fmaxf(floorf((zc + wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
                         const int zb_lo = static_cast<int>(zlo_f), zb_hi = static_cast<int>(zhi_f);
                         const int ebase = ev * G.bins_per_event + Ld.bin_base;
+                        int n_compat = 0;
                         for (int i = 0; i < nphib; ++i) {
                             int pb = (pb_lo + i) % Ld.nphi;
                             if (pb < 0) pb += Ld.nphi;
@@ -467,6 +512,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                                 const float x2 = chi2_of(I, u, v);
                                 if (!(x2 < cut)) continue;
                                 const int orig = __float_as_int(hr.w);
+                                ++n_compat;
                                 // insert into the lane's list, sorted by (chi2, orig), at most N
                                 if (nlist == N) {
                                     const float wc = lchi[(N - 1) * 32 + lane];
@@ -493,6 +539,37 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                                 lv[j * 32 + lane] = v;
                                 if (nlist < N) ++nlist;
                             }
+                        }
+                        // learned pruning / feature dump over the candidate's list (its
+                        // N best compatible hits); the MLP scores a list only when the
+                        // candidate has two or more compatible hits
+                        if ((A.feat_out || (A.mlp && n_compat >= 2)) && nlist > 0) {
+                            int kept = 0;
+                            for (int j = 0; j < nlist; ++j) {
+                                const float x2 = lchi[j * 32 + lane], u = lu[j * 32 + lane], v = lv[j * 32 + lane];
+                                const int orig = lorig[j * 32 + lane];
+                                float fe[12];
+                                pair_features(u, v, I, x2, cut, chi2, bk, l, G.n_layers, Ld.kind, p, cot, fe);
+                                if (A.feat_out) {
+                                    const int at = atomicAdd(A.feat_count, 1);
+                                    if (at < A.feat_cap) {
+#pragma unroll
+                                        for (int q = 0; q < 12; ++q) A.feat_out[(int64_t)at * 12 + q] = fe[q];
+                                        A.feat_ref[(int64_t)at * 3] = seed;
+                                        A.feat_ref[(int64_t)at * 3 + 1] = orig;
+                                        A.feat_ref[(int64_t)at * 3 + 2] = n_compat;
+                                    }
+                                }
+                                if (A.mlp && n_compat >= 2 && mlp_logit(WS, fe) < A.mlp_tau) continue;
+                                if (kept != j) {
+                                    lchi[kept * 32 + lane] = x2;
+                                    lorig[kept * 32 + lane] = orig;
+                                    lu[kept * 32 + lane] = u;
+                                    lv[kept * 32 + lane] = v;
+                                }
+                                ++kept;
+                            }
+                            nlist = kept;
                         }
                     }
                 } else {
@@ -591,6 +668,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                 ++c_up;
             } else if (code == kCodeMiss) {
                 bk.consec += 1;
+                bk.nmiss = min(bk.nmiss + 1, 15);
                 if (bk.consec >= A.max_consec) {
                     bk.done = true;
                     bk.missstop = true;
@@ -717,6 +795,13 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     A.out_status = status;
     A.counters = counters;
     A.fault = ctx->fault;
+    A.mlp = params->mlp_bf16;
+    A.mlp_tau = params->mlp_tau;
+    A.feat_out = params->feat_out;
+    A.feat_ref = params->feat_ref;
+    A.feat_count = params->feat_count;
+    A.feat_cap = params->feat_cap;
+    if (A.feat_out && (!A.feat_ref || !A.feat_count || A.feat_cap < 0)) return MKF_ERR_ARG;
     const size_t smem = find_smem_bytes(ctx->geom.n_layers, N, threads);
     if (smem > 200 * 1024) return MKF_ERR_CAPACITY;
     MKF_CUDA_TRY(cudaFuncSetAttribute(find_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
