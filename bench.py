@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--events", type=int, default=EVENTS, help="events per GPU (profiling runs only)")
     ap.add_argument("--n-best", type=int, default=N_BEST, help="candidates kept per seed (profiling runs only)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-pruning comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-events leg")
+    ap.add_argument("--batched-events", type=int, default=512)
     return ap.parse_args()
 
 
@@ -268,6 +270,63 @@ def learned_leg(dev, reps: int = 30):
 
 
 # ---------------------------------------------------------------------------
+# batched uneven events in one persistent launch, replayed from a CUDA graph
+# ---------------------------------------------------------------------------
+
+def batched_leg(dev, n_events: int = 512, reps: int = 10):
+    """Dense geometry, per-event track counts floor(exp(U[ln 100, ln 20000])) and
+    noise counts floor(exp(U[ln 1e3, ln 3e5])); the binning + finding step is
+    captured in a CUDA graph after choosing the finder's block size; per-event
+    latency = time from the finder's first block start until the event's last
+    seed is written (GPU global timer)."""
+    import torch
+
+    from paper_1811_04141_gb300 import Context
+    from paper_1811_04141_gb300.runtime import CapturedStep, tune_find_block
+    from synth import make_batch
+    rng = np.random.default_rng(4_181_104)
+    tracks = np.floor(np.exp(rng.uniform(np.log(100), np.log(20000), n_events))).astype(int)
+    noise = np.floor(np.exp(rng.uniform(np.log(1e3), np.log(3e5), n_events))).astype(int)
+    t0 = time.perf_counter()
+    b = make_batch("dense45", list(range(5000, 5000 + n_events)), n_tracks=list(tracks), n_noise=list(noise))
+    gen_s = time.perf_counter() - t0
+    ctx = Context(dev.index, torch.cuda.current_stream(dev))
+    ctx.geometry_load(b.layers, b.bz)
+    to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    xyz, layer, evo = to(b.xyz, torch.float32), to(b.layer, torch.int32), to(b.event_offsets, torch.int32)
+    sh, se = to(b.seed_hits, torch.int32), to(b.seed_event, torch.int32)
+    max_out = len(b.layers) + 3
+    bins = ctx.hits_bin(xyz, layer, evo)
+    bt, tune = tune_find_block(ctx, bins, sh, se, n_best=N_BEST, max_out=max_out)
+    et = torch.zeros(n_events + 1, dtype=torch.int64, device=dev)
+    step = CapturedStep(ctx, xyz, layer, evo, sh, se, n_best=N_BEST, max_out=max_out, block_threads=bt,
+                        event_times=et)
+    for _ in range(3):
+        step.replay()
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        out = step.replay()
+    e.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / reps
+    t = et.cpu().numpy().astype(np.int64)
+    lat_ms = (t[:n_events] - t[n_events]) / 1e6
+    cl = int(out["counters"][0].sum().item())
+    ctx.close()
+    return {"workload": f"{n_events} events, dense geometry (17 cylinders + 2x14 disks), tracks/event "
+                        "floor(exp(U[ln 100, ln 20000])), noise/event floor(exp(U[ln 1e3, ln 3e5])), N=10; "
+                        "binning + finding replayed from one CUDA graph",
+            "events": n_events, "hits": b.n_hits, "seeds": b.n_seeds, "generation_s": round(gen_s, 2),
+            "ms_per_replay": ms, "events_per_s": n_events / (ms * 1e-3),
+            "cand_layer_updates_per_s": cl / (ms * 1e-3),
+            "event_latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                                 "max": float(lat_ms.max())},
+            "autotune": {"block_threads": bt, "ms_by_block_threads": tune.get("ms")}}
+
+
+# ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
 
@@ -395,6 +454,9 @@ def run_ours(args, world, rank, local, pg):
     learned = None
     if rank == 0 and world == 1 and not args.no_learned:
         learned = learned_leg(dev)
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = batched_leg(dev, args.batched_events)
 
     launches_per_step = 8  # bin_keys, scan_tiles, scan_blocksums, scan_write, scatter, bin_sort, seed, find
     line = {
@@ -410,6 +472,7 @@ def run_ours(args, world, rank, local, pg):
                    "l2": "flushed between steps (256 MiB write, outside the per-step CUDA events)",
                    "wall_s_timed_region": round(wall, 3), "parallelism": f"events sharded, {world} GPU(s)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "learned": learned,
+        "batched": batched,
         "gpu_launches": launches_per_step * K,
     }
     if rank == 0:

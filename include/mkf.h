@@ -243,6 +243,10 @@ typedef struct {
     int32_t *feat_ref;
     int32_t *feat_count;
     int32_t feat_cap;
+    /* Per-event completion times (device [n_events + 1] or NULL): entry e is the
+     * GPU global timer (ns) when the last seed of event e was written, entry
+     * n_events the earliest start of a finding block; set by the call. */
+    uint64_t *event_times;
 } mkf_find_params;
 
 /* Find tracks from seeds.

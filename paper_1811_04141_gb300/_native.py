@@ -51,7 +51,7 @@ class MkfFindParams(C.Structure):
     _fields_ = [("n_best", C.c_int32), ("chi2_cut", C.c_float), ("max_consec_miss", C.c_int32),
                 ("block_threads", C.c_int32), ("mlp_bf16", C.c_void_p), ("mlp_tau", C.c_float),
                 ("feat_out", C.c_void_p), ("feat_ref", C.c_void_p), ("feat_count", C.c_void_p),
-                ("feat_cap", C.c_int32)]
+                ("feat_cap", C.c_int32), ("event_times", C.c_void_p)]
 
 
 MLP_IN = 12

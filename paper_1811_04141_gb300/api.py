@@ -166,8 +166,10 @@ def mkf_fit(ctx, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, out=None
 
 
 def find_params(n_best=10, chi2_cut=30.0, max_consec_miss=3, block_threads=0, mlp_bf16=None, mlp_tau=0.0,
-                feat=None) -> N.MkfFindParams:
+                feat=None, event_times=None) -> N.MkfFindParams:
     prm = N.MkfFindParams(int(n_best), float(chi2_cut), int(max_consec_miss), int(block_threads))
+    if event_times is not None:
+        prm.event_times = event_times.data_ptr()
     if mlp_bf16 is not None:
         prm.mlp_bf16 = mlp_bf16.data_ptr()
         prm.mlp_tau = float(mlp_tau)
@@ -187,7 +189,7 @@ def feature_buffer(cap: int, device="cuda") -> dict:
 
 def mkf_find(ctx, bins: HitBins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
              n_layers=None, out=None, counters=True, block_threads=0, device: int | None = None, mlp_bf16=None,
-             mlp_tau=0.0, feat=None):
+             mlp_tau=0.0, feat=None, event_times=None):
     """Find tracks; returns dict(par, cov, chi2, n_hits, hits [max_out, n], status, counters [3, n]).
     mlp_bf16 (int16 tensor of MLP_PARAMS bfloat16 patterns) turns on learned pruning at mlp_tau;
     feat (from feature_buffer) receives the features of every compatible hit."""
@@ -209,7 +211,9 @@ def mkf_find(ctx, bins: HitBins, seed_hits, seed_event, n_best=10, chi2_cut=30.0
                    hits=torch.empty(max_out, n, dtype=torch.int32, device=dev),
                    status=torch.empty(n, dtype=torch.int32, device=dev),
                    counters=torch.empty(3, n, dtype=torch.int32, device=dev) if counters else None)
-    prm = find_params(n_best, chi2_cut, max_consec_miss, block_threads, mlp_bf16, mlp_tau, feat)
+    if event_times is not None:
+        _need(event_times, "event_times", torch.int64, None, device)
+    prm = find_params(n_best, chi2_cut, max_consec_miss, block_threads, mlp_bf16, mlp_tau, feat, event_times)
     N.check("mkf_find", N.lib().mkf_find(_h(ctx), bins.handle, _ptr(seed_hits), _ptr(seed_event), n, C.byref(prm),
                                          _ptr(out["par"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out["n_hits"]),
                                          _ptr(out["hits"]), int(out["hits"].shape[0]), _ptr(out["status"]),
@@ -300,7 +304,7 @@ class Context:
         return mkf_fit(self.handle, xyz, hit_layer, hit_idx, seed_par, seed_cov, out, self.device)
 
     def find(self, bins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
-             out=None, counters=True, block_threads=0, mlp_bf16=None, mlp_tau=0.0, feat=None):
+             out=None, counters=True, block_threads=0, mlp_bf16=None, mlp_tau=0.0, feat=None, event_times=None):
         nl = len(self.layers) if self.layers else None
         return mkf_find(self.handle, bins, seed_hits, seed_event, n_best, chi2_cut, max_consec_miss, max_out, nl, out,
-                        counters, block_threads, self.device, mlp_bf16, mlp_tau, feat)
+                        counters, block_threads, self.device, mlp_bf16, mlp_tau, feat, event_times)

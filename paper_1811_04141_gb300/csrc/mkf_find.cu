@@ -62,6 +62,8 @@ struct FindArgs {
     int32_t *feat_ref;
     int32_t *feat_count;
     int32_t feat_cap;
+    int32_t *work_counter;                // persistent warps' shared seed-group counter
+    unsigned long long *event_times;      // [n_events + 1] or nullptr
 };
 
 // Fitted-seed record, structure of arrays over seeds.
@@ -72,6 +74,12 @@ enum {
 
 __device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) {
     if (atomicCAS(&f->code, 0, code) == 0) f->where = where;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // Order-preserving map of a float to uint32 (larger float -> larger integer).
@@ -365,6 +373,9 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
     for (int k = 0; k < 3; ++k) B[(SF_HITS + k) * (int64_t)n + t] = __int_as_float(hidx[k]);
 }
 
+// kLearned: the variant with learned pruning and the feature dump compiled in;
+// the plain finder is built without them.
+template <bool kLearned>
 __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ FindArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Geom SG;
@@ -373,7 +384,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
         const int *src = reinterpret_cast<const int *>(&A.G);
         int *dst = reinterpret_cast<int *>(&SG);
         for (int i = threadIdx.x; i < static_cast<int>(sizeof(Geom) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
-        if (A.mlp)
+        if (kLearned && A.mlp)
             for (int i = threadIdx.x; i < MKF_MLP_PARAMS; i += blockDim.x)
                 WS[i] = __uint_as_float(static_cast<uint32_t>(A.mlp[i]) << 16);
     }
@@ -385,9 +396,6 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     const int slot = lane / N, rank = lane - slot * N;
     const int base = slot * N;
     const bool lane_used = slot < spw;
-    const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
-    const int seed = gwarp * spw + slot;
-    const bool has_seed = lane_used && seed < A.n_seeds;
     const int nwarps = blockDim.x >> 5;
 
     // shared memory: per-step history, then the per-lane child lists
@@ -399,344 +407,357 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     float *lv = lchi + 3 * N * 32;
 
     const float cut = A.cut;
-    float p[6], C[21];
-    Lo lo{0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int i = 0; i < 6; ++i) p[i] = 0.f;
-#pragma unroll
-    for (int k = 0; k < 21; ++k) C[k] = 0.f;
-    Innov I;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) I.HCu[k] = I.HCv[k] = 0.f;
-    I.Suu = I.Suv = I.Svv = I.Iuu = I.Iuv = I.Ivv = 0.f;
-    float chi2 = 0.f;
-    Book bk{0, 0, -1, -1, true, false, 0};
-    bool live = false;
-    uint32_t status = 0;
-    int c_cl = 0, c_ht = 0, c_up = 0;
-    int dir = 1, ev = 0;
-    unsigned long long mask = 0;
-    int sh0 = -1, sh1 = -1, sh2 = -1;
+    if (A.event_times && threadIdx.x == 0) atomicMin(&A.event_times[A.n_events], globaltimer_ns());
 
-    // ---- the fitted seed (rank-0 lane), from seed_kernel
-    if (has_seed && rank == 0) {
-        const float *Bs = A.seedbuf;
-        const int64_t n = A.n_seeds;
-        status = __float_as_uint(Bs[SF_STATUS * n + seed]);
-        ev = A.seed_event[seed];
-        if (!(status & MKF_ST_BADSEED)) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) p[i] = Bs[(SF_P + i) * n + seed];
-            lo.x = Bs[(SF_LO + 0) * n + seed];
-            lo.y = Bs[(SF_LO + 1) * n + seed];
-            lo.z = Bs[(SF_LO + 2) * n + seed];
-            lo.phi = Bs[(SF_LO + 3) * n + seed];
-#pragma unroll
-            for (int k = 0; k < 21; ++k) C[k] = Bs[(SF_C + k) * n + seed];
-            chi2 = Bs[SF_CHI2 * n + seed];
-            bk = unpack_book(__float_as_uint(Bs[SF_BOOK * n + seed]));
-            mask = static_cast<unsigned long long>(__float_as_uint(Bs[SF_MASK_LO * n + seed])) |
-                   (static_cast<unsigned long long>(__float_as_uint(Bs[SF_MASK_HI * n + seed])) << 32);
-            dir = __float_as_int(Bs[SF_DIR * n + seed]);
-            sh0 = __float_as_int(Bs[(SF_HITS + 0) * n + seed]);
-            sh1 = __float_as_int(Bs[(SF_HITS + 1) * n + seed]);
-            sh2 = __float_as_int(Bs[(SF_HITS + 2) * n + seed]);
-            live = true;
-        }
-    }
-    {
-        const int src = lane_used ? base : lane;
-        ev = __shfl_sync(kFull, ev, src);
-        mask = __shfl_sync(kFull, mask, src);
-        dir = __shfl_sync(kFull, dir, src);
-    }
+    // persistent warps: each takes the next group of seeds from a shared counter
+    const int n_groups = (A.n_seeds + spw - 1) / spw;
+    for (;;) {
+        int grp = 0;
+        if (lane == 0) grp = atomicAdd(A.work_counter, 1);
+        grp = __shfl_sync(kFull, grp, 0);
+        if (grp >= n_groups) break;
+        const int seed = grp * spw + slot;
+        const bool has_seed = lane_used && seed < A.n_seeds;
+        float p[6], C[21];
+        Lo lo{0.f, 0.f, 0.f, 0.f};
+    #pragma unroll
+        for (int i = 0; i < 6; ++i) p[i] = 0.f;
+    #pragma unroll
+        for (int k = 0; k < 21; ++k) C[k] = 0.f;
+        Innov I;
+    #pragma unroll
+        for (int k = 0; k < 6; ++k) I.HCu[k] = I.HCv[k] = 0.f;
+        I.Suu = I.Suv = I.Svv = I.Iuu = I.Iuv = I.Ivv = 0.f;
+        float chi2 = 0.f;
+        Book bk{0, 0, -1, -1, true, false, 0};
+        bool live = false;
+        uint32_t status = 0;
+        int c_cl = 0, c_ht = 0, c_up = 0;
+        int dir = 1, ev = 0;
+        unsigned long long mask = 0;
+        int sh0 = -1, sh1 = -1, sh2 = -1;
 
-    int step = 0;
-    while (true) {
-        const bool active = live && !bk.done;
-        if (!__any_sync(kFull, active)) break;  // every candidate of the warp has finished
-        // ---- 1. expansion: next layer, propagation, window search
-        int nlist = 0;
-        bool searched = false;
-        if (active) {
-            float sphi, cphi;
-            sincos_pair(p[4], lo.phi, sphi, cphi);
-            const float cot = cot_of(p[5]);
-            float s = 0.f;
-            const int l =
-                finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
-            if (l == -2) status |= MKF_ST_NONFINITE;
-            if (l < 0) {
-                bk.done = true;
-            } else {
-                const LayerDesc &Ld = G.L[l];
-                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-                searched = true;
-                ++c_cl;
-                const Frame f = frame_of(p);
-                if (innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
-                    {
-                        const float wu = sqrtf(cut * I.Suu), wv = sqrtf(cut * I.Svv);
-                        const float wu_m = wu * 1.0001f, wv_m = wv * 1.0001f;
-                        const float lever = Ld.kind == 0 ? Ld.rz : f.rt;
-                        const float dphiw = wu_m / lever + 2e-6f;
-                        const float zc = Ld.kind == 0 ? p[2] : f.rt;
-                        const float wz = wv_m + 1e-5f;
-                        const float phic = atan2f(p[1], p[0]);
-                        int pb_lo, nphib;
-                        if (dphiw >= kPi) {
-                            pb_lo = 0;
-                            nphib = Ld.nphi;
-                        } else {
-                            pb_lo = static_cast<int>(floorf((phic - dphiw + kPi) * Ld.phi_scale));
-                            const int pb_hi = static_cast<int>(floorf((phic + dphiw + kPi) * Ld.phi_scale));
-                            nphib = min(pb_hi - pb_lo + 1, Ld.nphi);
-                        }
-                        const float zlo_f = fminf(fmaxf(floorf((zc - wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
-                        const float zhi_f = fminf(fmaxf(floorf((zc + wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
-                        const int zb_lo = static_cast<int>(zlo_f), zb_hi = static_cast<int>(zhi_f);
-                        const int ebase = ev * G.bins_per_event + Ld.bin_base;
-                        int n_compat = 0;
-                        for (int i = 0; i < nphib; ++i) {
-                            int pb = (pb_lo + i) % Ld.nphi;
-                            if (pb < 0) pb += Ld.nphi;
-                            const int bin = ebase + pb * Ld.nzr;
-                            const int k0 = A.offsets[bin + zb_lo], k1 = A.offsets[bin + zb_hi + 1];
-                            for (int k = k0; k < k1; ++k) {
-                                const float4 hr = A.rec[k];
-                                if (fabsf(hr.z - zc) > wv_m) continue;
-                                float u, v;
-                                residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
-                                if (fabsf(u) > wu_m) continue;
-                                if (fabsf(u) <= wu && fabsf(v) <= wv) ++c_ht;
-                                const float x2 = chi2_of(I, u, v);
-                                if (!(x2 < cut)) continue;
-                                const int orig = __float_as_int(hr.w);
-                                ++n_compat;
-                                // insert into the lane's list, sorted by (chi2, orig), at most N
-                                if (nlist == N) {
-                                    const float wc = lchi[(N - 1) * 32 + lane];
-                                    const int wo = lorig[(N - 1) * 32 + lane];
-                                    if (!(x2 < wc || (x2 == wc && orig < wo))) continue;
-                                }
-                                int j = nlist < N ? nlist : N - 1;
-                                while (j > 0) {
-                                    const float pc = lchi[(j - 1) * 32 + lane];
-                                    const int po = lorig[(j - 1) * 32 + lane];
-                                    if (pc > x2 || (pc == x2 && po > orig)) {
-                                        lchi[j * 32 + lane] = pc;
-                                        lorig[j * 32 + lane] = po;
-                                        lu[j * 32 + lane] = lu[(j - 1) * 32 + lane];
-                                        lv[j * 32 + lane] = lv[(j - 1) * 32 + lane];
-                                        --j;
-                                    } else {
-                                        break;
-                                    }
-                                }
-                                lchi[j * 32 + lane] = x2;
-                                lorig[j * 32 + lane] = orig;
-                                lu[j * 32 + lane] = u;
-                                lv[j * 32 + lane] = v;
-                                if (nlist < N) ++nlist;
-                            }
-                        }
-                        // learned pruning / feature dump over the candidate's list (its
-                        // N best compatible hits); the MLP scores a list only when the
-                        // candidate has two or more compatible hits
-                        if ((A.feat_out || (A.mlp && n_compat >= 2)) && nlist > 0) {
-                            int kept = 0;
-                            for (int j = 0; j < nlist; ++j) {
-                                const float x2 = lchi[j * 32 + lane], u = lu[j * 32 + lane], v = lv[j * 32 + lane];
-                                const int orig = lorig[j * 32 + lane];
-                                float fe[12];
-                                pair_features(u, v, I, x2, cut, chi2, bk, l, G.n_layers, Ld.kind, p, cot, fe);
-                                if (A.feat_out) {
-                                    const int at = atomicAdd(A.feat_count, 1);
-                                    if (at < A.feat_cap) {
-#pragma unroll
-                                        for (int q = 0; q < 12; ++q) A.feat_out[(int64_t)at * 12 + q] = fe[q];
-                                        A.feat_ref[(int64_t)at * 3] = seed;
-                                        A.feat_ref[(int64_t)at * 3 + 1] = orig;
-                                        A.feat_ref[(int64_t)at * 3 + 2] = n_compat;
-                                    }
-                                }
-                                if (A.mlp && n_compat >= 2 && mlp_logit(WS, fe) < A.mlp_tau) continue;
-                                if (kept != j) {
-                                    lchi[kept * 32 + lane] = x2;
-                                    lorig[kept * 32 + lane] = orig;
-                                    lu[kept * 32 + lane] = u;
-                                    lv[kept * 32 + lane] = v;
-                                }
-                                ++kept;
-                            }
-                            nlist = kept;
-                        }
-                    }
-                } else {
-                    status |= MKF_ST_BADS;
-                }
+        // ---- the fitted seed (rank-0 lane), from seed_kernel
+        if (has_seed && rank == 0) {
+            const float *Bs = A.seedbuf;
+            const int64_t n = A.n_seeds;
+            status = __float_as_uint(Bs[SF_STATUS * n + seed]);
+            ev = A.seed_event[seed];
+            if (!(status & MKF_ST_BADSEED)) {
+    #pragma unroll
+                for (int i = 0; i < 6; ++i) p[i] = Bs[(SF_P + i) * n + seed];
+                lo.x = Bs[(SF_LO + 0) * n + seed];
+                lo.y = Bs[(SF_LO + 1) * n + seed];
+                lo.z = Bs[(SF_LO + 2) * n + seed];
+                lo.phi = Bs[(SF_LO + 3) * n + seed];
+    #pragma unroll
+                for (int k = 0; k < 21; ++k) C[k] = Bs[(SF_C + k) * n + seed];
+                chi2 = Bs[SF_CHI2 * n + seed];
+                bk = unpack_book(__float_as_uint(Bs[SF_BOOK * n + seed]));
+                mask = static_cast<unsigned long long>(__float_as_uint(Bs[SF_MASK_LO * n + seed])) |
+                       (static_cast<unsigned long long>(__float_as_uint(Bs[SF_MASK_HI * n + seed])) << 32);
+                dir = __float_as_int(Bs[SF_DIR * n + seed]);
+                sh0 = __float_as_int(Bs[(SF_HITS + 0) * n + seed]);
+                sh1 = __float_as_int(Bs[(SF_HITS + 1) * n + seed]);
+                sh2 = __float_as_int(Bs[(SF_HITS + 2) * n + seed]);
+                live = true;
             }
         }
-        __syncwarp();
-
-        // ---- 2. selection of the N best children of each seed: N rounds of a
-        // segmented max over the lanes' best remaining child.  The score is
-        // compared as an order-preserving 32-bit integer; exact score ties (rare)
-        // are resolved by a second reduction on (parent rank, hit index).
-        const float score = cut * static_cast<float>(bk.nh) - chi2;
-        const int n_children = live ? (searched ? nlist + 1 : 1) : 0;
-        int head = 0;
-        unsigned long long mine = 0;
-        if (N == 1) {
-            if (n_children > 0) {
-                mine = head < nlist ? child_key(score + cut - lchi[lane], 0, static_cast<uint32_t>(lorig[lane]))
-                                    : child_key(score, 0, searched ? kCodeMiss : kCodePass);
-            }
-        } else {
-            for (int j = 0; j < N; ++j) {
-                const bool has = head < n_children;
-                if (!__any_sync(kFull, has)) break;
-                uint32_t k32 = 0, lo32 = 0;
-                if (has) {
-                    const bool is_hit = head < nlist;
-                    const float sc = is_hit ? score + cut - lchi[head * 32 + lane] : score;
-                    const uint32_t code = is_hit ? static_cast<uint32_t>(lorig[head * 32 + lane])
-                                                 : (searched ? kCodeMiss : kCodePass);
-                    k32 = ord_float(sc);
-                    lo32 = (static_cast<uint32_t>(15 - rank) << 28) | (kHitMask - code);
-                }
-                const uint32_t m32 = seg_max32(k32, rank, N, base);
-                const bool cand = has && k32 == m32;
-                // the lanes of my segment holding the maximum score
-                const unsigned seg_bits = (N == 32 ? kFull : ((1u << N) - 1u)) << (base & 31);
-                const unsigned tied = __ballot_sync(kFull, cand) & seg_bits;
-                uint32_t mlo;
-                if (__any_sync(kFull, lane_used && __popc(tied) > 1)) {
-                    mlo = seg_max32(cand ? lo32 : 0u, rank, N, base);
-                } else {
-                    mlo = __shfl_sync(kFull, lo32, tied ? (__ffs(tied) - 1) : lane);
-                }
-                if (m32 != 0u && lane_used) {
-                    const int wr = 15 - static_cast<int>(mlo >> 28);
-                    if (wr == rank) ++head;
-                    if (j == rank) mine = (static_cast<unsigned long long>(m32) << 32) | mlo;
-                }
-            }
+        {
+            const int src = lane_used ? base : lane;
+            ev = __shfl_sync(kFull, ev, src);
+            mask = __shfl_sync(kFull, mask, src);
+            dir = __shfl_sync(kFull, dir, src);
         }
 
-        // ---- 3. each lane becomes one child: its parent's propagated state,
-        // and the parent's S^-1 and H C, by shuffles
-        const int prank = mine ? 15 - static_cast<int>((mine >> 28) & 15ull) : rank;
-        const int src = lane_used ? base + prank : lane;
-        uint32_t bw = pack_book(bk);
-        bw = __shfl_sync(kFull, bw, src);
-        chi2 = __shfl_sync(kFull, chi2, src);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) p[i] = __shfl_sync(kFull, p[i], src);
-#pragma unroll
-        for (int k = 0; k < 21; ++k) C[k] = __shfl_sync(kFull, C[k], src);
-        lo.x = __shfl_sync(kFull, lo.x, src);
-        lo.y = __shfl_sync(kFull, lo.y, src);
-        lo.z = __shfl_sync(kFull, lo.z, src);
-        lo.phi = __shfl_sync(kFull, lo.phi, src);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            I.HCu[k] = __shfl_sync(kFull, I.HCu[k], src);
-            I.HCv[k] = __shfl_sync(kFull, I.HCv[k], src);
-        }
-        I.Iuu = __shfl_sync(kFull, I.Iuu, src);
-        I.Iuv = __shfl_sync(kFull, I.Iuv, src);
-        I.Ivv = __shfl_sync(kFull, I.Ivv, src);
-        bk = unpack_book(bw);
-        live = lane_used && mine != 0ull;
-        if (live) {
-            const uint32_t code = kHitMask - static_cast<uint32_t>(mine & kHitMask);
-            if (code < kCodeMiss) {
-                // the hit's residual and chi2 from the parent's list
-                float u = 0.f, v = 0.f, x2 = 0.f;
-                for (int j = 0; j < N; ++j)
-                    if (lorig[j * 32 + src] == static_cast<int>(code)) {
-                        u = lu[j * 32 + src];
-                        v = lv[j * 32 + src];
-                        x2 = lchi[j * 32 + src];
-                        break;
-                    }
-                chi2 += x2;
-                kf_apply(I, u, v, p, lo, C);
-                bk.nh += 1;
-                bk.consec = 0;
-                ++c_up;
-            } else if (code == kCodeMiss) {
-                bk.consec += 1;
-                bk.nmiss = min(bk.nmiss + 1, 15);
-                if (bk.consec >= A.max_consec) {
+        int step = 0;
+        while (true) {
+            const bool active = live && !bk.done;
+            if (!__any_sync(kFull, active)) break;  // every candidate of the warp has finished
+            // ---- 1. expansion: next layer, propagation, window search
+            int nlist = 0;
+            bool searched = false;
+            if (active) {
+                float sphi, cphi;
+                sincos_pair(p[4], lo.phi, sphi, cphi);
+                const float cot = cot_of(p[5]);
+                float s = 0.f;
+                const int l =
+                    finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
+                if (l == -2) status |= MKF_ST_NONFINITE;
+                if (l < 0) {
                     bk.done = true;
-                    bk.missstop = true;
+                } else {
+                    const LayerDesc &Ld = G.L[l];
+                    propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+                    searched = true;
+                    ++c_cl;
+                    const Frame f = frame_of(p);
+                    if (innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
+                        {
+                            const float wu = sqrtf(cut * I.Suu), wv = sqrtf(cut * I.Svv);
+                            const float wu_m = wu * 1.0001f, wv_m = wv * 1.0001f;
+                            const float lever = Ld.kind == 0 ? Ld.rz : f.rt;
+                            const float dphiw = wu_m / lever + 2e-6f;
+                            const float zc = Ld.kind == 0 ? p[2] : f.rt;
+                            const float wz = wv_m + 1e-5f;
+                            const float phic = atan2f(p[1], p[0]);
+                            int pb_lo, nphib;
+                            if (dphiw >= kPi) {
+                                pb_lo = 0;
+                                nphib = Ld.nphi;
+                            } else {
+                                pb_lo = static_cast<int>(floorf((phic - dphiw + kPi) * Ld.phi_scale));
+                                const int pb_hi = static_cast<int>(floorf((phic + dphiw + kPi) * Ld.phi_scale));
+                                nphib = min(pb_hi - pb_lo + 1, Ld.nphi);
+                            }
+                            const float zlo_f = fminf(fmaxf(floorf((zc - wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
+                            const float zhi_f = fminf(fmaxf(floorf((zc + wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
+                            const int zb_lo = static_cast<int>(zlo_f), zb_hi = static_cast<int>(zhi_f);
+                            const int ebase = ev * G.bins_per_event + Ld.bin_base;
+                            int n_compat = 0;
+                            for (int i = 0; i < nphib; ++i) {
+                                int pb = (pb_lo + i) % Ld.nphi;
+                                if (pb < 0) pb += Ld.nphi;
+                                const int bin = ebase + pb * Ld.nzr;
+                                const int k0 = A.offsets[bin + zb_lo], k1 = A.offsets[bin + zb_hi + 1];
+                                for (int k = k0; k < k1; ++k) {
+                                    const float4 hr = A.rec[k];
+                                    if (fabsf(hr.z - zc) > wv_m) continue;
+                                    float u, v;
+                                    residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
+                                    if (fabsf(u) > wu_m) continue;
+                                    if (fabsf(u) <= wu && fabsf(v) <= wv) ++c_ht;
+                                    const float x2 = chi2_of(I, u, v);
+                                    if (!(x2 < cut)) continue;
+                                    const int orig = __float_as_int(hr.w);
+                                    ++n_compat;
+                                    // insert into the lane's list, sorted by (chi2, orig), at most N
+                                    if (nlist == N) {
+                                        const float wc = lchi[(N - 1) * 32 + lane];
+                                        const int wo = lorig[(N - 1) * 32 + lane];
+                                        if (!(x2 < wc || (x2 == wc && orig < wo))) continue;
+                                    }
+                                    int j = nlist < N ? nlist : N - 1;
+                                    while (j > 0) {
+                                        const float pc = lchi[(j - 1) * 32 + lane];
+                                        const int po = lorig[(j - 1) * 32 + lane];
+                                        if (pc > x2 || (pc == x2 && po > orig)) {
+                                            lchi[j * 32 + lane] = pc;
+                                            lorig[j * 32 + lane] = po;
+                                            lu[j * 32 + lane] = lu[(j - 1) * 32 + lane];
+                                            lv[j * 32 + lane] = lv[(j - 1) * 32 + lane];
+                                            --j;
+                                        } else {
+                                            break;
+                                        }
+                                    }
+                                    lchi[j * 32 + lane] = x2;
+                                    lorig[j * 32 + lane] = orig;
+                                    lu[j * 32 + lane] = u;
+                                    lv[j * 32 + lane] = v;
+                                    if (nlist < N) ++nlist;
+                                }
+                            }
+                            // learned pruning / feature dump over the candidate's list (its
+                            // N best compatible hits); the MLP scores a list only when the
+                            // candidate has two or more compatible hits
+                            if (kLearned && (A.feat_out || (A.mlp && n_compat >= 2)) && nlist > 0) {
+                                int kept = 0;
+                                for (int j = 0; j < nlist; ++j) {
+                                    const float x2 = lchi[j * 32 + lane], u = lu[j * 32 + lane], v = lv[j * 32 + lane];
+                                    const int orig = lorig[j * 32 + lane];
+                                    float fe[12];
+                                    pair_features(u, v, I, x2, cut, chi2, bk, l, G.n_layers, Ld.kind, p, cot, fe);
+                                    if (A.feat_out) {
+                                        const int at = atomicAdd(A.feat_count, 1);
+                                        if (at < A.feat_cap) {
+    #pragma unroll
+                                            for (int q = 0; q < 12; ++q) A.feat_out[(int64_t)at * 12 + q] = fe[q];
+                                            A.feat_ref[(int64_t)at * 3] = seed;
+                                            A.feat_ref[(int64_t)at * 3 + 1] = orig;
+                                            A.feat_ref[(int64_t)at * 3 + 2] = n_compat;
+                                        }
+                                    }
+                                    if (A.mlp && n_compat >= 2 && mlp_logit(WS, fe) < A.mlp_tau) continue;
+                                    if (kept != j) {
+                                        lchi[kept * 32 + lane] = x2;
+                                        lorig[kept * 32 + lane] = orig;
+                                        lu[kept * 32 + lane] = u;
+                                        lv[kept * 32 + lane] = v;
+                                    }
+                                    ++kept;
+                                }
+                                nlist = kept;
+                            }
+                        }
+                    } else {
+                        status |= MKF_ST_BADS;
+                    }
                 }
             }
-            hist[step * 32 + lane] = (static_cast<uint32_t>(prank) << 28) | code;
-        }
-        ++step;
-        if (step >= A.max_steps) {
-            if (lane == 0) record_fault(A.fault, kFaultHistOverflow, gwarp);
-            break;
+            __syncwarp();
+
+            // ---- 2. selection of the N best children of each seed: N rounds of a
+            // segmented max over the lanes' best remaining child.  The score is
+            // compared as an order-preserving 32-bit integer; exact score ties (rare)
+            // are resolved by a second reduction on (parent rank, hit index).
+            const float score = cut * static_cast<float>(bk.nh) - chi2;
+            const int n_children = live ? (searched ? nlist + 1 : 1) : 0;
+            int head = 0;
+            unsigned long long mine = 0;
+            if (N == 1) {
+                if (n_children > 0) {
+                    mine = head < nlist ? child_key(score + cut - lchi[lane], 0, static_cast<uint32_t>(lorig[lane]))
+                                        : child_key(score, 0, searched ? kCodeMiss : kCodePass);
+                }
+            } else {
+                for (int j = 0; j < N; ++j) {
+                    const bool has = head < n_children;
+                    if (!__any_sync(kFull, has)) break;
+                    uint32_t k32 = 0, lo32 = 0;
+                    if (has) {
+                        const bool is_hit = head < nlist;
+                        const float sc = is_hit ? score + cut - lchi[head * 32 + lane] : score;
+                        const uint32_t code = is_hit ? static_cast<uint32_t>(lorig[head * 32 + lane])
+                                                     : (searched ? kCodeMiss : kCodePass);
+                        k32 = ord_float(sc);
+                        lo32 = (static_cast<uint32_t>(15 - rank) << 28) | (kHitMask - code);
+                    }
+                    const uint32_t m32 = seg_max32(k32, rank, N, base);
+                    const bool cand = has && k32 == m32;
+                    // the lanes of my segment holding the maximum score
+                    const unsigned seg_bits = (N == 32 ? kFull : ((1u << N) - 1u)) << (base & 31);
+                    const unsigned tied = __ballot_sync(kFull, cand) & seg_bits;
+                    uint32_t mlo;
+                    if (__any_sync(kFull, lane_used && __popc(tied) > 1)) {
+                        mlo = seg_max32(cand ? lo32 : 0u, rank, N, base);
+                    } else {
+                        mlo = __shfl_sync(kFull, lo32, tied ? (__ffs(tied) - 1) : lane);
+                    }
+                    if (m32 != 0u && lane_used) {
+                        const int wr = 15 - static_cast<int>(mlo >> 28);
+                        if (wr == rank) ++head;
+                        if (j == rank) mine = (static_cast<unsigned long long>(m32) << 32) | mlo;
+                    }
+                }
+            }
+
+            // ---- 3. each lane becomes one child: its parent's propagated state,
+            // and the parent's S^-1 and H C, by shuffles
+            const int prank = mine ? 15 - static_cast<int>((mine >> 28) & 15ull) : rank;
+            const int src = lane_used ? base + prank : lane;
+            uint32_t bw = pack_book(bk);
+            bw = __shfl_sync(kFull, bw, src);
+            chi2 = __shfl_sync(kFull, chi2, src);
+    #pragma unroll
+            for (int i = 0; i < 6; ++i) p[i] = __shfl_sync(kFull, p[i], src);
+    #pragma unroll
+            for (int k = 0; k < 21; ++k) C[k] = __shfl_sync(kFull, C[k], src);
+            lo.x = __shfl_sync(kFull, lo.x, src);
+            lo.y = __shfl_sync(kFull, lo.y, src);
+            lo.z = __shfl_sync(kFull, lo.z, src);
+            lo.phi = __shfl_sync(kFull, lo.phi, src);
+    #pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                I.HCu[k] = __shfl_sync(kFull, I.HCu[k], src);
+                I.HCv[k] = __shfl_sync(kFull, I.HCv[k], src);
+            }
+            I.Iuu = __shfl_sync(kFull, I.Iuu, src);
+            I.Iuv = __shfl_sync(kFull, I.Iuv, src);
+            I.Ivv = __shfl_sync(kFull, I.Ivv, src);
+            bk = unpack_book(bw);
+            live = lane_used && mine != 0ull;
+            if (live) {
+                const uint32_t code = kHitMask - static_cast<uint32_t>(mine & kHitMask);
+                if (code < kCodeMiss) {
+                    // the hit's residual and chi2 from the parent's list
+                    float u = 0.f, v = 0.f, x2 = 0.f;
+                    for (int j = 0; j < N; ++j)
+                        if (lorig[j * 32 + src] == static_cast<int>(code)) {
+                            u = lu[j * 32 + src];
+                            v = lv[j * 32 + src];
+                            x2 = lchi[j * 32 + src];
+                            break;
+                        }
+                    chi2 += x2;
+                    kf_apply(I, u, v, p, lo, C);
+                    bk.nh += 1;
+                    bk.consec = 0;
+                    ++c_up;
+                } else if (code == kCodeMiss) {
+                    bk.consec += 1;
+                    bk.nmiss = min(bk.nmiss + 1, 15);
+                    if (bk.consec >= A.max_consec) {
+                        bk.done = true;
+                        bk.missstop = true;
+                    }
+                }
+                hist[step * 32 + lane] = (static_cast<uint32_t>(prank) << 28) | code;
+            }
+            ++step;
+            if (step >= A.max_steps) {
+                if (lane == 0) record_fault(A.fault, kFaultHistOverflow, grp);
+                break;
+            }
+            __syncwarp();
         }
         __syncwarp();
-    }
-    __syncwarp();
 
-    // ---- output: rank 0 of each seed holds the best candidate
-    c_cl = seg_sum(c_cl, rank, N);
-    c_ht = seg_sum(c_ht, rank, N);
-    c_up = seg_sum(c_up, rank, N);
-    status = seg_or(status, rank, N);
-    if (has_seed && rank == 0) {
-        const int n = A.n_seeds;
-        const bool ok = !(status & MKF_ST_BADSEED) && live;
-        int nout = 0;
-        if (ok) {
-            const int shs[3] = {sh0, sh1, sh2};
-            for (int k = 0; k < 3 && nout < A.max_out; ++k) A.out_hits[(int64_t)(nout++) * n + seed] = shs[k];
-            // walk the history back from the best candidate, then write forwards
-            int r = 0, cnt = 0;
-            for (int st = step - 1; st >= 0; --st) {
-                const uint32_t rec = hist[st * 32 + base + r];
-                if ((rec & kHitMask) < kCodeMiss) ++cnt;
-                r = static_cast<int>(rec >> 28);
-            }
-            int pos = nout + cnt - 1;
-            r = 0;
-            for (int st = step - 1; st >= 0; --st) {
-                const uint32_t rec = hist[st * 32 + base + r];
-                const uint32_t code = rec & kHitMask;
-                if (code < kCodeMiss) {
-                    if (pos < A.max_out) A.out_hits[(int64_t)pos * n + seed] = static_cast<int>(code);
-                    --pos;
+        // ---- output: rank 0 of each seed holds the best candidate
+        c_cl = seg_sum(c_cl, rank, N);
+        c_ht = seg_sum(c_ht, rank, N);
+        c_up = seg_sum(c_up, rank, N);
+        status = seg_or(status, rank, N);
+        if (has_seed && rank == 0) {
+            const int n = A.n_seeds;
+            const bool ok = !(status & MKF_ST_BADSEED) && live;
+            int nout = 0;
+            if (ok) {
+                const int shs[3] = {sh0, sh1, sh2};
+                for (int k = 0; k < 3 && nout < A.max_out; ++k) A.out_hits[(int64_t)(nout++) * n + seed] = shs[k];
+                // walk the history back from the best candidate, then write forwards
+                int r = 0, cnt = 0;
+                for (int st = step - 1; st >= 0; --st) {
+                    const uint32_t rec = hist[st * 32 + base + r];
+                    if ((rec & kHitMask) < kCodeMiss) ++cnt;
+                    r = static_cast<int>(rec >> 28);
                 }
-                r = static_cast<int>(rec >> 28);
+                int pos = nout + cnt - 1;
+                r = 0;
+                for (int st = step - 1; st >= 0; --st) {
+                    const uint32_t rec = hist[st * 32 + base + r];
+                    const uint32_t code = rec & kHitMask;
+                    if (code < kCodeMiss) {
+                        if (pos < A.max_out) A.out_hits[(int64_t)pos * n + seed] = static_cast<int>(code);
+                        --pos;
+                    }
+                    r = static_cast<int>(rec >> 28);
+                }
+                if (nout + cnt > A.max_out) status |= MKF_ST_TRUNC;
+                nout = min(nout + cnt, A.max_out);
+                if (bk.missstop) status |= MKF_ST_MISSSTOP;
+                if (!finite_state(p) || !isfinite(chi2)) status |= MKF_ST_NONFINITE;
             }
-            if (nout + cnt > A.max_out) status |= MKF_ST_TRUNC;
-            nout = min(nout + cnt, A.max_out);
-            if (bk.missstop) status |= MKF_ST_MISSSTOP;
-            if (!finite_state(p) || !isfinite(chi2)) status |= MKF_ST_NONFINITE;
-        }
-        for (int k = nout; k < A.max_out; ++k) A.out_hits[(int64_t)k * n + seed] = -1;
-        const float nanv = __int_as_float(0x7fc00000);
-        p[0] += lo.x;
-        p[1] += lo.y;
-        p[2] += lo.z;
-        p[4] += lo.phi;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) A.out_par[(int64_t)i * n + seed] = ok ? p[i] : nanv;
-#pragma unroll
-        for (int k = 0; k < 21; ++k) A.out_cov[(int64_t)k * n + seed] = ok ? C[k] : nanv;
-        A.out_chi2[seed] = ok ? chi2 : nanv;
-        A.out_nhits[seed] = ok ? bk.nh : 0;
-        A.out_status[seed] = status;
-        if (A.counters) {
-            A.counters[seed] = c_cl;
-            A.counters[(int64_t)n + seed] = c_ht;
-            A.counters[2 * (int64_t)n + seed] = c_up;
+            for (int k = nout; k < A.max_out; ++k) A.out_hits[(int64_t)k * n + seed] = -1;
+            const float nanv = __int_as_float(0x7fc00000);
+            p[0] += lo.x;
+            p[1] += lo.y;
+            p[2] += lo.z;
+            p[4] += lo.phi;
+    #pragma unroll
+            for (int i = 0; i < 6; ++i) A.out_par[(int64_t)i * n + seed] = ok ? p[i] : nanv;
+    #pragma unroll
+            for (int k = 0; k < 21; ++k) A.out_cov[(int64_t)k * n + seed] = ok ? C[k] : nanv;
+            A.out_chi2[seed] = ok ? chi2 : nanv;
+            A.out_nhits[seed] = ok ? bk.nh : 0;
+            A.out_status[seed] = status;
+            if (A.counters) {
+                A.counters[seed] = c_cl;
+                A.counters[(int64_t)n + seed] = c_ht;
+                A.counters[2 * (int64_t)n + seed] = c_up;
+            }
+            if (A.event_times && ev >= 0 && ev < A.n_events) atomicMax(&A.event_times[ev], globaltimer_ns());
         }
     }
 }
@@ -804,18 +825,49 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     if (A.feat_out && (!A.feat_ref || !A.feat_count || A.feat_cap < 0)) return MKF_ERR_ARG;
     const size_t smem = find_smem_bytes(ctx->geom.n_layers, N, threads);
     if (smem > 200 * 1024) return MKF_ERR_CAPACITY;
-    MKF_CUDA_TRY(cudaFuncSetAttribute(find_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(std::max<size_t>(smem, 48 * 1024))));
+    // raise the kernel's dynamic shared-memory limit only when needed (not during
+    // a stream capture after the first call)
+    const bool learned = params->mlp_bf16 || params->feat_out;
+    const void *kfn = learned ? reinterpret_cast<const void *>(find_kernel<true>)
+                              : reinterpret_cast<const void *>(find_kernel<false>);
+    if (static_cast<int>(smem) > ctx->find_smem_attr) {
+        const int want = static_cast<int>(std::max<size_t>(smem, 48 * 1024));
+        MKF_CUDA_TRY(cudaFuncSetAttribute(find_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, want));
+        MKF_CUDA_TRY(cudaFuncSetAttribute(find_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, want));
+        ctx->find_smem_attr = want;
+    }
     void *scratch = nullptr;
-    mkf_status st = mkf_scratch(ctx, sizeof(float) * (size_t)kSeedFields * n_seeds, &scratch);
+    const size_t seed_bytes = ((sizeof(float) * (size_t)kSeedFields * n_seeds + 255) / 256) * 256;
+    mkf_status st = mkf_scratch(ctx, seed_bytes + 256, &scratch);
     if (st != MKF_OK) return st;
     A.seedbuf = static_cast<float *>(scratch);
+    A.work_counter = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + seed_bytes);
+    A.event_times = reinterpret_cast<unsigned long long *>(params->event_times);
+    MKF_CUDA_TRY(cudaMemsetAsync(A.work_counter, 0, sizeof(int32_t), ctx->stream));
+    if (A.event_times) {
+        MKF_CUDA_TRY(cudaMemsetAsync(A.event_times, 0, sizeof(uint64_t) * bins->n_events, ctx->stream));
+        MKF_CUDA_TRY(cudaMemsetAsync(A.event_times + bins->n_events, 0xff, sizeof(uint64_t), ctx->stream));
+    }
     seed_kernel<<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A);
     MKF_CUDA_TRY(cudaGetLastError());
+    // persistent grid: as many blocks as fit on the device at once, or fewer
     const int spw = 32 / N;
     const int seeds_per_block = spw * (threads / 32);
-    const int blocks = (n_seeds + seeds_per_block - 1) / seeds_per_block;
-    find_kernel<<<blocks, threads, smem, ctx->stream>>>(A);
+    const int need = (n_seeds + seeds_per_block - 1) / seeds_per_block;
+    // occupancy of this configuration (queried once, so that a later call can
+    // be captured into a CUDA graph without runtime queries)
+    const int vi = learned ? 1 : 0;
+    if (ctx->find_occ_threads[vi] != threads || ctx->find_occ_smem[vi] != static_cast<int>(smem)) {
+        int occ = 0;
+        MKF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, threads, smem));
+        ctx->find_occ_threads[vi] = threads;
+        ctx->find_occ_smem[vi] = static_cast<int>(smem);
+        ctx->find_occ_blocks[vi] = occ;
+    }
+    const int per_sm = ctx->find_occ_blocks[vi];
+    const int blocks = std::max(1, std::min(need, std::max(1, per_sm) * ctx->num_sms));
+    if (learned) find_kernel<true><<<blocks, threads, smem, ctx->stream>>>(A);
+    else find_kernel<false><<<blocks, threads, smem, ctx->stream>>>(A);
     MKF_CUDA_TRY(cudaGetLastError());
     return MKF_OK;
 }

@@ -35,6 +35,8 @@ struct mkf_ctx {
     void *scratch;
     size_t scratch_bytes;
     int num_sms;
+    int find_smem_attr;  // dynamic shared memory the find kernel is configured for
+    int find_occ_threads[2], find_occ_smem[2], find_occ_blocks[2];  // cached occupancy (plain, learned)
 };
 
 struct mkf_hitbins {
