@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-pruning comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-events leg")
     ap.add_argument("--batched-events", type=int, default=512)
+    ap.add_argument("--no-fit", action="store_true", help="skip the 10^6-track fit leg")
     return ap.parse_args()
 
 
@@ -327,6 +328,49 @@ def batched_leg(dev, n_events: int = 512, reps: int = 10):
 
 
 # ---------------------------------------------------------------------------
+# fit: 10^6 tracks along their hit lists
+# ---------------------------------------------------------------------------
+
+def fit_leg(dev, n_tracks: int = 1_000_000, reps: int = 20):
+    """KF fit of 10^6 tracks (10 barrel cylinders, |eta| < 1, 3.8 T, seeds from the
+    first three hits): track-layer updates/s and the fit kernel's FP32 roofline."""
+    import torch
+
+    from paper_1811_04141_gb300 import Context, flops
+    from synth import make_batch
+    n_ev = 5
+    b = make_batch("fit10", range(n_ev), n_tracks=n_tracks // n_ev)
+    ctx = Context(dev.index, torch.cuda.current_stream(dev))
+    ctx.geometry_load(b.layers, b.bz)
+    to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    xyz, layer, th = to(b.xyz, torch.float32), to(b.layer, torch.int32), to(b.track_hits, torch.int32)
+    out = ctx.fit(xyz, layer, th)
+    for _ in range(3):
+        ctx.fit(xyz, layer, th, out=out)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    ts = []
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.fit(xyz, layer, th, out=out)
+        e.record()
+        ts.append((a, e))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(e) for a, e in ts]))
+    layers = int((b.track_hits >= 0).sum())
+    fl = flops.FLOPS_PER_FIT_LAYER * layers
+    peak = flops.fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count, 2070.0)
+    ctx.close()
+    return {"workload": f"{n_ev} events x {n_tracks // n_ev} tracks, 10 barrel cylinders R=4..100 cm, |z|<=125, 3.8 T, |eta|<1, "
+                        "pT U[0.5,10] GeV, 20 um / 100 um hits, seeds from the first three hits",
+            "track_layer_updates_per_s": layers / (ms * 1e-3), "ms": ms,
+            "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": fl / (ms * 1e-3) / 1e12 / peak, "kernel": "fit_kernel"}}
+
+
+# ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
 
@@ -341,8 +385,9 @@ def run_ours(args, world, rank, local, pg):
     barrier(pg)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    from paper_1811_04141_gb300.shard import combine, events_for_rank
     E, NB = args.events, args.n_best
-    events = list(range(rank * E, (rank + 1) * E))
+    events = events_for_rank(rank, world, E)
     batch = make_batch(CONFIG, events)
     ctx = Context(local, torch.cuda.current_stream(dev))
     ctx.geometry_load(batch.layers, batch.bz)
@@ -392,8 +437,7 @@ def run_ours(args, world, rank, local, pg):
     step_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in ev]))
     find_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
     bin_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
-    step_ms_max = allreduce_max(pg, step_ms)
-    units_all = allreduce_sum(pg, cl)
+    units_all, step_ms_max = combine(pg, cl, step_ms, dev)
     value = units_all / (step_ms_max * 1e-3)
 
     # roofline of the dominant kernel (find): FP32 ALU bound
@@ -457,6 +501,9 @@ def run_ours(args, world, rank, local, pg):
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = batched_leg(dev, args.batched_events)
+    fit = None
+    if rank == 0 and world == 1 and not args.no_fit:
+        fit = fit_leg(dev)
 
     launches_per_step = 8  # bin_keys, scan_tiles, scan_blocksums, scan_write, scatter, bin_sort, seed, find
     line = {
@@ -472,7 +519,7 @@ def run_ours(args, world, rank, local, pg):
                    "l2": "flushed between steps (256 MiB write, outside the per-step CUDA events)",
                    "wall_s_timed_region": round(wall, 3), "parallelism": f"events sharded, {world} GPU(s)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "learned": learned,
-        "batched": batched,
+        "batched": batched, "fit": fit,
         "gpu_launches": launches_per_step * K,
     }
     if rank == 0:
