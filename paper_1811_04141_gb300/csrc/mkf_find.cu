@@ -64,13 +64,18 @@ struct FindArgs {
     int32_t feat_cap;
     int32_t *work_counter;                // persistent warps' shared seed-group counter
     unsigned long long *event_times;      // [n_events + 1] or nullptr
+    float *beam;                          // [kBeamFields][n_seeds * n_best] candidates after the first step
+    int32_t step1;                        // the seed kernel takes the first step (plain finder)
 };
 
 // Fitted-seed record, structure of arrays over seeds.
 enum {
     SF_P = 0, SF_LO = 6, SF_C = 10, SF_CHI2 = 31, SF_BOOK = 32, SF_MASK_LO = 33, SF_MASK_HI = 34, SF_DIR = 35,
-    SF_STATUS = 36, SF_HITS = 37, kSeedFields = 40
+    SF_STATUS = 36, SF_HITS = 37, SF_BEAM = 40, SF_CCL = 41, SF_CHT = 42, SF_CUP = 43, kSeedFields = 44
 };
+
+// Candidate after the first step, structure of arrays over (seed, rank).
+enum { BF_P = 0, BF_LO = 6, BF_C = 10, BF_CHI2 = 31, BF_BOOK = 32, BF_CODE = 33, kBeamFields = 34 };
 
 __device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) {
     if (atomicCAS(&f->code, 0, code) == 0) f->where = where;
@@ -252,6 +257,117 @@ __device__ __forceinline__ float mlp_logit(const float *ws, const float f[12]) {
     return z;
 }
 
+// Result of expanding a candidate to its next layer.
+struct Expansion {
+    int layer;      // layer reached, or -1 (none left) / -2 (non-finite state)
+    bool searched;  // propagated onto the layer and searched
+    int nlist;      // compatible hits kept (at most N), sorted by (chi2, hit index)
+    int n_compat;   // all compatible hits
+    float cot;      // cot(theta) before the move
+};
+
+// One candidate to its next layer: next-layer choice, propagation and
+// covariance transport, S^-1 and H C, the bins of the chi2 window, and the
+// list of its N best compatible hits (chi2, hit index, residual u, v) at list
+// stride `ls` (lane-interleaved shared memory in the finder, contiguous local
+// arrays in the seed kernel).  p, lo, C move onto the layer; a candidate with no
+// layer left is marked done.
+__device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev, unsigned long long mask, int dir,
+                                       int N, float cut, float p[6], Lo &lo, float C[21], Book &bk, Innov &I,
+                                       uint32_t &status, int &c_cl, int &c_ht, float *lchi, int *lorig, float *lu,
+                                       float *lv, int ls, Expansion &X) {
+    float sphi, cphi;
+    sincos_pair(p[4], lo.phi, sphi, cphi);
+    const float cot = cot_of(p[5]);
+    X.cot = cot;
+    X.searched = false;
+    X.nlist = 0;
+    X.n_compat = 0;
+    float s = 0.f;
+    const int l = finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
+    X.layer = l;
+    if (l == -2) status |= MKF_ST_NONFINITE;
+    if (l < 0) {
+        bk.done = true;
+        return;
+    }
+    const LayerDesc &Ld = G.L[l];
+    propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+    X.searched = true;
+    ++c_cl;
+    const Frame f = frame_of(p);
+    if (!innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
+        status |= MKF_ST_BADS;
+        return;
+    }
+    const float wu = sqrtf(cut * I.Suu), wv = sqrtf(cut * I.Svv);
+    const float wu_m = wu * 1.0001f, wv_m = wv * 1.0001f;
+    const float lever = Ld.kind == 0 ? Ld.rz : f.rt;
+    const float dphiw = wu_m / lever + 2e-6f;
+    const float zc = Ld.kind == 0 ? p[2] : f.rt;
+    const float wz = wv_m + 1e-5f;
+    const float phic = atan2f(p[1], p[0]);
+    int pb_lo, nphib;
+    if (dphiw >= kPi) {
+        pb_lo = 0;
+        nphib = Ld.nphi;
+    } else {
+        pb_lo = static_cast<int>(floorf((phic - dphiw + kPi) * Ld.phi_scale));
+        const int pb_hi = static_cast<int>(floorf((phic + dphiw + kPi) * Ld.phi_scale));
+        nphib = min(pb_hi - pb_lo + 1, Ld.nphi);
+    }
+    const float zlo_f = fminf(fmaxf(floorf((zc - wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
+    const float zhi_f = fminf(fmaxf(floorf((zc + wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
+    const int zb_lo = static_cast<int>(zlo_f), zb_hi = static_cast<int>(zhi_f);
+    const int ebase = ev * G.bins_per_event + Ld.bin_base;
+    int nlist = 0, n_compat = 0;
+    for (int i = 0; i < nphib; ++i) {
+        int pb = (pb_lo + i) % Ld.nphi;
+        if (pb < 0) pb += Ld.nphi;
+        const int bin = ebase + pb * Ld.nzr;
+        const int k0 = A.offsets[bin + zb_lo], k1 = A.offsets[bin + zb_hi + 1];
+        for (int k = k0; k < k1; ++k) {
+            const float4 hr = A.rec[k];
+            if (fabsf(hr.z - zc) > wv_m) continue;
+            float u, v;
+            residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
+            if (fabsf(u) > wu_m) continue;
+            if (fabsf(u) <= wu && fabsf(v) <= wv) ++c_ht;
+            const float x2 = chi2_of(I, u, v);
+            if (!(x2 < cut)) continue;
+            const int orig = __float_as_int(hr.w);
+            ++n_compat;
+            // insert into the list, sorted by (chi2, orig), at most N
+            if (nlist == N) {
+                const float wc = lchi[(N - 1) * ls];
+                const int wo = lorig[(N - 1) * ls];
+                if (!(x2 < wc || (x2 == wc && orig < wo))) continue;
+            }
+            int j = nlist < N ? nlist : N - 1;
+            while (j > 0) {
+                const float pc = lchi[(j - 1) * ls];
+                const int po = lorig[(j - 1) * ls];
+                if (pc > x2 || (pc == x2 && po > orig)) {
+                    lchi[j * ls] = pc;
+                    lorig[j * ls] = po;
+                    lu[j * ls] = lu[(j - 1) * ls];
+                    lv[j * ls] = lv[(j - 1) * ls];
+                    --j;
+                } else {
+                    break;
+                }
+            }
+            lchi[j * ls] = x2;
+            lorig[j * ls] = orig;
+            lu[j * ls] = u;
+            lv[j * ls] = v;
+            if (nlist < N) ++nlist;
+        }
+    }
+    X.nlist = nlist;
+    X.n_compat = n_compat;
+}
+
 // Seed fit, one thread per seed: state from the three hits (circle + line),
 // then the Kalman fit through them (the first hit without propagation), the
 // tracking region from the seed's eta, the direction along z and the first
@@ -355,6 +471,70 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
                 }
         }
     }
+    // The first step of the finder for this seed (one parent, so no selection
+    // across candidates): its children are the compatible hits in list order
+    // (chi2, hit index), then the miss (or the pass when no layer is left), the
+    // first N of them kept -- the order the finder's warp selection gives a
+    // single parent.  Each child gets its Kalman update here.
+    int nbeam = 0, c_cl = 0, c_ht = 0, c_up = 0;
+    if (A.step1 && ok) {
+        const int N = A.n_best;
+        const float cut = A.cut;
+        float lchi[MKF_MAX_NBEST], lu[MKF_MAX_NBEST], lv[MKF_MAX_NBEST];
+        int lorig[MKF_MAX_NBEST];
+        Book pb = bk;
+        Innov I;
+        Expansion X;
+        expand(A, G, ev, mask, dir, N, cut, p, lo, C, pb, I, status, c_cl, c_ht, lchi, lorig, lu, lv, 1, X);
+        nbeam = min(X.searched ? X.nlist + 1 : 1, N);
+        const int64_t nn = static_cast<int64_t>(n) * N, e0 = static_cast<int64_t>(t) * N;
+        float *Bm = A.beam;
+        for (int r = 0; r < nbeam; ++r) {
+            float q[6], Q[21];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) q[i] = p[i];
+#pragma unroll
+            for (int k = 0; k < 21; ++k) Q[k] = C[k];
+            Lo qlo = lo;
+            float qchi2 = chi2;
+            Book qb = pb;
+            uint32_t code;
+            if (r < X.nlist) {
+                kf_apply(I, lu[r], lv[r], q, qlo, Q);
+                qchi2 += lchi[r];
+                qb.nh += 1;
+                qb.consec = 0;
+                ++c_up;
+                code = static_cast<uint32_t>(lorig[r]);
+            } else if (X.searched) {
+                qb.consec += 1;
+                qb.nmiss = min(qb.nmiss + 1, 15);
+                if (qb.consec >= A.max_consec) {
+                    qb.done = true;
+                    qb.missstop = true;
+                }
+                code = kCodeMiss;
+            } else {
+                code = kCodePass;
+            }
+            const int64_t e = e0 + r;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) Bm[(BF_P + i) * nn + e] = q[i];
+            Bm[(BF_LO + 0) * nn + e] = qlo.x;
+            Bm[(BF_LO + 1) * nn + e] = qlo.y;
+            Bm[(BF_LO + 2) * nn + e] = qlo.z;
+            Bm[(BF_LO + 3) * nn + e] = qlo.phi;
+#pragma unroll
+            for (int k = 0; k < 21; ++k) Bm[(BF_C + k) * nn + e] = Q[k];
+            Bm[BF_CHI2 * nn + e] = qchi2;
+            Bm[BF_BOOK * nn + e] = __uint_as_float(pack_book(qb));
+            Bm[BF_CODE * nn + e] = __uint_as_float(code);
+        }
+    }
+    B[SF_BEAM * (int64_t)n + t] = __int_as_float(nbeam);
+    B[SF_CCL * (int64_t)n + t] = __int_as_float(c_cl);
+    B[SF_CHT * (int64_t)n + t] = __int_as_float(c_ht);
+    B[SF_CUP * (int64_t)n + t] = __int_as_float(c_up);
 #pragma unroll
     for (int i = 0; i < 6; ++i) B[(SF_P + i) * (int64_t)n + t] = p[i];
     B[(SF_LO + 0) * (int64_t)n + t] = lo.x;
@@ -437,8 +617,47 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
         unsigned long long mask = 0;
         int sh0 = -1, sh1 = -1, sh2 = -1;
 
-        // ---- the fitted seed (rank-0 lane), from seed_kernel
-        if (has_seed && rank == 0) {
+        int step = 0;
+        if (!kLearned && A.step1) {
+            // ---- the candidates after the first step, from seed_kernel: rank r
+            // takes child r; the seed-level record goes to rank 0
+            if (has_seed) {
+                const float *Bs = A.seedbuf;
+                const int64_t n = A.n_seeds;
+                const int nb = __float_as_int(Bs[SF_BEAM * n + seed]);
+                if (rank == 0) {
+                    status = __float_as_uint(Bs[SF_STATUS * n + seed]);
+                    ev = A.seed_event[seed];
+                    mask = static_cast<unsigned long long>(__float_as_uint(Bs[SF_MASK_LO * n + seed])) |
+                           (static_cast<unsigned long long>(__float_as_uint(Bs[SF_MASK_HI * n + seed])) << 32);
+                    dir = __float_as_int(Bs[SF_DIR * n + seed]);
+                    sh0 = __float_as_int(Bs[(SF_HITS + 0) * n + seed]);
+                    sh1 = __float_as_int(Bs[(SF_HITS + 1) * n + seed]);
+                    sh2 = __float_as_int(Bs[(SF_HITS + 2) * n + seed]);
+                    c_cl = __float_as_int(Bs[SF_CCL * n + seed]);
+                    c_ht = __float_as_int(Bs[SF_CHT * n + seed]);
+                    c_up = __float_as_int(Bs[SF_CUP * n + seed]);
+                }
+                if (rank < nb) {
+                    const float *Bm = A.beam;
+                    const int64_t nn = n * N, e = static_cast<int64_t>(seed) * N + rank;
+    #pragma unroll
+                    for (int i = 0; i < 6; ++i) p[i] = Bm[(BF_P + i) * nn + e];
+                    lo.x = Bm[(BF_LO + 0) * nn + e];
+                    lo.y = Bm[(BF_LO + 1) * nn + e];
+                    lo.z = Bm[(BF_LO + 2) * nn + e];
+                    lo.phi = Bm[(BF_LO + 3) * nn + e];
+    #pragma unroll
+                    for (int k = 0; k < 21; ++k) C[k] = Bm[(BF_C + k) * nn + e];
+                    chi2 = Bm[BF_CHI2 * nn + e];
+                    bk = unpack_book(__float_as_uint(Bm[BF_BOOK * nn + e]));
+                    hist[lane] = __float_as_uint(Bm[BF_CODE * nn + e]);  // parent rank 0
+                    live = true;
+                }
+            }
+            step = 1;
+        } else if (has_seed && rank == 0) {
+            // ---- the fitted seed (rank-0 lane), from seed_kernel
             const float *Bs = A.seedbuf;
             const int64_t n = A.n_seeds;
             status = __float_as_uint(Bs[SF_STATUS * n + seed]);
@@ -470,132 +689,49 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             dir = __shfl_sync(kFull, dir, src);
         }
 
-        int step = 0;
         while (true) {
             const bool active = live && !bk.done;
             if (!__any_sync(kFull, active)) break;  // every candidate of the warp has finished
             // ---- 1. expansion: next layer, propagation, window search
-            int nlist = 0;
-            bool searched = false;
+            Expansion X{-1, false, 0, 0, 0.f};
             if (active) {
-                float sphi, cphi;
-                sincos_pair(p[4], lo.phi, sphi, cphi);
-                const float cot = cot_of(p[5]);
-                float s = 0.f;
-                const int l =
-                    finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
-                if (l == -2) status |= MKF_ST_NONFINITE;
-                if (l < 0) {
-                    bk.done = true;
-                } else {
-                    const LayerDesc &Ld = G.L[l];
-                    propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-                    searched = true;
-                    ++c_cl;
-                    const Frame f = frame_of(p);
-                    if (innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
-                        {
-                            const float wu = sqrtf(cut * I.Suu), wv = sqrtf(cut * I.Svv);
-                            const float wu_m = wu * 1.0001f, wv_m = wv * 1.0001f;
-                            const float lever = Ld.kind == 0 ? Ld.rz : f.rt;
-                            const float dphiw = wu_m / lever + 2e-6f;
-                            const float zc = Ld.kind == 0 ? p[2] : f.rt;
-                            const float wz = wv_m + 1e-5f;
-                            const float phic = atan2f(p[1], p[0]);
-                            int pb_lo, nphib;
-                            if (dphiw >= kPi) {
-                                pb_lo = 0;
-                                nphib = Ld.nphi;
-                            } else {
-                                pb_lo = static_cast<int>(floorf((phic - dphiw + kPi) * Ld.phi_scale));
-                                const int pb_hi = static_cast<int>(floorf((phic + dphiw + kPi) * Ld.phi_scale));
-                                nphib = min(pb_hi - pb_lo + 1, Ld.nphi);
-                            }
-                            const float zlo_f = fminf(fmaxf(floorf((zc - wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
-                            const float zhi_f = fminf(fmaxf(floorf((zc + wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
-                            const int zb_lo = static_cast<int>(zlo_f), zb_hi = static_cast<int>(zhi_f);
-                            const int ebase = ev * G.bins_per_event + Ld.bin_base;
-                            int n_compat = 0;
-                            for (int i = 0; i < nphib; ++i) {
-                                int pb = (pb_lo + i) % Ld.nphi;
-                                if (pb < 0) pb += Ld.nphi;
-                                const int bin = ebase + pb * Ld.nzr;
-                                const int k0 = A.offsets[bin + zb_lo], k1 = A.offsets[bin + zb_hi + 1];
-                                for (int k = k0; k < k1; ++k) {
-                                    const float4 hr = A.rec[k];
-                                    if (fabsf(hr.z - zc) > wv_m) continue;
-                                    float u, v;
-                                    residual(Ld.kind, Ld.rz, p, lo, f, hr.x, hr.y, hr.z, u, v);
-                                    if (fabsf(u) > wu_m) continue;
-                                    if (fabsf(u) <= wu && fabsf(v) <= wv) ++c_ht;
-                                    const float x2 = chi2_of(I, u, v);
-                                    if (!(x2 < cut)) continue;
-                                    const int orig = __float_as_int(hr.w);
-                                    ++n_compat;
-                                    // insert into the lane's list, sorted by (chi2, orig), at most N
-                                    if (nlist == N) {
-                                        const float wc = lchi[(N - 1) * 32 + lane];
-                                        const int wo = lorig[(N - 1) * 32 + lane];
-                                        if (!(x2 < wc || (x2 == wc && orig < wo))) continue;
-                                    }
-                                    int j = nlist < N ? nlist : N - 1;
-                                    while (j > 0) {
-                                        const float pc = lchi[(j - 1) * 32 + lane];
-                                        const int po = lorig[(j - 1) * 32 + lane];
-                                        if (pc > x2 || (pc == x2 && po > orig)) {
-                                            lchi[j * 32 + lane] = pc;
-                                            lorig[j * 32 + lane] = po;
-                                            lu[j * 32 + lane] = lu[(j - 1) * 32 + lane];
-                                            lv[j * 32 + lane] = lv[(j - 1) * 32 + lane];
-                                            --j;
-                                        } else {
-                                            break;
-                                        }
-                                    }
-                                    lchi[j * 32 + lane] = x2;
-                                    lorig[j * 32 + lane] = orig;
-                                    lu[j * 32 + lane] = u;
-                                    lv[j * 32 + lane] = v;
-                                    if (nlist < N) ++nlist;
-                                }
-                            }
-                            // learned pruning / feature dump over the candidate's list (its
-                            // N best compatible hits); the MLP scores a list only when the
-                            // candidate has two or more compatible hits
-                            if (kLearned && (A.feat_out || (A.mlp && n_compat >= 2)) && nlist > 0) {
-                                int kept = 0;
-                                for (int j = 0; j < nlist; ++j) {
-                                    const float x2 = lchi[j * 32 + lane], u = lu[j * 32 + lane], v = lv[j * 32 + lane];
-                                    const int orig = lorig[j * 32 + lane];
-                                    float fe[12];
-                                    pair_features(u, v, I, x2, cut, chi2, bk, l, G.n_layers, Ld.kind, p, cot, fe);
-                                    if (A.feat_out) {
-                                        const int at = atomicAdd(A.feat_count, 1);
-                                        if (at < A.feat_cap) {
-    #pragma unroll
-                                            for (int q = 0; q < 12; ++q) A.feat_out[(int64_t)at * 12 + q] = fe[q];
-                                            A.feat_ref[(int64_t)at * 3] = seed;
-                                            A.feat_ref[(int64_t)at * 3 + 1] = orig;
-                                            A.feat_ref[(int64_t)at * 3 + 2] = n_compat;
-                                        }
-                                    }
-                                    if (A.mlp && n_compat >= 2 && mlp_logit(WS, fe) < A.mlp_tau) continue;
-                                    if (kept != j) {
-                                        lchi[kept * 32 + lane] = x2;
-                                        lorig[kept * 32 + lane] = orig;
-                                        lu[kept * 32 + lane] = u;
-                                        lv[kept * 32 + lane] = v;
-                                    }
-                                    ++kept;
-                                }
-                                nlist = kept;
+                expand(A, G, ev, mask, dir, N, cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi + lane, lorig + lane,
+                       lu + lane, lv + lane, 32, X);
+                // learned pruning / feature dump over the candidate's list (its
+                // N best compatible hits); the MLP scores a list only when the
+                // candidate has two or more compatible hits
+                if (kLearned && X.searched && (A.feat_out || (A.mlp && X.n_compat >= 2)) && X.nlist > 0) {
+                    const LayerDesc &Ld = G.L[X.layer];
+                    int kept = 0;
+                    for (int j = 0; j < X.nlist; ++j) {
+                        const float x2 = lchi[j * 32 + lane], u = lu[j * 32 + lane], v = lv[j * 32 + lane];
+                        const int orig = lorig[j * 32 + lane];
+                        float fe[12];
+                        pair_features(u, v, I, x2, cut, chi2, bk, X.layer, G.n_layers, Ld.kind, p, X.cot, fe);
+                        if (A.feat_out) {
+                            const int at = atomicAdd(A.feat_count, 1);
+                            if (at < A.feat_cap) {
+#pragma unroll
+                                for (int q = 0; q < 12; ++q) A.feat_out[(int64_t)at * 12 + q] = fe[q];
+                                A.feat_ref[(int64_t)at * 3] = seed;
+                                A.feat_ref[(int64_t)at * 3 + 1] = orig;
+                                A.feat_ref[(int64_t)at * 3 + 2] = X.n_compat;
                             }
                         }
-                    } else {
-                        status |= MKF_ST_BADS;
+                        if (A.mlp && X.n_compat >= 2 && mlp_logit(WS, fe) < A.mlp_tau) continue;
+                        if (kept != j) {
+                            lchi[kept * 32 + lane] = x2;
+                            lorig[kept * 32 + lane] = orig;
+                            lu[kept * 32 + lane] = u;
+                            lv[kept * 32 + lane] = v;
+                        }
+                        ++kept;
                     }
+                    X.nlist = kept;
                 }
             }
+            const int nlist = X.nlist;
+            const bool searched = X.searched;
             __syncwarp();
 
             // ---- 2. selection of the N best children of each seed: N rounds of a
@@ -838,10 +974,16 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     }
     void *scratch = nullptr;
     const size_t seed_bytes = ((sizeof(float) * (size_t)kSeedFields * n_seeds + 255) / 256) * 256;
-    mkf_status st = mkf_scratch(ctx, seed_bytes + 256, &scratch);
+    // the plain finder's first step runs in the seed kernel (one thread per
+    // seed instead of one busy lane of N); its candidates go through the beam
+    A.step1 = learned ? 0 : 1;
+    const size_t beam_bytes =
+        A.step1 ? ((sizeof(float) * (size_t)kBeamFields * n_seeds * N + 255) / 256) * 256 : 0;
+    mkf_status st = mkf_scratch(ctx, seed_bytes + beam_bytes + 256, &scratch);
     if (st != MKF_OK) return st;
     A.seedbuf = static_cast<float *>(scratch);
-    A.work_counter = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + seed_bytes);
+    A.beam = A.step1 ? reinterpret_cast<float *>(static_cast<char *>(scratch) + seed_bytes) : nullptr;
+    A.work_counter = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + seed_bytes + beam_bytes);
     A.event_times = reinterpret_cast<unsigned long long *>(params->event_times);
     MKF_CUDA_TRY(cudaMemsetAsync(A.work_counter, 0, sizeof(int32_t), ctx->stream));
     if (A.event_times) {

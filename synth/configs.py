@@ -68,11 +68,11 @@ CONFIGS = {
                      ineff=0.0, noise_mode="none", noise=0.0),
     # Track finding: 10 cylinders + 5 disks per side, |eta| < 2.4, 2 % inefficiency,
     # uniform noise at 5x each layer's signal count.
-    "find20": dict(layers=_barrel10(128, 16) + _disks10(128, 16), bz=3.8, n_tracks=2000,
+    "find20": dict(layers=_barrel10(256, 32) + _disks10(256, 32), bz=3.8, n_tracks=2000,
                    eta_max=2.4, pt_min=0.5, pt_max=10.0, pt_spectrum="flat", z0_half=5.0,
                    ineff=0.02, noise_mode="per_signal", noise=5.0),
     # Dense occupancy: 17 cylinders + 2 x 14 disks, pT^-3, 200k noise hits per event.
-    "dense45": dict(layers=_dense45(128, 16), bz=3.8, n_tracks=6000, eta_max=2.4,
+    "dense45": dict(layers=_dense45(256, 32), bz=3.8, n_tracks=6000, eta_max=2.4,
                     pt_min=0.5, pt_max=100.0, pt_spectrum="power3", z0_half=5.0,
                     ineff=0.02, noise_mode="total", noise=200000.0),
 }

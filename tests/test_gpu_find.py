@@ -168,3 +168,26 @@ def test_find_region_plans():
     geo = O.Geometry(b.layers, b.bz, edges, masks)
     ref = run_oracle(b, 10, geo=geo)
     compare(out, ref)
+
+
+@pytest.mark.parametrize("cfg,n_best", [("find20", 10), ("dense45", 16), ("dense45", 1)])
+def test_first_step_paths_agree(cfg, n_best):
+    """The plain finder takes its first step in the seed kernel (one thread per
+    seed); the feature-dump variant takes it in the warp like every other step.
+    Both must find the same tracks with the same parameters."""
+    from paper_1811_04141_gb300.api import feature_buffer
+    b = make_batch(cfg, [31], n_tracks=800, n_noise=30000 if cfg == "dense45" else None)
+    ctx = make_ctx(b)
+    d = upload(b)
+    bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
+    mo = len(b.layers) + 3
+    a = to_np(ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=n_best, max_out=mo))
+    w = to_np(ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=n_best, max_out=mo, feat=feature_buffer(1 << 20)))
+    ctx.sync()
+    same = (a["hits"] == w["hits"]).all(axis=0)
+    assert same.mean() >= 0.999, same.mean()
+    assert (a["status"][same] == w["status"][same]).all()
+    assert (a["counters"][:, same] == w["counters"][:, same]).all()
+    ok = same & (a["status"] & O.ST_BADSEED == 0)
+    assert np.allclose(a["par"][:, ok], w["par"][:, ok], rtol=1e-5, atol=1e-6)
+    assert np.allclose(a["chi2"][ok], w["chi2"][ok], rtol=1e-4, atol=1e-5)
