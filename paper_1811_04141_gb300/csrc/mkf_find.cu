@@ -64,18 +64,19 @@ struct FindArgs {
     int32_t feat_cap;
     int32_t *work_counter;                // persistent warps' shared seed-group counter
     unsigned long long *event_times;      // [n_events + 1] or nullptr
-    float *beam;                          // [kBeamFields][n_seeds * n_best] candidates after the first step
+    float *beam;                          // [n_best][kListFields][n_seeds] first-step hit lists
     int32_t step1;                        // the seed kernel takes the first step (plain finder)
 };
 
 // Fitted-seed record, structure of arrays over seeds.
 enum {
     SF_P = 0, SF_LO = 6, SF_C = 10, SF_CHI2 = 31, SF_BOOK = 32, SF_MASK_LO = 33, SF_MASK_HI = 34, SF_DIR = 35,
-    SF_STATUS = 36, SF_HITS = 37, SF_BEAM = 40, SF_CCL = 41, SF_CHT = 42, SF_CUP = 43, kSeedFields = 44
+    SF_STATUS = 36, SF_HITS = 37, SF_BEAM = 40, SF_CCL = 41, SF_CHT = 42, SF_NLIST = 43, SF_SEARCHED = 44,
+    SF_I = 45, kSeedFields = 60
 };
 
-// Candidate after the first step, structure of arrays over (seed, rank).
-enum { BF_P = 0, BF_LO = 6, BF_C = 10, BF_CHI2 = 31, BF_BOOK = 32, BF_CODE = 33, kBeamFields = 34 };
+// First-step hit list of a seed, [entry][field][seed].
+enum { LF_CHI2 = 0, LF_ORIG = 1, LF_U = 2, LF_V = 3, kListFields = 4 };
 
 __device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) {
     if (atomicCAS(&f->code, 0, code) == 0) f->where = where;
@@ -198,7 +199,9 @@ __device__ __forceinline__ int next_layer(const Geom &G, unsigned long long mask
     return -1;
 }
 
-// Segmented reductions over the N lanes [base, base + N) of a seed.
+// Segmented reductions over the N lanes [base, base + N) of a seed, by
+// shuffles.  (The redux unit with one member mask per segment measured ~20 %
+// slower for the whole finder.)
 __device__ __forceinline__ uint32_t seg_max32(uint32_t v, int rank, int N, int base) {
 #pragma unroll
     for (int off = 1; off < 16; off <<= 1) {
@@ -255,6 +258,26 @@ __device__ __forceinline__ float mlp_logit(const float *ws, const float f[12]) {
         z = fmaf(ws[MKF_MLP_IN * MKF_MLP_HIDDEN + MKF_MLP_HIDDEN + j], fmaxf(a, 0.f), z);
     }
     return z;
+}
+
+// A child of its (propagated) parent: the Kalman update with its hit, or the
+// bookkeeping of a miss; a pass (no layer left) leaves the parent as it is.
+__device__ __forceinline__ void make_child(uint32_t code, const Innov &I, float u, float v, float x2, int max_consec,
+                                           float p[6], Lo &lo, float C[21], float &chi2, Book &bk, int &c_up) {
+    if (code < kCodeMiss) {
+        chi2 += x2;
+        kf_apply(I, u, v, p, lo, C);
+        bk.nh += 1;
+        bk.consec = 0;
+        ++c_up;
+    } else if (code == kCodeMiss) {
+        bk.consec += 1;
+        bk.nmiss = min(bk.nmiss + 1, 15);
+        if (bk.consec >= max_consec) {
+            bk.done = true;
+            bk.missstop = true;
+        }
+    }
 }
 
 // Result of expanding a candidate to its next layer.
@@ -472,69 +495,47 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
         }
     }
     // The first step of the finder for this seed (one parent, so no selection
-    // across candidates): its children are the compatible hits in list order
-    // (chi2, hit index), then the miss (or the pass when no layer is left), the
-    // first N of them kept -- the order the finder's warp selection gives a
-    // single parent.  Each child gets its Kalman update here.
-    int nbeam = 0, c_cl = 0, c_ht = 0, c_up = 0;
+    // across candidates): the move to the next layer and the hit list.  The
+    // seed's children are its compatible hits in list order (chi2, hit index),
+    // then the miss (or the pass when no layer is left), the first N of them --
+    // the order the finder's warp selection gives a single parent; the finder's
+    // lanes make the children (one Kalman update each) from the moved seed,
+    // its S^-1 and H C, and the list.
+    int nbeam = 0, c_cl = 0, c_ht = 0, nlist = 0;
+    bool searched = false;
+    Innov I;
     if (A.step1 && ok) {
         const int N = A.n_best;
-        const float cut = A.cut;
         float lchi[MKF_MAX_NBEST], lu[MKF_MAX_NBEST], lv[MKF_MAX_NBEST];
         int lorig[MKF_MAX_NBEST];
-        Book pb = bk;
-        Innov I;
         Expansion X;
-        expand(A, G, ev, mask, dir, N, cut, p, lo, C, pb, I, status, c_cl, c_ht, lchi, lorig, lu, lv, 1, X);
-        nbeam = min(X.searched ? X.nlist + 1 : 1, N);
-        const int64_t nn = static_cast<int64_t>(n) * N, e0 = static_cast<int64_t>(t) * N;
-        float *Bm = A.beam;
-        for (int r = 0; r < nbeam; ++r) {
-            float q[6], Q[21];
+        expand(A, G, ev, mask, dir, N, A.cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi, lorig, lu, lv, 1, X);
+        nlist = X.nlist;
+        searched = X.searched;
+        nbeam = min(searched ? nlist + 1 : 1, N);
+        float *L = A.beam;
+        for (int k = 0; k < nlist; ++k) {
+            L[((int64_t)k * kListFields + LF_CHI2) * n + t] = lchi[k];
+            L[((int64_t)k * kListFields + LF_ORIG) * n + t] = __int_as_float(lorig[k]);
+            L[((int64_t)k * kListFields + LF_U) * n + t] = lu[k];
+            L[((int64_t)k * kListFields + LF_V) * n + t] = lv[k];
+        }
+        if (nlist > 0) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) q[i] = p[i];
-#pragma unroll
-            for (int k = 0; k < 21; ++k) Q[k] = C[k];
-            Lo qlo = lo;
-            float qchi2 = chi2;
-            Book qb = pb;
-            uint32_t code;
-            if (r < X.nlist) {
-                kf_apply(I, lu[r], lv[r], q, qlo, Q);
-                qchi2 += lchi[r];
-                qb.nh += 1;
-                qb.consec = 0;
-                ++c_up;
-                code = static_cast<uint32_t>(lorig[r]);
-            } else if (X.searched) {
-                qb.consec += 1;
-                qb.nmiss = min(qb.nmiss + 1, 15);
-                if (qb.consec >= A.max_consec) {
-                    qb.done = true;
-                    qb.missstop = true;
-                }
-                code = kCodeMiss;
-            } else {
-                code = kCodePass;
+            for (int k = 0; k < 6; ++k) {
+                B[(SF_I + k) * (int64_t)n + t] = I.HCu[k];
+                B[(SF_I + 6 + k) * (int64_t)n + t] = I.HCv[k];
             }
-            const int64_t e = e0 + r;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) Bm[(BF_P + i) * nn + e] = q[i];
-            Bm[(BF_LO + 0) * nn + e] = qlo.x;
-            Bm[(BF_LO + 1) * nn + e] = qlo.y;
-            Bm[(BF_LO + 2) * nn + e] = qlo.z;
-            Bm[(BF_LO + 3) * nn + e] = qlo.phi;
-#pragma unroll
-            for (int k = 0; k < 21; ++k) Bm[(BF_C + k) * nn + e] = Q[k];
-            Bm[BF_CHI2 * nn + e] = qchi2;
-            Bm[BF_BOOK * nn + e] = __uint_as_float(pack_book(qb));
-            Bm[BF_CODE * nn + e] = __uint_as_float(code);
+            B[(SF_I + 12) * (int64_t)n + t] = I.Iuu;
+            B[(SF_I + 13) * (int64_t)n + t] = I.Iuv;
+            B[(SF_I + 14) * (int64_t)n + t] = I.Ivv;
         }
     }
+    B[SF_NLIST * (int64_t)n + t] = __int_as_float(nlist);
+    B[SF_SEARCHED * (int64_t)n + t] = __int_as_float(searched ? 1 : 0);
     B[SF_BEAM * (int64_t)n + t] = __int_as_float(nbeam);
     B[SF_CCL * (int64_t)n + t] = __int_as_float(c_cl);
     B[SF_CHT * (int64_t)n + t] = __int_as_float(c_ht);
-    B[SF_CUP * (int64_t)n + t] = __int_as_float(c_up);
 #pragma unroll
     for (int i = 0; i < 6; ++i) B[(SF_P + i) * (int64_t)n + t] = p[i];
     B[(SF_LO + 0) * (int64_t)n + t] = lo.x;
@@ -577,6 +578,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     const int base = slot * N;
     const bool lane_used = slot < spw;
     const int nwarps = blockDim.x >> 5;
+    const unsigned seg_bits = lane_used ? ((N == 32 ? kFull : ((1u << N) - 1u)) << base) : 0u;
 
     // shared memory: per-step history, then the per-lane child lists
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem) + warp * (A.max_steps * 32);
@@ -636,22 +638,39 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                     sh2 = __float_as_int(Bs[(SF_HITS + 2) * n + seed]);
                     c_cl = __float_as_int(Bs[SF_CCL * n + seed]);
                     c_ht = __float_as_int(Bs[SF_CHT * n + seed]);
-                    c_up = __float_as_int(Bs[SF_CUP * n + seed]);
                 }
                 if (rank < nb) {
-                    const float *Bm = A.beam;
-                    const int64_t nn = n * N, e = static_cast<int64_t>(seed) * N + rank;
+                    // child `rank` of the moved seed
     #pragma unroll
-                    for (int i = 0; i < 6; ++i) p[i] = Bm[(BF_P + i) * nn + e];
-                    lo.x = Bm[(BF_LO + 0) * nn + e];
-                    lo.y = Bm[(BF_LO + 1) * nn + e];
-                    lo.z = Bm[(BF_LO + 2) * nn + e];
-                    lo.phi = Bm[(BF_LO + 3) * nn + e];
+                    for (int i = 0; i < 6; ++i) p[i] = Bs[(SF_P + i) * n + seed];
+                    lo.x = Bs[(SF_LO + 0) * n + seed];
+                    lo.y = Bs[(SF_LO + 1) * n + seed];
+                    lo.z = Bs[(SF_LO + 2) * n + seed];
+                    lo.phi = Bs[(SF_LO + 3) * n + seed];
     #pragma unroll
-                    for (int k = 0; k < 21; ++k) C[k] = Bm[(BF_C + k) * nn + e];
-                    chi2 = Bm[BF_CHI2 * nn + e];
-                    bk = unpack_book(__float_as_uint(Bm[BF_BOOK * nn + e]));
-                    hist[lane] = __float_as_uint(Bm[BF_CODE * nn + e]);  // parent rank 0
+                    for (int k = 0; k < 21; ++k) C[k] = Bs[(SF_C + k) * n + seed];
+                    chi2 = Bs[SF_CHI2 * n + seed];
+                    bk = unpack_book(__float_as_uint(Bs[SF_BOOK * n + seed]));
+                    const int nl = __float_as_int(Bs[SF_NLIST * n + seed]);
+                    uint32_t code = __float_as_int(Bs[SF_SEARCHED * n + seed]) ? kCodeMiss : kCodePass;
+                    float u = 0.f, v = 0.f, x2 = 0.f;
+                    if (rank < nl) {
+    #pragma unroll
+                        for (int k = 0; k < 6; ++k) {
+                            I.HCu[k] = Bs[(SF_I + k) * n + seed];
+                            I.HCv[k] = Bs[(SF_I + 6 + k) * n + seed];
+                        }
+                        I.Iuu = Bs[(SF_I + 12) * n + seed];
+                        I.Iuv = Bs[(SF_I + 13) * n + seed];
+                        I.Ivv = Bs[(SF_I + 14) * n + seed];
+                        const float *L = A.beam;
+                        x2 = L[((int64_t)rank * kListFields + LF_CHI2) * n + seed];
+                        code = __float_as_uint(L[((int64_t)rank * kListFields + LF_ORIG) * n + seed]);
+                        u = L[((int64_t)rank * kListFields + LF_U) * n + seed];
+                        v = L[((int64_t)rank * kListFields + LF_V) * n + seed];
+                    }
+                    make_child(code, I, u, v, x2, A.max_consec, p, lo, C, chi2, bk, c_up);
+                    hist[lane] = code;  // parent rank 0
                     live = true;
                 }
             }
@@ -763,7 +782,6 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                     const uint32_t m32 = seg_max32(k32, rank, N, base);
                     const bool cand = has && k32 == m32;
                     // the lanes of my segment holding the maximum score
-                    const unsigned seg_bits = (N == 32 ? kFull : ((1u << N) - 1u)) << (base & 31);
                     const unsigned tied = __ballot_sync(kFull, cand) & seg_bits;
                     uint32_t mlo;
                     if (__any_sync(kFull, lane_used && __popc(tied) > 1)) {
@@ -806,9 +824,9 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             live = lane_used && mine != 0ull;
             if (live) {
                 const uint32_t code = kHitMask - static_cast<uint32_t>(mine & kHitMask);
-                if (code < kCodeMiss) {
-                    // the hit's residual and chi2 from the parent's list
-                    float u = 0.f, v = 0.f, x2 = 0.f;
+                // the hit's residual and chi2 from the parent's list
+                float u = 0.f, v = 0.f, x2 = 0.f;
+                if (code < kCodeMiss)
                     for (int j = 0; j < N; ++j)
                         if (lorig[j * 32 + src] == static_cast<int>(code)) {
                             u = lu[j * 32 + src];
@@ -816,19 +834,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                             x2 = lchi[j * 32 + src];
                             break;
                         }
-                    chi2 += x2;
-                    kf_apply(I, u, v, p, lo, C);
-                    bk.nh += 1;
-                    bk.consec = 0;
-                    ++c_up;
-                } else if (code == kCodeMiss) {
-                    bk.consec += 1;
-                    bk.nmiss = min(bk.nmiss + 1, 15);
-                    if (bk.consec >= A.max_consec) {
-                        bk.done = true;
-                        bk.missstop = true;
-                    }
-                }
+                make_child(code, I, u, v, x2, A.max_consec, p, lo, C, chi2, bk, c_up);
                 hist[step * 32 + lane] = (static_cast<uint32_t>(prank) << 28) | code;
             }
             ++step;
@@ -978,7 +984,7 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     // seed instead of one busy lane of N); its candidates go through the beam
     A.step1 = learned ? 0 : 1;
     const size_t beam_bytes =
-        A.step1 ? ((sizeof(float) * (size_t)kBeamFields * n_seeds * N + 255) / 256) * 256 : 0;
+        A.step1 ? ((sizeof(float) * (size_t)kListFields * n_seeds * N + 255) / 256) * 256 : 0;
     mkf_status st = mkf_scratch(ctx, seed_bytes + beam_bytes + 256, &scratch);
     if (st != MKF_OK) return st;
     A.seedbuf = static_cast<float *>(scratch);

@@ -174,7 +174,9 @@ def test_find_region_plans():
 def test_first_step_paths_agree(cfg, n_best):
     """The plain finder takes its first step in the seed kernel (one thread per
     seed); the feature-dump variant takes it in the warp like every other step.
-    Both must find the same tracks with the same parameters."""
+    Both must find the same tracks with the same parameters; they may differ by
+    FP32 rounding (the two kernels contract multiply-adds differently), so chi2
+    is held to the FP32 floor the oracle parity uses."""
     from paper_1811_04141_gb300.api import feature_buffer
     b = make_batch(cfg, [31], n_tracks=800, n_noise=30000 if cfg == "dense45" else None)
     ctx = make_ctx(b)
@@ -190,4 +192,5 @@ def test_first_step_paths_agree(cfg, n_best):
     assert (a["counters"][:, same] == w["counters"][:, same]).all()
     ok = same & (a["status"] & O.ST_BADSEED == 0)
     assert np.allclose(a["par"][:, ok], w["par"][:, ok], rtol=1e-5, atol=1e-6)
-    assert np.allclose(a["chi2"][ok], w["chi2"][ok], rtol=1e-4, atol=1e-5)
+    ndf = 2 * a["n_hits"][ok] - 5
+    assert chi2_ok(a["chi2"][ok], w["chi2"][ok].astype(np.float64), ndf)
