@@ -153,9 +153,36 @@ __device__ __forceinline__ float asinc(float x) {
     return asinf(x) / x;
 }
 
+// sin and cos of a bounded angle, |x| <= 8 (state angles, half turning
+// angles): Cody-Waite reduction x = k pi/2 + r with pi/2 split into two floats
+// (the FMA forms k * hi exactly; |k| <= 5 keeps the split's own error below
+// 1e-14), then the Taylor series of sin to r^9 and of cos to r^10 on
+// |r| <= pi/4 (truncation below 2e-9 relative), and the quadrant swap.
+__device__ __forceinline__ void sincos_small(float x, float &s, float &c) {
+    constexpr float kPio2Hi = 1.57079637050628662109375f;   // float(pi/2)
+    constexpr float kPio2Lo = -4.37113900018624283e-8f;     // pi/2 - float(pi/2)
+    const float k = rintf(x * 0.636619772367581343f);       // x * 2/pi
+    float r = fmaf(k, -kPio2Hi, x);
+    r = fmaf(k, -kPio2Lo, r);
+    const float r2 = r * r;
+    float ps = fmaf(r2, 1.f / 362880.f, -1.f / 5040.f);
+    ps = fmaf(r2, ps, 1.f / 120.f);
+    ps = fmaf(r2, ps, -1.f / 6.f);
+    ps = fmaf(r2 * r, ps, r);
+    float pc = fmaf(r2, -1.f / 3628800.f, 1.f / 40320.f);
+    pc = fmaf(r2, pc, -1.f / 720.f);
+    pc = fmaf(r2, pc, 1.f / 24.f);
+    pc = fmaf(r2, pc, -0.5f);
+    pc = fmaf(r2, pc, 1.f);
+    const int q = static_cast<int>(k) & 3;
+    const float sa = (q & 1) ? pc : ps, ca = (q & 1) ? ps : pc;
+    s = (q & 2) ? -sa : sa;
+    c = ((q + 1) & 2) ? -ca : ca;
+}
+
 __device__ __forceinline__ float cot_of(float theta) {
     float st, ct;
-    sincosf(theta, &st, &ct);
+    sincos_small(theta, st, ct);
     return ct / st;
 }
 
@@ -207,7 +234,7 @@ __device__ __forceinline__ bool path_to_layer(const LayerDesc& Ld, float kb, con
 __device__ __forceinline__ void helix_point(const float p[6], float sphi, float cphi, float cot, float h, float s,
                                             float& x, float& y, float& z) {
     float a = 0.5f * h * s, sa, ca, sn, dsn;
-    sincosf(a, &sa, &ca);
+    sincos_small(a, sa, ca);
     sinc_and_deriv(a, sa, ca, sn, dsn);
     float L = s * sn;
     float cm = cphi * ca - sphi * sa, sm = sphi * ca + cphi * sa;
@@ -223,14 +250,15 @@ __device__ __forceinline__ void propagate_transport(const LayerDesc& Ld, float k
     const float h = -p[3] * kb;
     const float a = 0.5f * h * s;
     float sa, ca, sn, dsn;
-    sincosf(a, &sa, &ca);
+    sincos_small(a, sa, ca);
     sinc_and_deriv(a, sa, ca, sn, dsn);
     const float L = s * sn;
     const float cm = cphi * ca - sphi * sa, sm = sphi * ca + cphi * sa;  // direction phi + a
     const float dx = L * cm, dy = L * sm;
     const float c2a = 1.f - 2.f * sa * sa, s2a = 2.f * sa * ca;
     const float cpe = cphi * c2a - sphi * s2a, spe = sphi * c2a + cphi * s2a;  // direction at the end
-    const float st = sinf(p[5]);
+    float st, ct_unused;
+    sincos_small(p[5], st, ct_unused);
     const float xe = p[0] + dx, ye = p[1] + dy;
 
     // fixed-path Jacobian entries
@@ -453,7 +481,7 @@ __device__ __forceinline__ bool seed_state(const LayerDesc& L1, float kb, const 
 // sin and cos of the phi pair (first-order correction for the low part).
 __device__ __forceinline__ void sincos_pair(float hi, float lo, float& s, float& c) {
     float s0, c0;
-    sincosf(hi, &s0, &c0);
+    sincos_small(hi, s0, c0);
     s = fmaf(c0, lo, s0);
     c = fmaf(-s0, lo, c0);
 }
