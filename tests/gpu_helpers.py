@@ -8,6 +8,12 @@ import oracle as O
 # (x, y, z: 1e-4 cm; q/pT: 1e-6 c/GeV; phi, theta: 1e-5 rad).
 PAR_REL = 1e-4
 PAR_FLOOR = np.array([1e-4, 1e-4, 1e-4, 1e-6, 1e-5, 1e-5])
+# plus 1 % of the state's own standard deviation: a found candidate stopped by
+# misses reports its state extrapolated to the last crossed layer, up to a full
+# turn past its last hit, where FP32 rounding of the path (~1e-6 relative over
+# a few metres) reaches microns while the state is known only to millimetres.
+# At a measured layer sigma is tens of microns, so the floors still decide.
+PAR_SIGMA_FRAC = 1e-2
 # chi2: relative 1e-3 of max(chi2, ndf) on >= 98 % of tracks and 3e-3 on all.
 # The FP32 rounding of a residual is a fixed fraction of the hit resolution, so
 # its effect on chi2 scales with the number of measurements, not with chi2 itself
@@ -24,11 +30,16 @@ def wrap(a):
     return (a + np.pi) % (2 * np.pi) - np.pi
 
 
-def par_errors(gpu, ref):
-    """|gpu - ref| / (rel * |ref| + floor), per component; <= 1 passes."""
+def par_errors(gpu, ref, ref_cov21=None):
+    """|gpu - ref| / (rel * |ref| + floor [+ 1 % of sigma]), per component; <= 1 passes.
+    ref_cov21: the reference covariance (21 packed values per track) for the sigma term."""
     d = np.abs(gpu - ref)
     d[4] = np.abs(wrap(gpu[4] - ref[4]))
-    return d / (PAR_REL * np.abs(ref) + PAR_FLOOR[:, None])
+    tol = PAR_REL * np.abs(ref) + PAR_FLOOR[:, None]
+    if ref_cov21 is not None:
+        diag = np.asarray(ref_cov21)[[0, 2, 5, 9, 14, 20]]
+        tol = tol + PAR_SIGMA_FRAC * np.sqrt(np.maximum(diag, 0.0))
+    return d / tol
 
 
 def chi2_errors(gpu, ref, ndf):
