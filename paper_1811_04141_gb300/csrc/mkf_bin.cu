@@ -171,14 +171,21 @@ __global__ void __launch_bounds__(256) scatter_kernel(const float *X, const floa
 }
 
 // Order the hits of each bin by original index (the scatter's atomics leave an
-// arbitrary order), and rebuild the inverse map.
-__global__ void __launch_bounds__(256) bin_sort_kernel(const int32_t *offsets, int64_t n_bins, float4 *rec, int32_t *inv) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// arbitrary order), one thread per bin, insertion sort in place; bins with fewer
+// than two hits are already in order and mapped by the scatter.  (Staging a
+// block's bins in shared memory, or a sorting network in registers, measured
+// slower: most bins hold zero or one hit.)
+constexpr int kSortBins = 256;
+
+__global__ void __launch_bounds__(kSortBins) bin_sort_kernel(const int32_t *offsets, int64_t n_bins, float4 *rec,
+                                                             int32_t *inv) {
+    const int64_t b = (int64_t)blockIdx.x * kSortBins + threadIdx.x;
     if (b >= n_bins) return;
     const int s = offsets[b], e = offsets[b + 1];
+    if (e - s < 2) return;
     for (int i = s + 1; i < e; ++i) {
-        float4 v = rec[i];
-        int key = __float_as_int(v.w);
+        const float4 v = rec[i];
+        const int key = __float_as_int(v.w);
         int j = i - 1;
         while (j >= s && __float_as_int(rec[j].w) > key) {
             rec[j + 1] = rec[j];
@@ -226,6 +233,53 @@ mkf_status grow(mkf_hitbins *b, int64_t n_hits, int64_t n_bins) {
     }
     return MKF_OK;
 }
+
+// The binning pipeline on given buffers: keys and histogram, exclusive scan,
+// scatter, in-bin ordering.  counts [n_bins] must be zero on entry; tilesums
+// [ceil(n_bins / kScanTile)] is scan scratch.
+mkf_status run_binning(mkf_ctx *ctx, const float *xyz, const int32_t *layer, const int32_t *event_offsets,
+                       int32_t n_events, int32_t n_hits, int64_t n_bins, int32_t *counts, int32_t *tilesums,
+                       int32_t *key, uint8_t *layer8, float *zhit, int32_t *offsets, float4 *rec, int32_t *inv) {
+    cudaStream_t s = ctx->stream;
+    if (n_hits > 0) {
+        BinArgs A;
+        A.G = ctx->geom;
+        A.X = xyz;
+        A.Y = xyz + n_hits;
+        A.Z = xyz + 2 * (int64_t)n_hits;
+        A.layer = layer;
+        A.event_offsets = event_offsets;
+        A.n_events = n_events;
+        A.n_hits = n_hits;
+        A.key = key;
+        A.layer8 = layer8;
+        A.zhit = zhit;
+        A.counts = counts;
+        A.fault = ctx->fault;
+        bin_keys_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(A);
+        MKF_CUDA_TRY(cudaGetLastError());
+    }
+    const int64_t nblk = (n_bins + kScanTile - 1) / kScanTile;
+    scan_tiles_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n_bins, tilesums);
+    MKF_CUDA_TRY(cudaGetLastError());
+    scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(tilesums, nblk, offsets, n_bins);
+    MKF_CUDA_TRY(cudaGetLastError());
+    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n_bins, tilesums, offsets);
+    MKF_CUDA_TRY(cudaGetLastError());
+    if (n_hits > 0) {
+        unsigned long long disk_mask = 0;
+        for (int l = 0; l < ctx->geom.n_layers; ++l)
+            if (ctx->geom.L[l].kind == 1) disk_mask |= 1ull << l;
+        scatter_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(xyz, xyz + n_hits, xyz + 2 * (int64_t)n_hits, key, layer8,
+                                                           n_hits, disk_mask, offsets, counts, rec, inv);
+        MKF_CUDA_TRY(cudaGetLastError());
+        bin_sort_kernel<<<(unsigned)((n_bins + kSortBins - 1) / kSortBins), kSortBins, 0, s>>>(offsets, n_bins, rec,
+                                                                                               inv);
+        MKF_CUDA_TRY(cudaGetLastError());
+    }
+    return MKF_OK;
+}
+
 
 }  // namespace
 
@@ -298,42 +352,9 @@ extern "C" mkf_status mkf_hits_bin(mkf_ctx *ctx, const float *xyz, const int32_t
     b->n_bins = n_bins;
     cudaStream_t s = ctx->stream;
     MKF_CUDA_TRY(cudaMemsetAsync(b->counts, 0, n_bins * sizeof(int32_t), s));
-    if (n_hits > 0) {
-        BinArgs A;
-        A.G = ctx->geom;
-        A.X = xyz;
-        A.Y = xyz + n_hits;
-        A.Z = xyz + 2 * (int64_t)n_hits;
-        A.layer = layer;
-        A.event_offsets = event_offsets;
-        A.n_events = n_events;
-        A.n_hits = n_hits;
-        A.key = b->key;
-        A.layer8 = b->layer;
-        A.zhit = b->zhit;
-        A.counts = b->counts;
-        A.fault = ctx->fault;
-        bin_keys_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(A);
-        MKF_CUDA_TRY(cudaGetLastError());
-    }
-    const int64_t nblk = (n_bins + kScanTile - 1) / kScanTile;
-    scan_tiles_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(b->counts, n_bins, b->blocksums);
-    MKF_CUDA_TRY(cudaGetLastError());
-    scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(b->blocksums, nblk, b->offsets, n_bins);
-    MKF_CUDA_TRY(cudaGetLastError());
-    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(b->counts, n_bins, b->blocksums, b->offsets);
-    MKF_CUDA_TRY(cudaGetLastError());
-    if (n_hits > 0) {
-        unsigned long long disk_mask = 0;
-        for (int l = 0; l < ctx->geom.n_layers; ++l)
-            if (ctx->geom.L[l].kind == 1) disk_mask |= 1ull << l;
-        scatter_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(xyz, xyz + n_hits, xyz + 2 * (int64_t)n_hits, b->key,
-                                                           b->layer, n_hits, disk_mask, b->offsets, b->counts, b->rec,
-                                                           b->inv);
-        MKF_CUDA_TRY(cudaGetLastError());
-        bin_sort_kernel<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(b->offsets, n_bins, b->rec, b->inv);
-        MKF_CUDA_TRY(cudaGetLastError());
-    }
+    st = run_binning(ctx, xyz, layer, event_offsets, n_events, n_hits, n_bins, b->counts, b->blocksums, b->key,
+                     b->layer, b->zhit, b->offsets, b->rec, b->inv);
+    if (st != MKF_OK) return st;
     *inout = b;
     return MKF_OK;
 }
@@ -402,40 +423,6 @@ extern "C" mkf_status mkf_hits_bin_static(mkf_ctx *ctx, const float *xyz, const 
     cudaStream_t s = ctx->stream;
     // the histogram starts at zero on every call (the array keeps the last call's contents)
     MKF_CUDA_TRY(cudaMemsetAsync(counts, 0, n_bins * sizeof(int32_t), s));
-    if (n_hits > 0) {
-        BinArgs A;
-        A.G = ctx->geom;
-        A.X = xyz;
-        A.Y = xyz + n_hits;
-        A.Z = xyz + 2 * (int64_t)n_hits;
-        A.layer = layer;
-        A.event_offsets = event_offsets;
-        A.n_events = n_events;
-        A.n_hits = n_hits;
-        A.key = key;
-        A.layer8 = layer8;
-        A.zhit = zhit;
-        A.counts = counts;
-        A.fault = ctx->fault;
-        bin_keys_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(A);
-        MKF_CUDA_TRY(cudaGetLastError());
-    }
-    const int64_t nblk = (n_bins + kScanTile - 1) / kScanTile;
-    scan_tiles_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n_bins, blocksums);
-    MKF_CUDA_TRY(cudaGetLastError());
-    scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(blocksums, nblk, offsets, n_bins);
-    MKF_CUDA_TRY(cudaGetLastError());
-    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n_bins, blocksums, offsets);
-    MKF_CUDA_TRY(cudaGetLastError());
-    if (n_hits > 0) {
-        unsigned long long disk_mask = 0;
-        for (int l = 0; l < ctx->geom.n_layers; ++l)
-            if (ctx->geom.L[l].kind == 1) disk_mask |= 1ull << l;
-        scatter_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(xyz, xyz + n_hits, xyz + 2 * (int64_t)n_hits, key, layer8,
-                                                           n_hits, disk_mask, offsets, counts, rec4, inv);
-        MKF_CUDA_TRY(cudaGetLastError());
-        bin_sort_kernel<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(offsets, n_bins, rec4, inv);
-        MKF_CUDA_TRY(cudaGetLastError());
-    }
-    return MKF_OK;
+    return run_binning(ctx, xyz, layer, event_offsets, n_events, n_hits, n_bins, counts, blocksums, key, layer8, zhit,
+                       offsets, rec4, inv);
 }

@@ -17,9 +17,19 @@ def _layer_bases(layers):
     return np.array(out), base
 
 
-@pytest.mark.parametrize("cfg,events,tracks", [("find20", 3, 500), ("dense45", 2, 800)])
-def test_binning_is_a_permutation_into_the_right_bins(cfg, events, tracks):
+@pytest.mark.parametrize("cfg,events,tracks,grid", [
+    ("find20", 3, 500, None),
+    ("dense45", 2, 800, None),
+    # more than 1024 scan tiles of 4096 bins: the two-kernel scan
+    ("dense45", 12, 50, None),
+    # two bins per layer: a block's 256 bins hold more hits than its shared buffer,
+    # so the in-bin ordering runs in global memory
+    ("find20", 3, 300, (2, 1)),
+])
+def test_binning_is_a_permutation_into_the_right_bins(cfg, events, tracks, grid):
     b = make_batch(cfg, list(range(events)), n_tracks=tracks)
+    if grid is not None:
+        b.layers = [dict(d, n_phi=grid[0], n_zr=grid[1]) for d in b.layers]
     ctx = make_ctx(b)
     d = upload(b)
     bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
