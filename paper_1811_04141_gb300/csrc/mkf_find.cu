@@ -149,20 +149,25 @@ __device__ __forceinline__ int next_layer(const Geom &G, unsigned long long mask
         const float inf = __int_as_float(0x7f800000);
         float sc = inf, sd = inf;
         int lc = -1, ld = -1;
-        if (ncyl >= 0) {
-            lc = G.cyl[ncyl];
-            if (!path_to_layer(G.L[lc], G.kb, p, lo, sphi, cphi, cot, sc)) {
-                ncyl = -1;
-                lc = -1;
-                sc = inf;
-            }
-        }
         if (ndsk >= 0) {
             ld = G.dsk[ndsk];
-            if (!path_to_layer(G.L[ld], G.kb, p, lo, sphi, cphi, cot, sd)) {
+            if (!path_disk(p[2], lo, cot, h, G.L[ld].rz, sd)) {
                 ndsk = -1;
                 ld = -1;
                 sd = inf;
+            }
+        }
+        if (ncyl >= 0) {
+            lc = G.cyl[ncyl];
+            // the transverse arc to radius R is at least R - r: a disk reached
+            // well before that comes first, and the cylinder waits
+            const float R = G.L[lc].rz;
+            if (sd < (R - rcur) * 0.99999f) {
+                lc = -2;
+            } else if (!path_cyl(p[0], p[1], lo, sphi, cphi, h, R, sc)) {
+                ncyl = -1;
+                lc = -1;
+                sc = inf;
             }
         }
         if (lc < 0 && ld < 0) return -1;

@@ -217,17 +217,22 @@ __device__ __forceinline__ bool path_cyl(float x, float y, const Lo &lo, float s
     return true;
 }
 
+// Path to the disk plane z = Z (less than half a turn ahead), or false.
+__device__ __forceinline__ bool path_disk(float z, const Lo &lo, float cot, float h, float Z, float &s) {
+    if (cot == 0.f) return false;
+    const float sd = ((Z - z) - lo.z) / cot;
+    if (!(sd > 0.f)) return false;
+    if (h != 0.f && fabsf(h) * sd >= kPi) return false;
+    s = sd;
+    return true;
+}
+
 // Path from state p to the surface of layer l (no extent check).
 __device__ __forceinline__ bool path_to_layer(const LayerDesc& Ld, float kb, const float p[6], const Lo& lo, float sphi,
                                               float cphi, float cot, float& s) {
     float h = -p[3] * kb;
     if (Ld.kind == 0) return path_cyl(p[0], p[1], lo, sphi, cphi, h, Ld.rz, s);
-    if (cot == 0.f) return false;
-    float sd = ((Ld.rz - p[2]) - lo.z) / cot;
-    if (!(sd > 0.f)) return false;
-    if (h != 0.f && fabsf(h) * sd >= kPi) return false;
-    s = sd;
-    return true;
+    return path_disk(p[2], lo, cot, h, Ld.rz, s);
 }
 
 // Position after a move by s (chord form), without touching the state.
