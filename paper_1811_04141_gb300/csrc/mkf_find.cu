@@ -625,6 +625,11 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
         int sh0 = -1, sh1 = -1, sh2 = -1;
 
         int step = 0;
+        // the child this lane becomes (its parent's moved state is in p, lo, C,
+        // chi2, bk, I): made at the top of the next step
+        bool pend = false;
+        uint32_t pcode = 0;
+        float pu = 0.f, pv = 0.f, px2 = 0.f;
         if (!kLearned && A.step1) {
             // ---- the candidates after the first step, from seed_kernel: rank r
             // takes child r; the seed-level record goes to rank 0
@@ -674,7 +679,12 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                         u = L[((int64_t)rank * kListFields + LF_U) * n + seed];
                         v = L[((int64_t)rank * kListFields + LF_V) * n + seed];
                     }
-                    make_child(code, I, u, v, x2, A.max_consec, p, lo, C, chi2, bk, c_up);
+                    // made at the top of the first step, like every other child
+                    pend = true;
+                    pcode = code;
+                    pu = u;
+                    pv = v;
+                    px2 = x2;
                     hist[lane] = code;  // parent rank 0
                     live = true;
                 }
@@ -714,6 +724,15 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
         }
 
         while (true) {
+            // ---- 0. the pending child: Kalman update with its hit, or the miss
+            if (pend) {
+                make_child(pcode, I, pu, pv, px2, A.max_consec, p, lo, C, chi2, bk, c_up);
+                pend = false;
+            }
+            if (step >= A.max_steps) {
+                if (lane == 0) record_fault(A.fault, kFaultHistOverflow, grp);
+                break;
+            }
             const bool active = live && !bk.done;
             if (!__any_sync(kFull, active)) break;  // every candidate of the warp has finished
             // ---- 1. expansion: next layer, propagation, window search
@@ -803,7 +822,8 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             }
 
             // ---- 3. each lane becomes one child: its parent's propagated state,
-            // and the parent's S^-1 and H C, by shuffles
+            // and the parent's S^-1 and H C, by shuffles; the update follows at
+            // the top of the next step
             const int prank = mine ? 15 - static_cast<int>((mine >> 28) & 15ull) : rank;
             const int src = lane_used ? base + prank : lane;
             uint32_t bw = pack_book(bk);
@@ -839,14 +859,14 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                             x2 = lchi[j * 32 + src];
                             break;
                         }
-                make_child(code, I, u, v, x2, A.max_consec, p, lo, C, chi2, bk, c_up);
+                pend = true;
+                pcode = code;
+                pu = u;
+                pv = v;
+                px2 = x2;
                 hist[step * 32 + lane] = (static_cast<uint32_t>(prank) << 28) | code;
             }
             ++step;
-            if (step >= A.max_steps) {
-                if (lane == 0) record_fault(A.fault, kFaultHistOverflow, grp);
-                break;
-            }
             __syncwarp();
         }
         __syncwarp();
