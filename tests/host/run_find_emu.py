@@ -1,0 +1,39 @@
+"""Run the finder's device code under host warp emulation on one synthetic
+batch and save the outputs (a separate process: a warp divergence ends it)."""
+import ctypes as C
+import sys
+
+import numpy as np
+
+
+def main(so, cfg, event, n_tracks, n_noise, n_best, step1, out_path):
+    sys.path.insert(0, sys.argv[-1])
+    from paper_1811_04141_gb300 import _native as NN
+    from synth import make_batch
+    b = make_batch(cfg, [event], n_tracks=n_tracks, n_noise=n_noise)
+    lib = C.CDLL(so)
+    lay = b.layers
+    arr = (NN.MkfLayer * len(lay))()
+    for i, d in enumerate(lay):
+        arr[i] = NN.MkfLayer(int(d["kind"]), float(d["r_or_z"]), float(d["lo"]), float(d["hi"]), float(d["sigma_u"]),
+                             float(d["sigma_v"]), int(d["n_phi"]), int(d["n_zr"]))
+    n, mo = b.n_seeds, len(lay) + 3
+    out = dict(par=np.zeros((6, n), np.float32), cov=np.zeros((21, n), np.float32), chi2=np.zeros(n, np.float32),
+               n_hits=np.zeros(n, np.int32), hits=np.full((mo, n), -7, np.int32), status=np.zeros(n, np.uint32),
+               counters=np.zeros((3, n), np.int32), fault=np.zeros(2, np.int32))
+    X, Y, Z = [np.ascontiguousarray(b.xyz[i], dtype=np.float32) for i in range(3)]
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    keep = [i32(b.layer), i32(b.event_offsets), i32(b.seed_hits), i32(b.seed_event)]
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    rc = lib.emu_find(arr, len(lay), C.c_float(b.bz), p(X), p(Y), p(Z), p(keep[0]), b.n_hits, p(keep[1]),
+                      len(b.event_offsets) - 1, p(keep[2]), p(keep[3]), n, n_best, C.c_float(30.0), 3, mo, step1,
+                      p(out["par"]), p(out["cov"]), p(out["chi2"]), p(out["n_hits"]), p(out["hits"]), p(out["status"]),
+                      p(out["counters"]), p(out["fault"]))
+    if rc != 0:
+        raise SystemExit(f"emu_find failed: {rc}")
+    np.savez(out_path, **out)
+
+
+if __name__ == "__main__":
+    a = sys.argv[1:]
+    main(a[0], a[1], int(a[2]), int(a[3]), None if a[4] == "none" else int(a[4]), int(a[5]), int(a[6]), a[7])

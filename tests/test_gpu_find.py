@@ -10,15 +10,9 @@ import torch
 
 import oracle as O
 from synth import make_batch
-from tests.gpu_helpers import chi2_errors, chi2_ok, make_ctx, par_errors, to_np, upload
+from tests.gpu_helpers import TIE_CUT, TIE_GEO, TIE_SCORE, chi2_errors, chi2_ok, compare, make_ctx, par_errors, to_np, upload
 
 pytestmark = pytest.mark.gpu
-
-# near-tie thresholds on the oracle's margins (see oracle.find)
-TIE_SCORE = 5e-3   # score gap / max(1, chi2) at a keep/drop or final-order decision
-TIE_CUT = 2e-3     # |chi2 - cut| / cut of a tested hit
-TIE_GEO = 1e-4     # relative gap of a layer-order or extent decision
-
 
 def run_gpu(b, n_best, plans=None, edges=None, max_out=None, block_threads=0):
     ctx = make_ctx(b, plans, edges)
@@ -34,39 +28,6 @@ def run_oracle(b, n_best, seed_list=None, geo=None, max_out=None):
     geo = geo or O.geometry_for(b)
     return O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                   n_best=n_best, seed_list=seed_list, max_out=max_out or len(b.layers) + 3)
-
-
-def compare(out, ref, sel=None, min_same=0.999):
-    if sel is None:
-        sel = np.arange(ref["hits"].shape[1])
-    gh = out["hits"][:, sel]
-    same = (gh == ref["hits"]).all(axis=0)
-    diff = np.nonzero(~same)[0]
-    m = ref["margins"]
-    for k in diff:
-        near = m[0, k] < TIE_SCORE or m[1, k] < TIE_CUT or m[2, k] < TIE_GEO
-        assert near, (int(sel[k]), m[:, k], gh[:, k], ref["hits"][:, k])
-    n_allowed = max(1, int(np.floor((1 - min_same) * sel.size + 1e-9)))
-    assert diff.size <= n_allowed, (diff.size, sel.size)
-    ok = same & (ref["status"] & O.ST_BADSEED == 0)
-    assert (out["n_hits"][sel][ok] == ref["n_hits"][ok]).all()
-    assert par_errors(out["par"][:, sel][:, ok], ref["par"][:, ok], ref["cov"][:, ok]).max() <= 1.0
-    ndf = 2 * ref["n_hits"][ok] - 5
-    assert chi2_ok(out["chi2"][sel][ok], ref["chi2"][ok], ndf)
-    # the work counters are unique where no ranking decision was a near-tie; a
-    # near-tie at the keep/drop boundary can swap a non-final candidate (and so
-    # the counts) without changing the best track
-    strict = ok & (m[0] >= TIE_SCORE)
-    assert (out["counters"][0, sel][strict] == ref["counters"][0, strict]).all()
-    assert (out["counters"][2, sel][strict] == ref["counters"][2, strict]).all()
-    for i in (0, 2):
-        assert abs(int(out["counters"][i, sel][ok].sum()) - int(ref["counters"][i, ok].sum())) <= \
-            0.005 * ref["counters"][i, ok].sum() + 2
-    # hits inside the window rectangle: FP32 and FP64 may disagree at its edge
-    assert np.abs(out["counters"][1, sel][strict] - ref["counters"][1, strict]).max(initial=0) <= 2
-    st_mask = O.ST_BADSEED | O.ST_MISSSTOP | O.ST_TRUNC
-    assert ((out["status"][sel][ok] & st_mask) == (ref["status"][ok] & st_mask)).all()
-    return same.mean()
 
 
 @pytest.mark.parametrize("n_best", [1, 10])
