@@ -34,43 +34,69 @@ __device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) 
     if (atomicCAS(&f->code, 0, code) == 0) f->where = where;
 }
 
-__global__ void __launch_bounds__(256) bin_keys_kernel(const __grid_constant__ BinArgs A) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n_hits) return;
-    // event of hit i: first e with event_offsets[e + 1] > i
+// Key computation: several hits per thread, strided by the block size so that
+// every load stays coalesced, their loads issued before the dependent work, and
+// one event search per thread.  (The scatter and the in-bin ordering keep one
+// item per thread: their per-item work has data-dependent loops, which would run
+// one after another inside a thread; measured slower.)
+constexpr int kBinItems = 4;
+constexpr int kBinThreads = 256;
+
+__global__ void __launch_bounds__(kBinThreads) bin_keys_kernel(const __grid_constant__ BinArgs A) {
+    const int base = blockIdx.x * kBinThreads * kBinItems + threadIdx.x;
+    if (base >= A.n_hits) return;
+    float x[kBinItems], y[kBinItems], z[kBinItems];
+    int l[kBinItems];
+#pragma unroll
+    for (int j = 0; j < kBinItems; ++j) {
+        const int i = base + j * kBinThreads;
+        if (i < A.n_hits) {
+            x[j] = A.X[i];
+            y[j] = A.Y[i];
+            z[j] = A.Z[i];
+            l[j] = A.layer[i];
+        }
+    }
+    // event of the first hit: first e with event_offsets[e + 1] > base; the
+    // later hits of this thread walk forward from it
     int lo = 0, hi = A.n_events;
     while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (A.event_offsets[mid + 1] <= i) lo = mid + 1;
+        const int mid = (lo + hi) >> 1;
+        if (A.event_offsets[mid + 1] <= base) lo = mid + 1;
         else hi = mid;
     }
-    const int ev = lo;
-    const int l = A.layer[i];
-    if (ev >= A.n_events || i < A.event_offsets[0]) {
-        record_fault(A.fault, kFaultBadEvent, i);
-        A.key[i] = -1;
-        A.layer8[i] = 255;
-        return;
+    int ev = lo;
+    const int first_hit = A.event_offsets[0];
+#pragma unroll
+    for (int j = 0; j < kBinItems; ++j) {
+        const int i = base + j * kBinThreads;
+        if (i >= A.n_hits) break;
+        while (ev < A.n_events && A.event_offsets[ev + 1] <= i) ++ev;
+        if (ev >= A.n_events || i < first_hit) {
+            record_fault(A.fault, kFaultBadEvent, i);
+            A.key[i] = -1;
+            A.layer8[i] = 255;
+            continue;
+        }
+        if (l[j] < 0 || l[j] >= A.G.n_layers) {
+            record_fault(A.fault, kFaultBadLayer, i);
+            A.key[i] = -1;
+            A.layer8[i] = 255;
+            continue;
+        }
+        const LayerDesc &Ld = A.G.L[l[j]];
+        A.zhit[i] = z[j];
+        const float phi = atan2f(y[j], x[j]);
+        const float zr = Ld.kind == 0 ? z[j] : sqrtf(fmaf(x[j], x[j], y[j] * y[j]));
+        int pb = static_cast<int>(floorf((phi + kPi) * Ld.phi_scale));
+        pb = min(max(pb, 0), Ld.nphi - 1);
+        int zb = static_cast<int>(floorf((zr - Ld.lo) * Ld.zr_scale));
+        zb = min(max(zb, 0), Ld.nzr - 1);
+        const int k = ev * A.G.bins_per_event + Ld.bin_base + pb * Ld.nzr + zb;
+        A.key[i] = k;
+        A.layer8[i] = static_cast<uint8_t>(l[j]);
+        atomicAdd(&A.counts[k], 1);
     }
-    if (l < 0 || l >= A.G.n_layers) {
-        record_fault(A.fault, kFaultBadLayer, i);
-        A.key[i] = -1;
-        A.layer8[i] = 255;
-        return;
-    }
-    const LayerDesc &Ld = A.G.L[l];
-    const float x = A.X[i], y = A.Y[i], z = A.Z[i];
-    A.zhit[i] = z;
-    const float phi = atan2f(y, x);
-    const float zr = Ld.kind == 0 ? z : sqrtf(fmaf(x, x, y * y));
-    int pb = static_cast<int>(floorf((phi + kPi) * Ld.phi_scale));
-    pb = min(max(pb, 0), Ld.nphi - 1);
-    int zb = static_cast<int>(floorf((zr - Ld.lo) * Ld.zr_scale));
-    zb = min(max(zb, 0), Ld.nzr - 1);
-    const int k = ev * A.G.bins_per_event + Ld.bin_base + pb * Ld.nzr + zb;
-    A.key[i] = k;
-    A.layer8[i] = static_cast<uint8_t>(l);
-    atomicAdd(&A.counts[k], 1);
 }
 
 // Block-wide exclusive scan of kScanTile elements; returns the block total.
@@ -152,10 +178,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const int32_t 
     }
 }
 
-__global__ void __launch_bounds__(256) scatter_kernel(const float *X, const float *Y, const float *Z, const int32_t *key,
-                                                      const uint8_t *layer8, int32_t n_hits,
-                                                      unsigned long long disk_mask, const int32_t *offsets,
-                                                      int32_t *counts, float4 *rec, int32_t *inv) {
+__global__ void __launch_bounds__(kBinThreads) scatter_kernel(const float *X, const float *Y, const float *Z,
+                                                              const int32_t *key, const uint8_t *layer8, int32_t n_hits,
+                                                              unsigned long long disk_mask, const int32_t *offsets,
+                                                              int32_t *counts, float4 *rec, int32_t *inv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_hits) return;
     const int k = key[i];
@@ -163,16 +189,19 @@ __global__ void __launch_bounds__(256) scatter_kernel(const float *X, const floa
         inv[i] = -1;
         return;
     }
-    const int pos = offsets[k] + atomicSub(&counts[k], 1) - 1;
+    // slots are handed out from the front of the bin in arrival order, which
+    // follows the original index for most bins (warps run roughly in order), so
+    // the in-bin ordering pass usually finds a bin already in order
+    const int pos = offsets[k + 1] - atomicSub(&counts[k], 1);
     const float x = X[i], y = Y[i], z = Z[i];
     const float zr = ((disk_mask >> layer8[i]) & 1ull) == 0 ? z : sqrtf(fmaf(x, x, y * y));
     rec[pos] = make_float4(x, y, zr, __int_as_float(i));
     inv[i] = pos;
 }
 
-// Order the hits of each bin by original index (the scatter's atomics leave an
-// arbitrary order), one thread per bin, insertion sort in place; bins with fewer
-// than two hits are already in order and mapped by the scatter.  (Staging a
+// Order the hits of each bin by original index (the scatter's atomics leave
+// arrival order), one thread per bin, insertion sort in place; bins with fewer
+// than two hits, or already in order, are left as the scatter mapped them.  (Staging a
 // block's bins in shared memory, or a sorting network in registers, measured
 // slower: most bins hold zero or one hit.)
 constexpr int kSortBins = 256;
@@ -183,6 +212,9 @@ __global__ void __launch_bounds__(kSortBins) bin_sort_kernel(const int32_t *offs
     if (b >= n_bins) return;
     const int s = offsets[b], e = offsets[b + 1];
     if (e - s < 2) return;
+    bool sorted = true;
+    for (int i = s + 1; i < e && sorted; ++i) sorted = __float_as_int(rec[i - 1].w) < __float_as_int(rec[i].w);
+    if (sorted) return;
     for (int i = s + 1; i < e; ++i) {
         const float4 v = rec[i];
         const int key = __float_as_int(v.w);
@@ -256,7 +288,7 @@ mkf_status run_binning(mkf_ctx *ctx, const float *xyz, const int32_t *layer, con
         A.zhit = zhit;
         A.counts = counts;
         A.fault = ctx->fault;
-        bin_keys_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(A);
+        bin_keys_kernel<<<(n_hits + kBinThreads * kBinItems - 1) / (kBinThreads * kBinItems), kBinThreads, 0, s>>>(A);
         MKF_CUDA_TRY(cudaGetLastError());
     }
     const int64_t nblk = (n_bins + kScanTile - 1) / kScanTile;
@@ -270,7 +302,7 @@ mkf_status run_binning(mkf_ctx *ctx, const float *xyz, const int32_t *layer, con
         unsigned long long disk_mask = 0;
         for (int l = 0; l < ctx->geom.n_layers; ++l)
             if (ctx->geom.L[l].kind == 1) disk_mask |= 1ull << l;
-        scatter_kernel<<<(n_hits + 255) / 256, 256, 0, s>>>(xyz, xyz + n_hits, xyz + 2 * (int64_t)n_hits, key, layer8,
+        scatter_kernel<<<(n_hits + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(xyz, xyz + n_hits, xyz + 2 * (int64_t)n_hits, key, layer8,
                                                            n_hits, disk_mask, offsets, counts, rec, inv);
         MKF_CUDA_TRY(cudaGetLastError());
         bin_sort_kernel<<<(unsigned)((n_bins + kSortBins - 1) / kSortBins), kSortBins, 0, s>>>(offsets, n_bins, rec,
