@@ -132,7 +132,9 @@ mkf_status mkf_geometry_load(mkf_ctx *ctx, const mkf_layer *layers, int32_t n_la
  * *inout: NULL to allocate a new bin store, or a store from an earlier call to
  * refill (its device memory is reused, grown only when too small).  Hits with
  * an invalid layer id are dropped and recorded as a device fault (mkf_sync).
- * The order of hits within one bin is ascending original index.
+ * The store keeps the hits of a bin in the order the scatter placed them
+ * (nothing the library computes depends on that order); mkf_hitbins_export
+ * first puts every bin into ascending original index.
  * Errors: MKF_ERR_ARG, MKF_ERR_GEOMETRY (no geometry), MKF_ERR_CAPACITY
  * (n_hits > MKF_MAX_HITS), MKF_ERR_CUDA. */
 mkf_status mkf_hits_bin(mkf_ctx *ctx, const float *xyz, const int32_t *layer, const int32_t *event_offsets,
@@ -146,7 +148,10 @@ void mkf_hitbins_free(mkf_hitbins *bins);
 mkf_status mkf_hitbins_info(const mkf_hitbins *bins, int32_t *n_hits, int32_t *n_events, int64_t *n_bins);
 
 /* Copy a bin store into caller-owned device buffers (asynchronous, on the
- * context's stream; any pointer may be NULL to skip that array):
+ * context's stream; any pointer may be NULL to skip that array).  When rec or
+ * inv is requested, the store's bins are first put into ascending original
+ * index in place (stream-ordered; a call on another stream that uses the store
+ * at the same time must be ordered with this one):
  *  rec [n_hits][4] float: binned hits (x, y, z on cylinders or r on disks, the
  *      original index as int32 bits), grouped by bin, ascending original index
  *      within a bin;

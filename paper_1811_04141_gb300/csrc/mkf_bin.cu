@@ -267,11 +267,12 @@ mkf_status grow(mkf_hitbins *b, int64_t n_hits, int64_t n_bins) {
 }
 
 // The binning pipeline on given buffers: keys and histogram, exclusive scan,
-// scatter, in-bin ordering.  counts [n_bins] must be zero on entry; tilesums
+// scatter, and (order_bins) the in-bin ordering by original index.  counts [n_bins] must be zero on entry; tilesums
 // [ceil(n_bins / kScanTile)] is scan scratch.
 mkf_status run_binning(mkf_ctx *ctx, const float *xyz, const int32_t *layer, const int32_t *event_offsets,
                        int32_t n_events, int32_t n_hits, int64_t n_bins, int32_t *counts, int32_t *tilesums,
-                       int32_t *key, uint8_t *layer8, float *zhit, int32_t *offsets, float4 *rec, int32_t *inv) {
+                       int32_t *key, uint8_t *layer8, float *zhit, int32_t *offsets, float4 *rec, int32_t *inv,
+                       bool order_bins) {
     cudaStream_t s = ctx->stream;
     if (n_hits > 0) {
         BinArgs A;
@@ -305,9 +306,11 @@ mkf_status run_binning(mkf_ctx *ctx, const float *xyz, const int32_t *layer, con
         scatter_kernel<<<(n_hits + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(xyz, xyz + n_hits, xyz + 2 * (int64_t)n_hits, key, layer8,
                                                            n_hits, disk_mask, offsets, counts, rec, inv);
         MKF_CUDA_TRY(cudaGetLastError());
-        bin_sort_kernel<<<(unsigned)((n_bins + kSortBins - 1) / kSortBins), kSortBins, 0, s>>>(offsets, n_bins, rec,
-                                                                                               inv);
-        MKF_CUDA_TRY(cudaGetLastError());
+        if (order_bins) {
+            bin_sort_kernel<<<(unsigned)((n_bins + kSortBins - 1) / kSortBins), kSortBins, 0, s>>>(offsets, n_bins, rec,
+                                                                                                   inv);
+            MKF_CUDA_TRY(cudaGetLastError());
+        }
     }
     return MKF_OK;
 }
@@ -343,6 +346,15 @@ extern "C" mkf_status mkf_hitbins_export(mkf_ctx *ctx, const mkf_hitbins *b, flo
     DeviceGuard g(ctx->device);
     if (!g.ok) return MKF_ERR_CUDA;
     cudaStream_t s = ctx->stream;
+    if ((rec || inv) && !b->ordered) {
+        // put each bin into ascending original index, in place (the store's
+        // contents stay the same set; later calls see the ordered layout)
+        mkf_hitbins *m = const_cast<mkf_hitbins *>(b);
+        bin_sort_kernel<<<(unsigned)((b->n_bins + kSortBins - 1) / kSortBins), kSortBins, 0, s>>>(m->offsets, m->n_bins,
+                                                                                                  m->rec, m->inv);
+        MKF_CUDA_TRY(cudaGetLastError());
+        m->ordered = 1;
+    }
     if (rec && b->n_hits)
         MKF_CUDA_TRY(cudaMemcpyAsync(rec, b->rec, sizeof(float4) * b->n_hits, cudaMemcpyDeviceToDevice, s));
     if (inv && b->n_hits)
@@ -384,9 +396,12 @@ extern "C" mkf_status mkf_hits_bin(mkf_ctx *ctx, const float *xyz, const int32_t
     b->n_bins = n_bins;
     cudaStream_t s = ctx->stream;
     MKF_CUDA_TRY(cudaMemsetAsync(b->counts, 0, n_bins * sizeof(int32_t), s));
+    // the finder does not depend on the order of hits within a bin, so the store
+    // keeps arrival order; mkf_hitbins_export orders it when asked for the layout
     st = run_binning(ctx, xyz, layer, event_offsets, n_events, n_hits, n_bins, b->counts, b->blocksums, b->key,
-                     b->layer, b->zhit, b->offsets, b->rec, b->inv);
+                     b->layer, b->zhit, b->offsets, b->rec, b->inv, false);
     if (st != MKF_OK) return st;
+    b->ordered = n_hits == 0;
     *inout = b;
     return MKF_OK;
 }
@@ -456,5 +471,5 @@ extern "C" mkf_status mkf_hits_bin_static(mkf_ctx *ctx, const float *xyz, const 
     // the histogram starts at zero on every call (the array keeps the last call's contents)
     MKF_CUDA_TRY(cudaMemsetAsync(counts, 0, n_bins * sizeof(int32_t), s));
     return run_binning(ctx, xyz, layer, event_offsets, n_events, n_hits, n_bins, counts, blocksums, key, layer8, zhit,
-                       offsets, rec4, inv);
+                       offsets, rec4, inv, true);
 }

@@ -55,6 +55,7 @@ struct mkf_hitbins {
     int32_t *counts;    // [n_bins] scratch histogram
     int32_t *blocksums; // scan scratch
     int64_t cap_blocks;
+    int ordered;        // hits within each bin in ascending original index
 };
 
 #define MKF_CUDA_TRY(expr)                                  \
