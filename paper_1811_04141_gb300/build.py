@@ -15,11 +15,13 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmkf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-# The finder divides and takes square roots with the approximate forms (division
-# within 2 ulp, no IEEE slow paths): its code shrinks and it runs 7-11 % faster,
-# while its differences from the FP64 oracle keep the same distribution (they are
-# set by the FP32 state and residual rounding, not by these operations).
-FILE_FLAGS = {"mkf_find.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+# The finder and the fit divide and take square roots with the approximate forms
+# (division within 2 ulp, no IEEE slow paths): their code shrinks and they run
+# 7-11 % faster, while their differences from the FP64 oracle keep the same
+# distribution (they are set by the FP32 state and residual rounding, not by
+# these operations).
+_APPROX = ["-prec-div=false", "-prec-sqrt=false"]
+FILE_FLAGS = {"mkf_find.cu": _APPROX, "mkf_fit.cu": _APPROX}
 
 
 def _nvcc():

@@ -26,7 +26,7 @@ __device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) 
     if (atomicCAS(&f->code, 0, code) == 0) f->where = where;
 }
 
-__global__ void __launch_bounds__(128) fit_kernel(const __grid_constant__ FitArgs A) {
+__global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ FitArgs A) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= A.n) return;
     const Geom &G = A.G;
