@@ -370,6 +370,88 @@ def fit_leg(dev, n_tracks: int = 1_000_000, reps: int = 20):
                          "frac": fl / (ms * 1e-3) / 1e12 / peak, "kernel": "fit_kernel"}}
 
 
+def _carve(arena, specs):
+    """Typed views into one byte arena: specs = [(name, dtype, shape)], each view
+    256-byte aligned.  Returns (views, bytes used)."""
+    import torch
+    views, off = {}, 0
+    for name, dt, shape in specs:
+        n = int(np.prod(shape)) * torch.empty(0, dtype=dt).element_size()
+        views[name] = arena[off:off + n].view(dt).view(*shape)
+        off += (n + 255) // 256 * 256
+    return views, off
+
+
+def e2e_pipelined(ctx, batch, bins, NB, max_out, K, W, units_all, pg, dev):
+    """Host -> device copy of the step's inputs (one pinned arena, one copy),
+    binning + finding, device -> host copy of all its outputs (one arena, one
+    copy); three streams, two device buffer sets, events between the stages.
+    Timed from the first timed step's input copy to its last read-back, on the
+    device; the working set of two steps in flight (~190 MB) exceeds the L2, and
+    every step's inputs arrive fresh from the host."""
+    import torch
+    n, S, E = batch.n_hits, batch.n_seeds, len(batch.event_offsets) - 1
+    in_specs = [("xyz", torch.float32, (3, n)), ("layer", torch.int32, (n,)), ("evo", torch.int32, (E + 1,)),
+                ("sh", torch.int32, (3, S)), ("se", torch.int32, (S,))]
+    out_specs = [("par", torch.float32, (6, S)), ("cov", torch.float32, (21, S)), ("chi2", torch.float32, (S,)),
+                 ("n_hits", torch.int32, (S,)), ("hits", torch.int32, (max_out, S)), ("status", torch.int32, (S,)),
+                 ("counters", torch.int32, (3, S))]
+    size = lambda specs: sum((int(np.prod(sh)) * torch.empty(0, dtype=dt).element_size() + 255) // 256 * 256
+                             for _, dt, sh in specs)
+    in_bytes, out_bytes = size(in_specs), size(out_specs)
+    h_in_arena = torch.empty(in_bytes, dtype=torch.uint8).pin_memory()
+    h_in, _ = _carve(h_in_arena, in_specs)
+    for k, arr in (("xyz", batch.xyz), ("layer", batch.layer), ("evo", batch.event_offsets), ("sh", batch.seed_hits),
+                   ("se", batch.seed_event)):
+        h_in[k].copy_(torch.as_tensor(np.ascontiguousarray(arr)))
+    h_out_arena = torch.empty(out_bytes, dtype=torch.uint8).pin_memory()
+    d_in_arena = [torch.empty(in_bytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+    d_out_arena = [torch.empty(out_bytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+    d_in = [_carve(a, in_specs)[0] for a in d_in_arena]
+    d_out = [_carve(a, out_specs)[0] for a in d_out_arena]
+    s_in, s_comp, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
+    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "comp", "out")}
+    ctx.set_stream(s_comp)
+
+    def step(i):
+        b = i % 2
+        if i >= 2:
+            s_in.wait_event(ev["comp"][b])
+        with torch.cuda.stream(s_in):
+            d_in_arena[b].copy_(h_in_arena, non_blocking=True)
+            ev["in"][b].record(s_in)
+        s_comp.wait_event(ev["in"][b])
+        if i >= 2:
+            s_comp.wait_event(ev["out"][b])
+        with torch.cuda.stream(s_comp):
+            x = d_in[b]
+            ctx.hits_bin(x["xyz"], x["layer"], x["evo"], bins)
+            ctx.find(bins, x["sh"], x["se"], n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC,
+                     max_out=max_out, out=d_out[b])
+            ev["comp"][b].record(s_comp)
+        s_out.wait_event(ev["comp"][b])
+        with torch.cuda.stream(s_out):
+            h_out_arena.copy_(d_out_arena[b], non_blocking=True)
+            ev["out"][b].record(s_out)
+
+    for i in range(W):
+        step(i)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(s_in)
+    for i in range(W, W + K):
+        step(i)
+    t1.record(s_out)
+    torch.cuda.synchronize()
+    # the copied-back tracks are the device's
+    assert torch.equal(h_out_arena, d_out_arena[(W + K - 1) % 2].cpu())
+    ms = allreduce_max(pg, t0.elapsed_time(t1) / K)
+    return {"value": units_all / (ms * 1e-3), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": int(sum(v.numel() * v.element_size() for v in h_in.values())),
+            "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in d_out[0].values())), "copies": "1 H2D + 1 D2H per step on their own streams, "
+            "overlapped with the neighbouring steps' compute (2 device buffer sets)"}
+
+
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
@@ -450,44 +532,14 @@ def run_ours(args, world, rank, local, pg):
                 "kernel": "find_kernel", "kernel_ms": round(find_ms, 4),
                 "flops_per_launch": fl, "peak_basis": f"{peak_mhz:.0f} MHz x SMs x 128 FP32 lanes x 2 (derived)"}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies its
+    # inputs from pinned host memory and reads its tracks back; copies run on
+    # their own streams, overlapped with the previous / next step's compute
+    # (two device buffer sets), as a serving pipeline would run them
     e2e = None
     if not args.no_e2e:
-        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
-        h_xyz, h_layer, h_evo = pin(batch.xyz), pin(batch.layer), pin(batch.event_offsets)
-        h_sh, h_se = pin(batch.seed_hits), pin(batch.seed_event)
-        outs_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items() if v is not None}
-        d_xyz, d_layer, d_evo = torch.empty_like(xyz), torch.empty_like(layer), torch.empty_like(evo)
-        d_sh, d_se = torch.empty_like(sh), torch.empty_like(se)
-        h2d = sum(t.numel() * t.element_size() for t in (h_xyz, h_layer, h_evo, h_sh, h_se))
-        d2h = sum(t.numel() * t.element_size() for t in outs_h.values())
-
-        def e2e_step():
-            d_xyz.copy_(h_xyz, non_blocking=True)
-            d_layer.copy_(h_layer, non_blocking=True)
-            d_evo.copy_(h_evo, non_blocking=True)
-            d_sh.copy_(h_sh, non_blocking=True)
-            d_se.copy_(h_se, non_blocking=True)
-            ctx.hits_bin(d_xyz, d_layer, d_evo, bins)
-            ctx.find(bins, d_sh, d_se, n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out,
-                     out=out)
-            for k, v in outs_h.items():
-                v.copy_(out[k], non_blocking=True)
-
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
-        torch.cuda.synchronize()
-        es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        for i in range(K):
-            flush.fill_(float(i))
-            es[i][0].record(stream)
-            e2e_step()
-            es[i][1].record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = allreduce_max(pg, float(np.mean([a.elapsed_time(b) for a, b in es])))
-        e2e = {"value": units_all / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
-
+        e2e = e2e_pipelined(ctx, batch, bins, NB, max_out, K, max(3, args.warmup), units_all, pg, dev)
+        ctx.set_stream(stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, nseeds, secs = oracle_rate(batch, args.cpu_seconds)
