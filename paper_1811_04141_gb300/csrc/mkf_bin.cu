@@ -14,7 +14,7 @@ namespace {
 using namespace mkf;
 
 constexpr int kScanThreads = 1024;
-constexpr int kScanPerThread = 4;
+constexpr int kScanPerThread = 16;  // a thread's run of 16 counts: four 16-byte loads
 constexpr int kScanTile = kScanThreads * kScanPerThread;
 
 struct BinArgs {
@@ -103,13 +103,27 @@ __global__ void __launch_bounds__(kBinThreads) bin_keys_kernel(const __grid_cons
 __device__ int block_scan_tile(const int32_t *in, int64_t n, int64_t base, int vals[kScanPerThread]) {
     __shared__ int warp_tot[kScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t first = base + (int64_t)tid * kScanPerThread;
+    int v[kScanPerThread];
+    if (first + kScanPerThread <= n && (reinterpret_cast<uintptr_t>(in + first) & 15) == 0) {
+        const int4 *q = reinterpret_cast<const int4 *>(in + first);
+#pragma unroll
+        for (int k = 0; k < kScanPerThread / 4; ++k) {
+            const int4 w = q[k];
+            v[4 * k] = w.x;
+            v[4 * k + 1] = w.y;
+            v[4 * k + 2] = w.z;
+            v[4 * k + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanPerThread; ++k) v[k] = first + k < n ? in[first + k] : 0;
+    }
     int s = 0;
 #pragma unroll
     for (int k = 0; k < kScanPerThread; ++k) {
-        int64_t idx = base + (int64_t)tid * kScanPerThread + k;
-        int v = idx < n ? in[idx] : 0;
         vals[k] = s;
-        s += v;
+        s += v[k];
     }
     int incl = s;
 #pragma unroll
@@ -171,10 +185,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const int32_t 
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     block_scan_tile(counts, n, base, vals);
     const int add = blocksums[blockIdx.x];
+    const int64_t first = base + (int64_t)threadIdx.x * kScanPerThread;
+    if (first + kScanPerThread <= n && (reinterpret_cast<uintptr_t>(offsets + first) & 15) == 0) {
+        int4 *q = reinterpret_cast<int4 *>(offsets + first);
 #pragma unroll
-    for (int k = 0; k < kScanPerThread; ++k) {
-        int64_t idx = base + (int64_t)threadIdx.x * kScanPerThread + k;
-        if (idx < n) offsets[idx] = vals[k] + add;
+        for (int k = 0; k < kScanPerThread / 4; ++k)
+            q[k] = make_int4(vals[4 * k] + add, vals[4 * k + 1] + add, vals[4 * k + 2] + add, vals[4 * k + 3] + add);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanPerThread; ++k)
+            if (first + k < n) offsets[first + k] = vals[k] + add;
     }
 }
 
