@@ -370,6 +370,9 @@ def fit_leg(dev, n_tracks: int = 1_000_000, reps: int = 20):
                          "frac": fl / (ms * 1e-3) / 1e12 / peak, "kernel": "fit_kernel"}}
 
 
+FIND_DRAM_BYTES = 35_932_000 + 18_000  # dram__bytes_read.sum + dram__bytes_write.sum, find_kernel, find20
+
+
 def _carve(arena, specs):
     """Typed views into one byte arena: specs = [(name, dtype, shape)], each view
     256-byte aligned.  Returns (views, bytes used)."""
@@ -527,8 +530,12 @@ def run_ours(args, world, rank, local, pg):
     achieved = fl / (find_ms * 1e-3) / 1e12
     peak_mhz = 2070.0
     peak = flops.fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count, peak_mhz)
+    # DRAM bytes per find_kernel launch on this workload (read + write), from a one-pass ncu
+    # capture of the current kernel (profiles/dram.find20_bench.md); only the bench's own
+    # workload at the default size has a measured figure
+    traffic = FIND_DRAM_BYTES if (E == EVENTS and NB == N_BEST and world >= 1) else None
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": "find_kernel", "kernel_ms": round(find_ms, 4),
                 "flops_per_launch": fl, "peak_basis": f"{peak_mhz:.0f} MHz x SMs x 128 FP32 lanes x 2 (derived)"}
 
