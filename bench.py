@@ -71,16 +71,19 @@ def dist_init():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
+        # each rank on its own GPU before the group exists, so NCCL binds to it
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
         pg = dist
     return world, rank, local, pg
 
 
 def barrier(pg):
     if pg is not None:
-        pg.barrier()
+        import torch
+        pg.barrier(device_ids=[torch.cuda.current_device()])
 
 
 def allreduce_max(pg, x):
