@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
         }
         const int pos = A.inv[hidx[k]];
         hl[k] = A.layer8[hidx[k]];
-        if (pos < 0 || hl[k] >= G.n_layers) {
+        if (pos < 0 || pos >= A.n_hits || hl[k] >= G.n_layers) {
             ok = false;
             continue;
         }
