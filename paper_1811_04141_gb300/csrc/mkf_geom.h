@@ -13,6 +13,12 @@
 
 inline mkf_status mkf_build_geom(const mkf_layer *layers, int32_t n_layers, const mkf_plan *plans, int32_t n_plans,
                                  const float *region_eta_edges, float bz_tesla, mkf::Geom &G) {
+    if (!layers || n_layers < 1) return MKF_ERR_ARG;
+    if (n_layers > MKF_MAX_LAYERS) return MKF_ERR_CAPACITY;
+    if (n_plans < 0) return MKF_ERR_ARG;
+    if (n_plans > MKF_MAX_REGIONS) return MKF_ERR_CAPACITY;
+    if (n_plans > 0 && !plans) return MKF_ERR_ARG;
+    if (n_plans > 1 && !region_eta_edges) return MKF_ERR_ARG;
     if (!std::isfinite(bz_tesla)) return MKF_ERR_GEOMETRY;
     std::memset(&G, 0, sizeof(G));
     G.n_layers = n_layers;
