@@ -883,15 +883,12 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             if (ok) {
                 const int shs[3] = {sh0, sh1, sh2};
                 for (int k = 0; k < 3 && nout < A.max_out; ++k) A.out_hits[(int64_t)(nout++) * n + seed] = shs[k];
-                // walk the history back from the best candidate, then write forwards
-                int r = 0, cnt = 0;
-                for (int st = step - 1; st >= 0; --st) {
-                    const uint32_t rec = hist[st * 32 + base + r];
-                    if ((rec & kHitMask) < kCodeMiss) ++cnt;
-                    r = static_cast<int>(rec >> 28);
-                }
+                // the hits the finder added (the candidate's count beyond its three
+                // seed hits), written from the last backwards while the history is
+                // walked back from the best candidate
+                const int cnt = bk.nh - 3;
                 int pos = nout + cnt - 1;
-                r = 0;
+                int r = 0;
                 for (int st = step - 1; st >= 0; --st) {
                     const uint32_t rec = hist[st * 32 + base + r];
                     const uint32_t code = rec & kHitMask;
