@@ -258,12 +258,29 @@ def learned_leg(dev, reps: int = 30):
     ms_plain = timed(None)
     ms_pruned = timed(tau) if tau is not None else None
     ep, fp, cp = run(de)
+    # best-hit finding (N = 1) on the same held-out events: what branching buys here
+    out1 = ctx.find(de["bins"], de["sh"], de["se"], n_best=1, max_out=max_out)
+    for _ in range(3):
+        ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
+        ctx.find(de["bins"], de["sh"], de["se"], n_best=1, max_out=max_out, out=out1)
+    torch.cuda.synchronize()
+    a1, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a1.record()
+    for _ in range(reps):
+        ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
+        ctx.find(de["bins"], de["sh"], de["se"], n_best=1, max_out=max_out, out=out1)
+    b1.record()
+    torch.cuda.synchronize()
+    ms_best = a1.elapsed_time(b1) / reps
+    e1, f1 = L.efficiency(out1["hits"], de["hp"], de["sp"])
     res = {"workload": "dense45: 17 cylinders + 2x14 disks, 6000 tracks (pT^-3 from 0.5 GeV) + 200k noise hits "
                        "per event; trained on 10 events, evaluated on 10 held-out events; N=10",
            "metric": "events/s (hit binning + finding)", "train_pairs": int(feat.shape[0]),
            "train_loss_first_last": [st["losses"][0], st["losses"][-1]] if st["losses"] else None,
            "plain": {"events_per_s": 10 / (ms_plain * 1e-3), "ms": ms_plain, "efficiency": ep, "fake_rate": fp,
-                     "cand_layers": int(cp[0]), "updates": int(cp[2])}}
+                     "cand_layers": int(cp[0]), "updates": int(cp[2])},
+           "best_hit_n1": {"events_per_s": 10 / (ms_best * 1e-3), "ms": ms_best, "efficiency": e1, "fake_rate": f1,
+                           "cand_layers": int(out1["counters"][0].sum().item())}}
     if tau is not None:
         el, fl, cl = run(de, tau)
         res["pruned"] = {"tau": tau, "events_per_s": 10 / (ms_pruned * 1e-3), "ms": ms_pruned, "efficiency": el,
