@@ -155,3 +155,43 @@ def test_first_step_paths_agree(cfg, n_best):
     assert np.allclose(a["par"][:, ok], w["par"][:, ok], rtol=1e-5, atol=1e-6)
     ndf = 2 * a["n_hits"][ok] - 5
     assert chi2_ok(a["chi2"][ok], w["chi2"][ok].astype(np.float64), ndf)
+
+
+@pytest.mark.parametrize("n_best", [1, 4])
+def test_find_zero_field(n_best):
+    """B = 0: straight tracks, q/pT unobservable (its prior only)."""
+    b = make_batch("fit10_b0", [27], n_tracks=300)
+    compare(run_gpu(b, n_best), run_oracle(b, n_best))
+
+
+def test_find_batch_with_empty_event():
+    """An event with no hits and no seeds between two others: its bins stay empty
+    and the other events' tracks are unchanged."""
+    b = make_batch("find20", [70, 71, 72], n_tracks=[150, 0, 120], n_noise=[2000, 0, 1500])
+    assert b.event_offsets[1] == b.event_offsets[2]
+    ctx = make_ctx(b)
+    d = upload(b)
+    bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
+    out = to_np(ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=10, max_out=len(b.layers) + 3))
+    ctx.sync()
+    compare(out, run_oracle(b, 10))
+    ex = bins.export(ctx)
+    off = ex["offsets"].cpu().numpy()
+    per_event = sum(l["n_phi"] * l["n_zr"] for l in b.layers)
+    assert (off[per_event:2 * per_event + 1] == b.event_offsets[1]).all()
+
+
+@pytest.mark.parametrize("cut,miss", [(10.0, 1), (60.0, 15)])
+def test_find_cut_and_miss_limit(cut, miss):
+    """Other chi2 cuts and consecutive-miss limits than the defaults."""
+    b = make_batch("find20", [73], n_tracks=300)
+    ctx = make_ctx(b)
+    d = upload(b)
+    bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
+    mo = len(b.layers) + 3
+    out = to_np(ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=4, chi2_cut=cut, max_consec_miss=miss,
+                         max_out=mo))
+    ctx.sync()
+    ref = O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+                 n_best=4, chi2_cut=cut, max_consec=miss, max_out=mo)
+    compare(out, ref)
