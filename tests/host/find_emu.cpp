@@ -17,6 +17,7 @@ unsigned char *g_smem;
 extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *X, const float *Y, const float *Z,
                         const int *layer, int n_hits, const int *event_offsets, int n_events, const int *seed_hits,
                         const int *seed_event, int n_seeds, int N, float cut, int max_consec, int max_out, int step1,
+                        const uint16_t *mlp_bf16, float mlp_tau,
                         float *out_par, float *out_cov, float *out_chi2, int *out_nh, int *out_hits,
                         unsigned *out_status, int *counters, int *fault_out) {
     static Geom G;
@@ -80,7 +81,9 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
     A.fault = &fault;
     A.seedbuf = seedbuf.data();
     A.beam = lists.data();
-    A.step1 = step1;
+    A.step1 = mlp_bf16 ? 0 : step1;  // the learned variant takes its first step in the warp
+    A.mlp = mlp_bf16;
+    A.mlp_tau = mlp_tau;
     A.work_counter = &work;
     blockDim.x = 128;
     for (int t = 0; t < n_seeds; ++t) {
@@ -98,7 +101,10 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
         lanes.emplace_back([&, l] {
             threadIdx.x = l;
             blockIdx.x = 0;
-            find_kernel<false>(A);
+            if (mlp_bf16)
+                find_kernel<true>(A);
+            else
+                find_kernel<false>(A);
         });
     for (auto &t : lanes) t.join();
     fault_out[0] = fault.code;

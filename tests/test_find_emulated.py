@@ -54,10 +54,16 @@ def emu_so():
     return so
 
 
-def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1):
-    out = os.path.join(tempfile.mkdtemp(), "out.npz")
+def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1, mlp_bf16=None, tau=0.0):
+    d = tempfile.mkdtemp()
+    out = os.path.join(d, "out.npz")
+    wpath = "none"
+    if mlp_bf16 is not None:
+        wpath = os.path.join(d, "w.npy")
+        np.save(wpath, mlp_bf16)
     r = subprocess.run([sys.executable, os.path.join(HERE, "host", "run_find_emu.py"), so, cfg, str(event),
-                        str(n_tracks), "none" if n_noise is None else str(n_noise), str(n_best), str(step1), out, ROOT],
+                        str(n_tracks), "none" if n_noise is None else str(n_noise), str(n_best), str(step1), out,
+                        wpath, str(tau), ROOT],
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     z = np.load(out)
@@ -87,3 +93,34 @@ def test_emulated_first_step_paths_identical(emu_so):
     for k in ("par", "cov", "chi2", "n_hits", "hits", "status", "counters"):
         assert np.array_equal(a[k].view(np.uint32) if a[k].dtype == np.float32 else a[k],
                               w[k].view(np.uint32) if w[k].dtype == np.float32 else w[k]), k
+
+
+def _bf16_bits(w):
+    """float32 -> bfloat16 bit patterns, round to nearest even (the plain definition)."""
+    u = np.ascontiguousarray(w, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16)
+
+
+@pytest.mark.parametrize("tau", [-0.5, 0.5])
+def test_emulated_learned_pruning_matches_oracle(emu_so, tau):
+    """The finder's learned variant (MLP scores of each candidate's compatible
+    hits, pairs below tau dropped before the selection) on the CPU, against the
+    oracle with the same bfloat16 weights."""
+    from oracle import mlp
+    w = mlp.init_weights(21)
+    bits = _bf16_bits(w)
+    wb = (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    b = make_batch("dense45", [44], n_tracks=100, n_noise=200000)
+    out = run_emu(emu_so, "dense45", 44, 100, 200000, 10, 1, mlp_bf16=bits, tau=tau)
+    geo = O.geometry_for(b)
+    ref = O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+                 n_best=10, mlp_w=wb, mlp_tau=tau, max_out=len(b.layers) + 3)
+    plain = O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+                   n_best=10, max_out=len(b.layers) + 3)
+    # the network does prune here: fewer updates than the plain finder
+    assert ref["counters"][2].sum() < plain["counters"][2].sum()
+    same = (out["hits"] == ref["hits"]).all(axis=0)
+    m = ref["margins"]
+    for k in np.nonzero(~same)[0]:
+        assert m[0, k] < 5e-3 or m[1, k] < 2e-3 or m[2, k] < 1e-4 or m[3, k] < 2e-2, (k, m[:, k])
+    assert same.mean() >= 0.98
