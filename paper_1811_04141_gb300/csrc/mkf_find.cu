@@ -95,12 +95,9 @@ __device__ __forceinline__ uint32_t ord_float(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// Child key: larger = better.  (score desc, parent rank asc, hit index asc,
-// the child without a hit last).
-__device__ __forceinline__ unsigned long long child_key(float score, int prank, uint32_t code) {
-    uint32_t lo = (static_cast<uint32_t>(15 - prank) << 28) | (kHitMask - code);
-    return (static_cast<unsigned long long>(ord_float(score)) << 32) | lo;
-}
+// Selection key of a child: its score as an order-preserving integer, the low
+// 4 bits holding a per-parent tag (larger key = better child).
+__device__ __forceinline__ uint32_t sel_key(float score, uint32_t tag) { return (ord_float(score) & ~15u) | tag; }
 
 // Candidate bookkeeping packed into one word for the lane-to-lane transfer.
 struct Book {
@@ -207,15 +204,6 @@ __device__ __forceinline__ int next_layer(const Geom &G, unsigned long long mask
 // Segmented reductions over the N lanes [base, base + N) of a seed, by
 // shuffles.  (The redux unit with one member mask per segment measured ~20 %
 // slower for the whole finder.)
-__device__ __forceinline__ uint32_t seg_max32(uint32_t v, int rank, int N, int base) {
-#pragma unroll
-    for (int off = 1; off < 16; off <<= 1) {
-        const uint32_t o = __shfl_down_sync(kFull, v, off);
-        if (rank + off < N && o > v) v = o;
-    }
-    return __shfl_sync(kFull, v, base & 31);
-}
-
 __device__ __forceinline__ int seg_sum(int v, int rank, int N) {
 #pragma unroll
     for (int off = 1; off < 16; off <<= 1) {
@@ -343,6 +331,9 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
         pb_lo = static_cast<int>(floorf((phic - dphiw + kPi) * Ld.phi_scale));
         const int pb_hi = static_cast<int>(floorf((phic + dphiw + kPi) * Ld.phi_scale));
         nphib = min(pb_hi - pb_lo + 1, Ld.nphi);
+        // |phic| <= pi and dphiw < pi put pb_lo in [-nphi/2 - 1, nphi]; the clamp
+        // keeps every pb_lo + i below in [-nphi, 2 nphi) whatever the floats
+        pb_lo = min(max(pb_lo, -Ld.nphi), Ld.nphi);
     }
     const float zlo_f = fminf(fmaxf(floorf((zc - wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
     const float zhi_f = fminf(fmaxf(floorf((zc + wz - Ld.lo) * Ld.zr_scale), 0.f), Ld.nzr - 1.f);
@@ -350,8 +341,9 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
     const int ebase = ev * G.bins_per_event + Ld.bin_base;
     int nlist = 0, n_compat = 0;
     for (int i = 0; i < nphib; ++i) {
-        int pb = (pb_lo + i) % Ld.nphi;
+        int pb = pb_lo + i;
         if (pb < 0) pb += Ld.nphi;
+        else if (pb >= Ld.nphi) pb -= Ld.nphi;
         const int bin = ebase + pb * Ld.nzr;
         const int k0 = A.offsets[bin + zb_lo], k1 = A.offsets[bin + zb_hi + 1];
         for (int k = k0; k < k1; ++k) {
@@ -583,15 +575,18 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     const int base = slot * N;
     const bool lane_used = slot < spw;
     const int nwarps = blockDim.x >> 5;
-    const unsigned seg_bits = lane_used ? ((N == 32 ? kFull : ((1u << N) - 1u)) << base) : 0u;
 
-    // shared memory: per-step history, then the per-lane child lists
+    // shared memory: per-step history, then the per-lane child lists, then the
+    // per-lane selection slots (index of the chosen child in its parent's list)
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem) + warp * (A.max_steps * 32);
     float *lchi = reinterpret_cast<float *>(reinterpret_cast<uint32_t *>(smem) + nwarps * A.max_steps * 32) +
                   warp * (N * 32 * 4);
     int *lorig = reinterpret_cast<int *>(lchi) + N * 32;
     float *lu = lchi + 2 * N * 32;
     float *lv = lchi + 3 * N * 32;
+    int *sel = reinterpret_cast<int *>(reinterpret_cast<float *>(reinterpret_cast<uint32_t *>(smem) + nwarps * A.max_steps * 32) +
+                                       nwarps * (N * 32 * 4)) +
+               warp * 32;
 
     const float cut = A.cut;
     if (A.event_times && threadIdx.x == 0) atomicMin(&A.event_times[A.n_events], globaltimer_ns());
@@ -777,54 +772,87 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             const bool searched = X.searched;
             __syncwarp();
 
-            // ---- 2. selection of the N best children of each seed: N rounds of a
-            // segmented max over the lanes' best remaining child.  The score is
-            // compared as an order-preserving 32-bit integer; exact score ties (rare)
-            // are resolved by a second reduction on (parent rank, hit index).
+            // ---- 2. selection of the N best children of each seed: rounds of a
+            // segmented top-2 over the lanes' two best remaining children, each
+            // round taking the seed's next two.  The key is the score as an
+            // order-preserving integer whose low 4 bits are replaced by (15 -
+            // parent rank): keys of different parents differ, the key names its
+            // parent, and scores that agree to 2^-19 relative are ordered by
+            // parent rank.  A lane holds the keys of its four best remaining
+            // children, so a win moves on without waiting on a shared-memory load.
+            // The winner records each child (its step-history word and its index
+            // in the parent's list) for the lane that takes it.
             const float score = cut * static_cast<float>(bk.nh) - chi2;
             const int n_children = live ? (searched ? nlist + 1 : 1) : 0;
-            int head = 0;
-            unsigned long long mine = 0;
+            const uint32_t nohit = searched ? kCodeMiss : kCodePass;
+            bool got = false;
             if (N == 1) {
                 if (n_children > 0) {
-                    mine = head < nlist ? child_key(score + cut - lchi[lane], 0, static_cast<uint32_t>(lorig[lane]))
-                                        : child_key(score, 0, searched ? kCodeMiss : kCodePass);
+                    got = true;
+                    hist[step * 32 + lane] = nlist > 0 ? static_cast<uint32_t>(lorig[lane]) : nohit;
+                    sel[lane] = 0;
                 }
             } else {
-                for (int j = 0; j < N; ++j) {
-                    const bool has = head < n_children;
-                    if (!__any_sync(kFull, has)) break;
-                    uint32_t k32 = 0, lo32 = 0;
-                    if (has) {
-                        const bool is_hit = head < nlist;
-                        const float sc = is_hit ? score + cut - lchi[head * 32 + lane] : score;
-                        const uint32_t code = is_hit ? static_cast<uint32_t>(lorig[head * 32 + lane])
-                                                     : (searched ? kCodeMiss : kCodePass);
-                        k32 = ord_float(sc);
-                        lo32 = (static_cast<uint32_t>(15 - rank) << 28) | (kHitMask - code);
+                const uint32_t tag = 15u - static_cast<uint32_t>(rank);
+                auto key_of = [&](int c) -> uint32_t {
+                    return c < n_children ? sel_key(c < nlist ? score + cut - lchi[c * 32 + lane] : score, tag) : 0u;
+                };
+                auto take = [&](int jj, int c) {
+                    hist[step * 32 + base + jj] =
+                        (static_cast<uint32_t>(rank) << 28) | (c < nlist ? static_cast<uint32_t>(lorig[c * 32 + lane]) : nohit);
+                    sel[base + jj] = c;
+                };
+                int head = 0;
+                uint32_t k1 = key_of(0), k2 = key_of(1), k3 = key_of(2), k4 = key_of(3);
+                for (int j = 0; j < N; j += 2) {
+                    if (!__any_sync(kFull, k1 != 0u)) break;
+                    uint32_t a1 = k1, a2 = k2;
+#pragma unroll
+                    for (int off = 1; off < 16; off <<= 1) {
+                        // merge the pair (b1 >= b2) from lane + off into (a1 >= a2)
+                        const uint32_t b1 = __shfl_down_sync(kFull, a1, off);
+                        const uint32_t b2 = __shfl_down_sync(kFull, a2, off);
+                        if (rank + off < N) {
+                            if (b1 > a1) {
+                                a2 = max(a1, b2);
+                                a1 = b1;
+                            } else {
+                                a2 = max(a2, b1);
+                            }
+                        }
                     }
-                    const uint32_t m32 = seg_max32(k32, rank, N, base);
-                    const bool cand = has && k32 == m32;
-                    // the lanes of my segment holding the maximum score
-                    const unsigned tied = __ballot_sync(kFull, cand) & seg_bits;
-                    uint32_t mlo;
-                    if (__any_sync(kFull, lane_used && __popc(tied) > 1)) {
-                        mlo = seg_max32(cand ? lo32 : 0u, rank, N, base);
-                    } else {
-                        mlo = __shfl_sync(kFull, lo32, tied ? (__ffs(tied) - 1) : lane);
-                    }
-                    if (m32 != 0u && lane_used) {
-                        const int wr = 15 - static_cast<int>(mlo >> 28);
-                        if (wr == rank) ++head;
-                        if (j == rank) mine = (static_cast<unsigned long long>(m32) << 32) | mlo;
+                    const uint32_t m1 = __shfl_sync(kFull, a1, base & 31);
+                    const uint32_t m2 = __shfl_sync(kFull, a2, base & 31);
+                    if (m1 != 0u && lane_used) {
+                        const bool two = m2 != 0u && j + 1 < N;
+                        if (rank == j || (two && rank == j + 1)) got = true;
+                        const bool w1 = (m1 & 15u) == tag, w2 = two && (m2 & 15u) == tag;
+                        if (w1 && w2) {
+                            take(j, head);
+                            take(j + 1, head + 1);
+                            head += 2;
+                            k1 = k3;
+                            k2 = k4;
+                            k3 = key_of(head + 2);
+                            k4 = key_of(head + 3);
+                        } else if (w1 || w2) {
+                            take(w1 ? j : j + 1, head);
+                            ++head;
+                            k1 = k2;
+                            k2 = k3;
+                            k3 = k4;
+                            k4 = key_of(head + 3);
+                        }
                     }
                 }
             }
+            __syncwarp();
 
             // ---- 3. each lane becomes one child: its parent's propagated state,
             // and the parent's S^-1 and H C, by shuffles; the update follows at
             // the top of the next step
-            const int prank = mine ? 15 - static_cast<int>((mine >> 28) & 15ull) : rank;
+            const uint32_t rec = got ? hist[step * 32 + lane] : 0u;
+            const int prank = got ? static_cast<int>(rec >> 28) : rank;
             const int src = lane_used ? base + prank : lane;
             uint32_t bw = pack_book(bk);
             bw = __shfl_sync(kFull, bw, src);
@@ -846,25 +874,22 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             I.Iuv = __shfl_sync(kFull, I.Iuv, src);
             I.Ivv = __shfl_sync(kFull, I.Ivv, src);
             bk = unpack_book(bw);
-            live = lane_used && mine != 0ull;
+            live = got;
             if (live) {
-                const uint32_t code = kHitMask - static_cast<uint32_t>(mine & kHitMask);
                 // the hit's residual and chi2 from the parent's list
+                const uint32_t code = rec & kHitMask;
                 float u = 0.f, v = 0.f, x2 = 0.f;
-                if (code < kCodeMiss)
-                    for (int j = 0; j < N; ++j)
-                        if (lorig[j * 32 + src] == static_cast<int>(code)) {
-                            u = lu[j * 32 + src];
-                            v = lv[j * 32 + src];
-                            x2 = lchi[j * 32 + src];
-                            break;
-                        }
+                if (code < kCodeMiss) {
+                    const int at = sel[lane] * 32 + src;
+                    u = lu[at];
+                    v = lv[at];
+                    x2 = lchi[at];
+                }
                 pend = true;
                 pcode = code;
                 pu = u;
                 pv = v;
                 px2 = x2;
-                hist[step * 32 + lane] = (static_cast<uint32_t>(prank) << 28) | code;
             }
             ++step;
             __syncwarp();
@@ -926,15 +951,15 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     }
 }
 
-}  // namespace
-
 // steps: at most one per layer + one final step with no layer left
-static int find_max_steps(int n_layers) { return n_layers + 2; }
+int find_max_steps(int n_layers) { return n_layers + 2; }
 
-static size_t find_smem_bytes(int n_layers, int n_best, int threads) {
+size_t find_smem_bytes(int n_layers, int n_best, int threads) {
     const int nwarps = threads / 32;
-    return static_cast<size_t>(nwarps) * (find_max_steps(n_layers) * 32 * 4 + n_best * 32 * 16);
+    return static_cast<size_t>(nwarps) * (find_max_steps(n_layers) * 32 * 4 + n_best * 32 * 16 + 32 * 4);
 }
+
+}  // namespace
 
 extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int32_t *seed_hits,
                                const int32_t *seed_event, int32_t n_seeds, const mkf_find_params *params,

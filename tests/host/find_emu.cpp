@@ -69,7 +69,7 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
     A.n_best = N;
     A.cut = cut;
     A.max_consec = max_consec;
-    A.max_steps = nl + 2;
+    A.max_steps = find_max_steps(nl);
     A.out_par = out_par;
     A.out_cov = out_cov;
     A.out_chi2 = out_chi2;
@@ -92,7 +92,7 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
         seed_kernel(A);
     }
     blockDim.x = 32;
-    std::vector<unsigned char> smem(static_cast<size_t>(A.max_steps) * 32 * 4 + static_cast<size_t>(N) * 32 * 16);
+    std::vector<unsigned char> smem(find_smem_bytes(nl, N, 32));
     g_smem = smem.data();
     WarpEmu w;
     g_warp = &w;
