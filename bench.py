@@ -390,7 +390,7 @@ def fit_leg(dev, n_tracks: int = 1_000_000, reps: int = 20):
                          "frac": fl / (ms * 1e-3) / 1e12 / peak, "kernel": "fit_kernel"}}
 
 
-FIND_DRAM_BYTES = None  # dram__bytes_read.sum + dram__bytes_write.sum of find_kernel on find20; None until re-measured for this kernel version
+FIND_DRAM_BYTES = 35_944_000 + 18_900  # dram__bytes_read.sum + dram__bytes_write.sum, find_kernel, find20
 
 
 def _carve(arena, specs):

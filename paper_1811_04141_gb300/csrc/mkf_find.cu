@@ -204,6 +204,15 @@ __device__ __forceinline__ int next_layer(const Geom &G, unsigned long long mask
 // Segmented reductions over the N lanes [base, base + N) of a seed, by
 // shuffles.  (The redux unit with one member mask per segment measured ~20 %
 // slower for the whole finder.)
+__device__ __forceinline__ uint32_t seg_max32(uint32_t v, int rank, int N, int base) {
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        const uint32_t o = __shfl_down_sync(kFull, v, off);
+        if (rank + off < N && o > v) v = o;
+    }
+    return __shfl_sync(kFull, v, base & 31);
+}
+
 __device__ __forceinline__ int seg_sum(int v, int rank, int N) {
 #pragma unroll
     for (int off = 1; off < 16; off <<= 1) {
@@ -735,28 +744,36 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             if (active) {
                 expand(A, G, ev, mask, dir, N, cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi + lane, lorig + lane,
                        lu + lane, lv + lane, 32, X);
-                // learned pruning / feature dump over the candidate's list (its
-                // N best compatible hits); the MLP scores a list only when the
-                // candidate has two or more compatible hits
-                if (kLearned && X.searched && (A.feat_out || (A.mlp && X.n_compat >= 2)) && X.nlist > 0) {
-                    const LayerDesc &Ld = G.L[X.layer];
-                    int kept = 0;
-                    for (int j = 0; j < X.nlist; ++j) {
-                        const float x2 = lchi[j * 32 + lane], u = lu[j * 32 + lane], v = lv[j * 32 + lane];
-                        const int orig = lorig[j * 32 + lane];
-                        float fe[12];
-                        pair_features(u, v, I, x2, cut, chi2, bk, X.layer, G.n_layers, Ld.kind, p, X.cot, fe);
-                        if (A.feat_out) {
-                            const int at = atomicAdd(A.feat_count, 1);
-                            if (at < A.feat_cap) {
+            }
+            // learned pruning / feature dump over the candidate's list (its N best
+            // compatible hits); the MLP scores a list only when the candidate has
+            // two or more compatible hits.  The lanes step through the list
+            // positions together, so the MLP runs once per position for the warp
+            if (kLearned) {
+                const bool score_it = X.searched && X.nlist > 0 && (A.feat_out || (A.mlp && X.n_compat >= 2));
+                const int ly = X.layer >= 0 ? X.layer : 0;
+                const LayerDesc &Ld = G.L[ly];
+                int kept = 0;
+                for (int j = 0; __any_sync(kFull, score_it && j < X.nlist); ++j) {
+                    const bool has = score_it && j < X.nlist;
+                    const int jj = has ? j : 0;
+                    const float x2 = lchi[jj * 32 + lane], u = lu[jj * 32 + lane], v = lv[jj * 32 + lane];
+                    const int orig = lorig[jj * 32 + lane];
+                    float fe[12];
+                    pair_features(u, v, I, x2, cut, chi2, bk, ly, G.n_layers, Ld.kind, p, X.cot, fe);
+                    if (A.feat_out && has) {
+                        const int at = atomicAdd(A.feat_count, 1);
+                        if (at < A.feat_cap) {
 #pragma unroll
-                                for (int q = 0; q < 12; ++q) A.feat_out[(int64_t)at * 12 + q] = fe[q];
-                                A.feat_ref[(int64_t)at * 3] = seed;
-                                A.feat_ref[(int64_t)at * 3 + 1] = orig;
-                                A.feat_ref[(int64_t)at * 3 + 2] = X.n_compat;
-                            }
+                            for (int q = 0; q < 12; ++q) A.feat_out[(int64_t)at * 12 + q] = fe[q];
+                            A.feat_ref[(int64_t)at * 3] = seed;
+                            A.feat_ref[(int64_t)at * 3 + 1] = orig;
+                            A.feat_ref[(int64_t)at * 3 + 2] = X.n_compat;
                         }
-                        if (A.mlp && X.n_compat >= 2 && mlp_logit(WS, fe) < A.mlp_tau) continue;
+                    }
+                    const float logit = A.mlp ? mlp_logit(WS, fe) : 0.f;
+                    const bool drop = A.mlp && X.n_compat >= 2 && logit < A.mlp_tau;
+                    if (has && !drop) {
                         if (kept != j) {
                             lchi[kept * 32 + lane] = x2;
                             lorig[kept * 32 + lane] = orig;
@@ -765,23 +782,25 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                         }
                         ++kept;
                     }
-                    X.nlist = kept;
                 }
+                if (score_it) X.nlist = kept;
             }
             const int nlist = X.nlist;
             const bool searched = X.searched;
             __syncwarp();
 
-            // ---- 2. selection of the N best children of each seed: rounds of a
-            // segmented top-2 over the lanes' two best remaining children, each
-            // round taking the seed's next two.  The key is the score as an
-            // order-preserving integer whose low 4 bits are replaced by (15 -
-            // parent rank): keys of different parents differ, the key names its
-            // parent, and scores that agree to 2^-19 relative are ordered by
-            // parent rank.  A lane holds the keys of its four best remaining
-            // children, so a win moves on without waiting on a shared-memory load.
-            // The winner records each child (its step-history word and its index
-            // in the parent's list) for the lane that takes it.
+            // ---- 2. selection of the N best children of each seed: up to N rounds
+            // of a segmented max over the lanes' best remaining child.  The key is
+            // the score as an order-preserving integer whose low 4 bits are
+            // replaced by (15 - parent rank): keys are unique within a seed, the
+            // maximum names the winning parent, and scores that agree to 2^-19
+            // relative are ordered by parent rank.  Each lane holds the keys of its
+            // two best remaining children and reads the one after them every round,
+            // so a win moves on by selects, with no shared-memory wait and no
+            // divergent branch in the round (a branch there measured 3-4 % slower
+            // for the plain finder and 2x for the learned one).  The winner records
+            // the child (its step-history word and its index in the parent's list)
+            // for the lane that takes it.
             const float score = cut * static_cast<float>(bk.nh) - chi2;
             const int n_children = live ? (searched ? nlist + 1 : 1) : 0;
             const uint32_t nohit = searched ? kCodeMiss : kCodePass;
@@ -794,56 +813,32 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                 }
             } else {
                 const uint32_t tag = 15u - static_cast<uint32_t>(rank);
-                auto key_of = [&](int c) -> uint32_t {
-                    return c < n_children ? sel_key(c < nlist ? score + cut - lchi[c * 32 + lane] : score, tag) : 0u;
-                };
-                auto take = [&](int jj, int c) {
-                    hist[step * 32 + base + jj] =
-                        (static_cast<uint32_t>(rank) << 28) | (c < nlist ? static_cast<uint32_t>(lorig[c * 32 + lane]) : nohit);
-                    sel[base + jj] = c;
-                };
                 int head = 0;
-                uint32_t k1 = key_of(0), k2 = key_of(1), k3 = key_of(2), k4 = key_of(3);
-                for (int j = 0; j < N; j += 2) {
-                    if (!__any_sync(kFull, k1 != 0u)) break;
-                    uint32_t a1 = k1, a2 = k2;
-#pragma unroll
-                    for (int off = 1; off < 16; off <<= 1) {
-                        // merge the pair (b1 >= b2) from lane + off into (a1 >= a2)
-                        const uint32_t b1 = __shfl_down_sync(kFull, a1, off);
-                        const uint32_t b2 = __shfl_down_sync(kFull, a2, off);
-                        if (rank + off < N) {
-                            if (b1 > a1) {
-                                a2 = max(a1, b2);
-                                a1 = b1;
-                            } else {
-                                a2 = max(a2, b1);
-                            }
-                        }
+                uint32_t key = n_children > 0 ? sel_key(nlist > 0 ? score + cut - lchi[lane] : score, tag) : 0u;
+                uint32_t knext = n_children > 1 ? sel_key(nlist > 1 ? score + cut - lchi[32 + lane] : score, tag) : 0u;
+                // step-history payload of the lane's best remaining child
+                uint32_t code = nlist > 0 ? static_cast<uint32_t>(lorig[lane]) : nohit;
+                for (int j = 0; j < N; ++j) {
+                    if (!__any_sync(kFull, key != 0u)) break;
+                    const uint32_t m = seg_max32(key, rank, N, base);
+                    const bool seg_ok = m != 0u && lane_used;
+                    got = got || (seg_ok && rank == j);
+                    const bool win = seg_ok && (m & 15u) == tag;
+                    if (win) {
+                        hist[step * 32 + base + j] = (static_cast<uint32_t>(rank) << 28) | code;
+                        sel[base + j] = head;
                     }
-                    const uint32_t m1 = __shfl_sync(kFull, a1, base & 31);
-                    const uint32_t m2 = __shfl_sync(kFull, a2, base & 31);
-                    if (m1 != 0u && lane_used) {
-                        const bool two = m2 != 0u && j + 1 < N;
-                        if (rank == j || (two && rank == j + 1)) got = true;
-                        const bool w1 = (m1 & 15u) == tag, w2 = two && (m2 & 15u) == tag;
-                        if (w1 && w2) {
-                            take(j, head);
-                            take(j + 1, head + 1);
-                            head += 2;
-                            k1 = k3;
-                            k2 = k4;
-                            k3 = key_of(head + 2);
-                            k4 = key_of(head + 3);
-                        } else if (w1 || w2) {
-                            take(w1 ? j : j + 1, head);
-                            ++head;
-                            k1 = k2;
-                            k2 = k3;
-                            k3 = k4;
-                            k4 = key_of(head + 3);
-                        }
-                    }
+                    // every lane reads what it would move on to (in-bounds rows), the
+                    // winner takes it: no divergent branch in the round
+                    const int h1 = head + 1, h2 = head + 2;
+                    const float x2n = lchi[min(h2, N - 1) * 32 + lane];
+                    const int on = lorig[min(h1, N - 1) * 32 + lane];
+                    const uint32_t k2 = h2 < n_children ? sel_key(h2 < nlist ? score + cut - x2n : score, tag) : 0u;
+                    const uint32_t c1 = h1 < nlist ? static_cast<uint32_t>(on) : nohit;
+                    head = win ? h1 : head;
+                    key = win ? knext : key;
+                    knext = win ? k2 : knext;
+                    code = win ? c1 : code;
                 }
             }
             __syncwarp();
