@@ -62,6 +62,9 @@ def _load():
             lib.or_seed.restype = C.c_int
             lib.or_fit.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, d, d, d, i32, u32]
             lib.or_fit.restype = C.c_int
+            lib.or_fit_backward.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, C.c_double, d, d,
+                                                   d, i32, u32]
+            lib.or_fit_backward.restype = C.c_int
             lib.or_find.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, i32, i32, C.c_int64, i64, C.c_int64,
                                            C.c_int, C.c_double, C.c_int, d, d, d, i32, i32, C.c_int, u32, i64, d,
                                            d, C.c_double, d, i32, i64, C.c_int64]
@@ -191,6 +194,28 @@ def fit(geo: Geometry, xyz, hit_layer, hit_idx, seed_par=None, seed_cov21=None):
                     _p(chi2, C.c_double), _p(ndf, C.c_int32), _p(st, C.c_uint32))
     if rc != 0:
         raise RuntimeError(f"or_fit failed: {rc}")
+    return dict(par=par, cov=cov, chi2=chi2, ndf=ndf, status=st)
+
+
+def fit_backward(geo: Geometry, xyz, hit_layer, hit_idx, last_par, last_cov21, inflate=100.0):
+    """Backward fit along fixed hit lists (hits in path order) from the state at
+    each track's last hit (last_par [6, n], last_cov21 [21, n]); returns the state
+    at the first hit with chi2 and ndf over every hit used."""
+    lib = _load()
+    xyz = _f64(xyz)
+    n_hits = xyz.shape[1]
+    hit_layer = np.ascontiguousarray(hit_layer, dtype=np.int32)
+    hit_idx = np.ascontiguousarray(hit_idx, dtype=np.int32)
+    max_hits, n = hit_idx.shape
+    par, cov = np.zeros((6, n)), np.zeros((21, n))
+    chi2, ndf, st = np.zeros(n), np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.uint32)
+    lp, lc = _f64(last_par), _f64(last_cov21)
+    rc = lib.or_fit_backward(*geo.args(), _p(xyz, C.c_double), n_hits, _p(hit_layer, C.c_int32),
+                             _p(hit_idx, C.c_int32), max_hits, n, _p(lp, C.c_double), _p(lc, C.c_double),
+                             C.c_double(inflate), _p(par, C.c_double), _p(cov, C.c_double), _p(chi2, C.c_double),
+                             _p(ndf, C.c_int32), _p(st, C.c_uint32))
+    if rc != 0:
+        raise RuntimeError(f"or_fit_backward failed: {rc}")
     return dict(par=par, cov=cov, chi2=chi2, ndf=ndf, status=st)
 
 

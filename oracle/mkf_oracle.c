@@ -526,6 +526,88 @@ int or_fit(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_laye
 }
 
 /* ------------------------------------------------------------------------- */
+/* Backward fit: the same filter through the hits in reverse order           */
+/* ------------------------------------------------------------------------- */
+
+/* The helix traversed the other way: the same curve with the momentum turned
+ * around, p -> (x, y, z, -q/pT, phi + pi, pi - theta).  Its derivative is
+ * F = diag(1, 1, 1, -1, 1, -1), so C -> F C F flips the sign of the covariances
+ * between {q/pT, theta} and the other parameters. */
+static void reverse_state(double p[6], double C[36]) {
+    static const double f[6] = {1, 1, 1, -1, 1, -1};
+    p[3] = -p[3];
+    p[4] = wrap_pi(p[4] + OR_PI);
+    p[5] = OR_PI - p[5];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) C[i * 6 + j] *= f[i] * f[j];
+}
+
+/* Backward fit along fixed hit lists (the reverse pass over a fitted or found
+ * track, whose result is the state at its first hit with every hit used).
+ * xyz, hit_layer, hit_idx as in or_fit (hits in path order).  last_par [6][n],
+ * last_cov [21][n] (packed): the state on the surface of each track's last hit,
+ * e.g. or_fit's output.  The state is turned around, its covariance multiplied
+ * by inflate (>= 1), updated with the last hit, then moved to each earlier hit
+ * in turn and updated; at the first hit it is turned back.  Outputs as or_fit,
+ * reported on the surface of the first hit used. */
+int or_fit_backward(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_layer, const int32_t *hit_idx,
+                    int max_hits, int64_t n, const double *last_par, const double *last_cov, double inflate,
+                    double *out_par, double *out_cov, double *out_chi2, int32_t *out_ndf, uint32_t *out_status) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS)) return -1;
+    if (!last_par || !last_cov || !(inflate >= 1.0)) return -1;
+    const double *X = xyz, *Y = xyz + n_hits, *Z = xyz + 2 * n_hits;
+    for (int64_t t = 0; t < n; ++t) {
+        double p[6], C[36];
+        uint32_t st = 0;
+        int idx[OR_MAXL + 8];
+        int nh = 0;
+        for (int k = 0; k < max_hits && k < OR_MAXL + 8; ++k) {
+            int32_t hi_ = hit_idx[(int64_t)k * n + t];
+            if (hi_ >= 0 && hi_ < n_hits) idx[nh++] = hi_;
+        }
+        double chi2 = 0;
+        int used = 0;
+        if (nh < 3) st |= OR_ST_BADSEED;
+        if (!(st & OR_ST_BADSEED)) {
+            for (int i = 0; i < 6; ++i) p[i] = last_par[(int64_t)i * n + t];
+            unpack21(last_cov + t, n, C);
+            reverse_state(p, C);
+            for (int i = 0; i < 36; ++i) C[i] *= inflate;
+            for (int k = nh - 1; k >= 0; --k) {
+                int hid = idx[k], l = hit_layer[hid];
+                if (k < nh - 1) {
+                    double s, q[6], J[36], Cn[36];
+                    if (!path_to_layer(&g, p, l, &s)) { st |= OR_ST_UNREACHABLE; continue; }
+                    helix_move(p, turn_rate(&g, p[3]), s, q);
+                    prop_jacobian(&g, p, l, s, q, J);
+                    transport(J, C, Cn);
+                    memcpy(p, q, sizeof(q));
+                    memcpy(C, Cn, sizeof(Cn));
+                }
+                double H[12], r[2], S[4], Si[4], HC[12];
+                residual(&g, l, p, X[hid], Y[hid], Z[hid], r, H);
+                if (!residual_cov(&g, l, C, H, S, Si, HC)) { st |= OR_ST_BADS; continue; }
+                chi2 += kf_update(HC, Si, r, p, C);
+                used++;
+            }
+            reverse_state(p, C);
+        }
+        if (!finite6(p) || !isfinite(chi2)) st |= OR_ST_NONFINITE;
+        for (int i = 0; i < 6; ++i) out_par[(int64_t)i * n + t] = (st & OR_ST_BADSEED) ? NAN : p[i];
+        if (st & OR_ST_BADSEED) {
+            for (int k = 0; k < 21; ++k) out_cov[(int64_t)k * n + t] = NAN;
+        } else {
+            pack21(C, out_cov + t, n);
+        }
+        out_chi2[t] = chi2;
+        out_ndf[t] = 2 * used - (g.bz != 0.0 ? 5 : 4);
+        out_status[t] = st;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Finding                                                                    */
 /* ------------------------------------------------------------------------- */
 

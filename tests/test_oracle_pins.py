@@ -393,7 +393,8 @@ def _global_ls(geo, b, t):
     sol = so.least_squares(resid, v0, x_scale="jac", xtol=1e-14, ftol=1e-14, gtol=1e-14)
     P = path(*sol.x)
     last = np.array([P[-1, 0], P[-1, 1], P[-1, 2], sol.x[2], wrap(P[-1, 3]), sol.x[4]])
-    return (sol.fun ** 2).sum(), last
+    first = np.array([P[0, 0], P[0, 1], P[0, 2], sol.x[2], wrap(P[0, 3]), sol.x[4]])
+    return (sol.fun ** 2).sum(), last, first
 
 
 def test_fit_matches_global_least_squares():
@@ -404,11 +405,143 @@ def test_fit_matches_global_least_squares():
     for t in range(b.n_seeds):
         if b.particle_nhits[b.seed_particle[t]] < 10:
             continue
-        chi2_ls, last = _global_ls(geo, b, t)
+        chi2_ls, last, _ = _global_ls(geo, b, t)
         d = r["par"][:, t] - last
         d[4] = wrap(d[4])
         assert np.abs(d / np.sqrt(np.diag(Cm[t]))).max() < 0.05, t
         assert abs(r["chi2"][t] - chi2_ls) < 0.05 * max(1.0, chi2_ls), t
+
+
+# --------------------------------------------------------------------------
+# backward fit
+# --------------------------------------------------------------------------
+
+def _first_hits(b):
+    return np.array([b.track_hits[:, t][b.track_hits[:, t] >= 0][0] for t in range(b.n_seeds)])
+
+
+def test_backfit_noise_free_recovers_truth():
+    """Noise-free hits: the backward pass from the forward result returns the
+    generator's state at each track's first hit, whatever the inflation."""
+    for cfg in ["fit10", "fit10_b0", "find20", "dense45"]:
+        b = make_batch(cfg, [4], n_tracks=200, smear=False)
+        geo = O.geometry_for(b)
+        r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
+        ok = r["status"] == 0
+        ts = b.true_state[:, _first_hits(b)]
+        for inflate in (1.0, 100.0, 1e4):
+            rb = O.fit_backward(geo, b.xyz64, b.layer, b.track_hits, r["par"], r["cov"], inflate)
+            assert (rb["status"][ok] == 0).all(), cfg
+            d = rb["par"][:, ok] - ts[:, ok]
+            d[4] = wrap(d[4])
+            if b.bz == 0:
+                d[3] = 0
+            scale = np.maximum(1.0, np.abs(ts[:, ok]))
+            assert np.abs(d / scale).max() < 1e-9, (cfg, inflate)
+            assert rb["chi2"][ok].max() < 1e-12
+            assert (rb["ndf"][ok] == r["ndf"][ok]).all()
+
+
+@pytest.mark.slow
+def test_backfit_pulls_and_chi2():
+    """Smeared hits: pulls of the state at the first hit against the generator
+    are N(0, 1) and chi2/ndf is 1 (a sign error in the turned-around covariance
+    or transport shows in both)."""
+    b = make_batch("find20", list(range(3)), n_tracks=1500)
+    geo = O.geometry_for(b)
+    r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
+    rb = O.fit_backward(geo, b.xyz64, b.layer, b.track_hits, r["par"], r["cov"], 1e4)
+    ok = (rb["status"] == 0) & (r["status"] == 0)
+    first = _first_hits(b)
+    assert (geo.kind[b.layer[first]] == 0).all()  # every track starts on a cylinder
+    ts = b.true_state[:, first]
+    Cm = O.unpack21(rb["cov"][:, ok])
+    # position along the surface (r-phi): x and y alone mix in the radial
+    # direction, whose variance on the surface is zero to first order
+    phi_pos = np.arctan2(ts[1, ok], ts[0, ok])
+    hu = np.zeros((ok.sum(), 6))
+    hu[:, 0], hu[:, 1] = -np.sin(phi_pos), np.cos(phi_pos)
+    du = hu[:, 0] * (rb["par"][0, ok] - ts[0, ok]) + hu[:, 1] * (rb["par"][1, ok] - ts[1, ok])
+    pulls = {"u": du / np.sqrt(np.einsum("ti,tij,tj->t", hu, Cm, hu))}
+    for i in range(2, 6):
+        d = rb["par"][i, ok] - ts[i, ok]
+        if i == 4:
+            d = wrap(d)
+        pulls[i] = d / np.sqrt(Cm[:, i, i])
+    for k, pull in pulls.items():
+        assert abs(pull.mean()) < 0.05, k
+        assert abs(pull.std() - 1) < 0.05, k
+    assert abs(rb["chi2"][ok].sum() / rb["ndf"][ok].sum() - 1) < 0.03
+
+
+def test_backfit_matches_global_least_squares():
+    """With a vague prior (inflation 1e4) the backward pass is the least-squares
+    helix through all the hits, reported at the first hit: state and chi2 agree
+    with an independent global fit (scipy)."""
+    b = make_batch("fit10", [6], n_tracks=40)
+    geo = O.geometry_for(b)
+    r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
+    rb = O.fit_backward(geo, b.xyz64, b.layer, b.track_hits, r["par"], r["cov"], 1e4)
+    Cm = O.unpack21(rb["cov"])
+    n_checked = 0
+    for t in range(b.n_seeds):
+        if b.particle_nhits[b.seed_particle[t]] < 10:
+            continue
+        chi2_ls, _, first = _global_ls(geo, b, t)
+        d = rb["par"][:, t] - first
+        d[4] = wrap(d[4])
+        assert np.abs(d / np.sqrt(np.diag(Cm[t]))).max() < 0.05, t
+        assert abs(rb["chi2"][t] - chi2_ls) < 0.05 * max(1.0, chi2_ls), t
+        n_checked += 1
+    assert n_checked >= 20
+
+
+@pytest.mark.parametrize("cfg", ["fit10", "find20"])
+def test_backfit_transport_round_trip(cfg):
+    """With hit errors of 1e4 cm the updates do nothing measurable, so the
+    backward pass only carries the state and covariance from the last hit back
+    to the first: it must return the first-hit state and the on-surface
+    covariance that the forward Jacobians (or_propagate, or_transport) carried
+    from the first hit to the last.  A wrong sign in the turned-around
+    covariance, or a transport that does not invert, fails here."""
+    b = make_batch(cfg, [8], n_tracks=60, smear=False)
+    geo = O.geometry_for(b)
+    big = O.Geometry([dict(d, sigma_u=1e4, sigma_v=1e4) for d in b.layers], b.bz)
+    lp, lc, p0s, c0s = [], [], [], []
+    for t in range(b.n_seeds):
+        hh = b.track_hits[:, t]
+        hh = hh[hh >= 0]
+        p, Cm = O.seed(geo, *[b.xyz64[:, i] for i in hh[:3]], b.layer[hh[0]])
+        p = b.true_state[:, hh[0]].copy()
+        p0s.append(p.copy())
+        c0s.append(Cm.copy())
+        for h in hh[1:]:
+            q, J, _ = O.propagate(geo, p, b.layer[h])
+            Cm = O.transport(J, Cm)
+            p = q
+        lp.append(p)
+        lc.append(Cm)
+    rb = O.fit_backward(big, b.xyz64, b.layer, b.track_hits, np.array(lp).T, O.pack21(np.array(lc)), 1.0)
+    assert (rb["status"] == 0).all()
+    d = rb["par"] - np.array(p0s).T
+    d[4] = wrap(d[4])
+    assert np.abs(d).max() < 1e-9
+    Cb = O.unpack21(rb["cov"])
+    C0 = np.array(c0s)
+    sd = np.sqrt(np.einsum("tii->ti", C0))
+    assert (np.abs(Cb - C0) / (sd[:, :, None] * sd[:, None, :] + 1e-300)).max() < 1e-5
+
+
+def test_backfit_short_lists_and_errors():
+    b = make_batch("fit10", [7], n_tracks=20)
+    geo = O.geometry_for(b)
+    hidx = b.track_hits.copy()
+    hidx[2:, 3] = -1  # two hits: no fit
+    r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
+    rb = O.fit_backward(geo, b.xyz64, b.layer, hidx, r["par"], r["cov"], 100.0)
+    assert rb["status"][3] & 2 and np.isnan(rb["par"][:, 3]).all()
+    with pytest.raises(RuntimeError):
+        O.fit_backward(geo, b.xyz64, b.layer, hidx, r["par"], r["cov"], 0.5)
 
 
 # --------------------------------------------------------------------------
