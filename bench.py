@@ -379,15 +379,34 @@ def fit_leg(dev, n_tracks: int = 1_000_000, reps: int = 20):
         ts.append((a, e))
     torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(e) for a, e in ts]))
+    # backward fit of the same tracks from the forward result at the last hit
+    outb = ctx.fit_backward(xyz, layer, th, out["par"], out["cov"], 100.0)
+    for _ in range(3):
+        ctx.fit_backward(xyz, layer, th, out["par"], out["cov"], 100.0, out=outb)
+    torch.cuda.synchronize()
+    tb = []
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.fit_backward(xyz, layer, th, out["par"], out["cov"], 100.0, out=outb)
+        e.record()
+        tb.append((a, e))
+    torch.cuda.synchronize()
+    ms_b = float(np.mean([a.elapsed_time(e) for a, e in tb]))
     layers = int((b.track_hits >= 0).sum())
     fl = flops.FLOPS_PER_FIT_LAYER * layers
     peak = flops.fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count, 2070.0)
     ctx.close()
+    roof = lambda t, k: {"bound": "alu", "achieved": fl / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": fl / (t * 1e-3) / 1e12 / peak, "kernel": k}
     return {"workload": f"{n_ev} events x {n_tracks // n_ev} tracks, 10 barrel cylinders R=4..100 cm, |z|<=125, 3.8 T, |eta|<1, "
                         "pT U[0.5,10] GeV, 20 um / 100 um hits, seeds from the first three hits",
-            "track_layer_updates_per_s": layers / (ms * 1e-3), "ms": ms,
-            "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": fl / (ms * 1e-3) / 1e12 / peak, "kernel": "fit_kernel"}}
+            "track_layer_updates_per_s": layers / (ms * 1e-3), "ms": ms, "roofline": roof(ms, "fit_kernel"),
+            "backward": {"workload": "the same tracks fitted in reverse from the forward result at the last hit "
+                                     "(covariance x100), state at the first hit",
+                         "track_layer_updates_per_s": layers / (ms_b * 1e-3), "ms": ms_b,
+                         "roofline": roof(ms_b, "fit_kernel (backward)")}}
 
 
 FIND_DRAM_BYTES = 35_944_000 + 18_900  # dram__bytes_read.sum + dram__bytes_write.sum, find_kernel, find20

@@ -217,6 +217,29 @@ mkf_status mkf_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit_layer, int
                    int32_t max_hits, int32_t n, const float *seed_par, const float *seed_cov, float *out_par,
                    float *out_cov, float *chi2, int32_t *ndf, uint32_t *status);
 
+/* Backward fit along fixed hit lists: the Kalman filter of mkf_fit run through
+ * each track's hits in reverse order, the pass that delivers a fitted or found
+ * track's parameters at its first (innermost) hit with every hit used (the
+ * paper's layer plans carry layers used only during backward fitting, Sec. 2.1).
+ * xyz, hit_layer, n_hits, hit_idx, max_hits, n and the outputs are as for
+ * mkf_fit (hits listed in path order, -1 = none).  last_par [6][n], last_cov
+ * [21][n] (device, packed as above): the state on the surface of each track's
+ * last valid hit, e.g. mkf_fit's output.  That state is turned around (the same
+ * helix with the momentum reversed: q/pT -> -q/pT, phi -> phi + pi, theta ->
+ * pi - theta, and the matching sign changes of the covariance), its covariance
+ * is multiplied by `inflate` (>= 1; large values make the pass independent of
+ * the incoming covariance), it is updated with the last hit without moving,
+ * then propagated to each earlier hit and updated; at the first hit it is turned
+ * back.  Outputs: the state and covariance on the surface of the first hit used,
+ * chi2 and ndf over the hits used, status bits as for mkf_fit (fewer than 3
+ * valid hits: MKF_ST_BADSEED, NaN outputs).  Errors: MKF_ERR_ARG (inflate < 1
+ * or not finite, last_par or last_cov NULL with n > 0, other arguments as for
+ * mkf_fit), MKF_ERR_GEOMETRY, MKF_ERR_CAPACITY, MKF_ERR_CUDA. */
+mkf_status mkf_fit_backward(mkf_ctx *ctx, const float *xyz, const int32_t *hit_layer, int32_t n_hits,
+                            const int32_t *hit_idx, int32_t max_hits, int32_t n, const float *last_par,
+                            const float *last_cov, float inflate, float *out_par, float *out_cov, float *chi2,
+                            int32_t *ndf, uint32_t *status);
+
 /* ------------------------------------------------------------------------ */
 /* Finding (Sec. 1: layer-by-layer finding with selection of the best chi2   */
 /* extensions before the final Kalman updates)                               */

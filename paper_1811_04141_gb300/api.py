@@ -1,5 +1,5 @@
 """Python binding of the C ABI with the same names (mkf_create, mkf_geometry_load,
-mkf_hits_bin, mkf_fit, mkf_find, mkf_sync, mkf_destroy), plus a small Context
+mkf_hits_bin, mkf_fit, mkf_fit_backward, mkf_find, mkf_sync, mkf_destroy), plus a small Context
 class.  PyTorch supplies device memory and streams; this module only checks
 tensor shapes, dtypes and devices and passes raw pointers to libmkf.so.
 """
@@ -165,6 +165,30 @@ def mkf_fit(ctx, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, out=None
     return out
 
 
+def mkf_fit_backward(ctx, xyz, hit_layer, hit_idx, last_par, last_cov, inflate=100.0, out=None,
+                     device: int | None = None):
+    """Backward fit along fixed hit lists (path order) from the state at each
+    track's last hit; returns dict(par [6,n], cov [21,n], chi2, ndf, status) at
+    the first hit."""
+    n_hits = xyz.shape[1]
+    _need(xyz, "xyz", torch.float32, (3, n_hits), device)
+    _need(hit_layer, "hit_layer", torch.int32, (n_hits,), device)
+    max_hits, n = hit_idx.shape
+    _need(hit_idx, "hit_idx", torch.int32, (max_hits, n), device)
+    _need(last_par, "last_par", torch.float32, (6, n), device)
+    _need(last_cov, "last_cov", torch.float32, (21, n), device)
+    dev = xyz.device
+    if out is None:
+        out = dict(par=torch.empty(6, n, device=dev), cov=torch.empty(21, n, device=dev),
+                   chi2=torch.empty(n, device=dev), ndf=torch.empty(n, dtype=torch.int32, device=dev),
+                   status=torch.empty(n, dtype=torch.int32, device=dev))
+    N.check("mkf_fit_backward", N.lib().mkf_fit_backward(
+        ctx, _ptr(xyz), _ptr(hit_layer), n_hits, _ptr(hit_idx), max_hits, n, _ptr(last_par), _ptr(last_cov),
+        C.c_float(inflate), _ptr(out["par"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out["ndf"]),
+        _ptr(out["status"])))
+    return out
+
+
 def find_params(n_best=10, chi2_cut=30.0, max_consec_miss=3, block_threads=0, mlp_bf16=None, mlp_tau=0.0,
                 feat=None, event_times=None) -> N.MkfFindParams:
     prm = N.MkfFindParams(int(n_best), float(chi2_cut), int(max_consec_miss), int(block_threads))
@@ -302,6 +326,9 @@ class Context:
 
     def fit(self, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, out=None):
         return mkf_fit(self.handle, xyz, hit_layer, hit_idx, seed_par, seed_cov, out, self.device)
+
+    def fit_backward(self, xyz, hit_layer, hit_idx, last_par, last_cov, inflate=100.0, out=None):
+        return mkf_fit_backward(self.handle, xyz, hit_layer, hit_idx, last_par, last_cov, inflate, out, self.device)
 
     def find(self, bins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
              out=None, counters=True, block_threads=0, mlp_bf16=None, mlp_tau=0.0, feat=None, event_times=None):

@@ -1,5 +1,6 @@
 // Track fit along fixed hit lists: one thread per track, state and covariance in
-// registers for the whole hit list (Sec. 1: Kalman-filter fitting).
+// registers for the whole hit list (Sec. 1: Kalman-filter fitting), and the
+// backward fit, the same filter through the hits in reverse order.
 #include <cuda_runtime.h>
 
 #include "mkf_internal.h"
@@ -16,6 +17,7 @@ struct FitArgs {
     const int32_t *hit_idx;
     int32_t max_hits, n;
     const float *seed_par, *seed_cov;
+    float inflate;  // backward fit: factor on the starting covariance
     float *out_par, *out_cov, *chi2;
     int32_t *ndf;
     uint32_t *status;
@@ -26,6 +28,28 @@ __device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) 
     if (atomicCAS(&f->code, 0, code) == 0) f->where = where;
 }
 
+// The helix traversed the other way: the same curve with the momentum turned
+// around, p -> (x, y, z, -q/pT, phi + pi, pi - theta) with pi as a float pair,
+// and C -> F C F with F = diag(1, 1, 1, -1, 1, -1) (the covariances between
+// {q/pT, theta} and the other parameters change sign).
+__device__ __forceinline__ void reverse_state(float p[6], Lo &lo, float C[21]) {
+    constexpr float kPiHi = 3.14159274101257324219f;  // float(pi)
+    constexpr float kPiLo = -8.74227765734758e-8f;    // pi - float(pi)
+    p[3] = -p[3];
+    df_add(p[4], lo.phi, kPiHi);
+    df_add(p[4], lo.phi, kPiLo);
+    df_wrap_pi(p[4], lo.phi);
+    p[5] = (kPiHi - p[5]) + kPiLo;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j)
+            if ((i == 3 || i == 5) != (j == 3 || j == 5)) C[sym(i, j)] = -C[sym(i, j)];
+}
+
+// kBackward: hits in reverse order from the given state at the last hit, turned
+// around and inflated; the result at the first hit is turned back.
+template <bool kBackward>
 __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ FitArgs A) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= A.n) return;
@@ -58,6 +82,11 @@ __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ Fit
             for (int i = 0; i < 6; ++i) p[i] = A.seed_par[(int64_t)i * A.n + t];
 #pragma unroll
             for (int k = 0; k < 21; ++k) C[k] = A.seed_cov[(int64_t)k * A.n + t];
+            if (kBackward) {
+                reverse_state(p, lo, C);
+#pragma unroll
+                for (int k = 0; k < 21; ++k) C[k] *= A.inflate;
+            }
         } else {
             float h1[3], h2[3], h3[3], eta;
             h1[0] = A.X[first[0]]; h1[1] = A.Y[first[0]]; h1[2] = A.Z[first[0]];
@@ -70,7 +99,8 @@ __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ Fit
 
     if (ok) {
         bool firsthit = true;
-        for (int k = 0; k < A.max_hits; ++k) {
+        for (int kk = 0; kk < A.max_hits; ++kk) {
+            const int k = kBackward ? A.max_hits - 1 - kk : kk;
             const int h = A.hit_idx[(int64_t)k * A.n + t];
             if (h < 0 || h >= A.n_hits) continue;
             const int l = A.hit_layer[h];
@@ -105,6 +135,7 @@ __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ Fit
             kf_apply(I, u, v, p, lo, C);
             ++used;
         }
+        if (kBackward) reverse_state(p, lo, C);
         if (!finite_state(p) || !isfinite(chi2)) st |= MKF_ST_NONFINITE;
     }
     const float nanv = __int_as_float(0x7fc00000);
@@ -123,18 +154,20 @@ __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ Fit
 
 }  // namespace
 
-extern "C" mkf_status mkf_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit_layer, int32_t n_hits,
-                              const int32_t *hit_idx, int32_t max_hits, int32_t n, const float *seed_par,
-                              const float *seed_cov, float *out_par, float *out_cov, float *chi2, int32_t *ndf,
-                              uint32_t *status) {
+static mkf_status launch_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit_layer, int32_t n_hits,
+                             const int32_t *hit_idx, int32_t max_hits, int32_t n, const float *seed_par,
+                             const float *seed_cov, float inflate, bool backward, float *out_par, float *out_cov,
+                             float *chi2, int32_t *ndf, uint32_t *status) {
     if (!ctx) return MKF_ERR_ARG;
     if (!ctx->has_geom) return MKF_ERR_GEOMETRY;
     if (n < 0 || n_hits < 0 || max_hits < 1) return MKF_ERR_ARG;
     if (max_hits > MKF_MAX_LAYERS) return MKF_ERR_CAPACITY;
     if (n_hits > MKF_MAX_HITS) return MKF_ERR_CAPACITY;
     if ((seed_par == nullptr) != (seed_cov == nullptr)) return MKF_ERR_ARG;
+    if (backward && !(inflate >= 1.f && inflate < 3.0e38f)) return MKF_ERR_ARG;
     if (n == 0) return MKF_OK;
     if (!xyz || !hit_layer || !hit_idx || !out_par || !out_cov || !chi2 || !ndf || !status) return MKF_ERR_ARG;
+    if (backward && !seed_par) return MKF_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return MKF_ERR_CUDA;
     FitArgs A;
@@ -149,6 +182,7 @@ extern "C" mkf_status mkf_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit
     A.n = n;
     A.seed_par = seed_par;
     A.seed_cov = seed_cov;
+    A.inflate = inflate;
     A.out_par = out_par;
     A.out_cov = out_cov;
     A.chi2 = chi2;
@@ -157,7 +191,24 @@ extern "C" mkf_status mkf_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit
     A.fault = ctx->fault;
     const int threads = 128;
     const int blocks = (n + threads - 1) / threads;
-    fit_kernel<<<blocks, threads, 0, ctx->stream>>>(A);
+    if (backward) fit_kernel<true><<<blocks, threads, 0, ctx->stream>>>(A);
+    else fit_kernel<false><<<blocks, threads, 0, ctx->stream>>>(A);
     MKF_CUDA_TRY(cudaGetLastError());
     return MKF_OK;
+}
+
+extern "C" mkf_status mkf_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit_layer, int32_t n_hits,
+                              const int32_t *hit_idx, int32_t max_hits, int32_t n, const float *seed_par,
+                              const float *seed_cov, float *out_par, float *out_cov, float *chi2, int32_t *ndf,
+                              uint32_t *status) {
+    return launch_fit(ctx, xyz, hit_layer, n_hits, hit_idx, max_hits, n, seed_par, seed_cov, 1.f, false, out_par,
+                      out_cov, chi2, ndf, status);
+}
+
+extern "C" mkf_status mkf_fit_backward(mkf_ctx *ctx, const float *xyz, const int32_t *hit_layer, int32_t n_hits,
+                                       const int32_t *hit_idx, int32_t max_hits, int32_t n, const float *last_par,
+                                       const float *last_cov, float inflate, float *out_par, float *out_cov,
+                                       float *chi2, int32_t *ndf, uint32_t *status) {
+    return launch_fit(ctx, xyz, hit_layer, n_hits, hit_idx, max_hits, n, last_par, last_cov, inflate, true, out_par,
+                      out_cov, chi2, ndf, status);
 }

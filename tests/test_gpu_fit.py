@@ -70,6 +70,72 @@ def test_fit_given_seed_states_and_ragged_lists():
     assert par_errors(out2["par"][:, ok2], ref2["par"][:, ok2]).max() <= 1.0
 
 
+def _backward_pair(b, hidx, inflate, ctx=None):
+    """GPU and oracle backward fits from the same start: the oracle's forward fit
+    at the last hit, rounded to FP32, given to both."""
+    import oracle as O
+    geo = O.geometry_for(b)
+    f = O.fit(geo, b.xyz.astype(np.float64), b.layer, hidx)
+    lp = np.ascontiguousarray(f["par"], dtype=np.float32)
+    lc = np.ascontiguousarray(f["cov"], dtype=np.float32)
+    ctx = ctx or make_ctx(b)
+    d = upload(b)
+    out = to_np(ctx.fit_backward(d["xyz"], d["layer"], torch.as_tensor(hidx, device="cuda"),
+                                 torch.as_tensor(lp, device="cuda"), torch.as_tensor(lc, device="cuda"), inflate))
+    ctx.sync()
+    ref = O.fit_backward(geo, b.xyz.astype(np.float64), b.layer, hidx, lp.astype(np.float64), lc.astype(np.float64),
+                         inflate)
+    return out, ref, f
+
+
+@pytest.mark.parametrize("cfg,tracks,inflate", [("fit10", 1000, 100.0), ("fit10_b0", 1000, 100.0),
+                                                ("find20", 700, 100.0), ("dense45", 500, 1e4),
+                                                ("find20", 300, 1.0)])
+def test_fit_backward_parity(cfg, tracks, inflate):
+    """Backward fit (mkf_fit_backward) against the oracle's backward pass: state
+    at the first hit, chi2, ndf, status and covariance diagonal."""
+    b = make_batch(cfg, [14], n_tracks=tracks)
+    out, ref, f = _backward_pair(b, b.track_hits, inflate)
+    assert (out["status"] == ref["status"]).all()
+    assert (out["ndf"] == ref["ndf"]).all()
+    ok = (ref["status"] == 0) & (f["status"] == 0)
+    assert ok.mean() > 0.95
+    e = par_errors(out["par"][:, ok], ref["par"][:, ok], ref["cov"][:, ok])
+    assert e.max() <= 1.0, e.max(axis=1)
+    c = chi2_errors(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
+    assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok]), (np.quantile(c, 0.98), c.max())
+    for k in (0, 2, 5, 9, 14, 20):
+        scale = np.maximum(np.abs(ref["cov"][k, ok]), 1e-9 * np.abs(ref["cov"][:, ok]).max(axis=0))
+        r = np.abs(out["cov"][k, ok] - ref["cov"][k, ok]) / scale
+        assert r.max() < 5e-2, (k, r.max())
+
+
+def test_fit_backward_ragged_lists_and_errors():
+    """-1 gaps inside the lists, a 3-hit track, a 2-hit track (no fit), a ragged
+    tail of tracks; argument errors."""
+    b = make_batch("find20", [15], n_tracks=333)
+    hidx = b.track_hits.copy()
+    hidx[4, ::3] = -1
+    hidx[3:, 7] = -1
+    hidx[2:, 8] = -1
+    out, ref, f = _backward_pair(b, hidx, 100.0)
+    assert out["status"][8] & 2 and ref["status"][8] & 2 and np.isnan(out["par"][:, 8]).all()
+    assert (out["status"] == ref["status"]).all()
+    ok = (ref["status"] == 0) & (f["status"] == 0)
+    assert par_errors(out["par"][:, ok], ref["par"][:, ok], ref["cov"][:, ok]).max() <= 1.0
+    from paper_1811_04141_gb300._native import MkfError
+    ctx = make_ctx(b)
+    d = upload(b)
+    lp = torch.zeros(6, b.n_seeds, device="cuda")
+    lc = torch.zeros(21, b.n_seeds, device="cuda")
+    for bad in (0.5, float("nan"), float("inf")):
+        with pytest.raises(MkfError):
+            ctx.fit_backward(d["xyz"], d["layer"], d["track_hits"], lp, lc, bad)
+    empty = torch.empty(10, 0, dtype=torch.int32, device="cuda")
+    o = ctx.fit_backward(d["xyz"], d["layer"], empty, lp[:, :0].contiguous(), lc[:, :0].contiguous(), 100.0)
+    assert o["par"].shape == (6, 0)
+
+
 def test_fit_empty_and_errors():
     b = make_batch("fit10", [13], n_tracks=10)
     ctx = make_ctx(b)
