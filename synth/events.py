@@ -90,6 +90,9 @@ class Batch:
     particle_event: np.ndarray  # int32 [n_particles]
     particle_par: np.ndarray   # float64 [6, n_particles]: state at the vertex
     meta: dict = field(default_factory=dict)
+    # seeds of overlap twins (make_batch(..., overlap=p)): for each seed, the index
+    # of the seed it repeats with one hit replaced by that hit's twin, else -1
+    seed_dup_of: np.ndarray = None
 
     @property
     def n_hits(self) -> int:
@@ -109,8 +112,14 @@ class Batch:
 
 def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: int | None = None,
                base_seed: int = BASE_SEED, ineff: float | None = None, noise_scale: float = 1.0,
-               eta_max: float | None = None, smear: bool = True):
-    """One event as a dict of per-event arrays (local hit and particle indices)."""
+               eta_max: float | None = None, smear: bool = True, overlap: float = 0.0):
+    """One event as a dict of per-event arrays (local hit and particle indices).
+
+    overlap > 0: each signal hit gets, with that probability, a second hit of the
+    same particle on the same layer (overlapping sensors: the same crossing
+    measured again with its own smearing).  These hits follow the noise hits and
+    their random numbers are drawn after everything else, so the other arrays do
+    not change."""
     cfg = get_config(config)
     layers = cfg["layers"]
     rng = _rng(config, event, base_seed)
@@ -214,15 +223,35 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
     noise_xyz = np.stack([nr * np.cos(nph), nr * np.sin(nph), nzc])
 
     n_sig_hits = pid_l.size
-    xyz64 = np.concatenate([sig_xyz, noise_xyz], axis=1)
-    layer = np.concatenate([lay_l, nz_layer]).astype(np.int32)
-    particle = np.concatenate([pid_l, np.full(nz_layer.size, -1)]).astype(np.int32)
-    true_state = np.concatenate([sig_state, np.full((6, nz_layer.size), np.nan)], axis=1)
-    true_xyz = np.concatenate([sig_true_xyz, np.full((3, nz_layer.size), np.nan)], axis=1)
+    # Overlap twins: one uniform per signal hit, then two normals per twin.
+    if overlap > 0.0:
+        twin_of = np.flatnonzero(rng.random(n_sig_hits) < overlap)
+        gt = rng.standard_normal((twin_of.size, 2)) if smear else np.zeros((twin_of.size, 2))
+    else:
+        twin_of = np.zeros(0, dtype=np.int64)
+        gt = np.zeros((0, 2))
+    tl = lay_l[twin_of]
+    tx, ty, tz = sig_true_xyz[0, twin_of], sig_true_xyz[1, twin_of], sig_true_xyz[2, twin_of]
+    trt = np.hypot(tx, ty)
+    tcyl = kinds[tl] == 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tph = np.arctan2(ty, tx) + gt[:, 0] * su[tl] / np.where(trt > 0, trt, 1.0)
+    tr = np.where(tcyl, rz[tl], trt + gt[:, 1] * sv[tl])
+    tzz = np.where(tcyl, tz + gt[:, 1] * sv[tl], rz[tl])
+    twin_xyz = np.stack([tr * np.cos(tph), tr * np.sin(tph), tzz])
+
+    xyz64 = np.concatenate([sig_xyz, noise_xyz, twin_xyz], axis=1)
+    layer = np.concatenate([lay_l, nz_layer, tl]).astype(np.int32)
+    particle = np.concatenate([pid_l, np.full(nz_layer.size, -1), pid_l[twin_of]]).astype(np.int32)
+    true_state = np.concatenate([sig_state, np.full((6, nz_layer.size), np.nan), sig_state[:, twin_of]], axis=1)
+    true_xyz = np.concatenate([sig_true_xyz, np.full((3, nz_layer.size), np.nan), sig_true_xyz[:, twin_of]], axis=1)
     nhits_p = np.bincount(pid_l, minlength=P).astype(np.int32)
     first = np.concatenate([[0], np.cumsum(nhits_p)[:-1]]).astype(np.int64)
+    # local index of each twin, and of the signal hit it repeats
+    twin_idx = n_sig_hits + nz_layer.size + np.arange(twin_of.size)
     return dict(xyz64=xyz64, layer=layer, particle=particle, true_state=true_state,
                 true_xyz=true_xyz, nhits_p=nhits_p, first_hit_p=first, n_signal=n_sig_hits,
+                twin_idx=twin_idx, twin_of=twin_of,
                 par0=np.stack([np.zeros(P), np.zeros(P), z0, q / pt, phi0, theta]))
 
 
@@ -243,7 +272,7 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
     max_hits = max([1] + [int(p["nhits_p"].max(initial=0)) for p in parts])
     offs = np.zeros(E + 1, dtype=np.int64)
     xyz64, layer, hp, ts, tx = [], [], [], [], []
-    seed_hits, seed_event, seed_part, track_hits = [], [], [], []
+    seed_hits, seed_event, seed_part, track_hits, seed_dup = [], [], [], [], []
     p_nh, p_ev, p_par = [], [], []
     pbase = 0
     for i, p in enumerate(parts):
@@ -255,14 +284,32 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
         P = p["nhits_p"].shape[0]
         ok = np.nonzero(p["nhits_p"] >= min_seed_hits)[0]
         f = p["first_hit_p"][ok]
-        seed_hits.append(np.stack([f, f + 1, f + 2]) + base)
-        seed_event.append(np.full(ok.size, i))
-        seed_part.append(ok + pbase)
+        sh = np.stack([f, f + 1, f + 2])
         th = np.full((max_hits, ok.size), -1, dtype=np.int64)
         for j in range(max_hits):
             valid = j < p["nhits_p"][ok]
-            th[j, valid] = f[valid] + j + base
-        track_hits.append(th)
+            th[j, valid] = f[valid] + j
+        dup = np.full(ok.size, -1, dtype=np.int64)
+        # a twin of a seed hit gives the particle a second seed (that hit replaced)
+        if p["twin_of"].size:
+            first_of = np.full(p["n_signal"], -1, dtype=np.int64)  # seed index of each signal hit in a seed
+            slot_of = np.full(p["n_signal"], -1, dtype=np.int64)
+            for k in range(3):
+                first_of[sh[k]] = np.arange(ok.size)
+                slot_of[sh[k]] = k
+            sel = first_of[p["twin_of"]] >= 0
+            ds, dk, dt = first_of[p["twin_of"][sel]], slot_of[p["twin_of"][sel]], p["twin_idx"][sel]
+            sh2, th2 = sh[:, ds].copy(), th[:, ds].copy()
+            sh2[dk, np.arange(ds.size)] = dt
+            th2[dk, np.arange(ds.size)] = dt
+            sh, th = np.concatenate([sh, sh2], axis=1), np.concatenate([th, th2], axis=1)
+            dup = np.concatenate([dup, ds + sum(x.shape[1] for x in seed_hits)])
+            ok = np.concatenate([ok, ok[ds]])
+        seed_hits.append(sh + base)
+        seed_event.append(np.full(ok.size, i))
+        seed_part.append(ok + pbase)
+        track_hits.append(np.where(th >= 0, th + base, -1))
+        seed_dup.append(dup)
         p_nh.append(p["nhits_p"]); p_ev.append(np.full(P, i)); p_par.append(p["par0"])
         pbase += P
     if offs[-1] >= (1 << 28) - 2:
@@ -282,4 +329,5 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
         particle_event=np.concatenate(p_ev).astype(np.int32),
         particle_par=np.concatenate(p_par, axis=1),
         meta=dict(events=events, base_seed=base_seed),
+        seed_dup_of=np.concatenate(seed_dup).astype(np.int32),
     )
