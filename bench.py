@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-events leg")
     ap.add_argument("--batched-events", type=int, default=512)
     ap.add_argument("--no-fit", action="store_true", help="skip the 10^6-track fit leg")
+    ap.add_argument("--no-post", action="store_true", help="skip the seed-cleaning / duplicate-removal timing")
     return ap.parse_args()
 
 
@@ -598,6 +599,37 @@ def run_ours(args, world, rank, local, pg):
                     "step_ms": round(ms1 + bin_ms, 4), "candidate_layers": cl1,
                     "cand_layer_updates_per_s": cl1 / ((ms1 + bin_ms) * 1e-3)}
 
+    # seed cleaning (fit over each seed's three hits + duplicate test) and
+    # duplicate-track removal on the step's found tracks: a separate object
+    post = None
+    if rank == 0 and world == 1 and not args.no_post:
+        def timed(fn, reps=20):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a, b_ in e2:
+                flush.fill_(1.0)
+                a.record(stream)
+                fn()
+                b_.record(stream)
+            torch.cuda.synchronize()
+            return float(np.mean([a.elapsed_time(b_) for a, b_ in e2]))
+        sfit = ctx.fit(xyz, layer, sh)
+        keep_s = ctx.seeds_clean(sh, batch.n_hits, sfit["par"])
+        keep_t = ctx.tracks_dedup(out["hits"], batch.n_hits, out["n_hits"], out["chi2"])
+        ms_clean = timed(lambda: (ctx.fit(xyz, layer, sh, out=sfit),
+                                  ctx.seeds_clean(sh, batch.n_hits, sfit["par"], keep=keep_s)))
+        ms_dedup = timed(lambda: ctx.tracks_dedup(out["hits"], batch.n_hits, out["n_hits"], out["chi2"], keep=keep_t))
+        n_seeds = int(sh.shape[1])
+        post = {"workload": "the same 20 events: seed cleaning (fit over the 3 seed hits, then the shared-hit and "
+                            "(q/pT, eta, phi) duplicate test) and duplicate-track removal on the found tracks "
+                            "(shared hits >= half the shorter track)",
+                "seed_clean_ms": round(ms_clean, 4), "seeds_per_s": n_seeds / (ms_clean * 1e-3),
+                "seeds_removed": int((keep_s == 0).sum().item()),
+                "dedup_ms": round(ms_dedup, 4), "tracks_per_s": n_seeds / (ms_dedup * 1e-3),
+                "tracks_removed": int((keep_t == 0).sum().item())}
+
     # end to end through the public API with host buffers: every step copies its
     # inputs from pinned host memory and reads its tracks back; copies run on
     # their own streams, overlapped with the previous / next step's compute
@@ -637,7 +669,7 @@ def run_ours(args, world, rank, local, pg):
                    "l2": "flushed between steps (256 MiB write, outside the per-step CUDA events)",
                    "wall_s_timed_region": round(wall, 3), "parallelism": f"events sharded, {world} GPU(s)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "learned": learned,
-        "batched": batched, "fit": fit, "best_hit": best_hit,
+        "batched": batched, "fit": fit, "best_hit": best_hit, "post": post,
         "gpu_launches": launches_per_step * K,
     }
     if rank == 0:

@@ -241,6 +241,36 @@ mkf_status mkf_fit_backward(mkf_ctx *ctx, const float *xyz, const int32_t *hit_l
                             int32_t *ndf, uint32_t *status);
 
 /* ------------------------------------------------------------------------ */
+/* Seed cleaning and duplicate-track removal (Sec. 2.2: repeated seeds of one */
+/* particle are removed using the identity of their hits and their fitted     */
+/* pT, eta and phi; Sec. 3: duplicate tracks are to be removed after finding) */
+/* ------------------------------------------------------------------------ */
+
+/* Seed cleaning.  seed_hits [3][n_seeds] (device, hit indices; entries outside
+ * [0, n_hits) are ignored), seed_par [6][n_seeds] (device, the seeds' fitted
+ * states, e.g. mkf_fit over their three hits; rows 3, 4, 5 = q/pT, phi, theta
+ * are used).  Two seeds are duplicates when they share at least one hit and
+ * |d(q/pT)| <= max_dqpt, |d eta| <= max_deta, |d phi| (wrapped) <= max_dphi,
+ * eta = -ln tan(theta/2), differences taken in double.  keep [n_seeds]
+ * (device, written): 0 when a duplicate with a lower index exists, else 1 (a
+ * rule that needs no processing order).  Errors: MKF_ERR_ARG (negative sizes
+ * or tolerances, NULL pointers with n_seeds > 0), MKF_ERR_CAPACITY, MKF_ERR_CUDA. */
+mkf_status mkf_seeds_clean(mkf_ctx *ctx, const int32_t *seed_hits, int32_t n_seeds, int32_t n_hits,
+                           const float *seed_par, float max_dqpt, float max_deta, float max_dphi, int32_t *keep);
+
+/* Duplicate-track removal.  hit_idx [max_hits][n] (device, each track's hits,
+ * -1 = none; e.g. mkf_find's hit_idx), track_nhits [n] and chi2 [n] (device,
+ * e.g. mkf_find's n_hits and chi2).  Two tracks are duplicates when the hits
+ * they share number at least max(1, min_frac x the smaller of their hit
+ * counts) (0 <= min_frac <= 1; a hit listed twice by one track counts once).
+ * keep [n] (device, written): 0 when a duplicate ranks above the track -- more
+ * hits, then lower chi2, then lower index -- else 1.  Errors: MKF_ERR_ARG,
+ * MKF_ERR_CAPACITY (max_hits > MKF_MAX_LAYERS + 8, n_hits > MKF_MAX_HITS),
+ * MKF_ERR_CUDA. */
+mkf_status mkf_tracks_dedup(mkf_ctx *ctx, const int32_t *hit_idx, int32_t max_hits, int32_t n, int32_t n_hits,
+                            const int32_t *track_nhits, const float *chi2, float min_frac, int32_t *keep);
+
+/* ------------------------------------------------------------------------ */
 /* Finding (Sec. 1: layer-by-layer finding with selection of the best chi2   */
 /* extensions before the final Kalman updates)                               */
 /* ------------------------------------------------------------------------ */

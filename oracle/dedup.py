@@ -46,7 +46,7 @@ def _shared_pairs(hit_lists, n_hits):
     return s.row[off], s.col[off], s.data[off]
 
 
-def clean_seeds(seed_hits, n_hits, seed_par, max_dqpt=0.15, max_deta=0.02, max_dphi=0.02):
+def clean_seeds(seed_hits, n_hits, seed_par, max_dqpt=0.5, max_deta=0.02, max_dphi=0.02):
     """keep [n] (bool) for seeds seed_hits [3][n] with fitted states seed_par [6][n]
     (q/pT, phi, theta in rows 3, 4, 5)."""
     seed_hits = np.asarray(seed_hits)

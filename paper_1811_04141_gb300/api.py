@@ -1,5 +1,6 @@
 """Python binding of the C ABI with the same names (mkf_create, mkf_geometry_load,
-mkf_hits_bin, mkf_fit, mkf_fit_backward, mkf_find, mkf_sync, mkf_destroy), plus a small Context
+mkf_hits_bin, mkf_fit, mkf_fit_backward, mkf_seeds_clean, mkf_tracks_dedup, mkf_find, mkf_sync,
+mkf_destroy), plus a small Context
 class.  PyTorch supplies device memory and streams; this module only checks
 tensor shapes, dtypes and devices and passes raw pointers to libmkf.so.
 """
@@ -189,6 +190,34 @@ def mkf_fit_backward(ctx, xyz, hit_layer, hit_idx, last_par, last_cov, inflate=1
     return out
 
 
+def mkf_seeds_clean(ctx, seed_hits, n_hits, seed_par, max_dqpt=0.5, max_deta=0.02, max_dphi=0.02, keep=None,
+                    device: int | None = None):
+    """keep [n_seeds] int32 (1 = keep, 0 = duplicate of a lower-index seed)."""
+    n = seed_hits.shape[1]
+    _need(seed_hits, "seed_hits", torch.int32, (3, n), device)
+    _need(seed_par, "seed_par", torch.float32, (6, n), device)
+    if keep is None:
+        keep = torch.empty(n, dtype=torch.int32, device=seed_hits.device)
+    N.check("mkf_seeds_clean", N.lib().mkf_seeds_clean(ctx, _ptr(seed_hits), n, int(n_hits), _ptr(seed_par),
+                                                       C.c_float(max_dqpt), C.c_float(max_deta), C.c_float(max_dphi),
+                                                       _ptr(keep)))
+    return keep
+
+
+def mkf_tracks_dedup(ctx, hit_idx, n_hits, track_nhits, chi2, min_frac=0.5, keep=None, device: int | None = None):
+    """keep [n] int32 (1 = keep, 0 = a better duplicate exists)."""
+    max_hits, n = hit_idx.shape
+    _need(hit_idx, "hit_idx", torch.int32, (max_hits, n), device)
+    _need(track_nhits, "track_nhits", torch.int32, (n,), device)
+    _need(chi2, "chi2", torch.float32, (n,), device)
+    if keep is None:
+        keep = torch.empty(n, dtype=torch.int32, device=hit_idx.device)
+    N.check("mkf_tracks_dedup", N.lib().mkf_tracks_dedup(ctx, _ptr(hit_idx), max_hits, n, int(n_hits),
+                                                         _ptr(track_nhits), _ptr(chi2), C.c_float(min_frac),
+                                                         _ptr(keep)))
+    return keep
+
+
 def find_params(n_best=10, chi2_cut=30.0, max_consec_miss=3, block_threads=0, mlp_bf16=None, mlp_tau=0.0,
                 feat=None, event_times=None) -> N.MkfFindParams:
     prm = N.MkfFindParams(int(n_best), float(chi2_cut), int(max_consec_miss), int(block_threads))
@@ -326,6 +355,13 @@ class Context:
 
     def fit(self, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, out=None):
         return mkf_fit(self.handle, xyz, hit_layer, hit_idx, seed_par, seed_cov, out, self.device)
+
+    def seeds_clean(self, seed_hits, n_hits, seed_par, max_dqpt=0.5, max_deta=0.02, max_dphi=0.02, keep=None):
+        return mkf_seeds_clean(self.handle, seed_hits, n_hits, seed_par, max_dqpt, max_deta, max_dphi, keep,
+                               self.device)
+
+    def tracks_dedup(self, hit_idx, n_hits, track_nhits, chi2, min_frac=0.5, keep=None):
+        return mkf_tracks_dedup(self.handle, hit_idx, n_hits, track_nhits, chi2, min_frac, keep, self.device)
 
     def fit_backward(self, xyz, hit_layer, hit_idx, last_par, last_cov, inflate=100.0, out=None):
         return mkf_fit_backward(self.handle, xyz, hit_layer, hit_idx, last_par, last_cov, inflate, out, self.device)

@@ -338,6 +338,23 @@ mkf_status run_binning(mkf_ctx *ctx, const float *xyz, const int32_t *layer, con
 
 }  // namespace
 
+int64_t mkf_scan_tilesums(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+mkf_status mkf_run_scan(cudaStream_t s, const int32_t *counts, int64_t n, int32_t *tilesums, int32_t *offsets) {
+    const int64_t nblk = mkf_scan_tilesums(n);
+    if (nblk == 0) {
+        MKF_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int32_t), s));
+        return MKF_OK;
+    }
+    scan_tiles_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n, tilesums);
+    MKF_CUDA_TRY(cudaGetLastError());
+    scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(tilesums, nblk, offsets, n);
+    MKF_CUDA_TRY(cudaGetLastError());
+    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n, tilesums, offsets);
+    MKF_CUDA_TRY(cudaGetLastError());
+    return MKF_OK;
+}
+
 extern "C" void mkf_hitbins_free(mkf_hitbins *b) {
     if (!b) return;
     DeviceGuard g(b->device);

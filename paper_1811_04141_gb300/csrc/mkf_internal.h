@@ -80,3 +80,8 @@ struct DeviceGuard {
 
 // Context scratch of at least `bytes` (grown with cudaMalloc, never shrunk).
 mkf_status mkf_scratch(mkf_ctx *ctx, size_t bytes, void **out);
+
+// Exclusive scan of counts [n] into offsets [n + 1] (offsets[n] = the total),
+// enqueued on `s`; tilesums is scratch of mkf_scan_tilesums(n) ints.
+int64_t mkf_scan_tilesums(int64_t n);
+mkf_status mkf_run_scan(cudaStream_t s, const int32_t *counts, int64_t n, int32_t *tilesums, int32_t *offsets);

@@ -106,10 +106,13 @@ def _seed_fit(b):
     return r["par"].astype(np.float32), r["status"]
 
 
-def test_seed_cleaning_on_overlap_events():
+@pytest.mark.parametrize("cfg", ["find20", "dense45"])
+def test_seed_cleaning_on_overlap_events(cfg):
     """Every repeated seed of a particle (one hit replaced by its twin) is removed;
-    seeds of different particles never are."""
-    b = make_batch("find20", [0, 1], n_tracks=400, overlap=0.15)
+    seeds of different particles never are (default tolerances; on dense45 the
+    inner disks' short lever arm spreads the 3-hit q/pT of a repeated seed up to
+    0.2 c/GeV from its original)."""
+    b = make_batch(cfg, [0, 1], n_tracks=400, overlap=0.15)
     par, st = _seed_fit(b)
     assert (st == 0).all()
     keep = D.clean_seeds(b.seed_hits, b.n_hits, par)
