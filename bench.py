@@ -655,7 +655,7 @@ def run_ours(args, world, rank, local, pg):
     if rank == 0 and world == 1 and not args.no_fit:
         fit = fit_leg(dev)
 
-    launches_per_step = 7  # bin_keys, scan_tiles, scan_blocksums, scan_write, scatter, seed, find
+    launches_per_step = 6  # bin_keys, scan_tiles, scan_write, scatter, seed, find
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(step_ms_max, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -27,6 +27,7 @@ struct BinArgs {
     uint8_t *layer8;
     float *zhit;
     int32_t *counts;
+    int32_t *slot;  // [n_hits] each hit's place among its bin's hits (the inverse-map buffer)
     mkf_fault *fault;
 };
 
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_keys_kernel(const __grid_cons
         const int k = ev * A.G.bins_per_event + Ld.bin_base + pb * Ld.nzr + zb;
         A.key[i] = k;
         A.layer8[i] = static_cast<uint8_t>(l[j]);
-        atomicAdd(&A.counts[k], 1);
+        A.slot[i] = atomicAdd(&A.counts[k], 1);
     }
 }
 
@@ -161,47 +162,59 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int32_t 
     if (threadIdx.x == 0) blocksums[blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_blocksums_kernel(int32_t *blocksums, int64_t nb, int32_t *offsets,
-                                                                    int64_t n) {
-    int carry = 0;
-    for (int64_t base = 0; base < nb; base += kScanTile) {
-        int vals[kScanPerThread];
-        int t = block_scan_tile(blocksums, nb, base, vals);
-        __syncthreads();
+// Offsets of one tile: the tile's exclusive scan plus the sum of the tile
+// totals before it (summed by the block itself, so no pass over the totals is
+// needed); the last tile also writes the grand total offsets[n].  zero_counts:
+// the block clears the counts it has read, leaving the histogram ready for the
+// next call.
+__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(int32_t *counts, int64_t n, const int32_t *tilesums,
+                                                                int64_t nblk, int32_t *offsets, bool zero_counts) {
+    __shared__ int red[kScanThreads / 32];
+    __shared__ int add_s;
+    int part = 0;
+    for (int64_t b = threadIdx.x; b < (int64_t)blockIdx.x; b += kScanThreads) part += tilesums[b];
 #pragma unroll
-        for (int k = 0; k < kScanPerThread; ++k) {
-            int64_t idx = base + (int64_t)threadIdx.x * kScanPerThread + k;
-            if (idx < nb) blocksums[idx] = vals[k] + carry;
-        }
-        carry += t;
-        __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = red[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) add_s = v;
     }
-    if (threadIdx.x == 0) offsets[n] = carry;
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const int32_t *counts, int64_t n,
-                                                                const int32_t *blocksums, int32_t *offsets) {
+    __syncthreads();
+    const int add = add_s;
     int vals[kScanPerThread];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    block_scan_tile(counts, n, base, vals);
-    const int add = blocksums[blockIdx.x];
+    const int total = block_scan_tile(counts, n, base, vals);
     const int64_t first = base + (int64_t)threadIdx.x * kScanPerThread;
-    if (first + kScanPerThread <= n && (reinterpret_cast<uintptr_t>(offsets + first) & 15) == 0) {
+    if (first + kScanPerThread <= n && (reinterpret_cast<uintptr_t>(offsets + first) & 15) == 0 &&
+        (reinterpret_cast<uintptr_t>(counts + first) & 15) == 0) {
         int4 *q = reinterpret_cast<int4 *>(offsets + first);
 #pragma unroll
         for (int k = 0; k < kScanPerThread / 4; ++k)
             q[k] = make_int4(vals[4 * k] + add, vals[4 * k + 1] + add, vals[4 * k + 2] + add, vals[4 * k + 3] + add);
+        if (zero_counts) {
+            int4 *c = reinterpret_cast<int4 *>(counts + first);
+#pragma unroll
+            for (int k = 0; k < kScanPerThread / 4; ++k) c[k] = make_int4(0, 0, 0, 0);
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < kScanPerThread; ++k)
-            if (first + k < n) offsets[first + k] = vals[k] + add;
+            if (first + k < n) {
+                offsets[first + k] = vals[k] + add;
+                if (zero_counts) counts[first + k] = 0;
+            }
     }
+    if (blockIdx.x == nblk - 1 && threadIdx.x == 0) offsets[n] = add + total;
 }
 
 __global__ void __launch_bounds__(kBinThreads) scatter_kernel(const float *X, const float *Y, const float *Z,
                                                               const int32_t *key, const uint8_t *layer8, int32_t n_hits,
                                                               unsigned long long disk_mask, const int32_t *offsets,
-                                                              int32_t *counts, float4 *rec, int32_t *inv) {
+                                                              float4 *rec, int32_t *inv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_hits) return;
     const int k = key[i];
@@ -209,10 +222,11 @@ __global__ void __launch_bounds__(kBinThreads) scatter_kernel(const float *X, co
         inv[i] = -1;
         return;
     }
-    // slots are handed out from the front of the bin in arrival order, which
-    // follows the original index for most bins (warps run roughly in order), so
-    // the in-bin ordering pass usually finds a bin already in order
-    const int pos = offsets[k + 1] - atomicSub(&counts[k], 1);
+    // the key pass left the hit's place among its bin's hits in inv[i]; places
+    // were handed out in arrival order, which follows the original index for
+    // most bins (warps run roughly in order), so the in-bin ordering pass
+    // usually finds a bin already in order
+    const int pos = offsets[k] + inv[i];
     const float x = X[i], y = Y[i], z = Z[i];
     const float zr = ((disk_mask >> layer8[i]) & 1ull) == 0 ? z : sqrtf(fmaf(x, x, y * y));
     rec[pos] = make_float4(x, y, zr, __int_as_float(i));
@@ -286,9 +300,11 @@ mkf_status grow(mkf_hitbins *b, int64_t n_hits, int64_t n_bins) {
     return MKF_OK;
 }
 
-// The binning pipeline on given buffers: keys and histogram, exclusive scan,
-// scatter, and (order_bins) the in-bin ordering by original index.  counts [n_bins] must be zero on entry; tilesums
-// [ceil(n_bins / kScanTile)] is scan scratch.
+// The binning pipeline on given buffers: keys, histogram and each hit's place
+// in its bin; exclusive scan (which clears the histogram again); scatter; and
+// (order_bins) the in-bin ordering by original index.  counts [n_bins] must be
+// zero on entry and is zero on exit; tilesums [ceil(n_bins / kScanTile)] is
+// scan scratch; inv carries the places from the key pass to the scatter.
 mkf_status run_binning(mkf_ctx *ctx, const float *xyz, const int32_t *layer, const int32_t *event_offsets,
                        int32_t n_events, int32_t n_hits, int64_t n_bins, int32_t *counts, int32_t *tilesums,
                        int32_t *key, uint8_t *layer8, float *zhit, int32_t *offsets, float4 *rec, int32_t *inv,
@@ -308,6 +324,7 @@ mkf_status run_binning(mkf_ctx *ctx, const float *xyz, const int32_t *layer, con
         A.layer8 = layer8;
         A.zhit = zhit;
         A.counts = counts;
+        A.slot = inv;
         A.fault = ctx->fault;
         bin_keys_kernel<<<(n_hits + kBinThreads * kBinItems - 1) / (kBinThreads * kBinItems), kBinThreads, 0, s>>>(A);
         MKF_CUDA_TRY(cudaGetLastError());
@@ -315,16 +332,14 @@ mkf_status run_binning(mkf_ctx *ctx, const float *xyz, const int32_t *layer, con
     const int64_t nblk = (n_bins + kScanTile - 1) / kScanTile;
     scan_tiles_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n_bins, tilesums);
     MKF_CUDA_TRY(cudaGetLastError());
-    scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(tilesums, nblk, offsets, n_bins);
-    MKF_CUDA_TRY(cudaGetLastError());
-    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n_bins, tilesums, offsets);
+    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n_bins, tilesums, nblk, offsets, true);
     MKF_CUDA_TRY(cudaGetLastError());
     if (n_hits > 0) {
         unsigned long long disk_mask = 0;
         for (int l = 0; l < ctx->geom.n_layers; ++l)
             if (ctx->geom.L[l].kind == 1) disk_mask |= 1ull << l;
         scatter_kernel<<<(n_hits + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(xyz, xyz + n_hits, xyz + 2 * (int64_t)n_hits, key, layer8,
-                                                           n_hits, disk_mask, offsets, counts, rec, inv);
+                                                           n_hits, disk_mask, offsets, rec, inv);
         MKF_CUDA_TRY(cudaGetLastError());
         if (order_bins) {
             bin_sort_kernel<<<(unsigned)((n_bins + kSortBins - 1) / kSortBins), kSortBins, 0, s>>>(offsets, n_bins, rec,
@@ -348,9 +363,9 @@ mkf_status mkf_run_scan(cudaStream_t s, const int32_t *counts, int64_t n, int32_
     }
     scan_tiles_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n, tilesums);
     MKF_CUDA_TRY(cudaGetLastError());
-    scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(tilesums, nblk, offsets, n);
-    MKF_CUDA_TRY(cudaGetLastError());
-    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(counts, n, tilesums, offsets);
+    // the counts stay as they are (the caller hands out places from them)
+    scan_write_kernel<<<(unsigned)nblk, kScanThreads, 0, s>>>(const_cast<int32_t *>(counts), n, tilesums, nblk, offsets,
+                                                              false);
     MKF_CUDA_TRY(cudaGetLastError());
     return MKF_OK;
 }
