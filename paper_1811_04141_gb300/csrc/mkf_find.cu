@@ -870,21 +870,18 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             I.Ivv = __shfl_sync(kFull, I.Ivv, src);
             bk = unpack_book(bw);
             live = got;
-            if (live) {
-                // the hit's residual and chi2 from the parent's list
+            {
+                // the hit's residual and chi2 from the parent's list (every lane
+                // reads an in-bounds row; the lanes that take a hit keep it)
                 const uint32_t code = rec & kHitMask;
-                float u = 0.f, v = 0.f, x2 = 0.f;
-                if (code < kCodeMiss) {
-                    const int at = sel[lane] * 32 + src;
-                    u = lu[at];
-                    v = lv[at];
-                    x2 = lchi[at];
-                }
-                pend = true;
+                const bool hit = got && code < kCodeMiss;
+                const int at = min(max(got ? sel[lane] : 0, 0), N - 1) * 32 + src;
+                const float u = lu[at], v = lv[at], x2 = lchi[at];
+                pend = got;
                 pcode = code;
-                pu = u;
-                pv = v;
-                px2 = x2;
+                pu = hit ? u : 0.f;
+                pv = hit ? v : 0.f;
+                px2 = hit ? x2 : 0.f;
             }
             ++step;
             __syncwarp();
