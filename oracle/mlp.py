@@ -4,8 +4,9 @@ A 2-layer perceptron, 12 features -> 64 ReLU units -> 1 logit, scores a
 (candidate, compatible hit) pair; pairs with logit below a threshold are dropped
 before the N-best selection.  Training minimises the mean binary cross-entropy
 against truth labels with Adam.  The paper has no learned component; the
-network, its features and its training are the BASELINE configuration's
-"learned pruning" pattern.  Written as plain matrix algebra in float64.
+network, its features and its training are this project's learned-pruning
+workload (12 features, 64 hidden units, bfloat16 weights).  Written as plain
+matrix algebra in float64.
 
 Parameter vector layout (897 values): W1[64][12] (row = hidden unit), b1[64],
 w2[64], b2.  The forward pass of the GPU uses the weights rounded to bfloat16;

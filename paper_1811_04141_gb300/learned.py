@@ -7,8 +7,8 @@ belongs to the seed's particle), the network is trained by mkf_mlp_train_step
 (forward, backward and Adam run in libmkf's CUDA kernels; torch only holds the
 buffers and draws the batch permutation), and the pruning threshold is the
 largest one that keeps the finding efficiency within a tolerance of the plain
-finder.  The plain chi2 selection stays the judge: efficiency and fake rate are
-computed from the found hit lists and the truth.
+finder.  The plain chi2 selection stays the reference: efficiency and fake rate
+are computed from the found hit lists and the truth.
 """
 from __future__ import annotations
 
