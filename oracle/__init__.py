@@ -49,7 +49,7 @@ def _load():
             lib = C.CDLL(_LIB_PATH)
             d, i32, i64, u64 = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)
             u32 = C.POINTER(C.c_uint32)
-            geom = [C.c_int, i32, d, d, d, d, d, C.c_double, C.c_int, d, u64]
+            geom = [C.c_int, i32, d, d, d, d, d, d, C.c_double, C.c_int, d, u64]
             lib.or_propagate.argtypes = geom + [d, C.c_int, d, d, d]
             lib.or_propagate.restype = C.c_int
             lib.or_helix_move.argtypes = geom + [d, C.c_double, d]
@@ -60,6 +60,8 @@ def _load():
             lib.or_update.restype = C.c_double
             lib.or_seed.argtypes = geom + [d, d, d, C.c_int, d, d]
             lib.or_seed.restype = C.c_int
+            lib.or_scattering.argtypes = geom + [C.c_int, d, d]
+            lib.or_scattering.restype = C.c_int
             lib.or_fit.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, d, d, d, i32, u32]
             lib.or_fit.restype = C.c_int
             lib.or_fit_backward.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, C.c_double, d, d,
@@ -91,6 +93,8 @@ class Geometry:
         self.hi = np.ascontiguousarray([d["hi"] for d in layers], dtype=np.float64)
         self.su = np.ascontiguousarray([d["sigma_u"] for d in layers], dtype=np.float64)
         self.sv = np.ascontiguousarray([d["sigma_v"] for d in layers], dtype=np.float64)
+        # material: radiation lengths at normal incidence (optional "x0" key)
+        self.x0 = np.ascontiguousarray([d.get("x0", 0.0) for d in layers], dtype=np.float64)
         self.bz = float(bz)
         edges = [] if region_edges is None else list(region_edges)
         self.n_regions = len(edges) + 1
@@ -101,8 +105,9 @@ class Geometry:
 
     def args(self):
         return [self.n, _p(self.kind, C.c_int32), _p(self.rz, C.c_double), _p(self.lo, C.c_double),
-                _p(self.hi, C.c_double), _p(self.su, C.c_double), _p(self.sv, C.c_double), self.bz,
-                self.n_regions, _p(self.edges, C.c_double), _p(self.masks, C.c_uint64)]
+                _p(self.hi, C.c_double), _p(self.su, C.c_double), _p(self.sv, C.c_double),
+                _p(self.x0, C.c_double), self.bz, self.n_regions, _p(self.edges, C.c_double),
+                _p(self.masks, C.c_uint64)]
 
 
 def _f64(a):
@@ -147,6 +152,16 @@ def update(geo: Geometry, layer, hit, p, Cm):
     chi2 = lib.or_update(*geo.args(), int(layer), _p(hit, C.c_double), _p(p, C.c_double), _p(Cm, C.c_double),
                          _p(r, C.c_double), _p(S, C.c_double), _p(Cj, C.c_double))
     return p, Cm.reshape(6, 6), float(chi2), r, S.reshape(2, 2), Cj.reshape(6, 6)
+
+
+def scattering(geo: Geometry, layer, p):
+    """Multiple-scattering noise (6x6) the material of `layer` adds at state p."""
+    lib = _load()
+    p = _f64(p)
+    Q = np.zeros(36)
+    if lib.or_scattering(*geo.args(), int(layer), _p(p, C.c_double), _p(Q, C.c_double)) < 0:
+        raise ValueError("bad arguments")
+    return Q.reshape(6, 6)
 
 
 def seed(geo: Geometry, h1, h2, h3, layer1):

@@ -58,6 +58,7 @@ typedef struct {
     int n;
     int kind[OR_MAXL];
     double rz[OR_MAXL], lo[OR_MAXL], hi[OR_MAXL], su[OR_MAXL], sv[OR_MAXL];
+    double x0[OR_MAXL]; /* material: radiation lengths at normal incidence */
     double bz;
     int n_regions;
     double edges[OR_MAXR];
@@ -65,8 +66,8 @@ typedef struct {
 } geom_t;
 
 static int geom_init(geom_t *g, int n_layers, const int32_t *kind, const double *rz, const double *lo,
-                     const double *hi, const double *su, const double *sv, double bz, int n_regions,
-                     const double *edges, const uint64_t *masks) {
+                     const double *hi, const double *su, const double *sv, const double *x0, double bz,
+                     int n_regions, const double *edges, const uint64_t *masks) {
     if (n_layers < 1 || n_layers > OR_MAXL) return -1;
     if (n_regions < 1 || n_regions > OR_MAXR) return -1;
     g->n = n_layers;
@@ -77,6 +78,7 @@ static int geom_init(geom_t *g, int n_layers, const int32_t *kind, const double 
         g->hi[i] = hi[i];
         g->su[i] = su[i];
         g->sv[i] = sv[i];
+        g->x0[i] = x0 ? x0[i] : 0.0;
     }
     g->bz = bz;
     g->n_regions = n_regions;
@@ -234,6 +236,37 @@ static void transport(const double J[36], const double C[36], double Co[36]) {
 
 /* Residual (u, v) of hit (xh, yh, zh) against a state on layer l's surface and
  * the 2x6 projection H. */
+/* Multiple scattering in the material of layer l (x0[l] radiation lengths at
+ * normal incidence), added to the covariance of the state p on the layer's
+ * surface.  theta0 = 0.0136 GeV / (beta p) sqrt(x) (1 + 0.038 ln(x / beta^2))
+ * (Highland, as tabulated by the Particle Data Group; unit charge, pion mass
+ * 0.13957 GeV) for the path x = x0 / |cos a|, a = the angle between the
+ * direction and the surface normal (radial on a cylinder, z on a disk).  The
+ * projected angles receive independent noise: Var(theta) += theta0^2,
+ * Var(phi) += theta0^2 / sin^2(theta); the momentum magnitude is unchanged, so
+ * q/pT = q / (p sin theta) follows theta: d(q/pT) = -(q/pT) cot(theta) d(theta),
+ * giving Var(q/pT) += (q/pT cot theta theta0)^2 and
+ * Cov(q/pT, theta) += -(q/pT) cot(theta) theta0^2.  Kicks along the path do not
+ * move the position on the layer, so nothing else changes. */
+#define OR_PION_MASS 0.13957
+static void add_scattering(const geom_t *g, int l, const double p[6], double C[36]) {
+    const double t = g->x0[l];
+    if (!(t > 0.0)) return;
+    const double st = sin(p[5]), ct = cos(p[5]);
+    double cosa = g->kind[l] == 0 ? fabs(st * cos(p[4] - atan2(p[1], p[0]))) : fabs(ct);
+    if (cosa < 1e-6) cosa = 1e-6;
+    const double pm = 1.0 / (fabs(p[3]) * fabs(st));
+    const double beta = pm / sqrt(pm * pm + OR_PION_MASS * OR_PION_MASS);
+    const double x = t / cosa;
+    const double th0 = 0.0136 / (beta * pm) * sqrt(x) * (1.0 + 0.038 * log(x / (beta * beta)));
+    const double v = th0 * th0, wc = p[3] * ct / st;
+    C[5 * 6 + 5] += v;
+    C[4 * 6 + 4] += v / (st * st);
+    C[3 * 6 + 3] += wc * wc * v;
+    C[3 * 6 + 5] -= wc * v;
+    C[5 * 6 + 3] -= wc * v;
+}
+
 static void residual(const geom_t *g, int l, const double p[6], double xh, double yh, double zh,
                      double r[2], double H[12]) {
     double phip = atan2(p[1], p[0]);
@@ -380,9 +413,9 @@ static void unpack21(const double *in, int64_t stride, double C[36]) {
 
 #define GEOM_ARGS                                                                                     \
     int n_layers, const int32_t *kind, const double *rz, const double *lo, const double *hi,        \
-        const double *su, const double *sv, double bz, int n_regions, const double *edges,           \
-        const uint64_t *masks
-#define GEOM_PASS n_layers, kind, rz, lo, hi, su, sv, bz, n_regions, edges, masks
+        const double *su, const double *sv, const double *x0, double bz, int n_regions,              \
+        const double *edges, const uint64_t *masks
+#define GEOM_PASS n_layers, kind, rz, lo, hi, su, sv, x0, bz, n_regions, edges, masks
 
 /* Propagate p to layer l: writes q, J (6x6 row-major) and s.  Returns 1 on
  * success, 0 if unreachable, -1 on bad arguments. */
@@ -446,6 +479,14 @@ double or_update(GEOM_ARGS, int l, const double *hit, double *p, double *C, doub
     return chi2;
 }
 
+/* Scattering noise of layer l at the state p (on its surface), added to C (6x6). */
+int or_scattering(GEOM_ARGS, int l, const double *p, double *C) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS) || l < 0 || l >= g.n) return -1;
+    add_scattering(&g, l, p, C);
+    return 1;
+}
+
 /* Seed state and prior covariance (6x6) from three hits; returns 1 or 0. */
 int or_seed(GEOM_ARGS, const double *h1, const double *h2, const double *h3, int layer1, double *p, double *C) {
     geom_t g;
@@ -502,6 +543,7 @@ int or_fit(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_laye
                     transport(J, C, Cn);
                     memcpy(p, q, sizeof(q));
                     memcpy(C, Cn, sizeof(Cn));
+                    add_scattering(&g, l, p, C);
                 }
                 double H[12], r[2], S[4], Si[4], HC[12];
                 residual(&g, l, p, X[hid], Y[hid], Z[hid], r, H);
@@ -585,6 +627,10 @@ int or_fit_backward(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t 
                     memcpy(p, q, sizeof(q));
                     memcpy(C, Cn, sizeof(Cn));
                 }
+                /* reversed in time, the layer's material follows its hit; the
+                 * noise does not touch what the hit measures, so it is added
+                 * here at every hit, the last one included */
+                add_scattering(&g, l, p, C);
                 double H[12], r[2], S[4], Si[4], HC[12];
                 residual(&g, l, p, X[hid], Y[hid], Z[hid], r, H);
                 if (!residual_cov(&g, l, C, H, S, Si, HC)) { st |= OR_ST_BADS; continue; }
@@ -862,6 +908,7 @@ static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *ou
                 transport(J, c0.C, Cn);
                 memcpy(c0.p, q, sizeof(q));
                 memcpy(c0.C, Cn, sizeof(Cn));
+                add_scattering(g, l, c0.p, c0.C);
             }
             double H[12], r[2], S[4], Si[4], HC[12];
             residual(g, l, c0.p, f->X[hid], f->Y[hid], f->Z[hid], r, H);
@@ -948,6 +995,7 @@ static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *ou
             transport(J, c->C, Cn);
             memcpy(c->p, q, sizeof(q));
             memcpy(c->C, Cn, sizeof(Cn));
+            add_scattering(g, l, c->p, c->C);
             cnt[0]++;
             /* window half-widths from S at the predicted state */
             double H[12], rr[2], S[4], Si[4], HC[12];

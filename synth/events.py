@@ -64,6 +64,94 @@ def _cylinder_crossings(h, phi0, radii, s_max):
     return s
 
 
+PION_MASS = 0.13957  # GeV; mass hypothesis for the scattering angle
+
+
+def _highland(p, x0_path):
+    """RMS projected multiple-scattering angle (Highland, as tabulated by the
+    Particle Data Group) for momentum p (GeV) through x0_path radiation lengths,
+    unit charge, pion mass."""
+    beta = p / np.sqrt(p * p + PION_MASS * PION_MASS)
+    t = np.maximum(x0_path, 1e-12)
+    return 0.0136 / (beta * p) * np.sqrt(t) * (1.0 + 0.038 * np.log(t / (beta * beta)))
+
+
+def _cylinder_path_from(x, y, phi, h, R):
+    """Transverse path from (x, y) with azimuth phi and turning rate h to the
+    first crossing of radius R ahead (NaN if none): the intersection of the
+    particle's circle (centre c, radius 1/|h|) with the circle of radius R; the
+    straight line for h = 0."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        b = x * np.cos(phi) + y * np.sin(phi)
+        disc = b * b - (x * x + y * y - R * R)
+        s_line = np.where(disc >= 0, -b + np.sqrt(np.maximum(disc, 0.0)), np.nan)
+        hs = np.where(h == 0.0, 1.0, h)
+        cx, cy = x - np.sin(phi) / hs, y + np.cos(phi) / hs
+        A, B = 2.0 * cx / hs, -2.0 * cy / hs
+        M = np.hypot(A, B)
+        qv = (R * R - cx * cx - cy * cy - 1.0 / (hs * hs)) / M
+        a = np.arcsin(np.clip(qv, -1.0, 1.0))
+        d = np.arctan2(B, A)
+        best = np.full(np.shape(x), np.inf)
+        for u in (a - d, np.pi - a - d):
+            du = np.where(hs > 0, u - phi, phi - u)
+            du = np.mod(du, 2.0 * np.pi)
+            du = np.where(du <= 1e-12, 2.0 * np.pi, du)
+            best = np.minimum(best, du / np.abs(hs))
+        s_helix = np.where(np.abs(qv) <= 1.0, best, np.nan)
+    return np.where(h == 0.0, s_line, s_helix)
+
+
+def _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, x0, rng_ms, s_max):
+    """Crossings of every cylinder (in radius order) with a multiple-scattering
+    kick at each one crossed inside its z extent: the particle moves on a helix
+    from crossing to crossing; at a crossing its polar angle and azimuth receive
+    Gaussian kicks of width theta0 (Highland, path x0 / |cos| of the angle to
+    the cylinder normal) and theta0 / sin(theta), the momentum magnitude staying
+    the same (so q/pT follows theta).  Returns per (particle, layer) the path
+    from the vertex, the crossing point, and (q/pT, phi, theta) after the kick;
+    NaN where the cylinder is not reached."""
+    P, L = h.shape[0], rz.shape[0]
+    out = {k: np.full((P, L), np.nan) for k in ("S", "X", "Y", "Z", "W", "PHI", "TH")}
+    x, y, z = np.zeros(P), np.zeros(P), z0.copy()
+    phi, th = phi0.copy(), theta.copy()
+    w = q / pt
+    pmom = pt / np.sin(theta)
+    s_tot, turned = np.zeros(P), np.zeros(P)
+    alive = np.ones(P, dtype=bool)
+    for l in np.argsort(rz):
+        hh = -w * K_FIELD * bz
+        s = _cylinder_path_from(x, y, phi, hh, rz[l])
+        ok = alive & np.isfinite(s) & (turned + np.abs(hh) * np.nan_to_num(s) < np.pi) & (s_tot + np.nan_to_num(s) < s_max)
+        sf = np.where(ok, s, 0.0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            hsafe = np.where(hh == 0.0, 1.0, hh)
+            xn = np.where(hh == 0.0, x + sf * np.cos(phi), x + (np.sin(phi + hh * sf) - np.sin(phi)) / hsafe)
+            yn = np.where(hh == 0.0, y + sf * np.sin(phi), y - (np.cos(phi + hh * sf) - np.cos(phi)) / hsafe)
+        zn = z + sf / np.tan(th)
+        phin = phi + hh * sf
+        inside = ok & (zn >= lo[l]) & (zn <= hi[l])
+        # kick (drawn for every particle and layer, used where the layer is crossed)
+        gk = rng_ms.standard_normal((P, 2))
+        cosa = np.abs(np.sin(th) * np.cos(phin - np.arctan2(yn, xn)))
+        t0 = _highland(pmom, x0 / np.maximum(cosa, 1e-6))
+        th2 = np.where(inside, th + t0 * gk[:, 0], th)
+        phi2 = np.where(inside, phin + t0 * gk[:, 1] / np.sin(th), phin)
+        w2 = np.where(inside, np.sign(w) / (pmom * np.sin(th2)), w)
+        sel = inside
+        out["S"][sel, l] = (s_tot + sf)[sel]
+        out["X"][sel, l], out["Y"][sel, l], out["Z"][sel, l] = xn[sel], yn[sel], zn[sel]
+        out["W"][sel, l] = w2[sel]
+        out["PHI"][sel, l] = np.arctan2(np.sin(phi2[sel]), np.cos(phi2[sel]))
+        out["TH"][sel, l] = th2[sel]
+        x, y, z = np.where(ok, xn, x), np.where(ok, yn, y), np.where(ok, zn, z)
+        phi, th, w = np.where(ok, phi2, phi), np.where(ok, th2, th), np.where(ok, w2, w)
+        turned = turned + np.where(ok, np.abs(hh) * sf, 0.0)
+        s_tot = s_tot + sf
+        alive = ok
+    return out
+
+
 @dataclass
 class Batch:
     """A batch of events, hit arrays concatenated event after event.
@@ -112,14 +200,19 @@ class Batch:
 
 def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: int | None = None,
                base_seed: int = BASE_SEED, ineff: float | None = None, noise_scale: float = 1.0,
-               eta_max: float | None = None, smear: bool = True, overlap: float = 0.0):
+               eta_max: float | None = None, smear: bool = True, overlap: float = 0.0, material: float = 0.0):
     """One event as a dict of per-event arrays (local hit and particle indices).
 
     overlap > 0: each signal hit gets, with that probability, a second hit of the
     same particle on the same layer (overlapping sensors: the same crossing
     measured again with its own smearing).  These hits follow the noise hits and
     their random numbers are drawn after everything else, so the other arrays do
-    not change."""
+    not change.
+
+    material > 0 (layouts of cylinders only): every layer is that many radiation
+    lengths thick at normal incidence and the particles scatter at each layer
+    they cross (see _scattered_cylinder_crossings); the kicks come from a stream
+    of their own, so the other random numbers do not change."""
     cfg = get_config(config)
     layers = cfg["layers"]
     rng = _rng(config, event, base_seed)
@@ -163,9 +256,20 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
             sd = (rz[dsk][None, :] - z0[:, None]) / cot[:, None]
         ok = np.isfinite(sd) & (sd > 0) & (sd < s_max[:, None])
         S[:, dsk] = np.where(ok, sd, np.nan)
+    ms = None
+    if material > 0.0:
+        if dsk.size:
+            raise ValueError("material is supported for layouts of cylinders only")
+        key = (int(base_seed) << 64) | (CONFIG_IDS[config] << 32) | (int(event) & 0xFFFFFFFF)
+        rng_ms = np.random.Generator(np.random.Philox(key=key ^ (0x5CA77E8 << 96)))
+        ms = _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, float(material), rng_ms, s_max)
+        S = ms["S"]
     Sf = np.where(np.isnan(S), 1.0, S)
-    X, Y = _helix_xy(np.repeat(h[:, None], L, 1), np.repeat(phi0[:, None], L, 1), Sf)
-    Z = z0[:, None] + Sf * cot[:, None]
+    if ms is None:
+        X, Y = _helix_xy(np.repeat(h[:, None], L, 1), np.repeat(phi0[:, None], L, 1), Sf)
+        Z = z0[:, None] + Sf * cot[:, None]
+    else:
+        X, Y, Z = (np.where(np.isnan(ms[k]), 0.0, ms[k]) for k in ("X", "Y", "Z"))
     Rt = np.hypot(X, Y)
     in_ext = np.where(kinds[None, :] == 0, (Z >= lo[None, :]) & (Z <= hi[None, :]),
                       (Rt >= lo[None, :]) & (Rt <= hi[None, :]))
@@ -199,9 +303,14 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
         sig_true_xyz[k_] = arr.ravel()[flat]
     sig_state = np.empty((6, n_sig))
     sig_state[:3] = sig_true_xyz
-    sig_state[3] = (q / pt)[pid_l]
-    sig_state[4] = np.arctan2(np.sin(phi0[pid_l] + h[pid_l] * ss), np.cos(phi0[pid_l] + h[pid_l] * ss))
-    sig_state[5] = theta[pid_l]
+    if ms is None:
+        sig_state[3] = (q / pt)[pid_l]
+        sig_state[4] = np.arctan2(np.sin(phi0[pid_l] + h[pid_l] * ss), np.cos(phi0[pid_l] + h[pid_l] * ss))
+        sig_state[5] = theta[pid_l]
+    else:  # after the layer's scattering
+        sig_state[3] = ms["W"].ravel()[flat]
+        sig_state[4] = ms["PHI"].ravel()[flat]
+        sig_state[5] = ms["TH"].ravel()[flat]
 
     # Noise hits, uniform in (phi, z) on cylinders and uniform in area on disks.
     if cfg["noise_mode"] == "none" and n_noise is None:
@@ -315,8 +424,12 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
     if offs[-1] >= (1 << 28) - 2:
         raise ValueError("too many hits for 28-bit hit indices")
     xyz64 = np.concatenate(xyz64, axis=1)
+    layers = [dict(d) for d in cfg["layers"]]
+    if kw.get("material", 0.0) > 0.0:
+        for d in layers:
+            d["x0"] = float(kw["material"])
     return Batch(
-        config=config, layers=[dict(d) for d in cfg["layers"]], bz=float(cfg["bz"]),
+        config=config, layers=layers, bz=float(cfg["bz"]),
         xyz=np.ascontiguousarray(xyz64.astype(np.float32)), xyz64=xyz64,
         layer=np.concatenate(layer).astype(np.int32), hit_particle=np.concatenate(hp).astype(np.int32),
         event_offsets=offs.astype(np.int32), true_state=np.concatenate(ts, axis=1),

@@ -545,6 +545,98 @@ def test_backfit_short_lists_and_errors():
 
 
 # --------------------------------------------------------------------------
+# material: multiple scattering
+# --------------------------------------------------------------------------
+
+def _pulls(par, truth, cov21, idx=(2, 3, 4, 5)):
+    Cm = O.unpack21(cov21)
+    out = {}
+    for i in idx:
+        d = par[i] - truth[i]
+        if i == 4:
+            d = wrap(d)
+        out[i] = d / np.sqrt(Cm[:, i, i])
+    return out
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_scattering_noise_is_the_kick_covariance(kind):
+    """The noise the oracle adds at a layer equals the covariance of the kick
+    model it stands for, sampled: the polar angle and azimuth kicked by theta0
+    and theta0 / sin(theta) (theta0 from the generator's Highland function at
+    the path through the layer), the momentum magnitude kept, q/pT recomputed
+    from it -- which fixes the 1 / sin^2 factor and the q/pT-theta coupling."""
+    from synth.events import _highland
+    lay = (dict(kind=0, r_or_z=30.0, lo=-100.0, hi=100.0, sigma_u=0.01, sigma_v=0.01, x0=0.05) if kind == 0 else
+           dict(kind=1, r_or_z=100.0, lo=5.0, hi=60.0, sigma_u=0.01, sigma_v=0.01, x0=0.05))
+    geo = O.Geometry([lay], 3.8)
+    rng = np.random.default_rng(11 + kind)
+    for p in ([30 * math.cos(0.4), 30 * math.sin(0.4), 10.0, 0.7, 0.7, 0.55],
+              [21.0, 9.0, 100.0, -1.6, -2.9, 0.35] if kind else [-12.0, 27.4955, -40.0, -1.6, 1.4, 2.3]):
+        p = np.array(p)
+        if kind == 0:
+            p[:2] *= 30.0 / math.hypot(p[0], p[1])
+        Q = O.scattering(geo, 0, p)
+        st = math.sin(p[5])
+        cosa = abs(st * math.cos(p[4] - math.atan2(p[1], p[0]))) if kind == 0 else abs(math.cos(p[5]))
+        pm = 1.0 / (abs(p[3]) * st)
+        t0 = float(_highland(pm, 0.05 / cosa))
+        g = rng.standard_normal((2, 2_000_000))
+        dth = t0 * g[0]
+        dphi = t0 * g[1] / st
+        dw = np.sign(p[3]) / (pm * np.sin(p[5] + dth)) - p[3]
+        S = np.cov(np.stack([dw, dphi, dth]))
+        q = Q[3:, 3:]
+        for i in range(3):
+            assert abs(S[i, i] / q[i, i] - 1) < 0.01, (i, S[i, i], q[i, i])
+        assert abs(S[0, 2] / q[0, 2] - 1) < 0.02
+        assert abs(q[0, 1]) == 0 and abs(q[1, 2]) == 0 and abs(S[0, 1]) < 0.01 * math.sqrt(S[0, 0] * S[1, 1])
+        assert (Q[:3] == 0).all() and (Q[:, :3] == 0).all()
+
+
+def test_fit_with_scattering_pulls_and_chi2():
+    """Tracks that scatter in 0.03 X0 per layer (the generator moves them layer
+    by layer with Gaussian kicks): with the scattering noise the fit's pulls at
+    the last hit are N(0, 1) and chi2/ndf is 1; without it chi2/ndf is far above
+    1 (the test has the power to see a wrong noise)."""
+    b = make_batch("fit10", list(range(6)), n_tracks=1000, material=0.03)
+    geo = O.geometry_for(b)
+    assert (geo.x0 == 0.03).all()
+    r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
+    ok = r["status"] == 0
+    assert ok.mean() > 0.99
+    for i, pull in _pulls(r["par"][:, ok], b.true_state[:, _last_hits(b)][:, ok], r["cov"][:, ok]).items():
+        assert abs(pull.mean()) < 0.05, i
+        assert abs(pull.std() - 1) < 0.05, i
+    assert abs(r["chi2"][ok].sum() / r["ndf"][ok].sum() - 1) < 0.03
+    bare = O.Geometry([{k: v for k, v in d.items() if k != "x0"} for d in b.layers], b.bz)
+    r0 = O.fit(bare, b.xyz64, b.layer, b.track_hits)
+    assert r0["chi2"][ok].sum() / r0["ndf"][ok].sum() > 5
+
+
+def test_backfit_with_scattering_pulls_and_chi2():
+    """The backward pass adds each layer's scattering after its hit (reversed in
+    time) and ends before the first layer's material: its state at the first
+    hit is the particle's state there before any scattering -- the vertex
+    direction turned by h s and the vertex q/pT and theta."""
+    b = make_batch("fit10", list(range(6)), n_tracks=1000, material=0.03)
+    geo = O.geometry_for(b)
+    r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
+    rb = O.fit_backward(geo, b.xyz64, b.layer, b.track_hits, r["par"], r["cov"], 1e4)
+    ok = (r["status"] == 0) & (rb["status"] == 0)
+    first = _first_hits(b)
+    pp = b.particle_par[:, b.seed_particle]
+    x1, y1 = b.true_xyz[0, first], b.true_xyz[1, first]
+    h = -pp[3] * K_FIELD * b.bz
+    s1 = 2.0 * np.arcsin(np.hypot(x1, y1) * np.abs(h) / 2.0) / np.abs(h)
+    truth = np.stack([x1, y1, b.true_xyz[2, first], pp[3], wrap(pp[4] + h * s1), pp[5]])
+    for i, pull in _pulls(rb["par"][:, ok], truth[:, ok], rb["cov"][:, ok]).items():
+        assert abs(pull.mean()) < 0.05, i
+        assert abs(pull.std() - 1) < 0.05, i
+    assert abs(rb["chi2"][ok].sum() / rb["ndf"][ok].sum() - 1) < 0.03
+
+
+# --------------------------------------------------------------------------
 # finding
 # --------------------------------------------------------------------------
 
