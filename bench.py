@@ -410,7 +410,7 @@ def fit_leg(dev, n_tracks: int = 1_000_000, reps: int = 20):
                          "roofline": roof(ms_b, "fit_kernel (backward)")}}
 
 
-FIND_DRAM_BYTES = 35_941_000 + 18_200  # dram__bytes_read.sum + dram__bytes_write.sum, find_kernel, find20
+FIND_DRAM_BYTES = None  # dram__bytes_read.sum + dram__bytes_write.sum of find_kernel on find20; None until re-measured for this kernel version
 
 
 def _carve(arena, specs):

@@ -247,11 +247,14 @@ static void transport(const double J[36], const double C[36], double Co[36]) {
  * q/pT = q / (p sin theta) follows theta: d(q/pT) = -(q/pT) cot(theta) d(theta),
  * giving Var(q/pT) += (q/pT cot theta theta0)^2 and
  * Cov(q/pT, theta) += -(q/pT) cot(theta) theta0^2.  Kicks along the path do not
- * move the position on the layer, so nothing else changes. */
+ * move the position on the layer, so nothing else changes.  Without a field
+ * q/pT is not measured (0 in the state): the momentum is taken as infinite and
+ * no noise is added. */
 #define OR_PION_MASS 0.13957
 static void add_scattering(const geom_t *g, int l, const double p[6], double C[36]) {
     const double t = g->x0[l];
-    if (!(t > 0.0)) return;
+    /* q/pT = 0: no field, momentum not measured; taken as infinite (no noise) */
+    if (!(t > 0.0) || !(fabs(p[3]) > 0.0)) return;
     const double st = sin(p[5]), ct = cos(p[5]);
     double cosa = g->kind[l] == 0 ? fabs(st * cos(p[4] - atan2(p[1], p[0]))) : fabs(ct);
     if (cosa < 1e-6) cosa = 1e-6;

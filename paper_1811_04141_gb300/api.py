@@ -58,8 +58,9 @@ def mkf_sync(ctx) -> None:
 
 
 def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None) -> None:
-    """layers: list of dicts (kind, r_or_z, lo, hi, sigma_u, sigma_v, n_phi, n_zr);
-    plans: list of layer-id lists, one per region (None = one region, all layers)."""
+    """layers: list of dicts (kind, r_or_z, lo, hi, sigma_u, sigma_v, n_phi, n_zr,
+    optional x0 = material in radiation lengths); plans: list of layer-id lists,
+    one per region (None = one region, all layers)."""
     arr = (N.MkfLayer * len(layers))()
     for i, d in enumerate(layers):
         arr[i] = N.MkfLayer(int(d["kind"]), float(d["r_or_z"]), float(d["lo"]), float(d["hi"]),
@@ -78,6 +79,15 @@ def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None)
         edges = (C.c_float * max(1, len(e)))(*[float(x) for x in e])
     N.check("mkf_geometry_load", N.lib().mkf_geometry_load(
         ctx, arr, len(layers), parr, n_plans, edges, float(bz)))
+    if any(float(d.get("x0", 0.0)) > 0.0 for d in layers):
+        mkf_geometry_material(ctx, [float(d.get("x0", 0.0)) for d in layers])
+
+
+def mkf_geometry_material(ctx, x0) -> None:
+    """Per-layer material of the loaded geometry, in radiation lengths at normal
+    incidence (layer dicts passed to mkf_geometry_load may carry it as "x0")."""
+    arr = (C.c_float * max(1, len(x0)))(*[float(v) for v in x0])
+    N.check("mkf_geometry_material", N.lib().mkf_geometry_material(ctx, arr, len(x0)))
 
 
 class HitBins:

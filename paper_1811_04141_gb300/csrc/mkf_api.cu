@@ -107,3 +107,13 @@ extern "C" mkf_status mkf_geometry_load(mkf_ctx *ctx, const mkf_layer *layers, i
     ctx->geom_version++;
     return MKF_OK;
 }
+
+extern "C" mkf_status mkf_geometry_material(mkf_ctx *ctx, const float *x0, int32_t n_layers) {
+    if (!ctx) return MKF_ERR_ARG;
+    if (!ctx->has_geom) return MKF_ERR_GEOMETRY;
+    if (!x0 || n_layers != ctx->geom.n_layers) return MKF_ERR_ARG;
+    for (int l = 0; l < n_layers; ++l)
+        if (!(x0[l] >= 0.f && x0[l] < 1.0e3f)) return MKF_ERR_GEOMETRY;
+    for (int l = 0; l < n_layers; ++l) ctx->geom.L[l].x0 = x0[l];
+    return MKF_OK;
+}

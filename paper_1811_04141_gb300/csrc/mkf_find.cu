@@ -318,6 +318,7 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
     }
     const LayerDesc &Ld = G.L[l];
     propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+    add_scattering(Ld, p, C);
     X.searched = true;
     ++c_cl;
     const Frame f = frame_of(p);
@@ -448,6 +449,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
                 break;
             }
             propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+            add_scattering(Ld, p, C);
         }
         const Frame f = frame_of(p);
         Innov I;

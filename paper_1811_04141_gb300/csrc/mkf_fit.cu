@@ -120,7 +120,12 @@ __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ Fit
                     continue;
                 }
                 propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+                if (!kBackward) add_scattering(Ld, p, C);
             }
+            // reversed in time a layer's material follows its hit; the noise does
+            // not touch what the hit measures, so the backward pass adds it here
+            // at every hit, the last one included
+            if (kBackward) add_scattering(Ld, p, C);
             firsthit = false;
             const Frame f = frame_of(p);
             Innov I;

@@ -44,6 +44,7 @@ struct LayerDesc {
     int bin_base;     // first bin of this layer inside an event's bin block
     float phi_scale;  // nphi / (2 pi)
     float zr_scale;   // nzr / (hi - lo)
+    float x0;         // material: radiation lengths at normal incidence (0 = none)
 };
 
 struct Geom {
@@ -345,6 +346,41 @@ __device__ __forceinline__ void propagate_transport(const LayerDesc& Ld, float k
     }
     df_add(p[4], lo.phi, 2.f * a);
     df_wrap_pi(p[4], lo.phi);
+}
+
+// Multiple scattering in the layer's material, added to the covariance of a
+// state on its surface (Sec. 2.1 takes radiation lengths from an r-z table;
+// here each layer has one thickness): theta0 = 0.0136 GeV / (beta p) sqrt(x) (1 + 0.038 ln(x / beta^2))
+// (Highland, as tabulated by the Particle Data Group; unit charge, pion mass)
+// for the path x = x0 / |cos a| through the layer, a = angle between the
+// direction and the surface normal; Var(theta) += theta0^2, Var(phi) +=
+// theta0^2 / sin^2(theta), and with |p| unchanged q/pT follows theta:
+// Var(q/pT) += (q/pT cot(theta) theta0)^2, Cov(q/pT, theta) += -(q/pT) cot(theta) theta0^2.
+__device__ __forceinline__ void add_scattering(const LayerDesc& Ld, const float p[6], float C[21]) {
+    const float t = Ld.x0;
+    // q/pT = 0: no field, momentum not measured; taken as infinite (no noise)
+    if (!(t > 0.f) || !(fabsf(p[3]) > 0.f)) return;
+    constexpr float kPionMass2 = 0.13957f * 0.13957f;
+    float st, ct;
+    sincos_small(p[5], st, ct);
+    float cosa;
+    if (Ld.kind == 0) {
+        float sp, cp;
+        sincos_small(p[4], sp, cp);
+        cosa = fabsf(st * fmaf(cp, p[0], sp * p[1]) / sqrtf(fmaf(p[0], p[0], p[1] * p[1])));
+    } else {
+        cosa = fabsf(ct);
+    }
+    cosa = fmaxf(cosa, 1e-6f);
+    const float pm = 1.f / (fabsf(p[3]) * st);
+    const float beta = pm / sqrtf(fmaf(pm, pm, kPionMass2));
+    const float x = t / cosa;
+    const float th0 = 0.0136f / (beta * pm) * sqrtf(x) * (1.f + 0.038f * logf(x / (beta * beta)));
+    const float v = th0 * th0, wc = p[3] * ct / st;
+    C[sym(5, 5)] += v;
+    C[sym(4, 4)] += v / (st * st);
+    C[sym(3, 3)] += wc * wc * v;
+    C[sym(5, 3)] -= wc * v;
 }
 
 // Measurement frame at the state's position: unit radial vector (cp, sp), radius.

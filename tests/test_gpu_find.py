@@ -195,3 +195,17 @@ def test_find_cut_and_miss_limit(cut, miss):
     ref = O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=4, chi2_cut=cut, max_consec=miss, max_out=mo)
     compare(out, ref)
+
+
+@pytest.mark.parametrize("cfg,material,n_best", [("fit10", 0.03, 10), ("find20", 0.02, 10), ("find20", 0.02, 1)])
+def test_find_with_material(cfg, material, n_best):
+    """Finding with multiple scattering in every layer (cylinders and disks):
+    on fit10 the generator scatters the tracks; on find20 (disks too) the hits
+    are unscattered and only the filter adds the noise; the same parity bar."""
+    if cfg == "fit10":
+        b = make_batch(cfg, [74], n_tracks=800, material=material)
+    else:
+        b = make_batch(cfg, [74], n_tracks=500)
+        for d in b.layers:
+            d["x0"] = material
+    compare(run_gpu(b, n_best), run_oracle(b, n_best))
