@@ -297,6 +297,7 @@ struct Expansion {
 // stride `ls` (lane-interleaved shared memory in the finder, contiguous local
 // arrays in the seed kernel).  p, lo, C move onto the layer; a candidate with no
 // layer left is marked done.
+template <bool kMaterial>
 __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev, unsigned long long mask, int dir,
                                        int N, float cut, float p[6], Lo &lo, float C[21], Book &bk, Innov &I,
                                        uint32_t &status, int &c_cl, int &c_ht, float *lchi, int *lorig, float *lu,
@@ -318,7 +319,7 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
     }
     const LayerDesc &Ld = G.L[l];
     propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-    add_scattering(Ld, p, C);
+    if (kMaterial) add_scattering(Ld, p, C);
     X.searched = true;
     ++c_cl;
     const Frame f = frame_of(p);
@@ -517,7 +518,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
         float lchi[MKF_MAX_NBEST], lu[MKF_MAX_NBEST], lv[MKF_MAX_NBEST];
         int lorig[MKF_MAX_NBEST];
         Expansion X;
-        expand(A, G, ev, mask, dir, N, A.cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi, lorig, lu, lv, 1, X);
+        expand<true>(A, G, ev, mask, dir, N, A.cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi, lorig, lu, lv, 1, X);
         nlist = X.nlist;
         searched = X.searched;
         nbeam = min(searched ? nlist + 1 : 1, N);
@@ -563,8 +564,9 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
 }
 
 // kLearned: the variant with learned pruning and the feature dump compiled in;
-// the plain finder is built without them.
-template <bool kLearned>
+// the plain finder is built without them.  kMaterial: multiple scattering
+// compiled in (selected when any layer has material).
+template <bool kLearned, bool kMaterial>
 __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ FindArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Geom SG;
@@ -744,7 +746,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             // ---- 1. expansion: next layer, propagation, window search
             Expansion X{-1, false, 0, 0, 0.f};
             if (active) {
-                expand(A, G, ev, mask, dir, N, cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi + lane, lorig + lane,
+                expand<kMaterial>(A, G, ev, mask, dir, N, cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi + lane, lorig + lane,
                        lu + lane, lv + lane, 32, X);
             }
             // learned pruning / feature dump over the candidate's list (its N best
@@ -1011,12 +1013,20 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     // raise the kernel's dynamic shared-memory limit only when needed (not during
     // a stream capture after the first call)
     const bool learned = params->mlp_bf16 || params->feat_out;
-    const void *kfn = learned ? reinterpret_cast<const void *>(find_kernel<true>)
-                              : reinterpret_cast<const void *>(find_kernel<false>);
+    // material anywhere in the geometry selects the variant with the scattering
+    // noise compiled in; the others carry no trace of it
+    bool material = false;
+    for (int l = 0; l < ctx->geom.n_layers; ++l) material = material || ctx->geom.L[l].x0 > 0.f;
+    const int vi = (learned ? 2 : 0) + (material ? 1 : 0);
+    const void *const kfns[4] = {reinterpret_cast<const void *>(find_kernel<false, false>),
+                                 reinterpret_cast<const void *>(find_kernel<false, true>),
+                                 reinterpret_cast<const void *>(find_kernel<true, false>),
+                                 reinterpret_cast<const void *>(find_kernel<true, true>)};
+    const void *kfn = kfns[vi];
     if (static_cast<int>(smem) > ctx->find_smem_attr) {
         const int want = static_cast<int>(std::max<size_t>(smem, 48 * 1024));
-        MKF_CUDA_TRY(cudaFuncSetAttribute(find_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, want));
-        MKF_CUDA_TRY(cudaFuncSetAttribute(find_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, want));
+        for (int v = 0; v < 4; ++v)
+            MKF_CUDA_TRY(cudaFuncSetAttribute(kfns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, want));
         ctx->find_smem_attr = want;
     }
     void *scratch = nullptr;
@@ -1045,7 +1055,6 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     const int need = (n_seeds + seeds_per_block - 1) / seeds_per_block;
     // occupancy of this configuration (queried once, so that a later call can
     // be captured into a CUDA graph without runtime queries)
-    const int vi = learned ? 1 : 0;
     if (ctx->find_occ_threads[vi] != threads || ctx->find_occ_smem[vi] != static_cast<int>(smem)) {
         int occ = 0;
         MKF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, threads, smem));
@@ -1055,8 +1064,12 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     }
     const int per_sm = ctx->find_occ_blocks[vi];
     const int blocks = std::max(1, std::min(need, std::max(1, per_sm) * ctx->num_sms));
-    if (learned) find_kernel<true><<<blocks, threads, smem, ctx->stream>>>(A);
-    else find_kernel<false><<<blocks, threads, smem, ctx->stream>>>(A);
+    switch (vi) {
+        case 0: find_kernel<false, false><<<blocks, threads, smem, ctx->stream>>>(A); break;
+        case 1: find_kernel<false, true><<<blocks, threads, smem, ctx->stream>>>(A); break;
+        case 2: find_kernel<true, false><<<blocks, threads, smem, ctx->stream>>>(A); break;
+        default: find_kernel<true, true><<<blocks, threads, smem, ctx->stream>>>(A); break;
+    }
     MKF_CUDA_TRY(cudaGetLastError());
     return MKF_OK;
 }

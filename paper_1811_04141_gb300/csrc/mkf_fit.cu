@@ -48,8 +48,9 @@ __device__ __forceinline__ void reverse_state(float p[6], Lo &lo, float C[21]) {
 }
 
 // kBackward: hits in reverse order from the given state at the last hit, turned
-// around and inflated; the result at the first hit is turned back.
-template <bool kBackward>
+// around and inflated; the result at the first hit is turned back.  kMaterial:
+// multiple scattering compiled in (selected when any layer has material).
+template <bool kBackward, bool kMaterial>
 __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ FitArgs A) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= A.n) return;
@@ -120,12 +121,12 @@ __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ Fit
                     continue;
                 }
                 propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-                if (!kBackward) add_scattering(Ld, p, C);
+                if (!kBackward && kMaterial) add_scattering(Ld, p, C);
             }
             // reversed in time a layer's material follows its hit; the noise does
             // not touch what the hit measures, so the backward pass adds it here
             // at every hit, the last one included
-            if (kBackward) add_scattering(Ld, p, C);
+            if (kBackward && kMaterial) add_scattering(Ld, p, C);
             firsthit = false;
             const Frame f = frame_of(p);
             Innov I;
@@ -196,8 +197,12 @@ static mkf_status launch_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit_
     A.fault = ctx->fault;
     const int threads = 128;
     const int blocks = (n + threads - 1) / threads;
-    if (backward) fit_kernel<true><<<blocks, threads, 0, ctx->stream>>>(A);
-    else fit_kernel<false><<<blocks, threads, 0, ctx->stream>>>(A);
+    bool material = false;
+    for (int l = 0; l < ctx->geom.n_layers; ++l) material = material || ctx->geom.L[l].x0 > 0.f;
+    if (backward && material) fit_kernel<true, true><<<blocks, threads, 0, ctx->stream>>>(A);
+    else if (backward) fit_kernel<true, false><<<blocks, threads, 0, ctx->stream>>>(A);
+    else if (material) fit_kernel<false, true><<<blocks, threads, 0, ctx->stream>>>(A);
+    else fit_kernel<false, false><<<blocks, threads, 0, ctx->stream>>>(A);
     MKF_CUDA_TRY(cudaGetLastError());
     return MKF_OK;
 }

@@ -36,7 +36,7 @@ struct mkf_ctx {
     size_t scratch_bytes;
     int num_sms;
     int find_smem_attr;  // dynamic shared memory the find kernel is configured for
-    int find_occ_threads[2], find_occ_smem[2], find_occ_blocks[2];  // cached occupancy (plain, learned)
+    int find_occ_threads[4], find_occ_smem[4], find_occ_blocks[4];  // cached occupancy (plain, learned) x (material)
 };
 
 struct mkf_hitbins {

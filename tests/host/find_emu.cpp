@@ -102,9 +102,9 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
             threadIdx.x = l;
             blockIdx.x = 0;
             if (mlp_bf16)
-                find_kernel<true>(A);
+                find_kernel<true, false>(A);
             else
-                find_kernel<false>(A);
+                find_kernel<false, false>(A);
         });
     for (auto &t : lanes) t.join();
     fault_out[0] = fault.code;
