@@ -1,0 +1,89 @@
+"""CPU check of the fit kernel (mkf_fit.cu) compiled for the host and run thread
+by thread, in its four variants -- forward or backward, with or without
+multiple scattering -- against the oracle, with the FP32 tolerances of the GPU
+parity tests."""
+import ctypes as C
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import make_batch
+from tests.gpu_helpers import chi2_ok, par_errors
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1811_04141_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    src = open(os.path.join(CSRC, "mkf_fit.cu")).read()
+    a = src.index("namespace {")
+    b = src.index("}  // namespace") + len("}  // namespace")
+    body = src[a:b].replace("template <bool kBackward, bool kMaterial>\n__global__ void __launch_bounds__(128, 8) "
+                            "fit_kernel(const __grid_constant__ FitArgs A)",
+                            "template <bool kBackward, bool kMaterial>\nvoid fit_kernel(const FitArgs &A)")
+    assert "void fit_kernel(const FitArgs &A)" in body
+    d = tempfile.mkdtemp()
+    with open(os.path.join(d, "fit_dev.inc"), "w") as f:
+        f.write('#include "mkf_internal.h"\n' + body.replace("namespace {", "namespace fitdev {", 1)
+                + "\nusing namespace fitdev;\n")
+    so = os.path.join(d, "fit_emu.so")
+    subprocess.run([gxx, "-O2", "-std=c++17", "-fPIC", "-shared", "-I" + os.path.join(HERE, "host"), "-I" + d,
+                    "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-o", so,
+                    os.path.join(HERE, "host", "fit_emu.cpp")], check=True)
+    return C.CDLL(so)
+
+
+def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0):
+    from paper_1811_04141_gb300 import _native as NN
+    lay = b.layers
+    arr = (NN.MkfLayer * len(lay))()
+    for i, d in enumerate(lay):
+        arr[i] = NN.MkfLayer(int(d["kind"]), float(d["r_or_z"]), float(d["lo"]), float(d["hi"]), float(d["sigma_u"]),
+                             float(d["sigma_v"]), int(d["n_phi"]), int(d["n_zr"]))
+    n = hidx.shape[1]
+    xyz = np.ascontiguousarray(b.xyz, dtype=np.float32)
+    hl = np.ascontiguousarray(b.layer, dtype=np.int32)
+    hi = np.ascontiguousarray(hidx, dtype=np.int32)
+    out = dict(par=np.zeros((6, n), np.float32), cov=np.zeros((21, n), np.float32), chi2=np.zeros(n, np.float32),
+               ndf=np.zeros(n, np.int32), status=np.zeros(n, np.uint32))
+    p = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
+    x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float32)
+    sp, sc = (None, None) if seed is None else (np.ascontiguousarray(seed[0], dtype=np.float32),
+                                                np.ascontiguousarray(seed[1], dtype=np.float32))
+    rc = lib.emu_fit(arr, len(lay), C.c_float(b.bz), p(x0a), p(xyz), p(hl), b.n_hits, p(hi), hi.shape[0], n, p(sp),
+                     p(sc), int(backward), C.c_float(inflate), p(out["par"]), p(out["cov"]), p(out["chi2"]),
+                     p(out["ndf"]), p(out["status"]))
+    assert rc == 0
+    return out
+
+
+@pytest.mark.parametrize("cfg,material", [("fit10", 0.0), ("find20", 0.0), ("fit10", 0.03), ("fit10_b0", 0.02)])
+def test_fit_kernel_on_host(lib, cfg, material):
+    b = make_batch(cfg, [31], n_tracks=400, material=material) if material else make_batch(cfg, [31], n_tracks=400)
+    geo = O.geometry_for(b)
+    x0 = [d.get("x0", 0.0) for d in b.layers]
+    out = _run(lib, b, b.track_hits, x0)
+    ref = O.fit(geo, b.xyz.astype(np.float64), b.layer, b.track_hits)
+    assert (out["status"] == ref["status"]).all() and (out["ndf"] == ref["ndf"]).all()
+    ok = ref["status"] == 0
+    assert par_errors(out["par"][:, ok], ref["par"][:, ok], ref["cov"][:, ok]).max() <= 1.0
+    assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
+    # backward pass from the oracle's forward result (FP32) on both sides
+    lp, lc = ref["par"].astype(np.float32), ref["cov"].astype(np.float32)
+    outb = _run(lib, b, b.track_hits, x0, (lp, lc), True, 100.0)
+    refb = O.fit_backward(geo, b.xyz.astype(np.float64), b.layer, b.track_hits, lp.astype(np.float64),
+                          lc.astype(np.float64), 100.0)
+    assert (outb["status"] == refb["status"]).all()
+    okb = ok & (refb["status"] == 0)
+    assert par_errors(outb["par"][:, okb], refb["par"][:, okb], refb["cov"][:, okb]).max() <= 1.0
+    assert chi2_ok(outb["chi2"][okb], refb["chi2"][okb], refb["ndf"][okb])
