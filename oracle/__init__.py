@@ -49,7 +49,7 @@ def _load():
             lib = C.CDLL(_LIB_PATH)
             d, i32, i64, u64 = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)
             u32 = C.POINTER(C.c_uint32)
-            geom = [C.c_int, i32, d, d, d, d, d, d, C.c_double, C.c_int, d, u64]
+            geom = [C.c_int, i32, d, d, d, d, d, d, d, C.c_double, C.c_int, d, u64]
             lib.or_propagate.argtypes = geom + [d, C.c_int, d, d, d]
             lib.or_propagate.restype = C.c_int
             lib.or_helix_move.argtypes = geom + [d, C.c_double, d]
@@ -95,6 +95,8 @@ class Geometry:
         self.sv = np.ascontiguousarray([d["sigma_v"] for d in layers], dtype=np.float64)
         # material: radiation lengths at normal incidence (optional "x0" key)
         self.x0 = np.ascontiguousarray([d.get("x0", 0.0) for d in layers], dtype=np.float64)
+        # mean energy loss per radiation length at minimum ionisation, GeV (optional "eloss")
+        self.eloss = np.ascontiguousarray([d.get("eloss", 0.0) for d in layers], dtype=np.float64)
         self.bz = float(bz)
         edges = [] if region_edges is None else list(region_edges)
         self.n_regions = len(edges) + 1
@@ -106,7 +108,8 @@ class Geometry:
     def args(self):
         return [self.n, _p(self.kind, C.c_int32), _p(self.rz, C.c_double), _p(self.lo, C.c_double),
                 _p(self.hi, C.c_double), _p(self.su, C.c_double), _p(self.sv, C.c_double),
-                _p(self.x0, C.c_double), self.bz, self.n_regions, _p(self.edges, C.c_double),
+                _p(self.x0, C.c_double), _p(self.eloss, C.c_double), self.bz, self.n_regions,
+                _p(self.edges, C.c_double),
                 _p(self.masks, C.c_uint64)]
 
 

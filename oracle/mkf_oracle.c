@@ -59,6 +59,7 @@ typedef struct {
     int kind[OR_MAXL];
     double rz[OR_MAXL], lo[OR_MAXL], hi[OR_MAXL], su[OR_MAXL], sv[OR_MAXL];
     double x0[OR_MAXL]; /* material: radiation lengths at normal incidence */
+    double eloss[OR_MAXL]; /* mean energy loss per radiation length at minimum ionisation, GeV */
     double bz;
     int n_regions;
     double edges[OR_MAXR];
@@ -66,8 +67,8 @@ typedef struct {
 } geom_t;
 
 static int geom_init(geom_t *g, int n_layers, const int32_t *kind, const double *rz, const double *lo,
-                     const double *hi, const double *su, const double *sv, const double *x0, double bz,
-                     int n_regions, const double *edges, const uint64_t *masks) {
+                     const double *hi, const double *su, const double *sv, const double *x0,
+                     const double *eloss, double bz, int n_regions, const double *edges, const uint64_t *masks) {
     if (n_layers < 1 || n_layers > OR_MAXL) return -1;
     if (n_regions < 1 || n_regions > OR_MAXR) return -1;
     g->n = n_layers;
@@ -79,6 +80,7 @@ static int geom_init(geom_t *g, int n_layers, const int32_t *kind, const double 
         g->su[i] = su[i];
         g->sv[i] = sv[i];
         g->x0[i] = x0 ? x0[i] : 0.0;
+        g->eloss[i] = eloss ? eloss[i] : 0.0;
     }
     g->bz = bz;
     g->n_regions = n_regions;
@@ -270,6 +272,30 @@ static void add_scattering(const geom_t *g, int l, const double p[6], double C[3
     C[5 * 6 + 3] -= wc * v;
 }
 
+/* Mean energy loss in the material of layer l (no straggling): the particle
+ * loses dE = eloss[l] * x / beta^2 for the path x = x0[l] / |cos a| (eloss =
+ * the loss per radiation length at minimum ionisation; pion mass), at fixed
+ * direction; sign +1 loses it (forward in time), -1 gains it back (the backward
+ * pass).  q/pT scales by r = p / p', and so do the q/pT row and column of C. */
+static void add_eloss(const geom_t *g, int l, double p[6], double C[36], double sign) {
+    const double k = g->eloss[l], t = g->x0[l];
+    if (!(k > 0.0) || !(t > 0.0) || !(fabs(p[3]) > 0.0)) return;
+    const double st = sin(p[5]), ct = cos(p[5]);
+    double cosa = g->kind[l] == 0 ? fabs(st * cos(p[4] - atan2(p[1], p[0]))) : fabs(ct);
+    if (cosa < 1e-6) cosa = 1e-6;
+    const double pm = 1.0 / (fabs(p[3]) * fabs(st));
+    const double e = sqrt(pm * pm + OR_PION_MASS * OR_PION_MASS);
+    const double beta = pm / e;
+    const double e2 = e - sign * k * (t / cosa) / (beta * beta);
+    if (!(e2 > OR_PION_MASS)) return; /* stopped: left as it is */
+    const double r = pm / sqrt(e2 * e2 - OR_PION_MASS * OR_PION_MASS);
+    p[3] *= r;
+    for (int i = 0; i < 6; ++i) {
+        C[3 * 6 + i] *= r;
+        C[i * 6 + 3] *= r;
+    }
+}
+
 static void residual(const geom_t *g, int l, const double p[6], double xh, double yh, double zh,
                      double r[2], double H[12]) {
     double phip = atan2(p[1], p[0]);
@@ -416,9 +442,9 @@ static void unpack21(const double *in, int64_t stride, double C[36]) {
 
 #define GEOM_ARGS                                                                                     \
     int n_layers, const int32_t *kind, const double *rz, const double *lo, const double *hi,        \
-        const double *su, const double *sv, const double *x0, double bz, int n_regions,              \
-        const double *edges, const uint64_t *masks
-#define GEOM_PASS n_layers, kind, rz, lo, hi, su, sv, x0, bz, n_regions, edges, masks
+        const double *su, const double *sv, const double *x0, const double *eloss, double bz,         \
+        int n_regions, const double *edges, const uint64_t *masks
+#define GEOM_PASS n_layers, kind, rz, lo, hi, su, sv, x0, eloss, bz, n_regions, edges, masks
 
 /* Propagate p to layer l: writes q, J (6x6 row-major) and s.  Returns 1 on
  * success, 0 if unreachable, -1 on bad arguments. */
@@ -547,6 +573,7 @@ int or_fit(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_laye
                     memcpy(p, q, sizeof(q));
                     memcpy(C, Cn, sizeof(Cn));
                     add_scattering(&g, l, p, C);
+                    add_eloss(&g, l, p, C, 1.0);
                 }
                 double H[12], r[2], S[4], Si[4], HC[12];
                 residual(&g, l, p, X[hid], Y[hid], Z[hid], r, H);
@@ -630,15 +657,19 @@ int or_fit_backward(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t 
                     memcpy(p, q, sizeof(q));
                     memcpy(C, Cn, sizeof(Cn));
                 }
-                /* reversed in time, the layer's material follows its hit; the
-                 * noise does not touch what the hit measures, so it is added
-                 * here at every hit, the last one included */
-                add_scattering(&g, l, p, C);
                 double H[12], r[2], S[4], Si[4], HC[12];
                 residual(&g, l, p, X[hid], Y[hid], Z[hid], r, H);
-                if (!residual_cov(&g, l, C, H, S, Si, HC)) { st |= OR_ST_BADS; continue; }
-                chi2 += kf_update(HC, Si, r, p, C);
-                used++;
+                if (residual_cov(&g, l, C, H, S, Si, HC)) {
+                    chi2 += kf_update(HC, Si, r, p, C);
+                    used++;
+                } else {
+                    st |= OR_ST_BADS;
+                }
+                /* reversed in time, the layer's material follows its hit (at
+                 * every hit, the last one included): the energy lost there is
+                 * gained back, then the scattering noise is added */
+                add_eloss(&g, l, p, C, -1.0);
+                add_scattering(&g, l, p, C);
             }
             reverse_state(p, C);
         }
@@ -912,6 +943,7 @@ static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *ou
                 memcpy(c0.p, q, sizeof(q));
                 memcpy(c0.C, Cn, sizeof(Cn));
                 add_scattering(g, l, c0.p, c0.C);
+                add_eloss(g, l, c0.p, c0.C, 1.0);
             }
             double H[12], r[2], S[4], Si[4], HC[12];
             residual(g, l, c0.p, f->X[hid], f->Y[hid], f->Z[hid], r, H);
@@ -999,6 +1031,7 @@ static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *ou
             memcpy(c->p, q, sizeof(q));
             memcpy(c->C, Cn, sizeof(Cn));
             add_scattering(g, l, c->p, c->C);
+            add_eloss(g, l, c->p, c->C, 1.0);
             cnt[0]++;
             /* window half-widths from S at the predicted state */
             double H[12], rr[2], S[4], Si[4], HC[12];

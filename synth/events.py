@@ -102,13 +102,15 @@ def _cylinder_path_from(x, y, phi, h, R):
     return np.where(h == 0.0, s_line, s_helix)
 
 
-def _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, x0, rng_ms, s_max):
+def _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, x0, rng_ms, s_max, eloss=0.0):
     """Crossings of every cylinder (in radius order) with a multiple-scattering
     kick at each one crossed inside its z extent: the particle moves on a helix
     from crossing to crossing; at a crossing its polar angle and azimuth receive
     Gaussian kicks of width theta0 (Highland, path x0 / |cos| of the angle to
     the cylinder normal) and theta0 / sin(theta), the momentum magnitude staying
-    the same (so q/pT follows theta).  Returns per (particle, layer) the path
+    the same (so q/pT follows theta); then, with eloss > 0 (GeV per radiation
+    length at minimum ionisation), the particle loses the mean energy
+    eloss * x / beta^2 for the same path x (no straggling).  Returns per (particle, layer) the path
     from the vertex, the crossing point, and (q/pT, phi, theta) after the kick;
     NaN where the cylinder is not reached."""
     P, L = h.shape[0], rz.shape[0]
@@ -137,6 +139,12 @@ def _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, x0,
         t0 = _highland(pmom, x0 / np.maximum(cosa, 1e-6))
         th2 = np.where(inside, th + t0 * gk[:, 0], th)
         phi2 = np.where(inside, phin + t0 * gk[:, 1] / np.sin(th), phin)
+        if eloss > 0.0:
+            beta = pmom / np.sqrt(pmom * pmom + PION_MASS * PION_MASS)
+            e_new = np.sqrt(pmom * pmom + PION_MASS * PION_MASS) - eloss * (x0 / np.maximum(cosa, 1e-6)) / (beta * beta)
+            stops = inside & (e_new <= PION_MASS)
+            pmom = np.where(inside & ~stops, np.sqrt(np.maximum(e_new * e_new - PION_MASS * PION_MASS, 1e-30)), pmom)
+            ok = ok & ~stops
         w2 = np.where(inside, np.sign(w) / (pmom * np.sin(th2)), w)
         sel = inside
         out["S"][sel, l] = (s_tot + sf)[sel]
@@ -200,7 +208,8 @@ class Batch:
 
 def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: int | None = None,
                base_seed: int = BASE_SEED, ineff: float | None = None, noise_scale: float = 1.0,
-               eta_max: float | None = None, smear: bool = True, overlap: float = 0.0, material: float = 0.0):
+               eta_max: float | None = None, smear: bool = True, overlap: float = 0.0, material: float = 0.0,
+               eloss: float = 0.0):
     """One event as a dict of per-event arrays (local hit and particle indices).
 
     overlap > 0: each signal hit gets, with that probability, a second hit of the
@@ -212,7 +221,9 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
     material > 0 (layouts of cylinders only): every layer is that many radiation
     lengths thick at normal incidence and the particles scatter at each layer
     they cross (see _scattered_cylinder_crossings); the kicks come from a stream
-    of their own, so the other random numbers do not change."""
+    of their own, so the other random numbers do not change.  eloss > 0 (with
+    material): the mean energy loss per radiation length at minimum ionisation
+    (GeV), lost at each layer crossed."""
     cfg = get_config(config)
     layers = cfg["layers"]
     rng = _rng(config, event, base_seed)
@@ -262,7 +273,8 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
             raise ValueError("material is supported for layouts of cylinders only")
         key = (int(base_seed) << 64) | (CONFIG_IDS[config] << 32) | (int(event) & 0xFFFFFFFF)
         rng_ms = np.random.Generator(np.random.Philox(key=key ^ (0x5CA77E8 << 96)))
-        ms = _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, float(material), rng_ms, s_max)
+        ms = _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, float(material), rng_ms, s_max,
+                                           float(eloss))
         S = ms["S"]
     Sf = np.where(np.isnan(S), 1.0, S)
     if ms is None:
@@ -428,6 +440,8 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
     if kw.get("material", 0.0) > 0.0:
         for d in layers:
             d["x0"] = float(kw["material"])
+            if kw.get("eloss", 0.0) > 0.0:
+                d["eloss"] = float(kw["eloss"])
     return Batch(
         config=config, layers=layers, bz=float(cfg["bz"]),
         xyz=np.ascontiguousarray(xyz64.astype(np.float32)), xyz64=xyz64,

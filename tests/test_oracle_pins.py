@@ -614,12 +614,34 @@ def test_fit_with_scattering_pulls_and_chi2():
     assert r0["chi2"][ok].sum() / r0["ndf"][ok].sum() > 5
 
 
-def test_backfit_with_scattering_pulls_and_chi2():
-    """The backward pass adds each layer's scattering after its hit (reversed in
-    time) and ends before the first layer's material: its state at the first
-    hit is the particle's state there before any scattering -- the vertex
-    direction turned by h s and the vertex q/pT and theta."""
-    b = make_batch("fit10", list(range(6)), n_tracks=1000, material=0.03)
+def test_fit_with_energy_loss_pulls():
+    """Tracks that also lose energy (0.15 GeV per X0, exaggerated so that the
+    loss is several q/pT sigmas over the track): with the mean loss in the
+    filter the q/pT pull at the last hit is N(0, 1); without it the pull widens
+    past 1.5."""
+    b = make_batch("fit10", list(range(6)), n_tracks=1000, material=0.03, eloss=0.15)
+    geo = O.geometry_for(b)
+    assert (geo.eloss == 0.15).all()
+    r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
+    ok = r["status"] == 0
+    truth = b.true_state[:, _last_hits(b)][:, ok]
+    for i, pull in _pulls(r["par"][:, ok], truth, r["cov"][:, ok]).items():
+        assert abs(pull.mean()) < 0.05, i
+        assert abs(pull.std() - 1) < 0.05, i
+    assert abs(r["chi2"][ok].sum() / r["ndf"][ok].sum() - 1) < 0.03
+    bare = O.Geometry([{k: v for k, v in d.items() if k != "eloss"} for d in b.layers], b.bz)
+    r0 = O.fit(bare, b.xyz64, b.layer, b.track_hits)
+    assert _pulls(r0["par"][:, ok], truth, r0["cov"][:, ok], (3,))[3].std() > 1.5
+
+
+@pytest.mark.parametrize("eloss", [0.0, 0.15])
+def test_backfit_with_scattering_pulls_and_chi2(eloss):
+    """The backward pass adds each layer's material after its hit (reversed in
+    time: the lost energy gained back, then the scattering noise) and ends
+    before the first layer's material: its state at the first hit is the
+    particle's state there before any scattering or loss -- the vertex direction
+    turned by h s and the vertex q/pT and theta."""
+    b = make_batch("fit10", list(range(6)), n_tracks=1000, material=0.03, eloss=eloss)
     geo = O.geometry_for(b)
     r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
     rb = O.fit_backward(geo, b.xyz64, b.layer, b.track_hits, r["par"], r["cov"], 1e4)
