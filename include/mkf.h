@@ -118,18 +118,23 @@ typedef struct {
 mkf_status mkf_geometry_load(mkf_ctx *ctx, const mkf_layer *layers, int32_t n_layers, const mkf_plan *plans,
                              int32_t n_plans, const float *region_eta_edges, float bz_tesla);
 
-/* Material (Sec. 2.1: multiple scattering from the radiation lengths of the
- * detector; here one thickness per layer): x0 [n_layers] (host, copied), each
- * layer's thickness in radiation lengths at normal incidence, 0 = none, for
- * the geometry loaded last (n_layers must match it; mkf_geometry_load resets
- * every layer to 0).  Fit, backward fit and finding then add multiple
- * scattering on arriving at a layer by propagation (the backward fit at every
- * hit): the Highland angle theta0 (unit charge, pion mass) for the path through
- * the layer, Var(theta) += theta0^2, Var(phi) += theta0^2 / sin^2(theta), and
- * q/pT following theta at fixed |p|.  Hit bins stay valid.  Errors:
- * MKF_ERR_ARG (n_layers differs, x0 NULL), MKF_ERR_GEOMETRY (no geometry, a
- * value negative, not finite or >= 1000). */
-mkf_status mkf_geometry_material(mkf_ctx *ctx, const float *x0, int32_t n_layers);
+/* Material (Sec. 2.1: multiple scattering and energy loss from the radiation
+ * lengths of the detector; here one thickness per layer): x0 [n_layers] (host,
+ * copied), each layer's thickness in radiation lengths at normal incidence,
+ * 0 = none; eloss [n_layers] (host, copied, or NULL = none), the mean energy
+ * loss per radiation length at minimum ionisation (GeV), for the geometry
+ * loaded last (n_layers must match it; mkf_geometry_load resets every layer to
+ * none).  Fit and finding then apply, on arriving at a layer by propagation,
+ * multiple scattering -- the Highland angle theta0 (unit charge, pion mass) for
+ * the path through the layer: Var(theta) += theta0^2, Var(phi) += theta0^2 /
+ * sin^2(theta), q/pT following theta at fixed |p| -- and then the mean energy
+ * loss eloss * path / beta^2 (q/pT and its covariance row scaled by p / p');
+ * the backward fit applies them after each hit in reverse (energy gained back,
+ * then the noise).  Without a field q/pT is not measured (0) and nothing is
+ * applied.  Hit bins stay valid.  Errors: MKF_ERR_ARG (n_layers differs, x0
+ * NULL), MKF_ERR_GEOMETRY (no geometry, a value negative, not finite or
+ * >= 1000). */
+mkf_status mkf_geometry_material(mkf_ctx *ctx, const float *x0, const float *eloss, int32_t n_layers);
 
 /* ------------------------------------------------------------------------ */
 /* Hit binning (per event and layer, phi x z or phi x r bins)               */

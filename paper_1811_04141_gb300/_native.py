@@ -117,7 +117,7 @@ def lib():
             L.mkf_fit.restype = i32
             L.mkf_fit_backward.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, vp, C.c_float, vp, vp, vp, vp, vp]
             L.mkf_fit_backward.restype = i32
-            L.mkf_geometry_material.argtypes = [vp, vp, i32]
+            L.mkf_geometry_material.argtypes = [vp, vp, vp, i32]
             L.mkf_geometry_material.restype = i32
             L.mkf_seeds_clean.argtypes = [vp, vp, i32, i32, vp, C.c_float, C.c_float, C.c_float, vp]
             L.mkf_seeds_clean.restype = i32

@@ -80,14 +80,18 @@ def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None)
     N.check("mkf_geometry_load", N.lib().mkf_geometry_load(
         ctx, arr, len(layers), parr, n_plans, edges, float(bz)))
     if any(float(d.get("x0", 0.0)) > 0.0 for d in layers):
-        mkf_geometry_material(ctx, [float(d.get("x0", 0.0)) for d in layers])
+        mkf_geometry_material(ctx, [float(d.get("x0", 0.0)) for d in layers],
+                              [float(d.get("eloss", 0.0)) for d in layers])
 
 
-def mkf_geometry_material(ctx, x0) -> None:
-    """Per-layer material of the loaded geometry, in radiation lengths at normal
-    incidence (layer dicts passed to mkf_geometry_load may carry it as "x0")."""
+def mkf_geometry_material(ctx, x0, eloss=None) -> None:
+    """Per-layer material of the loaded geometry: x0 in radiation lengths at
+    normal incidence, eloss the mean energy loss per radiation length (GeV) or
+    None (layer dicts passed to mkf_geometry_load may carry them as "x0" and
+    "eloss")."""
     arr = (C.c_float * max(1, len(x0)))(*[float(v) for v in x0])
-    N.check("mkf_geometry_material", N.lib().mkf_geometry_material(ctx, arr, len(x0)))
+    earr = None if eloss is None else (C.c_float * max(1, len(eloss)))(*[float(v) for v in eloss])
+    N.check("mkf_geometry_material", N.lib().mkf_geometry_material(ctx, arr, earr, len(x0)))
 
 
 class HitBins:

@@ -108,12 +108,17 @@ extern "C" mkf_status mkf_geometry_load(mkf_ctx *ctx, const mkf_layer *layers, i
     return MKF_OK;
 }
 
-extern "C" mkf_status mkf_geometry_material(mkf_ctx *ctx, const float *x0, int32_t n_layers) {
+extern "C" mkf_status mkf_geometry_material(mkf_ctx *ctx, const float *x0, const float *eloss, int32_t n_layers) {
     if (!ctx) return MKF_ERR_ARG;
     if (!ctx->has_geom) return MKF_ERR_GEOMETRY;
     if (!x0 || n_layers != ctx->geom.n_layers) return MKF_ERR_ARG;
-    for (int l = 0; l < n_layers; ++l)
+    for (int l = 0; l < n_layers; ++l) {
         if (!(x0[l] >= 0.f && x0[l] < 1.0e3f)) return MKF_ERR_GEOMETRY;
-    for (int l = 0; l < n_layers; ++l) ctx->geom.L[l].x0 = x0[l];
+        if (eloss && !(eloss[l] >= 0.f && eloss[l] < 1.0e3f)) return MKF_ERR_GEOMETRY;
+    }
+    for (int l = 0; l < n_layers; ++l) {
+        ctx->geom.L[l].x0 = x0[l];
+        ctx->geom.L[l].eloss = eloss ? eloss[l] : 0.f;
+    }
     return MKF_OK;
 }

@@ -319,7 +319,10 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
     }
     const LayerDesc &Ld = G.L[l];
     propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-    if (kMaterial) add_scattering(Ld, p, C);
+    if (kMaterial) {
+        add_scattering(Ld, p, C);
+        apply_eloss(Ld, p, C, 1.f);
+    }
     X.searched = true;
     ++c_cl;
     const Frame f = frame_of(p);
@@ -451,6 +454,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
             }
             propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
             add_scattering(Ld, p, C);
+            apply_eloss(Ld, p, C, 1.f);
         }
         const Frame f = frame_of(p);
         Innov I;

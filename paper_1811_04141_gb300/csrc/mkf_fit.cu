@@ -121,25 +121,31 @@ __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ Fit
                     continue;
                 }
                 propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-                if (!kBackward && kMaterial) add_scattering(Ld, p, C);
+                if (!kBackward && kMaterial) {
+                    add_scattering(Ld, p, C);
+                    apply_eloss(Ld, p, C, 1.f);
+                }
             }
-            // reversed in time a layer's material follows its hit; the noise does
-            // not touch what the hit measures, so the backward pass adds it here
-            // at every hit, the last one included
-            if (kBackward && kMaterial) add_scattering(Ld, p, C);
             firsthit = false;
             const Frame f = frame_of(p);
             Innov I;
-            if (!innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
+            if (innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
+                float u, v;
+                const float zr = Ld.kind == 0 ? zh : sqrtf(fmaf(xh, xh, yh * yh));
+                residual(Ld.kind, Ld.rz, p, lo, f, xh, yh, zr, u, v);
+                chi2 += chi2_of(I, u, v);
+                kf_apply(I, u, v, p, lo, C);
+                ++used;
+            } else {
                 st |= MKF_ST_BADS;
-                continue;
             }
-            float u, v;
-            const float zr = Ld.kind == 0 ? zh : sqrtf(fmaf(xh, xh, yh * yh));
-            residual(Ld.kind, Ld.rz, p, lo, f, xh, yh, zr, u, v);
-            chi2 += chi2_of(I, u, v);
-            kf_apply(I, u, v, p, lo, C);
-            ++used;
+            // reversed in time a layer's material follows its hit (at every hit,
+            // the last one included): the energy lost there is gained back, then
+            // the scattering noise is added
+            if (kBackward && kMaterial) {
+                apply_eloss(Ld, p, C, -1.f);
+                add_scattering(Ld, p, C);
+            }
         }
         if (kBackward) reverse_state(p, lo, C);
         if (!finite_state(p) || !isfinite(chi2)) st |= MKF_ST_NONFINITE;

@@ -48,6 +48,7 @@ inline mkf_status mkf_build_geom(const mkf_layer *layers, int32_t n_layers, cons
         d.phi_scale = static_cast<float>(s.n_phi_bins / (2.0 * M_PI));
         d.zr_scale = static_cast<float>(s.n_zr_bins / (static_cast<double>(s.hi) - s.lo));
         d.x0 = 0.f;  // material comes from mkf_geometry_material
+        d.eloss = 0.f;
         base += static_cast<int64_t>(s.n_phi_bins) * s.n_zr_bins;
         if (base > (int64_t(1) << 26)) return MKF_ERR_CAPACITY;
     }

@@ -45,6 +45,7 @@ struct LayerDesc {
     float phi_scale;  // nphi / (2 pi)
     float zr_scale;   // nzr / (hi - lo)
     float x0;         // material: radiation lengths at normal incidence (0 = none)
+    float eloss;      // mean energy loss per radiation length at minimum ionisation, GeV (0 = none)
 };
 
 struct Geom {
@@ -381,6 +382,36 @@ __device__ __forceinline__ void add_scattering(const LayerDesc& Ld, const float 
     C[sym(4, 4)] += v / (st * st);
     C[sym(3, 3)] += wc * wc * v;
     C[sym(5, 3)] -= wc * v;
+}
+
+// Mean energy loss in the layer's material (no straggling): dE = eloss * x /
+// beta^2 for the path x = x0 / |cos a| (pion mass), at fixed direction; sign
+// +1 loses it (forward in time), -1 gains it back (the backward fit).  q/pT
+// scales by r = p / p', and so do the q/pT row and column of C.
+__device__ __forceinline__ void apply_eloss(const LayerDesc& Ld, float p[6], float C[21], float sign) {
+    const float k = Ld.eloss, t = Ld.x0;
+    if (!(k > 0.f) || !(t > 0.f) || !(fabsf(p[3]) > 0.f)) return;
+    constexpr float kPionMass = 0.13957f;
+    float st, ct;
+    sincos_small(p[5], st, ct);
+    float cosa;
+    if (Ld.kind == 0) {
+        float sp, cp;
+        sincos_small(p[4], sp, cp);
+        cosa = fabsf(st * fmaf(cp, p[0], sp * p[1]) / sqrtf(fmaf(p[0], p[0], p[1] * p[1])));
+    } else {
+        cosa = fabsf(ct);
+    }
+    cosa = fmaxf(cosa, 1e-6f);
+    const float pm = 1.f / (fabsf(p[3]) * st);
+    const float e = sqrtf(fmaf(pm, pm, kPionMass * kPionMass));
+    const float beta = pm / e;
+    const float e2 = e - sign * k * (t / cosa) / (beta * beta);
+    if (!(e2 > kPionMass)) return;  // stopped: left as it is
+    const float r = pm / sqrtf(fmaf(e2, e2, -kPionMass * kPionMass));
+    p[3] *= r;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) C[sym(3, i)] *= (i == 3 ? r * r : r);
 }
 
 // Measurement frame at the state's position: unit radial vector (cp, sp), radius.

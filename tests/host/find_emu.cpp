@@ -17,12 +17,15 @@ unsigned char *g_smem;
 extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *X, const float *Y, const float *Z,
                         const int *layer, int n_hits, const int *event_offsets, int n_events, const int *seed_hits,
                         const int *seed_event, int n_seeds, int N, float cut, int max_consec, int max_out, int step1,
-                        const uint16_t *mlp_bf16, float mlp_tau, float material,
+                        const uint16_t *mlp_bf16, float mlp_tau, float material, float eloss,
                         float *out_par, float *out_cov, float *out_chi2, int *out_nh, int *out_hits,
                         unsigned *out_status, int *counters, int *fault_out) {
     static Geom G;
     if (mkf_build_geom(layers, nl, nullptr, 0, nullptr, bz, G) != MKF_OK) return -1;
-    for (int l = 0; l < nl; ++l) G.L[l].x0 = material;  // as mkf_geometry_material sets it
+    for (int l = 0; l < nl; ++l) {  // as mkf_geometry_material sets them
+        G.L[l].x0 = material;
+        G.L[l].eloss = eloss;
+    }
     const int64_t n_bins = static_cast<int64_t>(n_events) * G.bins_per_event;
     std::vector<int> key(n_hits);
     for (int i = 0; i < n_hits; ++i) {

@@ -13,7 +13,7 @@ dim3 blockDim;
 #include "fit_dev.inc"
 #include "mkf_geom.h"
 
-extern "C" int emu_fit(const mkf_layer *layers, int nl, float bz, const float *x0, const float *xyz,
+extern "C" int emu_fit(const mkf_layer *layers, int nl, float bz, const float *x0, const float *eloss, const float *xyz,
                        const int32_t *hit_layer, int32_t n_hits, const int32_t *hit_idx, int32_t max_hits, int32_t n,
                        const float *seed_par, const float *seed_cov, int backward, float inflate, float *out_par,
                        float *out_cov, float *chi2, int32_t *ndf, uint32_t *status) {
@@ -22,6 +22,7 @@ extern "C" int emu_fit(const mkf_layer *layers, int nl, float bz, const float *x
     bool material = false;
     for (int l = 0; l < nl; ++l) {
         A.G.L[l].x0 = x0 ? x0[l] : 0.f;
+        A.G.L[l].eloss = eloss ? eloss[l] : 0.f;
         material = material || A.G.L[l].x0 > 0.f;
     }
     mkf_fault fault{0, 0};

@@ -54,7 +54,7 @@ def emu_so():
     return so
 
 
-def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1, mlp_bf16=None, tau=0.0, material=0.0):
+def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1, mlp_bf16=None, tau=0.0, material=0.0, eloss=0.0):
     d = tempfile.mkdtemp()
     out = os.path.join(d, "out.npz")
     wpath = "none"
@@ -63,7 +63,7 @@ def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1, mlp_bf16=None, tau
         np.save(wpath, mlp_bf16)
     r = subprocess.run([sys.executable, os.path.join(HERE, "host", "run_find_emu.py"), so, cfg, str(event),
                         str(n_tracks), "none" if n_noise is None else str(n_noise), str(n_best), str(step1), out,
-                        wpath, str(tau), str(material), ROOT],
+                        wpath, str(tau), str(material), str(eloss), ROOT],
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     z = np.load(out)
@@ -86,16 +86,18 @@ def test_emulated_finder_matches_oracle(emu_so, cfg, event, tracks, noise, n_bes
     compare(out, ref)
 
 
-@pytest.mark.parametrize("n_best", [1, 10])
-def test_emulated_finder_with_material_matches_oracle(emu_so, n_best):
-    """The finder variant with multiple scattering (0.02 X0 in every layer,
-    cylinders and disks) against the oracle with the same material."""
+@pytest.mark.parametrize("n_best,eloss", [(1, 0.0), (10, 0.0), (10, 0.1)])
+def test_emulated_finder_with_material_matches_oracle(emu_so, n_best, eloss):
+    """The finder variant with material (0.02 X0 in every layer, cylinders and
+    disks; scattering, and energy loss when eloss > 0) against the oracle with
+    the same material."""
     b = make_batch("find20", [45], n_tracks=150)
     for d in b.layers:
         d["x0"] = 0.02
+        d["eloss"] = eloss
     ref = O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=n_best, max_out=len(b.layers) + 3)
-    out = run_emu(emu_so, "find20", 45, 150, None, n_best, 1, material=0.02)
+    out = run_emu(emu_so, "find20", 45, 150, None, n_best, 1, material=0.02, eloss=eloss)
     compare(out, ref)
 
 

@@ -43,7 +43,7 @@ def lib():
     return C.CDLL(so)
 
 
-def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0):
+def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0, eloss=None):
     from paper_1811_04141_gb300 import _native as NN
     lay = b.layers
     arr = (NN.MkfLayer * len(lay))()
@@ -58,21 +58,25 @@ def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0):
                ndf=np.zeros(n, np.int32), status=np.zeros(n, np.uint32))
     p = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
     x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float32)
+    ela = None if eloss is None else np.ascontiguousarray(eloss, dtype=np.float32)
     sp, sc = (None, None) if seed is None else (np.ascontiguousarray(seed[0], dtype=np.float32),
                                                 np.ascontiguousarray(seed[1], dtype=np.float32))
-    rc = lib.emu_fit(arr, len(lay), C.c_float(b.bz), p(x0a), p(xyz), p(hl), b.n_hits, p(hi), hi.shape[0], n, p(sp),
+    rc = lib.emu_fit(arr, len(lay), C.c_float(b.bz), p(x0a), p(ela), p(xyz), p(hl), b.n_hits, p(hi), hi.shape[0], n, p(sp),
                      p(sc), int(backward), C.c_float(inflate), p(out["par"]), p(out["cov"]), p(out["chi2"]),
                      p(out["ndf"]), p(out["status"]))
     assert rc == 0
     return out
 
 
-@pytest.mark.parametrize("cfg,material", [("fit10", 0.0), ("find20", 0.0), ("fit10", 0.03), ("fit10_b0", 0.02)])
-def test_fit_kernel_on_host(lib, cfg, material):
-    b = make_batch(cfg, [31], n_tracks=400, material=material) if material else make_batch(cfg, [31], n_tracks=400)
+@pytest.mark.parametrize("cfg,material,eloss", [("fit10", 0.0, 0.0), ("find20", 0.0, 0.0), ("fit10", 0.03, 0.0),
+                                               ("fit10", 0.03, 0.15), ("fit10_b0", 0.02, 0.0)])
+def test_fit_kernel_on_host(lib, cfg, material, eloss):
+    b = (make_batch(cfg, [31], n_tracks=400, material=material, eloss=eloss) if material
+         else make_batch(cfg, [31], n_tracks=400))
     geo = O.geometry_for(b)
     x0 = [d.get("x0", 0.0) for d in b.layers]
-    out = _run(lib, b, b.track_hits, x0)
+    el = [d.get("eloss", 0.0) for d in b.layers]
+    out = _run(lib, b, b.track_hits, x0, eloss=el)
     ref = O.fit(geo, b.xyz.astype(np.float64), b.layer, b.track_hits)
     assert (out["status"] == ref["status"]).all() and (out["ndf"] == ref["ndf"]).all()
     ok = ref["status"] == 0
@@ -80,7 +84,7 @@ def test_fit_kernel_on_host(lib, cfg, material):
     assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
     # backward pass from the oracle's forward result (FP32) on both sides
     lp, lc = ref["par"].astype(np.float32), ref["cov"].astype(np.float32)
-    outb = _run(lib, b, b.track_hits, x0, (lp, lc), True, 100.0)
+    outb = _run(lib, b, b.track_hits, x0, (lp, lc), True, 100.0, el)
     refb = O.fit_backward(geo, b.xyz.astype(np.float64), b.layer, b.track_hits, lp.astype(np.float64),
                           lc.astype(np.float64), 100.0)
     assert (outb["status"] == refb["status"]).all()

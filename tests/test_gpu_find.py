@@ -197,15 +197,18 @@ def test_find_cut_and_miss_limit(cut, miss):
     compare(out, ref)
 
 
-@pytest.mark.parametrize("cfg,material,n_best", [("fit10", 0.03, 10), ("find20", 0.02, 10), ("find20", 0.02, 1)])
-def test_find_with_material(cfg, material, n_best):
-    """Finding with multiple scattering in every layer (cylinders and disks):
-    on fit10 the generator scatters the tracks; on find20 (disks too) the hits
-    are unscattered and only the filter adds the noise; the same parity bar."""
+@pytest.mark.parametrize("cfg,material,n_best,eloss", [("fit10", 0.03, 10, 0.0), ("fit10", 0.03, 10, 0.15),
+                                                       ("find20", 0.02, 10, 0.1), ("find20", 0.02, 1, 0.0)])
+def test_find_with_material(cfg, material, n_best, eloss):
+    """Finding with material in every layer (cylinders and disks; energy loss
+    when eloss > 0): on fit10 the generator scatters the tracks (and takes their
+    energy); on find20 (disks too) the hits are unscattered and only the filter
+    applies the material; the same parity bar."""
     if cfg == "fit10":
-        b = make_batch(cfg, [74], n_tracks=800, material=material)
+        b = make_batch(cfg, [74], n_tracks=800, material=material, eloss=eloss)
     else:
         b = make_batch(cfg, [74], n_tracks=500)
         for d in b.layers:
             d["x0"] = material
+            d["eloss"] = eloss
     compare(run_gpu(b, n_best), run_oracle(b, n_best))

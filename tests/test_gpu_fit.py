@@ -136,11 +136,12 @@ def test_fit_backward_ragged_lists_and_errors():
     assert o["par"].shape == (6, 0)
 
 
-@pytest.mark.parametrize("cfg,material", [("fit10", 0.03), ("fit10_b0", 0.02)])
-def test_fit_with_material_parity(cfg, material):
-    """Forward and backward fit with multiple scattering (tracks scattered by
-    the generator in `material` X0 per layer) against the oracle."""
-    b = make_batch(cfg, [16], n_tracks=800, material=material)
+@pytest.mark.parametrize("cfg,material,eloss", [("fit10", 0.03, 0.0), ("fit10", 0.03, 0.15), ("fit10_b0", 0.02, 0.0)])
+def test_fit_with_material_parity(cfg, material, eloss):
+    """Forward and backward fit with material (tracks scattered by the
+    generator in `material` X0 per layer, losing energy when eloss > 0) against
+    the oracle."""
+    b = make_batch(cfg, [16], n_tracks=800, material=material, eloss=eloss)
     assert all(d["x0"] == material for d in b.layers)
     ctx = make_ctx(b)
     d = upload(b)
