@@ -49,7 +49,9 @@ def _load():
             lib = C.CDLL(_LIB_PATH)
             d, i32, i64, u64 = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)
             u32 = C.POINTER(C.c_uint32)
-            geom = [C.c_int, i32, d, d, d, d, d, d, d, C.c_double, C.c_int, d, u64]
+            geom = [C.c_int, i32, d, d, d, d, d, d, d, C.c_double, C.c_int, C.c_double, C.c_int, d, u64]
+            lib.or_field.argtypes = geom + [d, d]
+            lib.or_field.restype = C.c_int
             lib.or_propagate.argtypes = geom + [d, C.c_int, d, d, d]
             lib.or_propagate.restype = C.c_int
             lib.or_helix_move.argtypes = geom + [d, C.c_double, d]
@@ -84,7 +86,7 @@ def _p(a, ctype):
 class Geometry:
     """Layer table + field + optional tracking regions (layer masks by seed eta)."""
 
-    def __init__(self, layers, bz, region_edges=None, region_masks=None):
+    def __init__(self, layers, bz, region_edges=None, region_masks=None, field_alpha=None):
         self.layers = [dict(d) for d in layers]
         self.n = len(layers)
         self.kind = np.ascontiguousarray([d["kind"] for d in layers], dtype=np.int32)
@@ -98,6 +100,10 @@ class Geometry:
         # mean energy loss per radiation length at minimum ionisation, GeV (optional "eloss")
         self.eloss = np.ascontiguousarray([d.get("eloss", 0.0) for d in layers], dtype=np.float64)
         self.bz = float(bz)
+        # field: uniform (None) or parameterised with fall-off coefficient alpha
+        # (1/cm^2; alpha = 0 is the uniform field integrated numerically)
+        self.field_kind = 0 if field_alpha is None else 1
+        self.alpha = 0.0 if field_alpha is None else float(field_alpha)
         edges = [] if region_edges is None else list(region_edges)
         self.n_regions = len(edges) + 1
         self.edges = np.ascontiguousarray(edges + [0.0], dtype=np.float64)
@@ -108,7 +114,8 @@ class Geometry:
     def args(self):
         return [self.n, _p(self.kind, C.c_int32), _p(self.rz, C.c_double), _p(self.lo, C.c_double),
                 _p(self.hi, C.c_double), _p(self.su, C.c_double), _p(self.sv, C.c_double),
-                _p(self.x0, C.c_double), _p(self.eloss, C.c_double), self.bz, self.n_regions,
+                _p(self.x0, C.c_double), _p(self.eloss, C.c_double), self.bz, self.field_kind, self.alpha,
+                self.n_regions,
                 _p(self.edges, C.c_double),
                 _p(self.masks, C.c_uint64)]
 
@@ -281,4 +288,14 @@ def find(geo: Geometry, xyz, hit_layer, event_offsets, seed_hits, seed_event, n_
 
 
 def geometry_for(batch, region_edges=None, region_masks=None) -> Geometry:
-    return Geometry(batch.layers, batch.bz, region_edges, region_masks)
+    return Geometry(batch.layers, batch.bz, region_edges, region_masks, batch.meta.get("field_alpha"))
+
+
+def field(geo: Geometry, r):
+    """The field (T) at position r (cm)."""
+    lib = _load()
+    r = _f64(r)
+    B = np.zeros(3)
+    if lib.or_field(*geo.args(), _p(r, C.c_double), _p(B, C.c_double)) < 0:
+        raise ValueError("bad arguments")
+    return B

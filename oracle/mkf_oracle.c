@@ -61,6 +61,8 @@ typedef struct {
     double x0[OR_MAXL]; /* material: radiation lengths at normal incidence */
     double eloss[OR_MAXL]; /* mean energy loss per radiation length at minimum ionisation, GeV */
     double bz;
+    int field_kind; /* 0: uniform Bz; 1: parameterised field (field_at), RK4 propagation */
+    double alpha;   /* parameterised field: fall-off coefficient, 1/cm^2 */
     int n_regions;
     double edges[OR_MAXR];
     uint64_t mask[OR_MAXR];
@@ -68,7 +70,8 @@ typedef struct {
 
 static int geom_init(geom_t *g, int n_layers, const int32_t *kind, const double *rz, const double *lo,
                      const double *hi, const double *su, const double *sv, const double *x0,
-                     const double *eloss, double bz, int n_regions, const double *edges, const uint64_t *masks) {
+                     const double *eloss, double bz, int field_kind, double alpha, int n_regions,
+                     const double *edges, const uint64_t *masks) {
     if (n_layers < 1 || n_layers > OR_MAXL) return -1;
     if (n_regions < 1 || n_regions > OR_MAXR) return -1;
     g->n = n_layers;
@@ -83,6 +86,9 @@ static int geom_init(geom_t *g, int n_layers, const int32_t *kind, const double 
         g->eloss[i] = eloss ? eloss[i] : 0.0;
     }
     g->bz = bz;
+    if (field_kind != 0 && field_kind != 1) return -1;
+    g->field_kind = field_kind;
+    g->alpha = field_kind ? alpha : 0.0;
     g->n_regions = n_regions;
     for (int r = 0; r + 1 < n_regions; ++r) g->edges[r] = edges[r];
     for (int r = 0; r < n_regions; ++r) {
@@ -104,7 +110,27 @@ static double cot_of(double theta) { return cos(theta) / sin(theta); }
 /* Helix and propagation                                                     */
 /* ------------------------------------------------------------------------- */
 
-static double turn_rate(const geom_t *g, double w) { return -w * OR_K * g->bz; }
+/* Magnetic field.  Uniform: B = (0, 0, bz).  Parameterised (sec. 2.1: the
+ * field type is chosen per propagation): the field of a solenoid near its
+ * centre to second order, from the scalar potential that solves Laplace's
+ * equation with axial symmetry,
+ *   Bz = bz (1 - alpha (z^2 - r^2 / 2)),  Br = bz alpha r z,
+ * i.e. Bx = bz alpha x z, By = bz alpha y z: divergence- and curl-free, Bz
+ * falling off along z and rising slightly with r for alpha > 0. */
+static void field_at(const geom_t *g, double x, double y, double z, double B[3]) {
+    const double a = g->alpha;
+    B[0] = g->bz * a * x * z;
+    B[1] = g->bz * a * y * z;
+    B[2] = g->bz * (1.0 - a * (z * z - 0.5 * (x * x + y * y)));
+}
+
+/* Turning rate per unit transverse path from the axial field at the state's
+ * position (the uniform field's h in constant mode). */
+static double turn_rate(const geom_t *g, const double p[6]) {
+    double B[3];
+    field_at(g, p[0], p[1], p[2], B);
+    return -p[3] * OR_K * B[2];
+}
 
 /* Move state p along the helix by transverse path s (closed form). */
 static void helix_move(const double p[6], double h, double s, double q[6]) {
@@ -162,7 +188,7 @@ static int cyl_path(double x, double y, double phi, double h, double R, double *
 /* Path to the surface of layer l, or 0 if the helix does not reach it going
  * forward within half a turn.  No extent check. */
 static int path_to_layer(const geom_t *g, const double p[6], int l, double *s) {
-    double h = turn_rate(g, p[3]);
+    double h = turn_rate(g, p);
     if (g->kind[l] == 0) return cyl_path(p[0], p[1], p[4], h, g->rz[l], s);
     double ct = cot_of(p[5]);
     if (ct == 0.0) return 0;
@@ -178,7 +204,7 @@ static void prop_jacobian(const geom_t *g, const double p[6], int l, double s, c
                           double J[36]) {
     double A[36];
     memset(A, 0, sizeof(A));
-    double h = turn_rate(g, p[3]);
+    double h = turn_rate(g, p);
     double dhdw = -OR_K * g->bz;
     double phi = p[4], phis = phi + h * s;
     double dx = q[0] - p[0], dy = q[1] - p[1];
@@ -208,6 +234,117 @@ static void prop_jacobian(const geom_t *g, const double p[6], int l, double s, c
     }
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) J[i * 6 + j] = A[i * 6 + j] + d[i] * dsdp[j];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Propagation in the parameterised field: fourth-order Runge-Kutta          */
+/* ------------------------------------------------------------------------- */
+
+/* Equation of motion of a unit charge with lambda = q/p in the field, with the
+ * path length S as variable: dr/dS = T, dT/dS = K lambda T x B(r) (T the unit
+ * direction); lambda is constant.  X = (x, y, z, Tx, Ty, Tz, lambda). */
+static void eom(const geom_t *g, const double X[7], double dX[7]) {
+    double B[3];
+    field_at(g, X[0], X[1], X[2], B);
+    const double k = OR_K * X[6];
+    dX[0] = X[3];
+    dX[1] = X[4];
+    dX[2] = X[5];
+    dX[3] = k * (X[4] * B[2] - X[5] * B[1]);
+    dX[4] = k * (X[5] * B[0] - X[3] * B[2]);
+    dX[5] = k * (X[3] * B[1] - X[4] * B[0]);
+    dX[6] = 0.0;
+}
+
+/* One classical Runge-Kutta step of length d (may be negative). */
+static void rk4_step(const geom_t *g, double X[7], double d) {
+    double k1[7], k2[7], k3[7], k4[7], Y[7];
+    eom(g, X, k1);
+    for (int i = 0; i < 7; ++i) Y[i] = X[i] + 0.5 * d * k1[i];
+    eom(g, Y, k2);
+    for (int i = 0; i < 7; ++i) Y[i] = X[i] + 0.5 * d * k2[i];
+    eom(g, Y, k3);
+    for (int i = 0; i < 7; ++i) Y[i] = X[i] + d * k3[i];
+    eom(g, Y, k4);
+    for (int i = 0; i < 7; ++i) X[i] += d / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+#define OR_RK_TURN 0.05  /* largest turning angle per step, rad */
+#define OR_RK_LEN 10.0   /* largest step, cm of path */
+#define OR_RK_MAXN 16    /* most steps per propagation */
+#define OR_RK_NEWTON 2   /* correction steps onto the surface */
+
+/* Number of equal steps over the estimated transverse path s (turning |h| s). */
+static int rk_steps(const double p[6], double h, double s) {
+    const double S = s / sin(p[5]);
+    double n = ceil(fmax(fabs(h) * s / OR_RK_TURN, fabs(S) / OR_RK_LEN));
+    if (!(n >= 1.0)) n = 1.0;
+    return n > OR_RK_MAXN ? OR_RK_MAXN : (int)n;
+}
+
+/* Move p onto layer l: n equal steps over the path s estimated by the helix in
+ * the local axial field, then OR_RK_NEWTON Newton steps on the distance to the
+ * surface (the signed path to it along the current direction, linearised:
+ * (R - r) / (dr/dS) on a cylinder, (Z - z) / Tz on a disk). */
+static void rk_move(const geom_t *g, const double p[6], int l, double s, int n, double q[6]) {
+    const double st = sin(p[5]);
+    double X[7] = {p[0], p[1], p[2], st * cos(p[4]), st * sin(p[4]), cos(p[5]), p[3] * st};
+    const double S = s / st;
+    for (int i = 0; i < n; ++i) rk4_step(g, X, S / n);
+    for (int it = 0; it < OR_RK_NEWTON; ++it) {
+        double d;
+        if (g->kind[l] == 0) {
+            const double r = hypot(X[0], X[1]);
+            d = (g->rz[l] - r) / ((X[0] * X[3] + X[1] * X[4]) / r);
+        } else {
+            d = (g->rz[l] - X[2]) / X[5];
+        }
+        rk4_step(g, X, d);
+    }
+    const double tn = sqrt(X[3] * X[3] + X[4] * X[4] + X[5] * X[5]);
+    const double tt = hypot(X[3], X[4]) / tn;
+    q[0] = X[0];
+    q[1] = X[1];
+    q[2] = X[2];
+    q[3] = X[6] / tt;
+    q[4] = atan2(X[4], X[3]);
+    q[5] = atan2(tt, X[5] / tn);
+}
+
+/* Jacobian of rk_move by central differences (the step count held fixed), the
+ * azimuth difference wrapped. */
+static void rk_jacobian(const geom_t *g, const double p[6], int l, int n, double J[36]) {
+    const double eps[6] = {1e-4, 1e-4, 1e-4, 1e-6 * fmax(fabs(p[3]), 1e-2), 1e-6, 1e-6};
+    for (int j = 0; j < 6; ++j) {
+        double pp[6], pm[6], qp[6], qm[6], s;
+        memcpy(pp, p, sizeof(pp));
+        memcpy(pm, p, sizeof(pm));
+        pp[j] += eps[j];
+        pm[j] -= eps[j];
+        if (!path_to_layer(g, pp, l, &s)) s = 0.0;
+        rk_move(g, pp, l, s, n, qp);
+        if (!path_to_layer(g, pm, l, &s)) s = 0.0;
+        rk_move(g, pm, l, s, n, qm);
+        for (int i = 0; i < 6; ++i) {
+            double dq = qp[i] - qm[i];
+            if (i == 4) dq = wrap_pi(dq);
+            J[i * 6 + j] = dq / (2.0 * eps[j]);
+        }
+    }
+}
+
+/* Move p by the estimated transverse path s onto layer l: the closed-form helix
+ * and its Jacobian in the uniform field, Runge-Kutta steps and the Jacobian of
+ * that map in the parameterised one. */
+static void move_to_layer(const geom_t *g, const double p[6], int l, double s, double q[6], double J[36]) {
+    if (g->field_kind == 0) {
+        helix_move(p, turn_rate(g, p), s, q);
+        prop_jacobian(g, p, l, s, q, J);
+        return;
+    }
+    const int n = rk_steps(p, turn_rate(g, p), s);
+    rk_move(g, p, l, s, n, q);
+    rk_jacobian(g, p, l, n, J);
 }
 
 /* C' = J C J^T (full matrices), symmetrised. */
@@ -383,8 +520,10 @@ static int seed_state(const geom_t *g, const double *h1, const double *h2, const
     if (!(la > 0 && lb > 0 && lc > 0)) return 0;
     double kappa = 2.0 * (ax * by - ay * bx) / (la * lb * lc); /* signed curvature = h */
     double h = kappa;
-    double w = (g->bz != 0.0) ? -h / (OR_K * g->bz) : 0.0;
-    if (g->bz == 0.0) h = 0.0;
+    double B2[3];
+    field_at(g, h2[0], h2[1], h2[2], B2); /* the field at the middle hit sets the scale */
+    double w = (B2[2] != 0.0) ? -h / (OR_K * B2[2]) : 0.0;
+    if (B2[2] == 0.0) h = 0.0;
     double a12 = (h == 0.0) ? 0.0 : asin(fmax(-1.0, fmin(1.0, 0.5 * h * la)));
     double phi0 = atan2(ay, ax) - a12;
     double s13 = (h == 0.0) ? lb : 2.0 * asin(fmax(-1.0, fmin(1.0, 0.5 * h * lb))) / h;
@@ -443,8 +582,8 @@ static void unpack21(const double *in, int64_t stride, double C[36]) {
 #define GEOM_ARGS                                                                                     \
     int n_layers, const int32_t *kind, const double *rz, const double *lo, const double *hi,        \
         const double *su, const double *sv, const double *x0, const double *eloss, double bz,         \
-        int n_regions, const double *edges, const uint64_t *masks
-#define GEOM_PASS n_layers, kind, rz, lo, hi, su, sv, x0, eloss, bz, n_regions, edges, masks
+        int field_kind, double alpha, int n_regions, const double *edges, const uint64_t *masks
+#define GEOM_PASS n_layers, kind, rz, lo, hi, su, sv, x0, eloss, bz, field_kind, alpha, n_regions, edges, masks
 
 /* Propagate p to layer l: writes q, J (6x6 row-major) and s.  Returns 1 on
  * success, 0 if unreachable, -1 on bad arguments. */
@@ -453,9 +592,16 @@ int or_propagate(GEOM_ARGS, const double *p, int l, double *q, double *J, double
     if (geom_init(&g, GEOM_PASS) || l < 0 || l >= g.n) return -1;
     double ss;
     if (!path_to_layer(&g, p, l, &ss)) return 0;
-    helix_move(p, turn_rate(&g, p[3]), ss, q);
-    prop_jacobian(&g, p, l, ss, q, J);
+    move_to_layer(&g, p, l, ss, q, J);
     *s = ss;
+    return 1;
+}
+
+/* The field at (x, y, z). */
+int or_field(GEOM_ARGS, const double *r, double *B) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS)) return -1;
+    field_at(&g, r[0], r[1], r[2], B);
     return 1;
 }
 
@@ -463,7 +609,7 @@ int or_propagate(GEOM_ARGS, const double *p, int l, double *q, double *J, double
 int or_helix_move(GEOM_ARGS, const double *p, double s, double *q) {
     geom_t g;
     if (geom_init(&g, GEOM_PASS)) return -1;
-    helix_move(p, turn_rate(&g, p[3]), s, q);
+    helix_move(p, turn_rate(&g, p), s, q);
     return 1;
 }
 
@@ -567,8 +713,7 @@ int or_fit(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_laye
                 if (k > 0) {
                     double s, q[6], J[36], Cn[36];
                     if (!path_to_layer(&g, p, l, &s)) { st |= OR_ST_UNREACHABLE; continue; }
-                    helix_move(p, turn_rate(&g, p[3]), s, q);
-                    prop_jacobian(&g, p, l, s, q, J);
+                    move_to_layer(&g, p, l, s, q, J);
                     transport(J, C, Cn);
                     memcpy(p, q, sizeof(q));
                     memcpy(C, Cn, sizeof(Cn));
@@ -651,8 +796,7 @@ int or_fit_backward(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t 
                 if (k < nh - 1) {
                     double s, q[6], J[36], Cn[36];
                     if (!path_to_layer(&g, p, l, &s)) { st |= OR_ST_UNREACHABLE; continue; }
-                    helix_move(p, turn_rate(&g, p[3]), s, q);
-                    prop_jacobian(&g, p, l, s, q, J);
+                    move_to_layer(&g, p, l, s, q, J);
                     transport(J, C, Cn);
                     memcpy(p, q, sizeof(q));
                     memcpy(C, Cn, sizeof(Cn));
@@ -798,7 +942,7 @@ static int next_layer(const find_ctx_t *f, cand_t *c, uint64_t mask, double *s_o
         int l = use_cyl ? lc : ld;
         double s = use_cyl ? sc : sd;
         double q[6];
-        helix_move(c->p, turn_rate(g, c->p[3]), s, q);
+        helix_move(c->p, turn_rate(g, c->p), s, q);
         double coord = (g->kind[l] == 0) ? q[2] : hypot(q[0], q[1]);
         double span = g->hi[l] - g->lo[l];
         upd_min(mgeo, fmin(fabs(coord - g->lo[l]), fabs(coord - g->hi[l])) / span);
@@ -937,8 +1081,7 @@ static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *ou
             if (k > 0) {
                 double s, q[6], J[36], Cn[36];
                 if (!path_to_layer(g, c0.p, l, &s)) { ok = 0; break; }
-                helix_move(c0.p, turn_rate(g, c0.p[3]), s, q);
-                prop_jacobian(g, c0.p, l, s, q, J);
+                move_to_layer(g, c0.p, l, s, q, J);
                 transport(J, c0.C, Cn);
                 memcpy(c0.p, q, sizeof(q));
                 memcpy(c0.C, Cn, sizeof(Cn));
@@ -1025,8 +1168,7 @@ static int find_one(const find_ctx_t *f, int ev, const int32_t sh[3], double *ou
             }
             /* propagate the parent in place: its children start from here */
             double q[6], J[36], Cn[36];
-            helix_move(c->p, turn_rate(g, c->p[3]), s, q);
-            prop_jacobian(g, c->p, l, s, q, J);
+            move_to_layer(g, c->p, l, s, q, J);
             transport(J, c->C, Cn);
             memcpy(c->p, q, sizeof(q));
             memcpy(c->C, Cn, sizeof(Cn));

@@ -160,6 +160,88 @@ def _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, x0,
     return out
 
 
+def solenoid_field(bz, alpha, x, y, z):
+    """Second-order solenoid field (tesla) at positions in cm: from the scalar
+    potential solving Laplace's equation with axial symmetry,
+    Bz = bz (1 - alpha (z^2 - r^2 / 2)), Bx = bz alpha x z, By = bz alpha y z."""
+    return bz * alpha * x * z, bz * alpha * y * z, bz * (1.0 - alpha * (z * z - 0.5 * (x * x + y * y)))
+
+
+def _field_rhs(bz, alpha, lam, r, t):
+    """d(position)/dS, d(direction)/dS for unit charge with lam = q/p (1/GeV)."""
+    bx, by, bzz = solenoid_field(bz, alpha, r[0], r[1], r[2])
+    k = K_FIELD * lam
+    dt = np.stack([k * (t[1] * bzz - t[2] * by), k * (t[2] * bx - t[0] * bzz), k * (t[0] * by - t[1] * bx)])
+    return t, dt
+
+
+def _field_step(bz, alpha, lam, r, t, d):
+    """Classical Runge-Kutta step of path d (arrays of shape [3, n])."""
+    a1, b1 = _field_rhs(bz, alpha, lam, r, t)
+    a2, b2 = _field_rhs(bz, alpha, lam, r + 0.5 * d * a1, t + 0.5 * d * b1)
+    a3, b3 = _field_rhs(bz, alpha, lam, r + 0.5 * d * a2, t + 0.5 * d * b2)
+    a4, b4 = _field_rhs(bz, alpha, lam, r + d * a3, t + d * b3)
+    return r + d / 6.0 * (a1 + 2 * a2 + 2 * a3 + a4), t + d / 6.0 * (b1 + 2 * b2 + 2 * b3 + b4)
+
+
+FIELD_STEP = 0.5  # cm of path per generator step in the parameterised field
+
+
+def _field_cylinder_crossings(phi0, z0, theta, q, pt, bz, alpha, rz, ds=FIELD_STEP):
+    """Crossings of every cylinder (in radius order) of particles moving in the
+    parameterised field (solenoid_field): the equation of motion integrated in
+    fixed steps of ds cm of path; a step that ends beyond the next radius is
+    replaced by Newton steps from its start onto the cylinder.  A particle whose
+    radius stops growing before the next cylinder (it turns back) crosses no
+    further layer.  Returns per (particle, layer) the path from the vertex, the
+    crossing point and (q/pT, phi, theta) there (q/pT = q / (p sin theta) with
+    |p| fixed: it changes where the field bends theta); NaN where the cylinder
+    is not reached."""
+    P, L = phi0.shape[0], rz.shape[0]
+    out = {k: np.full((P, L), np.nan) for k in ("S", "X", "Y", "Z", "W", "PHI", "TH")}
+    r = np.stack([np.zeros(P), np.zeros(P), z0.astype(np.float64)])
+    t = np.stack([np.sin(theta) * np.cos(phi0), np.sin(theta) * np.sin(phi0), np.cos(theta)])
+    lam = q * np.sin(theta) / pt
+    S = np.zeros(P)
+    alive = np.ones(P, dtype=bool)
+    for l in np.argsort(rz):
+        R = rz[l]
+        todo = alive.copy()
+        for _ in range(100000):
+            idx = np.flatnonzero(todo)
+            if idx.size == 0:
+                break
+            rn, tn = _field_step(bz, alpha, lam[idx], r[:, idx], t[:, idx], ds)
+            cross = np.hypot(rn[0], rn[1]) >= R
+            # particles whose step ends beyond R: Newton steps from the step's start
+            c = idx[cross]
+            if c.size:
+                rc, tc, Sc = r[:, c], t[:, c], S[c].copy()
+                for _n in range(6):
+                    rr = np.hypot(rc[0], rc[1])
+                    d = (R - rr) / ((rc[0] * tc[0] + rc[1] * tc[1]) / rr)
+                    rc, tc = _field_step(bz, alpha, lam[c], rc, tc, d)
+                    Sc = Sc + d
+                r[:, c], t[:, c], S[c] = rc, tc, Sc
+                tt = np.hypot(tc[0], tc[1])
+                out["S"][c, l] = Sc
+                out["X"][c, l], out["Y"][c, l], out["Z"][c, l] = rc[0], rc[1], rc[2]
+                th = np.arctan2(tt, tc[2])
+                out["W"][c, l] = lam[c] / np.sin(th)
+                out["PHI"][c, l] = np.arctan2(tc[1], tc[0])
+                out["TH"][c, l] = th
+                todo[c] = False
+            # the others take the step; those turning back are done for good
+            k = idx[~cross]
+            if k.size:
+                rk, tk = rn[:, ~cross], tn[:, ~cross]
+                back = (rk[0] * tk[0] + rk[1] * tk[1]) <= 0.0
+                r[:, k], t[:, k], S[k] = rk, tk, S[k] + ds
+                todo[k[back]] = False
+                alive[k[back]] = False
+    return out
+
+
 @dataclass
 class Batch:
     """A batch of events, hit arrays concatenated event after event.
@@ -209,7 +291,7 @@ class Batch:
 def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: int | None = None,
                base_seed: int = BASE_SEED, ineff: float | None = None, noise_scale: float = 1.0,
                eta_max: float | None = None, smear: bool = True, overlap: float = 0.0, material: float = 0.0,
-               eloss: float = 0.0):
+               eloss: float = 0.0, field_alpha: float | None = None):
     """One event as a dict of per-event arrays (local hit and particle indices).
 
     overlap > 0: each signal hit gets, with that probability, a second hit of the
@@ -223,7 +305,12 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
     they cross (see _scattered_cylinder_crossings); the kicks come from a stream
     of their own, so the other random numbers do not change.  eloss > 0 (with
     material): the mean energy loss per radiation length at minimum ionisation
-    (GeV), lost at each layer crossed."""
+    (GeV), lost at each layer crossed.
+
+    field_alpha (layouts of cylinders only, no material): the particles move in
+    the parameterised field solenoid_field(bz, field_alpha, ...) instead of the
+    uniform one (see _field_cylinder_crossings); no random numbers are drawn
+    for it."""
     cfg = get_config(config)
     layers = cfg["layers"]
     rng = _rng(config, event, base_seed)
@@ -268,7 +355,12 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
         ok = np.isfinite(sd) & (sd > 0) & (sd < s_max[:, None])
         S[:, dsk] = np.where(ok, sd, np.nan)
     ms = None
-    if material > 0.0:
+    if field_alpha is not None:
+        if dsk.size or material > 0.0:
+            raise ValueError("the parameterised field is supported for layouts of cylinders without material")
+        ms = _field_cylinder_crossings(phi0, z0, theta, q, pt, bz, float(field_alpha), rz)
+        S = ms["S"]
+    elif material > 0.0:
         if dsk.size:
             raise ValueError("material is supported for layouts of cylinders only")
         key = (int(base_seed) << 64) | (CONFIG_IDS[config] << 32) | (int(event) & 0xFFFFFFFF)
@@ -455,6 +547,6 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
         particle_nhits=np.concatenate(p_nh).astype(np.int32),
         particle_event=np.concatenate(p_ev).astype(np.int32),
         particle_par=np.concatenate(p_par, axis=1),
-        meta=dict(events=events, base_seed=base_seed),
+        meta=dict(events=events, base_seed=base_seed, field_alpha=kw.get("field_alpha")),
         seed_dup_of=np.concatenate(seed_dup).astype(np.int32),
     )
