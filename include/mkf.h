@@ -136,6 +136,24 @@ mkf_status mkf_geometry_load(mkf_ctx *ctx, const mkf_layer *layers, int32_t n_la
  * >= 1000). */
 mkf_status mkf_geometry_material(mkf_ctx *ctx, const float *x0, const float *eloss, int32_t n_layers);
 
+/* Field type (Sec. 2.1: a constant or a parameterised magnetic field, chosen
+ * per propagation) for the geometry loaded last (mkf_geometry_load resets it to
+ * the uniform field).  kind 0: uniform Bz = bz_tesla, propagation along the
+ * closed-form helix.  kind 1: the field of a solenoid near its centre to
+ * second order, Bz = bz (1 - alpha (z^2 - r^2 / 2)), Bx = bz alpha x z,
+ * By = bz alpha y z (cm, tesla; divergence- and curl-free), alpha in 1/cm^2
+ * (0 = the uniform field integrated numerically).  In it fit and finding
+ * propagate by classical fourth-order Runge-Kutta steps in path length (at most
+ * 0.05 rad of turning and 10 cm per step, at most 16 steps, over the path that
+ * the helix in the local axial field estimates, then two Newton steps onto the
+ * surface) and transport the covariance with the Jacobian integrated along the
+ * trajectory (the field's gradient left out); layer order and extent checks
+ * use the local helix, and seeds take their curvature scale from the field at
+ * the middle hit.  The material effects apply as set.  Hit bins stay valid.
+ * Errors: MKF_ERR_ARG (kind not 0 or 1, alpha not finite or |alpha| >= 1e-2),
+ * MKF_ERR_GEOMETRY (no geometry). */
+mkf_status mkf_geometry_field(mkf_ctx *ctx, int32_t kind, float alpha);
+
 /* ------------------------------------------------------------------------ */
 /* Hit binning (per event and layer, phi x z or phi x r bins)               */
 /* ------------------------------------------------------------------------ */

@@ -282,10 +282,24 @@ static int rk_steps(const double p[6], double h, double s) {
     return n > OR_RK_MAXN ? OR_RK_MAXN : (int)n;
 }
 
+/* Root nearest 0 of a d^2 + b d + c = 0; the parabola's vertex when it has no
+ * real root, the linear root when a = 0. */
+static double nearest_root(double a, double b, double c) {
+    const double disc = b * b - 4.0 * a * c;
+    if (a == 0.0) return b != 0.0 ? -c / b : 0.0;
+    if (disc < 0.0) return -b / (2.0 * a);
+    const double q = -0.5 * (b + copysign(sqrt(disc), b));
+    if (q == 0.0) return 0.0;
+    const double r1 = q / a, r2 = c / q;
+    return fabs(r1) < fabs(r2) ? r1 : r2;
+}
+
 /* Move p onto layer l: n equal steps over the path s estimated by the helix in
- * the local axial field, then OR_RK_NEWTON Newton steps on the distance to the
- * surface (the signed path to it along the current direction, linearised:
- * (R - r) / (dr/dS) on a cylinder, (Z - z) / Tz on a disk). */
+ * the local axial field, then OR_RK_NEWTON correction steps onto the surface:
+ * on a cylinder the nearest root of the second-order expansion of
+ * x(S)^2 + y(S)^2 - R^2 about the current point (the bending term keeps it
+ * exact enough where the track meets the cylinder at a grazing angle), on a
+ * disk the linear (Z - z) / Tz. */
 static void rk_move(const geom_t *g, const double p[6], int l, double s, int n, double q[6]) {
     const double st = sin(p[5]);
     double X[7] = {p[0], p[1], p[2], st * cos(p[4]), st * sin(p[4]), cos(p[5]), p[3] * st};
@@ -294,8 +308,12 @@ static void rk_move(const geom_t *g, const double p[6], int l, double s, int n, 
     for (int it = 0; it < OR_RK_NEWTON; ++it) {
         double d;
         if (g->kind[l] == 0) {
-            const double r = hypot(X[0], X[1]);
-            d = (g->rz[l] - r) / ((X[0] * X[3] + X[1] * X[4]) / r);
+            double dX[7];
+            eom(g, X, dX);
+            const double c = X[0] * X[0] + X[1] * X[1] - g->rz[l] * g->rz[l];
+            const double bq = 2.0 * (X[0] * X[3] + X[1] * X[4]);
+            const double aq = X[3] * X[3] + X[4] * X[4] + X[0] * dX[3] + X[1] * dX[4];
+            d = nearest_root(aq, bq, c);
         } else {
             d = (g->rz[l] - X[2]) / X[5];
         }

@@ -57,10 +57,11 @@ def mkf_sync(ctx) -> None:
     N.check("mkf_sync", N.lib().mkf_sync(ctx))
 
 
-def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None) -> None:
+def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None, field_alpha=None) -> None:
     """layers: list of dicts (kind, r_or_z, lo, hi, sigma_u, sigma_v, n_phi, n_zr,
     optional x0 = material in radiation lengths); plans: list of layer-id lists,
-    one per region (None = one region, all layers)."""
+    one per region (None = one region, all layers); field_alpha: None for the
+    uniform field, else the parameterised field's fall-off (1/cm^2)."""
     arr = (N.MkfLayer * len(layers))()
     for i, d in enumerate(layers):
         arr[i] = N.MkfLayer(int(d["kind"]), float(d["r_or_z"]), float(d["lo"]), float(d["hi"]),
@@ -82,6 +83,8 @@ def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None)
     if any(float(d.get("x0", 0.0)) > 0.0 for d in layers):
         mkf_geometry_material(ctx, [float(d.get("x0", 0.0)) for d in layers],
                               [float(d.get("eloss", 0.0)) for d in layers])
+    if field_alpha is not None:
+        mkf_geometry_field(ctx, 1, field_alpha)
 
 
 def mkf_geometry_material(ctx, x0, eloss=None) -> None:
@@ -92,6 +95,12 @@ def mkf_geometry_material(ctx, x0, eloss=None) -> None:
     arr = (C.c_float * max(1, len(x0)))(*[float(v) for v in x0])
     earr = None if eloss is None else (C.c_float * max(1, len(eloss)))(*[float(v) for v in eloss])
     N.check("mkf_geometry_material", N.lib().mkf_geometry_material(ctx, arr, earr, len(x0)))
+
+
+def mkf_geometry_field(ctx, kind: int, alpha: float = 0.0) -> None:
+    """Field type of the loaded geometry: 0 uniform, 1 parameterised
+    (Bz = bz (1 - alpha (z^2 - r^2 / 2)), Br = bz alpha r z; alpha in 1/cm^2)."""
+    N.check("mkf_geometry_field", N.lib().mkf_geometry_field(ctx, int(kind), float(alpha)))
 
 
 class HitBins:
@@ -360,9 +369,12 @@ class Context:
     def sync(self):
         mkf_sync(self.handle)
 
-    def geometry_load(self, layers, bz, plans=None, region_eta_edges=None):
-        mkf_geometry_load(self.handle, layers, bz, plans, region_eta_edges)
+    def geometry_load(self, layers, bz, plans=None, region_eta_edges=None, field_alpha=None):
+        mkf_geometry_load(self.handle, layers, bz, plans, region_eta_edges, field_alpha)
         self.layers = [dict(d) for d in layers]
+
+    def geometry_field(self, kind, alpha=0.0):
+        mkf_geometry_field(self.handle, kind, alpha)
 
     def hits_bin(self, xyz, layer, event_offsets, bins=None):
         return mkf_hits_bin(self.handle, xyz, layer, event_offsets, bins, self.device)

@@ -122,3 +122,13 @@ extern "C" mkf_status mkf_geometry_material(mkf_ctx *ctx, const float *x0, const
     }
     return MKF_OK;
 }
+
+extern "C" mkf_status mkf_geometry_field(mkf_ctx *ctx, int32_t kind, float alpha) {
+    if (!ctx) return MKF_ERR_ARG;
+    if (kind != 0 && kind != 1) return MKF_ERR_ARG;
+    if (!(fabsf(alpha) < 1.0e-2f)) return MKF_ERR_ARG;
+    if (!ctx->has_geom) return MKF_ERR_GEOMETRY;
+    ctx->geom.field_kind = kind;
+    ctx->geom.alpha = kind == 1 ? alpha : 0.f;
+    return MKF_OK;
+}

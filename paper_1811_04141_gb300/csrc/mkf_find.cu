@@ -128,11 +128,12 @@ __device__ __forceinline__ Book unpack_book(uint32_t w) {
 // Next layer of a candidate (the nearer of its next cylinder and next disk in
 // path length, within the region's layer mask); layers crossed outside their
 // extent, and layers already behind the candidate, are passed over.  Returns
-// the layer id and the path, or -1.
-__device__ __forceinline__ int next_layer(const Geom &G, unsigned long long mask, const float p[6], const Lo &lo,
-                                          float sphi, float cphi, float cot, int dir, int &ncyl, int &ndsk,
-                                          float &s_out) {
-    const float h = -p[3] * G.kb;
+// the layer id and the path, or -1.  kbl: K Bz at the candidate (the helix of
+// the local axial field estimates the paths in the parameterised field).
+__device__ __forceinline__ int next_layer(const Geom &G, float kbl, unsigned long long mask, const float p[6],
+                                          const Lo &lo, float sphi, float cphi, float cot, int dir, int &ncyl,
+                                          int &ndsk, float &s_out) {
+    const float h = -p[3] * kbl;
     const float rcur = sqrtf(fmaf(p[0], p[0], p[1] * p[1])), zcur = p[2] + lo.z;
     for (int guard = 0; guard < 2 * kMaxLayers + 2; ++guard) {
         // layers outside the region's plan, and layers already behind the
@@ -296,8 +297,9 @@ struct Expansion {
 // list of its N best compatible hits (chi2, hit index, residual u, v) at list
 // stride `ls` (lane-interleaved shared memory in the finder, contiguous local
 // arrays in the seed kernel).  p, lo, C move onto the layer; a candidate with no
-// layer left is marked done.
-template <bool kMaterial>
+// layer left is marked done.  kPhys: 0 uniform field, 1 material effects,
+// 2 parameterised field (Runge-Kutta propagation) and material effects.
+template <int kPhys>
 __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev, unsigned long long mask, int dir,
                                        int N, float cut, float p[6], Lo &lo, float C[21], Book &bk, Innov &I,
                                        uint32_t &status, int &c_cl, int &c_ht, float *lchi, int *lorig, float *lu,
@@ -310,7 +312,8 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
     X.nlist = 0;
     X.n_compat = 0;
     float s = 0.f;
-    const int l = finite_state(p) ? next_layer(G, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
+    const float kbl = kPhys == 2 ? G.kb * bz_factor(G.alpha, p[0], p[1], p[2]) : G.kb;
+    const int l = finite_state(p) ? next_layer(G, kbl, mask, p, lo, sphi, cphi, cot, dir, bk.ncyl, bk.ndsk, s) : -2;
     X.layer = l;
     if (l == -2) status |= MKF_ST_NONFINITE;
     if (l < 0) {
@@ -318,8 +321,11 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
         return;
     }
     const LayerDesc &Ld = G.L[l];
-    propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-    if (kMaterial) {
+    if (kPhys == 2)
+        propagate_field(Ld, G.kb, G.alpha, p, lo, C, sphi, cphi, -p[3] * kbl, s);
+    else
+        propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+    if (kPhys >= 1) {
         add_scattering(Ld, p, C);
         apply_eloss(Ld, p, C, 1.f);
     }
@@ -406,6 +412,8 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
 // then the Kalman fit through them (the first hit without propagation), the
 // tracking region from the seed's eta, the direction along z and the first
 // layers beyond the third hit.
+// kParamField: the parameterised field (Runge-Kutta propagation).
+template <bool kParamField>
 __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindArgs A) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= A.n_seeds) return;
@@ -440,7 +448,9 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
     Lo lo{0.f, 0.f, 0.f, 0.f};
     if (ok) {
         const float h1[3] = {hx[0], hy[0], hz[0]}, h2[3] = {hx[1], hy[1], hz[1]}, h3[3] = {hx[2], hy[2], hz[2]};
-        ok = seed_state(G.L[hl[0]], G.kb, h1, h2, h3, p, C, eta);
+        // the parameterised field at the middle hit sets the curvature scale
+        const float kbs = kParamField ? G.kb * bz_factor(G.alpha, h2[0], h2[1], h2[2]) : G.kb;
+        ok = seed_state(G.L[hl[0]], kbs, h1, h2, h3, p, C, eta);
     }
     for (int k = 0; k < 3 && ok; ++k) {
         const LayerDesc &Ld = G.L[hl[k]];
@@ -448,11 +458,15 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
             float sphi, cphi, s;
             sincos_pair(p[4], lo.phi, sphi, cphi);
             const float cot = cot_of(p[5]);
-            if (!path_to_layer(Ld, G.kb, p, lo, sphi, cphi, cot, s)) {
+            const float kbl = kParamField ? G.kb * bz_factor(G.alpha, p[0], p[1], p[2]) : G.kb;
+            if (!path_to_layer(Ld, kbl, p, lo, sphi, cphi, cot, s)) {
                 ok = false;
                 break;
             }
-            propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+            if (kParamField)
+                propagate_field(Ld, G.kb, G.alpha, p, lo, C, sphi, cphi, -p[3] * kbl, s);
+            else
+                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
             add_scattering(Ld, p, C);
             apply_eloss(Ld, p, C, 1.f);
         }
@@ -522,7 +536,8 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
         float lchi[MKF_MAX_NBEST], lu[MKF_MAX_NBEST], lv[MKF_MAX_NBEST];
         int lorig[MKF_MAX_NBEST];
         Expansion X;
-        expand<true>(A, G, ev, mask, dir, N, A.cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi, lorig, lu, lv, 1, X);
+        expand<kParamField ? 2 : 1>(A, G, ev, mask, dir, N, A.cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi, lorig,
+                                    lu, lv, 1, X);
         nlist = X.nlist;
         searched = X.searched;
         nbeam = min(searched ? nlist + 1 : 1, N);
@@ -568,9 +583,10 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
 }
 
 // kLearned: the variant with learned pruning and the feature dump compiled in;
-// the plain finder is built without them.  kMaterial: multiple scattering
-// compiled in (selected when any layer has material).
-template <bool kLearned, bool kMaterial>
+// the plain finder is built without them.  kPhys: 0 uniform field; 1 the
+// material effects compiled in (selected when any layer has material); 2 the
+// parameterised field (Runge-Kutta propagation) with the material effects.
+template <bool kLearned, int kPhys>
 __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ FindArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Geom SG;
@@ -750,7 +766,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             // ---- 1. expansion: next layer, propagation, window search
             Expansion X{-1, false, 0, 0, 0.f};
             if (active) {
-                expand<kMaterial>(A, G, ev, mask, dir, N, cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi + lane, lorig + lane,
+                expand<kPhys>(A, G, ev, mask, dir, N, cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi + lane, lorig + lane,
                        lu + lane, lv + lane, 32, X);
             }
             // learned pruning / feature dump over the candidate's list (its N best
@@ -1017,19 +1033,21 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     // raise the kernel's dynamic shared-memory limit only when needed (not during
     // a stream capture after the first call)
     const bool learned = params->mlp_bf16 || params->feat_out;
-    // material anywhere in the geometry selects the variant with the scattering
-    // noise compiled in; the others carry no trace of it
-    bool material = false;
-    for (int l = 0; l < ctx->geom.n_layers; ++l) material = material || ctx->geom.L[l].x0 > 0.f;
-    const int vi = (learned ? 2 : 0) + (material ? 1 : 0);
-    const void *const kfns[4] = {reinterpret_cast<const void *>(find_kernel<false, false>),
-                                 reinterpret_cast<const void *>(find_kernel<false, true>),
-                                 reinterpret_cast<const void *>(find_kernel<true, false>),
-                                 reinterpret_cast<const void *>(find_kernel<true, true>)};
+    // material anywhere in the geometry selects the variant with the material
+    // effects compiled in, the parameterised field the one with Runge-Kutta
+    // propagation; the others carry no trace of them
+    const int phys = mkf_phys_variant(ctx->geom);
+    const int vi = (learned ? 3 : 0) + phys;
+    const void *const kfns[6] = {reinterpret_cast<const void *>(find_kernel<false, 0>),
+                                 reinterpret_cast<const void *>(find_kernel<false, 1>),
+                                 reinterpret_cast<const void *>(find_kernel<false, 2>),
+                                 reinterpret_cast<const void *>(find_kernel<true, 0>),
+                                 reinterpret_cast<const void *>(find_kernel<true, 1>),
+                                 reinterpret_cast<const void *>(find_kernel<true, 2>)};
     const void *kfn = kfns[vi];
     if (static_cast<int>(smem) > ctx->find_smem_attr) {
         const int want = static_cast<int>(std::max<size_t>(smem, 48 * 1024));
-        for (int v = 0; v < 4; ++v)
+        for (int v = 0; v < 6; ++v)
             MKF_CUDA_TRY(cudaFuncSetAttribute(kfns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, want));
         ctx->find_smem_attr = want;
     }
@@ -1051,7 +1069,10 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
         MKF_CUDA_TRY(cudaMemsetAsync(A.event_times, 0, sizeof(uint64_t) * bins->n_events, ctx->stream));
         MKF_CUDA_TRY(cudaMemsetAsync(A.event_times + bins->n_events, 0xff, sizeof(uint64_t), ctx->stream));
     }
-    seed_kernel<<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A);
+    if (phys == 2)
+        seed_kernel<true><<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A);
+    else
+        seed_kernel<false><<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A);
     MKF_CUDA_TRY(cudaGetLastError());
     // persistent grid: as many blocks as fit on the device at once, or fewer
     const int spw = 32 / N;
@@ -1069,10 +1090,12 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     const int per_sm = ctx->find_occ_blocks[vi];
     const int blocks = std::max(1, std::min(need, std::max(1, per_sm) * ctx->num_sms));
     switch (vi) {
-        case 0: find_kernel<false, false><<<blocks, threads, smem, ctx->stream>>>(A); break;
-        case 1: find_kernel<false, true><<<blocks, threads, smem, ctx->stream>>>(A); break;
-        case 2: find_kernel<true, false><<<blocks, threads, smem, ctx->stream>>>(A); break;
-        default: find_kernel<true, true><<<blocks, threads, smem, ctx->stream>>>(A); break;
+        case 0: find_kernel<false, 0><<<blocks, threads, smem, ctx->stream>>>(A); break;
+        case 1: find_kernel<false, 1><<<blocks, threads, smem, ctx->stream>>>(A); break;
+        case 2: find_kernel<false, 2><<<blocks, threads, smem, ctx->stream>>>(A); break;
+        case 3: find_kernel<true, 0><<<blocks, threads, smem, ctx->stream>>>(A); break;
+        case 4: find_kernel<true, 1><<<blocks, threads, smem, ctx->stream>>>(A); break;
+        default: find_kernel<true, 2><<<blocks, threads, smem, ctx->stream>>>(A); break;
     }
     MKF_CUDA_TRY(cudaGetLastError());
     return MKF_OK;

@@ -48,10 +48,13 @@ __device__ __forceinline__ void reverse_state(float p[6], Lo &lo, float C[21]) {
 }
 
 // kBackward: hits in reverse order from the given state at the last hit, turned
-// around and inflated; the result at the first hit is turned back.  kMaterial:
-// multiple scattering compiled in (selected when any layer has material).
-template <bool kBackward, bool kMaterial>
-__global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ FitArgs A) {
+// around and inflated; the result at the first hit is turned back.  kPhys: 0
+// uniform field without material; 1 material effects compiled in (selected
+// when any layer has material); 2 the parameterised field (Runge-Kutta
+// propagation) with the material effects.
+template <bool kBackward, int kPhys>
+__global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __grid_constant__ FitArgs A) {
+    constexpr bool kMaterial = kPhys >= 1, kParamField = kPhys == 2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= A.n) return;
     const Geom &G = A.G;
@@ -93,7 +96,9 @@ __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ Fit
             h1[0] = A.X[first[0]]; h1[1] = A.Y[first[0]]; h1[2] = A.Z[first[0]];
             h2[0] = A.X[first[1]]; h2[1] = A.Y[first[1]]; h2[2] = A.Z[first[1]];
             h3[0] = A.X[first[2]]; h3[1] = A.Y[first[2]]; h3[2] = A.Z[first[2]];
-            ok = seed_state(G.L[l0], G.kb, h1, h2, h3, p, C, eta);
+            // the parameterised field at the middle hit sets the curvature scale
+            const float kbs = kParamField ? G.kb * bz_factor(G.alpha, h2[0], h2[1], h2[2]) : G.kb;
+            ok = seed_state(G.L[l0], kbs, h1, h2, h3, p, C, eta);
         }
     }
     if (!ok) st |= MKF_ST_BADSEED;
@@ -115,12 +120,17 @@ __global__ void __launch_bounds__(128, 8) fit_kernel(const __grid_constant__ Fit
                 float sphi, cphi;
                 sincos_pair(p[4], lo.phi, sphi, cphi);
                 const float cot = cot_of(p[5]);
+                // path estimate from the helix in the local axial field
+                const float kbl = kParamField ? G.kb * bz_factor(G.alpha, p[0], p[1], p[2]) : G.kb;
                 float s;
-                if (!path_to_layer(Ld, G.kb, p, lo, sphi, cphi, cot, s)) {
+                if (!path_to_layer(Ld, kbl, p, lo, sphi, cphi, cot, s)) {
                     st |= MKF_ST_UNREACHABLE;
                     continue;
                 }
-                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+                if (kParamField)
+                    propagate_field(Ld, G.kb, G.alpha, p, lo, C, sphi, cphi, -p[3] * kbl, s);
+                else
+                    propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
                 if (!kBackward && kMaterial) {
                     add_scattering(Ld, p, C);
                     apply_eloss(Ld, p, C, 1.f);
@@ -203,12 +213,14 @@ static mkf_status launch_fit(mkf_ctx *ctx, const float *xyz, const int32_t *hit_
     A.fault = ctx->fault;
     const int threads = 128;
     const int blocks = (n + threads - 1) / threads;
-    bool material = false;
-    for (int l = 0; l < ctx->geom.n_layers; ++l) material = material || ctx->geom.L[l].x0 > 0.f;
-    if (backward && material) fit_kernel<true, true><<<blocks, threads, 0, ctx->stream>>>(A);
-    else if (backward) fit_kernel<true, false><<<blocks, threads, 0, ctx->stream>>>(A);
-    else if (material) fit_kernel<false, true><<<blocks, threads, 0, ctx->stream>>>(A);
-    else fit_kernel<false, false><<<blocks, threads, 0, ctx->stream>>>(A);
+    switch (mkf_phys_variant(ctx->geom) + (backward ? 3 : 0)) {
+        case 0: fit_kernel<false, 0><<<blocks, threads, 0, ctx->stream>>>(A); break;
+        case 1: fit_kernel<false, 1><<<blocks, threads, 0, ctx->stream>>>(A); break;
+        case 2: fit_kernel<false, 2><<<blocks, threads, 0, ctx->stream>>>(A); break;
+        case 3: fit_kernel<true, 0><<<blocks, threads, 0, ctx->stream>>>(A); break;
+        case 4: fit_kernel<true, 1><<<blocks, threads, 0, ctx->stream>>>(A); break;
+        default: fit_kernel<true, 2><<<blocks, threads, 0, ctx->stream>>>(A); break;
+    }
     MKF_CUDA_TRY(cudaGetLastError());
     return MKF_OK;
 }

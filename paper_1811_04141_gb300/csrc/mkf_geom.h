@@ -23,6 +23,8 @@ inline mkf_status mkf_build_geom(const mkf_layer *layers, int32_t n_layers, cons
     std::memset(&G, 0, sizeof(G));
     G.n_layers = n_layers;
     G.kb = mkf::kField * bz_tesla;
+    G.field_kind = 0;  // the parameterised field comes from mkf_geometry_field
+    G.alpha = 0.f;
     int64_t base = 0;
     for (int l = 0; l < n_layers; ++l) {
         const mkf_layer &s = layers[l];

@@ -36,7 +36,9 @@ struct mkf_ctx {
     size_t scratch_bytes;
     int num_sms;
     int find_smem_attr;  // dynamic shared memory the find kernel is configured for
-    int find_occ_threads[4], find_occ_smem[4], find_occ_blocks[4];  // cached occupancy (plain, learned) x (material)
+    // cached occupancy per finder variant: (plain, learned) x (uniform field,
+    // material, parameterised field)
+    int find_occ_threads[6], find_occ_smem[6], find_occ_blocks[6];
 };
 
 struct mkf_hitbins {
@@ -80,6 +82,15 @@ struct DeviceGuard {
 
 // Context scratch of at least `bytes` (grown with cudaMalloc, never shrunk).
 mkf_status mkf_scratch(mkf_ctx *ctx, size_t bytes, void **out);
+
+// Physics variant of the kernels for a geometry: 2 parameterised field (with
+// the material effects compiled in), 1 material in some layer, 0 neither.
+inline int mkf_phys_variant(const mkf::Geom &G) {
+    if (G.field_kind == 1) return 2;
+    for (int l = 0; l < G.n_layers; ++l)
+        if (G.L[l].x0 > 0.f) return 1;
+    return 0;
+}
 
 // Exclusive scan of counts [n] into offsets [n + 1] (offsets[n] = the total),
 // enqueued on `s`; tilesums is scratch of mkf_scan_tilesums(n) ints.

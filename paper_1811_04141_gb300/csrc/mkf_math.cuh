@@ -52,7 +52,9 @@ struct Geom {
     int n_layers;
     float cyl_hi_beyond[kMaxLayers];  // max z-extent end of the cylinders at and after each sorted position
     float cyl_lo_beyond[kMaxLayers];  // min z-extent start of the same
-    float kb;  // K * Bz
+    float kb;  // K * Bz (at the centre for the parameterised field)
+    int field_kind;  // 0 uniform, 1 parameterised (RK4 propagation)
+    float alpha;     // parameterised field: fall-off coefficient, 1/cm^2
     int n_cyl, n_dsk;
     int bins_per_event;
     int n_regions;
@@ -347,6 +349,287 @@ __device__ __forceinline__ void propagate_transport(const LayerDesc& Ld, float k
     }
     df_add(p[4], lo.phi, 2.f * a);
     df_wrap_pi(p[4], lo.phi);
+}
+
+// ---------------------------------------------------------------------------
+// Parameterised field (Sec. 2.1: a constant or a parameterised field, chosen
+// per propagation).  The field of a solenoid near its centre to second order,
+// from an axially symmetric scalar potential (divergence- and curl-free):
+// K B = kb (alpha x z, alpha y z, 1 - alpha (z^2 - r^2 / 2)), kb = K Bz(0).
+// Propagation integrates the equation of motion with the path length S as
+// variable, dr/dS = T, dT/dS = lambda T x (K B), lambda = q/p, by classical
+// Runge-Kutta steps.
+
+constexpr float kRkTurn = 0.05f;  // largest turning angle per step, rad
+constexpr float kRkLen = 10.f;    // largest step, cm of path
+constexpr int kRkMaxN = 16;       // most steps per propagation
+constexpr int kRkNewton = 2;      // correction steps onto the surface
+
+// Bz(x, y, z) / Bz(0).
+__device__ __forceinline__ float bz_factor(float alpha, float x, float y, float z) {
+    return fmaf(-alpha, fmaf(z, z, -0.5f * fmaf(x, x, y * y)), 1.f);
+}
+
+__device__ __forceinline__ void kfield(float kb, float alpha, float x, float y, float z, float b[3]) {
+    const float kaz = kb * alpha * z;
+    b[0] = kaz * x;
+    b[1] = kaz * y;
+    b[2] = kb * bz_factor(alpha, x, y, z);
+}
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3]) {
+    c[0] = fmaf(a[1], b[2], -a[2] * b[1]);
+    c[1] = fmaf(a[2], b[0], -a[0] * b[2]);
+    c[2] = fmaf(a[0], b[1], -a[1] * b[0]);
+}
+
+// Trajectory data of one Runge-Kutta stage: position, direction, field K B,
+// T x (K B).
+struct RkStage {
+    float x[3], T[3], b[3], tb[3];
+};
+
+__device__ __forceinline__ void rk_stage(float kb, float alpha, const float r0[3], const float d[3], const float T[3],
+                                         RkStage &S) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        S.x[i] = r0[i] + d[i];
+        S.T[i] = T[i];
+    }
+    kfield(kb, alpha, S.x[0], S.x[1], S.x[2], S.b);
+    cross3(T, S.b, S.tb);
+}
+
+// Variational equation of the direction at a stage: d(dT)/dS = dlambda (T x b)
+// + lambda (dT x b) + lambda T x (grad b . dr), with the field's gradient
+// grad b . dr = kb alpha (z dx + x dz, z dy + y dz, x dx + y dy - 2 z dz).
+__device__ __forceinline__ void tangent_rhs(const RkStage &S, float kba, float lam, float dlam, const float dr[3],
+                                            const float dt[3], float out[3]) {
+    const float x = S.x[0], y = S.x[1], z = S.x[2];
+    const float g[3] = {kba * fmaf(z, dr[0], x * dr[2]), kba * fmaf(z, dr[1], y * dr[2]),
+                        kba * fmaf(x, dr[0], fmaf(y, dr[1], -2.f * z * dr[2]))};
+    float u[3], v[3];
+    cross3(dt, S.b, u);
+    cross3(S.T, g, v);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i] = fmaf(dlam, S.tb[i], lam * (u[i] + v[i]));
+}
+
+// One classical Runge-Kutta step of path hs for the trajectory (d, T) and then,
+// over the same stages, for the six tangent columns (Dr, DT) of the parameters
+// (x, y, z, q/pT, phi, theta), whose lambda derivatives are dl.
+__device__ __forceinline__ void rk_step(float kb, float alpha, const float r0[3], float lam, const float dl[6],
+                                        float d[3], float T[3], float Dr[6][3], float DT[6][3], float hs) {
+    RkStage S[4];
+    const float hh = 0.5f * hs, h6 = hs * (1.f / 6.f);
+    float dd[3], tt[3], sd[3], st[3];
+    rk_stage(kb, alpha, r0, d, T, S[0]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dd[i] = fmaf(hh, T[i], d[i]);
+        tt[i] = fmaf(hh * lam, S[0].tb[i], T[i]);
+        sd[i] = T[i];
+        st[i] = S[0].tb[i];
+    }
+    rk_stage(kb, alpha, r0, dd, tt, S[1]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dd[i] = fmaf(hh, S[1].T[i], d[i]);
+        tt[i] = fmaf(hh * lam, S[1].tb[i], T[i]);
+        sd[i] = fmaf(2.f, S[1].T[i], sd[i]);
+        st[i] = fmaf(2.f, S[1].tb[i], st[i]);
+    }
+    rk_stage(kb, alpha, r0, dd, tt, S[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dd[i] = fmaf(hs, S[2].T[i], d[i]);
+        tt[i] = fmaf(hs * lam, S[2].tb[i], T[i]);
+        sd[i] = fmaf(2.f, S[2].T[i], sd[i]);
+        st[i] = fmaf(2.f, S[2].tb[i], st[i]);
+    }
+    rk_stage(kb, alpha, r0, dd, tt, S[3]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        d[i] = fmaf(h6, sd[i] + S[3].T[i], d[i]);
+        T[i] = fmaf(h6 * lam, st[i] + S[3].tb[i], T[i]);
+    }
+    const float kba = kb * alpha;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float ar[3], at[3], ir[3], it[3], k[3];
+        // stage 1
+        tangent_rhs(S[0], kba, lam, dl[c], Dr[c], DT[c], k);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            ar[i] = DT[c][i];
+            at[i] = k[i];
+            ir[i] = fmaf(hh, DT[c][i], Dr[c][i]);
+            it[i] = fmaf(hh, k[i], DT[c][i]);
+        }
+        // stage 2
+        tangent_rhs(S[1], kba, lam, dl[c], ir, it, k);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            ar[i] = fmaf(2.f, it[i], ar[i]);
+            at[i] = fmaf(2.f, k[i], at[i]);
+            ir[i] = fmaf(hh, it[i], Dr[c][i]);
+            it[i] = fmaf(hh, k[i], DT[c][i]);
+        }
+        // stage 3
+        tangent_rhs(S[2], kba, lam, dl[c], ir, it, k);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            ar[i] = fmaf(2.f, it[i], ar[i]);
+            at[i] = fmaf(2.f, k[i], at[i]);
+            ir[i] = fmaf(hs, it[i], Dr[c][i]);
+            it[i] = fmaf(hs, k[i], DT[c][i]);
+        }
+        // stage 4
+        tangent_rhs(S[3], kba, lam, dl[c], ir, it, k);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            Dr[c][i] = fmaf(h6, ar[i] + it[i], Dr[c][i]);
+            DT[c][i] = fmaf(h6, at[i] + k[i], DT[c][i]);
+        }
+    }
+}
+
+// Root nearest 0 of a d^2 + b d + c = 0; the parabola's vertex when it has no
+// real root, the linear root when a = 0.
+__device__ __forceinline__ float nearest_root(float a, float b, float c) {
+    const float disc = fmaf(b, b, -4.f * a * c);
+    if (a == 0.f) return b != 0.f ? -c / b : 0.f;
+    if (disc < 0.f) return -b / (2.f * a);
+    const float q = -0.5f * (b + copysignf(sqrtf(disc), b));
+    if (q == 0.f) return 0.f;
+    const float r1 = q / a, r2 = c / q;
+    return fabsf(r1) < fabsf(r2) ? r1 : r2;
+}
+
+// Move p onto the surface of layer Ld through the parameterised field and
+// transport C.  n equal steps over the path s estimated by the helix in the
+// local axial field (turning rate h), n from the turning angle and the path
+// length, then kRkNewton correction steps onto the surface (on a cylinder the
+// nearest root of the second-order expansion of x(S)^2 + y(S)^2 - R^2, whose
+// bending term keeps grazing crossings converging; on a disk (Z - z) / Tz).  The Jacobian: the six
+// parameter columns (dr, dT) integrated with the trajectory (the variational
+// equations, the field's gradient included), then the surface constraint
+// dS = -(n . dr) / (n . T) moves every column along (T, dT/dS) at the end.
+__device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, float alpha, float p[6], Lo &lo,
+                                                float C[21], float sphi, float cphi, float h, float s) {
+    float st, ct;
+    sincos_small(p[5], st, ct);
+    const float lam = p[3] * st;
+    const float dl[6] = {0.f, 0.f, 0.f, st, 0.f, p[3] * ct};  // d lambda / d(x, y, z, q/pT, phi, theta)
+    float T[3] = {st * cphi, st * sphi, ct};
+    float d[3] = {0.f, 0.f, 0.f};
+    float Dr[6][3], DT[6][3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            Dr[c][i] = c == i ? 1.f : 0.f;
+            DT[c][i] = 0.f;
+        }
+    DT[4][0] = -st * sphi, DT[4][1] = st * cphi;
+    DT[5][0] = ct * cphi, DT[5][1] = ct * sphi, DT[5][2] = -st;
+    const float r0[3] = {p[0], p[1], p[2]};
+    const float S = s / st;
+    const float nf = ceilf(fmaxf(fabsf(h) * s * (1.f / kRkTurn), fabsf(S) * (1.f / kRkLen)));
+    const int n = nf >= 1.f ? (nf < static_cast<float>(kRkMaxN) ? static_cast<int>(nf) : kRkMaxN) : 1;
+    const float hs = S / static_cast<float>(n);
+    for (int i = 0; i < n; ++i) rk_step(kb, alpha, r0, lam, dl, d, T, Dr, DT, hs);
+    for (int it = 0; it < kRkNewton; ++it) {
+        float dn;
+        if (Ld.kind == 0) {
+            // r^2 - R^2 from the position pair without cancellation
+            const float xl = lo.x + d[0], yl = lo.y + d[1];
+            const float x = p[0] + xl, y = p[1] + yl;
+            const float c = 2.f * fmaf(p[0], xl, p[1] * yl) + fmaf(xl, xl, yl * yl) - diff_sq2(Ld.rz, 0.f, p[0], p[1]);
+            float b[3];
+            kfield(kb, alpha, r0[0] + d[0], r0[1] + d[1], r0[2] + d[2], b);
+            const float Fx = lam * fmaf(T[1], b[2], -T[2] * b[1]), Fy = lam * fmaf(T[2], b[0], -T[0] * b[2]);
+            const float aq = fmaf(T[0], T[0], fmaf(T[1], T[1], fmaf(x, Fx, y * Fy)));
+            dn = nearest_root(aq, 2.f * fmaf(x, T[0], y * T[1]), c);
+        } else {
+            dn = ((Ld.rz - p[2]) - (lo.z + d[2])) / T[2];
+        }
+        rk_step(kb, alpha, r0, lam, dl, d, T, Dr, DT, dn);
+    }
+
+    // end point: dT/dS, surface normal, output conversions
+    float b[3], F[3];
+    kfield(kb, alpha, r0[0] + d[0], r0[1] + d[1], r0[2] + d[2], b);
+    cross3(T, b, F);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[i] *= lam;
+    float nv[3] = {0.f, 0.f, 1.f};
+    if (Ld.kind == 0) {
+        const float x = p[0] + (lo.x + d[0]), y = p[1] + (lo.y + d[1]);
+        const float ir = 1.f / sqrtf(fmaf(x, x, y * y));
+        nv[0] = x * ir, nv[1] = y * ir, nv[2] = 0.f;
+    }
+    const float inT = -1.f / fmaf(nv[0], T[0], fmaf(nv[1], T[1], nv[2] * T[2]));
+    const float tt2 = fmaf(T[0], T[0], T[1] * T[1]), tn2 = fmaf(T[2], T[2], tt2);
+    const float tt = sqrtf(tt2), itt = 1.f / tt, itt2 = itt * itt;
+    const float sth = tt / sqrtf(tn2);  // sin(theta) at the end
+    // J columns (outputs x, y, z, q/pT, phi, theta) of a tangent (dr, dT, dlambda)
+    float J[6][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const float *dr = Dr[j], *dT = DT[j];
+        const float dlam = dl[j];
+        const float dS = fmaf(nv[0], dr[0], fmaf(nv[1], dr[1], nv[2] * dr[2])) * inT;
+        float r[3], t[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            r[i] = fmaf(T[i], dS, dr[i]);
+            t[i] = fmaf(F[i], dS, dT[i]);
+        }
+        const float dtt = fmaf(T[0], t[0], T[1] * t[1]) * itt;
+        J[0][j] = r[0];
+        J[1][j] = r[1];
+        J[2][j] = r[2];
+        J[3][j] = fmaf(dlam, itt, -lam * dtt * itt2);
+        J[4][j] = fmaf(T[0], t[1], -T[1] * t[0]) * itt2;
+        J[5][j] = fmaf(T[2], dtt, -tt * t[2]) / tn2;
+    }
+
+    // C' = J C J^T
+    float M[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float a = 0.f;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) a = fmaf(J[i][m], C[sym(m, k)], a);
+            M[i][k] = a;
+        }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            float a = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a = fmaf(M[i][k], J[j][k], a);
+            C[sym(i, j)] = a;
+        }
+
+    // state at the end: position pairs, azimuth turned by the angle between
+    // the start and end transverse directions, theta and q/pT = lambda / sin(theta)
+    df_add(p[0], lo.x, d[0]);
+    df_add(p[1], lo.y, d[1]);
+    if (Ld.kind == 1) {
+        p[2] = Ld.rz;
+        lo.z = 0.f;
+    } else {
+        df_add(p[2], lo.z, d[2]);
+    }
+    df_add(p[4], lo.phi, atan2f(fmaf(cphi, T[1], -sphi * T[0]), fmaf(cphi, T[0], sphi * T[1])));
+    df_wrap_pi(p[4], lo.phi);
+    p[5] = atan2f(tt, T[2]);
+    p[3] = lam / sth;
 }
 
 // Multiple scattering in the layer's material, added to the covariance of a

@@ -66,7 +66,9 @@ def make_ctx(batch, plans=None, edges=None):
     from paper_1811_04141_gb300 import Context, build
     build.build()
     ctx = Context(0)
-    ctx.geometry_load(batch.layers, batch.bz, plans, edges)
+    # the parameterised field where the batch names one (as the oracle's
+    # geometry_for reads it)
+    ctx.geometry_load(batch.layers, batch.bz, plans, edges, batch.meta.get("field_alpha"))
     return ctx
 
 

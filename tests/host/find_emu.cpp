@@ -17,7 +17,8 @@ unsigned char *g_smem;
 extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *X, const float *Y, const float *Z,
                         const int *layer, int n_hits, const int *event_offsets, int n_events, const int *seed_hits,
                         const int *seed_event, int n_seeds, int N, float cut, int max_consec, int max_out, int step1,
-                        const uint16_t *mlp_bf16, float mlp_tau, float material, float eloss,
+                        const uint16_t *mlp_bf16, float mlp_tau, float material, float eloss, int field_kind,
+                        float alpha,
                         float *out_par, float *out_cov, float *out_chi2, int *out_nh, int *out_hits,
                         unsigned *out_status, int *counters, int *fault_out) {
     static Geom G;
@@ -26,6 +27,9 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
         G.L[l].x0 = material;
         G.L[l].eloss = eloss;
     }
+    G.field_kind = field_kind;  // as mkf_geometry_field sets it
+    G.alpha = field_kind ? alpha : 0.f;
+    const int phys = mkf_phys_variant(G);
     const int64_t n_bins = static_cast<int64_t>(n_events) * G.bins_per_event;
     std::vector<int> key(n_hits);
     for (int i = 0; i < n_hits; ++i) {
@@ -93,7 +97,10 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
     for (int t = 0; t < n_seeds; ++t) {
         blockIdx.x = t / 128;
         threadIdx.x = t % 128;
-        seed_kernel(A);
+        if (phys == 2)
+            seed_kernel<true>(A);
+        else
+            seed_kernel<false>(A);
     }
     blockDim.x = 32;
     std::vector<unsigned char> smem(find_smem_bytes(nl, N, 32));
@@ -105,14 +112,14 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
         lanes.emplace_back([&, l] {
             threadIdx.x = l;
             blockIdx.x = 0;
-            if (mlp_bf16 && material > 0.f)
-                find_kernel<true, true>(A);
-            else if (mlp_bf16)
-                find_kernel<true, false>(A);
-            else if (material > 0.f)
-                find_kernel<false, true>(A);
-            else
-                find_kernel<false, false>(A);
+            switch (phys + (mlp_bf16 ? 3 : 0)) {
+                case 0: find_kernel<false, 0>(A); break;
+                case 1: find_kernel<false, 1>(A); break;
+                case 2: find_kernel<false, 2>(A); break;
+                case 3: find_kernel<true, 0>(A); break;
+                case 4: find_kernel<true, 1>(A); break;
+                default: find_kernel<true, 2>(A); break;
+            }
         });
     for (auto &t : lanes) t.join();
     fault_out[0] = fault.code;

@@ -1,7 +1,7 @@
 // Host run of the fit kernel (tests only): the kernel of mkf_fit.cu, compiled
 // for the host, called once per thread of its grid; the geometry table comes
-// from the library's own builder, with the layers' material set as
-// mkf_geometry_material sets it.
+// from the library's own builder, with the layers' material and the field set
+// as mkf_geometry_material and mkf_geometry_field set them.
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -13,18 +13,20 @@ dim3 blockDim;
 #include "fit_dev.inc"
 #include "mkf_geom.h"
 
-extern "C" int emu_fit(const mkf_layer *layers, int nl, float bz, const float *x0, const float *eloss, const float *xyz,
+extern "C" int emu_fit(const mkf_layer *layers, int nl, float bz, const float *x0, const float *eloss, int field_kind,
+                       float alpha, const float *xyz,
                        const int32_t *hit_layer, int32_t n_hits, const int32_t *hit_idx, int32_t max_hits, int32_t n,
                        const float *seed_par, const float *seed_cov, int backward, float inflate, float *out_par,
                        float *out_cov, float *chi2, int32_t *ndf, uint32_t *status) {
     FitArgs A;
     if (mkf_build_geom(layers, nl, nullptr, 0, nullptr, bz, A.G) != MKF_OK) return -1;
-    bool material = false;
     for (int l = 0; l < nl; ++l) {
         A.G.L[l].x0 = x0 ? x0[l] : 0.f;
         A.G.L[l].eloss = eloss ? eloss[l] : 0.f;
-        material = material || A.G.L[l].x0 > 0.f;
     }
+    A.G.field_kind = field_kind;
+    A.G.alpha = field_kind ? alpha : 0.f;
+    const int phys = mkf_phys_variant(A.G);
     mkf_fault fault{0, 0};
     A.X = xyz;
     A.Y = xyz + n_hits;
@@ -47,10 +49,14 @@ extern "C" int emu_fit(const mkf_layer *layers, int nl, float bz, const float *x
     for (int t = 0; t < (n + 127) / 128 * 128; ++t) {
         blockIdx.x = t / 128;
         threadIdx.x = t % 128;
-        if (backward && material) fit_kernel<true, true>(A);
-        else if (backward) fit_kernel<true, false>(A);
-        else if (material) fit_kernel<false, true>(A);
-        else fit_kernel<false, false>(A);
+        switch (phys + (backward ? 3 : 0)) {
+            case 0: fit_kernel<false, 0>(A); break;
+            case 1: fit_kernel<false, 1>(A); break;
+            case 2: fit_kernel<false, 2>(A); break;
+            case 3: fit_kernel<true, 0>(A); break;
+            case 4: fit_kernel<true, 1>(A); break;
+            default: fit_kernel<true, 2>(A); break;
+        }
     }
     return fault.code;
 }

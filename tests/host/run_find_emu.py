@@ -6,11 +6,15 @@ import sys
 import numpy as np
 
 
-def main(so, cfg, event, n_tracks, n_noise, n_best, step1, out_path, mlp_path=None, tau=0.0, material=0.0, eloss=0.0):
+def main(so, cfg, event, n_tracks, n_noise, n_best, step1, out_path, mlp_path=None, tau=0.0, material=0.0, eloss=0.0,
+         alpha=None, gen_field=False):
     sys.path.insert(0, sys.argv[-1])  # repository root
     from paper_1811_04141_gb300 import _native as NN
     from synth import make_batch
-    b = make_batch(cfg, [event], n_tracks=n_tracks, n_noise=n_noise)
+    if gen_field:
+        b = make_batch(cfg, [event], n_tracks=n_tracks, n_noise=n_noise, field_alpha=alpha)
+    else:
+        b = make_batch(cfg, [event], n_tracks=n_tracks, n_noise=n_noise)
     lib = C.CDLL(so)
     lay = b.layers
     arr = (NN.MkfLayer * len(lay))()
@@ -29,6 +33,7 @@ def main(so, cfg, event, n_tracks, n_noise, n_best, step1, out_path, mlp_path=No
     rc = lib.emu_find(arr, len(lay), C.c_float(b.bz), p(X), p(Y), p(Z), p(keep[0]), b.n_hits, p(keep[1]),
                       len(b.event_offsets) - 1, p(keep[2]), p(keep[3]), n, n_best, C.c_float(30.0), 3, mo, step1,
                       None if w is None else p(w), C.c_float(tau), C.c_float(material), C.c_float(eloss),
+                      0 if alpha is None else 1, C.c_float(0.0 if alpha is None else alpha),
                       p(out["par"]), p(out["cov"]), p(out["chi2"]), p(out["n_hits"]), p(out["hits"]), p(out["status"]),
                       p(out["counters"]), p(out["fault"]))
     if rc != 0:
@@ -39,4 +44,5 @@ def main(so, cfg, event, n_tracks, n_noise, n_best, step1, out_path, mlp_path=No
 if __name__ == "__main__":
     a = sys.argv[1:]
     main(a[0], a[1], int(a[2]), int(a[3]), None if a[4] == "none" else int(a[4]), int(a[5]), int(a[6]), a[7],
-         None if a[8] == "none" else a[8], float(a[9]), float(a[10]), float(a[11]))
+         None if a[8] == "none" else a[8], float(a[9]), float(a[10]), float(a[11]),
+         None if a[12] == "none" else float(a[12]), a[13] == "1")

@@ -54,7 +54,8 @@ def emu_so():
     return so
 
 
-def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1, mlp_bf16=None, tau=0.0, material=0.0, eloss=0.0):
+def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1, mlp_bf16=None, tau=0.0, material=0.0, eloss=0.0,
+            alpha=None, gen_field=False):
     d = tempfile.mkdtemp()
     out = os.path.join(d, "out.npz")
     wpath = "none"
@@ -63,7 +64,8 @@ def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1, mlp_bf16=None, tau
         np.save(wpath, mlp_bf16)
     r = subprocess.run([sys.executable, os.path.join(HERE, "host", "run_find_emu.py"), so, cfg, str(event),
                         str(n_tracks), "none" if n_noise is None else str(n_noise), str(n_best), str(step1), out,
-                        wpath, str(tau), str(material), str(eloss), ROOT],
+                        wpath, str(tau), str(material), str(eloss), "none" if alpha is None else repr(alpha),
+                        "1" if gen_field else "0", ROOT],
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     z = np.load(out)
@@ -98,6 +100,22 @@ def test_emulated_finder_with_material_matches_oracle(emu_so, n_best, eloss):
     ref = O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=n_best, max_out=len(b.layers) + 3)
     out = run_emu(emu_so, "find20", 45, 150, None, n_best, 1, material=0.02, eloss=eloss)
+    compare(out, ref)
+
+
+@pytest.mark.parametrize("cfg,gen_field,n_best", [("fit10", True, 10), ("find20", False, 10), ("find20", False, 1)])
+def test_emulated_finder_in_parameterised_field_matches_oracle(emu_so, cfg, gen_field, n_best):
+    """The finder variant with Runge-Kutta propagation in the parameterised
+    field against the oracle in the same field: on fit10 the generator moves
+    the particles through that field; on find20 (disks too) the hits come from
+    the uniform field and only the filter uses the other one."""
+    alpha = 1e-5 if gen_field else 1e-6  # find20's disks reach z = 270 cm
+    b = (make_batch(cfg, [46], n_tracks=120, field_alpha=alpha) if gen_field
+         else make_batch(cfg, [46], n_tracks=120))
+    geo = O.Geometry(b.layers, b.bz, field_alpha=alpha)
+    ref = O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+                 n_best=n_best, max_out=len(b.layers) + 3)
+    out = run_emu(emu_so, cfg, 46, 120, None, n_best, 1, alpha=alpha, gen_field=gen_field)
     compare(out, ref)
 
 

@@ -28,9 +28,9 @@ def lib():
     src = open(os.path.join(CSRC, "mkf_fit.cu")).read()
     a = src.index("namespace {")
     b = src.index("}  // namespace") + len("}  // namespace")
-    body = src[a:b].replace("template <bool kBackward, bool kMaterial>\n__global__ void __launch_bounds__(128, 8) "
+    body = src[a:b].replace("template <bool kBackward, int kPhys>\n__global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) "
                             "fit_kernel(const __grid_constant__ FitArgs A)",
-                            "template <bool kBackward, bool kMaterial>\nvoid fit_kernel(const FitArgs &A)")
+                            "template <bool kBackward, int kPhys>\nvoid fit_kernel(const FitArgs &A)")
     assert "void fit_kernel(const FitArgs &A)" in body
     d = tempfile.mkdtemp()
     with open(os.path.join(d, "fit_dev.inc"), "w") as f:
@@ -43,7 +43,7 @@ def lib():
     return C.CDLL(so)
 
 
-def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0, eloss=None):
+def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0, eloss=None, alpha=None):
     from paper_1811_04141_gb300 import _native as NN
     lay = b.layers
     arr = (NN.MkfLayer * len(lay))()
@@ -61,22 +61,32 @@ def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0, eloss=No
     ela = None if eloss is None else np.ascontiguousarray(eloss, dtype=np.float32)
     sp, sc = (None, None) if seed is None else (np.ascontiguousarray(seed[0], dtype=np.float32),
                                                 np.ascontiguousarray(seed[1], dtype=np.float32))
-    rc = lib.emu_fit(arr, len(lay), C.c_float(b.bz), p(x0a), p(ela), p(xyz), p(hl), b.n_hits, p(hi), hi.shape[0], n, p(sp),
+    rc = lib.emu_fit(arr, len(lay), C.c_float(b.bz), p(x0a), p(ela), 0 if alpha is None else 1,
+                     C.c_float(0.0 if alpha is None else alpha), p(xyz), p(hl), b.n_hits, p(hi), hi.shape[0], n, p(sp),
                      p(sc), int(backward), C.c_float(inflate), p(out["par"]), p(out["cov"]), p(out["chi2"]),
                      p(out["ndf"]), p(out["status"]))
     assert rc == 0
     return out
 
 
-@pytest.mark.parametrize("cfg,material,eloss", [("fit10", 0.0, 0.0), ("find20", 0.0, 0.0), ("fit10", 0.03, 0.0),
-                                               ("fit10", 0.03, 0.15), ("fit10_b0", 0.02, 0.0)])
-def test_fit_kernel_on_host(lib, cfg, material, eloss):
-    b = (make_batch(cfg, [31], n_tracks=400, material=material, eloss=eloss) if material
-         else make_batch(cfg, [31], n_tracks=400))
-    geo = O.geometry_for(b)
+@pytest.mark.parametrize("cfg,material,eloss,alpha", [
+    ("fit10", 0.0, 0.0, None), ("find20", 0.0, 0.0, None), ("fit10", 0.03, 0.0, None), ("fit10", 0.03, 0.15, None),
+    ("fit10_b0", 0.02, 0.0, None), ("fit10", 0.0, 0.0, 1e-5), ("find20", 0.0, 0.0, 1e-6)])
+def test_fit_kernel_on_host(lib, cfg, material, eloss, alpha):
+    """alpha: the parameterised field (Runge-Kutta variant); fit10 tracks then
+    move through it, find20 tracks (disks) come from the uniform field, so
+    their field differs from the filter's by alpha z^2 (7 % at the last disk,
+    z = 270 cm, for alpha = 1e-6)."""
+    if material:
+        b = make_batch(cfg, [31], n_tracks=400, material=material, eloss=eloss)
+    elif alpha is not None and cfg == "fit10":
+        b = make_batch(cfg, [31], n_tracks=400, field_alpha=alpha)
+    else:
+        b = make_batch(cfg, [31], n_tracks=400)
+    geo = O.Geometry(b.layers, b.bz, field_alpha=alpha)
     x0 = [d.get("x0", 0.0) for d in b.layers]
     el = [d.get("eloss", 0.0) for d in b.layers]
-    out = _run(lib, b, b.track_hits, x0, eloss=el)
+    out = _run(lib, b, b.track_hits, x0, eloss=el, alpha=alpha)
     ref = O.fit(geo, b.xyz.astype(np.float64), b.layer, b.track_hits)
     assert (out["status"] == ref["status"]).all() and (out["ndf"] == ref["ndf"]).all()
     ok = ref["status"] == 0
@@ -84,7 +94,7 @@ def test_fit_kernel_on_host(lib, cfg, material, eloss):
     assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
     # backward pass from the oracle's forward result (FP32) on both sides
     lp, lc = ref["par"].astype(np.float32), ref["cov"].astype(np.float32)
-    outb = _run(lib, b, b.track_hits, x0, (lp, lc), True, 100.0, el)
+    outb = _run(lib, b, b.track_hits, x0, (lp, lc), True, 100.0, el, alpha)
     refb = O.fit_backward(geo, b.xyz.astype(np.float64), b.layer, b.track_hits, lp.astype(np.float64),
                           lc.astype(np.float64), 100.0)
     assert (outb["status"] == refb["status"]).all()

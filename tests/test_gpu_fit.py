@@ -169,6 +169,38 @@ def test_fit_with_material_parity(cfg, material, eloss):
     assert chi2_ok(outb["chi2"][okb], refb["chi2"][okb], refb["ndf"][okb])
 
 
+@pytest.mark.parametrize("cfg,alpha", [("fit10", 1e-5), ("find20", 1e-6)])
+def test_fit_in_parameterised_field_parity(cfg, alpha):
+    """Forward and backward fit in the parameterised field (the Runge-Kutta
+    variant) against the oracle: on fit10 the generator moves the tracks
+    through that field; on find20 (disks, up to z = 270 cm) the tracks come
+    from the uniform field and only the filter uses the other one."""
+    if cfg == "fit10":
+        b = make_batch(cfg, [17], n_tracks=800, field_alpha=alpha)
+    else:
+        b = make_batch(cfg, [17], n_tracks=500)
+        b.meta["field_alpha"] = alpha
+    ctx = make_ctx(b)
+    d = upload(b)
+    out = to_np(ctx.fit(d["xyz"], d["layer"], d["track_hits"]))
+    ctx.sync()
+    ref = oracle_fit(b)
+    assert (out["status"] == ref["status"]).all()
+    ok = ref["status"] == 0
+    assert par_errors(out["par"][:, ok], ref["par"][:, ok], ref["cov"][:, ok]).max() <= 1.0
+    assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
+    pos = ref["cov"][0, ok] + ref["cov"][2, ok]
+    for k in (0, 2, 5, 9, 14, 20):
+        floor = 1e-2 * pos if k in (0, 2) else 1e-9 * np.abs(ref["cov"][:, ok]).max(axis=0)
+        r = np.abs(out["cov"][k, ok] - ref["cov"][k, ok]) / np.maximum(np.abs(ref["cov"][k, ok]), floor)
+        assert np.quantile(r, 0.99) < 5e-2 and r.max() < 1.5e-1, (k, np.quantile(r, 0.99), r.max())
+    outb, refb, f = _backward_pair(b, b.track_hits, 100.0, ctx)
+    okb = (refb["status"] == 0) & (f["status"] == 0)
+    assert (outb["status"] == refb["status"]).all()
+    assert par_errors(outb["par"][:, okb], refb["par"][:, okb], refb["cov"][:, okb]).max() <= 1.0
+    assert chi2_ok(outb["chi2"][okb], refb["chi2"][okb], refb["ndf"][okb])
+
+
 def test_fit_empty_and_errors():
     b = make_batch("fit10", [13], n_tracks=10)
     ctx = make_ctx(b)
