@@ -124,7 +124,7 @@ mkf_status mkf_geometry_load(mkf_ctx *ctx, const mkf_layer *layers, int32_t n_la
  * 0 = none; eloss [n_layers] (host, copied, or NULL = none), the mean energy
  * loss per radiation length at minimum ionisation (GeV), for the geometry
  * loaded last (n_layers must match it; mkf_geometry_load resets every layer to
- * none).  Fit and finding then apply, on arriving at a layer by propagation,
+ * none; an r-z map from mkf_geometry_material_map takes precedence).  Fit and finding then apply, on arriving at a layer by propagation,
  * multiple scattering -- the Highland angle theta0 (unit charge, pion mass) for
  * the path through the layer: Var(theta) += theta0^2, Var(phi) += theta0^2 /
  * sin^2(theta), q/pT following theta at fixed |p| -- and then the mean energy
@@ -153,6 +153,26 @@ mkf_status mkf_geometry_material(mkf_ctx *ctx, const float *x0, const float *elo
  * Errors: MKF_ERR_ARG (kind not 0 or 1, alpha not finite or |alpha| >= 1e-2),
  * MKF_ERR_GEOMETRY (no geometry). */
 mkf_status mkf_geometry_field(mkf_ctx *ctx, int32_t kind, float alpha);
+
+/* r-z material map (Sec. 2.1: radiation and interaction lengths from
+ * two-dimensional arrays indexed in r and z) for the geometry loaded last
+ * (mkf_geometry_load removes it): nr x nz cells of equal size over
+ * [0, r_max) x [z_min, z_max) (cm), x0 [nr * nz] (host, copied; cell (ir, iz)
+ * at ir * nz + iz) the thickness in radiation lengths at normal incidence that
+ * a particle crossing a layer there traverses, eloss [nr * nz] (host, copied,
+ * or NULL = none) the mean energy loss per radiation length at minimum
+ * ionisation (GeV).  While a map is loaded it replaces the layers' own
+ * material (mkf_geometry_material): each arrival at a layer takes x0 and eloss
+ * from the cell holding the state's (r, z), points outside the map from the
+ * nearest edge cell; the effects are those of mkf_geometry_material.  The
+ * cell is chosen in FP32 on the device, so a crossing within rounding of a
+ * cell edge may take either cell: keep edges away from layer surfaces.
+ * nr = nz = 0 removes the map.  The copy waits for the context's stream.
+ * Errors: MKF_ERR_ARG (sizes out of range or over 2^20 cells, x0 NULL,
+ * r_max <= 0, z_max <= z_min), MKF_ERR_GEOMETRY (no geometry, a value negative,
+ * not finite or >= 1000), MKF_ERR_CUDA. */
+mkf_status mkf_geometry_material_map(mkf_ctx *ctx, int32_t nr, int32_t nz, float r_max, float z_min, float z_max,
+                                     const float *x0, const float *eloss);
 
 /* ------------------------------------------------------------------------ */
 /* Hit binning (per event and layer, phi x z or phi x r bins)               */

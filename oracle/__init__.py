@@ -49,7 +49,8 @@ def _load():
             lib = C.CDLL(_LIB_PATH)
             d, i32, i64, u64 = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)
             u32 = C.POINTER(C.c_uint32)
-            geom = [C.c_int, i32, d, d, d, d, d, d, d, C.c_double, C.c_int, C.c_double, C.c_int, d, u64]
+            geom = [C.c_int, i32, d, d, d, d, d, d, d, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
+                    C.c_double, C.c_double, C.c_double, d, d, C.c_int, d, u64]
             lib.or_field.argtypes = geom + [d, d]
             lib.or_field.restype = C.c_int
             lib.or_propagate.argtypes = geom + [d, C.c_int, d, d, d]
@@ -86,7 +87,7 @@ def _p(a, ctype):
 class Geometry:
     """Layer table + field + optional tracking regions (layer masks by seed eta)."""
 
-    def __init__(self, layers, bz, region_edges=None, region_masks=None, field_alpha=None):
+    def __init__(self, layers, bz, region_edges=None, region_masks=None, field_alpha=None, material_map=None):
         self.layers = [dict(d) for d in layers]
         self.n = len(layers)
         self.kind = np.ascontiguousarray([d["kind"] for d in layers], dtype=np.int32)
@@ -104,6 +105,18 @@ class Geometry:
         # (1/cm^2; alpha = 0 is the uniform field integrated numerically)
         self.field_kind = 0 if field_alpha is None else 1
         self.alpha = 0.0 if field_alpha is None else float(field_alpha)
+        # r-z material map: dict(r_max, z_min, z_max, x0 [nr, nz], eloss [nr, nz] or
+        # None); it replaces the layers' own material values
+        self.material_map = material_map
+        if material_map is None:
+            self.map_args = [0, 0, 0.0, 0.0, 0.0, None, None]
+        else:
+            mx = np.ascontiguousarray(material_map["x0"], dtype=np.float64)
+            me = material_map.get("eloss")
+            me = None if me is None else np.ascontiguousarray(me, dtype=np.float64)
+            self._map = (mx, me)
+            self.map_args = [mx.shape[0], mx.shape[1], float(material_map["r_max"]), float(material_map["z_min"]),
+                             float(material_map["z_max"]), _p(mx, C.c_double), _p(me, C.c_double)]
         edges = [] if region_edges is None else list(region_edges)
         self.n_regions = len(edges) + 1
         self.edges = np.ascontiguousarray(edges + [0.0], dtype=np.float64)
@@ -115,7 +128,7 @@ class Geometry:
         return [self.n, _p(self.kind, C.c_int32), _p(self.rz, C.c_double), _p(self.lo, C.c_double),
                 _p(self.hi, C.c_double), _p(self.su, C.c_double), _p(self.sv, C.c_double),
                 _p(self.x0, C.c_double), _p(self.eloss, C.c_double), self.bz, self.field_kind, self.alpha,
-                self.n_regions,
+                *self.map_args, self.n_regions,
                 _p(self.edges, C.c_double),
                 _p(self.masks, C.c_uint64)]
 
@@ -288,7 +301,8 @@ def find(geo: Geometry, xyz, hit_layer, event_offsets, seed_hits, seed_event, n_
 
 
 def geometry_for(batch, region_edges=None, region_masks=None) -> Geometry:
-    return Geometry(batch.layers, batch.bz, region_edges, region_masks, batch.meta.get("field_alpha"))
+    return Geometry(batch.layers, batch.bz, region_edges, region_masks, batch.meta.get("field_alpha"),
+                    batch.meta.get("material_map"))
 
 
 def field(geo: Geometry, r):

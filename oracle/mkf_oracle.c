@@ -63,6 +63,12 @@ typedef struct {
     double bz;
     int field_kind; /* 0: uniform Bz; 1: parameterised field (field_at), RK4 propagation */
     double alpha;   /* parameterised field: fall-off coefficient, 1/cm^2 */
+    /* r-z material map (sec. 2.1): map_nr x map_nz cells of equal size over
+     * [0, map_rmax) x [map_zmin, map_zmax), x0 and eloss per cell (index
+     * ir * map_nz + iz); map_nr = 0: the layers' own values */
+    int map_nr, map_nz;
+    double map_rmax, map_zmin, map_zmax;
+    const double *map_x0, *map_eloss;
     int n_regions;
     double edges[OR_MAXR];
     uint64_t mask[OR_MAXR];
@@ -70,8 +76,9 @@ typedef struct {
 
 static int geom_init(geom_t *g, int n_layers, const int32_t *kind, const double *rz, const double *lo,
                      const double *hi, const double *su, const double *sv, const double *x0,
-                     const double *eloss, double bz, int field_kind, double alpha, int n_regions,
-                     const double *edges, const uint64_t *masks) {
+                     const double *eloss, double bz, int field_kind, double alpha, int map_nr, int map_nz,
+                     double map_rmax, double map_zmin, double map_zmax, const double *map_x0,
+                     const double *map_eloss, int n_regions, const double *edges, const uint64_t *masks) {
     if (n_layers < 1 || n_layers > OR_MAXL) return -1;
     if (n_regions < 1 || n_regions > OR_MAXR) return -1;
     g->n = n_layers;
@@ -89,6 +96,15 @@ static int geom_init(geom_t *g, int n_layers, const int32_t *kind, const double 
     if (field_kind != 0 && field_kind != 1) return -1;
     g->field_kind = field_kind;
     g->alpha = field_kind ? alpha : 0.0;
+    if (map_nr < 0 || map_nz < 0 || (map_nr > 0) != (map_nz > 0)) return -1;
+    if (map_nr > 0 && (!map_x0 || !(map_rmax > 0.0) || !(map_zmax > map_zmin))) return -1;
+    g->map_nr = map_nr;
+    g->map_nz = map_nz;
+    g->map_rmax = map_rmax;
+    g->map_zmin = map_zmin;
+    g->map_zmax = map_zmax;
+    g->map_x0 = map_x0;
+    g->map_eloss = map_eloss;
     g->n_regions = n_regions;
     for (int r = 0; r + 1 < n_regions; ++r) g->edges[r] = edges[r];
     for (int r = 0; r < n_regions; ++r) {
@@ -393,8 +409,8 @@ static void transport(const double J[36], const double C[36], double Co[36]) {
 
 /* Residual (u, v) of hit (xh, yh, zh) against a state on layer l's surface and
  * the 2x6 projection H. */
-/* Multiple scattering in the material of layer l (x0[l] radiation lengths at
- * normal incidence), added to the covariance of the state p on the layer's
+/* Multiple scattering in the material where p crosses layer l (x0 radiation
+ * lengths at normal incidence, material_at), added to the covariance of the state p on the layer's
  * surface.  theta0 = 0.0136 GeV / (beta p) sqrt(x) (1 + 0.038 ln(x / beta^2))
  * (Highland, as tabulated by the Particle Data Group; unit charge, pion mass
  * 0.13957 GeV) for the path x = x0 / |cos a|, a = the angle between the
@@ -408,8 +424,28 @@ static void transport(const double J[36], const double C[36], double Co[36]) {
  * q/pT is not measured (0 in the state): the momentum is taken as infinite and
  * no noise is added. */
 #define OR_PION_MASS 0.13957
+
+/* Material where the state p crosses layer l: from the r-z map's cell that
+ * holds (r, z) when a map is loaded (points outside it take the nearest edge
+ * cell), else the layer's own x0 and eloss. */
+static void material_at(const geom_t *g, int l, const double p[6], double *x0, double *k) {
+    if (g->map_nr == 0) {
+        *x0 = g->x0[l];
+        *k = g->eloss[l];
+        return;
+    }
+    const double r = hypot(p[0], p[1]);
+    int ir = (int)floor(r / g->map_rmax * g->map_nr);
+    int iz = (int)floor((p[2] - g->map_zmin) / (g->map_zmax - g->map_zmin) * g->map_nz);
+    ir = ir < 0 ? 0 : (ir >= g->map_nr ? g->map_nr - 1 : ir);
+    iz = iz < 0 ? 0 : (iz >= g->map_nz ? g->map_nz - 1 : iz);
+    *x0 = g->map_x0[ir * g->map_nz + iz];
+    *k = g->map_eloss ? g->map_eloss[ir * g->map_nz + iz] : 0.0;
+}
+
 static void add_scattering(const geom_t *g, int l, const double p[6], double C[36]) {
-    const double t = g->x0[l];
+    double t, k_unused;
+    material_at(g, l, p, &t, &k_unused);
     /* q/pT = 0: no field, momentum not measured; taken as infinite (no noise) */
     if (!(t > 0.0) || !(fabs(p[3]) > 0.0)) return;
     const double st = sin(p[5]), ct = cos(p[5]);
@@ -427,13 +463,15 @@ static void add_scattering(const geom_t *g, int l, const double p[6], double C[3
     C[5 * 6 + 3] -= wc * v;
 }
 
-/* Mean energy loss in the material of layer l (no straggling): the particle
- * loses dE = eloss[l] * x / beta^2 for the path x = x0[l] / |cos a| (eloss =
+/* Mean energy loss in the material where p crosses layer l (no straggling):
+ * the particle loses dE = eloss * x / beta^2 for the path x = x0 / |cos a| (eloss =
  * the loss per radiation length at minimum ionisation; pion mass), at fixed
  * direction; sign +1 loses it (forward in time), -1 gains it back (the backward
- * pass).  q/pT scales by r = p / p', and so do the q/pT row and column of C. */
+ * pass).  q/pT scales by r = p / p'; C is transported with the derivative of
+ * that map in (q/pT, theta) through the momentum (the loss grows as beta falls). */
 static void add_eloss(const geom_t *g, int l, double p[6], double C[36], double sign) {
-    const double k = g->eloss[l], t = g->x0[l];
+    double t, k;
+    material_at(g, l, p, &t, &k);
     if (!(k > 0.0) || !(t > 0.0) || !(fabs(p[3]) > 0.0)) return;
     const double st = sin(p[5]), ct = cos(p[5]);
     double cosa = g->kind[l] == 0 ? fabs(st * cos(p[4] - atan2(p[1], p[0]))) : fabs(ct);
@@ -441,14 +479,27 @@ static void add_eloss(const geom_t *g, int l, double p[6], double C[36], double 
     const double pm = 1.0 / (fabs(p[3]) * fabs(st));
     const double e = sqrt(pm * pm + OR_PION_MASS * OR_PION_MASS);
     const double beta = pm / e;
-    const double e2 = e - sign * k * (t / cosa) / (beta * beta);
+    const double kx = sign * k * (t / cosa);
+    const double e2 = e - kx / (beta * beta);
     if (!(e2 > OR_PION_MASS)) return; /* stopped: left as it is */
-    const double r = pm / sqrt(e2 * e2 - OR_PION_MASS * OR_PION_MASS);
+    const double p2 = sqrt(e2 * e2 - OR_PION_MASS * OR_PION_MASS);
+    const double r = pm / p2;
+    /* Jacobian of q/pT' = q/pT * g(p), g = p / p'(p), p = 1 / (|q/pT| sin theta):
+     * dp'/dp = (E' / p') (p / E + 2 kx m^2 / p^3), g' = 1 / p' - p dp'/dp / p'^2;
+     * d(q/pT')/d(q/pT) = g - p g', d(q/pT')/d(theta) = -(q/pT) p cot(theta) g'
+     * (the path through the layer held fixed) */
+    const double dp2 = e2 / p2 * (pm / e + 2.0 * kx * OR_PION_MASS * OR_PION_MASS / (pm * pm * pm));
+    const double gp = 1.0 / p2 - pm * dp2 / (p2 * p2);
+    const double a = r - pm * gp, c = -p[3] * pm * (ct / st) * gp;
     p[3] *= r;
-    for (int i = 0; i < 6; ++i) {
-        C[3 * 6 + i] *= r;
-        C[i * 6 + 3] *= r;
+    double row[6];
+    for (int j = 0; j < 6; ++j) row[j] = a * C[3 * 6 + j] + c * C[5 * 6 + j];
+    const double c33 = a * row[3] + c * row[5];
+    for (int j = 0; j < 6; ++j) {
+        C[3 * 6 + j] = row[j];
+        C[j * 6 + 3] = row[j];
     }
+    C[3 * 6 + 3] = c33;
 }
 
 static void residual(const geom_t *g, int l, const double p[6], double xh, double yh, double zh,
@@ -600,8 +651,12 @@ static void unpack21(const double *in, int64_t stride, double C[36]) {
 #define GEOM_ARGS                                                                                     \
     int n_layers, const int32_t *kind, const double *rz, const double *lo, const double *hi,        \
         const double *su, const double *sv, const double *x0, const double *eloss, double bz,         \
-        int field_kind, double alpha, int n_regions, const double *edges, const uint64_t *masks
-#define GEOM_PASS n_layers, kind, rz, lo, hi, su, sv, x0, eloss, bz, field_kind, alpha, n_regions, edges, masks
+        int field_kind, double alpha, int map_nr, int map_nz, double map_rmax, double map_zmin,           \
+        double map_zmax, const double *map_x0, const double *map_eloss, int n_regions, const double *edges, \
+        const uint64_t *masks
+#define GEOM_PASS                                                                                       \
+    n_layers, kind, rz, lo, hi, su, sv, x0, eloss, bz, field_kind, alpha, map_nr, map_nz, map_rmax, map_zmin, \
+        map_zmax, map_x0, map_eloss, n_regions, edges, masks
 
 /* Propagate p to layer l: writes q, J (6x6 row-major) and s.  Returns 1 on
  * success, 0 if unreachable, -1 on bad arguments. */

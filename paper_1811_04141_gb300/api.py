@@ -57,11 +57,14 @@ def mkf_sync(ctx) -> None:
     N.check("mkf_sync", N.lib().mkf_sync(ctx))
 
 
-def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None, field_alpha=None) -> None:
+def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None, field_alpha=None,
+                      material_map=None) -> None:
     """layers: list of dicts (kind, r_or_z, lo, hi, sigma_u, sigma_v, n_phi, n_zr,
     optional x0 = material in radiation lengths); plans: list of layer-id lists,
     one per region (None = one region, all layers); field_alpha: None for the
-    uniform field, else the parameterised field's fall-off (1/cm^2)."""
+    uniform field, else the parameterised field's fall-off (1/cm^2);
+    material_map: None, or an r-z map dict (r_max, z_min, z_max, x0 [nr, nz],
+    eloss [nr, nz] or None)."""
     arr = (N.MkfLayer * len(layers))()
     for i, d in enumerate(layers):
         arr[i] = N.MkfLayer(int(d["kind"]), float(d["r_or_z"]), float(d["lo"]), float(d["hi"]),
@@ -85,6 +88,9 @@ def mkf_geometry_load(ctx, layers, bz: float, plans=None, region_eta_edges=None,
                               [float(d.get("eloss", 0.0)) for d in layers])
     if field_alpha is not None:
         mkf_geometry_field(ctx, 1, field_alpha)
+    if material_map is not None:
+        mkf_geometry_material_map(ctx, material_map["x0"], material_map["r_max"], material_map["z_min"],
+                                  material_map["z_max"], material_map.get("eloss"))
 
 
 def mkf_geometry_material(ctx, x0, eloss=None) -> None:
@@ -101,6 +107,24 @@ def mkf_geometry_field(ctx, kind: int, alpha: float = 0.0) -> None:
     """Field type of the loaded geometry: 0 uniform, 1 parameterised
     (Bz = bz (1 - alpha (z^2 - r^2 / 2)), Br = bz alpha r z; alpha in 1/cm^2)."""
     N.check("mkf_geometry_field", N.lib().mkf_geometry_field(ctx, int(kind), float(alpha)))
+
+
+def mkf_geometry_material_map(ctx, x0, r_max: float, z_min: float, z_max: float, eloss=None) -> None:
+    """r-z material map of the loaded geometry: x0 and eloss arrays [nr, nz]
+    over [0, r_max) x [z_min, z_max); x0 = None removes the map."""
+    if x0 is None:
+        N.check("mkf_geometry_material_map", N.lib().mkf_geometry_material_map(ctx, 0, 0, 1.0, 0.0, 1.0, None, None))
+        return
+    import numpy as np
+    a = np.ascontiguousarray(x0, dtype=np.float32)
+    if a.ndim != 2:
+        raise ValueError("x0 must be [nr, nz]")
+    e = None if eloss is None else np.ascontiguousarray(eloss, dtype=np.float32)
+    if e is not None and e.shape != a.shape:
+        raise ValueError("eloss must have the shape of x0")
+    N.check("mkf_geometry_material_map", N.lib().mkf_geometry_material_map(
+        ctx, a.shape[0], a.shape[1], float(r_max), float(z_min), float(z_max), a.ctypes.data,
+        None if e is None else e.ctypes.data))
 
 
 class HitBins:
@@ -369,8 +393,8 @@ class Context:
     def sync(self):
         mkf_sync(self.handle)
 
-    def geometry_load(self, layers, bz, plans=None, region_eta_edges=None, field_alpha=None):
-        mkf_geometry_load(self.handle, layers, bz, plans, region_eta_edges, field_alpha)
+    def geometry_load(self, layers, bz, plans=None, region_eta_edges=None, field_alpha=None, material_map=None):
+        mkf_geometry_load(self.handle, layers, bz, plans, region_eta_edges, field_alpha, material_map)
         self.layers = [dict(d) for d in layers]
 
     def geometry_field(self, kind, alpha=0.0):

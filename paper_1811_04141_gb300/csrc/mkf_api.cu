@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "mkf_geom.h"
 #include "mkf_internal.h"
@@ -55,6 +56,7 @@ extern "C" void mkf_destroy(mkf_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->fault);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->mat_map) cudaFree(ctx->mat_map);
     delete ctx;
 }
 
@@ -130,5 +132,48 @@ extern "C" mkf_status mkf_geometry_field(mkf_ctx *ctx, int32_t kind, float alpha
     if (!ctx->has_geom) return MKF_ERR_GEOMETRY;
     ctx->geom.field_kind = kind;
     ctx->geom.alpha = kind == 1 ? alpha : 0.f;
+    return MKF_OK;
+}
+
+extern "C" mkf_status mkf_geometry_material_map(mkf_ctx *ctx, int32_t nr, int32_t nz, float r_max, float z_min,
+                                                float z_max, const float *x0, const float *eloss) {
+    if (!ctx) return MKF_ERR_ARG;
+    if (!ctx->has_geom) return MKF_ERR_GEOMETRY;
+    if (nr == 0 && nz == 0) {  // back to the layers' own material
+        ctx->geom.mat_map = nullptr;
+        ctx->geom.map_nr = ctx->geom.map_nz = 0;
+        return MKF_OK;
+    }
+    if (nr < 1 || nz < 1 || nr > 4096 || nz > 4096 || static_cast<int64_t>(nr) * nz > (1 << 20)) return MKF_ERR_ARG;
+    if (!x0 || !(r_max > 0.f && r_max < 1.0e6f) || !(z_max > z_min) || !(z_min > -1.0e6f && z_max < 1.0e6f))
+        return MKF_ERR_ARG;
+    const size_t cells = static_cast<size_t>(nr) * nz;
+    std::vector<float2> h(cells);
+    for (size_t i = 0; i < cells; ++i) {
+        if (!(x0[i] >= 0.f && x0[i] < 1.0e3f)) return MKF_ERR_GEOMETRY;
+        if (eloss && !(eloss[i] >= 0.f && eloss[i] < 1.0e3f)) return MKF_ERR_GEOMETRY;
+        h[i] = make_float2(x0[i], eloss ? eloss[i] : 0.f);
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return MKF_ERR_CUDA;
+    if (cells > ctx->mat_map_cells) {
+        if (ctx->mat_map) {
+            MKF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            MKF_CUDA_TRY(cudaFree(ctx->mat_map));
+            ctx->mat_map = nullptr;
+            ctx->mat_map_cells = 0;
+        }
+        MKF_CUDA_TRY(cudaMalloc(&ctx->mat_map, cells * sizeof(float2)));
+        ctx->mat_map_cells = cells;
+    }
+    // kernels queued before this call may still read the previous map
+    MKF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    MKF_CUDA_TRY(cudaMemcpy(ctx->mat_map, h.data(), cells * sizeof(float2), cudaMemcpyHostToDevice));
+    ctx->geom.mat_map = ctx->mat_map;
+    ctx->geom.map_nr = nr;
+    ctx->geom.map_nz = nz;
+    ctx->geom.map_rinv = static_cast<float>(nr) / r_max;
+    ctx->geom.map_zmin = z_min;
+    ctx->geom.map_zinv = static_cast<float>(nz) / (z_max - z_min);
     return MKF_OK;
 }

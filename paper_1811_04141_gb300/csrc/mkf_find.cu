@@ -326,8 +326,10 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
     else
         propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
     if (kPhys >= 1) {
-        add_scattering(Ld, p, C);
-        apply_eloss(Ld, p, C, 1.f);
+        float mx0, mk;
+        material_at(G, Ld, p, mx0, mk);
+        add_scattering(Ld.kind, mx0, p, C);
+        apply_eloss(Ld.kind, mx0, mk, p, C, 1.f);
     }
     X.searched = true;
     ++c_cl;
@@ -467,8 +469,10 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
                 propagate_field(Ld, G.kb, G.alpha, p, lo, C, sphi, cphi, -p[3] * kbl, s);
             else
                 propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-            add_scattering(Ld, p, C);
-            apply_eloss(Ld, p, C, 1.f);
+            float mx0, mk;
+            material_at(G, Ld, p, mx0, mk);
+            add_scattering(Ld.kind, mx0, p, C);
+            apply_eloss(Ld.kind, mx0, mk, p, C, 1.f);
         }
         const Frame f = frame_of(p);
         Innov I;

@@ -132,8 +132,10 @@ __global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __gr
                 else
                     propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
                 if (!kBackward && kMaterial) {
-                    add_scattering(Ld, p, C);
-                    apply_eloss(Ld, p, C, 1.f);
+                    float mx0, mk;
+                    material_at(G, Ld, p, mx0, mk);
+                    add_scattering(Ld.kind, mx0, p, C);
+                    apply_eloss(Ld.kind, mx0, mk, p, C, 1.f);
                 }
             }
             firsthit = false;
@@ -153,8 +155,10 @@ __global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __gr
             // the last one included): the energy lost there is gained back, then
             // the scattering noise is added
             if (kBackward && kMaterial) {
-                apply_eloss(Ld, p, C, -1.f);
-                add_scattering(Ld, p, C);
+                float mx0, mk;
+                material_at(G, Ld, p, mx0, mk);
+                apply_eloss(Ld.kind, mx0, mk, p, C, -1.f);
+                add_scattering(Ld.kind, mx0, p, C);
             }
         }
         if (kBackward) reverse_state(p, lo, C);

@@ -25,6 +25,9 @@ inline mkf_status mkf_build_geom(const mkf_layer *layers, int32_t n_layers, cons
     G.kb = mkf::kField * bz_tesla;
     G.field_kind = 0;  // the parameterised field comes from mkf_geometry_field
     G.alpha = 0.f;
+    G.mat_map = nullptr;  // the r-z material map comes from mkf_geometry_material_map
+    G.map_nr = G.map_nz = 0;
+    G.map_rinv = G.map_zmin = G.map_zinv = 0.f;
     int64_t base = 0;
     for (int l = 0; l < n_layers; ++l) {
         const mkf_layer &s = layers[l];

@@ -39,6 +39,9 @@ struct mkf_ctx {
     // cached occupancy per finder variant: (plain, learned) x (uniform field,
     // material, parameterised field)
     int find_occ_threads[6], find_occ_smem[6], find_occ_blocks[6];
+    // r-z material map in device memory (geom.mat_map points here when loaded)
+    float2 *mat_map;
+    size_t mat_map_cells;
 };
 
 struct mkf_hitbins {
@@ -87,6 +90,7 @@ mkf_status mkf_scratch(mkf_ctx *ctx, size_t bytes, void **out);
 // the material effects compiled in), 1 material in some layer, 0 neither.
 inline int mkf_phys_variant(const mkf::Geom &G) {
     if (G.field_kind == 1) return 2;
+    if (G.mat_map) return 1;
     for (int l = 0; l < G.n_layers; ++l)
         if (G.L[l].x0 > 0.f) return 1;
     return 0;

@@ -55,6 +55,12 @@ struct Geom {
     float kb;  // K * Bz (at the centre for the parameterised field)
     int field_kind;  // 0 uniform, 1 parameterised (RK4 propagation)
     float alpha;     // parameterised field: fall-off coefficient, 1/cm^2
+    // r-z material map (device memory of the context; null = the layers' own
+    // material): map_nr x map_nz cells over [0, r_max) x [z_min, z_max), cell
+    // (ir, iz) at ir * map_nz + iz holding (x0, eloss)
+    const float2 *mat_map;
+    int map_nr, map_nz;
+    float map_rinv, map_zmin, map_zinv;  // map_nr / r_max, z_min, map_nz / (z_max - z_min)
     int n_cyl, n_dsk;
     int bins_per_event;
     int n_regions;
@@ -640,15 +646,32 @@ __device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, f
 // direction and the surface normal; Var(theta) += theta0^2, Var(phi) +=
 // theta0^2 / sin^2(theta), and with |p| unchanged q/pT follows theta:
 // Var(q/pT) += (q/pT cot(theta) theta0)^2, Cov(q/pT, theta) += -(q/pT) cot(theta) theta0^2.
-__device__ __forceinline__ void add_scattering(const LayerDesc& Ld, const float p[6], float C[21]) {
-    const float t = Ld.x0;
+// Material where the state p crosses layer Ld: the r-z map's cell holding
+// (r, z) when a map is loaded (cells of equal size; points outside it take the
+// nearest edge cell), else the layer's own thickness x0 and loss coefficient k.
+__device__ __forceinline__ void material_at(const Geom &G, const LayerDesc &Ld, const float p[6], float &x0, float &k) {
+    if (G.mat_map == nullptr) {
+        x0 = Ld.x0;
+        k = Ld.eloss;
+        return;
+    }
+    const float r = sqrtf(fmaf(p[0], p[0], p[1] * p[1]));
+    const int ir = min(max(static_cast<int>(floorf(r * G.map_rinv)), 0), G.map_nr - 1);
+    const int iz = min(max(static_cast<int>(floorf((p[2] - G.map_zmin) * G.map_zinv)), 0), G.map_nz - 1);
+    const float2 m = G.mat_map[ir * G.map_nz + iz];
+    x0 = m.x;
+    k = m.y;
+}
+
+// t: thickness in radiation lengths at normal incidence (material_at).
+__device__ __forceinline__ void add_scattering(int kind, float t, const float p[6], float C[21]) {
     // q/pT = 0: no field, momentum not measured; taken as infinite (no noise)
     if (!(t > 0.f) || !(fabsf(p[3]) > 0.f)) return;
     constexpr float kPionMass2 = 0.13957f * 0.13957f;
     float st, ct;
     sincos_small(p[5], st, ct);
     float cosa;
-    if (Ld.kind == 0) {
+    if (kind == 0) {
         float sp, cp;
         sincos_small(p[4], sp, cp);
         cosa = fabsf(st * fmaf(cp, p[0], sp * p[1]) / sqrtf(fmaf(p[0], p[0], p[1] * p[1])));
@@ -667,18 +690,20 @@ __device__ __forceinline__ void add_scattering(const LayerDesc& Ld, const float 
     C[sym(5, 3)] -= wc * v;
 }
 
-// Mean energy loss in the layer's material (no straggling): dE = eloss * x /
-// beta^2 for the path x = x0 / |cos a| (pion mass), at fixed direction; sign
-// +1 loses it (forward in time), -1 gains it back (the backward fit).  q/pT
-// scales by r = p / p', and so do the q/pT row and column of C.
-__device__ __forceinline__ void apply_eloss(const LayerDesc& Ld, float p[6], float C[21], float sign) {
-    const float k = Ld.eloss, t = Ld.x0;
+// Mean energy loss in the material (no straggling): dE = k * x / beta^2 for the
+// path x = t / |cos a| (pion mass), at fixed direction; sign +1 loses it
+// (forward in time), -1 gains it back (the backward fit).  q/pT scales by
+// r = p / p'; C is transported with the derivative of q/pT' = q/pT g(p),
+// g = p / p'(p), p = 1 / (|q/pT| sin theta), in q/pT and theta (the path held
+// fixed): dp'/dp = (E' / p') (p / E + 2 k x m^2 / p^3), g' = 1 / p' - p dp'/dp / p'^2,
+// d(q/pT')/d(q/pT) = g - p g', d(q/pT')/d(theta) = -(q/pT) p cot(theta) g'.
+__device__ __forceinline__ void apply_eloss(int kind, float t, float k, float p[6], float C[21], float sign) {
     if (!(k > 0.f) || !(t > 0.f) || !(fabsf(p[3]) > 0.f)) return;
     constexpr float kPionMass = 0.13957f;
     float st, ct;
     sincos_small(p[5], st, ct);
     float cosa;
-    if (Ld.kind == 0) {
+    if (kind == 0) {
         float sp, cp;
         sincos_small(p[4], sp, cp);
         cosa = fabsf(st * fmaf(cp, p[0], sp * p[1]) / sqrtf(fmaf(p[0], p[0], p[1] * p[1])));
@@ -689,12 +714,21 @@ __device__ __forceinline__ void apply_eloss(const LayerDesc& Ld, float p[6], flo
     const float pm = 1.f / (fabsf(p[3]) * st);
     const float e = sqrtf(fmaf(pm, pm, kPionMass * kPionMass));
     const float beta = pm / e;
-    const float e2 = e - sign * k * (t / cosa) / (beta * beta);
+    const float kx = sign * k * (t / cosa);
+    const float e2 = e - kx / (beta * beta);
     if (!(e2 > kPionMass)) return;  // stopped: left as it is
-    const float r = pm / sqrtf(fmaf(e2, e2, -kPionMass * kPionMass));
+    const float p2 = sqrtf(fmaf(e2, e2, -kPionMass * kPionMass));
+    const float r = pm / p2;
+    const float dp2 = e2 / p2 * (pm / e + 2.f * kx * (kPionMass * kPionMass) / (pm * pm * pm));
+    const float gp = 1.f / p2 - pm * dp2 / (p2 * p2);
+    const float a = r - pm * gp, c = -p[3] * pm * (ct / st) * gp;
     p[3] *= r;
+    float row[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) C[sym(3, i)] *= (i == 3 ? r * r : r);
+    for (int j = 0; j < 6; ++j) row[j] = fmaf(a, C[sym(3, j)], c * C[sym(5, j)]);
+    const float c33 = fmaf(a, row[3], c * row[5]);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) C[sym(3, j)] = j == 3 ? c33 : row[j];
 }
 
 // Measurement frame at the state's position: unit radial vector (cp, sp), radius.

@@ -110,7 +110,11 @@ def _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, x0,
     the cylinder normal) and theta0 / sin(theta), the momentum magnitude staying
     the same (so q/pT follows theta); then, with eloss > 0 (GeV per radiation
     length at minimum ionisation), the particle loses the mean energy
-    eloss * x / beta^2 for the same path x (no straggling).  Returns per (particle, layer) the path
+    eloss * x / beta^2 for the same path x (no straggling).  x0 may also be an
+    r-z material map (dict: r_max, z_min, z_max, x0 [nr, nz], eloss [nr, nz] or
+    None; cells of equal size, points outside it in the nearest edge cell): each
+    crossing then takes x0 and eloss from the cell holding its (r, z) and the
+    eloss argument is not used.  Returns per (particle, layer) the path
     from the vertex, the crossing point, and (q/pT, phi, theta) after the kick;
     NaN where the cylinder is not reached."""
     P, L = h.shape[0], rz.shape[0]
@@ -133,15 +137,25 @@ def _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, x0,
         zn = z + sf / np.tan(th)
         phin = phi + hh * sf
         inside = ok & (zn >= lo[l]) & (zn <= hi[l])
+        if isinstance(x0, dict):
+            nr, nz = np.shape(x0["x0"])
+            ir = np.clip(np.floor(rz[l] / x0["r_max"] * nr), 0, nr - 1).astype(np.int64)
+            iz = np.clip(np.floor((np.nan_to_num(zn) - x0["z_min"]) / (x0["z_max"] - x0["z_min"]) * nz),
+                         0, nz - 1).astype(np.int64)
+            x0v = np.asarray(x0["x0"], dtype=np.float64)[ir, iz]
+            elv = (np.zeros(P) if x0.get("eloss") is None
+                   else np.asarray(x0["eloss"], dtype=np.float64)[ir, iz])
+        else:
+            x0v, elv = np.full(P, float(x0)), np.full(P, float(eloss))
         # kick (drawn for every particle and layer, used where the layer is crossed)
         gk = rng_ms.standard_normal((P, 2))
         cosa = np.abs(np.sin(th) * np.cos(phin - np.arctan2(yn, xn)))
-        t0 = _highland(pmom, x0 / np.maximum(cosa, 1e-6))
+        t0 = np.where(x0v > 0.0, _highland(pmom, np.maximum(x0v, 1e-30) / np.maximum(cosa, 1e-6)), 0.0)
         th2 = np.where(inside, th + t0 * gk[:, 0], th)
         phi2 = np.where(inside, phin + t0 * gk[:, 1] / np.sin(th), phin)
-        if eloss > 0.0:
+        if (elv > 0.0).any():
             beta = pmom / np.sqrt(pmom * pmom + PION_MASS * PION_MASS)
-            e_new = np.sqrt(pmom * pmom + PION_MASS * PION_MASS) - eloss * (x0 / np.maximum(cosa, 1e-6)) / (beta * beta)
+            e_new = np.sqrt(pmom * pmom + PION_MASS * PION_MASS) - elv * (x0v / np.maximum(cosa, 1e-6)) / (beta * beta)
             stops = inside & (e_new <= PION_MASS)
             pmom = np.where(inside & ~stops, np.sqrt(np.maximum(e_new * e_new - PION_MASS * PION_MASS, 1e-30)), pmom)
             ok = ok & ~stops
@@ -291,7 +305,7 @@ class Batch:
 def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: int | None = None,
                base_seed: int = BASE_SEED, ineff: float | None = None, noise_scale: float = 1.0,
                eta_max: float | None = None, smear: bool = True, overlap: float = 0.0, material: float = 0.0,
-               eloss: float = 0.0, field_alpha: float | None = None):
+               eloss: float = 0.0, field_alpha: float | None = None, material_map: dict | None = None):
     """One event as a dict of per-event arrays (local hit and particle indices).
 
     overlap > 0: each signal hit gets, with that probability, a second hit of the
@@ -310,7 +324,12 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
     field_alpha (layouts of cylinders only, no material): the particles move in
     the parameterised field solenoid_field(bz, field_alpha, ...) instead of the
     uniform one (see _field_cylinder_crossings); no random numbers are drawn
-    for it."""
+    for it.
+
+    material_map (layouts of cylinders only, instead of material / eloss): an
+    r-z map (dict: r_max, z_min, z_max, x0 [nr, nz], eloss [nr, nz] or None)
+    from which each crossing takes its material; the same random stream as
+    material."""
     cfg = get_config(config)
     layers = cfg["layers"]
     rng = _rng(config, event, base_seed)
@@ -360,13 +379,16 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
             raise ValueError("the parameterised field is supported for layouts of cylinders without material")
         ms = _field_cylinder_crossings(phi0, z0, theta, q, pt, bz, float(field_alpha), rz)
         S = ms["S"]
-    elif material > 0.0:
+    elif material > 0.0 or material_map is not None:
         if dsk.size:
             raise ValueError("material is supported for layouts of cylinders only")
+        if material_map is not None and (material > 0.0 or eloss > 0.0):
+            raise ValueError("give either material / eloss or material_map")
         key = (int(base_seed) << 64) | (CONFIG_IDS[config] << 32) | (int(event) & 0xFFFFFFFF)
         rng_ms = np.random.Generator(np.random.Philox(key=key ^ (0x5CA77E8 << 96)))
-        ms = _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, float(material), rng_ms, s_max,
-                                           float(eloss))
+        ms = _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi,
+                                           material_map if material_map is not None else float(material), rng_ms,
+                                           s_max, float(eloss))
         S = ms["S"]
     Sf = np.where(np.isnan(S), 1.0, S)
     if ms is None:
@@ -547,6 +569,7 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
         particle_nhits=np.concatenate(p_nh).astype(np.int32),
         particle_event=np.concatenate(p_ev).astype(np.int32),
         particle_par=np.concatenate(p_par, axis=1),
-        meta=dict(events=events, base_seed=base_seed, field_alpha=kw.get("field_alpha")),
+        meta=dict(events=events, base_seed=base_seed, field_alpha=kw.get("field_alpha"),
+              material_map=kw.get("material_map")),
         seed_dup_of=np.concatenate(seed_dup).astype(np.int32),
     )

@@ -66,9 +66,10 @@ def make_ctx(batch, plans=None, edges=None):
     from paper_1811_04141_gb300 import Context, build
     build.build()
     ctx = Context(0)
-    # the parameterised field where the batch names one (as the oracle's
-    # geometry_for reads it)
-    ctx.geometry_load(batch.layers, batch.bz, plans, edges, batch.meta.get("field_alpha"))
+    # the parameterised field and the r-z material map where the batch names
+    # them (as the oracle's geometry_for reads them)
+    ctx.geometry_load(batch.layers, batch.bz, plans, edges, batch.meta.get("field_alpha"),
+                      batch.meta.get("material_map"))
     return ctx
 
 

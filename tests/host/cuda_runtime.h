@@ -8,3 +8,5 @@ enum { cudaSuccess = 0 };
 inline int cudaGetDevice(int *d) { *d = 0; return 0; }
 inline int cudaSetDevice(int) { return 0; }
 struct float4 { float x, y, z, w; };
+struct float2 { float x, y; };
+inline float2 make_float2(float x, float y) { return float2{x, y}; }

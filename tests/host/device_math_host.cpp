@@ -1,14 +1,6 @@
 // Host build of the device math header (FP32, same expressions) for CPU tests
 // of its self-contained helpers.  Only the qualifiers are mapped away.
-#include <cmath>
-#include <cstdint>
-#include <cstring>
-#define __device__
-#define __host__
-#define __forceinline__ inline
-using std::isfinite;
-static inline float __int_as_float(int i) { float f; std::memcpy(&f, &i, 4); return f; }
-static inline int __float_as_int(float f) { int i; std::memcpy(&i, &f, 4); return i; }
+#include "host_prelude.h"
 #include "mkf_math.cuh"
 
 extern "C" void host_sincos_small(const float *x, float *s, float *c, int n) {

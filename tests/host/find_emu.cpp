@@ -18,7 +18,8 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
                         const int *layer, int n_hits, const int *event_offsets, int n_events, const int *seed_hits,
                         const int *seed_event, int n_seeds, int N, float cut, int max_consec, int max_out, int step1,
                         const uint16_t *mlp_bf16, float mlp_tau, float material, float eloss, int field_kind,
-                        float alpha,
+                        float alpha, int map_nr, int map_nz, float map_rmax, float map_zmin,
+                        float map_zmax, const float *map_x0, const float *map_eloss, 
                         float *out_par, float *out_cov, float *out_chi2, int *out_nh, int *out_hits,
                         unsigned *out_status, int *counters, int *fault_out) {
     static Geom G;
@@ -29,6 +30,18 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
     }
     G.field_kind = field_kind;  // as mkf_geometry_field sets it
     G.alpha = field_kind ? alpha : 0.f;
+    static std::vector<float2> mapv;
+    mapv.clear();
+    if (map_nr > 0) {  // as mkf_geometry_material_map sets it
+        mapv.resize(static_cast<size_t>(map_nr) * map_nz);
+        for (size_t i = 0; i < mapv.size(); ++i) mapv[i] = make_float2(map_x0[i], map_eloss ? map_eloss[i] : 0.f);
+        G.mat_map = mapv.data();
+        G.map_nr = map_nr;
+        G.map_nz = map_nz;
+        G.map_rinv = static_cast<float>(map_nr) / map_rmax;
+        G.map_zmin = map_zmin;
+        G.map_zinv = static_cast<float>(map_nz) / (map_zmax - map_zmin);
+    }
     const int phys = mkf_phys_variant(G);
     const int64_t n_bins = static_cast<int64_t>(n_events) * G.bins_per_event;
     std::vector<int> key(n_hits);

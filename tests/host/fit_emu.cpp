@@ -14,7 +14,8 @@ dim3 blockDim;
 #include "mkf_geom.h"
 
 extern "C" int emu_fit(const mkf_layer *layers, int nl, float bz, const float *x0, const float *eloss, int field_kind,
-                       float alpha, const float *xyz,
+                       float alpha, int map_nr, int map_nz, float map_rmax, float map_zmin,
+                       float map_zmax, const float *map_x0, const float *map_eloss, const float *xyz,
                        const int32_t *hit_layer, int32_t n_hits, const int32_t *hit_idx, int32_t max_hits, int32_t n,
                        const float *seed_par, const float *seed_cov, int backward, float inflate, float *out_par,
                        float *out_cov, float *chi2, int32_t *ndf, uint32_t *status) {
@@ -26,6 +27,17 @@ extern "C" int emu_fit(const mkf_layer *layers, int nl, float bz, const float *x
     }
     A.G.field_kind = field_kind;
     A.G.alpha = field_kind ? alpha : 0.f;
+    std::vector<float2> mapv;
+    if (map_nr > 0) {  // as mkf_geometry_material_map sets it
+        mapv.resize(static_cast<size_t>(map_nr) * map_nz);
+        for (size_t i = 0; i < mapv.size(); ++i) mapv[i] = make_float2(map_x0[i], map_eloss ? map_eloss[i] : 0.f);
+        A.G.mat_map = mapv.data();
+        A.G.map_nr = map_nr;
+        A.G.map_nz = map_nz;
+        A.G.map_rinv = static_cast<float>(map_nr) / map_rmax;
+        A.G.map_zmin = map_zmin;
+        A.G.map_zinv = static_cast<float>(map_nz) / (map_zmax - map_zmin);
+    }
     const int phys = mkf_phys_variant(A.G);
     mkf_fault fault{0, 0};
     A.X = xyz;

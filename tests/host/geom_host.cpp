@@ -1,13 +1,5 @@
 // Host build of the library's geometry-table construction (tests only).
-#include <cmath>
-#include <cstdint>
-#include <cstring>
-#define __device__
-#define __host__
-#define __forceinline__ inline
-using std::isfinite;
-static inline float __int_as_float(int i) { float f; std::memcpy(&f, &i, 4); return f; }
-static inline int __float_as_int(float f) { int i; std::memcpy(&i, &f, 4); return i; }
+#include "host_prelude.h"
 #include "mkf_geom.h"
 
 // out: [0] n_cyl, [1] n_dsk, [2] bins_per_event, [3..3+n) bin_base per layer,

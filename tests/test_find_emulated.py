@@ -55,17 +55,21 @@ def emu_so():
 
 
 def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1, mlp_bf16=None, tau=0.0, material=0.0, eloss=0.0,
-            alpha=None, gen_field=False):
+            alpha=None, gen_field=False, mmap=None):
     d = tempfile.mkdtemp()
     out = os.path.join(d, "out.npz")
-    wpath = "none"
+    wpath, mpath = "none", "none"
+    if mmap is not None:
+        mpath = os.path.join(d, "map.npz")
+        extra = {} if mmap.get("eloss") is None else {"eloss": mmap["eloss"]}
+        np.savez(mpath, r_max=mmap["r_max"], z_min=mmap["z_min"], z_max=mmap["z_max"], x0=mmap["x0"], **extra)
     if mlp_bf16 is not None:
         wpath = os.path.join(d, "w.npy")
         np.save(wpath, mlp_bf16)
     r = subprocess.run([sys.executable, os.path.join(HERE, "host", "run_find_emu.py"), so, cfg, str(event),
                         str(n_tracks), "none" if n_noise is None else str(n_noise), str(n_best), str(step1), out,
                         wpath, str(tau), str(material), str(eloss), "none" if alpha is None else repr(alpha),
-                        "1" if gen_field else "0", ROOT],
+                        "1" if gen_field else "0", mpath, ROOT],
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     z = np.load(out)
@@ -116,6 +120,19 @@ def test_emulated_finder_in_parameterised_field_matches_oracle(emu_so, cfg, gen_
     ref = O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=n_best, max_out=len(b.layers) + 3)
     out = run_emu(emu_so, cfg, 46, 120, None, n_best, 1, alpha=alpha, gen_field=gen_field)
+    compare(out, ref)
+
+
+@pytest.mark.parametrize("n_best", [1, 10])
+def test_emulated_finder_with_material_map_matches_oracle(emu_so, n_best):
+    """The finder with an r-z material map (each crossing's material from its
+    cell) on tracks the generator scatters and slows with the same map."""
+    from tests.test_oracle_material_map import _graded_map
+    mm = _graded_map()
+    b = make_batch("fit10", [47], n_tracks=150, material_map=mm)
+    ref = O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+                 n_best=n_best, max_out=len(b.layers) + 3)
+    out = run_emu(emu_so, "fit10", 47, 150, None, n_best, 1, mmap=mm)
     compare(out, ref)
 
 

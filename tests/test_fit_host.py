@@ -43,7 +43,18 @@ def lib():
     return C.CDLL(so)
 
 
-def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0, eloss=None, alpha=None):
+def _map_args(mm):
+    """ctypes arguments of an r-z material map (or of none)."""
+    if mm is None:
+        return [0, 0, C.c_float(1.0), C.c_float(0.0), C.c_float(1.0), None, None]
+    mx = np.ascontiguousarray(mm["x0"], dtype=np.float32)
+    me = None if mm.get("eloss") is None else np.ascontiguousarray(mm["eloss"], dtype=np.float32)
+    _map_args.keep = (mx, me)
+    return [mx.shape[0], mx.shape[1], C.c_float(mm["r_max"]), C.c_float(mm["z_min"]), C.c_float(mm["z_max"]),
+            mx.ctypes.data_as(C.c_void_p), None if me is None else me.ctypes.data_as(C.c_void_p)]
+
+
+def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0, eloss=None, alpha=None, mmap=None):
     from paper_1811_04141_gb300 import _native as NN
     lay = b.layers
     arr = (NN.MkfLayer * len(lay))()
@@ -62,7 +73,7 @@ def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0, eloss=No
     sp, sc = (None, None) if seed is None else (np.ascontiguousarray(seed[0], dtype=np.float32),
                                                 np.ascontiguousarray(seed[1], dtype=np.float32))
     rc = lib.emu_fit(arr, len(lay), C.c_float(b.bz), p(x0a), p(ela), 0 if alpha is None else 1,
-                     C.c_float(0.0 if alpha is None else alpha), p(xyz), p(hl), b.n_hits, p(hi), hi.shape[0], n, p(sp),
+                     C.c_float(0.0 if alpha is None else alpha), *_map_args(mmap), p(xyz), p(hl), b.n_hits, p(hi), hi.shape[0], n, p(sp),
                      p(sc), int(backward), C.c_float(inflate), p(out["par"]), p(out["cov"]), p(out["chi2"]),
                      p(out["ndf"]), p(out["status"]))
     assert rc == 0
@@ -95,6 +106,30 @@ def test_fit_kernel_on_host(lib, cfg, material, eloss, alpha):
     # backward pass from the oracle's forward result (FP32) on both sides
     lp, lc = ref["par"].astype(np.float32), ref["cov"].astype(np.float32)
     outb = _run(lib, b, b.track_hits, x0, (lp, lc), True, 100.0, el, alpha)
+    refb = O.fit_backward(geo, b.xyz.astype(np.float64), b.layer, b.track_hits, lp.astype(np.float64),
+                          lc.astype(np.float64), 100.0)
+    assert (outb["status"] == refb["status"]).all()
+    okb = ok & (refb["status"] == 0)
+    assert par_errors(outb["par"][:, okb], refb["par"][:, okb], refb["cov"][:, okb]).max() <= 1.0
+    assert chi2_ok(outb["chi2"][okb], refb["chi2"][okb], refb["ndf"][okb])
+
+
+def test_fit_kernel_on_host_with_material_map(lib):
+    """The fit kernel with an r-z material map (scattering and energy loss
+    from the cell of each crossing) on tracks the generator scatters and slows
+    with the same map, forward and backward, against the oracle."""
+    from tests.test_oracle_material_map import _graded_map
+    mm = _graded_map()
+    b = make_batch("fit10", [32], n_tracks=400, material_map=mm)
+    geo = O.geometry_for(b)
+    out = _run(lib, b, b.track_hits, mmap=mm)
+    ref = O.fit(geo, b.xyz.astype(np.float64), b.layer, b.track_hits)
+    assert (out["status"] == ref["status"]).all() and (out["ndf"] == ref["ndf"]).all()
+    ok = ref["status"] == 0
+    assert par_errors(out["par"][:, ok], ref["par"][:, ok], ref["cov"][:, ok]).max() <= 1.0
+    assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
+    lp, lc = ref["par"].astype(np.float32), ref["cov"].astype(np.float32)
+    outb = _run(lib, b, b.track_hits, None, (lp, lc), True, 100.0, mmap=mm)
     refb = O.fit_backward(geo, b.xyz.astype(np.float64), b.layer, b.track_hits, lp.astype(np.float64),
                           lc.astype(np.float64), 100.0)
     assert (outb["status"] == refb["status"]).all()

@@ -226,3 +226,12 @@ def test_find_in_parameterised_field(cfg, alpha, n_best):
         b = make_batch(cfg, [75], n_tracks=500)
         b.meta["field_alpha"] = alpha
     compare(run_gpu(b, n_best), run_oracle(b, n_best))
+
+
+@pytest.mark.parametrize("n_best", [1, 10])
+def test_find_with_material_map(n_best):
+    """Finding with an r-z material map on tracks the generator scatters and
+    slows with the same map; the same parity bar."""
+    from tests.test_oracle_material_map import _graded_map
+    b = make_batch("fit10", [76], n_tracks=800, material_map=_graded_map())
+    compare(run_gpu(b, n_best), run_oracle(b, n_best))

@@ -201,6 +201,28 @@ def test_fit_in_parameterised_field_parity(cfg, alpha):
     assert chi2_ok(outb["chi2"][okb], refb["chi2"][okb], refb["ndf"][okb])
 
 
+def test_fit_with_material_map_parity():
+    """Forward and backward fit with an r-z material map (each crossing's
+    scattering and energy loss from its cell) on tracks the generator scatters
+    and slows with the same map, against the oracle."""
+    from tests.test_oracle_material_map import _graded_map
+    b = make_batch("fit10", [18], n_tracks=800, material_map=_graded_map())
+    ctx = make_ctx(b)
+    d = upload(b)
+    out = to_np(ctx.fit(d["xyz"], d["layer"], d["track_hits"]))
+    ctx.sync()
+    ref = oracle_fit(b)
+    assert (out["status"] == ref["status"]).all()
+    ok = ref["status"] == 0
+    assert par_errors(out["par"][:, ok], ref["par"][:, ok], ref["cov"][:, ok]).max() <= 1.0
+    assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
+    outb, refb, f = _backward_pair(b, b.track_hits, 100.0, ctx)
+    okb = (refb["status"] == 0) & (f["status"] == 0)
+    assert (outb["status"] == refb["status"]).all()
+    assert par_errors(outb["par"][:, okb], refb["par"][:, okb], refb["cov"][:, okb]).max() <= 1.0
+    assert chi2_ok(outb["chi2"][okb], refb["chi2"][okb], refb["ndf"][okb])
+
+
 def test_fit_empty_and_errors():
     b = make_batch("fit10", [13], n_tracks=10)
     ctx = make_ctx(b)
