@@ -65,6 +65,8 @@ def _load():
             lib.or_seed.restype = C.c_int
             lib.or_scattering.argtypes = geom + [C.c_int, d, d]
             lib.or_scattering.restype = C.c_int
+            lib.or_eloss.argtypes = geom + [C.c_int, d, d, C.c_double]
+            lib.or_eloss.restype = C.c_int
             lib.or_fit.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, d, d, d, i32, u32]
             lib.or_fit.restype = C.c_int
             lib.or_fit_backward.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, C.c_double, d, d,
@@ -185,6 +187,17 @@ def scattering(geo: Geometry, layer, p):
     if lib.or_scattering(*geo.args(), int(layer), _p(p, C.c_double), _p(Q, C.c_double)) < 0:
         raise ValueError("bad arguments")
     return Q.reshape(6, 6)
+
+
+def eloss(geo: Geometry, layer, p, Cm, sign=1.0):
+    """Mean energy loss (sign +1) or gain (-1) where p crosses `layer`:
+    (p', C') from the state p and covariance Cm (6x6)."""
+    lib = _load()
+    p = _f64(p).copy()
+    Cm = _f64(Cm).reshape(36).copy()
+    if lib.or_eloss(*geo.args(), int(layer), _p(p, C.c_double), _p(Cm, C.c_double), float(sign)) < 0:
+        raise ValueError("bad arguments")
+    return p, Cm.reshape(6, 6)
 
 
 def seed(geo: Geometry, h1, h2, h3, layer1):

@@ -735,6 +735,15 @@ int or_scattering(GEOM_ARGS, int l, const double *p, double *C) {
     return 1;
 }
 
+/* Mean energy loss (sign +1) or gain (-1) in the material where p crosses
+ * layer l, applied to p and C in place. */
+int or_eloss(GEOM_ARGS, int l, double *p, double *C, double sign) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS) || l < 0 || l >= g.n) return -1;
+    add_eloss(&g, l, p, C, sign);
+    return 1;
+}
+
 /* Seed state and prior covariance (6x6) from three hits; returns 1 or 0. */
 int or_seed(GEOM_ARGS, const double *h1, const double *h2, const double *h3, int layer1, double *p, double *C) {
     geom_t g;

@@ -92,3 +92,35 @@ def test_fit_with_graded_map_pulls_and_chi2():
     flat = [dict(d, x0=float(mm["x0"].mean()), eloss=float(mm["eloss"].mean())) for d in b.layers]
     r0 = O.fit(O.Geometry(flat, b.bz), b.xyz64, b.layer, b.track_hits)
     assert abs(r0["chi2"][ok].sum() / r0["ndf"][ok].sum() - 1) > 0.05
+
+
+def test_eloss_covariance_is_the_derivative_of_the_loss_map():
+    """The covariance transform of the energy loss against the derivative of
+    the loss map itself (central differences of the state it returns), for loss
+    and gain, slow and fast, central and forward tracks: d(q/pT')/d(q/pT) to
+    1e-6 (the path through the layer does not depend on q/pT), and the whole
+    transform J C J^T to 2e-2, the differences in theta also moving the path
+    x0 / |cos a| that the transform holds fixed."""
+    b = make_batch("fit10", [0], n_tracks=1)
+    layers = [dict(d, x0=0.05, eloss=0.2) for d in b.layers]
+    geo = O.Geometry(layers, b.bz)
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((6, 6))
+    Cm = A @ A.T + 6 * np.eye(6)
+    e3 = np.zeros((6, 6))
+    e3[3, 3] = 1.0
+    R = layers[4]["r_or_z"]
+    for w, th, sign in ((2.0, 1.2, 1.0), (-1.5, 0.6, 1.0), (0.3, 1.5, 1.0), (1.8, 2.3, -1.0), (-0.9, 1.0, -1.0)):
+        p = np.array([R * np.cos(0.3), R * np.sin(0.3), 12.0, w, 0.35, th])
+        q, C2 = O.eloss(geo, 4, p, Cm, sign)
+        assert abs(q[3] / w - 1) > 1e-3  # the loss does act here
+        J = np.eye(6)
+        for j, e in ((3, 1e-6 * abs(w)), (5, 1e-6)):
+            a, bb = p.copy(), p.copy()
+            a[j] += e
+            bb[j] -= e
+            J[:, j] = (O.eloss(geo, 4, a, Cm, sign)[0] - O.eloss(geo, 4, bb, Cm, sign)[0]) / (2 * e)
+        a33 = np.sqrt(O.eloss(geo, 4, p, e3, sign)[1][3, 3])
+        assert abs(a33 - abs(J[3, 3])) < 1e-6 * abs(J[3, 3]), (w, th, sign, a33, J[3, 3])
+        want = J @ Cm @ J.T
+        assert np.abs(C2 - want).max() < 2e-2 * np.abs(want).max(), (w, th, sign, C2 - want)
