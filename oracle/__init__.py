@@ -72,6 +72,9 @@ def _load():
             lib.or_fit_backward.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, C.c_double, d, d,
                                                    d, i32, u32]
             lib.or_fit_backward.restype = C.c_int
+            lib.or_fit_smooth.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, C.c_double, d, d,
+                                                 d, i32, u32]
+            lib.or_fit_smooth.restype = C.c_int
             lib.or_find.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, i32, i32, C.c_int64, i64, C.c_int64,
                                            C.c_int, C.c_double, C.c_int, d, d, d, i32, i32, C.c_int, u32, i64, d,
                                            d, C.c_double, d, i32, i64, C.c_int64]
@@ -267,6 +270,27 @@ def fit_backward(geo: Geometry, xyz, hit_layer, hit_idx, last_par, last_cov21, i
                              _p(ndf, C.c_int32), _p(st, C.c_uint32))
     if rc != 0:
         raise RuntimeError(f"or_fit_backward failed: {rc}")
+    return dict(par=par, cov=cov, chi2=chi2, ndf=ndf, status=st)
+
+
+def fit_smooth(geo: Geometry, xyz, hit_layer, hit_idx, seed_par=None, seed_cov21=None, inflate=1e4):
+    """Smoothed state at every hit of fixed hit lists (two filters): par
+    [max_hits, 6, n], cov [max_hits, 21, n] per row of hit_idx (NaN where none),
+    and the forward fit's chi2, ndf, status."""
+    lib = _load()
+    xyz = _f64(xyz)
+    hl = np.ascontiguousarray(hit_layer, dtype=np.int32)
+    hi = np.ascontiguousarray(hit_idx, dtype=np.int32)
+    mh, n = hi.shape
+    par, cov = np.zeros((mh, 6, n)), np.zeros((mh, 21, n))
+    chi2, ndf, st = np.zeros(n), np.zeros(n, np.int32), np.zeros(n, np.uint32)
+    sp = None if seed_par is None else _f64(seed_par)
+    sc = None if seed_cov21 is None else _f64(seed_cov21)
+    rc = lib.or_fit_smooth(*geo.args(), _p(xyz, C.c_double), xyz.shape[1], _p(hl, C.c_int32), _p(hi, C.c_int32), mh,
+                           n, _p(sp, C.c_double), _p(sc, C.c_double), float(inflate), _p(par, C.c_double),
+                           _p(cov, C.c_double), _p(chi2, C.c_double), _p(ndf, C.c_int32), _p(st, C.c_uint32))
+    if rc < 0:
+        raise ValueError("bad arguments")
     return dict(par=par, cov=cov, chi2=chi2, ndf=ndf, status=st)
 
 

@@ -914,6 +914,240 @@ int or_fit_backward(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Smoothing: the state at every hit from all of the track's hits             */
+/* ------------------------------------------------------------------------- */
+
+/* Inverse of a symmetric positive definite n x n matrix (Gauss-Jordan with
+ * partial pivoting); 0 if singular. */
+static int invert_n(int n, const double *A, double *Ai) {
+    double M[5 * 10];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < 2 * n; ++j) M[i * 2 * n + j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(M[r * 2 * n + c]) > fabs(M[piv * 2 * n + c])) piv = r;
+        if (!(fabs(M[piv * 2 * n + c]) > 0.0)) return 0;
+        if (piv != c)
+            for (int j = 0; j < 2 * n; ++j) {
+                double tmp = M[c * 2 * n + j];
+                M[c * 2 * n + j] = M[piv * 2 * n + j];
+                M[piv * 2 * n + j] = tmp;
+            }
+        const double d = M[c * 2 * n + c];
+        for (int j = 0; j < 2 * n; ++j) M[c * 2 * n + j] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = M[r * 2 * n + c];
+            for (int j = 0; j < 2 * n; ++j) M[r * 2 * n + j] -= f * M[c * 2 * n + j];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Ai[i * n + j] = M[i * 2 * n + n + j];
+    return 1;
+}
+
+/* Weighted mean of two independent estimates of the state on layer l's
+ * surface: (pf, Cf) and (pb, Cb), both in the forward direction.  On a surface
+ * the state has five free parameters (the position along the normal is fixed),
+ * so the mean is taken in P p, P = the 5 x 6 projection onto (u, z, q/pT, phi,
+ * theta) on a cylinder (u along the surface, perpendicular to the radius at
+ * pf) and (x, y, q/pT, phi, theta) on a disk: with d = P (pb - pf) (phi
+ * wrapped), K = Cf P^T (P (Cf + Cb) P^T)^-1, ps = pf + K d, Cs = Cf - K P Cf. */
+static int combine(const geom_t *g, int l, const double pf[6], const double Cf[36], const double pb[6],
+                   const double Cb[36], double ps[6], double Cs[36]) {
+    double P[30];
+    memset(P, 0, sizeof(P));
+    if (g->kind[l] == 0) {
+        const double ph = atan2(pf[1], pf[0]);
+        P[0] = -sin(ph);
+        P[1] = cos(ph);
+        P[6 + 2] = 1.0;
+    } else {
+        P[0] = 1.0;
+        P[6 + 1] = 1.0;
+    }
+    P[12 + 3] = P[18 + 4] = P[24 + 5] = 1.0;
+    double dp[6];
+    for (int i = 0; i < 6; ++i) dp[i] = pb[i] - pf[i];
+    dp[4] = wrap_pi(dp[4]);
+    double d[5], S[25], Si[25], PC[30], K[30];
+    for (int a = 0; a < 5; ++a) {
+        d[a] = 0.0;
+        for (int i = 0; i < 6; ++i) d[a] += P[a * 6 + i] * dp[i];
+    }
+    for (int a = 0; a < 5; ++a)
+        for (int j = 0; j < 6; ++j) {
+            double v = 0.0;
+            for (int i = 0; i < 6; ++i) v += P[a * 6 + i] * (Cf[i * 6 + j] + Cb[i * 6 + j]);
+            PC[a * 6 + j] = v;
+        }
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) {
+            double v = 0.0;
+            for (int j = 0; j < 6; ++j) v += PC[a * 6 + j] * P[b * 6 + j];
+            S[a * 5 + b] = v;
+        }
+    if (!invert_n(5, S, Si)) return 0;
+    for (int i = 0; i < 6; ++i)
+        for (int b = 0; b < 5; ++b) {
+            double v = 0.0;
+            for (int a = 0; a < 5; ++a) {
+                double cp = 0.0;
+                for (int j = 0; j < 6; ++j) cp += Cf[i * 6 + j] * P[a * 6 + j];
+                v += cp * Si[a * 5 + b];
+            }
+            K[i * 5 + b] = v;
+        }
+    for (int i = 0; i < 6; ++i) {
+        double v = pf[i];
+        for (int a = 0; a < 5; ++a) v += K[i * 5 + a] * d[a];
+        ps[i] = v;
+    }
+    ps[4] = wrap_pi(ps[4]);
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double v = Cf[i * 6 + j];
+            for (int a = 0; a < 5; ++a) {
+                double pc = 0.0;
+                for (int m = 0; m < 6; ++m) pc += P[a * 6 + m] * Cf[m * 6 + j];
+                v -= K[i * 5 + a] * pc;
+            }
+            Cs[i * 6 + j] = v;
+        }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < i; ++j) Cs[i * 6 + j] = Cs[j * 6 + i] = 0.5 * (Cs[i * 6 + j] + Cs[j * 6 + i]);
+    return 1;
+}
+
+/* Smoothed states along fixed hit lists (two filters): the forward filter as
+ * or_fit, keeping its state after each hit; then the backward filter from the
+ * forward state at the last hit (turned around, covariance times inflate),
+ * which at each earlier hit predicts the state from the later hits alone and
+ * is then updated with that hit, as or_fit_backward.  The smoothed state at a
+ * hit is the weighted mean (combine) of the forward state after the hit and the
+ * backward prediction there; at the last hit it is the forward state.  Outputs:
+ * sm_par [max_hits][6][n], sm_cov [max_hits][21][n] (packed) per row of hit_idx
+ * (NaN where the row holds no hit or a step failed), and the forward fit's
+ * chi2, ndf and status (with the backward pass's status bits added). */
+int or_fit_smooth(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_layer, const int32_t *hit_idx,
+                  int max_hits, int64_t n, const double *seed_par, const double *seed_cov, double inflate,
+                  double *sm_par, double *sm_cov, double *out_chi2, int32_t *out_ndf, uint32_t *out_status) {
+    geom_t g;
+    if (geom_init(&g, GEOM_PASS)) return -1;
+    if (!(inflate >= 1.0) || max_hits > OR_MAXL + 8) return -1;
+    const double *X = xyz, *Y = xyz + n_hits, *Z = xyz + 2 * n_hits;
+    static double PF[OR_MAXL + 8][6], CF[OR_MAXL + 8][36];
+    for (int64_t t = 0; t < n; ++t) {
+        for (int k = 0; k < max_hits; ++k) {
+            for (int i = 0; i < 6; ++i) sm_par[((int64_t)k * 6 + i) * n + t] = NAN;
+            for (int i = 0; i < 21; ++i) sm_cov[((int64_t)k * 21 + i) * n + t] = NAN;
+        }
+        double p[6], C[36];
+        uint32_t st = 0;
+        int idx[OR_MAXL + 8], row[OR_MAXL + 8], ok[OR_MAXL + 8];
+        int nh = 0;
+        for (int k = 0; k < max_hits; ++k) {
+            int32_t hi_ = hit_idx[(int64_t)k * n + t];
+            if (hi_ >= 0 && hi_ < n_hits) {
+                row[nh] = k;
+                idx[nh++] = hi_;
+            }
+        }
+        double chi2 = 0;
+        int used = 0;
+        if (nh < 3) st |= OR_ST_BADSEED;
+        if (!(st & OR_ST_BADSEED)) {
+            if (seed_par) {
+                for (int i = 0; i < 6; ++i) p[i] = seed_par[(int64_t)i * n + t];
+                unpack21(seed_cov + t, n, C);
+            } else {
+                double a[3] = {X[idx[0]], Y[idx[0]], Z[idx[0]]};
+                double b[3] = {X[idx[1]], Y[idx[1]], Z[idx[1]]};
+                double c[3] = {X[idx[2]], Y[idx[2]], Z[idx[2]]};
+                if (!seed_state(&g, a, b, c, hit_layer[idx[0]], p, C)) st |= OR_ST_BADSEED;
+            }
+        }
+        int last = -1;
+        if (!(st & OR_ST_BADSEED)) {
+            for (int k = 0; k < nh; ++k) {
+                int hid = idx[k], l = hit_layer[hid];
+                ok[k] = 0;
+                if (k > 0) {
+                    double s, q[6], J[36], Cn[36];
+                    if (!path_to_layer(&g, p, l, &s)) { st |= OR_ST_UNREACHABLE; continue; }
+                    move_to_layer(&g, p, l, s, q, J);
+                    transport(J, C, Cn);
+                    memcpy(p, q, sizeof(q));
+                    memcpy(C, Cn, sizeof(Cn));
+                    add_scattering(&g, l, p, C);
+                    add_eloss(&g, l, p, C, 1.0);
+                }
+                double H[12], r[2], S[4], Si[4], HC[12];
+                residual(&g, l, p, X[hid], Y[hid], Z[hid], r, H);
+                if (!residual_cov(&g, l, C, H, S, Si, HC)) { st |= OR_ST_BADS; continue; }
+                chi2 += kf_update(HC, Si, r, p, C);
+                used++;
+                memcpy(PF[k], p, sizeof(p));
+                memcpy(CF[k], C, sizeof(C));
+                ok[k] = 1;
+                last = k;
+            }
+        }
+        if (last >= 0 && finite6(p) && isfinite(chi2)) {
+            /* backward filter from the forward state at the last hit */
+            memcpy(p, PF[last], sizeof(p));
+            memcpy(C, CF[last], sizeof(C));
+            reverse_state(p, C);
+            for (int i = 0; i < 36; ++i) C[i] *= inflate;
+            for (int k = last; k >= 0; --k) {
+                int hid = idx[k], l = hit_layer[hid];
+                if (k < last) {
+                    double s, q[6], J[36], Cn[36];
+                    if (!path_to_layer(&g, p, l, &s)) { st |= OR_ST_UNREACHABLE; continue; }
+                    move_to_layer(&g, p, l, s, q, J);
+                    transport(J, C, Cn);
+                    memcpy(p, q, sizeof(q));
+                    memcpy(C, Cn, sizeof(Cn));
+                }
+                double ps[6], Cs[36];
+                int have = 0;
+                if (ok[k] && k == last) {
+                    memcpy(ps, PF[k], sizeof(ps));
+                    memcpy(Cs, CF[k], sizeof(Cs));
+                    have = 1;
+                } else if (ok[k]) {
+                    double pb[6], Cb[36];
+                    memcpy(pb, p, sizeof(pb));
+                    memcpy(Cb, C, sizeof(Cb));
+                    reverse_state(pb, Cb);
+                    have = combine(&g, l, PF[k], CF[k], pb, Cb, ps, Cs);
+                    if (!have) st |= OR_ST_BADS;
+                }
+                if (have) {
+                    for (int i = 0; i < 6; ++i) sm_par[((int64_t)row[k] * 6 + i) * n + t] = ps[i];
+                    pack21(Cs, sm_cov + (int64_t)row[k] * 21 * n + t, n);
+                }
+                double H[12], r[2], S[4], Si[4], HC[12];
+                residual(&g, l, p, X[hid], Y[hid], Z[hid], r, H);
+                if (residual_cov(&g, l, C, H, S, Si, HC)) {
+                    kf_update(HC, Si, r, p, C);
+                } else {
+                    st |= OR_ST_BADS;
+                }
+                add_eloss(&g, l, p, C, -1.0);
+                add_scattering(&g, l, p, C);
+            }
+        }
+        if (!isfinite(chi2)) st |= OR_ST_NONFINITE;
+        out_chi2[t] = chi2;
+        out_ndf[t] = 2 * used - (g.bz != 0.0 ? 5 : 4);
+        out_status[t] = st;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Finding                                                                    */
 /* ------------------------------------------------------------------------- */
 
