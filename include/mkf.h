@@ -296,6 +296,26 @@ mkf_status mkf_fit_backward(mkf_ctx *ctx, const float *xyz, const int32_t *hit_l
                             const float *last_cov, float inflate, float *out_par, float *out_cov, float *chi2,
                             int32_t *ndf, uint32_t *status);
 
+/* Smoothed state at every hit of fixed hit lists (NEXT-1; Sec. 2.1 mentions
+ * back-fit layers): two filters.  The forward filter of mkf_fit (seeded as
+ * there) keeps its state after each hit; the backward filter starts from the
+ * forward state at the last hit, turned around with its covariance multiplied
+ * by inflate (>= 1; large values make the two filters nearly independent, e.g.
+ * 1e4), predicts each earlier hit from the later ones and is updated with it,
+ * its material applied in reverse as in mkf_fit_backward.  The smoothed state
+ * at a hit is the weighted mean of the forward state there and the backward
+ * prediction, taken in the five free parameters on the surface ((u, z) on a
+ * cylinder with u along it, (x, y) on a disk, then q/pT, phi, theta); at the
+ * last hit it is the forward state.  sm_par [max_hits][6][n] and sm_cov
+ * [max_hits][21][n] (device, caller-owned; packed lower triangles) are indexed
+ * by the row of hit_idx; rows without a hit, or where a step failed, are NaN.
+ * chi2, ndf, status: the forward fit's (status also gets the backward pass's
+ * bits).  Errors: as mkf_fit, plus MKF_ERR_ARG for inflate < 1. */
+mkf_status mkf_fit_smooth(mkf_ctx *ctx, const float *xyz, const int32_t *hit_layer, int32_t n_hits,
+                          const int32_t *hit_idx, int32_t max_hits, int32_t n, const float *seed_par,
+                          const float *seed_cov, float inflate, float *sm_par, float *sm_cov, float *chi2,
+                          int32_t *ndf, uint32_t *status);
+
 /* ------------------------------------------------------------------------ */
 /* Seed cleaning and duplicate-track removal (Sec. 2.2: repeated seeds of one */
 /* particle are removed using the identity of their hits and their fitted     */

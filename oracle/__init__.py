@@ -273,7 +273,7 @@ def fit_backward(geo: Geometry, xyz, hit_layer, hit_idx, last_par, last_cov21, i
     return dict(par=par, cov=cov, chi2=chi2, ndf=ndf, status=st)
 
 
-def fit_smooth(geo: Geometry, xyz, hit_layer, hit_idx, seed_par=None, seed_cov21=None, inflate=1e4):
+def fit_smooth(geo: Geometry, xyz, hit_layer, hit_idx, seed_par=None, seed_cov21=None, inflate=100.0):
     """Smoothed state at every hit of fixed hit lists (two filters): par
     [max_hits, 6, n], cov [max_hits, 21, n] per row of hit_idx (NaN where none),
     and the forward fit's chi2, ndf, status."""

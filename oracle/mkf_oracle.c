@@ -953,7 +953,9 @@ static int invert_n(int n, const double *A, double *Ai) {
  * so the mean is taken in P p, P = the 5 x 6 projection onto (u, z, q/pT, phi,
  * theta) on a cylinder (u along the surface, perpendicular to the radius at
  * pf) and (x, y, q/pT, phi, theta) on a disk: with d = P (pb - pf) (phi
- * wrapped), K = Cf P^T (P (Cf + Cb) P^T)^-1, ps = pf + K d, Cs = Cf - K P Cf. */
+ * wrapped), K = Cf P^T (P (Cf + Cb) P^T)^-1, ps = pf + K d (its position put
+ * back on the surface), Cs = Cf - K P Cf (its position block projected onto
+ * the tangent plane at ps). */
 static int combine(const geom_t *g, int l, const double pf[6], const double Cf[36], const double pb[6],
                    const double Cb[36], double ps[6], double Cs[36]) {
     double P[30];
@@ -1005,6 +1007,15 @@ static int combine(const geom_t *g, int l, const double pf[6], const double Cf[3
         ps[i] = v;
     }
     ps[4] = wrap_pi(ps[4]);
+    /* the mean lies on the surface: the position is put back on it (a move
+     * along the tangent leaves it by a second-order amount) */
+    if (g->kind[l] == 0) {
+        const double f = g->rz[l] / hypot(ps[0], ps[1]);
+        ps[0] *= f;
+        ps[1] *= f;
+    } else {
+        ps[2] = g->rz[l];
+    }
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) {
             double v = Cf[i * 6 + j];
@@ -1017,6 +1028,30 @@ static int combine(const geom_t *g, int l, const double pf[6], const double Cf[3
         }
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < i; ++j) Cs[i * 6 + j] = Cs[j * 6 + i] = 0.5 * (Cs[i * 6 + j] + Cs[j * 6 + i]);
+    /* no variance along the surface normal n at ps: Cs -> (I - n n^T) Cs (I - n n^T) */
+    double nv[3] = {0.0, 0.0, 1.0};
+    if (g->kind[l] == 0) {
+        const double r = hypot(ps[0], ps[1]);
+        nv[0] = ps[0] / r;
+        nv[1] = ps[1] / r;
+        nv[2] = 0.0;
+    }
+    double Pi[36];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) Pi[i * 6 + j] = (i == j ? 1.0 : 0.0) - (i < 3 && j < 3 ? nv[i] * nv[j] : 0.0);
+    double Tm[36];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double v = 0.0;
+            for (int m = 0; m < 6; ++m) v += Pi[i * 6 + m] * Cs[m * 6 + j];
+            Tm[i * 6 + j] = v;
+        }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double v = 0.0;
+            for (int m = 0; m < 6; ++m) v += Tm[i * 6 + m] * Pi[j * 6 + m];
+            Cs[i * 6 + j] = v;
+        }
     return 1;
 }
 

@@ -34,7 +34,7 @@ MAX_NBEST = 16
 
 # Symbols declared in include/mkf.h (checked by the ABI test).
 EXPORTS = ("mkf_create", "mkf_destroy", "mkf_set_stream", "mkf_sync", "mkf_status_string", "mkf_geometry_load",
-           "mkf_hits_bin", "mkf_hitbins_free", "mkf_hitbins_info", "mkf_hitbins_export", "mkf_hits_bin_static", "mkf_geometry_material", "mkf_geometry_field", "mkf_geometry_material_map", "mkf_fit", "mkf_fit_backward", "mkf_seeds_clean", "mkf_tracks_dedup", "mkf_find", "mkf_mlp_to_bf16",
+           "mkf_hits_bin", "mkf_hitbins_free", "mkf_hitbins_info", "mkf_hitbins_export", "mkf_hits_bin_static", "mkf_geometry_material", "mkf_geometry_field", "mkf_geometry_material_map", "mkf_fit", "mkf_fit_backward", "mkf_fit_smooth", "mkf_seeds_clean", "mkf_tracks_dedup", "mkf_find", "mkf_mlp_to_bf16",
            "mkf_mlp_forward", "mkf_mlp_grad", "mkf_mlp_train_step")
 
 
@@ -117,6 +117,8 @@ def lib():
             L.mkf_fit.restype = i32
             L.mkf_fit_backward.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, vp, C.c_float, vp, vp, vp, vp, vp]
             L.mkf_fit_backward.restype = i32
+            L.mkf_fit_smooth.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, vp, C.c_float, vp, vp, vp, vp, vp]
+            L.mkf_fit_smooth.restype = i32
             L.mkf_geometry_material.argtypes = [vp, vp, vp, i32]
             L.mkf_geometry_material.restype = i32
             L.mkf_geometry_field.argtypes = [vp, i32, C.c_float]

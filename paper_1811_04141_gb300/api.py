@@ -1,5 +1,5 @@
 """Python binding of the C ABI with the same names (mkf_create, mkf_geometry_load,
-mkf_hits_bin, mkf_fit, mkf_fit_backward, mkf_seeds_clean, mkf_tracks_dedup, mkf_find, mkf_sync,
+mkf_hits_bin, mkf_fit, mkf_fit_backward, mkf_fit_smooth, mkf_seeds_clean, mkf_tracks_dedup, mkf_find, mkf_sync,
 mkf_destroy), plus a small Context
 class.  PyTorch supplies device memory and streams; this module only checks
 tensor shapes, dtypes and devices and passes raw pointers to libmkf.so.
@@ -237,6 +237,34 @@ def mkf_fit_backward(ctx, xyz, hit_layer, hit_idx, last_par, last_cov, inflate=1
     return out
 
 
+def mkf_fit_smooth(ctx, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, inflate=100.0, out=None,
+                   device: int | None = None):
+    """Smoothed state at every hit of fixed hit lists (path order): dict(par
+    [max_hits, 6, n], cov [max_hits, 21, n] per row of hit_idx, NaN where none;
+    chi2, ndf, status of the forward fit)."""
+    n_hits = xyz.shape[1]
+    _need(xyz, "xyz", torch.float32, (3, n_hits), device)
+    _need(hit_layer, "hit_layer", torch.int32, (n_hits,), device)
+    max_hits, n = hit_idx.shape
+    _need(hit_idx, "hit_idx", torch.int32, (max_hits, n), device)
+    if (seed_par is None) != (seed_cov is None):
+        raise ValueError("give both seed_par and seed_cov or neither")
+    if seed_par is not None:
+        _need(seed_par, "seed_par", torch.float32, (6, n), device)
+        _need(seed_cov, "seed_cov", torch.float32, (21, n), device)
+    dev = xyz.device
+    if out is None:
+        out = dict(par=torch.empty(max_hits, 6, n, device=dev), cov=torch.empty(max_hits, 21, n, device=dev),
+                   chi2=torch.empty(n, device=dev), ndf=torch.empty(n, dtype=torch.int32, device=dev),
+                   status=torch.empty(n, dtype=torch.int32, device=dev))
+    N.check("mkf_fit_smooth", N.lib().mkf_fit_smooth(
+        ctx, _ptr(xyz), _ptr(hit_layer), n_hits, _ptr(hit_idx), max_hits, n,
+        None if seed_par is None else _ptr(seed_par), None if seed_cov is None else _ptr(seed_cov),
+        C.c_float(inflate), _ptr(out["par"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out["ndf"]),
+        _ptr(out["status"])))
+    return out
+
+
 def mkf_seeds_clean(ctx, seed_hits, n_hits, seed_par, max_dqpt=0.5, max_deta=0.02, max_dphi=0.02, keep=None,
                     device: int | None = None):
     """keep [n_seeds] int32 (1 = keep, 0 = duplicate of a lower-index seed)."""
@@ -415,6 +443,9 @@ class Context:
 
     def fit_backward(self, xyz, hit_layer, hit_idx, last_par, last_cov, inflate=100.0, out=None):
         return mkf_fit_backward(self.handle, xyz, hit_layer, hit_idx, last_par, last_cov, inflate, out, self.device)
+
+    def fit_smooth(self, xyz, hit_layer, hit_idx, seed_par=None, seed_cov=None, inflate=100.0, out=None):
+        return mkf_fit_smooth(self.handle, xyz, hit_layer, hit_idx, seed_par, seed_cov, inflate, out, self.device)
 
     def find(self, bins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
              out=None, counters=True, block_threads=0, mlp_bf16=None, mlp_tau=0.0, feat=None, event_times=None):

@@ -223,6 +223,39 @@ def test_fit_with_material_map_parity():
     assert chi2_ok(outb["chi2"][okb], refb["chi2"][okb], refb["ndf"][okb])
 
 
+@pytest.mark.parametrize("cfg,kw", [("fit10", {}), ("find20", {}), ("fit10", dict(material=0.03, eloss=0.04)),
+                                    ("fit10", dict(field_alpha=1e-5))])
+def test_fit_smooth_parity(cfg, kw):
+    """Smoothed states at every hit (mkf_fit_smooth, inflate 100) against the
+    oracle's smoother: parameters at every hit, the covariance diagonal as in
+    the fit tests with material (its maximum where the track does not graze the
+    layer), chi2 and status of the forward pass."""
+    import oracle as O
+    b = make_batch(cfg, [19], n_tracks=600, **kw)
+    ctx = make_ctx(b)
+    d = upload(b)
+    out = to_np(ctx.fit_smooth(d["xyz"], d["layer"], d["track_hits"], inflate=100.0))
+    ctx.sync()
+    ref = O.fit_smooth(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.track_hits, inflate=100.0)
+    assert (out["status"] == ref["status"]).all()
+    ok = ref["status"] == 0
+    assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
+    m = (b.track_hits >= 0) & ok[None, :]
+    assert np.array_equal(np.isnan(out["par"][:, 0]) & m, np.isnan(ref["par"][:, 0]) & m)
+    gp, rp = np.transpose(out["par"], (1, 0, 2))[:, m], np.transpose(ref["par"], (1, 0, 2))[:, m]
+    gc, rc = np.transpose(out["cov"], (1, 0, 2))[:, m], np.transpose(ref["cov"], (1, 0, 2))[:, m]
+    assert par_errors(gp, rp, rc).max() <= 1.0
+    hm = b.track_hits[m]
+    ts = b.true_state[:, hm]
+    disk = np.array([dd["kind"] for dd in b.layers])[b.layer[hm]] == 1
+    cosa = np.where(disk, np.abs(np.cos(ts[5])), np.abs(np.sin(ts[5]) * np.cos(ts[4] - np.arctan2(ts[1], ts[0]))))
+    pos = rc[0] + rc[2]
+    for k in (0, 2, 5, 9, 14, 20):
+        floor = 1e-2 * pos if k in (0, 2) else 1e-9 * np.abs(rc).max(axis=0)
+        r = np.abs(gc[k] - rc[k]) / np.maximum(np.abs(rc[k]), floor)
+        assert np.quantile(r, 0.99) < 5e-2 and r[cosa >= 0.3].max() < 1.5e-1, (k, np.quantile(r, 0.99))
+
+
 def test_fit_empty_and_errors():
     b = make_batch("fit10", [13], n_tracks=10)
     ctx = make_ctx(b)
