@@ -201,58 +201,65 @@ def _field_step(bz, alpha, lam, r, t, d):
 FIELD_STEP = 0.5  # cm of path per generator step in the parameterised field
 
 
-def _field_cylinder_crossings(phi0, z0, theta, q, pt, bz, alpha, rz, ds=FIELD_STEP):
-    """Crossings of every cylinder (in radius order) of particles moving in the
-    parameterised field (solenoid_field): the equation of motion integrated in
-    fixed steps of ds cm of path; a step that ends beyond the next radius is
-    replaced by Newton steps from its start onto the cylinder.  A particle whose
-    radius stops growing before the next cylinder (it turns back) crosses no
-    further layer.  Returns per (particle, layer) the path from the vertex, the
-    crossing point and (q/pT, phi, theta) there (q/pT = q / (p sin theta) with
-    |p| fixed: it changes where the field bends theta); NaN where the cylinder
-    is not reached."""
+def _field_crossings(phi0, z0, theta, q, pt, bz, alpha, kinds, rz, lo, hi, ds=FIELD_STEP, s_max=2000.0):
+    """Crossings of every layer by particles moving in the parameterised field
+    (solenoid_field): the equation of motion integrated in fixed steps of ds cm
+    of path from the vertex; a step that ends beyond a cylinder's radius (going
+    out) or across a disk's plane is replaced, for that layer, by Newton steps
+    from the step's start onto it.  A cylinder counts only on the way out (the
+    first crossing), and nothing counts once the particle has turned by half a
+    turn in the transverse plane or gone s_max cm (as with the helix: the
+    outward half-turn), nor once it has left the volume of the layers (lo, hi:
+    their extents).  Returns per (particle, layer) the path from the vertex,
+    the crossing point and (q/pT, phi, theta) there (q/pT = q / (p sin theta)
+    with |p| fixed); NaN where the layer is not crossed."""
     P, L = phi0.shape[0], rz.shape[0]
     out = {k: np.full((P, L), np.nan) for k in ("S", "X", "Y", "Z", "W", "PHI", "TH")}
     r = np.stack([np.zeros(P), np.zeros(P), z0.astype(np.float64)])
     t = np.stack([np.sin(theta) * np.cos(phi0), np.sin(theta) * np.sin(phi0), np.cos(theta)])
     lam = q * np.sin(theta) / pt
     S = np.zeros(P)
+    turned = np.zeros(P)
     alive = np.ones(P, dtype=bool)
-    for l in np.argsort(rz):
-        R = rz[l]
-        todo = alive.copy()
-        for _ in range(100000):
-            idx = np.flatnonzero(todo)
-            if idx.size == 0:
-                break
-            rn, tn = _field_step(bz, alpha, lam[idx], r[:, idx], t[:, idx], ds)
-            cross = np.hypot(rn[0], rn[1]) >= R
-            # particles whose step ends beyond R: Newton steps from the step's start
-            c = idx[cross]
-            if c.size:
-                rc, tc, Sc = r[:, c], t[:, c], S[c].copy()
-                for _n in range(6):
+    done = np.zeros((P, L), dtype=bool)
+    r_out = float(np.max(np.where(kinds == 0, rz, hi))) + 1.0
+    z_out = float(np.max(np.where(kinds == 1, np.abs(rz), np.maximum(np.abs(lo), np.abs(hi))))) + 1.0
+    cyl, dsk = np.nonzero(kinds == 0)[0], np.nonzero(kinds == 1)[0]
+    while alive.any():
+        idx = np.flatnonzero(alive)
+        r0, t0 = r[:, idx], t[:, idx]
+        rn, tn = _field_step(bz, alpha, lam[idx], r0, t0, ds)
+        rho0, rhon = np.hypot(r0[0], r0[1]), np.hypot(rn[0], rn[1])
+        for l in np.concatenate([cyl, dsk]):
+            if kinds[l] == 0:
+                hit = (rho0 < rz[l]) & (rhon >= rz[l]) & ~done[idx, l]
+            else:
+                hit = ((r0[2] - rz[l]) * (rn[2] - rz[l]) <= 0.0) & (r0[2] != rn[2]) & ~done[idx, l]
+            if not hit.any():
+                continue
+            c = idx[hit]
+            rc, tc, Sc = r0[:, hit], t0[:, hit], S[c].copy()
+            for _n in range(6):
+                if kinds[l] == 0:
                     rr = np.hypot(rc[0], rc[1])
-                    d = (R - rr) / ((rc[0] * tc[0] + rc[1] * tc[1]) / rr)
-                    rc, tc = _field_step(bz, alpha, lam[c], rc, tc, d)
-                    Sc = Sc + d
-                r[:, c], t[:, c], S[c] = rc, tc, Sc
-                tt = np.hypot(tc[0], tc[1])
-                out["S"][c, l] = Sc
-                out["X"][c, l], out["Y"][c, l], out["Z"][c, l] = rc[0], rc[1], rc[2]
-                th = np.arctan2(tt, tc[2])
-                out["W"][c, l] = lam[c] / np.sin(th)
-                out["PHI"][c, l] = np.arctan2(tc[1], tc[0])
-                out["TH"][c, l] = th
-                todo[c] = False
-            # the others take the step; those turning back are done for good
-            k = idx[~cross]
-            if k.size:
-                rk, tk = rn[:, ~cross], tn[:, ~cross]
-                back = (rk[0] * tk[0] + rk[1] * tk[1]) <= 0.0
-                r[:, k], t[:, k], S[k] = rk, tk, S[k] + ds
-                todo[k[back]] = False
-                alive[k[back]] = False
+                    d = (rz[l] - rr) / ((rc[0] * tc[0] + rc[1] * tc[1]) / rr)
+                else:
+                    d = (rz[l] - rc[2]) / tc[2]
+                rc, tc = _field_step(bz, alpha, lam[c], rc, tc, d)
+                Sc = Sc + d
+            tt = np.hypot(tc[0], tc[1])
+            th = np.arctan2(tt, tc[2])
+            out["S"][c, l] = Sc
+            out["X"][c, l], out["Y"][c, l], out["Z"][c, l] = rc[0], rc[1], rc[2]
+            out["W"][c, l] = lam[c] / np.sin(th)
+            out["PHI"][c, l] = np.arctan2(tc[1], tc[0])
+            out["TH"][c, l] = th
+            done[c, l] = True
+        # transverse turning of the step (angle between the transverse directions)
+        turned[idx] += np.abs(np.arctan2(t0[0] * tn[1] - t0[1] * tn[0], t0[0] * tn[0] + t0[1] * tn[1]))
+        r[:, idx], t[:, idx] = rn, tn
+        S[idx] += ds
+        alive[idx] = (turned[idx] < np.pi) & (S[idx] < s_max) & (rhon < r_out) & (np.abs(rn[2]) < z_out)
     return out
 
 
@@ -321,10 +328,9 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
     material): the mean energy loss per radiation length at minimum ionisation
     (GeV), lost at each layer crossed.
 
-    field_alpha (layouts of cylinders only, no material): the particles move in
-    the parameterised field solenoid_field(bz, field_alpha, ...) instead of the
-    uniform one (see _field_cylinder_crossings); no random numbers are drawn
-    for it.
+    field_alpha (no material): the particles move in the parameterised field
+    solenoid_field(bz, field_alpha, ...) instead of the uniform one (see
+    _field_crossings); no random numbers are drawn for it.
 
     material_map (layouts of cylinders only, instead of material / eloss): an
     r-z map (dict: r_max, z_min, z_max, x0 [nr, nz], eloss [nr, nz] or None)
@@ -375,9 +381,9 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
         S[:, dsk] = np.where(ok, sd, np.nan)
     ms = None
     if field_alpha is not None:
-        if dsk.size or material > 0.0:
-            raise ValueError("the parameterised field is supported for layouts of cylinders without material")
-        ms = _field_cylinder_crossings(phi0, z0, theta, q, pt, bz, float(field_alpha), rz)
+        if material > 0.0 or material_map is not None:
+            raise ValueError("the parameterised field is supported without material")
+        ms = _field_crossings(phi0, z0, theta, q, pt, bz, float(field_alpha), kinds, rz, lo, hi)
         S = ms["S"]
     elif material > 0.0 or material_map is not None:
         if dsk.size:

@@ -107,12 +107,12 @@ def test_emulated_finder_with_material_matches_oracle(emu_so, n_best, eloss):
     compare(out, ref)
 
 
-@pytest.mark.parametrize("cfg,gen_field,n_best", [("fit10", True, 10), ("find20", False, 10), ("find20", False, 1)])
+@pytest.mark.parametrize("cfg,gen_field,n_best", [("fit10", True, 10), ("find20", True, 10), ("find20", False, 1)])
 def test_emulated_finder_in_parameterised_field_matches_oracle(emu_so, cfg, gen_field, n_best):
     """The finder variant with Runge-Kutta propagation in the parameterised
-    field against the oracle in the same field: on fit10 the generator moves
-    the particles through that field; on find20 (disks too) the hits come from
-    the uniform field and only the filter uses the other one."""
+    field against the oracle in the same field, on tracks the generator moves
+    through that field (fit10; find20, disks too) and, once, on find20 hits
+    from the uniform field that only the filter sees in the other one."""
     alpha = 1e-5 if gen_field else 1e-6  # find20's disks reach z = 270 cm
     b = (make_batch(cfg, [46], n_tracks=120, field_alpha=alpha) if gen_field
          else make_batch(cfg, [46], n_tracks=120))

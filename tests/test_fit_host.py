@@ -87,13 +87,12 @@ def _run(lib, b, hidx, x0=None, seed=None, backward=False, inflate=1.0, eloss=No
     ("fit10", 0.0, 0.0, None), ("find20", 0.0, 0.0, None), ("fit10", 0.03, 0.0, None), ("fit10", 0.03, 0.15, None),
     ("fit10_b0", 0.02, 0.0, None), ("fit10", 0.0, 0.0, 1e-5), ("find20", 0.0, 0.0, 1e-6)])
 def test_fit_kernel_on_host(lib, cfg, material, eloss, alpha):
-    """alpha: the parameterised field (Runge-Kutta variant); fit10 tracks then
-    move through it, find20 tracks (disks) come from the uniform field, so
-    their field differs from the filter's by alpha z^2 (7 % at the last disk,
-    z = 270 cm, for alpha = 1e-6)."""
+    """alpha: the parameterised field (Runge-Kutta variant), the tracks moved
+    through it by the generator (find20: disks up to z = 270 cm, where Bz is
+    7 % lower for alpha = 1e-6)."""
     if material:
         b = make_batch(cfg, [31], n_tracks=400, material=material, eloss=eloss)
-    elif alpha is not None and cfg == "fit10":
+    elif alpha is not None:
         b = make_batch(cfg, [31], n_tracks=400, field_alpha=alpha)
     else:
         b = make_batch(cfg, [31], n_tracks=400)

@@ -217,14 +217,9 @@ def test_find_with_material(cfg, material, n_best, eloss):
 @pytest.mark.parametrize("cfg,alpha,n_best", [("fit10", 1e-5, 10), ("find20", 1e-6, 10), ("find20", 1e-6, 1)])
 def test_find_in_parameterised_field(cfg, alpha, n_best):
     """Finding in the parameterised field (the Runge-Kutta variants of the seed
-    and find kernels): on fit10 the generator moves the tracks through that
-    field; on find20 (disks too) the hits come from the uniform field and only
-    the filter uses the other one; the same parity bar."""
-    if cfg == "fit10":
-        b = make_batch(cfg, [75], n_tracks=800, field_alpha=alpha)
-    else:
-        b = make_batch(cfg, [75], n_tracks=500)
-        b.meta["field_alpha"] = alpha
+    and find kernels) on tracks the generator moves through that field (find20:
+    disks too); the same parity bar."""
+    b = make_batch(cfg, [75], n_tracks=800 if cfg == "fit10" else 500, field_alpha=alpha)
     compare(run_gpu(b, n_best), run_oracle(b, n_best))
 
 

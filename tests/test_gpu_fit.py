@@ -172,14 +172,9 @@ def test_fit_with_material_parity(cfg, material, eloss):
 @pytest.mark.parametrize("cfg,alpha", [("fit10", 1e-5), ("find20", 1e-6)])
 def test_fit_in_parameterised_field_parity(cfg, alpha):
     """Forward and backward fit in the parameterised field (the Runge-Kutta
-    variant) against the oracle: on fit10 the generator moves the tracks
-    through that field; on find20 (disks, up to z = 270 cm) the tracks come
-    from the uniform field and only the filter uses the other one."""
-    if cfg == "fit10":
-        b = make_batch(cfg, [17], n_tracks=800, field_alpha=alpha)
-    else:
-        b = make_batch(cfg, [17], n_tracks=500)
-        b.meta["field_alpha"] = alpha
+    variant) against the oracle, on tracks the generator moves through that
+    field (find20: disks up to z = 270 cm)."""
+    b = make_batch(cfg, [17], n_tracks=800 if cfg == "fit10" else 500, field_alpha=alpha)
     ctx = make_ctx(b)
     d = upload(b)
     out = to_np(ctx.fit(d["xyz"], d["layer"], d["track_hits"]))

@@ -247,3 +247,23 @@ def test_rk_from_hit_to_hit_including_grazing_crossings():
             radial = np.sin(want[5]) * np.cos(want[4] - np.arctan2(want[1], want[0]))
             grazing += radial < 0.15
     assert grazing >= 2
+
+
+def test_fit_in_parameterised_field_with_disks_pulls():
+    """find20 (5 disks per side up to |z| = 270 cm) moved through the field:
+    the fit's pulls are N(0, 1) there too; the uniform-field filter's chi2/ndf
+    is off on the same hits."""
+    alpha = 3e-6
+    b = make_batch("find20", [0, 1], n_tracks=1500, field_alpha=alpha)
+    geo = O.geometry_for(b)
+    r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
+    ok = r["status"] == 0
+    assert ok.mean() > 0.99
+    truth = b.true_state[:, _last_hits(b)][:, ok]
+    # q/pT, phi, theta (many tracks end on a disk, where z is fixed)
+    for i, pull in _pulls(r["par"][:, ok], truth, r["cov"][:, ok], (3, 4, 5)).items():
+        assert abs(pull.mean()) < 0.05, i
+        assert abs(pull.std() - 1) < 0.05, i
+    assert abs(r["chi2"][ok].sum() / r["ndf"][ok].sum() - 1) < 0.03
+    r0 = O.fit(O.Geometry(b.layers, b.bz), b.xyz64, b.layer, b.track_hits)
+    assert r0["chi2"][ok].sum() / r0["ndf"][ok].sum() > 2
