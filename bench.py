@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--batched-events", type=int, default=512)
     ap.add_argument("--no-fit", action="store_true", help="skip the 10^6-track fit leg")
     ap.add_argument("--no-post", action="store_true", help="skip the seed-cleaning / duplicate-removal timing")
+    ap.add_argument("--physics", action="store_true",
+                    help="also time the material and parameterised-field fits and the smoother (off by default)")
     return ap.parse_args()
 
 
@@ -410,6 +412,55 @@ def fit_leg(dev, n_tracks: int = 1_000_000, reps: int = 20):
                          "roofline": roof(ms_b, "fit_kernel (backward)")}}
 
 
+def physics_leg(dev, n_events: int = 5, per_event: int = 10000, reps: int = 10):
+    """Timing of the fit's physics variants on fit10 tracks (off by default,
+    --physics): the material variant (0.03 X0 and 0.04 GeV/X0 per layer, tracks
+    scattered and slowed by the generator), the parameterised-field variant
+    (alpha = 1e-5 /cm^2, tracks moved through that field by the generator) and
+    the smoother (state at every hit, inflate 100) on uniform-field tracks."""
+    import torch
+
+    from paper_1811_04141_gb300 import Context
+    from synth import make_batch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            e.record()
+            ts.append((a, e))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(e) for a, e in ts]))
+
+    res = {}
+    cases = (("material", dict(material=0.03, eloss=0.04), "fit"),
+             ("field", dict(field_alpha=1e-5), "fit"),
+             ("smoother", {}, "smooth"))
+    for name, kw, kind in cases:
+        b = make_batch("fit10", range(n_events), n_tracks=per_event, **kw)
+        ctx = Context(dev.index, torch.cuda.current_stream(dev))
+        ctx.geometry_load(b.layers, b.bz, field_alpha=b.meta.get("field_alpha"))
+        xyz, layer, th = to(b.xyz, torch.float32), to(b.layer, torch.int32), to(b.track_hits, torch.int32)
+        if kind == "fit":
+            out = ctx.fit(xyz, layer, th)
+            ms = timed(lambda: ctx.fit(xyz, layer, th, out=out))
+        else:
+            out = ctx.fit_smooth(xyz, layer, th)
+            ms = timed(lambda: ctx.fit_smooth(xyz, layer, th, out=out))
+        ctx.close()
+        layers = int((b.track_hits >= 0).sum())
+        res[name] = {"tracks": int(b.n_seeds), "ms": ms, "track_layer_updates_per_s": layers / (ms * 1e-3)}
+    return res
+
+
 FIND_DRAM_BYTES = None  # dram__bytes_read.sum + dram__bytes_write.sum of find_kernel on find20; None until re-measured for this kernel version
 
 
@@ -654,6 +705,9 @@ def run_ours(args, world, rank, local, pg):
     fit = None
     if rank == 0 and world == 1 and not args.no_fit:
         fit = fit_leg(dev)
+    physics = None
+    if rank == 0 and world == 1 and args.physics:
+        physics = physics_leg(dev)
 
     launches_per_step = 6  # bin_keys, scan_tiles, scan_write, scatter, seed, find
     line = {
@@ -669,7 +723,7 @@ def run_ours(args, world, rank, local, pg):
                    "l2": "flushed between steps (256 MiB write, outside the per-step CUDA events)",
                    "wall_s_timed_region": round(wall, 3), "parallelism": f"events sharded, {world} GPU(s)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "learned": learned,
-        "batched": batched, "fit": fit, "best_hit": best_hit, "post": post,
+        "batched": batched, "fit": fit, "best_hit": best_hit, "post": post, "physics": physics,
         "gpu_launches": launches_per_step * K,
     }
     if rank == 0:
