@@ -49,6 +49,12 @@ def test_status_strings_and_errors_without_gpu(libmkf):
     assert libmkf.mkf_sync(None) == N.MKF_ERR_ARG
     assert libmkf.mkf_fit(None, None, None, 0, None, 1, 0, None, None, None, None, None, None, None) == N.MKF_ERR_ARG
     assert libmkf.mkf_hitbins_info(None, None, None, None) == N.MKF_ERR_ARG
+    assert libmkf.mkf_fit_smooth(None, None, None, 0, None, 1, 0, None, None, ctypes.c_float(100.0), None, None,
+                                 None, None, None) == N.MKF_ERR_ARG
+    assert libmkf.mkf_geometry_field(None, 1, ctypes.c_float(1e-5)) == N.MKF_ERR_ARG
+    assert libmkf.mkf_geometry_material(None, None, None, 0) == N.MKF_ERR_ARG
+    assert libmkf.mkf_geometry_material_map(None, 1, 1, ctypes.c_float(1.0), ctypes.c_float(0.0), ctypes.c_float(1.0),
+                                            None, None) == N.MKF_ERR_ARG
 
 
 def test_product_path_does_not_import_oracle():
