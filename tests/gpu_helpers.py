@@ -119,3 +119,19 @@ def compare(out, ref, sel=None, min_same=0.999):
     st_mask = O.ST_BADSEED | O.ST_MISSSTOP | O.ST_TRUNC
     assert ((out["status"][sel][ok] & st_mask) == (ref["status"][ok] & st_mask)).all()
     return same.mean()
+
+
+def steep_crossing(batch, hits):
+    """|cos| of the angle between the true direction and the layer normal at
+    the given hits is at least 0.3.  At a grazing crossing the prior position
+    variance along the layer is up to ~1e7 times the posterior one, which FP32
+    cannot resolve: covariance bars take their maximum over steep crossings."""
+    ts = batch.true_state[:, hits]
+    disk = np.array([d["kind"] for d in batch.layers])[batch.layer[hits]] == 1
+    cosa = np.where(disk, np.abs(np.cos(ts[5])), np.abs(np.sin(ts[5]) * np.cos(ts[4] - np.arctan2(ts[1], ts[0]))))
+    return cosa >= 0.3
+
+
+def last_hits(batch):
+    """Each seed's last hit (path order)."""
+    return np.array([batch.track_hits[:, t][batch.track_hits[:, t] >= 0][-1] for t in range(batch.n_seeds)])

@@ -4,7 +4,8 @@ import pytest
 import torch
 
 from synth import make_batch
-from tests.gpu_helpers import chi2_errors, chi2_ok, make_ctx, oracle_fit, par_errors, to_np, upload
+from tests.gpu_helpers import (chi2_errors, chi2_ok, last_hits, make_ctx, oracle_fit, par_errors, steep_crossing, to_np,
+                               upload)
 
 pytestmark = pytest.mark.gpu
 
@@ -155,13 +156,15 @@ def test_fit_with_material_parity(cfg, material, eloss):
     # covariance diagonal: with scattering noise the FP32 filter's covariance
     # loses more to conditioning (each update shrinks a prior widened by the
     # noise) than without it: 99 % of the tracks within 5e-2 relative, every
-    # track within 1.5e-1; x and y against the transverse position variance (on
-    # a cylinder one of them is nearly radial, with a variance close to zero)
+    # track crossing its last layer steeply within 1.5e-1 (steep_crossing); x
+    # and y against the transverse position variance (on a cylinder one of them
+    # is nearly radial, with a variance close to zero)
     pos = ref["cov"][0, ok] + ref["cov"][2, ok]
+    steep = steep_crossing(b, last_hits(b)[ok])
     for k in (0, 2, 5, 9, 14, 20):
         floor = 1e-2 * pos if k in (0, 2) else 1e-9 * np.abs(ref["cov"][:, ok]).max(axis=0)
         r = np.abs(out["cov"][k, ok] - ref["cov"][k, ok]) / np.maximum(np.abs(ref["cov"][k, ok]), floor)
-        assert np.quantile(r, 0.99) < 5e-2 and r.max() < 1.5e-1, (k, np.quantile(r, 0.99), r.max())
+        assert np.quantile(r, 0.99) < 5e-2 and r[steep].max() < 1.5e-1, (k, np.quantile(r, 0.99), r[steep].max())
     outb, refb, f = _backward_pair(b, b.track_hits, 100.0, ctx)
     okb = (refb["status"] == 0) & (f["status"] == 0)
     assert (outb["status"] == refb["status"]).all()
@@ -185,10 +188,11 @@ def test_fit_in_parameterised_field_parity(cfg, alpha):
     assert par_errors(out["par"][:, ok], ref["par"][:, ok], ref["cov"][:, ok]).max() <= 1.0
     assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
     pos = ref["cov"][0, ok] + ref["cov"][2, ok]
+    steep = steep_crossing(b, last_hits(b)[ok])
     for k in (0, 2, 5, 9, 14, 20):
         floor = 1e-2 * pos if k in (0, 2) else 1e-9 * np.abs(ref["cov"][:, ok]).max(axis=0)
         r = np.abs(out["cov"][k, ok] - ref["cov"][k, ok]) / np.maximum(np.abs(ref["cov"][k, ok]), floor)
-        assert np.quantile(r, 0.99) < 5e-2 and r.max() < 1.5e-1, (k, np.quantile(r, 0.99), r.max())
+        assert np.quantile(r, 0.99) < 5e-2 and r[steep].max() < 1.5e-1, (k, np.quantile(r, 0.99), r[steep].max())
     outb, refb, f = _backward_pair(b, b.track_hits, 100.0, ctx)
     okb = (refb["status"] == 0) & (f["status"] == 0)
     assert (outb["status"] == refb["status"]).all()
@@ -240,15 +244,12 @@ def test_fit_smooth_parity(cfg, kw):
     gp, rp = np.transpose(out["par"], (1, 0, 2))[:, m], np.transpose(ref["par"], (1, 0, 2))[:, m]
     gc, rc = np.transpose(out["cov"], (1, 0, 2))[:, m], np.transpose(ref["cov"], (1, 0, 2))[:, m]
     assert par_errors(gp, rp, rc).max() <= 1.0
-    hm = b.track_hits[m]
-    ts = b.true_state[:, hm]
-    disk = np.array([dd["kind"] for dd in b.layers])[b.layer[hm]] == 1
-    cosa = np.where(disk, np.abs(np.cos(ts[5])), np.abs(np.sin(ts[5]) * np.cos(ts[4] - np.arctan2(ts[1], ts[0]))))
+    steep = steep_crossing(b, b.track_hits[m])
     pos = rc[0] + rc[2]
     for k in (0, 2, 5, 9, 14, 20):
         floor = 1e-2 * pos if k in (0, 2) else 1e-9 * np.abs(rc).max(axis=0)
         r = np.abs(gc[k] - rc[k]) / np.maximum(np.abs(rc[k]), floor)
-        assert np.quantile(r, 0.99) < 5e-2 and r[cosa >= 0.3].max() < 1.5e-1, (k, np.quantile(r, 0.99))
+        assert np.quantile(r, 0.99) < 5e-2 and r[steep].max() < 1.5e-1, (k, np.quantile(r, 0.99))
 
 
 def test_fit_empty_and_errors():
