@@ -424,8 +424,11 @@ __device__ __forceinline__ void tangent_rhs(const RkStage &S, float kba, float l
 // One classical Runge-Kutta step of path hs for the trajectory (d, T) and then,
 // over the same stages, for the six tangent columns (Dr, DT) of the parameters
 // (x, y, z, q/pT, phi, theta), whose lambda derivatives are dl.
+// d is the displacement from r0, dlo the rounding error of its updates (a
+// float pair, as the state's positions).
 __device__ __forceinline__ void rk_step(float kb, float alpha, const float r0[3], float lam, const float dl[6],
-                                        float d[3], float T[3], float Dr[6][3], float DT[6][3], float hs) {
+                                        float d[3], float dlo[3], float T[3], float Dr[6][3], float DT[6][3],
+                                        float hs) {
     RkStage S[4];
     const float hh = 0.5f * hs, h6 = hs * (1.f / 6.f);
     float dd[3], tt[3], sd[3], st[3];
@@ -456,7 +459,7 @@ __device__ __forceinline__ void rk_step(float kb, float alpha, const float r0[3]
     rk_stage(kb, alpha, r0, dd, tt, S[3]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        d[i] = fmaf(h6, sd[i] + S[3].T[i], d[i]);
+        df_add(d[i], dlo[i], h6 * (sd[i] + S[3].T[i]));
         T[i] = fmaf(h6 * lam, st[i] + S[3].tb[i], T[i]);
     }
     const float kba = kb * alpha;
@@ -528,7 +531,7 @@ __device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, f
     const float lam = p[3] * st;
     const float dl[6] = {0.f, 0.f, 0.f, st, 0.f, p[3] * ct};  // d lambda / d(x, y, z, q/pT, phi, theta)
     float T[3] = {st * cphi, st * sphi, ct};
-    float d[3] = {0.f, 0.f, 0.f};
+    float d[3] = {0.f, 0.f, 0.f}, dlo[3] = {0.f, 0.f, 0.f};
     float Dr[6][3], DT[6][3];
 #pragma unroll
     for (int c = 0; c < 6; ++c)
@@ -544,12 +547,12 @@ __device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, f
     const float nf = ceilf(fmaxf(fabsf(h) * s * (1.f / kRkTurn), fabsf(S) * (1.f / kRkLen)));
     const int n = nf >= 1.f ? (nf < static_cast<float>(kRkMaxN) ? static_cast<int>(nf) : kRkMaxN) : 1;
     const float hs = S / static_cast<float>(n);
-    for (int i = 0; i < n; ++i) rk_step(kb, alpha, r0, lam, dl, d, T, Dr, DT, hs);
+    for (int i = 0; i < n; ++i) rk_step(kb, alpha, r0, lam, dl, d, dlo, T, Dr, DT, hs);
     for (int it = 0; it < kRkNewton; ++it) {
         float dn;
         if (Ld.kind == 0) {
             // r^2 - R^2 from the position pair without cancellation
-            const float xl = lo.x + d[0], yl = lo.y + d[1];
+            const float xl = (lo.x + dlo[0]) + d[0], yl = (lo.y + dlo[1]) + d[1];
             const float x = p[0] + xl, y = p[1] + yl;
             const float c = 2.f * fmaf(p[0], xl, p[1] * yl) + fmaf(xl, xl, yl * yl) - diff_sq2(Ld.rz, 0.f, p[0], p[1]);
             float b[3];
@@ -558,9 +561,9 @@ __device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, f
             const float aq = fmaf(T[0], T[0], fmaf(T[1], T[1], fmaf(x, Fx, y * Fy)));
             dn = nearest_root(aq, 2.f * fmaf(x, T[0], y * T[1]), c);
         } else {
-            dn = ((Ld.rz - p[2]) - (lo.z + d[2])) / T[2];
+            dn = ((Ld.rz - p[2]) - ((lo.z + dlo[2]) + d[2])) / T[2];
         }
-        rk_step(kb, alpha, r0, lam, dl, d, T, Dr, DT, dn);
+        rk_step(kb, alpha, r0, lam, dl, d, dlo, T, Dr, DT, dn);
     }
 
     // end point: dT/dS, surface normal, output conversions
@@ -625,12 +628,15 @@ __device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, f
     // state at the end: position pairs, azimuth turned by the angle between
     // the start and end transverse directions, theta and q/pT = lambda / sin(theta)
     df_add(p[0], lo.x, d[0]);
+    df_add(p[0], lo.x, dlo[0]);
     df_add(p[1], lo.y, d[1]);
+    df_add(p[1], lo.y, dlo[1]);
     if (Ld.kind == 1) {
         p[2] = Ld.rz;
         lo.z = 0.f;
     } else {
         df_add(p[2], lo.z, d[2]);
+        df_add(p[2], lo.z, dlo[2]);
     }
     df_add(p[4], lo.phi, atan2f(fmaf(cphi, T[1], -sphi * T[0]), fmaf(cphi, T[0], sphi * T[1])));
     df_wrap_pi(p[4], lo.phi);
