@@ -30,6 +30,12 @@
  *    candidates are ranked by score = chi2_cut * n_hits - chi2_total, the best
  *    N children are kept and only they receive the Kalman update.
  *
+ * Beyond the uniform-field core (each written out where it is defined below):
+ * the backward fit and the two-filter smoother; material effects (Highland
+ * multiple scattering and the mean energy loss, per layer or from an r-z map);
+ * a parameterised solenoid field with fourth-order Runge-Kutta propagation and
+ * the Jacobian of that map by central differences.
+ *
  * Covariances are full 6x6 row-major arrays here.  Interfaces that exchange the
  * 21-value packed lower triangle use index i(i+1)/2 + j for i >= j.
  */
