@@ -202,3 +202,49 @@ def test_smooth_kernel_on_host(lib, cfg, material, eloss, alpha, use_map):
         floor = 1e-2 * pos if k in (0, 2) else 1e-9 * np.abs(rc_).max(axis=0)
         r = np.abs(gc[k] - rc_[k]) / np.maximum(np.abs(rc_[k]), floor)
         assert np.quantile(r, 0.99) < 5e-2 and r[steep].max() < 1.5e-1, (k, np.quantile(r, 0.99), r[steep].max())
+
+
+def test_smoother_weighted_mean_arithmetic(lib):
+    """The kernel's weighted mean of two estimates on a cylinder (base choice,
+    scaled Cholesky, Joseph form, projection back onto the surface) against the
+    plain FP64 definition, for forward/backward precision in both orders."""
+    rng = np.random.default_rng(1)
+    R = 4.0
+
+    def pack(M):
+        return np.array([M[i, j] for i in range(6) for j in range(i + 1)], np.float32)
+
+    for trial in range(8):
+        ph = rng.uniform(-3, 3)
+        T6 = np.zeros((6, 5))
+        T6[0, 0], T6[1, 0] = -np.sin(ph), np.cos(ph)
+        T6[2, 1] = T6[3, 2] = T6[4, 3] = T6[5, 4] = 1.0
+
+        def cov(sp, sa):
+            A = rng.standard_normal((5, 5)) * 0.3 + np.eye(5)
+            D = np.diag([sp, sp, sa, sa, sa])
+            return T6 @ (D @ A @ A.T @ D) @ T6.T
+
+        Cf, Cb = (cov(2e-3, 1e-2), cov(5e-3, 1e-5)) if trial % 2 == 0 else (cov(2e-3, 1e-5), cov(5e-3, 1e-2))
+        # inputs rounded to FP32 first, so that only the arithmetic is compared
+        f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+        pf = f32([R * np.cos(ph + 1e-4), R * np.sin(ph + 1e-4), 3.001, 0.5, ph + 0.202, 1.2])
+        pb = f32([R * np.cos(ph - 2e-4), R * np.sin(ph - 2e-4), 3.0, 0.501, ph + 0.2, 1.2])
+        Cf, Cb = f32(Cf), f32(Cb)
+        # plain definition in the five surface parameters at pf
+        P = np.zeros((5, 6))
+        P[0, 0], P[0, 1] = -np.sin(np.arctan2(pf[1], pf[0])), np.cos(np.arctan2(pf[1], pf[0]))
+        P[1, 2] = P[2, 3] = P[3, 4] = P[4, 5] = 1.0
+        K = Cf @ P.T @ np.linalg.inv(P @ (Cf + Cb) @ P.T)
+        ps_ref = pf + K @ (P @ (pb - pf))
+        Cs_ref = Cf - K @ P @ Cf
+        ps, Cs = np.zeros(6, np.float32), np.zeros(21, np.float32)
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        pf32, pb32, cf, cb = pf.astype(np.float32), pb.astype(np.float32), pack(Cf), pack(Cb)
+        assert lib.emu_combine5(0, C.c_float(R), p(pf32), p(cf), p(pb32), p(cb), p(ps), p(Cs)) == 1
+        sig = np.sqrt(np.diag(Cs_ref))
+        assert np.abs((ps - ps_ref) / sig)[2:].max() < 2e-2, trial
+        assert abs(np.hypot(ps[0], ps[1]) - R) < 1e-5
+        diag = Cs[[0, 2, 5, 9, 14, 20]]
+        ref_diag = np.diag(Cs_ref)
+        assert np.all(np.abs(diag[2:] - ref_diag[2:]) < 5e-3 * ref_diag[2:]), trial
