@@ -172,7 +172,7 @@ def oracle_rate(batch, target_s: float):
     """Candidate-layer updates/s of the oracle on a sample of seeds of `batch`,
     sized to take about target_s seconds on one host core."""
     import oracle as O
-    geo = O.geometry_for(batch)
+    geo = O.geometry_as_loaded(batch)
     xyz = batch.xyz.astype(np.float64)
     rng = np.random.default_rng(7)
     order = rng.permutation(batch.n_seeds)

@@ -73,7 +73,7 @@ def _load():
                                                    d, i32, u32]
             lib.or_fit_backward.restype = C.c_int
             lib.or_fit_smooth.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, C.c_int64, d, d, C.c_double, d, d,
-                                                 d, i32, u32]
+                                                 d, i32, u32, d]
             lib.or_fit_smooth.restype = C.c_int
             lib.or_find.argtypes = geom + [d, C.c_int64, i32, i32, C.c_int, i32, i32, C.c_int64, i64, C.c_int64,
                                            C.c_int, C.c_double, C.c_int, d, d, d, i32, i32, C.c_int, u32, i64, d,
@@ -276,22 +276,25 @@ def fit_backward(geo: Geometry, xyz, hit_layer, hit_idx, last_par, last_cov21, i
 def fit_smooth(geo: Geometry, xyz, hit_layer, hit_idx, seed_par=None, seed_cov21=None, inflate=100.0):
     """Smoothed state at every hit of fixed hit lists (two filters): par
     [max_hits, 6, n], cov [max_hits, 21, n] per row of hit_idx (NaN where none),
-    and the forward fit's chi2, ndf, status."""
+    the forward fit's chi2, ndf, status, and per track `shrink`, the largest
+    ratio of a predicted residual variance to the hit's variance met by the
+    backward filter (an update there shrinks its prior by about that factor)."""
     lib = _load()
     xyz = _f64(xyz)
     hl = np.ascontiguousarray(hit_layer, dtype=np.int32)
     hi = np.ascontiguousarray(hit_idx, dtype=np.int32)
     mh, n = hi.shape
     par, cov = np.zeros((mh, 6, n)), np.zeros((mh, 21, n))
-    chi2, ndf, st = np.zeros(n), np.zeros(n, np.int32), np.zeros(n, np.uint32)
+    chi2, ndf, st, shrink = np.zeros(n), np.zeros(n, np.int32), np.zeros(n, np.uint32), np.zeros(n)
     sp = None if seed_par is None else _f64(seed_par)
     sc = None if seed_cov21 is None else _f64(seed_cov21)
     rc = lib.or_fit_smooth(*geo.args(), _p(xyz, C.c_double), xyz.shape[1], _p(hl, C.c_int32), _p(hi, C.c_int32), mh,
                            n, _p(sp, C.c_double), _p(sc, C.c_double), float(inflate), _p(par, C.c_double),
-                           _p(cov, C.c_double), _p(chi2, C.c_double), _p(ndf, C.c_int32), _p(st, C.c_uint32))
+                           _p(cov, C.c_double), _p(chi2, C.c_double), _p(ndf, C.c_int32), _p(st, C.c_uint32),
+                           _p(shrink, C.c_double))
     if rc < 0:
         raise ValueError("bad arguments")
-    return dict(par=par, cov=cov, chi2=chi2, ndf=ndf, status=st)
+    return dict(par=par, cov=cov, chi2=chi2, ndf=ndf, status=st, shrink=shrink)
 
 
 def find(geo: Geometry, xyz, hit_layer, event_offsets, seed_hits, seed_event, n_best=10, chi2_cut=30.0,
@@ -338,8 +341,43 @@ def find(geo: Geometry, xyz, hit_layer, event_offsets, seed_hits, seed_event, n_
 
 
 def geometry_for(batch, region_edges=None, region_masks=None) -> Geometry:
+    """The batch's geometry with its values as the generator defines them
+    (e.g. cylinder radii 4 + 96 i / 9 cm exactly)."""
     return Geometry(batch.layers, batch.bz, region_edges, region_masks, batch.meta.get("field_alpha"),
                     batch.meta.get("material_map"))
+
+
+def _f32(v):
+    return float(np.float32(v))
+
+
+def geometry_as_loaded(batch, region_edges=None, region_masks=None, field_alpha="batch") -> Geometry:
+    """The batch's geometry with every real-valued entry rounded to FP32, the
+    precision in which the library's geometry calls take it (layer radii and
+    z positions, extents, resolutions, material, field strength and fall-off,
+    region edges, material-map cells and bounds).  A comparison of the library
+    with the oracle gives both the same problem: the radius of a cylinder at
+    4 + 96 i / 9 cm moves by up to 1.9e-6 cm when rounded to FP32, which shifts
+    the crossing point of a track and its residuals by about 1e-3 of a 20 um
+    resolution.  field_alpha: the batch's own field unless given (None = uniform)."""
+    layers = []
+    for d in batch.layers:
+        e = dict(d)
+        for k in ("r_or_z", "lo", "hi", "sigma_u", "sigma_v", "x0", "eloss"):
+            if k in e:
+                e[k] = _f32(e[k])
+        layers.append(e)
+    alpha = batch.meta.get("field_alpha") if isinstance(field_alpha, str) else field_alpha
+    mm = batch.meta.get("material_map")
+    if mm is not None:
+        mm = dict(mm)
+        for k in ("r_max", "z_min", "z_max"):
+            mm[k] = _f32(mm[k])
+        mm["x0"] = np.asarray(mm["x0"], dtype=np.float32).astype(np.float64)
+        if mm.get("eloss") is not None:
+            mm["eloss"] = np.asarray(mm["eloss"], dtype=np.float32).astype(np.float64)
+    edges = None if region_edges is None else [_f32(x) for x in region_edges]
+    return Geometry(layers, _f32(batch.bz), edges, region_masks, None if alpha is None else _f32(alpha), mm)
 
 
 def field(geo: Geometry, r):

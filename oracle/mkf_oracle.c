@@ -1073,7 +1073,8 @@ static int combine(const geom_t *g, int l, const double pf[6], const double Cf[3
  * chi2, ndf and status (with the backward pass's status bits added). */
 int or_fit_smooth(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *hit_layer, const int32_t *hit_idx,
                   int max_hits, int64_t n, const double *seed_par, const double *seed_cov, double inflate,
-                  double *sm_par, double *sm_cov, double *out_chi2, int32_t *out_ndf, uint32_t *out_status) {
+                  double *sm_par, double *sm_cov, double *out_chi2, int32_t *out_ndf, uint32_t *out_status,
+                  double *out_shrink) {
     geom_t g;
     if (geom_init(&g, GEOM_PASS)) return -1;
     if (!(inflate >= 1.0) || max_hits > OR_MAXL + 8) return -1;
@@ -1110,6 +1111,10 @@ int or_fit_smooth(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *h
             }
         }
         int last = -1;
+        /* conditioning log: the largest ratio of a predicted residual variance
+         * (H C H^T) to the hit's own variance over the backward filter's
+         * updates -- the factor by which an update shrinks the prior */
+        double shrink = 0.0;
         if (!(st & OR_ST_BADSEED)) {
             for (int k = 0; k < nh; ++k) {
                 int hid = idx[k], l = hit_layer[hid];
@@ -1172,6 +1177,8 @@ int or_fit_smooth(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *h
                 double H[12], r[2], S[4], Si[4], HC[12];
                 residual(&g, l, p, X[hid], Y[hid], Z[hid], r, H);
                 if (residual_cov(&g, l, C, H, S, Si, HC)) {
+                    const double vu = g.su[l] * g.su[l], vv = g.sv[l] * g.sv[l];
+                    shrink = fmax(shrink, fmax((S[0] - vu) / vu, (S[3] - vv) / vv));
                     kf_update(HC, Si, r, p, C);
                 } else {
                     st |= OR_ST_BADS;
@@ -1184,6 +1191,7 @@ int or_fit_smooth(GEOM_ARGS, const double *xyz, int64_t n_hits, const int32_t *h
         out_chi2[t] = chi2;
         out_ndf[t] = 2 * used - (g.bz != 0.0 ? 5 : 4);
         out_status[t] = st;
+        if (out_shrink) out_shrink[t] = shrink;
     }
     return 0;
 }

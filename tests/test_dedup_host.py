@@ -80,7 +80,7 @@ def test_kernels_match_oracle_random(lib, seed):
 
 def test_kernels_match_oracle_overlap_events(lib):
     b = make_batch("find20", [5], n_tracks=250, overlap=0.15)
-    geo = O.geometry_for(b)
+    geo = O.geometry_as_loaded(b)
     par = O.fit(geo, b.xyz.astype(np.float64), b.layer, b.seed_hits)["par"].astype(np.float32)
     keep = _seeds(lib, b.seed_hits, b.n_hits, par, (0.5, 0.02, 0.02))
     assert (keep.astype(bool) == D.clean_seeds(b.seed_hits, b.n_hits, par)).all()

@@ -86,7 +86,7 @@ def run_emu(so, cfg, event, n_tracks, n_noise, n_best, step1, mlp_bf16=None, tau
 ])
 def test_emulated_finder_matches_oracle(emu_so, cfg, event, tracks, noise, n_best):
     b = make_batch(cfg, [event], n_tracks=tracks, n_noise=noise)
-    ref = O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+    ref = O.find(O.geometry_as_loaded(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=n_best, max_out=len(b.layers) + 3)
     out = run_emu(emu_so, cfg, event, tracks, noise, n_best, 1)
     compare(out, ref)
@@ -101,7 +101,7 @@ def test_emulated_finder_with_material_matches_oracle(emu_so, n_best, eloss):
     for d in b.layers:
         d["x0"] = 0.02
         d["eloss"] = eloss
-    ref = O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+    ref = O.find(O.geometry_as_loaded(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=n_best, max_out=len(b.layers) + 3)
     out = run_emu(emu_so, "find20", 45, 150, None, n_best, 1, material=0.02, eloss=eloss)
     compare(out, ref)
@@ -116,7 +116,7 @@ def test_emulated_finder_in_parameterised_field_matches_oracle(emu_so, cfg, gen_
     alpha = 1e-5 if gen_field else 1e-6  # find20's disks reach z = 270 cm
     b = (make_batch(cfg, [46], n_tracks=120, field_alpha=alpha) if gen_field
          else make_batch(cfg, [46], n_tracks=120))
-    geo = O.Geometry(b.layers, b.bz, field_alpha=alpha)
+    geo = O.geometry_as_loaded(b, field_alpha=alpha)
     ref = O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=n_best, max_out=len(b.layers) + 3)
     out = run_emu(emu_so, cfg, 46, 120, None, n_best, 1, alpha=alpha, gen_field=gen_field)
@@ -130,7 +130,7 @@ def test_emulated_finder_with_material_map_matches_oracle(emu_so, n_best):
     from tests.test_oracle_material_map import _graded_map
     mm = _graded_map()
     b = make_batch("fit10", [47], n_tracks=150, material_map=mm)
-    ref = O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+    ref = O.find(O.geometry_as_loaded(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=n_best, max_out=len(b.layers) + 3)
     out = run_emu(emu_so, "fit10", 47, 150, None, n_best, 1, mmap=mm)
     compare(out, ref)
@@ -162,7 +162,7 @@ def test_emulated_learned_pruning_matches_oracle(emu_so, tau):
     wb = (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     b = make_batch("dense45", [44], n_tracks=100, n_noise=200000)
     out = run_emu(emu_so, "dense45", 44, 100, 200000, 10, 1, mlp_bf16=bits, tau=tau)
-    geo = O.geometry_for(b)
+    geo = O.geometry_as_loaded(b)
     ref = O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=10, mlp_w=wb, mlp_tau=tau, max_out=len(b.layers) + 3)
     plain = O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,

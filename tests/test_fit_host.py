@@ -96,7 +96,7 @@ def test_fit_kernel_on_host(lib, cfg, material, eloss, alpha):
         b = make_batch(cfg, [31], n_tracks=400, field_alpha=alpha)
     else:
         b = make_batch(cfg, [31], n_tracks=400)
-    geo = O.Geometry(b.layers, b.bz, field_alpha=alpha)
+    geo = O.geometry_as_loaded(b)
     x0 = [d.get("x0", 0.0) for d in b.layers]
     el = [d.get("eloss", 0.0) for d in b.layers]
     out = _run(lib, b, b.track_hits, x0, eloss=el, alpha=alpha)
@@ -123,7 +123,7 @@ def test_fit_kernel_on_host_with_material_map(lib):
     from tests.test_oracle_material_map import _graded_map
     mm = _graded_map()
     b = make_batch("fit10", [32], n_tracks=400, material_map=mm)
-    geo = O.geometry_for(b)
+    geo = O.geometry_as_loaded(b)
     out = _run(lib, b, b.track_hits, mmap=mm)
     ref = O.fit(geo, b.xyz.astype(np.float64), b.layer, b.track_hits)
     assert (out["status"] == ref["status"]).all() and (out["ndf"] == ref["ndf"]).all()
@@ -156,7 +156,7 @@ def test_smooth_kernel_on_host(lib, cfg, material, eloss, alpha, use_map):
         b = make_batch(cfg, [33], n_tracks=300, material_map=mm)
     else:
         b = make_batch(cfg, [33], n_tracks=300)
-    geo = O.geometry_for(b)
+    geo = O.geometry_as_loaded(b)
     from paper_1811_04141_gb300 import _native as NN
     lay = b.layers
     arr = (NN.MkfLayer * len(lay))()

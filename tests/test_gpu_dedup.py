@@ -19,7 +19,7 @@ def _t(a, dt):
 @pytest.mark.parametrize("cfg,tracks", [("find20", 1500), ("dense45", 1200)])
 def test_seeds_clean_parity(cfg, tracks):
     b = make_batch(cfg, [0, 1], n_tracks=tracks, overlap=0.1)
-    geo = O.geometry_for(b)
+    geo = O.geometry_as_loaded(b)
     par = O.fit(geo, b.xyz.astype(np.float64), b.layer, b.seed_hits)["par"].astype(np.float32)
     ctx = make_ctx(b)
     for tol in ((0.15, 0.02, 0.02), (5.0, 3.0, 4.0), (0.0, 0.0, 0.0), (0.05, 0.002, 0.002)):
@@ -34,7 +34,7 @@ def test_seeds_clean_parity(cfg, tracks):
 
 def test_tracks_dedup_parity_after_oracle_finding():
     b = make_batch("find20", [3], n_tracks=400, overlap=0.15)
-    geo = O.geometry_for(b)
+    geo = O.geometry_as_loaded(b)
     r = O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event, n_best=10,
                max_out=len(b.layers) + 3)
     c2 = r["chi2"].astype(np.float32)

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _oracle(b, sel, n_best=10):
-    return O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+    return O.find(O.geometry_as_loaded(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                   n_best=n_best, seed_list=sel, max_out=len(b.layers) + 3)
 
 
