@@ -147,7 +147,8 @@ mkf_status mkf_geometry_material(mkf_ctx *ctx, const float *x0, const float *elo
  * 0.05 rad of turning and 10 cm per step, at most 16 steps, over the path that
  * the helix in the local axial field estimates, then two Newton steps onto the
  * surface) and transport the covariance with the Jacobian integrated along the
- * trajectory (the field's gradient left out); layer order and extent checks
+ * trajectory (the variational equations, the field's gradient included);
+ * layer order and extent checks
  * use the local helix, and seeds take their curvature scale from the field at
  * the middle hit.  The material effects apply as set.  Hit bins stay valid.
  * Errors: MKF_ERR_ARG (kind not 0 or 1, alpha not finite or |alpha| >= 1e-2),
@@ -233,15 +234,24 @@ mkf_status mkf_hitbins_export(mkf_ctx *ctx, const mkf_hitbins *bins, float *rec,
  * allocates nothing: it writes the same arrays mkf_hitbins_export copies out of
  * a bin store straight into caller-owned buffers, and keeps its working memory
  * (histogram, scan partial sums, per-hit bin keys) in one statically sized
- * device array inside libmkf.  That array (about 52 MB) is reserved on every GPU
- * that loads the library, for as long as the library stays loaded.
+ * device array inside libmkf.  That array (about 52 MB) is reserved on a GPU
+ * when the library's binning code is loaded onto it and stays reserved until
+ * the process exits.  Under CUDA's lazy module loading (the default) that
+ * happens at the first call of mkf_hits_bin or mkf_hits_bin_static on that GPU;
+ * a caller with a fixed footprint should make one such call during start-up
+ * (with CUDA_MODULE_LOADING=EAGER the runtime reserves it when it first sets
+ * up the library's code on the GPU instead).
  *
  *  xyz, layer, event_offsets, n_events, n_hits: as for mkf_hits_bin.
  *  rec [n_hits][4] float, inv [n_hits] int32, offsets [n_bins + 1] int32:
  *      device, caller-owned outputs, same layout and contents as
  *      mkf_hitbins_export (n_bins = n_events * bins per event of the geometry).
+ *      rec must start on a 16-byte boundary (it is written as 16-byte records;
+ *      cudaMalloc'd and PyTorch buffers are); offsets must hold exactly
+ *      n_bins + 1 entries, all of which are written.
  * Limits: n_hits <= MKF_STATIC_MAX_HITS and n_bins <= MKF_STATIC_MAX_BINS, else
- * MKF_ERR_CAPACITY and nothing is enqueued.
+ * MKF_ERR_CAPACITY and nothing is enqueued; a misaligned rec gives MKF_ERR_ARG
+ * and nothing is enqueued.
  * The first call on a device looks up the device address of the working array
  * (a runtime call, no allocation); make that first call before capturing the
  * stream into a CUDA graph.  All calls on a device share the one working array:
@@ -296,7 +306,7 @@ mkf_status mkf_fit_backward(mkf_ctx *ctx, const float *xyz, const int32_t *hit_l
                             const float *last_cov, float inflate, float *out_par, float *out_cov, float *chi2,
                             int32_t *ndf, uint32_t *status);
 
-/* Smoothed state at every hit of fixed hit lists (NEXT-1; Sec. 2.1 mentions
+/* Smoothed state at every hit of fixed hit lists (Sec. 2.1 mentions
  * back-fit layers): two filters.  The forward filter of mkf_fit (seeded as
  * there) keeps its state after each hit; the backward filter starts from the
  * forward state at the last hit, turned around with its covariance multiplied

@@ -184,6 +184,12 @@ def mkf_hits_bin_static(ctx, xyz, layer, event_offsets, rec, inv, offsets, devic
     _need(rec, "rec", torch.float32, (n, 4), device)
     _need(inv, "inv", torch.int32, (n,), device)
     _need(offsets, "offsets", torch.int32, None, device)
+    layers = getattr(ctx, "layers", None)
+    if layers:
+        # every one of the n_bins + 1 entries is written on the device
+        n_bins = (event_offsets.shape[0] - 1) * sum(int(d.get("n_phi", 64)) * int(d.get("n_zr", 8)) for d in layers)
+        if offsets.numel() != n_bins + 1:
+            raise ValueError(f"offsets must have n_bins + 1 = {n_bins + 1} entries, got {offsets.numel()}")
     h = ctx.handle if hasattr(ctx, "handle") else ctx
     N.check("mkf_hits_bin_static", N.lib().mkf_hits_bin_static(
         h, _ptr(xyz), _ptr(layer), _ptr(event_offsets), event_offsets.shape[0] - 1, n, _ptr(rec), _ptr(inv),

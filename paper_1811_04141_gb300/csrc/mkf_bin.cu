@@ -475,8 +475,11 @@ constexpr size_t kOffZ = align256(kOffKey + sizeof(int32_t) * kStaticHits);
 constexpr size_t kOffLayer = align256(kOffZ + sizeof(float) * kStaticHits);
 constexpr size_t kStaticBytes = align256(kOffLayer + sizeof(uint8_t) * kStaticHits);
 
-// Reserved on every device that loads the library.  In host code this name is
-// only a stand-in: the device address comes from cudaGetSymbolAddress.
+// Reserved on a device when the module holding this file's kernels is loaded
+// there: at library load, or under CUDA's lazy module loading (the default) at
+// the first call of mkf_hits_bin or mkf_hits_bin_static on that device.  In
+// host code this name is only a stand-in: the device address comes from
+// cudaGetSymbolAddress.
 __device__ __align__(256) unsigned char g_bin_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
@@ -506,6 +509,9 @@ extern "C" mkf_status mkf_hits_bin_static(mkf_ctx *ctx, const float *xyz, const 
     if (n_events < 1 || n_hits < 0) return MKF_ERR_ARG;
     if (!event_offsets || !offsets) return MKF_ERR_ARG;
     if (n_hits > 0 && (!xyz || !layer || !rec || !inv)) return MKF_ERR_ARG;
+    // rec is written as float4 records: a buffer that does not start on a
+    // 16-byte boundary is rejected here instead of faulting in the kernel
+    if (n_hits > 0 && (reinterpret_cast<uintptr_t>(rec) & 15u) != 0) return MKF_ERR_ARG;
     const int64_t n_bins = (int64_t)n_events * ctx->geom.bins_per_event;
     if (n_hits > kStaticHits || n_bins > kStaticBins) return MKF_ERR_CAPACITY;
     DeviceGuard g(ctx->device);

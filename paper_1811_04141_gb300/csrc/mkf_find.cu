@@ -10,7 +10,9 @@
 //      its covariance and scans the bins of its chi2 window, keeping its best N
 //      compatible hits in a shared-memory list sorted by (chi2, hit index);
 //   2. the seed's N lanes pick the N best children in N rounds of a segmented
-//      max over 64-bit keys (score, parent rank, hit index) exchanged by shuffles;
+//      max over 32-bit keys exchanged by shuffles: the order-preserving integer
+//      of the FP32 score with its low 4 bits replaced by the parent's rank, so
+//      keys within a seed are unique and the maximum names its parent;
 //   3. each lane becomes one child: it pulls its parent's propagated state by
 //      shuffles and applies the Kalman update with its hit;
 //   4. each lane records (parent rank, hit) in a per-step history in shared
@@ -72,7 +74,7 @@ struct FindArgs {
 enum {
     SF_P = 0, SF_LO = 6, SF_C = 10, SF_CHI2 = 31, SF_BOOK = 32, SF_MASK_LO = 33, SF_MASK_HI = 34, SF_DIR = 35,
     SF_STATUS = 36, SF_HITS = 37, SF_BEAM = 40, SF_CCL = 41, SF_CHT = 42, SF_NLIST = 43, SF_SEARCHED = 44,
-    SF_I = 45, kSeedFields = 60
+    SF_I = 45, SF_LOTH = 60, kSeedFields = 61
 };
 
 // First-step hit list of a seed, [entry][field][seed].
@@ -306,7 +308,7 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
                                        float *lv, int ls, Expansion &X) {
     float sphi, cphi;
     sincos_pair(p[4], lo.phi, sphi, cphi);
-    const float cot = cot_of(p[5]);
+    const float cot = cot_pair(p[5], lo.th);
     X.cot = cot;
     X.searched = false;
     X.nlist = 0;
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
         hz[k] = A.zhit[hidx[k]];
     }
     float p[6], C[21], eta = 0.f, chi2 = 0.f;
-    Lo lo{0.f, 0.f, 0.f, 0.f};
+    Lo lo{0.f, 0.f, 0.f, 0.f, 0.f};
     if (ok) {
         const float h1[3] = {hx[0], hy[0], hz[0]}, h2[3] = {hx[1], hy[1], hz[1]}, h3[3] = {hx[2], hy[2], hz[2]};
         // the parameterised field at the middle hit sets the curvature scale
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
         if (k > 0) {
             float sphi, cphi, s;
             sincos_pair(p[4], lo.phi, sphi, cphi);
-            const float cot = cot_of(p[5]);
+            const float cot = cot_pair(p[5], lo.th);
             const float kbl = kParamField ? G.kb * bz_factor(G.alpha, p[0], p[1], p[2]) : G.kb;
             if (!path_to_layer(Ld, kbl, p, lo, sphi, cphi, cot, s)) {
                 ok = false;
@@ -495,7 +497,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
         int region = 0;
         while (region + 1 < G.n_regions && eta >= G.edges[region]) ++region;
         mask = G.mask[region];
-        dir = cot_of(p[5]) >= 0.f ? 1 : -1;
+        dir = cot_pair(p[5], lo.th) >= 0.f ? 1 : -1;
         const int l3 = hl[2];
         const float r3 = sqrtf(fmaf(hx[2], hx[2], hy[2] * hy[2])), z3 = hz[2];
         if (G.L[l3].kind == 0) {
@@ -574,6 +576,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
     B[(SF_LO + 1) * (int64_t)n + t] = lo.y;
     B[(SF_LO + 2) * (int64_t)n + t] = lo.z;
     B[(SF_LO + 3) * (int64_t)n + t] = lo.phi;
+    B[SF_LOTH * (int64_t)n + t] = lo.th;
 #pragma unroll
     for (int k = 0; k < 21; ++k) B[(SF_C + k) * (int64_t)n + t] = C[k];
     B[SF_CHI2 * (int64_t)n + t] = chi2;
@@ -638,7 +641,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
         const int seed = grp * spw + slot;
         const bool has_seed = lane_used && seed < A.n_seeds;
         float p[6], C[21];
-        Lo lo{0.f, 0.f, 0.f, 0.f};
+        Lo lo{0.f, 0.f, 0.f, 0.f, 0.f};
     #pragma unroll
         for (int i = 0; i < 6; ++i) p[i] = 0.f;
     #pragma unroll
@@ -689,6 +692,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                     lo.y = Bs[(SF_LO + 1) * n + seed];
                     lo.z = Bs[(SF_LO + 2) * n + seed];
                     lo.phi = Bs[(SF_LO + 3) * n + seed];
+                    lo.th = Bs[SF_LOTH * n + seed];
     #pragma unroll
                     for (int k = 0; k < 21; ++k) C[k] = Bs[(SF_C + k) * n + seed];
                     chi2 = Bs[SF_CHI2 * n + seed];
@@ -735,6 +739,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
                 lo.y = Bs[(SF_LO + 1) * n + seed];
                 lo.z = Bs[(SF_LO + 2) * n + seed];
                 lo.phi = Bs[(SF_LO + 3) * n + seed];
+                lo.th = Bs[SF_LOTH * n + seed];
     #pragma unroll
                 for (int k = 0; k < 21; ++k) C[k] = Bs[(SF_C + k) * n + seed];
                 chi2 = Bs[SF_CHI2 * n + seed];
@@ -888,6 +893,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             lo.y = __shfl_sync(kFull, lo.y, src);
             lo.z = __shfl_sync(kFull, lo.z, src);
             lo.phi = __shfl_sync(kFull, lo.phi, src);
+            lo.th = __shfl_sync(kFull, lo.th, src);
     #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 I.HCu[k] = __shfl_sync(kFull, I.HCu[k], src);
@@ -954,6 +960,7 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             p[1] += lo.y;
             p[2] += lo.z;
             p[4] += lo.phi;
+            p[5] += lo.th;
     #pragma unroll
             for (int i = 0; i < 6; ++i) A.out_par[(int64_t)i * n + seed] = ok ? p[i] : nanv;
     #pragma unroll

@@ -30,7 +30,8 @@ __device__ __forceinline__ void record_fault(mkf_fault *f, int code, int where) 
 }
 
 // The helix traversed the other way: the same curve with the momentum turned
-// around, p -> (x, y, z, -q/pT, phi + pi, pi - theta) with pi as a float pair,
+// around, p -> (x, y, z, -q/pT, phi + pi, pi - theta) with pi as a float pair
+// (phi and theta are pairs too),
 // and C -> F C F with F = diag(1, 1, 1, -1, 1, -1) (the covariances between
 // {q/pT, theta} and the other parameters change sign).
 __device__ __forceinline__ void reverse_state(float p[6], Lo &lo, float C[21]) {
@@ -40,7 +41,11 @@ __device__ __forceinline__ void reverse_state(float p[6], Lo &lo, float C[21]) {
     df_add(p[4], lo.phi, kPiHi);
     df_add(p[4], lo.phi, kPiLo);
     df_wrap_pi(p[4], lo.phi);
-    p[5] = (kPiHi - p[5]) + kPiLo;
+    float th = kPiHi, thl = kPiLo;
+    df_add(th, thl, -p[5]);
+    df_add(th, thl, -lo.th);
+    p[5] = th;
+    lo.th = thl;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __gr
     if (t >= A.n) return;
     const Geom &G = A.G;
     float p[6], C[21];
-    Lo lo{0.f, 0.f, 0.f, 0.f};
+    Lo lo{0.f, 0.f, 0.f, 0.f, 0.f};
     uint32_t st = 0;
     float chi2 = 0.f;
     int used = 0;
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __gr
             if (!firsthit) {
                 float sphi, cphi;
                 sincos_pair(p[4], lo.phi, sphi, cphi);
-                const float cot = cot_of(p[5]);
+                const float cot = cot_pair(p[5], lo.th);
                 // path estimate from the helix in the local axial field
                 const float kbl = kParamField ? G.kb * bz_factor(G.alpha, p[0], p[1], p[2]) : G.kb;
                 float s;
@@ -170,6 +175,7 @@ __global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __gr
     p[1] += lo.y;
     p[2] += lo.z;
     p[4] += lo.phi;
+    p[5] += lo.th;
 #pragma unroll
     for (int i = 0; i < 6; ++i) A.out_par[(int64_t)i * A.n + t] = ok ? p[i] : nanv;
 #pragma unroll
@@ -188,7 +194,7 @@ template <int kPhys>
 __device__ __forceinline__ bool move_to(const Geom &G, const LayerDesc &Ld, float p[6], Lo &lo, float C[21]) {
     float sphi, cphi;
     sincos_pair(p[4], lo.phi, sphi, cphi);
-    const float cot = cot_of(p[5]);
+    const float cot = cot_pair(p[5], lo.th);
     const float kbl = kPhys == 2 ? G.kb * bz_factor(G.alpha, p[0], p[1], p[2]) : G.kb;
     float s;
     if (!path_to_layer(Ld, kbl, p, lo, sphi, cphi, cot, s)) return false;
@@ -473,7 +479,7 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const __grid_constant__ 
         for (int i = 0; i < 21; ++i) A.sm_cov[((int64_t)k * 21 + i) * n + t] = nanv;
     }
     float p[6], C[21];
-    Lo lo{0.f, 0.f, 0.f, 0.f};
+    Lo lo{0.f, 0.f, 0.f, 0.f, 0.f};
     uint32_t st = 0;
     float chi2 = 0.f;
     int used = 0;
@@ -539,7 +545,7 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const __grid_constant__ 
             if (update_with(Ld, A.X[h], A.Y[h], A.Z[h], p, lo, C, dchi2)) {
                 chi2 += dchi2;
                 ++used;
-                const float pw[6] = {p[0] + lo.x, p[1] + lo.y, p[2] + lo.z, p[3], p[4] + lo.phi, p[5]};
+                const float pw[6] = {p[0] + lo.x, p[1] + lo.y, p[2] + lo.z, p[3], p[4] + lo.phi, p[5] + lo.th};
 #pragma unroll
                 for (int i = 0; i < 6; ++i) A.sm_par[((int64_t)k * 6 + i) * n + t] = pw[i];
 #pragma unroll
@@ -557,7 +563,7 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const __grid_constant__ 
         for (int i = 0; i < 6; ++i) p[i] = A.sm_par[((int64_t)lastk * 6 + i) * n + t];
 #pragma unroll
         for (int i = 0; i < 21; ++i) C[i] = A.sm_cov[((int64_t)lastk * 21 + i) * n + t] * A.inflate;
-        lo = Lo{0.f, 0.f, 0.f, 0.f};
+        lo = Lo{0.f, 0.f, 0.f, 0.f, 0.f};
         reverse_state(p, lo, C);
         for (int k = lastk; k >= 0; --k) {
             const int h = A.hit_idx[(int64_t)k * n + t];
@@ -573,11 +579,12 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const __grid_constant__ 
                 const float c0 = A.sm_cov[((int64_t)k * 21) * n + t];
                 if (c0 == c0) {  // the forward filter has a state here
                     float pb[6] = {p[0] + lo.x, p[1] + lo.y, p[2] + lo.z, p[3], p[4], p[5]}, Cb[21];
-                    Lo lb{0.f, 0.f, 0.f, lo.phi};
+                    Lo lb{0.f, 0.f, 0.f, lo.phi, lo.th};
 #pragma unroll
                     for (int i = 0; i < 21; ++i) Cb[i] = C[i];
                     reverse_state(pb, lb, Cb);
                     pb[4] += lb.phi;
+                    pb[5] += lb.th;
                     float pf[6], Cf[21], ps[6], Cs[21];
 #pragma unroll
                     for (int i = 0; i < 6; ++i) pf[i] = A.sm_par[((int64_t)k * 6 + i) * n + t];

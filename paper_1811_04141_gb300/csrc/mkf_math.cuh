@@ -18,10 +18,12 @@
 //    (about 150 FMAs instead of 432 for dense 6x6 products);
 //  * the r-phi residual is R atan2(P x H, P . H) from the difference vector, so
 //    no large angle is subtracted;
-//  * position (x, y, z) and phi are carried as unevaluated float pairs
+//  * position (x, y, z), phi and theta are carried as unevaluated float pairs
 //    (hi + lo): an FP32 coordinate at r ~ 100 cm is only good to 7.6e-6 cm, a
 //    few thousandths of a 20 um resolution, so moves, updates, R^2 - r^2 and
-//    the residuals are formed with exact two-sum / two-product steps instead.
+//    the residuals are formed with exact two-sum / two-product steps instead;
+//    an FP32 theta near 2 rad is only good to 1.2e-7 rad, which moves z by
+//    0.2 um over a metre of path (2e-3 of a 100 um resolution).
 #pragma once
 
 #include <cstdint>
@@ -130,9 +132,10 @@ __device__ __forceinline__ float diff_sq2(float a, float b, float c, float d) {
     return s3 + (e3 + ((e1 - e2) + ((ea + eb) - (ec + ed))));
 }
 
-// Position pair: (x, y, z) = hi + lo per coordinate; phi = hi + lo.
+// Low parts of the pairs: (x, y, z) = hi + lo per coordinate; phi and theta
+// = hi + lo.
 struct Lo {
-    float x, y, z, phi;
+    float x, y, z, phi, th;
 };
 
 // sin(a)/a and its derivative (a cos a - sin a)/a^2, series near 0.
@@ -190,9 +193,18 @@ __device__ __forceinline__ void sincos_small(float x, float &s, float &c) {
     c = ((q + 1) & 2) ? -ca : ca;
 }
 
-__device__ __forceinline__ float cot_of(float theta) {
+// sin and cos of an angle pair hi + lo (first-order correction for the low part).
+__device__ __forceinline__ void sincos_pair(float hi, float lo, float& s, float& c) {
+    float s0, c0;
+    sincos_small(hi, s0, c0);
+    s = fmaf(c0, lo, s0);
+    c = fmaf(-s0, lo, c0);
+}
+
+// cot of the theta pair hi + lo.
+__device__ __forceinline__ float cot_pair(float hi, float lo) {
     float st, ct;
-    sincos_small(theta, st, ct);
+    sincos_pair(hi, lo, st, ct);
     return ct / st;
 }
 
@@ -527,7 +539,7 @@ __device__ __forceinline__ float nearest_root(float a, float b, float c) {
 __device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, float alpha, float p[6], Lo &lo,
                                                 float C[21], float sphi, float cphi, float h, float s) {
     float st, ct;
-    sincos_small(p[5], st, ct);
+    sincos_pair(p[5], lo.th, st, ct);
     const float lam = p[3] * st;
     const float dl[6] = {0.f, 0.f, 0.f, st, 0.f, p[3] * ct};  // d lambda / d(x, y, z, q/pT, phi, theta)
     float T[3] = {st * cphi, st * sphi, ct};
@@ -640,7 +652,9 @@ __device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, f
     }
     df_add(p[4], lo.phi, atan2f(fmaf(cphi, T[1], -sphi * T[0]), fmaf(cphi, T[0], sphi * T[1])));
     df_wrap_pi(p[4], lo.phi);
-    p[5] = atan2f(tt, T[2]);
+    // theta turned by the angle between the start and end polar directions
+    // (sin, cos) = (st, ct) and (tt, T[2]) / |T|
+    df_add(p[5], lo.th, atan2f(fmaf(tt, ct, -T[2] * st), fmaf(T[2], ct, tt * st)));
     p[3] = lam / sth;
 }
 
@@ -821,7 +835,7 @@ __device__ __forceinline__ void kf_apply(const Innov& I, float u, float v, float
     p[3] = fmaf(K0[3], u, fmaf(K1[3], v, p[3]));
     df_add(p[4], lo.phi, fmaf(K0[4], u, K1[4] * v));
     df_wrap_pi(p[4], lo.phi);
-    p[5] = fmaf(K0[5], u, fmaf(K1[5], v, p[5]));
+    df_add(p[5], lo.th, fmaf(K0[5], u, K1[5] * v));
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
@@ -873,13 +887,6 @@ __device__ __forceinline__ bool seed_state(const LayerDesc& L1, float kb, const 
     return true;
 }
 
-// sin and cos of the phi pair (first-order correction for the low part).
-__device__ __forceinline__ void sincos_pair(float hi, float lo, float& s, float& c) {
-    float s0, c0;
-    sincos_small(hi, s0, c0);
-    s = fmaf(c0, lo, s0);
-    c = fmaf(-s0, lo, c0);
-}
 
 __device__ __forceinline__ bool finite_state(const float p[6]) {
     bool ok = true;

@@ -14,16 +14,17 @@ PAR_FLOOR = np.array([1e-4, 1e-4, 1e-4, 1e-6, 1e-5, 1e-5])
 # a few metres) reaches microns while the state is known only to millimetres.
 # At a measured layer sigma is tens of microns, so the floors still decide.
 PAR_SIGMA_FRAC = 1e-2
-# chi2: relative 1e-3 of max(chi2, ndf) on >= 98 % of tracks and 3e-3 on all.
+# chi2, per track: |chi2_gpu - chi2_oracle| <= 2e-3 max(chi2, ndf).
 # The FP32 rounding of a residual is a fixed fraction of the hit resolution, so
 # its effect on chi2 scales with the number of measurements, not with chi2 itself
-# (which can be ~0 by chance).  The FP64 oracle with only its state rounded to
-# FP32 after every step already differs by up to 0.9e-3 max(chi2, ndf), and a
-# disk crossing's path (Z - z) / cot(theta) carries the ~1e-7 relative error of
-# an FP32 sine/cosine, a few 1e-6 cm: a few 1e-3 of a 20 um resolution.
+# (which can be ~0 by chance).  The kernels compiled in FP64 agree with the
+# oracle to 1e-7 of this bar, so what remains is FP32 rounding spread over the
+# whole filter (propagation, gain, covariance update); it is largest on forward
+# tracks through five disks, where the covariance is most strongly correlated:
+# up to 1.5e-3 max(chi2, ndf) over ~2e4 tracks of the parity cases (98 % of
+# every case below 0.72e-3).
 CHI2_REL = 1e-3
-CHI2_QUANTILE = 0.98
-CHI2_MAX = 3.0  # in units of CHI2_REL
+CHI2_MAX = 2.0  # per track, in units of CHI2_REL
 
 
 def wrap(a):
@@ -48,10 +49,9 @@ def chi2_errors(gpu, ref, ndf):
 
 
 def chi2_ok(gpu, ref, ndf) -> bool:
+    """Every track within CHI2_MAX * CHI2_REL * max(chi2, ndf, 1)."""
     c = chi2_errors(gpu, ref, ndf)
-    if c.size == 0:
-        return True
-    return bool(np.quantile(c, CHI2_QUANTILE) <= 1.0 and c.max() <= CHI2_MAX)
+    return bool(c.size == 0 or c.max() <= CHI2_MAX)
 
 
 def upload(batch, device="cuda"):
@@ -67,14 +67,14 @@ def make_ctx(batch, plans=None, edges=None):
     build.build()
     ctx = Context(0)
     # the parameterised field and the r-z material map where the batch names
-    # them (as the oracle's geometry_for reads them)
+    # them (as the oracle's geometry_as_loaded reads them)
     ctx.geometry_load(batch.layers, batch.bz, plans, edges, batch.meta.get("field_alpha"),
                       batch.meta.get("material_map"))
     return ctx
 
 
 def oracle_fit(batch, hit_idx=None):
-    geo = O.geometry_for(batch)
+    geo = O.geometry_as_loaded(batch)
     return O.fit(geo, batch.xyz.astype(np.float64), batch.layer, batch.track_hits if hit_idx is None else hit_idx)
 
 
@@ -83,9 +83,12 @@ def to_np(d):
 
 
 # near-tie thresholds on the oracle's margins (see oracle.find)
-TIE_SCORE = 5e-3   # score gap / max(1, chi2) at a keep/drop or final-order decision
-TIE_CUT = 2e-3     # |chi2 - cut| / cut of a tested hit
-TIE_GEO = 1e-4     # relative gap of a layer-order or extent decision
+TIE_SCORE = 1e-3   # score gap / max(1, chi2) at a keep/drop or final-order decision
+TIE_CUT = 1e-3     # |chi2 - cut| / cut of a tested hit
+# relative gap of a layer-order or extent decision (which of two layers a
+# candidate reaches first, or whether a crossing lies inside a layer's extent):
+# decided on FP32 path lengths and positions, good to ~1e-6 relative
+TIE_GEO = 1e-4
 
 
 def compare(out, ref, sel=None, min_same=0.999):
@@ -98,7 +101,8 @@ def compare(out, ref, sel=None, min_same=0.999):
     for k in diff:
         near = m[0, k] < TIE_SCORE or m[1, k] < TIE_CUT or m[2, k] < TIE_GEO
         assert near, (int(sel[k]), m[:, k], gh[:, k], ref["hits"][:, k])
-    n_allowed = max(1, int(np.floor((1 - min_same) * sel.size + 1e-9)))
+    # at least min_same of the tracks identical, at every sample size
+    n_allowed = int(np.floor((1 - min_same) * sel.size + 1e-9))
     assert diff.size <= n_allowed, (diff.size, sel.size)
     ok = same & (ref["status"] & O.ST_BADSEED == 0)
     assert (out["n_hits"][sel][ok] == ref["n_hits"][ok]).all()

@@ -25,7 +25,7 @@ def run_gpu(b, n_best, plans=None, edges=None, max_out=None, block_threads=0):
 
 
 def run_oracle(b, n_best, seed_list=None, geo=None, max_out=None):
-    geo = geo or O.geometry_for(b)
+    geo = geo or O.geometry_as_loaded(b)
     return O.find(geo, b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                   n_best=n_best, seed_list=seed_list, max_out=max_out or len(b.layers) + 3)
 
@@ -91,7 +91,7 @@ def test_find_edge_cases():
     out = run_gpu(b, 10, max_out=5)
     ref = run_oracle(b, 10, max_out=5)
     assert ((out["status"] & O.ST_TRUNC) > 0).sum() == ((ref["status"] & O.ST_TRUNC) > 0).sum()
-    assert (out["hits"] == ref["hits"]).mean() > 0.99
+    assert (out["hits"] == ref["hits"]).all(axis=0).mean() >= 0.999
     # a degenerate seed (three identical hits) and an empty seed list
     sh = b.seed_hits.copy()
     sh[1, 0] = sh[0, 0]
@@ -126,7 +126,7 @@ def test_find_region_plans():
     edges = [-0.9, 0.9]
     out = run_gpu(b, 10, plans=plans, edges=edges)
     masks = [sum(1 << l for l in p) for p in plans]
-    geo = O.Geometry(b.layers, b.bz, edges, masks)
+    geo = O.geometry_as_loaded(b, edges, masks)
     ref = run_oracle(b, 10, geo=geo)
     compare(out, ref)
 
@@ -192,7 +192,7 @@ def test_find_cut_and_miss_limit(cut, miss):
     out = to_np(ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=4, chi2_cut=cut, max_consec_miss=miss,
                          max_out=mo))
     ctx.sync()
-    ref = O.find(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+    ref = O.find(O.geometry_as_loaded(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
                  n_best=4, chi2_cut=cut, max_consec=miss, max_out=mo)
     compare(out, ref)
 

@@ -53,7 +53,7 @@ def test_fit_given_seed_states_and_ragged_lists():
     assert par_errors(out["par"][:, ok], ref["par"][:, ok]).max() <= 1.0
     # seeds given explicitly: the oracle's own seed state (FP32-rounded)
     import oracle as O
-    geo = O.geometry_for(b)
+    geo = O.geometry_as_loaded(b)
     sp, sc = [], []
     for t in range(b.n_seeds):
         h = [x for x in hidx[:, t] if x >= 0][:3]
@@ -75,7 +75,7 @@ def _backward_pair(b, hidx, inflate, ctx=None):
     """GPU and oracle backward fits from the same start: the oracle's forward fit
     at the last hit, rounded to FP32, given to both."""
     import oracle as O
-    geo = O.geometry_for(b)
+    geo = O.geometry_as_loaded(b)
     f = O.fit(geo, b.xyz.astype(np.float64), b.layer, hidx)
     lp = np.ascontiguousarray(f["par"], dtype=np.float32)
     lc = np.ascontiguousarray(f["cov"], dtype=np.float32)
@@ -235,9 +235,19 @@ def test_fit_smooth_parity(cfg, kw):
     d = upload(b)
     out = to_np(ctx.fit_smooth(d["xyz"], d["layer"], d["track_hits"], inflate=100.0))
     ctx.sync()
-    ref = O.fit_smooth(O.geometry_for(b), b.xyz.astype(np.float64), b.layer, b.track_hits, inflate=100.0)
-    assert (out["status"] == ref["status"]).all()
-    ok = ref["status"] == 0
+    ref = O.fit_smooth(O.geometry_as_loaded(b), b.xyz.astype(np.float64), b.layer, b.track_hits, inflate=100.0)
+    # An FP32 update cannot resolve a posterior 2^20 times narrower than its
+    # prior (fewer than 4 of the 24 bits are left): the backward filter starts
+    # from the inflated forward state, and with material (its scattering makes
+    # the angles at the last hit poorly known) a low-pT track can reach its next
+    # hit with a prior ~1e7 times the hit's variance.  Only where the oracle
+    # logged such an update may the GPU flag the non-positive-definite residual
+    # covariance it meets after it (MKF_ST_BADS); those tracks are left out below.
+    diff = out["status"] != ref["status"]
+    assert (ref["shrink"][diff] >= 2.0 ** 20).all(), ref["shrink"][diff]
+    assert ((out["status"][diff] & ~np.uint32(O.ST_BADS)) == ref["status"][diff]).all()
+    assert diff.mean() <= 0.005
+    ok = (ref["status"] == 0) & ~diff
     assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
     m = (b.track_hits >= 0) & ok[None, :]
     assert np.array_equal(np.isnan(out["par"][:, 0]) & m, np.isnan(ref["par"][:, 0]) & m)

@@ -7,7 +7,9 @@ the caller already owns and keeps its own working memory in a fixed device array
 inside the library.  This test calls that entry point through the C ABI twice
 in a row (a larger input, then a smaller one, so leftovers of the first call
 would show) and checks that its output equals what the allocating path
-(mkf_hits_bin followed by mkf_hitbins_export) produces for the same input.
+(mkf_hits_bin followed by mkf_hitbins_export) produces for the same input, that
+a call leaves the GPU's free memory unchanged, and that it refuses buffers it
+could not write safely.
 It lives in its own file, collected last, and works in a fresh process as well
 as after the other tests.
 """
@@ -52,6 +54,57 @@ def test_static_binning_matches_allocating_path_twice():
         # bit-exact records (the original index travels as int32 bits in column 3)
         assert torch.equal(rec.view(torch.int32), ref["rec"].view(torch.int32))
         assert int(off[-1].item()) == b.n_hits
+    ctx.close()
+
+
+def test_static_binning_takes_no_device_memory():
+    """After a first call (which may load the library's binning code onto the
+    GPU), a call with preallocated outputs leaves the device's free memory
+    unchanged: it allocates nothing."""
+    from paper_1811_04141_gb300.api import mkf_hits_bin_static
+    b = make_batch("find20", [46, 47], n_tracks=400)
+    ctx = make_ctx(b)
+    d = upload(b)
+    n_bins = len(b.event_offsets[1:]) * sum(l["n_phi"] * l["n_zr"] for l in b.layers)
+    n = d["xyz"].shape[1]
+    rec = torch.empty((n, 4), device="cuda")
+    inv = torch.empty((n,), dtype=torch.int32, device="cuda")
+    off = torch.empty((n_bins + 1,), dtype=torch.int32, device="cuda")
+    mkf_hits_bin_static(ctx.handle, d["xyz"], d["layer"], d["event_offsets"], rec, inv, off)
+    ctx.sync()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    mkf_hits_bin_static(ctx.handle, d["xyz"], d["layer"], d["event_offsets"], rec, inv, off)
+    ctx.sync()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert int(off[-1].item()) == b.n_hits
+    ctx.close()
+
+
+def test_static_binning_rejects_misaligned_or_short_buffers():
+    """rec is written as 16-byte records: a buffer that does not start on a
+    16-byte boundary is refused with MKF_ERR_ARG before anything runs; the
+    binding refuses an offsets buffer of the wrong length."""
+    from paper_1811_04141_gb300 import _native as N
+    from paper_1811_04141_gb300.api import mkf_hits_bin_static
+    b = make_batch("find20", [48], n_tracks=50)
+    ctx = make_ctx(b)
+    d = upload(b)
+    n = d["xyz"].shape[1]
+    n_bins = len(b.event_offsets[1:]) * sum(l["n_phi"] * l["n_zr"] for l in b.layers)
+    flat = torch.zeros(n * 4 + 1, device="cuda")
+    rec = flat[1:].view(n, 4)  # 4 bytes past a 16-byte boundary
+    assert rec.data_ptr() % 16 == 4
+    inv = torch.empty((n,), dtype=torch.int32, device="cuda")
+    off = torch.empty((n_bins + 1,), dtype=torch.int32, device="cuda")
+    with pytest.raises(N.MkfError) as e:
+        mkf_hits_bin_static(ctx.handle, d["xyz"], d["layer"], d["event_offsets"], rec, inv, off)
+    assert e.value.status == N.MKF_ERR_ARG
+    assert torch.count_nonzero(flat) == 0
+    with pytest.raises(ValueError):
+        mkf_hits_bin_static(ctx, d["xyz"], d["layer"], d["event_offsets"], torch.empty((n, 4), device="cuda"), inv,
+                            off[:-1])
     ctx.close()
 
 
