@@ -1,19 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the Kalman-filter finding step on GB300 (one JSON line on stdout).
 
-A step is one pass of the whole finding path over one batch: hit binning
-(mkf_hits_bin) and seeded N-best finding (mkf_find: seed state and seed fit,
-per-layer propagation, covariance transport, window search, chi2, N-best
-selection, Kalman updates, output).  Workload: 20 synthetic events x 2000
-tracks, 10 barrel cylinders + 2 x 5 endcap disks in 3.8 T, |eta| < 2.4, 2 %
-hit inefficiency, uniform noise at 5x each layer's signal hits, N = 10 best
-candidates kept per seed, chi2 cut 30.  Metric: KF candidate-layer updates/s
-(one unit = one candidate propagated to one layer and searched).
+A step is one pass of the whole finding path over one batch of events: hit
+binning (mkf_hits_bin) and seeded N-best finding (mkf_find: seed state and seed
+fit, per-layer propagation, covariance transport, window search, chi2, N-best
+selection, Kalman updates, output), replayed from one captured CUDA graph.
+
+Workload (the largest single-GPU configuration): 512 synthetic events of
+uneven occupancy on the dense geometry (17 barrel cylinders + 2 x 14 endcap
+disks, 3.8 T), per event floor(exp(U[ln 100, ln 20000])) tracks with pT falling
+as pT^-3 from 0.5 GeV, |eta| < 2.4, 2 % hit inefficiency, and
+floor(exp(U[ln 1e3, ln 3e5])) uniform noise hits; N = 10 best candidates kept per
+seed, chi2 cut 30; the finder's block size from the autotuner.  Metric: KF
+candidate-layer updates/s (one unit = one candidate propagated to one layer and
+searched).  Extra objects time the 20-event find20 workload, the fit of 10^6
+tracks, learned pruning, seed cleaning and duplicate removal.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank processes its own 20 events (weak scaling, no
-collective on the data path); rank 0 prints the aggregate.
+Under torchrun (N > 1) every rank processes its own 512 events (weak scaling,
+no collective on the data path); rank 0 prints the aggregate.
 """
 from __future__ import annotations
 
@@ -33,32 +39,61 @@ if ROOT not in sys.path:
 
 METRIC = "KF candidate-layer updates/s"
 UNIT = "candidate-layer updates/s"
-CONFIG = "find20"
-EVENTS = 20
 N_BEST = 10
 CHI2_CUT = 30.0
 MAX_CONSEC = 3
-WORKLOAD = ("KF track finding, 20 events x 2000 tracks: 10 barrel cylinders r=4..100 cm + 2x5 endcap disks "
-            "|z|=120..270 cm, 3.8 T, |eta|<2.4, pT 0.5-10 GeV, 2% hit inefficiency, uniform noise 5x signal "
-            "per layer; N=10 best candidates per seed, chi2 cut 30")
+C4_EVENTS = 512
+C4_FIRST_EVENT = 5000
+WORKLOAD = ("KF track finding, 512 events of uneven occupancy in one CUDA-graph replay: 17 barrel cylinders + "
+            "2x14 endcap disks, 3.8 T, per event floor(exp(U[ln 100, ln 20000])) tracks (pT^-3 from 0.5 GeV, "
+            "|eta|<2.4, 2% hit inefficiency) and floor(exp(U[ln 1e3, ln 3e5])) uniform noise hits; N=10 best "
+            "candidates per seed, chi2 cut 30, autotuned finder launch")
+FIND20 = "find20"
+FIND20_EVENTS = 20
+FIND20_WORKLOAD = ("KF track finding, 20 events x 2000 tracks: 10 barrel cylinders r=4..100 cm + 2x5 endcap disks "
+                   "|z|=120..270 cm, 3.8 T, |eta|<2.4, pT 0.5-10 GeV, 2% hit inefficiency, uniform noise 5x signal "
+                   "per layer; N=10 best candidates per seed, chi2 cut 30")
+
+
+def c4_counts(rank: int):
+    """Per-event track and noise counts of the uneven workload's 512 events (rank
+    0 draws the same counts as the tests; other ranks their own)."""
+    rng = np.random.default_rng(4_181_104 if rank == 0 else [4_181_104, rank])
+    tracks = np.floor(np.exp(rng.uniform(np.log(100), np.log(20000), C4_EVENTS))).astype(int)
+    noise = np.floor(np.exp(rng.uniform(np.log(1e3), np.log(3e5), C4_EVENTS))).astype(int)
+    return tracks, noise
+
+
+def c4_batch(rank: int, n_events: int = C4_EVENTS, select=None, workers=None):
+    """The first n_events of the uneven dense workload of `rank` (event ids
+    C4_FIRST_EVENT + rank * 512 onwards), without per-hit truth; `select`: only
+    these event positions."""
+    from synth import make_batch
+    tracks, noise = c4_counts(rank)
+    pos = np.arange(min(n_events, C4_EVENTS)) if select is None else np.asarray(select)
+    ids = [C4_FIRST_EVENT + rank * C4_EVENTS + int(i) for i in pos]
+    return make_batch("dense45", ids, n_tracks=[int(tracks[i]) for i in pos], n_noise=[int(noise[i]) for i in pos],
+                      truth=False, workers=workers or os.cpu_count() or 1)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline sample")
-    ap.add_argument("--events", type=int, default=EVENTS, help="events per GPU (profiling runs only)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target wall time of each oracle baseline sample (one core, then all cores)")
+    ap.add_argument("--events", type=int, default=C4_EVENTS, help="events per GPU (profiling runs only)")
     ap.add_argument("--n-best", type=int, default=N_BEST, help="candidates kept per seed (profiling runs only)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-pruning comparison")
-    ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-events leg")
-    ap.add_argument("--batched-events", type=int, default=512)
+    ap.add_argument("--no-find20", action="store_true", help="skip the 20-event find20 leg")
     ap.add_argument("--no-fit", action="store_true", help="skip the 10^6-track fit leg")
     ap.add_argument("--no-post", action="store_true", help="skip the seed-cleaning / duplicate-removal timing")
+    ap.add_argument("--no-peak", action="store_true", help="skip the FP32 peak probe (roofline uses the derived peak)")
+    ap.add_argument("--block-threads", type=int, default=0, help="finder block size (0: the autotuner's choice)")
     ap.add_argument("--physics", action="store_true",
                     help="also time the material and parameterised-field fits and the smoother (off by default)")
     return ap.parse_args()
@@ -168,29 +203,99 @@ class ClockSampler:
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
 
-def oracle_rate(batch, target_s: float):
-    """Candidate-layer updates/s of the oracle on a sample of seeds of `batch`,
-    sized to take about target_s seconds on one host core."""
+def _event_slice(batch, e):
+    """Hits and seeds of event e as a one-event problem (hit indices made local),
+    so that each oracle call scans only that event's hits."""
+    lo, hi = int(batch.event_offsets[e]), int(batch.event_offsets[e + 1])
+    seeds = np.nonzero(batch.seed_event == e)[0]
+    return (np.ascontiguousarray(batch.xyz[:, lo:hi], dtype=np.float64), np.ascontiguousarray(batch.layer[lo:hi]),
+            np.array([0, hi - lo], dtype=np.int32), np.ascontiguousarray(batch.seed_hits[:, seeds] - lo),
+            np.zeros(seeds.size, dtype=np.int32))
+
+
+def oracle_rate(batch, target_s: float, threads: int = 1, n_best: int = N_BEST, seed: int = 7):
+    """Candidate-layer updates/s of the FP64 oracle on a bounded sample of the
+    batch: events in a seeded random order, each event's seeds in chunks of 16,
+    the chunks spread over `threads` host threads (the oracle's C code runs
+    without the interpreter lock), submitted until about target_s of wall time
+    has passed.  Returns (rate, seeds done, events touched, wall seconds)."""
+    from concurrent.futures import ThreadPoolExecutor, wait, FIRST_COMPLETED
+
     import oracle as O
     geo = O.geometry_as_loaded(batch)
-    xyz = batch.xyz.astype(np.float64)
-    rng = np.random.default_rng(7)
-    order = rng.permutation(batch.n_seeds)
-    done, units, t_used = 0, 0, 0.0
-    n = 20
-    while t_used < target_s and done < batch.n_seeds:
-        sel = np.sort(order[done:done + n])
-        t0 = time.perf_counter()
-        r = O.find(geo, xyz, batch.layer, batch.event_offsets, batch.seed_hits, batch.seed_event, n_best=N_BEST,
-                   chi2_cut=CHI2_CUT, max_consec=MAX_CONSEC, seed_list=sel)
-        t_used += time.perf_counter() - t0
-        units += int(r["counters"][0].sum())
-        done += sel.size
-        rate = max(t_used, 1e-6) / done
-        n = int(min(max(20, (target_s - t_used) / rate), batch.n_seeds - done))
-        if n <= 0:
-            break
-    return units / t_used, done, t_used
+    order = np.random.default_rng(seed).permutation(batch.n_events)
+
+    def job(ev, sel):
+        x, l, evo, sh, se = ev
+        r = O.find(geo, x, l, evo, sh, se, n_best=n_best, chi2_cut=CHI2_CUT, max_consec=MAX_CONSEC, seed_list=sel)
+        return int(r["counters"][0].sum()), sel.size
+
+    units = seeds = events = 0
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        pending = set()
+        for e in order:
+            ev = _event_slice(batch, int(e))
+            n = ev[3].shape[1]
+            if n == 0:
+                continue
+            events += 1
+            for c in range(0, n, 16):
+                sel = np.arange(c, min(n, c + 16), dtype=np.int64)
+                while len(pending) >= 2 * threads:
+                    done, pending = wait(pending, return_when=FIRST_COMPLETED)
+                    for f in done:
+                        u, k = f.result()
+                        units, seeds = units + u, seeds + k
+                if time.perf_counter() - t0 >= target_s:
+                    break
+                pending.add(ex.submit(job, ev, sel))
+            if time.perf_counter() - t0 >= target_s:
+                break
+        for f in pending:
+            u, k = f.result()
+            units, seeds = units + u, seeds + k
+    wall = time.perf_counter() - t0
+    return units / wall, seeds, events, wall
+
+
+def cpu_baseline(batch, target_s: float):
+    """The oracle on one host core and on all of them (one thread per core)."""
+    cores = os.cpu_count() or 1
+    r1, s1, e1, w1 = oracle_rate(batch, target_s, 1)
+    rn, sn, en, wn = oracle_rate(batch, target_s, cores, seed=8)
+    return {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sn} seeds of {en} randomly chosen events of the workload (each event's seeds in chunks "
+                      f"of 16 over {cores} threads, one per host core), {wn:.1f} s wall, FP64",
+            "single_core": {"value": r1, "unit": UNIT, "cores": 1,
+                            "sample": f"{s1} seeds of {e1} randomly chosen events, {w1:.1f} s on one host core"}}
+
+
+def fp32_peak(ctx, dev, iters: int = 50000, reps: int = 5):
+    """Measured FP32 rate of the library's FMA-chain probe (TFLOP/s, median of
+    `reps` launches timed with CUDA events on the context stream) and the SM
+    clock sampled meanwhile."""
+    import torch
+
+    from paper_1811_04141_gb300.api import mkf_fp32_probe
+    stream = torch.cuda.current_stream(dev)
+    out, fl = mkf_fp32_probe(ctx, 100, device=dev)
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, fl = mkf_fp32_probe(ctx, iters, out=out, device=dev)
+        b.record(stream)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    c = clk.stop()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ts]))
+    return {"tflops": fl / (ms * 1e-3) / 1e12, "ms": round(ms, 3), "flops_per_launch": fl,
+            "kernel": "fma_chains_kernel (mkf_fp32_probe: 8 blocks x 256 threads per SM, 8 FMA chains per thread)",
+            "clocks": c}
 
 
 # ---------------------------------------------------------------------------
@@ -294,67 +399,10 @@ def learned_leg(dev, reps: int = 30):
 
 
 # ---------------------------------------------------------------------------
-# batched uneven events in one persistent launch, replayed from a CUDA graph
-# ---------------------------------------------------------------------------
-
-def batched_leg(dev, n_events: int = 512, reps: int = 10):
-    """Dense geometry, per-event track counts floor(exp(U[ln 100, ln 20000])) and
-    noise counts floor(exp(U[ln 1e3, ln 3e5])); the binning + finding step is
-    captured in a CUDA graph after choosing the finder's block size; per-event
-    latency = time from the finder's first block start until the event's last
-    seed is written (GPU global timer)."""
-    import torch
-
-    from paper_1811_04141_gb300 import Context
-    from paper_1811_04141_gb300.runtime import CapturedStep, tune_find_block
-    from synth import make_batch
-    rng = np.random.default_rng(4_181_104)
-    tracks = np.floor(np.exp(rng.uniform(np.log(100), np.log(20000), n_events))).astype(int)
-    noise = np.floor(np.exp(rng.uniform(np.log(1e3), np.log(3e5), n_events))).astype(int)
-    t0 = time.perf_counter()
-    b = make_batch("dense45", list(range(5000, 5000 + n_events)), n_tracks=list(tracks), n_noise=list(noise))
-    gen_s = time.perf_counter() - t0
-    ctx = Context(dev.index, torch.cuda.current_stream(dev))
-    ctx.geometry_load(b.layers, b.bz)
-    to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
-    xyz, layer, evo = to(b.xyz, torch.float32), to(b.layer, torch.int32), to(b.event_offsets, torch.int32)
-    sh, se = to(b.seed_hits, torch.int32), to(b.seed_event, torch.int32)
-    max_out = len(b.layers) + 3
-    bins = ctx.hits_bin(xyz, layer, evo)
-    bt, tune = tune_find_block(ctx, bins, sh, se, n_best=N_BEST, max_out=max_out)
-    et = torch.zeros(n_events + 1, dtype=torch.int64, device=dev)
-    step = CapturedStep(ctx, xyz, layer, evo, sh, se, n_best=N_BEST, max_out=max_out, block_threads=bt,
-                        event_times=et)
-    for _ in range(3):
-        step.replay()
-    torch.cuda.synchronize()
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(reps):
-        out = step.replay()
-    e.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(e) / reps
-    t = et.cpu().numpy().astype(np.int64)
-    lat_ms = (t[:n_events] - t[n_events]) / 1e6
-    cl = int(out["counters"][0].sum().item())
-    ctx.close()
-    return {"workload": f"{n_events} events, dense geometry (17 cylinders + 2x14 disks), tracks/event "
-                        "floor(exp(U[ln 100, ln 20000])), noise/event floor(exp(U[ln 1e3, ln 3e5])), N=10; "
-                        "binning + finding replayed from one CUDA graph",
-            "events": n_events, "hits": b.n_hits, "seeds": b.n_seeds, "generation_s": round(gen_s, 2),
-            "ms_per_replay": ms, "events_per_s": n_events / (ms * 1e-3),
-            "cand_layer_updates_per_s": cl / (ms * 1e-3),
-            "event_latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
-                                 "max": float(lat_ms.max())},
-            "autotune": {"block_threads": bt, "ms_by_block_threads": tune.get("ms")}}
-
-
-# ---------------------------------------------------------------------------
 # fit: 10^6 tracks along their hit lists
 # ---------------------------------------------------------------------------
 
-def fit_leg(dev, n_tracks: int = 1_000_000, reps: int = 20):
+def fit_leg(dev, peak, n_tracks: int = 1_000_000, reps: int = 20):
     """KF fit of 10^6 tracks (10 barrel cylinders, |eta| < 1, 3.8 T, seeds from the
     first three hits): track-layer updates/s and the fit kernel's FP32 roofline."""
     import torch
@@ -399,7 +447,6 @@ def fit_leg(dev, n_tracks: int = 1_000_000, reps: int = 20):
     ms_b = float(np.mean([a.elapsed_time(e) for a, e in tb]))
     layers = int((b.track_hits >= 0).sum())
     fl = flops.FLOPS_PER_FIT_LAYER * layers
-    peak = flops.fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count, 2070.0)
     ctx.close()
     roof = lambda t, k: {"bound": "alu", "achieved": fl / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": fl / (t * 1e-3) / 1e12 / peak, "kernel": k}
@@ -461,7 +508,12 @@ def physics_leg(dev, n_events: int = 5, per_event: int = 10000, reps: int = 10):
     return res
 
 
-FIND_DRAM_BYTES = None  # dram__bytes_read.sum + dram__bytes_write.sum of find_kernel on find20; None until re-measured for this kernel version
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one mkf_find call
+# (seed_kernel + find_kernel) per candidate-layer it processes, from a one-pass
+# ncu capture of the current kernels on a 48-event subset of the uneven dense
+# workload (the whole 512 events exceed the capture size rule); traffic grows
+# with the candidate-layers processed.  None: not measured for this version.
+FIND_DRAM_BYTES_PER_CAND_LAYER = None
 
 
 def _carve(arena, specs):
@@ -476,7 +528,7 @@ def _carve(arena, specs):
     return views, off
 
 
-def e2e_pipelined(ctx, batch, bins, NB, max_out, K, W, units_all, pg, dev):
+def e2e_pipelined(ctx, batch, bins, NB, max_out, K, W, units_all, pg, dev, find_kw=None):
     """Host -> device copy of the step's inputs (one pinned arena, one copy),
     binning + finding, device -> host copy of all its outputs (one arena, one
     copy); three streams, two device buffer sets, events between the stages.
@@ -521,7 +573,7 @@ def e2e_pipelined(ctx, batch, bins, NB, max_out, K, W, units_all, pg, dev):
             x = d_in[b]
             ctx.hits_bin(x["xyz"], x["layer"], x["evo"], bins)
             ctx.find(bins, x["sh"], x["se"], n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC,
-                     max_out=max_out, out=d_out[b])
+                     max_out=max_out, out=d_out[b], **(find_kw or {}))
             ev["comp"][b].record(s_comp)
         s_out.wait_event(ev["comp"][b])
         with torch.cuda.stream(s_out):
@@ -550,21 +602,74 @@ def e2e_pipelined(ctx, batch, bins, NB, max_out, K, W, units_all, pg, dev):
 # our implementation
 # ---------------------------------------------------------------------------
 
+def find20_leg(dev, peak_tflops, steps: int = 50):
+    """The 20-event find20 workload (binning + N = 10 finding, eager launches,
+    L2 flushed between steps) and best-hit finding (N = 1) on the same events."""
+    import torch
+
+    from paper_1811_04141_gb300 import Context, flops
+    from synth import make_batch
+    batch = make_batch(FIND20, list(range(FIND20_EVENTS)))
+    ctx = Context(dev.index, torch.cuda.current_stream(dev))
+    ctx.geometry_load(batch.layers, batch.bz)
+    to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    xyz, layer = to(batch.xyz, torch.float32), to(batch.layer, torch.int32)
+    evo, sh, se = to(batch.event_offsets, torch.int32), to(batch.seed_hits, torch.int32), to(batch.seed_event,
+                                                                                             torch.int32)
+    max_out = len(batch.layers) + 3
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {"workload": FIND20_WORKLOAD}
+    for nb in (N_BEST, 1):
+        bins = ctx.hits_bin(xyz, layer, evo)
+        out = ctx.find(bins, sh, se, n_best=nb, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
+        for _ in range(3):
+            ctx.hits_bin(xyz, layer, evo, bins)
+            ctx.find(bins, sh, se, n_best=nb, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=out)
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            ctx.hits_bin(xyz, layer, evo, bins)
+            ev[i][1].record(stream)
+            ctx.find(bins, sh, se, n_best=nb, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=out)
+            ev[i][2].record(stream)
+        torch.cuda.synchronize()
+        ctx.sync()
+        step_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in ev]))
+        find_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+        cl, ht, up = (int(out["counters"][i].sum().item()) for i in range(3))
+        fl = flops.find_flops(cl, ht, up)
+        res["n_best_%d" % nb] = {
+            "cand_layer_updates_per_s": cl / (step_ms * 1e-3), "step_ms": round(step_ms, 4),
+            "bin_ms": round(step_ms - find_ms, 4), "find_ms": round(find_ms, 4), "candidate_layers": cl,
+            "hits_tested": ht, "updates": up,
+            "roofline": {"bound": "alu", "achieved": fl / (find_ms * 1e-3) / 1e12, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": fl / (find_ms * 1e-3) / 1e12 / peak_tflops,
+                         "kernel": "mkf_find (seed_kernel + find_kernel)"}}
+    ctx.close()
+    return res
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
     from paper_1811_04141_gb300 import Context, build, flops
-    from synth import make_batch
+    from paper_1811_04141_gb300.runtime import CapturedStep, tune_find_block
 
     if local == 0 or world == 1:
         build.build()
+    # the workload is generated (in spawned processes) before any GPU work
+    t0 = time.perf_counter()
+    batch = c4_batch(rank, args.events)
+    gen_s = time.perf_counter() - t0
     barrier(pg)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1811_04141_gb300.shard import combine, events_for_rank
-    E, NB = args.events, args.n_best
-    events = events_for_rank(rank, world, E)
-    batch = make_batch(CONFIG, events)
+    from paper_1811_04141_gb300.shard import combine
+    NB = args.n_best
+    E = batch.n_events
     ctx = Context(local, torch.cuda.current_stream(dev))
     ctx.geometry_load(batch.layers, batch.bz)
     to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
@@ -572,189 +677,227 @@ def run_ours(args, world, rank, local, pg):
     evo, sh, se = to(batch.event_offsets, torch.int32), to(batch.seed_hits, torch.int32), to(batch.seed_event,
                                                                                              torch.int32)
     max_out = len(batch.layers) + 3
+    fkw = dict(chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
+
+    # measured FP32 peak (the roofline's denominator)
+    peak = None
+    if not args.no_peak:
+        peak = fp32_peak(ctx, dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    derived = flops.fp32_peak_tflops(sm_count, 2070.0)
+    peak_tflops = peak["tflops"] if peak else derived
+
+    # finder launch from the autotuner (cached per GPU, geometry and size)
     bins = ctx.hits_bin(xyz, layer, evo)
-    out = ctx.find(bins, sh, se, n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
-    torch.cuda.synchronize()
+    if args.block_threads:
+        bt, tune = args.block_threads, {"ms": None, "fixed": True}
+    else:
+        bt, tune = tune_find_block(ctx, bins, sh, se, n_best=NB, **fkw)
+    fkw["block_threads"] = bt
+
+    # eager launches with events between the stages: binning and mkf_find times
+    out = ctx.find(bins, sh, se, n_best=NB, **fkw)
+    stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def step():
+    for _ in range(2):
         ctx.hits_bin(xyz, layer, evo, bins)
-        ctx.find(bins, sh, se, n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=out)
-
-    for _ in range(args.warmup):
-        flush.fill_(1.0)
-        step()
+        ctx.find(bins, sh, se, n_best=NB, out=out, **fkw)
+    torch.cuda.synchronize()
+    n_eager = 5
+    eg = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_eager)]
+    for i in range(n_eager):
+        flush.fill_(float(i))
+        eg[i][0].record(stream)
+        ctx.hits_bin(xyz, layer, evo, bins)
+        eg[i][1].record(stream)
+        ctx.find(bins, sh, se, n_best=NB, out=out, **fkw)
+        eg[i][2].record(stream)
+    torch.cuda.synchronize()
     ctx.sync()
+    bin_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in eg]))
+    find_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in eg]))
     cl = int(out["counters"][0].sum().item())
     ht = int(out["counters"][1].sum().item())
     up = int(out["counters"][2].sum().item())
 
+    # the timed step: binning + finding of all events, one CUDA-graph replay
+    et = torch.zeros(E + 1, dtype=torch.int64, device=dev)
+    step = CapturedStep(ctx, xyz, layer, evo, sh, se, n_best=NB, event_times=et, **fkw)
+    gs = step.stream
+    with torch.cuda.stream(gs):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step.replay()
+    torch.cuda.synchronize()
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    lat = []
     clocks = ClockSampler(local)
     clocks.start()
     barrier(pg)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    stream = torch.cuda.current_stream(dev)
-    for i in range(K):
-        flush.fill_(float(i))
-        ev[i][0].record(stream)
-        ctx.hits_bin(xyz, layer, evo, bins)
-        ev[i][1].record(stream)
-        ctx.find(bins, sh, se, n_best=NB, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out,
-                 out=out)
-        ev[i][2].record(stream)
+    w0 = time.perf_counter()
+    with torch.cuda.stream(gs):
+        for i in range(K):
+            flush.fill_(float(i))  # inputs (~0.9 GB) exceed the L2 anyway; the flush keeps outputs out too
+            ev[i][0].record(gs)
+            o = step.replay()
+            ev[i][1].record(gs)
     torch.cuda.synchronize()
     barrier(pg)
-    wall = time.perf_counter() - t0
+    wall = time.perf_counter() - w0
     clk = clocks.stop()
     ctx.sync()
-    step_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in ev]))
-    find_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
-    bin_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    t = et.cpu().numpy().astype(np.int64)
+    lat_ms = (t[:E] - t[E]) / 1e6
+    step_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    cl_g = int(o["counters"][0].sum().item())
+    assert cl_g == cl, (cl_g, cl)  # the replay does the same work as the eager launches
     units_all, step_ms_max = combine(pg, cl, step_ms, dev)
     value = units_all / (step_ms_max * 1e-3)
 
-    # roofline of the dominant kernel (find): FP32 ALU bound
+    # roofline of the dominant launch (mkf_find: seed_kernel + find_kernel), FP32 ALU bound
     fl = flops.find_flops(cl, ht, up)
     achieved = fl / (find_ms * 1e-3) / 1e12
-    peak_mhz = 2070.0
-    peak = flops.fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count, peak_mhz)
-    # DRAM bytes per find_kernel launch on this workload (read + write), from a one-pass ncu
-    # capture of the current kernel (profiles/dram.find20_bench.md); only the bench's own
-    # workload at the default size has a measured figure
-    traffic = FIND_DRAM_BYTES if (E == EVENTS and NB == N_BEST and world >= 1) else None
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "find_kernel", "kernel_ms": round(find_ms, 4),
-                "flops_per_launch": fl, "peak_basis": f"{peak_mhz:.0f} MHz x SMs x 128 FP32 lanes x 2 (derived)"}
+    traffic = (None if FIND_DRAM_BYTES_PER_CAND_LAYER is None or NB != N_BEST
+               else int(FIND_DRAM_BYTES_PER_CAND_LAYER * cl))
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
+                "kernel": "mkf_find (seed_kernel + find_kernel)", "kernel_ms": round(find_ms, 4),
+                "flops_per_launch": fl,
+                "peak_basis": ("measured: mkf_fp32_probe (FMA chains) on this GPU, median of 5 launches"
+                               if peak else f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x 2070 MHz"),
+                "derived_peak": round(derived, 2), "fp32_probe": peak}
 
-    # best-hit finding (N = 1) on the same binned events: a separate object
-    best_hit = None
-    if rank == 0 and world == 1:
-        o1 = ctx.find(bins, sh, se, n_best=1, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
-        for _ in range(3):
-            ctx.find(bins, sh, se, n_best=1, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=o1)
-        torch.cuda.synchronize()
-        e1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
-        for a, b_ in e1:
-            flush.fill_(1.0)
-            a.record(stream)
-            ctx.find(bins, sh, se, n_best=1, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=o1)
-            b_.record(stream)
-        torch.cuda.synchronize()
-        ms1 = float(np.mean([a.elapsed_time(b_) for a, b_ in e1]))
-        cl1 = int(o1["counters"][0].sum().item())
-        best_hit = {"workload": "the same 20 events, best-hit finding (N = 1), chi2 cut 30", "find_ms": round(ms1, 4),
-                    "step_ms": round(ms1 + bin_ms, 4), "candidate_layers": cl1,
-                    "cand_layer_updates_per_s": cl1 / ((ms1 + bin_ms) * 1e-3)}
-
-    # seed cleaning (fit over each seed's three hits + duplicate test) and
-    # duplicate-track removal on the step's found tracks: a separate object
-    post = None
-    if rank == 0 and world == 1 and not args.no_post:
-        def timed(fn, reps=20):
-            for _ in range(3):
-                fn()
-            torch.cuda.synchronize()
-            e2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-            for a, b_ in e2:
-                flush.fill_(1.0)
-                a.record(stream)
-                fn()
-                b_.record(stream)
-            torch.cuda.synchronize()
-            return float(np.mean([a.elapsed_time(b_) for a, b_ in e2]))
-        sfit = ctx.fit(xyz, layer, sh)
-        keep_s = ctx.seeds_clean(sh, batch.n_hits, sfit["par"])
-        keep_t = ctx.tracks_dedup(out["hits"], batch.n_hits, out["n_hits"], out["chi2"])
-        ms_clean = timed(lambda: (ctx.fit(xyz, layer, sh, out=sfit),
-                                  ctx.seeds_clean(sh, batch.n_hits, sfit["par"], keep=keep_s)))
-        ms_dedup = timed(lambda: ctx.tracks_dedup(out["hits"], batch.n_hits, out["n_hits"], out["chi2"], keep=keep_t))
-        n_seeds = int(sh.shape[1])
-        post = {"workload": "the same 20 events: seed cleaning (fit over the 3 seed hits, then the shared-hit and "
-                            "(q/pT, eta, phi) duplicate test) and duplicate-track removal on the found tracks "
-                            "(shared hits >= half the shorter track)",
-                "seed_clean_ms": round(ms_clean, 4), "seeds_per_s": n_seeds / (ms_clean * 1e-3),
-                "seeds_removed": int((keep_s == 0).sum().item()),
-                "dedup_ms": round(ms_dedup, 4), "tracks_per_s": n_seeds / (ms_dedup * 1e-3),
-                "tracks_removed": int((keep_t == 0).sum().item())}
-
-    # end to end through the public API with host buffers: every step copies its
-    # inputs from pinned host memory and reads its tracks back; copies run on
-    # their own streams, overlapped with the previous / next step's compute
-    # (two device buffer sets), as a serving pipeline would run them
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_pipelined(ctx, batch, bins, NB, max_out, K, max(3, args.warmup), units_all, pg, dev)
+        e2e = e2e_pipelined(ctx, batch, bins, NB, max_out, K, max(3, args.warmup), units_all, pg, dev,
+                            find_kw={"block_threads": bt})
         ctx.set_stream(stream)
+    ctx.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, nseeds, secs = oracle_rate(batch, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nseeds} randomly chosen seeds of the {batch.n_seeds} in the workload (all hits of "
-                         f"their events), {secs:.1f} s on one host core, FP64"}
-
-    learned = None
-    if rank == 0 and world == 1 and not args.no_learned:
-        learned = learned_leg(dev)
-    batched = None
-    if rank == 0 and world == 1 and not args.no_batched:
-        batched = batched_leg(dev, args.batched_events)
-    fit = None
-    if rank == 0 and world == 1 and not args.no_fit:
-        fit = fit_leg(dev)
-    physics = None
-    if rank == 0 and world == 1 and args.physics:
-        physics = physics_leg(dev)
+        cpu = cpu_baseline(batch, args.cpu_seconds)
+    extras = {}
+    if rank == 0 and world == 1:
+        if not args.no_find20:
+            extras["find20"] = find20_leg(dev, peak_tflops)
+        if not args.no_fit:
+            extras["fit"] = fit_leg(dev, peak_tflops)
+        if not args.no_post:
+            extras["post"] = post_leg(dev)
+        if not args.no_learned:
+            extras["learned"] = learned_leg(dev)
+        if args.physics:
+            extras["physics"] = physics_leg(dev)
 
     launches_per_step = 6  # bin_keys, scan_tiles, scan_write, scatter, seed, find
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(step_ms_max, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if (E, NB) == (EVENTS, N_BEST) else f"{WORKLOAD} [profiling variant: "
-                                                                                 f"{E} events, N={NB}]",
-                   "events_per_gpu": E, "tracks_per_event": 2000, "n_best": NB,
-                   "chi2_cut": CHI2_CUT, "hits_per_gpu": batch.n_hits, "seeds_per_gpu": batch.n_seeds,
-                   "cand_layers_per_step_per_gpu": cl, "hits_tested_per_step_per_gpu": ht,
-                   "updates_per_step_per_gpu": up, "bin_ms": round(bin_ms, 4), "find_ms": round(find_ms, 4),
-                   "l2": "flushed between steps (256 MiB write, outside the per-step CUDA events)",
-                   "wall_s_timed_region": round(wall, 3), "parallelism": f"events sharded, {world} GPU(s)"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "learned": learned,
-        "batched": batched, "fit": fit, "best_hit": best_hit, "post": post, "physics": physics,
+        "config": {"workload": WORKLOAD if (E, NB) == (C4_EVENTS, N_BEST) else f"{WORKLOAD} [profiling variant: "
+                                                                                  f"{E} events, N={NB}]",
+                   "events_per_gpu": E, "n_best": NB, "chi2_cut": CHI2_CUT, "hits_per_gpu": batch.n_hits,
+                   "seeds_per_gpu": batch.n_seeds, "cand_layers_per_step_per_gpu": cl,
+                   "hits_tested_per_step_per_gpu": ht, "updates_per_step_per_gpu": up,
+                   "bin_ms_eager": round(bin_ms, 4), "find_ms_eager": round(find_ms, 4),
+                   "events_per_s": units_all / cl * E / (step_ms_max * 1e-3),
+                   "event_latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                                        "p99": float(np.percentile(lat_ms, 99)), "max": float(lat_ms.max()),
+                                        "basis": "GPU global timer at each event's last seed output, from the "
+                                                 "finder's first block"},
+                   "launch": "binning + finding captured in one CUDA graph, replayed per step",
+                   "autotune": {"block_threads": bt, "ms_by_block_threads": tune.get("ms")},
+                   "l2": "inputs (~0.9 GB) larger than L2, and a 256 MiB write between steps outside the events",
+                   "generation_s": round(gen_s, 1), "wall_s_timed_region": round(wall, 3),
+                   "parallelism": f"events sharded, {world} GPU(s)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches_per_step * K,
     }
+    line.update(extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def post_leg(dev):
+    """Seed cleaning (fit over each seed's three hits + duplicate test) and
+    duplicate-track removal on the find20 step's 40 k seeds and found tracks."""
+    import torch
+
+    from paper_1811_04141_gb300 import Context
+    from synth import make_batch
+    batch = make_batch(FIND20, list(range(FIND20_EVENTS)))
+    ctx = Context(dev.index, torch.cuda.current_stream(dev))
+    ctx.geometry_load(batch.layers, batch.bz)
+    to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    xyz, layer = to(batch.xyz, torch.float32), to(batch.layer, torch.int32)
+    evo, sh, se = to(batch.event_offsets, torch.int32), to(batch.seed_hits, torch.int32), to(batch.seed_event,
+                                                                                             torch.int32)
+    bins = ctx.hits_bin(xyz, layer, evo)
+    out = ctx.find(bins, sh, se, n_best=N_BEST, max_out=len(batch.layers) + 3)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b_ in e2:
+            flush.fill_(1.0)
+            a.record(stream)
+            fn()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b_) for a, b_ in e2]))
+
+    sfit = ctx.fit(xyz, layer, sh)
+    keep_s = ctx.seeds_clean(sh, batch.n_hits, sfit["par"])
+    keep_t = ctx.tracks_dedup(out["hits"], batch.n_hits, out["n_hits"], out["chi2"])
+    ms_clean = timed(lambda: (ctx.fit(xyz, layer, sh, out=sfit),
+                              ctx.seeds_clean(sh, batch.n_hits, sfit["par"], keep=keep_s)))
+    ms_dedup = timed(lambda: ctx.tracks_dedup(out["hits"], batch.n_hits, out["n_hits"], out["chi2"], keep=keep_t))
+    n_seeds = int(sh.shape[1])
+    res = {"workload": "find20 (20 events x 2000 tracks): seed cleaning (fit over the 3 seed hits, then the "
+                       "shared-hit and (q/pT, eta, phi) duplicate test) and duplicate-track removal on the found "
+                       "tracks (shared hits >= half the shorter track)",
+           "seed_clean_ms": round(ms_clean, 4), "seeds_per_s": n_seeds / (ms_clean * 1e-3),
+           "seeds_removed": int((keep_s == 0).sum().item()),
+           "dedup_ms": round(ms_dedup, 4), "tracks_per_s": n_seeds / (ms_dedup * 1e-3),
+           "tracks_removed": int((keep_t == 0).sum().item())}
     ctx.close()
+    return res
 
 
 def run_reference(args, world, rank, local, pg):
-    """The FP64 oracle on the host cores, same metric and workload (a bounded
-    sample of seeds per step)."""
+    """The FP64 oracle on the host cores (one thread per core), same metric and
+    workload: each step a bounded sample of the uneven dense events.  Under
+    torchrun only rank 0 runs it."""
     if rank != 0:
         return
-    from synth import make_batch
-    batch = make_batch(CONFIG, list(range(EVENTS)))
-    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup) * 2)
-    for _ in range(args.warmup):
-        oracle_rate(batch, per_step / 4)
+    cores = os.cpu_count() or 1
+    # the sampled events only (events are independent and seeded by their id)
+    sel = np.random.default_rng(11).choice(C4_EVENTS, 24, replace=False)
+    batch = c4_batch(0, select=np.sort(sel))
+    per_step = max(0.5, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup):
+        oracle_rate(batch, per_step / 4, cores, seed=100 + i)
     rates, seeds, secs = [], 0, 0.0
-    for _ in range(args.steps):
-        r, n, s = oracle_rate(batch, per_step)
+    for i in range(args.steps):
+        r, n, _, w = oracle_rate(batch, per_step, cores, seed=200 + i)
         rates.append(r)
         seeds += n
-        secs += s
+        secs += w
     value = float(np.mean(rates))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "events": EVENTS, "tracks_per_event": 2000, "n_best": N_BEST,
-                       "chi2_cut": CHI2_CUT},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{seeds} seeds sampled over {args.steps} steps of about {per_step:.1f} s"},
+            "config": {"workload": WORKLOAD, "events_per_gpu": C4_EVENTS, "n_best": N_BEST, "chi2_cut": CHI2_CUT},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{seeds} seeds of 24 of the workload's events sampled over {args.steps} "
+                                       f"steps of about {per_step:.1f} s, {cores} threads (one per host core)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -455,6 +455,20 @@ mkf_status mkf_mlp_grad(mkf_ctx *ctx, const uint16_t *w_bf16, const float *feat,
 mkf_status mkf_mlp_train_step(mkf_ctx *ctx, const float *feat, const float *label, int32_t n, float *w, float *m,
                               float *v, int32_t t, const mkf_adam *hp, uint16_t *w_bf16, float *loss);
 
+/* ------------------------------------------------------------------------ */
+/* Measurement aid (not in the paper, which reports no roofline)             */
+/* ------------------------------------------------------------------------ */
+
+/* FP32 throughput probe: enqueues on the context stream one kernel in which
+ * every thread runs 8 independent dependent-FMA chains for 16 * iters rounds
+ * (8 blocks of 256 threads per SM), and returns in *flops (host) the number of
+ * FP32 operations it performs (2 per FMA).  Timing the launch (e.g. with CUDA
+ * events on the stream) gives the FP32 rate the fit and finder kernels are
+ * measured against.  out: device buffer of at least 8 * (SM count) floats that
+ * keeps the chains' result live (it is not written for these inputs).
+ * Errors: MKF_ERR_ARG (iters < 1, NULL pointers), MKF_ERR_CUDA. */
+mkf_status mkf_fp32_probe(mkf_ctx *ctx, int32_t iters, float *out, double *flops);
+
 #ifdef __cplusplus
 }
 #endif

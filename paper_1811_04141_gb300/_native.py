@@ -35,7 +35,7 @@ MAX_NBEST = 16
 # Symbols declared in include/mkf.h (checked by the ABI test).
 EXPORTS = ("mkf_create", "mkf_destroy", "mkf_set_stream", "mkf_sync", "mkf_status_string", "mkf_geometry_load",
            "mkf_hits_bin", "mkf_hitbins_free", "mkf_hitbins_info", "mkf_hitbins_export", "mkf_hits_bin_static", "mkf_geometry_material", "mkf_geometry_field", "mkf_geometry_material_map", "mkf_fit", "mkf_fit_backward", "mkf_fit_smooth", "mkf_seeds_clean", "mkf_tracks_dedup", "mkf_find", "mkf_mlp_to_bf16",
-           "mkf_mlp_forward", "mkf_mlp_grad", "mkf_mlp_train_step")
+           "mkf_mlp_forward", "mkf_mlp_grad", "mkf_mlp_train_step", "mkf_fp32_probe")
 
 
 class MkfLayer(C.Structure):
@@ -113,6 +113,8 @@ def lib():
             L.mkf_mlp_grad.restype = i32
             L.mkf_mlp_train_step.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, C.POINTER(MkfAdam), vp, vp]
             L.mkf_mlp_train_step.restype = i32
+            L.mkf_fp32_probe.argtypes = [vp, i32, vp, C.POINTER(C.c_double)]
+            L.mkf_fp32_probe.restype = i32
             L.mkf_fit.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
             L.mkf_fit.restype = i32
             L.mkf_fit_backward.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, vp, C.c_float, vp, vp, vp, vp, vp]

@@ -388,6 +388,19 @@ def mkf_mlp_grad(ctx, w_bf16, feat, label):
     return grad, loss
 
 
+def mkf_fp32_probe(ctx, iters: int, out=None, device=None):
+    """Enqueue the FP32 throughput probe (dependent-FMA chains) on the context
+    stream; returns (out buffer, FP32 operations of the launch)."""
+    h = _h(ctx)
+    if out is None:
+        sms = torch.cuda.get_device_properties(device if device is not None else torch.cuda.current_device())
+        out = torch.empty(8 * sms.multi_processor_count, dtype=torch.float32,
+                          device=device if device is not None else "cuda")
+    fl = C.c_double(0.0)
+    N.check("mkf_fp32_probe", N.lib().mkf_fp32_probe(h, int(iters), _ptr(out), C.byref(fl)))
+    return out, fl.value
+
+
 def mkf_mlp_train_step(ctx, feat, label, w, m, v, t, w_bf16, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, loss=None):
     """One Adam step on the batch (w, m, v, w_bf16 updated in place)."""
     n = feat.shape[0]

@@ -27,6 +27,33 @@ def split_events(n_events: int, rank: int, world: int) -> range:
     return range(lo, lo + base + (1 if rank < extra else 0))
 
 
+def event_costs(event_offsets, seed_event, bins_per_event: int):
+    """Estimated finding cost of each event: its seeds times (1 + the mean number
+    of hits per bin), i.e. seeds times the hits a window of a few bins holds."""
+    import numpy as np
+    evo = np.asarray(event_offsets, dtype=np.int64)
+    n_ev = evo.shape[0] - 1
+    seeds = np.bincount(np.asarray(seed_event, dtype=np.int64), minlength=n_ev)[:n_ev]
+    return seeds * (1.0 + np.diff(evo) / max(1, int(bins_per_event)))
+
+
+def balance_events(costs, world: int) -> list[list[int]]:
+    """Greedy balancing of whole events over `world` ranks by estimated cost:
+    events in decreasing cost, each to the rank with the least total so far
+    (ties to the lower rank); each rank's list comes back in event order."""
+    if world < 1:
+        raise ValueError("bad world")
+    import heapq
+    order = sorted(range(len(costs)), key=lambda e: (-float(costs[e]), e))
+    heap = [(0.0, r) for r in range(world)]
+    out = [[] for _ in range(world)]
+    for e in order:
+        tot, r = heapq.heappop(heap)
+        out[r].append(e)
+        heapq.heappush(heap, (tot + float(costs[e]), r))
+    return [sorted(x) for x in out]
+
+
 def combine(pg, units: float, step_ms: float, device=None):
     """(total units over ranks, slowest rank's step time) -- the job's throughput
     is total / slowest.  pg is torch.distributed (initialised) or None."""

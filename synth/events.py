@@ -496,9 +496,24 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
                 par0=np.stack([np.zeros(P), np.zeros(P), z0, q / pt, phi0, theta]))
 
 
+def _event_light(args):
+    """make_event for a worker process, without the per-hit truth arrays and with
+    the hit positions already rounded to float32 (what a timing run needs)."""
+    config, ev, nt, nn, base_seed, kw = args
+    p = make_event(config, ev, nt, nn, base_seed, **kw)
+    p["xyz32"] = np.ascontiguousarray(p.pop("xyz64").astype(np.float32))
+    for k in ("true_state", "true_xyz"):
+        p.pop(k)
+    return p
+
+
 def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int = BASE_SEED,
-               min_seed_hits: int = 3, **kw) -> Batch:
-    """Concatenate events.  `n_tracks` / `n_noise` may be scalars or per-event lists."""
+               min_seed_hits: int = 3, workers: int = 1, truth: bool = True, **kw) -> Batch:
+    """Concatenate events.  `n_tracks` / `n_noise` may be scalars or per-event lists.
+
+    truth=False leaves out the per-hit truth arrays (true_state, true_xyz, xyz64
+    are None); with workers > 1 (and truth=False) the events are generated in
+    that many spawned processes.  The events are the same either way."""
     cfg = get_config(config)
     events = list(events)
     E = len(events)
@@ -508,8 +523,19 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
             return v
         return v[i]
 
-    parts = [make_event(config, ev, per_event(n_tracks, i), per_event(n_noise, i), base_seed, **kw)
-             for i, ev in enumerate(events)]
+    if truth:
+        parts = [make_event(config, ev, per_event(n_tracks, i), per_event(n_noise, i), base_seed, **kw)
+                 for i, ev in enumerate(events)]
+    else:
+        jobs = [(config, ev, per_event(n_tracks, i), per_event(n_noise, i), base_seed, kw)
+                for i, ev in enumerate(events)]
+        if workers > 1 and E > 1:
+            import multiprocessing as mp
+            from concurrent.futures import ProcessPoolExecutor
+            with ProcessPoolExecutor(max_workers=min(workers, E), mp_context=mp.get_context("spawn")) as ex:
+                parts = list(ex.map(_event_light, jobs, chunksize=max(1, E // (4 * workers))))
+        else:
+            parts = [_event_light(j) for j in jobs]
     max_hits = max([1] + [int(p["nhits_p"].max(initial=0)) for p in parts])
     offs = np.zeros(E + 1, dtype=np.int64)
     xyz64, layer, hp, ts, tx = [], [], [], [], []
@@ -520,7 +546,9 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
         base = offs[i]
         n = p["layer"].shape[0]
         offs[i + 1] = base + n
-        xyz64.append(p["xyz64"]); layer.append(p["layer"]); ts.append(p["true_state"]); tx.append(p["true_xyz"])
+        xyz64.append(p["xyz64"] if truth else p["xyz32"]); layer.append(p["layer"])
+        if truth:
+            ts.append(p["true_state"]); tx.append(p["true_xyz"])
         hp.append(np.where(p["particle"] >= 0, p["particle"] + pbase, -1).astype(np.int32))
         P = p["nhits_p"].shape[0]
         ok = np.nonzero(p["nhits_p"] >= min_seed_hits)[0]
@@ -556,6 +584,9 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
     if offs[-1] >= (1 << 28) - 2:
         raise ValueError("too many hits for 28-bit hit indices")
     xyz64 = np.concatenate(xyz64, axis=1)
+    xyz32 = np.ascontiguousarray(xyz64.astype(np.float32)) if truth else xyz64
+    if not truth:
+        xyz64 = None
     layers = [dict(d) for d in cfg["layers"]]
     if kw.get("material", 0.0) > 0.0:
         for d in layers:
@@ -564,10 +595,10 @@ def make_batch(config: str, events, n_tracks=None, n_noise=None, base_seed: int 
                 d["eloss"] = float(kw["eloss"])
     return Batch(
         config=config, layers=layers, bz=float(cfg["bz"]),
-        xyz=np.ascontiguousarray(xyz64.astype(np.float32)), xyz64=xyz64,
+        xyz=xyz32, xyz64=xyz64,
         layer=np.concatenate(layer).astype(np.int32), hit_particle=np.concatenate(hp).astype(np.int32),
-        event_offsets=offs.astype(np.int32), true_state=np.concatenate(ts, axis=1),
-        true_xyz=np.concatenate(tx, axis=1),
+        event_offsets=offs.astype(np.int32), true_state=np.concatenate(ts, axis=1) if truth else None,
+        true_xyz=np.concatenate(tx, axis=1) if truth else None,
         seed_hits=np.ascontiguousarray(np.concatenate(seed_hits, axis=1).astype(np.int32)),
         seed_event=np.concatenate(seed_event).astype(np.int32),
         seed_particle=np.concatenate(seed_part).astype(np.int32),

@@ -6,7 +6,7 @@ import socket
 import pytest
 import torch.multiprocessing as mp
 
-from paper_1811_04141_gb300.shard import combine, events_for_rank, split_events
+from paper_1811_04141_gb300.shard import balance_events, combine, event_costs, events_for_rank, split_events
 
 
 def test_event_assignment():
@@ -17,6 +17,28 @@ def test_event_assignment():
     assert max(map(len, shards)) - min(map(len, shards)) <= 1
     with pytest.raises(ValueError):
         events_for_rank(2, 2, 5)
+
+
+def test_balance_events_greedy():
+    import numpy as np
+    costs = [10, 1, 7, 3, 3, 8, 2, 9]
+    shards = balance_events(costs, 3)
+    assert sorted(sum(shards, [])) == list(range(8))            # every event once
+    loads = [sum(costs[e] for e in s) for s in shards]
+    assert max(loads) - min(loads) <= max(costs)                 # greedy bound
+    assert shards == [[0, 1, 4], [3, 6, 7], [2, 5]] and loads == [14, 14, 15]
+    # log-uniform event sizes (as in the uneven workload): within 2 % of the mean
+    rng = np.random.default_rng(3)
+    c = np.floor(np.exp(rng.uniform(np.log(100), np.log(20000), 512)))
+    loads = [c[s].sum() for s in balance_events(c, 8)]
+    assert max(loads) / np.mean(loads) < 1.02
+    # contiguous shards of the same events are far less even
+    cont = [c[list(split_events(512, r, 8))].sum() for r in range(8)]
+    assert max(cont) / np.mean(cont) > max(loads) / np.mean(loads)
+    # the cost estimate: seeds x (1 + hits per bin)
+    evo = np.array([0, 100, 100, 400])
+    se = np.array([0, 0, 2, 2, 2])
+    assert np.allclose(event_costs(evo, se, 100), [2 * 2.0, 0.0, 3 * 4.0])
 
 
 def _free_port():
