@@ -5,8 +5,10 @@ may import this package.  The product path (the CUDA library and its binding)
 never does.  The arithmetic lives in `mkf_oracle.c` (plain C, double precision);
 this module compiles it with gcc on first use and marshals numpy arrays.
 
-Parity status of each function is stated in the oracle's test module
-(tests/test_oracle_pins.py); every exported function here is pinned there.
+Parity status of each function is stated in the oracle's test modules
+(tests/test_oracle_pins.py and, for the field, material map, smoother, seed
+cleaning, MLP and learned pruning, the other tests/test_oracle_*.py); every
+exported function here is pinned there.
 """
 from __future__ import annotations
 
@@ -79,6 +81,8 @@ def _load():
                                            C.c_int, C.c_double, C.c_int, d, d, d, i32, i32, C.c_int, u32, i64, d,
                                            d, C.c_double, d, i32, i64, C.c_int64]
             lib.or_find.restype = C.c_int
+            lib.or_mlp_logit.argtypes = [d, d, C.c_int64, d]
+            lib.or_mlp_logit.restype = None
             _lib = lib
     return _lib
 
@@ -337,6 +341,17 @@ def find(geo: Geometry, xyz, hit_layer, event_offsets, seed_hits, seed_event, n_
     if dump_cap:
         k = int(min(fcnt[0], dump_cap))
         out.update(feat=feat[:k], feat_ref=fref[:k], feat_count=int(fcnt[0]))
+    return out
+
+
+def mlp_logit(w, feat):
+    """The finder's MLP score of feature rows feat [n, 12] with weights w [897]
+    (as or_find applies it when pruning)."""
+    lib = _load()
+    w = _f64(w)
+    feat = _f64(feat).reshape(-1, 12)
+    out = np.zeros(feat.shape[0])
+    lib.or_mlp_logit(_p(w, C.c_double), _p(feat, C.c_double), feat.shape[0], _p(out, C.c_double))
     return out
 
 

@@ -34,7 +34,11 @@
  * the backward fit and the two-filter smoother; material effects (Highland
  * multiple scattering and the mean energy loss, per layer or from an r-z map);
  * a parameterised solenoid field with fourth-order Runge-Kutta propagation and
- * the Jacobian of that map by central differences.
+ * the Jacobian of that map by central differences; and the learned pruning of
+ * the finder's branching (12 features of a candidate-hit pair, a 12-64-1 MLP
+ * score, pairs below a threshold dropped before the N-best selection), pinned
+ * against the separate MLP oracle and against features rebuilt from the
+ * exported single-step calls (tests/test_oracle_pruning.py).
  *
  * Covariances are full 6x6 row-major arrays here.  Interfaces that exchange the
  * 21-value packed lower triangle use index i(i+1)/2 + j for i >= j.
@@ -1409,6 +1413,12 @@ static double mlp_logit(const double *w, const double fe[12]) {
         z += w[832 + j] * (a > 0 ? a : 0.0);
     }
     return z;
+}
+
+/* Logits of n feature rows fe [n][12] with weights w [897] (the finder's
+ * scoring function, exported for its pins). */
+void or_mlp_logit(const double *w, const double *fe, int64_t n, double *out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = mlp_logit(w, fe + 12 * i);
 }
 
 /* Find one seed.  Returns 0, or -1 on allocation failure. */
