@@ -174,6 +174,102 @@ def _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi, x0,
     return out
 
 
+def _scattered_crossings(h, phi0, z0, theta, q, pt, bz, kinds, rz, lo, hi, x0, rng_ms, s_max, eloss=0.0):
+    """As _scattered_cylinder_crossings, for layouts with cylinders and disks:
+    each particle moves on a helix from surface to surface, the next surface
+    being the nearer in path of its next cylinder (by radius) and its next disk
+    (by z in its direction of motion); a surface crossed inside its extent gets
+    a hit, the Highland kick (path x0 / |cos| of the angle to the surface normal:
+    sin(theta) cos(phi - phi_pos) on a cylinder, cos(theta) on a disk) and the
+    mean energy loss; one that is crossed outside it is passed with no material.
+    Normals are drawn for every particle at every step, in step order."""
+    P, L = h.shape[0], rz.shape[0]
+    out = {k: np.full((P, L), np.nan) for k in ("S", "X", "Y", "Z", "W", "PHI", "TH")}
+    cyl = np.where(kinds == 0)[0]
+    cyl = cyl[np.argsort(rz[cyl])]
+    dsk = np.where(kinds == 1)[0]
+    dsk = dsk[np.argsort(rz[dsk])]
+    nc_, nd_ = cyl.size, dsk.size
+    x, y, z = np.zeros(P), np.zeros(P), z0.copy()
+    phi, th = phi0.copy(), theta.copy()
+    w = q / pt
+    pmom = pt / np.sin(theta)
+    dirz = np.where(np.cos(theta) >= 0.0, 1, -1)
+    # index of the first disk ahead of the vertex in each particle's direction
+    if nd_:
+        zd = rz[dsk]
+        nd = np.where(dirz > 0, np.searchsorted(zd, z0, side="right"), np.searchsorted(zd, z0, side="left") - 1)
+    else:
+        nd = np.full(P, -1)
+    nc = np.zeros(P, dtype=np.int64)
+    s_tot, turned = np.zeros(P), np.zeros(P)
+    alive = np.ones(P, dtype=bool)
+    rows = np.arange(P)
+    for _ in range(L + 1):
+        if not alive.any():
+            break
+        hh = -w * K_FIELD * bz
+        has_c = alive & (nc < nc_)
+        Rc = np.where(has_c, rz[cyl[np.minimum(nc, max(nc_ - 1, 0))]] if nc_ else 0.0, 0.0)
+        sc = np.where(has_c, _cylinder_path_from(x, y, phi, hh, np.where(has_c, Rc, 1.0)), np.nan)
+        has_d = alive & (nd >= 0) & (nd < nd_)
+        Zd = np.where(has_d, rz[dsk[np.clip(nd, 0, max(nd_ - 1, 0))]] if nd_ else 0.0, 0.0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            sd = np.where(has_d, (Zd - z) * np.tan(th), np.nan)
+        sd = np.where(sd > 0, sd, np.nan)
+        use_c = np.isfinite(sc) & (~np.isfinite(sd) | (sc <= sd))
+        s = np.where(use_c, sc, sd)
+        ok = alive & np.isfinite(s) & (turned + np.abs(hh) * np.nan_to_num(s) < np.pi) & \
+            (s_tot + np.nan_to_num(s) < s_max)
+        l = np.where(use_c, cyl[np.minimum(nc, max(nc_ - 1, 0))] if nc_ else 0,
+                     dsk[np.clip(nd, 0, max(nd_ - 1, 0))] if nd_ else 0)
+        sf = np.where(ok, s, 0.0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            hsafe = np.where(hh == 0.0, 1.0, hh)
+            xn = np.where(hh == 0.0, x + sf * np.cos(phi), x + (np.sin(phi + hh * sf) - np.sin(phi)) / hsafe)
+            yn = np.where(hh == 0.0, y + sf * np.sin(phi), y - (np.cos(phi + hh * sf) - np.cos(phi)) / hsafe)
+        zn = np.where(use_c, z + sf / np.tan(th), Zd)
+        phin = phi + hh * sf
+        rn = np.hypot(xn, yn)
+        inside = ok & np.where(use_c, (zn >= lo[l]) & (zn <= hi[l]), (rn >= lo[l]) & (rn <= hi[l]))
+        x0v, elv = np.full(P, float(x0)), np.full(P, float(eloss))
+        gk = rng_ms.standard_normal((P, 2))
+        cosa = np.where(use_c, np.abs(np.sin(th) * np.cos(phin - np.arctan2(yn, xn))), np.abs(np.cos(th)))
+        t0 = np.where(x0v > 0.0, _highland(pmom, np.maximum(x0v, 1e-30) / np.maximum(cosa, 1e-6)), 0.0)
+        th2 = np.where(inside, th + t0 * gk[:, 0], th)
+        phi2 = np.where(inside, phin + t0 * gk[:, 1] / np.sin(th), phin)
+        if (elv > 0.0).any():
+            beta = pmom / np.sqrt(pmom * pmom + PION_MASS * PION_MASS)
+            e_new = np.sqrt(pmom * pmom + PION_MASS * PION_MASS) - elv * (x0v / np.maximum(cosa, 1e-6)) / (beta * beta)
+            stops = inside & (e_new <= PION_MASS)
+            pmom = np.where(inside & ~stops, np.sqrt(np.maximum(e_new * e_new - PION_MASS * PION_MASS, 1e-30)), pmom)
+            ok = ok & ~stops
+        w2 = np.where(inside, np.sign(w) / (pmom * np.sin(th2)), w)
+        sel = inside
+        li = l[sel]
+        out["S"][rows[sel], li] = (s_tot + sf)[sel]
+        out["X"][rows[sel], li], out["Y"][rows[sel], li], out["Z"][rows[sel], li] = xn[sel], yn[sel], zn[sel]
+        out["W"][rows[sel], li] = w2[sel]
+        out["PHI"][rows[sel], li] = np.arctan2(np.sin(phi2[sel]), np.cos(phi2[sel]))
+        out["TH"][rows[sel], li] = th2[sel]
+        x, y, z = np.where(ok, xn, x), np.where(ok, yn, y), np.where(ok, zn, z)
+        phi, th, w = np.where(ok, phi2, phi), np.where(ok, th2, th), np.where(ok, w2, w)
+        turned = turned + np.where(ok, np.abs(hh) * sf, 0.0)
+        s_tot = s_tot + sf
+        # the surface just reached is behind; a turned-back polar angle changes
+        # the direction along z (the next disk is then the one behind)
+        nc = np.where(ok & use_c, nc + 1, nc)
+        nd = np.where(ok & ~use_c, nd + dirz, nd)
+        nd_new_dir = np.where(np.cos(th) >= 0.0, 1, -1)
+        flip = ok & (nd_new_dir != dirz)
+        if flip.any() and nd_:
+            nd = np.where(flip, np.where(nd_new_dir > 0, np.searchsorted(rz[dsk], z, side="right"),
+                                          np.searchsorted(rz[dsk], z, side="left") - 1), nd)
+            dirz = np.where(flip, nd_new_dir, dirz)
+        alive = ok
+    return out
+
+
 def solenoid_field(bz, alpha, x, y, z):
     """Second-order solenoid field (tesla) at positions in cm: from the scalar
     potential solving Laplace's equation with axial symmetry,
@@ -321,10 +417,11 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
     their random numbers are drawn after everything else, so the other arrays do
     not change.
 
-    material > 0 (layouts of cylinders only): every layer is that many radiation
-    lengths thick at normal incidence and the particles scatter at each layer
-    they cross (see _scattered_cylinder_crossings); the kicks come from a stream
-    of their own, so the other random numbers do not change.  eloss > 0 (with
+    material > 0: every layer is that many radiation lengths thick at normal
+    incidence and the particles scatter at each layer they cross (see
+    _scattered_cylinder_crossings, and _scattered_crossings for layouts with
+    disks); the kicks come from a stream of their own, so the other random
+    numbers do not change.  eloss > 0 (with
     material): the mean energy loss per radiation length at minimum ionisation
     (GeV), lost at each layer crossed.
 
@@ -386,15 +483,19 @@ def make_event(config: str, event: int, n_tracks: int | None = None, n_noise: in
         ms = _field_crossings(phi0, z0, theta, q, pt, bz, float(field_alpha), kinds, rz, lo, hi)
         S = ms["S"]
     elif material > 0.0 or material_map is not None:
-        if dsk.size:
-            raise ValueError("material is supported for layouts of cylinders only")
         if material_map is not None and (material > 0.0 or eloss > 0.0):
             raise ValueError("give either material / eloss or material_map")
+        if dsk.size and material_map is not None:
+            raise ValueError("an r-z material map is supported for layouts of cylinders only")
         key = (int(base_seed) << 64) | (CONFIG_IDS[config] << 32) | (int(event) & 0xFFFFFFFF)
         rng_ms = np.random.Generator(np.random.Philox(key=key ^ (0x5CA77E8 << 96)))
-        ms = _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi,
-                                           material_map if material_map is not None else float(material), rng_ms,
-                                           s_max, float(eloss))
+        if dsk.size:
+            ms = _scattered_crossings(h, phi0, z0, theta, q, pt, bz, kinds, rz, lo, hi, float(material), rng_ms,
+                                      s_max, float(eloss))
+        else:
+            ms = _scattered_cylinder_crossings(h, phi0, z0, theta, q, pt, bz, rz, lo, hi,
+                                               material_map if material_map is not None else float(material), rng_ms,
+                                               s_max, float(eloss))
         S = ms["S"]
     Sf = np.where(np.isnan(S), 1.0, S)
     if ms is None:

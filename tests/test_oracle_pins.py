@@ -548,6 +548,13 @@ def test_backfit_short_lists_and_errors():
 # material: multiple scattering
 # --------------------------------------------------------------------------
 
+def _chi2_median_over_ndf(ndf):
+    """Mean over tracks of the median of chi2(ndf) / ndf (what the median of
+    chi2 / ndf is for a correct fit)."""
+    from scipy.stats import chi2 as chi2_dist
+    return float(np.median(chi2_dist.rvs(ndf, random_state=np.random.default_rng(0)) / ndf))
+
+
 def _pulls(par, truth, cov21, idx=(2, 3, 4, 5)):
     Cm = O.unpack21(cov21)
     out = {}
@@ -632,6 +639,35 @@ def test_fit_with_energy_loss_pulls():
     bare = O.Geometry([{k: v for k, v in d.items() if k != "eloss"} for d in b.layers], b.bz)
     r0 = O.fit(bare, b.xyz64, b.layer, b.track_hits)
     assert _pulls(r0["par"][:, ok], truth, r0["cov"][:, ok], (3,))[3].std() > 1.5
+
+
+def test_fit_with_material_on_cylinders_and_disks():
+    """The dense layout (17 cylinders + 2 x 14 disks) with 0.02 X0 and 0.04 GeV
+    per X0 in every layer: the generator moves the particles from surface to
+    surface in path order, kicking and slowing them at every layer crossed
+    (on a disk the path through it is x0 / |cos(theta)|); with the material
+    in the filter the pulls of q/pT, phi and theta at the last hit are N(0, 1)
+    and chi2/ndf is 1, without it chi2/ndf is far off."""
+    b = make_batch("dense45", [3, 4], n_tracks=1200, n_noise=0, material=0.02, eloss=0.04)
+    disk = np.array([d["kind"] for d in b.layers])[b.layer] == 1
+    assert disk[b.hit_particle >= 0].mean() > 0.2  # many hits on disks
+    geo = O.geometry_for(b)
+    r = O.fit(geo, b.xyz64, b.layer, b.track_hits)
+    ok = r["status"] == 0
+    assert ok.mean() > 0.99
+    truth = b.true_state[:, _last_hits(b)][:, ok]
+    # widths from the median absolute deviation: a few low-pT particles that
+    # lose most of their energy in the 45 layers leave the Gaussian regime
+    # (two of 2400 with |pull| > 6), which the standard deviation would weigh
+    for i, pull in _pulls(r["par"][:, ok], truth, r["cov"][:, ok], (3, 4, 5)).items():
+        med = np.median(pull)
+        assert abs(med) < 0.05, i
+        assert abs(1.4826 * np.median(np.abs(pull - med)) - 1) < 0.05, i
+        assert (np.abs(pull) > 6).mean() < 3e-3, i
+    assert abs(np.median(r["chi2"][ok] / r["ndf"][ok]) / _chi2_median_over_ndf(r["ndf"][ok]) - 1) < 0.05
+    bare = O.Geometry([{k: v for k, v in d.items() if k not in ("x0", "eloss")} for d in b.layers], b.bz)
+    r0 = O.fit(bare, b.xyz64, b.layer, b.track_hits)
+    assert r0["chi2"][ok].sum() / r0["ndf"][ok].sum() > 5
 
 
 @pytest.mark.parametrize("eloss", [0.0, 0.15])
