@@ -302,99 +302,120 @@ def fp32_peak(ctx, dev, iters: int = 50000, reps: int = 5):
 # learned pruning: events/s of the MLP-pruned finder vs the plain finder
 # ---------------------------------------------------------------------------
 
-def learned_leg(dev, reps: int = 30):
-    """Dense events (17 cylinders + 2 x 14 disks, 6000 tracks + 200k noise hits
-    per event): train the MLP on features the plain finder dumps on 10 training
-    events (labels from truth), take the largest threshold whose efficiency stays
-    within 0.5 points of the plain finder on those events, then time both finders
-    (binning + finding) on 10 held-out events."""
+def learned_leg(dev, n_train: int = 200, n_eval: int = 200, reps: int = 5):
+    """Learned branching on dense events (17 cylinders + 2 x 14 disks, 6000 tracks
+    + 200k noise hits per event), with material (0.02 X0 and 0.04 GeV per X0 in
+    every layer, particles scattered and slowed by the generator) and without.
+    The MLP is trained (library kernels) on the pairs the plain N-best finder
+    dumps on n_train training events (of the 2000-event training range, events
+    0..), labels from truth; the cascade's gate threshold is the smallest that
+    keeps efficiency and fake rate within 0.5 points of the plain finder on
+    them; timed on n_eval held-out events (10000..): the plain N = 10 finder, the
+    learned cascade (best-hit finding with the MLP gate, N-best finding of the
+    flagged seeds), the N-best finder with MLP pruning of pairs, and best-hit
+    finding; each with hit binning."""
     import torch
 
     from paper_1811_04141_gb300 import Context
     from paper_1811_04141_gb300 import learned as L
     from synth import make_batch
-    tr = make_batch("dense45", list(range(1000, 1010)))
-    ev = make_batch("dense45", list(range(10)))
-    ctx = Context(dev.index, torch.cuda.current_stream(dev))
-    ctx.geometry_load(tr.layers, tr.bz)
+    res = {"metric": "events/s (hit binning + finding)",
+           "training": f"{n_train} of the 2000 training events (0..{n_train - 1}), at most 30M pairs, "
+                       "1500 Adam steps of 4096 pairs",
+           "evaluation": f"{n_eval} held-out events (10000..{10000 + n_eval - 1})"}
+    for kind, mat in (("material", dict(material=0.02, eloss=0.04)), ("clean", {})):
+        tr = make_batch("dense45", list(range(n_train)), truth=False, workers=os.cpu_count() or 1, **mat)
+        ev = make_batch("dense45", list(range(10000, 10000 + n_eval)), truth=False, workers=os.cpu_count() or 1,
+                        **mat)
+        ctx = Context(dev.index, torch.cuda.current_stream(dev))
+        ctx.geometry_load(tr.layers, tr.bz)
+        mo = len(tr.layers) + 3
 
-    def prep(b):
-        to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
-        d = dict(xyz=to(b.xyz, torch.float32), layer=to(b.layer, torch.int32), evo=to(b.event_offsets, torch.int32),
-                 sh=to(b.seed_hits, torch.int32), se=to(b.seed_event, torch.int32),
-                 hp=to(b.hit_particle, torch.int32), sp=to(b.seed_particle, torch.int32))
-        d["bins"] = ctx.hits_bin(d["xyz"], d["layer"], d["evo"])
-        return d
+        def prep(b):
+            to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+            d = dict(xyz=to(b.xyz, torch.float32), layer=to(b.layer, torch.int32), evo=to(b.event_offsets, torch.int32),
+                     sh=to(b.seed_hits, torch.int32), se=to(b.seed_event, torch.int32),
+                     hp=to(b.hit_particle, torch.int32), sp=to(b.seed_particle, torch.int32))
+            d["bins"] = ctx.hits_bin(d["xyz"], d["layer"], d["evo"])
+            return d
 
-    dt, de = prep(tr), prep(ev)
-    feat, ref = L.collect_features(ctx, dt["bins"], dt["sh"], dt["se"], 8_000_000, n_best=N_BEST)
-    lab = L.label_pairs(ref, dt["hp"], dt["sp"])
-    st = L.train(ctx, feat, lab, steps=1500, batch=4096, lr=2e-3)
-    max_out = len(tr.layers) + 3
+        dt = prep(tr)
+        feat, ref = L.collect_features(ctx, dt["bins"], dt["sh"], dt["se"], 30_000_000, n_best=N_BEST, max_out=mo)
+        lab = L.label_pairs(ref, dt["hp"], dt["sp"])
+        st = L.train(ctx, feat, lab, steps=1500, batch=4096, lr=2e-3)
+        del feat, ref, lab
 
-    def run(d, tau=None):
-        kw = dict(n_best=N_BEST, max_out=max_out)
-        if tau is not None:
-            kw.update(mlp_bf16=st["w_bf16"], mlp_tau=tau)
-        out = ctx.find(d["bins"], d["sh"], d["se"], **kw)
-        ctx.sync()
-        e, f = L.efficiency(out["hits"], d["hp"], d["sp"])
-        return e, f, out["counters"].sum(dim=1).cpu().numpy()
+        def eff(d, out):
+            return L.efficiency(out["hits"], d["hp"], d["sp"])
 
-    e0, f0, _ = run(dt)
-    best = L.choose_tau(lambda t: run(dt, t)[:2], e0, [-4.0, -2.0, -1.0, 0.0, 1.0, 2.0, 3.0])
-    tau = best[0] if best else None
+        def plain(d, nb=N_BEST, out=None):
+            return ctx.find(d["bins"], d["sh"], d["se"], n_best=nb, max_out=mo, out=out)
 
-    def timed(tau_):
-        kw = dict(n_best=N_BEST, max_out=max_out)
-        if tau_ is not None:
-            kw.update(mlp_bf16=st["w_bf16"], mlp_tau=tau_)
-        out = ctx.find(de["bins"], de["sh"], de["se"], **kw)
-        for _ in range(3):
-            ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
-            ctx.find(de["bins"], de["sh"], de["se"], out=out, **kw)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(reps):
-            ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
-            ctx.find(de["bins"], de["sh"], de["se"], out=out, **kw)
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
+        def casc(d, tau, out=None, sub=None):
+            return L.cascade(ctx, d["bins"], d["sh"], d["se"], st["w_bf16"], tau, n_best=N_BEST, max_out=mo, out=out,
+                             subset=sub)
 
-    ms_plain = timed(None)
-    ms_pruned = timed(tau) if tau is not None else None
-    ep, fp, cp = run(de)
-    # best-hit finding (N = 1) on the same held-out events: what branching buys here
-    out1 = ctx.find(de["bins"], de["sh"], de["se"], n_best=1, max_out=max_out)
-    for _ in range(3):
-        ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
-        ctx.find(de["bins"], de["sh"], de["se"], n_best=1, max_out=max_out, out=out1)
-    torch.cuda.synchronize()
-    a1, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a1.record()
-    for _ in range(reps):
-        ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
-        ctx.find(de["bins"], de["sh"], de["se"], n_best=1, max_out=max_out, out=out1)
-    b1.record()
-    torch.cuda.synchronize()
-    ms_best = a1.elapsed_time(b1) / reps
-    e1, f1 = L.efficiency(out1["hits"], de["hp"], de["sp"])
-    res = {"workload": "dense45: 17 cylinders + 2x14 disks, 6000 tracks (pT^-3 from 0.5 GeV) + 200k noise hits "
-                       "per event; trained on 10 events, evaluated on 10 held-out events; N=10",
-           "metric": "events/s (hit binning + finding)", "train_pairs": int(feat.shape[0]),
-           "train_loss_first_last": [st["losses"][0], st["losses"][-1]] if st["losses"] else None,
-           "plain": {"events_per_s": 10 / (ms_plain * 1e-3), "ms": ms_plain, "efficiency": ep, "fake_rate": fp,
-                     "cand_layers": int(cp[0]), "updates": int(cp[2])},
-           "best_hit_n1": {"events_per_s": 10 / (ms_best * 1e-3), "ms": ms_best, "efficiency": e1, "fake_rate": f1,
-                           "cand_layers": int(out1["counters"][0].sum().item())}}
-    if tau is not None:
-        el, fl, cl = run(de, tau)
-        res["pruned"] = {"tau": tau, "events_per_s": 10 / (ms_pruned * 1e-3), "ms": ms_pruned, "efficiency": el,
-                         "fake_rate": fl, "cand_layers": int(cl[0]), "updates": int(cl[2])}
-        res["pruned_over_plain_events_per_s"] = ms_plain / ms_pruned
-    ctx.close()
+        def pruned(d, tau, out=None):
+            return ctx.find(d["bins"], d["sh"], d["se"], n_best=N_BEST, max_out=mo, mlp_bf16=st["w_bf16"],
+                            mlp_tau=tau, out=out)
+
+        e0, f0 = eff(dt, plain(dt))
+        gate = L.choose_gate_tau(lambda t: eff(dt, casc(dt, t)[0]), e0, f0, [-6.0, -4.0, -2.0, -1.0, 0.0, 1.0, 2.0,
+                                                                           3.0, 4.0, 6.0])
+        prune = L.choose_tau(lambda t: eff(dt, pruned(dt, t)), e0, [-4.0, -2.0, -1.0, 0.0, 1.0, 2.0, 3.0])
+        del dt
+        de = prep(ev)
+
+        def timed(fn):
+            for _ in range(2):
+                ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
+                fn()
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                ctx.hits_bin(de["xyz"], de["layer"], de["evo"], de["bins"])
+                fn()
+            z.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(z) / reps
+
+        entry = {}
+        o = plain(de)
+        ms = timed(lambda: plain(de, out=o))
+        e, f = eff(de, o)
+        cl = int(o["counters"][0].sum().item())
+        entry["plain_n10"] = {"events_per_s": n_eval / (ms * 1e-3), "ms": ms, "efficiency": e, "fake_rate": f,
+                              "cand_layers": cl}
+        o1 = plain(de, 1)
+        ms = timed(lambda: plain(de, 1, out=o1))
+        e, f = eff(de, o1)
+        entry["best_hit_n1"] = {"events_per_s": n_eval / (ms * 1e-3), "ms": ms, "efficiency": e, "fake_rate": f,
+                                "cand_layers": int(o1["counters"][0].sum().item())}
+        if gate is not None:
+            tau = gate[0]
+            oc, sub = casc(de, tau)
+            e, f = eff(de, oc)
+            flagged = int(sub[1].item())
+            ms = timed(lambda: casc(de, tau, out=oc, sub=sub))
+            entry["cascade"] = {"tau": tau, "events_per_s": n_eval / (ms * 1e-3), "ms": ms, "efficiency": e,
+                                "fake_rate": f, "flagged_seeds": flagged / ev.n_seeds}
+            p_ = entry["plain_n10"]
+            entry["cascade_over_plain_events_per_s"] = entry["cascade"]["events_per_s"] / p_["events_per_s"]
+            entry["cascade_equal_efficiency_and_fake"] = bool(abs(e - p_["efficiency"]) <= 0.005 and
+                                                              abs(f - p_["fake_rate"]) <= 0.005)
+        if prune is not None:
+            tau = prune[0]
+            op = pruned(de, tau)
+            e, f = eff(de, op)
+            ms = timed(lambda: pruned(de, tau, out=op))
+            entry["pruned_n10"] = {"tau": tau, "events_per_s": n_eval / (ms * 1e-3), "ms": ms, "efficiency": e,
+                                   "fake_rate": f, "cand_layers": int(op["counters"][0].sum().item())}
+        entry["train_loss_first_last"] = [st["losses"][0], st["losses"][-1]] if st["losses"] else None
+        res[kind] = entry
+        ctx.close()
+        del de
+        torch.cuda.empty_cache()
     return res
 
 

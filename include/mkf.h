@@ -56,6 +56,7 @@ typedef int32_t mkf_status;
 #define MKF_ST_BADS 8u        /* a residual covariance was not positive definite; that update was skipped */
 #define MKF_ST_MISSSTOP 16u   /* find: the best candidate stopped after max_consec_miss misses in a row */
 #define MKF_ST_TRUNC 32u      /* find: the hit list did not fit into max_out entries */
+#define MKF_ST_AMBIG 64u      /* find, MLP gate mode: the MLP doubted a best-chi2 extension of this seed */
 
 #define MKF_MAX_LAYERS 64
 #define MKF_MAX_REGIONS 16
@@ -391,6 +392,21 @@ typedef struct {
      * GPU global timer (ns) when the last seed of event e was written, entry
      * n_events the earliest start of a finding block; set by the call. */
     uint64_t *event_times;
+    /* Seed subset (device, or both NULL for every seed): only the seeds
+     * seed_list[0 .. *seed_count) (indices into seed_hits, each < n_seeds) are
+     * found; their outputs are written at their own indices and every other
+     * seed's outputs are left as they are.  The count is read on the device,
+     * so a subset chosen by an earlier call (mkf_seeds_where) needs no host
+     * round trip; *seed_count above n_seeds is taken as n_seeds, an index out
+     * of range is a device fault (MKF_ERR_DEVICE_CHECK at mkf_sync). */
+    const int32_t *seed_list;
+    const int32_t *seed_count;
+    /* With mlp_bf16: 0 prunes as described above; 1 (gate) drops nothing and
+     * instead scores, on each layer where a candidate has two or more
+     * compatible hits, its best one by chi2, setting MKF_ST_AMBIG on the seed
+     * when that logit < mlp_tau (the learned cascade: best-hit finding with the
+     * gate, then N-best finding of the flagged seeds only). */
+    int32_t mlp_mode;
 } mkf_find_params;
 
 /* Find tracks from seeds.
@@ -414,6 +430,18 @@ typedef struct {
 mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int32_t *seed_hits, const int32_t *seed_event,
                     int32_t n_seeds, const mkf_find_params *params, float *out_par, float *out_cov, float *chi2,
                     int32_t *n_hits, int32_t *hit_idx, int32_t max_out, uint32_t *status, int32_t *counters);
+
+/* Seeds whose status has any of `bits` set (e.g. MKF_ST_AMBIG after a gated
+ * best-hit pass, Sec. 1's selection of extensions done again with N
+ * candidates for them): status [n] (device), seed_list [n] (device, written:
+ * the indices in ascending order, so that the seeds of one event stay
+ * together), *seed_count (device, written).  For the seed_list / seed_count
+ * inputs of mkf_find; no host synchronisation.  Uses the context's scratch
+ * memory (4 bytes per 1024 seeds; a preceding mkf_find call on these seeds has
+ * sized it, so the call then allocates nothing and can be captured).
+ * Errors: MKF_ERR_ARG, MKF_ERR_CUDA. */
+mkf_status mkf_seeds_where(mkf_ctx *ctx, const uint32_t *status, int32_t n, uint32_t bits, int32_t *seed_list,
+                           int32_t *seed_count);
 
 /* ------------------------------------------------------------------------ */
 /* Learned hit ranking (not in the paper: a small MLP that scores a          */

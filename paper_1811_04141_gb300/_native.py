@@ -26,6 +26,7 @@ ST_NONFINITE = 4
 ST_BADS = 8
 ST_MISSSTOP = 16
 ST_TRUNC = 32
+ST_AMBIG = 64
 
 MAX_LAYERS = 64
 STATIC_MAX_HITS = 1 << 22
@@ -35,7 +36,7 @@ MAX_NBEST = 16
 # Symbols declared in include/mkf.h (checked by the ABI test).
 EXPORTS = ("mkf_create", "mkf_destroy", "mkf_set_stream", "mkf_sync", "mkf_status_string", "mkf_geometry_load",
            "mkf_hits_bin", "mkf_hitbins_free", "mkf_hitbins_info", "mkf_hitbins_export", "mkf_hits_bin_static", "mkf_geometry_material", "mkf_geometry_field", "mkf_geometry_material_map", "mkf_fit", "mkf_fit_backward", "mkf_fit_smooth", "mkf_seeds_clean", "mkf_tracks_dedup", "mkf_find", "mkf_mlp_to_bf16",
-           "mkf_mlp_forward", "mkf_mlp_grad", "mkf_mlp_train_step", "mkf_fp32_probe")
+           "mkf_mlp_forward", "mkf_mlp_grad", "mkf_mlp_train_step", "mkf_fp32_probe", "mkf_seeds_where")
 
 
 class MkfLayer(C.Structure):
@@ -51,7 +52,8 @@ class MkfFindParams(C.Structure):
     _fields_ = [("n_best", C.c_int32), ("chi2_cut", C.c_float), ("max_consec_miss", C.c_int32),
                 ("block_threads", C.c_int32), ("mlp_bf16", C.c_void_p), ("mlp_tau", C.c_float),
                 ("feat_out", C.c_void_p), ("feat_ref", C.c_void_p), ("feat_count", C.c_void_p),
-                ("feat_cap", C.c_int32), ("event_times", C.c_void_p)]
+                ("feat_cap", C.c_int32), ("event_times", C.c_void_p), ("seed_list", C.c_void_p),
+                ("seed_count", C.c_void_p), ("mlp_mode", C.c_int32)]
 
 
 MLP_IN = 12
@@ -115,6 +117,8 @@ def lib():
             L.mkf_mlp_train_step.restype = i32
             L.mkf_fp32_probe.argtypes = [vp, i32, vp, C.POINTER(C.c_double)]
             L.mkf_fp32_probe.restype = i32
+            L.mkf_seeds_where.argtypes = [vp, vp, i32, C.c_uint32, vp, vp]
+            L.mkf_seeds_where.restype = i32
             L.mkf_fit.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
             L.mkf_fit.restype = i32
             L.mkf_fit_backward.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, vp, C.c_float, vp, vp, vp, vp, vp]

@@ -300,8 +300,12 @@ def mkf_tracks_dedup(ctx, hit_idx, n_hits, track_nhits, chi2, min_frac=0.5, keep
 
 
 def find_params(n_best=10, chi2_cut=30.0, max_consec_miss=3, block_threads=0, mlp_bf16=None, mlp_tau=0.0,
-                feat=None, event_times=None) -> N.MkfFindParams:
+                feat=None, event_times=None, seed_list=None, seed_count=None, mlp_mode=0) -> N.MkfFindParams:
     prm = N.MkfFindParams(int(n_best), float(chi2_cut), int(max_consec_miss), int(block_threads))
+    if seed_list is not None:
+        prm.seed_list = seed_list.data_ptr()
+        prm.seed_count = seed_count.data_ptr()
+    prm.mlp_mode = int(mlp_mode)
     if event_times is not None:
         prm.event_times = event_times.data_ptr()
     if mlp_bf16 is not None:
@@ -323,10 +327,18 @@ def feature_buffer(cap: int, device="cuda") -> dict:
 
 def mkf_find(ctx, bins: HitBins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
              n_layers=None, out=None, counters=True, block_threads=0, device: int | None = None, mlp_bf16=None,
-             mlp_tau=0.0, feat=None, event_times=None):
+             mlp_tau=0.0, feat=None, event_times=None, seed_list=None, seed_count=None, mlp_mode=0):
     """Find tracks; returns dict(par, cov, chi2, n_hits, hits [max_out, n], status, counters [3, n]).
-    mlp_bf16 (int16 tensor of MLP_PARAMS bfloat16 patterns) turns on learned pruning at mlp_tau;
-    feat (from feature_buffer) receives the features of every compatible hit."""
+    mlp_bf16 (int16 tensor of MLP_PARAMS bfloat16 patterns) turns on learned pruning at mlp_tau
+    (mlp_mode 1: the gate, flagging seeds instead of dropping hits); feat (from feature_buffer)
+    receives the features of every compatible hit; seed_list / seed_count (int32 device
+    tensors, the count of one element) restrict the call to those seeds (outputs in `out`
+    at their indices)."""
+    if (seed_list is None) != (seed_count is None):
+        raise ValueError("give both seed_list and seed_count or neither")
+    if seed_list is not None:
+        _need(seed_list, "seed_list", torch.int32, None, device)
+        _need(seed_count, "seed_count", torch.int32, (1,), device)
     n = seed_hits.shape[1]
     _need(seed_hits, "seed_hits", torch.int32, (3, n), device)
     _need(seed_event, "seed_event", torch.int32, (n,), device)
@@ -347,12 +359,27 @@ def mkf_find(ctx, bins: HitBins, seed_hits, seed_event, n_best=10, chi2_cut=30.0
                    counters=torch.empty(3, n, dtype=torch.int32, device=dev) if counters else None)
     if event_times is not None:
         _need(event_times, "event_times", torch.int64, None, device)
-    prm = find_params(n_best, chi2_cut, max_consec_miss, block_threads, mlp_bf16, mlp_tau, feat, event_times)
+    prm = find_params(n_best, chi2_cut, max_consec_miss, block_threads, mlp_bf16, mlp_tau, feat, event_times,
+                      seed_list, seed_count, mlp_mode)
     N.check("mkf_find", N.lib().mkf_find(_h(ctx), bins.handle, _ptr(seed_hits), _ptr(seed_event), n, C.byref(prm),
                                          _ptr(out["par"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out["n_hits"]),
                                          _ptr(out["hits"]), int(out["hits"].shape[0]), _ptr(out["status"]),
                                          _ptr(out.get("counters"))))
     return out
+
+
+def mkf_seeds_where(ctx, status, bits, seed_list=None, seed_count=None):
+    """Indices of the seeds whose status has any of `bits` (device list and a
+    one-element device count, both written on the device)."""
+    n = status.shape[0]
+    _need(status, "status", torch.int32, (n,), None)
+    if seed_list is None:
+        seed_list = torch.empty(max(1, n), dtype=torch.int32, device=status.device)
+    if seed_count is None:
+        seed_count = torch.empty(1, dtype=torch.int32, device=status.device)
+    N.check("mkf_seeds_where", N.lib().mkf_seeds_where(_h(ctx), _ptr(status), n, int(bits), _ptr(seed_list),
+                                                         _ptr(seed_count)))
+    return seed_list, seed_count
 
 
 def _h(ctx):
@@ -467,7 +494,12 @@ class Context:
         return mkf_fit_smooth(self.handle, xyz, hit_layer, hit_idx, seed_par, seed_cov, inflate, out, self.device)
 
     def find(self, bins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
-             out=None, counters=True, block_threads=0, mlp_bf16=None, mlp_tau=0.0, feat=None, event_times=None):
+             out=None, counters=True, block_threads=0, mlp_bf16=None, mlp_tau=0.0, feat=None, event_times=None,
+             seed_list=None, seed_count=None, mlp_mode=0):
         nl = len(self.layers) if self.layers else None
         return mkf_find(self.handle, bins, seed_hits, seed_event, n_best, chi2_cut, max_consec_miss, max_out, nl, out,
-                        counters, block_threads, self.device, mlp_bf16, mlp_tau, feat, event_times)
+                        counters, block_threads, self.device, mlp_bf16, mlp_tau, feat, event_times, seed_list,
+                        seed_count, mlp_mode)
+
+    def seeds_where(self, status, bits, seed_list=None, seed_count=None):
+        return mkf_seeds_where(self.handle, status, bits, seed_list, seed_count)

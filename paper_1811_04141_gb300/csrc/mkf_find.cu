@@ -68,7 +68,16 @@ struct FindArgs {
     unsigned long long *event_times;      // [n_events + 1] or nullptr
     float *beam;                          // [n_best][kListFields][n_seeds] first-step hit lists
     int32_t step1;                        // the seed kernel takes the first step (plain finder)
+    const int32_t *seed_list;             // seeds to find (or nullptr: all), *seed_count of them
+    const int32_t *seed_count;
+    int32_t mlp_mode;                     // 0 prune, 1 gate (flag MKF_ST_AMBIG, drop nothing)
 };
+
+// Number of seeds this call finds: all of them, or the device-side count of
+// the seed list (clamped to n_seeds).
+__device__ __forceinline__ int seeds_in_call(const FindArgs &A) {
+    return A.seed_list ? min(max(*A.seed_count, 0), A.n_seeds) : A.n_seeds;
+}
 
 // Fitted-seed record, structure of arrays over seeds.
 enum {
@@ -419,8 +428,13 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
 // kParamField: the parameterised field (Runge-Kutta propagation).
 template <bool kParamField>
 __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindArgs A) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= A.n_seeds) return;
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= seeds_in_call(A)) return;
+    const int t = A.seed_list ? A.seed_list[li] : li;  // the seed
+    if (t < 0 || t >= A.n_seeds) {
+        record_fault(A.fault, kFaultBadSeedList, li);
+        return;
+    }
     const Geom &G = A.G;
     const int n = A.n_seeds;
     float *B = A.seedbuf;
@@ -632,14 +646,21 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     if (A.event_times && threadIdx.x == 0) atomicMin(&A.event_times[A.n_events], globaltimer_ns());
 
     // persistent warps: each takes the next group of seeds from a shared counter
-    const int n_groups = (A.n_seeds + spw - 1) / spw;
+    const int n_call = seeds_in_call(A);
+    const int n_groups = (n_call + spw - 1) / spw;
     for (;;) {
         int grp = 0;
         if (lane == 0) grp = atomicAdd(A.work_counter, 1);
         grp = __shfl_sync(kFull, grp, 0);
         if (grp >= n_groups) break;
-        const int seed = grp * spw + slot;
-        const bool has_seed = lane_used && seed < A.n_seeds;
+        const int li = grp * spw + slot;
+        int seed = li;
+        bool has_seed = lane_used && li < n_call;
+        if (A.seed_list && has_seed) {
+            seed = A.seed_list[li];
+            // an out-of-range entry was recorded by the seed kernel
+            has_seed = seed >= 0 && seed < A.n_seeds;
+        }
         float p[6], C[21];
         Lo lo{0.f, 0.f, 0.f, 0.f, 0.f};
     #pragma unroll
@@ -782,7 +803,19 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
             // compatible hits); the MLP scores a list only when the candidate has
             // two or more compatible hits.  The lanes step through the list
             // positions together, so the MLP runs once per position for the warp
-            if (kLearned) {
+            if (kLearned && A.mlp_mode == 1) {
+                // gate: the best compatible hit by chi2 of a candidate with two or
+                // more is scored; a doubtful one flags the seed (nothing dropped)
+                const bool score_it = X.searched && X.nlist > 0 && X.n_compat >= 2 && A.mlp;
+                if (__any_sync(kFull, score_it)) {
+                    const int ly = X.layer >= 0 ? X.layer : 0;
+                    float fe[12];
+                    pair_features(lu[lane], lv[lane], I, lchi[lane], cut, chi2, bk, ly, G.n_layers, G.L[ly].kind, p,
+                                  X.cot, fe);
+                    const float logit = mlp_logit(WS, fe);
+                    if (score_it && logit < A.mlp_tau) status |= MKF_ST_AMBIG;
+                }
+            } else if (kLearned) {
                 const bool score_it = X.searched && X.nlist > 0 && (A.feat_out || (A.mlp && X.n_compat >= 2));
                 const int ly = X.layer >= 0 ? X.layer : 0;
                 const LayerDesc &Ld = G.L[ly];
@@ -978,6 +1011,89 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     }
 }
 
+// Ordered compaction of the seeds whose status has any of `bits` (ascending
+// seed index, so a following seed-list call keeps the events' seeds together):
+// per tile of kWhereTile seeds a count, one exclusive scan over the tiles, then
+// each tile writes its seeds at its offset in order.
+constexpr int kWhereThreads = 256, kWherePer = 4, kWhereTile = kWhereThreads * kWherePer;
+
+__device__ __forceinline__ int where_flags(const uint32_t *status, int n, uint32_t bits, int first, bool f[kWherePer]) {
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < kWherePer; ++k) {
+        const int i = first + k;
+        f[k] = i < n && (status[i] & bits) != 0u;
+        c += f[k] ? 1 : 0;
+    }
+    return c;
+}
+
+// Exclusive prefix of v over the block's threads (kWhereThreads); total in *tot.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int *tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(kFull, x, off);
+        if (lane >= off) x += o;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < kWhereThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(kFull, s, off);
+            if (lane >= off) s += o;
+        }
+        if (lane < kWhereThreads / 32) warp_sums[lane] = s;  // inclusive warp totals
+    }
+    __syncthreads();
+    const int before = (w > 0 ? warp_sums[w - 1] : 0) + x - v;
+    *tot = warp_sums[kWhereThreads / 32 - 1];
+    return before;
+}
+
+__global__ void __launch_bounds__(kWhereThreads) where_count_kernel(const uint32_t *status, int n, uint32_t bits,
+                                                                    int32_t *tile_counts) {
+    __shared__ int warp_sums[kWhereThreads / 32];
+    bool f[kWherePer];
+    const int c = where_flags(status, n, bits, blockIdx.x * kWhereTile + threadIdx.x * kWherePer, f);
+    int tot;
+    block_exclusive_scan(c, warp_sums, &tot);
+    if (threadIdx.x == 0) tile_counts[blockIdx.x] = tot;
+}
+
+// One block: tile counts -> exclusive offsets (in place), the total to *count.
+__global__ void __launch_bounds__(kWhereThreads) where_scan_kernel(int32_t *tile_counts, int n_tiles,
+                                                                   int32_t *count) {
+    __shared__ int warp_sums[kWhereThreads / 32];
+    int carry = 0;
+    for (int base = 0; base < n_tiles; base += kWhereThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < n_tiles ? tile_counts[i] : 0;
+        int tot;
+        const int ex = block_exclusive_scan(v, warp_sums, &tot);
+        if (i < n_tiles) tile_counts[i] = carry + ex;
+        carry += tot;
+        __syncthreads();  // warp_sums reused by the next chunk
+    }
+    if (threadIdx.x == 0) *count = carry;
+}
+
+__global__ void __launch_bounds__(kWhereThreads) where_write_kernel(const uint32_t *status, int n, uint32_t bits,
+                                                                    const int32_t *tile_offsets, int32_t *list) {
+    __shared__ int warp_sums[kWhereThreads / 32];
+    bool f[kWherePer];
+    const int first = blockIdx.x * kWhereTile + threadIdx.x * kWherePer;
+    const int c = where_flags(status, n, bits, first, f);
+    int tot;
+    int at = tile_offsets[blockIdx.x] + block_exclusive_scan(c, warp_sums, &tot);
+#pragma unroll
+    for (int k = 0; k < kWherePer; ++k)
+        if (f[k]) list[at++] = first + k;
+}
+
 // steps: at most one per layer + one final step with no layer left
 int find_max_steps(int n_layers) { return n_layers + 2; }
 
@@ -1039,6 +1155,12 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     A.feat_count = params->feat_count;
     A.feat_cap = params->feat_cap;
     if (A.feat_out && (!A.feat_ref || !A.feat_count || A.feat_cap < 0)) return MKF_ERR_ARG;
+    if ((params->seed_list == nullptr) != (params->seed_count == nullptr)) return MKF_ERR_ARG;
+    if (params->mlp_mode != 0 && params->mlp_mode != 1) return MKF_ERR_ARG;
+    if (params->mlp_mode == 1 && (!params->mlp_bf16 || params->feat_out)) return MKF_ERR_ARG;
+    A.seed_list = params->seed_list;
+    A.seed_count = params->seed_count;
+    A.mlp_mode = params->mlp_mode;
     const size_t smem = find_smem_bytes(ctx->geom.n_layers, N, threads);
     if (smem > 200 * 1024) return MKF_ERR_CAPACITY;
     // raise the kernel's dynamic shared-memory limit only when needed (not during
@@ -1108,6 +1230,29 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
         case 4: find_kernel<true, 1><<<blocks, threads, smem, ctx->stream>>>(A); break;
         default: find_kernel<true, 2><<<blocks, threads, smem, ctx->stream>>>(A); break;
     }
+    MKF_CUDA_TRY(cudaGetLastError());
+    return MKF_OK;
+}
+
+extern "C" mkf_status mkf_seeds_where(mkf_ctx *ctx, const uint32_t *status, int32_t n, uint32_t bits,
+                                      int32_t *seed_list, int32_t *seed_count) {
+    if (!ctx || n < 0 || !seed_count || (n > 0 && (!status || !seed_list))) return MKF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return MKF_ERR_CUDA;
+    if (n == 0) {
+        MKF_CUDA_TRY(cudaMemsetAsync(seed_count, 0, sizeof(int32_t), ctx->stream));
+        return MKF_OK;
+    }
+    const int n_tiles = (n + kWhereTile - 1) / kWhereTile;
+    // the tile counts live in the context's scratch (which a finding call with
+    // these seeds has already sized far beyond them)
+    void *scratch = nullptr;
+    mkf_status st = mkf_scratch(ctx, sizeof(int32_t) * (size_t)n_tiles, &scratch);
+    if (st != MKF_OK) return st;
+    int32_t *tiles = static_cast<int32_t *>(scratch);
+    where_count_kernel<<<n_tiles, kWhereThreads, 0, ctx->stream>>>(status, n, bits, tiles);
+    where_scan_kernel<<<1, kWhereThreads, 0, ctx->stream>>>(tiles, n_tiles, seed_count);
+    where_write_kernel<<<n_tiles, kWhereThreads, 0, ctx->stream>>>(status, n, bits, tiles, seed_list);
     MKF_CUDA_TRY(cudaGetLastError());
     return MKF_OK;
 }

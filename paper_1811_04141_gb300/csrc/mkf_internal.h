@@ -22,6 +22,7 @@ enum : int {
     kFaultBadSeedHit = 3,     // seed hit index out of range
     kFaultHistOverflow = 4,   // candidate history longer than reserved
     kFaultBadHitIndex = 5,    // fit hit index out of range
+    kFaultBadSeedList = 6,    // finder seed-list entry out of range
 };
 
 struct mkf_ctx {

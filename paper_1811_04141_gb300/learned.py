@@ -9,6 +9,12 @@ buffers and draws the batch permutation), and the pruning threshold is the
 largest one that keeps the finding efficiency within a tolerance of the plain
 finder.  The plain chi2 selection stays the reference: efficiency and fake rate
 are computed from the found hit lists and the truth.
+
+Two uses of the trained network: pruning inside the N-best finder (pairs
+below the threshold dropped before the selection), and the cascade
+(`cascade`): best-hit finding of every seed with the network as a gate on its
+best-chi2 extensions, then N-best finding, with the plain chi2 selection, of
+the seeds whose extensions it doubted.
 """
 from __future__ import annotations
 
@@ -92,3 +98,28 @@ def choose_tau(run_find, eff_plain: float, taus, tolerance: float = 0.005):
         if eff >= eff_plain - tolerance:
             best = (tau, eff, fake)
     return best
+
+
+def cascade(ctx, bins, seed_hits, seed_event, w_bf16, tau, n_best=10, out=None, subset=None, **find_kw):
+    """The learned cascade, all on the device: best-hit finding of every seed
+    with the MLP gate (a seed is flagged when, on a layer where its candidate
+    has two or more compatible hits, the best one by chi2 scores below tau),
+    then N-best finding of the flagged seeds only, written over their best-hit
+    results.  Returns (out, (seed_list, seed_count)); pass both back in (`out`,
+    `subset`) to reuse the buffers (e.g. inside a CUDA graph capture)."""
+    out = ctx.find(bins, seed_hits, seed_event, n_best=1, mlp_bf16=w_bf16, mlp_tau=tau, mlp_mode=1, out=out,
+                   **find_kw)
+    lst, cnt = ctx.seeds_where(out["status"], N.ST_AMBIG, *(subset or (None, None)))
+    ctx.find(bins, seed_hits, seed_event, n_best=n_best, out=out, seed_list=lst, seed_count=cnt, **find_kw)
+    return out, (lst, cnt)
+
+
+def choose_gate_tau(run_cascade, eff_plain: float, fake_plain: float, taus, tolerance: float = 0.005):
+    """Smallest gate threshold (fewest seeds sent to N-best finding) whose
+    efficiency and fake rate stay within `tolerance` of the plain finder's.
+    run_cascade(tau) -> (efficiency, fake rate)."""
+    for tau in sorted(taus):
+        eff, fake = run_cascade(tau)
+        if eff >= eff_plain - tolerance and fake <= fake_plain + tolerance:
+            return tau, eff, fake
+    return None
