@@ -677,7 +677,7 @@ def run_ours(args, world, rank, local, pg):
     import torch
 
     from paper_1811_04141_gb300 import Context, build, flops
-    from paper_1811_04141_gb300.runtime import CapturedStep, tune_find_block
+    from paper_1811_04141_gb300.runtime import CapturedStep, tune_find_config
 
     if local == 0 or world == 1:
         build.build()
@@ -708,12 +708,13 @@ def run_ours(args, world, rank, local, pg):
     derived = flops.fp32_peak_tflops(sm_count, 2070.0)
     peak_tflops = peak["tflops"] if peak else derived
 
-    # finder launch from the autotuner (cached per GPU, geometry and size)
-    bins = ctx.hits_bin(xyz, layer, evo)
+    # hit-bin grid and finder launch from the autotuner (cached per GPU,
+    # geometry, size and occupancy)
     if args.block_threads:
-        bt, tune = args.block_threads, {"ms": None, "fixed": True}
+        bt, tune = args.block_threads, {"ms": None, "fixed": True, "grid": None}
     else:
-        bt, tune = tune_find_block(ctx, bins, sh, se, n_best=NB, **fkw)
+        _, bt, tune = tune_find_config(ctx, batch.layers, batch.bz, xyz, layer, evo, sh, se, n_best=NB, **fkw)
+    bins = ctx.hits_bin(xyz, layer, evo)
     fkw["block_threads"] = bt
 
     # eager launches with events between the stages: binning and mkf_find times
@@ -830,7 +831,8 @@ def run_ours(args, world, rank, local, pg):
                                         "basis": "GPU global timer at each event's last seed output, from the "
                                                  "finder's first block"},
                    "launch": "binning + finding captured in one CUDA graph, replayed per step",
-                   "autotune": {"block_threads": bt, "ms_by_block_threads": tune.get("ms")},
+                   "autotune": {"grid": tune.get("grid"), "block_threads": bt,
+                                "ms_by_grid_and_block": tune.get("ms"), "spread": tune.get("spread")},
                    "l2": "inputs (~0.9 GB) larger than L2, and a 256 MiB write between steps outside the events",
                    "generation_s": round(gen_s, 1), "wall_s_timed_region": round(wall, 3),
                    "parallelism": f"events sharded, {world} GPU(s)"},

@@ -1,5 +1,5 @@
 """Runtime helpers around the C ABI: a finding step captured in a CUDA graph,
-and a block-size autotuner for the finder.
+and autotuners for the finder's launch and the hit-bin grid.
 
 A captured step replays hit binning and finding on fixed device buffers with a
 single graph launch; the library performs no allocation or host
@@ -91,3 +91,69 @@ def tune_find_block(ctx, bins, seed_hits, seed_event, n_best=10, candidates=(64,
         except OSError:
             pass
     return best, rec
+
+
+GRIDS = ((128, 16), (256, 16), (256, 32), (512, 32))
+BLOCKS = (128, 256)
+
+
+def _occupancy_key(ctx, n_layers, n_best, n_seeds, n_hits, n_events):
+    name = torch.cuda.get_device_name(ctx.device)
+    b = lambda x: 1 << max(0, int(x).bit_length() - 1)
+    return (f"{name}|L{n_layers}|N{n_best}|S{b(n_seeds)}|H/ev{b(n_hits // max(1, n_events))}"
+            f"|S/ev{b(n_seeds // max(1, n_events))}")
+
+
+def tune_find_config(ctx, layers, bz, xyz, layer, event_offsets, seed_hits, seed_event, n_best=10, grids=GRIDS,
+                     blocks=BLOCKS, reps=3, cache=True, **find_kw):
+    """Hit-bin grid (the same n_phi x n_zr on every layer) and finder block size
+    of the fastest binning + finding step, timed with CUDA events on this
+    workload; cached by GPU, layer count, N, seed count and occupancy (hits and
+    seeds per event, powers of two).  Leaves the chosen grid loaded in `ctx`
+    (bins made before are then stale) and returns (layers with that grid,
+    block size, record with every configuration's time)."""
+    n_events = event_offsets.shape[0] - 1
+    key = "cfg|" + _occupancy_key(ctx, len(layers), n_best, seed_hits.shape[1], xyz.shape[1], n_events)
+    table = {}
+    if cache and os.path.exists(_CACHE):
+        try:
+            with open(_CACHE) as fh:
+                table = json.load(fh)
+        except (OSError, ValueError):
+            table = {}
+    with_grid = lambda g: [dict(d, n_phi=int(g[0]), n_zr=int(g[1])) for d in layers]
+    if key in table:
+        rec = table[key]
+        ctx.geometry_load(with_grid(rec["grid"]), bz)
+        return with_grid(rec["grid"]), int(rec["block_threads"]), rec
+    times = {}
+    for g in grids:
+        ctx.geometry_load(with_grid(g), bz)
+        bins = ctx.hits_bin(xyz, layer, event_offsets)
+        out = None
+        for bt in blocks:
+            out = ctx.find(bins, seed_hits, seed_event, n_best=n_best, block_threads=bt, out=out, **find_kw)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                ctx.hits_bin(xyz, layer, event_offsets, bins)
+                ctx.find(bins, seed_hits, seed_event, n_best=n_best, block_threads=bt, out=out, **find_kw)
+            b.record()
+            torch.cuda.synchronize()
+            times[f"{g[0]}x{g[1]}|{bt}"] = a.elapsed_time(b) / reps
+        del bins, out
+    best = min(times, key=times.get)
+    gs, bt = best.split("|")
+    grid = tuple(int(x) for x in gs.split("x"))
+    rec = {"grid": list(grid), "block_threads": int(bt), "ms": times,
+           "spread": max(times.values()) / min(times.values()) - 1.0}
+    if cache:
+        table[key] = rec
+        try:
+            with open(_CACHE, "w") as fh:
+                json.dump(table, fh, indent=1)
+        except OSError:
+            pass
+    ctx.geometry_load(with_grid(grid), bz)
+    return with_grid(grid), int(bt), rec
