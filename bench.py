@@ -711,11 +711,12 @@ def run_ours(args, world, rank, local, pg):
     # hit-bin grid and finder launch from the autotuner (cached per GPU,
     # geometry, size and occupancy)
     if args.block_threads:
-        bt, tune = args.block_threads, {"ms": None, "fixed": True, "grid": None}
+        bt, tune = args.block_threads, {"ms": None, "fixed": True, "grid": None, "seed_order": 0}
     else:
         _, bt, tune = tune_find_config(ctx, batch.layers, batch.bz, xyz, layer, evo, sh, se, n_best=NB, **fkw)
     bins = ctx.hits_bin(xyz, layer, evo)
     fkw["block_threads"] = bt
+    fkw["seed_order"] = tune.get("seed_order", 0)
 
     # eager launches with events between the stages: binning and mkf_find times
     out = ctx.find(bins, sh, se, n_best=NB, **fkw)
@@ -794,7 +795,7 @@ def run_ours(args, world, rank, local, pg):
     e2e = None
     if not args.no_e2e:
         e2e = e2e_pipelined(ctx, batch, bins, NB, max_out, K, max(3, args.warmup), units_all, pg, dev,
-                            find_kw={"block_threads": bt})
+                            find_kw={"block_threads": bt, "seed_order": fkw["seed_order"]})
         ctx.set_stream(stream)
     ctx.close()
 
@@ -831,7 +832,7 @@ def run_ours(args, world, rank, local, pg):
                                         "basis": "GPU global timer at each event's last seed output, from the "
                                                  "finder's first block"},
                    "launch": "binning + finding captured in one CUDA graph, replayed per step",
-                   "autotune": {"grid": tune.get("grid"), "block_threads": bt,
+                   "autotune": {"grid": tune.get("grid"), "block_threads": bt, "seed_order": fkw["seed_order"],
                                 "ms_by_grid_and_block": tune.get("ms"), "spread": tune.get("spread")},
                    "l2": "inputs (~0.9 GB) larger than L2, and a 256 MiB write between steps outside the events",
                    "generation_s": round(gen_s, 1), "wall_s_timed_region": round(wall, 3),

@@ -53,7 +53,7 @@ class MkfFindParams(C.Structure):
                 ("block_threads", C.c_int32), ("mlp_bf16", C.c_void_p), ("mlp_tau", C.c_float),
                 ("feat_out", C.c_void_p), ("feat_ref", C.c_void_p), ("feat_count", C.c_void_p),
                 ("feat_cap", C.c_int32), ("event_times", C.c_void_p), ("seed_list", C.c_void_p),
-                ("seed_count", C.c_void_p), ("mlp_mode", C.c_int32)]
+                ("seed_count", C.c_void_p), ("mlp_mode", C.c_int32), ("seed_order", C.c_int32)]
 
 
 MLP_IN = 12

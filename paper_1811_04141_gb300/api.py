@@ -300,12 +300,14 @@ def mkf_tracks_dedup(ctx, hit_idx, n_hits, track_nhits, chi2, min_frac=0.5, keep
 
 
 def find_params(n_best=10, chi2_cut=30.0, max_consec_miss=3, block_threads=0, mlp_bf16=None, mlp_tau=0.0,
-                feat=None, event_times=None, seed_list=None, seed_count=None, mlp_mode=0) -> N.MkfFindParams:
+                feat=None, event_times=None, seed_list=None, seed_count=None, mlp_mode=0,
+                seed_order=0) -> N.MkfFindParams:
     prm = N.MkfFindParams(int(n_best), float(chi2_cut), int(max_consec_miss), int(block_threads))
     if seed_list is not None:
         prm.seed_list = seed_list.data_ptr()
         prm.seed_count = seed_count.data_ptr()
     prm.mlp_mode = int(mlp_mode)
+    prm.seed_order = int(seed_order)
     if event_times is not None:
         prm.event_times = event_times.data_ptr()
     if mlp_bf16 is not None:
@@ -327,7 +329,7 @@ def feature_buffer(cap: int, device="cuda") -> dict:
 
 def mkf_find(ctx, bins: HitBins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
              n_layers=None, out=None, counters=True, block_threads=0, device: int | None = None, mlp_bf16=None,
-             mlp_tau=0.0, feat=None, event_times=None, seed_list=None, seed_count=None, mlp_mode=0):
+             mlp_tau=0.0, feat=None, event_times=None, seed_list=None, seed_count=None, mlp_mode=0, seed_order=0):
     """Find tracks; returns dict(par, cov, chi2, n_hits, hits [max_out, n], status, counters [3, n]).
     mlp_bf16 (int16 tensor of MLP_PARAMS bfloat16 patterns) turns on learned pruning at mlp_tau
     (mlp_mode 1: the gate, flagging seeds instead of dropping hits); feat (from feature_buffer)
@@ -360,7 +362,7 @@ def mkf_find(ctx, bins: HitBins, seed_hits, seed_event, n_best=10, chi2_cut=30.0
     if event_times is not None:
         _need(event_times, "event_times", torch.int64, None, device)
     prm = find_params(n_best, chi2_cut, max_consec_miss, block_threads, mlp_bf16, mlp_tau, feat, event_times,
-                      seed_list, seed_count, mlp_mode)
+                      seed_list, seed_count, mlp_mode, seed_order)
     N.check("mkf_find", N.lib().mkf_find(_h(ctx), bins.handle, _ptr(seed_hits), _ptr(seed_event), n, C.byref(prm),
                                          _ptr(out["par"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out["n_hits"]),
                                          _ptr(out["hits"]), int(out["hits"].shape[0]), _ptr(out["status"]),
@@ -495,11 +497,11 @@ class Context:
 
     def find(self, bins, seed_hits, seed_event, n_best=10, chi2_cut=30.0, max_consec_miss=3, max_out=None,
              out=None, counters=True, block_threads=0, mlp_bf16=None, mlp_tau=0.0, feat=None, event_times=None,
-             seed_list=None, seed_count=None, mlp_mode=0):
+             seed_list=None, seed_count=None, mlp_mode=0, seed_order=0):
         nl = len(self.layers) if self.layers else None
         return mkf_find(self.handle, bins, seed_hits, seed_event, n_best, chi2_cut, max_consec_miss, max_out, nl, out,
                         counters, block_threads, self.device, mlp_bf16, mlp_tau, feat, event_times, seed_list,
-                        seed_count, mlp_mode)
+                        seed_count, mlp_mode, seed_order)
 
     def seeds_where(self, status, bits, seed_list=None, seed_count=None):
         return mkf_seeds_where(self.handle, status, bits, seed_list, seed_count)

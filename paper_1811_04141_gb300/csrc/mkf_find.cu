@@ -71,7 +71,17 @@ struct FindArgs {
     const int32_t *seed_list;             // seeds to find (or nullptr: all), *seed_count of them
     const int32_t *seed_count;
     int32_t mlp_mode;                     // 0 prune, 1 gate (flag MKF_ST_AMBIG, drop nothing)
+    // processing order grouped by event and |eta| of the seed (or nullptr):
+    // the seed kernel writes each seed's key and place, order_scatter_kernel
+    // the order the finder's warps take the seeds in
+    int32_t *order_key, *order_pos, *order_counts;
 };
+
+// Seeds are taken by the finder grouped by event and by the |eta| of their
+// three-hit estimate in bins of 0.25 (16 bins): a warp's seeds then have
+// similar numbers of layers ahead, so fewer lanes idle while the longest one
+// ends (5 % on the uneven dense events), and each event's hits stay together.
+constexpr int kOrderBuckets = 16;
 
 // Number of seeds this call finds: all of them, or the device-side count of
 // the seed list (clamped to n_seeds).
@@ -504,6 +514,12 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
     }
     ok = ok && finite_state(p);
     uint32_t status = ok ? 0u : MKF_ST_BADSEED;
+    if (A.order_key) {
+        const int key = (ev >= 0 && ev < A.n_events ? ev : 0) * kOrderBuckets +
+                        (ok ? min(static_cast<int>(fabsf(eta) * 4.f), kOrderBuckets - 1) : 0);
+        A.order_key[t] = key;
+        A.order_pos[t] = atomicAdd(&A.order_counts[key], 1);
+    }
     unsigned long long mask = 0;
     int dir = 1;
     Book bk{3, 0, -1, -1, false, false, 0};
@@ -1011,6 +1027,14 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
     }
 }
 
+// The finder's processing order from the seed kernel's keys and places
+// (order_counts scanned into offsets; the last entry holds the total).
+__global__ void __launch_bounds__(256) order_scatter_kernel(const int32_t *key, const int32_t *pos,
+                                                            const int32_t *offsets, int n, int32_t *order) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) order[offsets[key[t]] + pos[t]] = t;
+}
+
 // Ordered compaction of the seeds whose status has any of `bits` (ascending
 // seed index, so a following seed-list call keeps the events' seeds together):
 // per tile of kWhereTile seeds a count, one exclusive scan over the tiles, then
@@ -1158,6 +1182,8 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     if ((params->seed_list == nullptr) != (params->seed_count == nullptr)) return MKF_ERR_ARG;
     if (params->mlp_mode != 0 && params->mlp_mode != 1) return MKF_ERR_ARG;
     if (params->mlp_mode == 1 && (!params->mlp_bf16 || params->feat_out)) return MKF_ERR_ARG;
+    if (params->seed_order != 0 && params->seed_order != 1) return MKF_ERR_ARG;
+    const bool grouped = params->seed_order == 0 && !params->seed_list;
     A.seed_list = params->seed_list;
     A.seed_count = params->seed_count;
     A.mlp_mode = params->mlp_mode;
@@ -1191,11 +1217,25 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     A.step1 = learned ? 0 : 1;
     const size_t beam_bytes =
         A.step1 ? ((sizeof(float) * (size_t)kListFields * n_seeds * N + 255) / 256) * 256 : 0;
-    mkf_status st = mkf_scratch(ctx, seed_bytes + beam_bytes + 256, &scratch);
+    // the processing order (grouped by event and |eta|): keys, places, order, key counts
+    const int n_keys = bins->n_events * kOrderBuckets;
+    const size_t order_bytes =
+        grouped ? ((sizeof(int32_t) * (3 * (size_t)n_seeds + n_keys + 1) + 255) / 256) * 256 : 0;
+    mkf_status st = mkf_scratch(ctx, seed_bytes + beam_bytes + order_bytes + 256, &scratch);
     if (st != MKF_OK) return st;
     A.seedbuf = static_cast<float *>(scratch);
     A.beam = A.step1 ? reinterpret_cast<float *>(static_cast<char *>(scratch) + seed_bytes) : nullptr;
-    A.work_counter = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + seed_bytes + beam_bytes);
+    A.work_counter = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + seed_bytes + beam_bytes + order_bytes);
+    int32_t *order = nullptr;
+    A.order_key = A.order_pos = A.order_counts = nullptr;
+    if (grouped) {
+        int32_t *ob = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + seed_bytes + beam_bytes);
+        A.order_key = ob;
+        A.order_pos = ob + n_seeds;
+        order = ob + 2 * (size_t)n_seeds;
+        A.order_counts = ob + 3 * (size_t)n_seeds;
+        MKF_CUDA_TRY(cudaMemsetAsync(A.order_counts, 0, sizeof(int32_t) * (n_keys + 1), ctx->stream));
+    }
     A.event_times = reinterpret_cast<unsigned long long *>(params->event_times);
     MKF_CUDA_TRY(cudaMemsetAsync(A.work_counter, 0, sizeof(int32_t), ctx->stream));
     if (A.event_times) {
@@ -1207,6 +1247,17 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     else
         seed_kernel<false><<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A);
     MKF_CUDA_TRY(cudaGetLastError());
+    if (grouped) {
+        // key counts -> offsets (the total, n_seeds, lands in the last entry),
+        // then the order; the finder takes the seeds through it
+        where_scan_kernel<<<1, kWhereThreads, 0, ctx->stream>>>(A.order_counts, n_keys, A.order_counts + n_keys);
+        order_scatter_kernel<<<(n_seeds + 255) / 256, 256, 0, ctx->stream>>>(A.order_key, A.order_pos,
+                                                                              A.order_counts, n_seeds, order);
+        MKF_CUDA_TRY(cudaGetLastError());
+        A.order_key = nullptr;  // the finder writes no keys
+        A.seed_list = order;
+        A.seed_count = A.order_counts + n_keys;
+    }
     // persistent grid: as many blocks as fit on the device at once, or fewer
     const int spw = 32 / N;
     const int seeds_per_block = spw * (threads / 32);

@@ -95,6 +95,7 @@ def tune_find_block(ctx, bins, seed_hits, seed_event, n_best=10, candidates=(64,
 
 GRIDS = ((128, 16), (256, 16), (256, 32), (512, 32))
 BLOCKS = (128, 256)
+ORDERS = (0, 1)  # seeds grouped by event and |eta| (the finder's default), input order
 
 
 def _occupancy_key(ctx, n_layers, n_best, n_seeds, n_hits, n_events):
@@ -105,13 +106,14 @@ def _occupancy_key(ctx, n_layers, n_best, n_seeds, n_hits, n_events):
 
 
 def tune_find_config(ctx, layers, bz, xyz, layer, event_offsets, seed_hits, seed_event, n_best=10, grids=GRIDS,
-                     blocks=BLOCKS, reps=3, cache=True, **find_kw):
-    """Hit-bin grid (the same n_phi x n_zr on every layer) and finder block size
-    of the fastest binning + finding step, timed with CUDA events on this
-    workload; cached by GPU, layer count, N, seed count and occupancy (hits and
-    seeds per event, powers of two).  Leaves the chosen grid loaded in `ctx`
-    (bins made before are then stale) and returns (layers with that grid,
-    block size, record with every configuration's time)."""
+                     blocks=BLOCKS, orders=ORDERS, reps=3, cache=True, **find_kw):
+    """Hit-bin grid (the same n_phi x n_zr on every layer), finder block size
+    and seed order of the fastest binning + finding step, timed with CUDA
+    events on this workload; cached by GPU, layer count, N, seed count and
+    occupancy (hits and seeds per event, powers of two).  Leaves the chosen grid
+    loaded in `ctx` (bins made before are then stale) and returns (layers with
+    that grid, block size, record with every configuration's time and the
+    chosen seed_order)."""
     n_events = event_offsets.shape[0] - 1
     key = "cfg|" + _occupancy_key(ctx, len(layers), n_best, seed_hits.shape[1], xyz.shape[1], n_events)
     table = {}
@@ -132,21 +134,23 @@ def tune_find_config(ctx, layers, bz, xyz, layer, event_offsets, seed_hits, seed
         bins = ctx.hits_bin(xyz, layer, event_offsets)
         out = None
         for bt in blocks:
-            out = ctx.find(bins, seed_hits, seed_event, n_best=n_best, block_threads=bt, out=out, **find_kw)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            for _ in range(reps):
-                ctx.hits_bin(xyz, layer, event_offsets, bins)
-                ctx.find(bins, seed_hits, seed_event, n_best=n_best, block_threads=bt, out=out, **find_kw)
-            b.record()
-            torch.cuda.synchronize()
-            times[f"{g[0]}x{g[1]}|{bt}"] = a.elapsed_time(b) / reps
+            for so in orders:
+                kw = dict(find_kw, block_threads=bt, seed_order=so)
+                out = ctx.find(bins, seed_hits, seed_event, n_best=n_best, out=out, **kw)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(reps):
+                    ctx.hits_bin(xyz, layer, event_offsets, bins)
+                    ctx.find(bins, seed_hits, seed_event, n_best=n_best, out=out, **kw)
+                b.record()
+                torch.cuda.synchronize()
+                times[f"{g[0]}x{g[1]}|{bt}|{so}"] = a.elapsed_time(b) / reps
         del bins, out
     best = min(times, key=times.get)
-    gs, bt = best.split("|")
+    gs, bt, so = best.split("|")
     grid = tuple(int(x) for x in gs.split("x"))
-    rec = {"grid": list(grid), "block_threads": int(bt), "ms": times,
+    rec = {"grid": list(grid), "block_threads": int(bt), "seed_order": int(so), "ms": times,
            "spread": max(times.values()) / min(times.values()) - 1.0}
     if cache:
         table[key] = rec

@@ -95,6 +95,11 @@ template <class T> T __shfl_down_sync(unsigned m, T v, unsigned off) {
     const int s = l + static_cast<int>(off);
     return __shfl_sync(m, v, s > 31 ? l : s);
 }
+template <class T> T __shfl_up_sync(unsigned m, T v, unsigned off) {
+    const int l = threadIdx.x & 31;
+    const int s = l - static_cast<int>(off);
+    return __shfl_sync(m, v, s < 0 ? l : s);
+}
 inline unsigned __ballot_sync(unsigned, bool p) {
     g_warp->v[threadIdx.x & 31] = p ? 1 : 0;
     g_warp->sync();

@@ -136,8 +136,8 @@ def _oracle_gate_scores(b, w):
 def test_gate_flags_match_oracle_and_leave_tracks_unchanged():
     """Gate mode (best-hit finding with the MLP on each candidate's best
     compatible hit): the seeds it flags equal the oracle's except where a score
-    is within TIE_MLP of the threshold, and the tracks are those of plain
-    best-hit finding, bit for bit."""
+    is within TIE_MLP of the threshold, and the tracks are those of the same
+    kernel without the gate, bit for bit."""
     from paper_1811_04141_gb300 import _native as NN
     from paper_1811_04141_gb300.api import mkf_mlp_to_bf16
     b = make_batch("dense45", [53], n_tracks=500, n_noise=60000, material=0.02, eloss=0.04)
@@ -150,8 +150,10 @@ def test_gate_flags_match_oracle_and_leave_tracks_unchanged():
     margin = np.full(b.n_seeds, np.inf)
     np.logical_or.at(flag_ref, seeds, logit < tau)
     np.minimum.at(margin, seeds, np.abs(logit - tau))
+    from paper_1811_04141_gb300.api import feature_buffer
     gated, _ = _gpu(ctx, b, n_best=1, mlp_bf16=wb, mlp_tau=tau, mlp_mode=1)
-    plain, _ = _gpu(ctx, b, n_best=1)
+    # the same kernel variant without the gate (feature dump, nothing pruned)
+    plain, _ = _gpu(ctx, b, n_best=1, feat=feature_buffer(1 << 20))
     gated, plain = to_np(gated), to_np(plain)
     for k in ("hits", "n_hits", "counters"):
         assert np.array_equal(gated[k], plain[k]), k

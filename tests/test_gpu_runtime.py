@@ -49,9 +49,10 @@ def test_autotuner_picks_a_valid_block_size():
 
 
 def test_config_autotuner_grid_and_block():
-    """The configuration tuner times every (bin grid, block size) pair, loads the
-    fastest grid, and the tracks found with it equal those of the default grid
-    bit for bit (the grid only accelerates the window search)."""
+    """The configuration tuner times every (bin grid, block size, seed order),
+    loads the fastest grid, and the tracks found with its choice equal those of
+    the default configuration bit for bit (the grid only accelerates the window
+    search, the order only schedules the seeds)."""
     from paper_1811_04141_gb300.runtime import tune_find_config
     b = make_batch("dense45", [63, 64], n_tracks=800, n_noise=40000)
     ctx = make_ctx(b)
@@ -63,11 +64,12 @@ def test_config_autotuner_grid_and_block():
     ref = {k: v.clone() for k, v in ref.items() if v is not None}
     layers, bt, rec = tune_find_config(ctx, b.layers, b.bz, d["xyz"], d["layer"], d["event_offsets"],
                                        d["seed_hits"], d["seed_event"], n_best=10, cache=False, max_out=mo)
-    assert len(rec["ms"]) == 8 and bt in (128, 256) and rec["spread"] > 0
+    assert len(rec["ms"]) == 16 and bt in (128, 256) and rec["seed_order"] in (0, 1) and rec["spread"] > 0
     assert all(l["n_phi"] == rec["grid"][0] and l["n_zr"] == rec["grid"][1] for l in layers)
     assert ctx.layers[0]["n_phi"] == rec["grid"][0]
     bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
-    out = ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=10, block_threads=bt, max_out=mo)
+    out = ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=10, block_threads=bt, max_out=mo,
+                   seed_order=rec["seed_order"])
     ctx.sync()
     for k in ("hits", "n_hits", "status"):
         assert torch.equal(out[k], ref[k]), k
