@@ -410,7 +410,7 @@ typedef struct {
     /* Order in which the seeds are worked on (results do not depend on it):
      * 0 (default) grouped by event and by |eta| of the seed's three-hit
      * estimate (bins of 0.25), so that the seeds sharing a warp have similar
-     * numbers of layers ahead; 1 the input order.  With seed_list, its order. */
+     * numbers of layers ahead; 1 the input order (with seed_list: its order). */
     int32_t seed_order;
 } mkf_find_params;
 

@@ -1028,11 +1028,16 @@ __global__ void __launch_bounds__(256, 2) find_kernel(const __grid_constant__ Fi
 }
 
 // The finder's processing order from the seed kernel's keys and places
-// (order_counts scanned into offsets; the last entry holds the total).
+// (order_counts scanned into offsets; the last entry holds the total): over
+// every seed, or over the seeds of a seed list.
 __global__ void __launch_bounds__(256) order_scatter_kernel(const int32_t *key, const int32_t *pos,
-                                                            const int32_t *offsets, int n, int32_t *order) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) order[offsets[key[t]] + pos[t]] = t;
+                                                            const int32_t *offsets, int n, const int32_t *list,
+                                                            const int32_t *list_count, int32_t *order) {
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    const int count = list ? min(max(*list_count, 0), n) : n;
+    if (li >= count) return;
+    const int t = list ? list[li] : li;
+    if (t >= 0 && t < n) order[offsets[key[t]] + pos[t]] = t;
 }
 
 // Ordered compaction of the seeds whose status has any of `bits` (ascending
@@ -1183,7 +1188,7 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
     if (params->mlp_mode != 0 && params->mlp_mode != 1) return MKF_ERR_ARG;
     if (params->mlp_mode == 1 && (!params->mlp_bf16 || params->feat_out)) return MKF_ERR_ARG;
     if (params->seed_order != 0 && params->seed_order != 1) return MKF_ERR_ARG;
-    const bool grouped = params->seed_order == 0 && !params->seed_list;
+    const bool grouped = params->seed_order == 0;
     A.seed_list = params->seed_list;
     A.seed_count = params->seed_count;
     A.mlp_mode = params->mlp_mode;
@@ -1251,8 +1256,8 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
         // key counts -> offsets (the total, n_seeds, lands in the last entry),
         // then the order; the finder takes the seeds through it
         where_scan_kernel<<<1, kWhereThreads, 0, ctx->stream>>>(A.order_counts, n_keys, A.order_counts + n_keys);
-        order_scatter_kernel<<<(n_seeds + 255) / 256, 256, 0, ctx->stream>>>(A.order_key, A.order_pos,
-                                                                              A.order_counts, n_seeds, order);
+        order_scatter_kernel<<<(n_seeds + 255) / 256, 256, 0, ctx->stream>>>(
+            A.order_key, A.order_pos, A.order_counts, n_seeds, A.seed_list, A.seed_count, order);
         MKF_CUDA_TRY(cudaGetLastError());
         A.order_key = nullptr;  // the finder writes no keys
         A.seed_list = order;
