@@ -530,11 +530,12 @@ def physics_leg(dev, n_events: int = 5, per_event: int = 10000, reps: int = 10):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one mkf_find call
-# (seed_kernel + find_kernel) per candidate-layer it processes, from a one-pass
-# ncu capture of the current kernels on a 48-event subset of the uneven dense
-# workload (the whole 512 events exceed the capture size rule); traffic grows
-# with the candidate-layers processed.  None: not measured for this version.
-FIND_DRAM_BYTES_PER_CAND_LAYER = None
+# (seed_kernel, the order's scan and scatter, find_kernel) per candidate-layer it
+# processes, from a one-pass ncu capture of the current kernels on 96 of the 512
+# uneven dense events (the whole workload exceeds the capture size rule): 619.6 MB
+# for 46.5 M candidate-layers (profiles/find_kernel.c4_96events.md); the traffic
+# (hit records, seed records, outputs) grows with the candidate-layers processed.
+FIND_DRAM_BYTES_PER_CAND_LAYER = 13.32
 
 
 def _carve(arena, specs):
@@ -815,7 +816,7 @@ def run_ours(args, world, rank, local, pg):
         if args.physics:
             extras["physics"] = physics_leg(dev)
 
-    launches_per_step = 6  # bin_keys, scan_tiles, scan_write, scatter, seed, find
+    launches_per_step = 8  # bin_keys, scan_tiles, scan_write, scatter, seed, where_scan, order_scatter, find
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(step_ms_max, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
