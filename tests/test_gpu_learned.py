@@ -265,3 +265,41 @@ def test_learned_cascade_beats_plain_finder_with_material():
     print(f"cascade tau={tau}: eff {ep:.4f}->{ec:.4f} fake {fp:.5f}->{fc:.5f} ms {t_plain:.3f}->{t_casc:.3f} "
           f"flagged {int(sub[1].item()) / de['seed_hits'].shape[1]:.3f}")
     assert t_casc < t_plain
+
+
+def test_cascade_replays_from_a_cuda_graph():
+    """The cascade's three calls (gated best-hit finding, seed compaction,
+    N-best finding of the listed seeds) need no host synchronisation: captured
+    once into a CUDA graph after a first call, a replay gives the eager result."""
+    from paper_1811_04141_gb300 import learned as L
+    from paper_1811_04141_gb300.api import mkf_mlp_to_bf16
+    b = make_batch("dense45", [57, 58], n_tracks=600, n_noise=40000, material=0.02, eloss=0.04)
+    ctx = make_ctx(b)
+    d = upload(b)
+    mo = len(b.layers) + 3
+    w = mlp.bf16_round(mlp.init_weights(29))
+    wb = mkf_mlp_to_bf16(ctx, torch.as_tensor(w, dtype=torch.float32, device="cuda"))
+    bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
+    eager, sub = L.cascade(ctx, bins, d["seed_hits"], d["seed_event"], wb, 0.0, max_out=mo)
+    ctx.sync()
+    eager = {k: v.clone() for k, v in eager.items() if v is not None}
+    n_flag = int(sub[1].item())
+    assert 0 < n_flag < b.n_seeds
+    out = {k: torch.empty_like(v) for k, v in eager.items()}
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    with torch.cuda.stream(stream):
+        L.cascade(ctx, bins, d["seed_hits"], d["seed_event"], wb, 0.0, max_out=mo, out=out, subset=sub)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        L.cascade(ctx, bins, d["seed_hits"], d["seed_event"], wb, 0.0, max_out=mo, out=out, subset=sub)
+    for v in out.values():
+        v.fill_(-3)
+    with torch.cuda.stream(stream):
+        g.replay()
+    stream.synchronize()
+    ctx.set_stream(torch.cuda.current_stream())
+    assert int(sub[1].item()) == n_flag
+    for k, v in eager.items():
+        assert torch.equal(out[k].view(torch.int32), v.view(torch.int32)), k
