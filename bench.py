@@ -468,6 +468,22 @@ def fit_leg(dev, peak, n_tracks: int = 1_000_000, reps: int = 20):
     ms_b = float(np.mean([a.elapsed_time(e) for a, e in tb]))
     layers = int((b.track_hits >= 0).sum())
     fl = flops.FLOPS_PER_FIT_LAYER * layers
+    # C1 as stated: one event of 1000 tracks, latency of one fit call (launch
+    # included), median of 50 back-to-back calls timed one by one
+    b1 = make_batch("fit10", [0], n_tracks=1000)
+    x1, l1, t1 = to(b1.xyz, torch.float32), to(b1.layer, torch.int32), to(b1.track_hits, torch.int32)
+    o1 = ctx.fit(x1, l1, t1)
+    for _ in range(5):
+        ctx.fit(x1, l1, t1, out=o1)
+    torch.cuda.synchronize()
+    lat = []
+    for _ in range(50):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.fit(x1, l1, t1, out=o1)
+        e.record()
+        e.synchronize()
+        lat.append(a.elapsed_time(e))
     ctx.close()
     roof = lambda t, k: {"bound": "alu", "achieved": fl / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": fl / (t * 1e-3) / 1e12 / peak, "kernel": k}
@@ -477,7 +493,9 @@ def fit_leg(dev, peak, n_tracks: int = 1_000_000, reps: int = 20):
             "backward": {"workload": "the same tracks fitted in reverse from the forward result at the last hit "
                                      "(covariance x100), state at the first hit",
                          "track_layer_updates_per_s": layers / (ms_b * 1e-3), "ms": ms_b,
-                         "roofline": roof(ms_b, "fit_kernel (backward)")}}
+                         "roofline": roof(ms_b, "fit_kernel (backward)")},
+            "c1_latency": {"workload": "1 event x 1000 tracks (fit10), one mkf_fit call",
+                           "ms_median": float(np.median(lat)), "ms_p90": float(np.percentile(lat, 90))}}
 
 
 def physics_leg(dev, n_events: int = 5, per_event: int = 10000, reps: int = 10):
@@ -624,14 +642,16 @@ def e2e_pipelined(ctx, batch, bins, NB, max_out, K, W, units_all, pg, dev, find_
 # our implementation
 # ---------------------------------------------------------------------------
 
-def find20_leg(dev, peak_tflops, steps: int = 50):
-    """The 20-event find20 workload (binning + N = 10 finding, eager launches,
-    L2 flushed between steps) and best-hit finding (N = 1) on the same events."""
+def find20_leg(dev, peak_tflops, steps: int = 50, config: str = FIND20, events=None, workload=FIND20_WORKLOAD):
+    """A fixed-size finding workload (binning + N = 10 finding, eager launches,
+    L2 flushed between steps) and best-hit finding (N = 1) on the same events:
+    by default find20 (20 events x 2000 tracks)."""
     import torch
 
     from paper_1811_04141_gb300 import Context, flops
     from synth import make_batch
-    batch = make_batch(FIND20, list(range(FIND20_EVENTS)))
+    batch = make_batch(config, list(range(FIND20_EVENTS)) if events is None else list(events), truth=False,
+                       workers=os.cpu_count() or 1)
     ctx = Context(dev.index, torch.cuda.current_stream(dev))
     ctx.geometry_load(batch.layers, batch.bz)
     to = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
@@ -641,7 +661,7 @@ def find20_leg(dev, peak_tflops, steps: int = 50):
     max_out = len(batch.layers) + 3
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    res = {"workload": FIND20_WORKLOAD}
+    res = {"workload": workload, "events": batch.n_events, "hits": batch.n_hits, "seeds": batch.n_seeds}
     for nb in (N_BEST, 1):
         bins = ctx.hits_bin(xyz, layer, evo)
         out = ctx.find(bins, sh, se, n_best=nb, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
@@ -807,6 +827,11 @@ def run_ours(args, world, rank, local, pg):
     if rank == 0 and world == 1:
         if not args.no_find20:
             extras["find20"] = find20_leg(dev, peak_tflops)
+            extras["dense50"] = find20_leg(
+                dev, peak_tflops, steps=10, config="dense45", events=range(50),
+                workload="KF track finding, 50 dense events x 6000 tracks (pT^-3 from 0.5 GeV) + 200k uniform noise "
+                         "hits: 17 barrel cylinders + 2x14 endcap disks, |eta|<2.4, 2% hit inefficiency; N=10, chi2 "
+                         "cut 30")
         if not args.no_fit:
             extras["fit"] = fit_leg(dev, peak_tflops)
         if not args.no_post:
