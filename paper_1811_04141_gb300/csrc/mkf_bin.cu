@@ -289,6 +289,7 @@ mkf_status grow(mkf_hitbins *b, int64_t n_hits, int64_t n_bins) {
         cudaFree(b->blocksums);
         b->offsets = b->counts = b->blocksums = nullptr;
         b->cap_bins = b->cap_blocks = 0;
+        b->zero_bins = 0;
         int64_t c = std::max<int64_t>(n_bins, 1024);
         int64_t cb = std::max<int64_t>((c + kScanTile - 1) / kScanTile, 1);
         MKF_CUDA_TRY(cudaMalloc(&b->offsets, (c + 1) * sizeof(int32_t)));
@@ -447,12 +448,19 @@ extern "C" mkf_status mkf_hits_bin(mkf_ctx *ctx, const float *xyz, const int32_t
     b->n_events = n_events;
     b->n_bins = n_bins;
     cudaStream_t s = ctx->stream;
-    MKF_CUDA_TRY(cudaMemsetAsync(b->counts, 0, n_bins * sizeof(int32_t), s));
+    // every binning leaves the histogram zero (the scan clears what it reads),
+    // so it is set here only when this call's bins reach beyond the part known
+    // to be zero (a new allocation, or a call that failed before its scan)
+    const int64_t zero_before = std::max<int64_t>(b->zero_bins, 0);
+    b->zero_bins = 0;  // until the scan has been enqueued
+    if (n_bins > zero_before)
+        MKF_CUDA_TRY(cudaMemsetAsync(b->counts, 0, n_bins * sizeof(int32_t), s));
     // the finder does not depend on the order of hits within a bin, so the store
     // keeps arrival order; mkf_hitbins_export orders it when asked for the layout
     st = run_binning(ctx, xyz, layer, event_offsets, n_events, n_hits, n_bins, b->counts, b->blocksums, b->key,
                      b->layer, b->zhit, b->offsets, b->rec, b->inv, false);
     if (st != MKF_OK) return st;
+    b->zero_bins = std::max(zero_before, n_bins);
     b->ordered = n_hits == 0;
     *inout = b;
     return MKF_OK;

@@ -59,6 +59,7 @@ struct mkf_hitbins {
     int32_t *key;       // [n_hits] bin of each original hit (-1 if dropped)
     int32_t *offsets;   // [n_bins + 1] CSR offsets of the bins
     int32_t *counts;    // [n_bins] scratch histogram
+    int64_t zero_bins;  // counts[0, zero_bins) hold zero between calls
     int32_t *blocksums; // scan scratch
     int64_t cap_blocks;
     int ordered;        // hits within each bin in ascending original index

@@ -10,3 +10,4 @@ inline int cudaSetDevice(int) { return 0; }
 struct float4 { float x, y, z, w; };
 struct float2 { float x, y; };
 inline float2 make_float2(float x, float y) { return float2{x, y}; }
+inline float4 make_float4(float x, float y, float z, float w) { return float4{x, y, z, w}; }

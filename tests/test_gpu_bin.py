@@ -79,6 +79,19 @@ def test_binning_reuse_and_empty():
     ex = bins.export(ctx)
     torch.cuda.synchronize()
     assert ex["n_hits"] == b2.n_hits and ex["offsets"][-1].item() == b2.n_hits
+    # more events (more bins than any call before), fewer, then as many again: the
+    # histogram left by each call must be zero for the next (a count left over
+    # would show as a gap in the offsets)
+    b3 = make_batch("find20", [7, 8, 9], n_tracks=120)
+    d3 = upload(b3)
+    for bb, dd in ((b3, d3), (b2, d2), (b3, d3), (b, d)):
+        bins = ctx.hits_bin(dd["xyz"], dd["layer"], dd["event_offsets"], bins)
+        ex = bins.export(ctx)
+        torch.cuda.synchronize()
+        off = ex["offsets"].cpu().numpy()
+        orig = ex["rec"].cpu().numpy()[:, 3].view(np.int32)
+        assert off[0] == 0 and off[-1] == bb.n_hits and (np.diff(off) >= 0).all()
+        assert np.array_equal(np.sort(orig), np.arange(bb.n_hits))
     # an event with no hits at all
     empty_xyz = torch.zeros(3, 0, device="cuda")
     e = ctx.hits_bin(empty_xyz, torch.zeros(0, dtype=torch.int32, device="cuda"),
