@@ -20,7 +20,7 @@ def _layer_bases(layers):
 @pytest.mark.parametrize("cfg,events,tracks,grid", [
     ("find20", 3, 500, None),
     ("dense45", 2, 800, None),
-    # more than 1024 scan tiles of 4096 bins: the two-kernel scan
+    # hundreds of scan tiles (each tile adds the totals of the tiles before it)
     ("dense45", 12, 50, None),
     # two bins per layer: a block's 256 bins hold more hits than its shared buffer,
     # so the in-bin ordering runs in global memory
