@@ -38,7 +38,9 @@ def test_find_parity_small(n_best):
     compare(out, ref)
 
 
-@pytest.mark.parametrize("n_best", [1, 4, 16])
+# widths that leave lanes of a warp without a seed (3: ten seeds and two idle
+# lanes, 7: four seeds and four idle lanes) as well as the ones that divide 32
+@pytest.mark.parametrize("n_best", [1, 3, 4, 7, 16])
 def test_find_parity_other_widths(n_best):
     b = make_batch("find20", [22, 23], n_tracks=200)
     compare(run_gpu(b, n_best), run_oracle(b, n_best))
