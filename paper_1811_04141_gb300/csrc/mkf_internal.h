@@ -38,8 +38,8 @@ struct mkf_ctx {
     int num_sms;
     int find_smem_attr;  // dynamic shared memory the find kernel is configured for
     // cached occupancy per finder variant: (plain, learned) x (uniform field,
-    // material, parameterised field)
-    int find_occ_threads[6], find_occ_smem[6], find_occ_blocks[6];
+    // material, parameterised field) x (beam width at run time, 1, 10)
+    int find_occ_threads[18], find_occ_smem[18], find_occ_blocks[18];
     // r-z material map in device memory (geom.mat_map points here when loaded)
     float2 *mat_map;
     size_t mat_map_cells;

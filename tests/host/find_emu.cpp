@@ -14,6 +14,25 @@ dim3 blockDim;
 WarpEmu *g_warp;
 unsigned char *g_smem;
 
+template <bool kLearned, int kPhys>
+static void run_width(int kn, const FindArgs &A) {
+    if (kn == 1) find_kernel<kLearned, kPhys, 1>(A);
+    else if (kn == 10) find_kernel<kLearned, kPhys, 10>(A);
+    else find_kernel<kLearned, kPhys, 0>(A);
+}
+
+static void run_variant(bool learned, int phys, int kn, const FindArgs &A) {
+    if (learned) {
+        if (phys == 0) run_width<true, 0>(kn, A);
+        else if (phys == 1) run_width<true, 1>(kn, A);
+        else find_kernel<true, 2, 0>(A);
+    } else {
+        if (phys == 0) run_width<false, 0>(kn, A);
+        else if (phys == 1) run_width<false, 1>(kn, A);
+        else find_kernel<false, 2, 0>(A);
+    }
+}
+
 extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *X, const float *Y, const float *Z,
                         const int *layer, int n_hits, const int *event_offsets, int n_events, const int *seed_hits,
                         const int *seed_event, int n_seeds, int N, float cut, int max_consec, int max_out, int step1,
@@ -125,14 +144,10 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
         lanes.emplace_back([&, l] {
             threadIdx.x = l;
             blockIdx.x = 0;
-            switch (phys + (mlp_bf16 ? 3 : 0)) {
-                case 0: find_kernel<false, 0>(A); break;
-                case 1: find_kernel<false, 1>(A); break;
-                case 2: find_kernel<false, 2>(A); break;
-                case 3: find_kernel<true, 0>(A); break;
-                case 4: find_kernel<true, 1>(A); break;
-                default: find_kernel<true, 2>(A); break;
-            }
+            // the variant the library launches: fixed beam width 1 or 10 except in
+            // the parameterised field
+            const int kn = phys == 2 ? 0 : (N == 1 ? 1 : (N == 10 ? 10 : 0));
+            run_variant(mlp_bf16 != nullptr, phys, kn, A);
         });
     for (auto &t : lanes) t.join();
     fault_out[0] = fault.code;
