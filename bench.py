@@ -11,7 +11,7 @@ uneven occupancy on the dense geometry (17 barrel cylinders + 2 x 14 endcap
 disks, 3.8 T), per event floor(exp(U[ln 100, ln 20000])) tracks with pT falling
 as pT^-3 from 0.5 GeV, |eta| < 2.4, 2 % hit inefficiency, and
 floor(exp(U[ln 1e3, ln 3e5])) uniform noise hits; N = 10 best candidates kept per
-seed, chi2 cut 30; the finder's block size from the autotuner.  Metric: KF
+seed, chi2 cut 30; bin grid, block size and seed order from the autotuner.  Metric: KF
 candidate-layer updates/s (one unit = one candidate propagated to one layer and
 searched).  Extra objects time the 20-event find20 workload, the fit of 10^6
 tracks, learned pruning, seed cleaning and duplicate removal.
@@ -645,10 +645,12 @@ def e2e_pipelined(ctx, batch, bins, NB, max_out, K, W, units_all, pg, dev, find_
 def find20_leg(dev, peak_tflops, steps: int = 50, config: str = FIND20, events=None, workload=FIND20_WORKLOAD):
     """A fixed-size finding workload (binning + N = 10 finding, eager launches,
     L2 flushed between steps) and best-hit finding (N = 1) on the same events:
-    by default find20 (20 events x 2000 tracks)."""
+    by default find20 (20 events x 2000 tracks); bin grid, block size and seed
+    order from the autotuner for each."""
     import torch
 
     from paper_1811_04141_gb300 import Context, flops
+    from paper_1811_04141_gb300.runtime import tune_find_config
     from synth import make_batch
     batch = make_batch(config, list(range(FIND20_EVENTS)) if events is None else list(events), truth=False,
                        workers=os.cpu_count() or 1)
@@ -663,11 +665,16 @@ def find20_leg(dev, peak_tflops, steps: int = 50, config: str = FIND20, events=N
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     res = {"workload": workload, "events": batch.n_events, "hits": batch.n_hits, "seeds": batch.n_seeds}
     for nb in (N_BEST, 1):
+        # bin grid, block size and seed order from the autotuner for this
+        # workload and N (it leaves the chosen grid loaded)
+        fkw = dict(chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
+        _, bt, tune = tune_find_config(ctx, batch.layers, batch.bz, xyz, layer, evo, sh, se, n_best=nb, **fkw)
+        fkw.update(block_threads=bt, seed_order=tune.get("seed_order", 0))
         bins = ctx.hits_bin(xyz, layer, evo)
-        out = ctx.find(bins, sh, se, n_best=nb, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out)
+        out = ctx.find(bins, sh, se, n_best=nb, **fkw)
         for _ in range(3):
             ctx.hits_bin(xyz, layer, evo, bins)
-            ctx.find(bins, sh, se, n_best=nb, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=out)
+            ctx.find(bins, sh, se, n_best=nb, out=out, **fkw)
         torch.cuda.synchronize()
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
         for i in range(steps):
@@ -675,7 +682,7 @@ def find20_leg(dev, peak_tflops, steps: int = 50, config: str = FIND20, events=N
             ev[i][0].record(stream)
             ctx.hits_bin(xyz, layer, evo, bins)
             ev[i][1].record(stream)
-            ctx.find(bins, sh, se, n_best=nb, chi2_cut=CHI2_CUT, max_consec_miss=MAX_CONSEC, max_out=max_out, out=out)
+            ctx.find(bins, sh, se, n_best=nb, out=out, **fkw)
             ev[i][2].record(stream)
         torch.cuda.synchronize()
         ctx.sync()
@@ -689,7 +696,9 @@ def find20_leg(dev, peak_tflops, steps: int = 50, config: str = FIND20, events=N
             "hits_tested": ht, "updates": up,
             "roofline": {"bound": "alu", "achieved": fl / (find_ms * 1e-3) / 1e12, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": fl / (find_ms * 1e-3) / 1e12 / peak_tflops,
-                         "kernel": "mkf_find (seed_kernel + find_kernel)"}}
+                         "kernel": "mkf_find (seed_kernel + find_kernel)"},
+            "autotune": {"grid": tune.get("grid"), "block_threads": bt, "seed_order": tune.get("seed_order", 0),
+                         "spread": tune.get("spread")}}
     ctx.close()
     return res
 
