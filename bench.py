@@ -551,7 +551,7 @@ def physics_leg(dev, n_events: int = 5, per_event: int = 10000, reps: int = 10):
 # (seed_kernel, the order's scan and scatter, find_kernel) per candidate-layer it
 # processes, from a one-pass ncu capture of the current kernels on 96 of the 512
 # uneven dense events (the whole workload exceeds the capture size rule): 619.3 MB
-# for 46.5 M candidate-layers (profiles/find_kernel.c4_96events.md); the traffic
+# for 46.5 M candidate-layers (the finder's ncu summary under profiles/); the traffic
 # (hit records, seed records, outputs) grows with the candidate-layers processed.
 FIND_DRAM_BYTES_PER_CAND_LAYER = 13.32
 
