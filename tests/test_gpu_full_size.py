@@ -19,12 +19,18 @@ def _oracle(b, sel, n_best=10):
 
 def test_dense_50_events_sampled():
     """50 events x 6000 tracks (pT^-3) + 200k noise hits each, 17 cylinders +
-    2 x 14 disks, N = 10."""
+    2 x 14 disks, N = 10, with the bin grid, block size and seed order the
+    tuner picks for it (as the bench's dense leg runs it)."""
+    from paper_1811_04141_gb300.runtime import tune_find_config
     b = make_batch("dense45", list(range(300, 350)))
     ctx = make_ctx(b)
     d = upload(b)
+    mo = len(b.layers) + 3
+    _, bt, rec = tune_find_config(ctx, b.layers, b.bz, d["xyz"], d["layer"], d["event_offsets"], d["seed_hits"],
+                                  d["seed_event"], n_best=10, cache=False, max_out=mo)
     bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
-    out = to_np(ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=10, max_out=len(b.layers) + 3))
+    out = to_np(ctx.find(bins, d["seed_hits"], d["seed_event"], n_best=10, max_out=mo, block_threads=bt,
+                         seed_order=rec["seed_order"]))
     ctx.sync()
     sel = np.sort(np.random.default_rng(3).choice(b.n_seeds, 150, replace=False))
     compare(out, _oracle(b, sel), sel)
@@ -33,9 +39,10 @@ def test_dense_50_events_sampled():
 
 def test_batched_512_uneven_events_graph_replay_sampled():
     """512 events with log-uniform track (100-20000) and noise (1e3-3e5) counts,
-    one binning + finding step captured in a CUDA graph with the autotuned block
-    size and replayed, as the bench's batched leg runs it."""
-    from paper_1811_04141_gb300.runtime import CapturedStep, tune_find_block
+    one binning + finding step captured in a CUDA graph with the autotuned bin
+    grid, block size and seed order and replayed, as the bench's headline runs
+    it."""
+    from paper_1811_04141_gb300.runtime import CapturedStep, tune_find_config
     rng = np.random.default_rng(4_181_104)
     n_ev = 512
     tracks = np.floor(np.exp(rng.uniform(np.log(100), np.log(20000), n_ev))).astype(int)
@@ -44,11 +51,11 @@ def test_batched_512_uneven_events_graph_replay_sampled():
     ctx = make_ctx(b)
     d = upload(b)
     mo = len(b.layers) + 3
-    bins = ctx.hits_bin(d["xyz"], d["layer"], d["event_offsets"])
-    bt, _ = tune_find_block(ctx, bins, d["seed_hits"], d["seed_event"], n_best=10, cache=False, max_out=mo)
+    _, bt, rec = tune_find_config(ctx, b.layers, b.bz, d["xyz"], d["layer"], d["event_offsets"], d["seed_hits"],
+                                  d["seed_event"], n_best=10, cache=False, max_out=mo)
     et = torch.zeros(n_ev + 1, dtype=torch.int64, device="cuda")
     step = CapturedStep(ctx, d["xyz"], d["layer"], d["event_offsets"], d["seed_hits"], d["seed_event"], n_best=10,
-                        max_out=mo, block_threads=bt, event_times=et)
+                        max_out=mo, block_threads=bt, seed_order=rec["seed_order"], event_times=et)
     for _ in range(2):
         out = step.replay()
     torch.cuda.synchronize()
