@@ -447,12 +447,15 @@ __device__ __forceinline__ void expand(const FindArgs &A, const Geom &G, int ev,
 }
 
 // Seed fit, one thread per seed: state from the three hits (circle + line),
-// then the Kalman fit through them (the first hit without propagation), the
-// tracking region from the seed's eta, the direction along z and the first
-// layers beyond the third hit.
-// kParamField: the parameterised field (Runge-Kutta propagation).
-template <bool kParamField>
+// then the Kalman fit through them (the first hit without propagation; the
+// covariance as a square root from the prior), the tracking region from the
+// seed's eta, the direction along z and the first layers beyond the third hit.
+// kPhys: 0 uniform field, 1 material effects, 2 parameterised field
+// (Runge-Kutta propagation) and material effects.
+template <int kPhys>
 __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindArgs A) {
+    constexpr bool kParamField = kPhys == 2;
+    constexpr int kSq = kPhys >= 1 ? 9 : 5;  // square-root columns (two per layer of material)
     const int li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= seeds_in_call(A)) return;
     const int t = A.seed_list ? A.seed_list[li] : li;  // the seed
@@ -488,12 +491,13 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
         hz[k] = A.zhit[hidx[k]];
     }
     float p[6], C[21], eta = 0.f, chi2 = 0.f;
+    SqrtCov<kSq> Q;
     Lo lo{0.f, 0.f, 0.f, 0.f, 0.f};
     if (ok) {
         const float h1[3] = {hx[0], hy[0], hz[0]}, h2[3] = {hx[1], hy[1], hz[1]}, h3[3] = {hx[2], hy[2], hz[2]};
         // the parameterised field at the middle hit sets the curvature scale
         const float kbs = kParamField ? G.kb * bz_factor(G.alpha, h2[0], h2[1], h2[2]) : G.kb;
-        ok = seed_state(G.L[hl[0]], kbs, h1, h2, h3, p, C, eta);
+        ok = seed_state(G.L[hl[0]], kbs, h1, h2, h3, p, Q, eta);
     }
     for (int k = 0; k < 3 && ok; ++k) {
         const LayerDesc &Ld = G.L[hl[k]];
@@ -507,26 +511,23 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
                 break;
             }
             if (kParamField)
-                propagate_field(Ld, G.kb, G.alpha, p, lo, C, sphi, cphi, -p[3] * kbl, s);
+                propagate_field(Ld, G.kb, G.alpha, p, lo, &Q, sphi, cphi, -p[3] * kbl, s);
             else
-                propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-            float mx0, mk;
-            material_at(G, Ld, p, mx0, mk);
-            add_scattering(Ld.kind, mx0, p, C);
-            apply_eloss(Ld.kind, mx0, mk, p, C, 1.f);
+                propagate_transport(Ld, G.kb, p, lo, &Q, sphi, cphi, cot, s);
+            if (kPhys >= 1) {
+                float mx0, mk;
+                material_at(G, Ld, p, mx0, mk);
+                add_scattering(Ld.kind, mx0, p, &Q);
+                apply_eloss(Ld.kind, mx0, mk, p, &Q, 1.f);
+            }
         }
         const Frame f = frame_of(p);
-        Innov I;
-        if (!innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
-            ok = false;
-            break;
-        }
         float u, v;
         const float zr = Ld.kind == 0 ? hz[k] : sqrtf(fmaf(hx[k], hx[k], hy[k] * hy[k]));
         residual(Ld.kind, Ld.rz, p, lo, f, hx[k], hy[k], zr, u, v);
-        chi2 += chi2_of(I, u, v);
-        kf_apply(I, u, v, p, lo, C);
+        chi2 += sqrt_update(Ld.kind, Ld.su2, Ld.sv2, f, u, v, p, lo, &Q);
     }
+    if (ok) sqrt_to_cov(Q, C);
     ok = ok && finite_state(p);
     uint32_t status = ok ? 0u : MKF_ST_BADSEED;
     if (A.order_key) {
@@ -587,8 +588,7 @@ __global__ void __launch_bounds__(128) seed_kernel(const __grid_constant__ FindA
         float lchi[MKF_MAX_NBEST], lu[MKF_MAX_NBEST], lv[MKF_MAX_NBEST];
         int lorig[MKF_MAX_NBEST];
         Expansion X;
-        expand<kParamField ? 2 : 1>(A, G, ev, mask, dir, N, A.cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi, lorig,
-                                    lu, lv, 1, X);
+        expand<kPhys>(A, G, ev, mask, dir, N, A.cut, p, lo, C, bk, I, status, c_cl, c_ht, lchi, lorig, lu, lv, 1, X);
         nlist = X.nlist;
         searched = X.searched;
         nbeam = min(searched ? nlist + 1 : 1, N);
@@ -1269,10 +1269,11 @@ extern "C" mkf_status mkf_find(mkf_ctx *ctx, const mkf_hitbins *bins, const int3
         MKF_CUDA_TRY(cudaMemsetAsync(A.event_times, 0, sizeof(uint64_t) * bins->n_events, ctx->stream));
         MKF_CUDA_TRY(cudaMemsetAsync(A.event_times + bins->n_events, 0xff, sizeof(uint64_t), ctx->stream));
     }
-    if (phys == 2)
-        seed_kernel<true><<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A);
-    else
-        seed_kernel<false><<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A);
+    switch (phys) {
+        case 0: seed_kernel<0><<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A); break;
+        case 1: seed_kernel<1><<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A); break;
+        default: seed_kernel<2><<<(n_seeds + 127) / 128, 128, 0, ctx->stream>>>(A); break;
+    }
     MKF_CUDA_TRY(cudaGetLastError());
     if (grouped) {
         // key counts -> offsets (the total, n_seeds, lands in the last entry),

@@ -3,6 +3,8 @@
 // backward fit, the same filter through the hits in reverse order.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mkf_internal.h"
 
 namespace {
@@ -53,18 +55,64 @@ __device__ __forceinline__ void reverse_state(float p[6], Lo &lo, float C[21]) {
             if ((i == 3 || i == 5) != (j == 3 || j == 5)) C[sym(i, j)] = -C[sym(i, j)];
 }
 
+// Move the state onto layer Ld (the helix or, for kPhys = 2, Runge-Kutta steps
+// in the parameterised field); false if the layer is not reached.
+template <int kPhys, class Cov>
+__device__ __forceinline__ bool move_to(const Geom &G, const LayerDesc &Ld, float p[6], Lo &lo, Cov C) {
+    float sphi, cphi;
+    sincos_pair(p[4], lo.phi, sphi, cphi);
+    const float cot = cot_pair(p[5], lo.th);
+    const float kbl = kPhys == 2 ? G.kb * bz_factor(G.alpha, p[0], p[1], p[2]) : G.kb;
+    float s;
+    if (!path_to_layer(Ld, kbl, p, lo, sphi, cphi, cot, s)) return false;
+    if (kPhys == 2)
+        propagate_field(Ld, G.kb, G.alpha, p, lo, C, sphi, cphi, -p[3] * kbl, s);
+    else
+        propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
+    return true;
+}
+
+// Kalman update with the hit (xh, yh, zh) on layer Ld; false if the residual
+// covariance is not positive definite.
+__device__ __forceinline__ bool update_with(const LayerDesc &Ld, float xh, float yh, float zh, float p[6], Lo &lo,
+                                            float C[21], float &dchi2) {
+    const Frame f = frame_of(p);
+    Innov I;
+    if (!innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) return false;
+    float u, v;
+    const float zr = Ld.kind == 0 ? zh : sqrtf(fmaf(xh, xh, yh * yh));
+    residual(Ld.kind, Ld.rz, p, lo, f, xh, yh, zr, u, v);
+    dchi2 = chi2_of(I, u, v);
+    kf_apply_joseph(I, u, v, p, lo, C);
+    return true;
+}
+
+// The same with the covariance as a square root (the seed hits).
+template <int K>
+__device__ __forceinline__ bool update_with(const LayerDesc &Ld, float xh, float yh, float zh, float p[6], Lo &lo,
+                                            SqrtCov<K> *Q, float &dchi2) {
+    const Frame f = frame_of(p);
+    float u, v;
+    const float zr = Ld.kind == 0 ? zh : sqrtf(fmaf(xh, xh, yh * yh));
+    residual(Ld.kind, Ld.rz, p, lo, f, xh, yh, zr, u, v);
+    dchi2 = sqrt_update(Ld.kind, Ld.su2, Ld.sv2, f, u, v, p, lo, Q);
+    return true;
+}
+
 // kBackward: hits in reverse order from the given state at the last hit, turned
 // around and inflated; the result at the first hit is turned back.  kPhys: 0
 // uniform field without material; 1 material effects compiled in (selected
 // when any layer has material); 2 the parameterised field (Runge-Kutta
 // propagation) with the material effects.
 template <bool kBackward, int kPhys>
-__global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __grid_constant__ FitArgs A) {
+__global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 6) fit_kernel(const __grid_constant__ FitArgs A) {
     constexpr bool kMaterial = kPhys >= 1, kParamField = kPhys == 2;
+    constexpr int kSq = kMaterial ? 9 : 5;  // square-root columns through the seed hits
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= A.n) return;
     const Geom &G = A.G;
     float p[6], C[21];
+    SqrtCov<kSq> Q;
     Lo lo{0.f, 0.f, 0.f, 0.f, 0.f};
     uint32_t st = 0;
     float chi2 = 0.f;
@@ -104,55 +152,38 @@ __global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __gr
             h3[0] = A.X[first[2]]; h3[1] = A.Y[first[2]]; h3[2] = A.Z[first[2]];
             // the parameterised field at the middle hit sets the curvature scale
             const float kbs = kParamField ? G.kb * bz_factor(G.alpha, h2[0], h2[1], h2[2]) : G.kb;
-            ok = seed_state(G.L[l0], kbs, h1, h2, h3, p, C, eta);
+            ok = seed_state(G.L[l0], kbs, h1, h2, h3, p, Q, eta);
         }
     }
     if (!ok) st |= MKF_ST_BADSEED;
 
     if (ok) {
         bool firsthit = true;
-        for (int kk = 0; kk < A.max_hits; ++kk) {
-            const int k = kBackward ? A.max_hits - 1 - kk : kk;
-            const int h = A.hit_idx[(int64_t)k * A.n + t];
-            if (h < 0 || h >= A.n_hits) continue;
+        // one hit: onto its layer (after the first), material, update; Cx is
+        // the covariance (float[21]) or, through the seed hits, its square root
+        auto hit = [&](auto Cx, int h) {
             const int l = A.hit_layer[h];
             if (l < 0 || l >= G.n_layers) {
                 record_fault(A.fault, kFaultBadLayer, h);
-                continue;
+                return;
             }
             const LayerDesc &Ld = G.L[l];
-            const float xh = A.X[h], yh = A.Y[h], zh = A.Z[h];
             if (!firsthit) {
-                float sphi, cphi;
-                sincos_pair(p[4], lo.phi, sphi, cphi);
-                const float cot = cot_pair(p[5], lo.th);
-                // path estimate from the helix in the local axial field
-                const float kbl = kParamField ? G.kb * bz_factor(G.alpha, p[0], p[1], p[2]) : G.kb;
-                float s;
-                if (!path_to_layer(Ld, kbl, p, lo, sphi, cphi, cot, s)) {
+                if (!move_to<kPhys>(G, Ld, p, lo, Cx)) {
                     st |= MKF_ST_UNREACHABLE;
-                    continue;
+                    return;
                 }
-                if (kParamField)
-                    propagate_field(Ld, G.kb, G.alpha, p, lo, C, sphi, cphi, -p[3] * kbl, s);
-                else
-                    propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
                 if (!kBackward && kMaterial) {
                     float mx0, mk;
                     material_at(G, Ld, p, mx0, mk);
-                    add_scattering(Ld.kind, mx0, p, C);
-                    apply_eloss(Ld.kind, mx0, mk, p, C, 1.f);
+                    add_scattering(Ld.kind, mx0, p, Cx);
+                    apply_eloss(Ld.kind, mx0, mk, p, Cx, 1.f);
                 }
             }
             firsthit = false;
-            const Frame f = frame_of(p);
-            Innov I;
-            if (innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) {
-                float u, v;
-                const float zr = Ld.kind == 0 ? zh : sqrtf(fmaf(xh, xh, yh * yh));
-                residual(Ld.kind, Ld.rz, p, lo, f, xh, yh, zr, u, v);
-                chi2 += chi2_of(I, u, v);
-                kf_apply(I, u, v, p, lo, C);
+            float dchi2;
+            if (update_with(Ld, A.X[h], A.Y[h], A.Z[h], p, lo, Cx, dchi2)) {
+                chi2 += dchi2;
                 ++used;
             } else {
                 st |= MKF_ST_BADS;
@@ -163,9 +194,28 @@ __global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __gr
             if (kBackward && kMaterial) {
                 float mx0, mk;
                 material_at(G, Ld, p, mx0, mk);
-                apply_eloss(Ld.kind, mx0, mk, p, C, -1.f);
-                add_scattering(Ld.kind, mx0, p, C);
+                apply_eloss(Ld.kind, mx0, mk, p, Cx, -1.f);
+                add_scattering(Ld.kind, mx0, p, Cx);
             }
+        };
+        auto hit_at = [&](int kk) {
+            const int k = kBackward ? A.max_hits - 1 - kk : kk;
+            const int h = A.hit_idx[(int64_t)k * A.n + t];
+            return h < 0 || h >= A.n_hits ? -1 : h;
+        };
+        int kk = 0;
+        if constexpr (!kBackward) {
+            if (!A.seed_par) {  // from the seed prior: the seed hits with the square root
+                for (; kk < A.max_hits && used < 3; ++kk) {
+                    const int h = hit_at(kk);
+                    if (h >= 0) hit(&Q, h);
+                }
+                sqrt_to_cov(Q, C);
+            }
+        }
+        for (; kk < A.max_hits; ++kk) {
+            const int h = hit_at(kk);
+            if (h >= 0) hit(C, h);
         }
         if (kBackward) reverse_state(p, lo, C);
         if (!finite_state(p) || !isfinite(chi2)) st |= MKF_ST_NONFINITE;
@@ -187,38 +237,6 @@ __global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) fit_kernel(const __gr
 
 // ---------------------------------------------------------------------------
 // Smoother: the state at every hit from all of the track's hits (two filters).
-
-// Move the state onto layer Ld (the helix or, for kPhys = 2, Runge-Kutta steps
-// in the parameterised field); false if the layer is not reached.
-template <int kPhys>
-__device__ __forceinline__ bool move_to(const Geom &G, const LayerDesc &Ld, float p[6], Lo &lo, float C[21]) {
-    float sphi, cphi;
-    sincos_pair(p[4], lo.phi, sphi, cphi);
-    const float cot = cot_pair(p[5], lo.th);
-    const float kbl = kPhys == 2 ? G.kb * bz_factor(G.alpha, p[0], p[1], p[2]) : G.kb;
-    float s;
-    if (!path_to_layer(Ld, kbl, p, lo, sphi, cphi, cot, s)) return false;
-    if (kPhys == 2)
-        propagate_field(Ld, G.kb, G.alpha, p, lo, C, sphi, cphi, -p[3] * kbl, s);
-    else
-        propagate_transport(Ld, G.kb, p, lo, C, sphi, cphi, cot, s);
-    return true;
-}
-
-// Kalman update with the hit (xh, yh, zh) on layer Ld; false if the residual
-// covariance is not positive definite.
-__device__ __forceinline__ bool update_with(const LayerDesc &Ld, float xh, float yh, float zh, float p[6], Lo &lo,
-                                            float C[21], float &dchi2) {
-    const Frame f = frame_of(p);
-    Innov I;
-    if (!innovation(Ld.kind, Ld.su2, Ld.sv2, f, C, I)) return false;
-    float u, v;
-    const float zr = Ld.kind == 0 ? zh : sqrtf(fmaf(xh, xh, yh * yh));
-    residual(Ld.kind, Ld.rz, p, lo, f, xh, yh, zr, u, v);
-    dchi2 = chi2_of(I, u, v);
-    kf_apply(I, u, v, p, lo, C);
-    return true;
-}
 
 // Weighted mean of two independent estimates (pf, Cf), (pb, Cb) of the state on
 // a surface, in its five free parameters P p: (u, z, q/pT, phi, theta) on a
@@ -478,7 +496,9 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const __grid_constant__ 
 #pragma unroll
         for (int i = 0; i < 21; ++i) A.sm_cov[((int64_t)k * 21 + i) * n + t] = nanv;
     }
+    constexpr int kSq = kMaterial ? 9 : 5;  // square-root columns through the seed hits
     float p[6], C[21];
+    SqrtCov<kSq> Q;
     Lo lo{0.f, 0.f, 0.f, 0.f, 0.f};
     uint32_t st = 0;
     float chi2 = 0.f;
@@ -510,7 +530,7 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const __grid_constant__ 
             h2[0] = A.X[first[1]]; h2[1] = A.Y[first[1]]; h2[2] = A.Z[first[1]];
             h3[0] = A.X[first[2]]; h3[1] = A.Y[first[2]]; h3[2] = A.Z[first[2]];
             const float kbs = kParamField ? G.kb * bz_factor(G.alpha, h2[0], h2[1], h2[2]) : G.kb;
-            ok = seed_state(G.L[l0], kbs, h1, h2, h3, p, C, eta);
+            ok = seed_state(G.L[l0], kbs, h1, h2, h3, p, Q, eta);
         }
     }
     if (!ok) st |= MKF_ST_BADSEED;
@@ -519,41 +539,60 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const __grid_constant__ 
     int lastk = -1;
     if (ok) {
         bool firsthit = true;
-        for (int k = 0; k < A.max_hits; ++k) {
-            const int h = A.hit_idx[(int64_t)k * n + t];
-            if (h < 0 || h >= A.n_hits) continue;
+        // one hit; Cx is the covariance (float[21]) or, through the seed hits,
+        // its square root
+        auto fwd = [&](auto Cx, int k, int h) {
             const int l = A.hit_layer[h];
             if (l < 0 || l >= G.n_layers) {
                 record_fault(A.fault, kFaultBadLayer, h);
-                continue;
+                return;
             }
             const LayerDesc &Ld = G.L[l];
             if (!firsthit) {
-                if (!move_to<kPhys>(G, Ld, p, lo, C)) {
+                if (!move_to<kPhys>(G, Ld, p, lo, Cx)) {
                     st |= MKF_ST_UNREACHABLE;
-                    continue;
+                    return;
                 }
                 if (kMaterial) {
                     float mx0, mk;
                     material_at(G, Ld, p, mx0, mk);
-                    add_scattering(Ld.kind, mx0, p, C);
-                    apply_eloss(Ld.kind, mx0, mk, p, C, 1.f);
+                    add_scattering(Ld.kind, mx0, p, Cx);
+                    apply_eloss(Ld.kind, mx0, mk, p, Cx, 1.f);
                 }
             }
             firsthit = false;
             float dchi2;
-            if (update_with(Ld, A.X[h], A.Y[h], A.Z[h], p, lo, C, dchi2)) {
+            if (update_with(Ld, A.X[h], A.Y[h], A.Z[h], p, lo, Cx, dchi2)) {
                 chi2 += dchi2;
                 ++used;
                 const float pw[6] = {p[0] + lo.x, p[1] + lo.y, p[2] + lo.z, p[3], p[4] + lo.phi, p[5] + lo.th};
 #pragma unroll
                 for (int i = 0; i < 6; ++i) A.sm_par[((int64_t)k * 6 + i) * n + t] = pw[i];
+                float Cw[21];
+                if constexpr (std::is_same_v<decltype(Cx), float *>) {
 #pragma unroll
-                for (int i = 0; i < 21; ++i) A.sm_cov[((int64_t)k * 21 + i) * n + t] = C[i];
+                    for (int i = 0; i < 21; ++i) Cw[i] = Cx[i];
+                } else {
+                    sqrt_to_cov(*Cx, Cw);
+                }
+#pragma unroll
+                for (int i = 0; i < 21; ++i) A.sm_cov[((int64_t)k * 21 + i) * n + t] = Cw[i];
                 lastk = k;
             } else {
                 st |= MKF_ST_BADS;
             }
+        };
+        int k = 0;
+        if (!A.seed_par) {  // from the seed prior: the seed hits with the square root
+            for (; k < A.max_hits && used < 3; ++k) {
+                const int h = A.hit_idx[(int64_t)k * n + t];
+                if (h >= 0 && h < A.n_hits) fwd(&Q, k, h);
+            }
+            sqrt_to_cov(Q, C);
+        }
+        for (; k < A.max_hits; ++k) {
+            const int h = A.hit_idx[(int64_t)k * n + t];
+            if (h >= 0 && h < A.n_hits) fwd(C, k, h);
         }
     }
 

@@ -138,6 +138,24 @@ struct Lo {
     float x, y, z, phi, th;
 };
 
+// The covariance through the seed hits, as a square root C = S S^T with K
+// columns (five for the prior, two more for each layer of material on the
+// way; unused columns hold zeros).  From the seed prior (variances 1e-4 rad^2
+// on the angles, (10 % of q/pT)^2 on q/pT) the three seed-hit updates shrink
+// C by up to six orders of magnitude in the directions the hits measure; the
+// FP32 entries of the transported prior (relative rounding 6e-8) no longer fix
+// the small eigenvalues that remain, and a track in a thousand came out with
+// its chi2 off by several 1e-3 of itself.  Rounding in the square root
+// perturbs C by FP32 precision times the square root of its condition number
+// instead (the classical property of square-root filters).  The seed hits'
+// updates are scalar steps in Potter's form (sqrt_update); C = S S^T after the
+// third hit continues in the plain FP32 filter.
+template <int K>
+struct SqrtCov {
+    float S[6][K];
+    int k;  // columns in use
+};
+
 // sin(a)/a and its derivative (a cos a - sin a)/a^2, series near 0.
 __device__ __forceinline__ void sinc_and_deriv(float a, float sa, float ca, float& sn, float& dsn) {
     float a2 = a * a;
@@ -270,9 +288,87 @@ __device__ __forceinline__ void helix_point(const float p[6], float sphi, float 
     z = fmaf(s, cot, p[2]);
 }
 
-// Move state p by path s onto the surface of layer Ld and transport C with the
+// Jacobian of the move onto a surface, J = A + d g^T: the entries of the
+// fixed-path Jacobian A that differ from the identity, d = dF/ds and the
+// nonzero entries of g = ds/dp (kind 0: cylinder, 1: disk).
+struct HelixJac {
+    float Axw, Ayw, Axf, Ayf, Azt, Afw;
+    float d0, d1, d2, d4;
+    float g0, g1, g2, g3, g4, g5;
+    int kind;
+};
+
+// C' = J C J^T from that structure (about 150 FMAs instead of 432).
+__device__ __forceinline__ void transport_cov(const HelixJac& J, float C[21]) {
+    // full symmetric C in registers
+    float Cf[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) Cf[i][j] = C[sym(i, j)];
+
+    // M = A C
+    float M[6][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        M[0][j] = fmaf(J.Axw, Cf[3][j], fmaf(J.Axf, Cf[4][j], Cf[0][j]));
+        M[1][j] = fmaf(J.Ayw, Cf[3][j], fmaf(J.Ayf, Cf[4][j], Cf[1][j]));
+        M[2][j] = fmaf(J.Azt, Cf[5][j], Cf[2][j]);
+        M[3][j] = Cf[3][j];
+        M[4][j] = fmaf(J.Afw, Cf[3][j], Cf[4][j]);
+        M[5][j] = Cf[5][j];
+    }
+    // M += d (g^T C)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        float v;
+        if (J.kind == 0) v = fmaf(J.g0, Cf[0][j], fmaf(J.g1, Cf[1][j], fmaf(J.g3, Cf[3][j], J.g4 * Cf[4][j])));
+        else v = fmaf(J.g2, Cf[2][j], J.g5 * Cf[5][j]);
+        M[0][j] = fmaf(J.d0, v, M[0][j]);
+        M[1][j] = fmaf(J.d1, v, M[1][j]);
+        M[2][j] = fmaf(J.d2, v, M[2][j]);
+        M[4][j] = fmaf(J.d4, v, M[4][j]);
+    }
+    // C' = M A^T + (M g) d^T, lower triangle
+    float u[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (J.kind == 0) u[i] = fmaf(J.g0, M[i][0], fmaf(J.g1, M[i][1], fmaf(J.g3, M[i][3], J.g4 * M[i][4])));
+        else u[i] = fmaf(J.g2, M[i][2], J.g5 * M[i][5]);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        C[sym(i, 0)] = fmaf(u[i], J.d0, fmaf(J.Axw, M[i][3], fmaf(J.Axf, M[i][4], M[i][0])));
+        if (i >= 1) C[sym(i, 1)] = fmaf(u[i], J.d1, fmaf(J.Ayw, M[i][3], fmaf(J.Ayf, M[i][4], M[i][1])));
+        if (i >= 2) C[sym(i, 2)] = fmaf(u[i], J.d2, fmaf(J.Azt, M[i][5], M[i][2]));
+        if (i >= 3) C[sym(i, 3)] = M[i][3];
+        if (i >= 4) C[sym(i, 4)] = fmaf(u[i], J.d4, fmaf(J.Afw, M[i][3], M[i][4]));
+        if (i >= 5) C[sym(i, 5)] = M[i][5];
+    }
+}
+
+// S' = J S, column by column.
+template <int K>
+__device__ __forceinline__ void transport_cov(const HelixJac& J, SqrtCov<K>* Q) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        float c[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) c[i] = Q->S[i][j];
+        const float v = J.kind == 0 ? fmaf(J.g0, c[0], fmaf(J.g1, c[1], fmaf(J.g3, c[3], J.g4 * c[4])))
+                                    : fmaf(J.g2, c[2], J.g5 * c[5]);
+        Q->S[0][j] = fmaf(J.d0, v, fmaf(J.Axw, c[3], fmaf(J.Axf, c[4], c[0])));
+        Q->S[1][j] = fmaf(J.d1, v, fmaf(J.Ayw, c[3], fmaf(J.Ayf, c[4], c[1])));
+        Q->S[2][j] = fmaf(J.d2, v, fmaf(J.Azt, c[5], c[2]));
+        Q->S[4][j] = fmaf(J.d4, v, fmaf(J.Afw, c[3], c[4]));
+    }
+}
+
+// Move state p by path s onto the surface of layer Ld and transport its
+// covariance (C as float[21], or a square root SqrtCov<K>*) with the
 // surface-constrained Jacobian J = A + d g^T.
-__device__ __forceinline__ void propagate_transport(const LayerDesc& Ld, float kb, float p[6], Lo& lo, float C[21],
+template <class Cov>
+__device__ __forceinline__ void propagate_transport(const LayerDesc& Ld, float kb, float p[6], Lo& lo, Cov C,
                                                    float sphi, float cphi, float cot, float s) {
     const float h = -p[3] * kb;
     const float a = 0.5f * h * s;
@@ -288,74 +384,36 @@ __device__ __forceinline__ void propagate_transport(const LayerDesc& Ld, float k
     sincos_small(p[5], st, ct_unused);
     const float xe = p[0] + dx, ye = p[1] + dy;
 
+    HelixJac J;
+    J.kind = Ld.kind;
     // fixed-path Jacobian entries
     const float dxdh = 0.5f * s * fmaf(s * dsn, cm, -dy);
     const float dydh = 0.5f * s * fmaf(s * dsn, sm, dx);
-    const float Axw = -kb * dxdh, Ayw = -kb * dydh;
-    const float Axf = -dy, Ayf = dx;
-    const float Azt = -s / (st * st);
-    const float Afw = -kb * s;
+    J.Axw = -kb * dxdh;
+    J.Ayw = -kb * dydh;
+    J.Axf = -dy;
+    J.Ayf = dx;
+    J.Azt = -s / (st * st);
+    J.Afw = -kb * s;
     // d = dF/ds
-    const float d0 = cpe, d1 = spe, d2 = cot, d4 = h;
+    J.d0 = cpe;
+    J.d1 = spe;
+    J.d2 = cot;
+    J.d4 = h;
     // g = ds/dp (only the nonzero entries)
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f;
+    J.g0 = J.g1 = J.g2 = J.g3 = J.g4 = J.g5 = 0.f;
     if (Ld.kind == 0) {
         const float inv = -1.f / fmaf(xe, cpe, ye * spe);
-        g0 = xe * inv;
-        g1 = ye * inv;
-        g3 = fmaf(xe, Axw, ye * Ayw) * inv;
-        g4 = fmaf(xe, Axf, ye * Ayf) * inv;
+        J.g0 = xe * inv;
+        J.g1 = ye * inv;
+        J.g3 = fmaf(xe, J.Axw, ye * J.Ayw) * inv;
+        J.g4 = fmaf(xe, J.Axf, ye * J.Ayf) * inv;
     } else {
         const float inv = -1.f / cot;
-        g2 = inv;
-        g5 = Azt * inv;
+        J.g2 = inv;
+        J.g5 = J.Azt * inv;
     }
-
-    // full symmetric C in registers
-    float Cf[6][6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) Cf[i][j] = C[sym(i, j)];
-
-    // M = A C
-    float M[6][6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        M[0][j] = fmaf(Axw, Cf[3][j], fmaf(Axf, Cf[4][j], Cf[0][j]));
-        M[1][j] = fmaf(Ayw, Cf[3][j], fmaf(Ayf, Cf[4][j], Cf[1][j]));
-        M[2][j] = fmaf(Azt, Cf[5][j], Cf[2][j]);
-        M[3][j] = Cf[3][j];
-        M[4][j] = fmaf(Afw, Cf[3][j], Cf[4][j]);
-        M[5][j] = Cf[5][j];
-    }
-    // M += d (g^T C)
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        float v;
-        if (Ld.kind == 0) v = fmaf(g0, Cf[0][j], fmaf(g1, Cf[1][j], fmaf(g3, Cf[3][j], g4 * Cf[4][j])));
-        else v = fmaf(g2, Cf[2][j], g5 * Cf[5][j]);
-        M[0][j] = fmaf(d0, v, M[0][j]);
-        M[1][j] = fmaf(d1, v, M[1][j]);
-        M[2][j] = fmaf(d2, v, M[2][j]);
-        M[4][j] = fmaf(d4, v, M[4][j]);
-    }
-    // C' = M A^T + (M g) d^T, lower triangle
-    float u[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        if (Ld.kind == 0) u[i] = fmaf(g0, M[i][0], fmaf(g1, M[i][1], fmaf(g3, M[i][3], g4 * M[i][4])));
-        else u[i] = fmaf(g2, M[i][2], g5 * M[i][5]);
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        C[sym(i, 0)] = fmaf(u[i], d0, fmaf(Axw, M[i][3], fmaf(Axf, M[i][4], M[i][0])));
-        if (i >= 1) C[sym(i, 1)] = fmaf(u[i], d1, fmaf(Ayw, M[i][3], fmaf(Ayf, M[i][4], M[i][1])));
-        if (i >= 2) C[sym(i, 2)] = fmaf(u[i], d2, fmaf(Azt, M[i][5], M[i][2]));
-        if (i >= 3) C[sym(i, 3)] = M[i][3];
-        if (i >= 4) C[sym(i, 4)] = fmaf(u[i], d4, fmaf(Afw, M[i][3], M[i][4]));
-        if (i >= 5) C[sym(i, 5)] = M[i][5];
-    }
+    transport_cov(J, C);
 
     df_add(p[0], lo.x, dx);
     df_add(p[1], lo.y, dy);
@@ -382,6 +440,47 @@ constexpr float kRkTurn = 0.05f;  // largest turning angle per step, rad
 constexpr float kRkLen = 10.f;    // largest step, cm of path
 constexpr int kRkMaxN = 16;       // most steps per propagation
 constexpr int kRkNewton = 2;      // correction steps onto the surface
+
+// C' = J C J^T for a dense Jacobian.
+__device__ __forceinline__ void transport_cov(const float (&J)[6][6], float C[21]) {
+    float M[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float a = 0.f;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) a = fmaf(J[i][m], C[sym(m, k)], a);
+            M[i][k] = a;
+        }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            float a = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a = fmaf(M[i][k], J[j][k], a);
+            C[sym(i, j)] = a;
+        }
+}
+
+// S' = J S for a dense Jacobian.
+template <int K>
+__device__ __forceinline__ void transport_cov(const float (&J)[6][6], SqrtCov<K>* Q) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        float c[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) c[i] = Q->S[i][j];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            float a = 0.f;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) a = fmaf(J[i][m], c[m], a);
+            Q->S[i][j] = a;
+        }
+    }
+}
 
 // Bz(x, y, z) / Bz(0).
 __device__ __forceinline__ float bz_factor(float alpha, float x, float y, float z) {
@@ -536,8 +635,9 @@ __device__ __forceinline__ float nearest_root(float a, float b, float c) {
 // parameter columns (dr, dT) integrated with the trajectory (the variational
 // equations, the field's gradient included), then the surface constraint
 // dS = -(n . dr) / (n . T) moves every column along (T, dT/dS) at the end.
+template <class Cov>
 __device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, float alpha, float p[6], Lo &lo,
-                                                float C[21], float sphi, float cphi, float h, float s) {
+                                                Cov C, float sphi, float cphi, float h, float s) {
     float st, ct;
     sincos_pair(p[5], lo.th, st, ct);
     const float lam = p[3] * st;
@@ -616,26 +716,7 @@ __device__ __forceinline__ void propagate_field(const LayerDesc &Ld, float kb, f
         J[5][j] = fmaf(T[2], dtt, -tt * t[2]) / tn2;
     }
 
-    // C' = J C J^T
-    float M[6][6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            float a = 0.f;
-#pragma unroll
-            for (int m = 0; m < 6; ++m) a = fmaf(J[i][m], C[sym(m, k)], a);
-            M[i][k] = a;
-        }
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            float a = 0.f;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) a = fmaf(M[i][k], J[j][k], a);
-            C[sym(i, j)] = a;
-        }
+    transport_cov(J, C);
 
     // state at the end: position pairs, azimuth turned by the angle between
     // the start and end transverse directions, theta and q/pT = lambda / sin(theta)
@@ -684,11 +765,12 @@ __device__ __forceinline__ void material_at(const Geom &G, const LayerDesc &Ld, 
 }
 
 // t: thickness in radiation lengths at normal incidence (material_at).
-__device__ __forceinline__ void add_scattering(int kind, float t, const float p[6], float C[21]) {
+// theta0, (q/pT) cot(theta) and sin(theta) of the crossing; false if no noise.
+__device__ __forceinline__ bool scatter_angle(int kind, float t, const float p[6], float &th0, float &wc, float &st) {
     // q/pT = 0: no field, momentum not measured; taken as infinite (no noise)
-    if (!(t > 0.f) || !(fabsf(p[3]) > 0.f)) return;
+    if (!(t > 0.f) || !(fabsf(p[3]) > 0.f)) return false;
     constexpr float kPionMass2 = 0.13957f * 0.13957f;
-    float st, ct;
+    float ct;
     sincos_small(p[5], st, ct);
     float cosa;
     if (kind == 0) {
@@ -702,12 +784,39 @@ __device__ __forceinline__ void add_scattering(int kind, float t, const float p[
     const float pm = 1.f / (fabsf(p[3]) * st);
     const float beta = pm / sqrtf(fmaf(pm, pm, kPionMass2));
     const float x = t / cosa;
-    const float th0 = 0.0136f / (beta * pm) * sqrtf(x) * (1.f + 0.038f * logf(x / (beta * beta)));
-    const float v = th0 * th0, wc = p[3] * ct / st;
+    th0 = 0.0136f / (beta * pm) * sqrtf(x) * (1.f + 0.038f * logf(x / (beta * beta)));
+    wc = p[3] * ct / st;
+    return true;
+}
+
+__device__ __forceinline__ void add_scattering(int kind, float t, const float p[6], float C[21]) {
+    float th0, wc, st;
+    if (!scatter_angle(kind, t, p, th0, wc, st)) return;
+    const float v = th0 * th0;
     C[sym(5, 5)] += v;
     C[sym(4, 4)] += v / (st * st);
     C[sym(3, 3)] += wc * wc * v;
     C[sym(5, 3)] -= wc * v;
+}
+
+// The same noise as two columns of the square root: theta0 (-wc e_q/pT + e_theta)
+// and theta0 / sin(theta) e_phi.  (Room for them is kept: material is met on
+// arrival at the second and third seed hits' layers only.)
+template <int K>
+__device__ __forceinline__ void add_scattering(int kind, float t, const float p[6], SqrtCov<K> *Q) {
+    float th0, wc, st;
+    if (!scatter_angle(kind, t, p, th0, wc, st)) return;
+    const int k = Q->k;
+    if (k + 2 > K) return;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if (j == k) {
+            Q->S[3][j] = -wc * th0;
+            Q->S[5][j] = th0;
+        }
+        if (j == k + 1) Q->S[4][j] = th0 / st;
+    }
+    Q->k = k + 2;
 }
 
 // Mean energy loss in the material (no straggling): dE = k * x / beta^2 for the
@@ -717,8 +826,10 @@ __device__ __forceinline__ void add_scattering(int kind, float t, const float p[
 // g = p / p'(p), p = 1 / (|q/pT| sin theta), in q/pT and theta (the path held
 // fixed): dp'/dp = (E' / p') (p / E + 2 k x m^2 / p^3), g' = 1 / p' - p dp'/dp / p'^2,
 // d(q/pT')/d(q/pT) = g - p g', d(q/pT')/d(theta) = -(q/pT) p cot(theta) g'.
-__device__ __forceinline__ void apply_eloss(int kind, float t, float k, float p[6], float C[21], float sign) {
-    if (!(k > 0.f) || !(t > 0.f) || !(fabsf(p[3]) > 0.f)) return;
+// q/pT scaled in place; (a, c) = the derivatives of q/pT' in q/pT and theta;
+// false if nothing changes.
+__device__ __forceinline__ bool eloss_map(int kind, float t, float k, float p[6], float sign, float &a, float &c) {
+    if (!(k > 0.f) || !(t > 0.f) || !(fabsf(p[3]) > 0.f)) return false;
     constexpr float kPionMass = 0.13957f;
     float st, ct;
     sincos_small(p[5], st, ct);
@@ -736,19 +847,35 @@ __device__ __forceinline__ void apply_eloss(int kind, float t, float k, float p[
     const float beta = pm / e;
     const float kx = sign * k * (t / cosa);
     const float e2 = e - kx / (beta * beta);
-    if (!(e2 > kPionMass)) return;  // stopped: left as it is
+    if (!(e2 > kPionMass)) return false;  // stopped: left as it is
     const float p2 = sqrtf(fmaf(e2, e2, -kPionMass * kPionMass));
     const float r = pm / p2;
     const float dp2 = e2 / p2 * (pm / e + 2.f * kx * (kPionMass * kPionMass) / (pm * pm * pm));
     const float gp = 1.f / p2 - pm * dp2 / (p2 * p2);
-    const float a = r - pm * gp, c = -p[3] * pm * (ct / st) * gp;
+    a = r - pm * gp;
+    c = -p[3] * pm * (ct / st) * gp;
     p[3] *= r;
+    return true;
+}
+
+__device__ __forceinline__ void apply_eloss(int kind, float t, float k, float p[6], float C[21], float sign) {
+    float a, c;
+    if (!eloss_map(kind, t, k, p, sign, a, c)) return;
     float row[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) row[j] = fmaf(a, C[sym(3, j)], c * C[sym(5, j)]);
     const float c33 = fmaf(a, row[3], c * row[5]);
 #pragma unroll
     for (int j = 0; j < 6; ++j) C[sym(3, j)] = j == 3 ? c33 : row[j];
+}
+
+// The same map on the square root's q/pT row.
+template <int K>
+__device__ __forceinline__ void apply_eloss(int kind, float t, float k, float p[6], SqrtCov<K> *Q, float sign) {
+    float a, c;
+    if (!eloss_map(kind, t, k, p, sign, a, c)) return;
+#pragma unroll
+    for (int j = 0; j < K; ++j) Q->S[3][j] = fmaf(a, Q->S[3][j], c * Q->S[5][j]);
 }
 
 // Measurement frame at the state's position: unit radial vector (cp, sp), radius.
@@ -821,9 +948,9 @@ __device__ __forceinline__ float chi2_of(const Innov& I, float u, float v) {
     return fmaf(u, fmaf(I.Iuu, u, I.Iuv * v), v * fmaf(I.Iuv, u, I.Ivv * v));
 }
 
-// Kalman update: K = C H^T S^-1, p += K r, C -= K (H C).
-__device__ __forceinline__ void kf_apply(const Innov& I, float u, float v, float p[6], Lo& lo, float C[21]) {
-    float K0[6], K1[6];
+// Kalman gain K = C H^T S^-1 and the state update p += K r.
+__device__ __forceinline__ void kf_gain_state(const Innov& I, float u, float v, float p[6], Lo& lo, float K0[6],
+                                              float K1[6]) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         K0[i] = fmaf(I.HCu[i], I.Iuu, I.HCv[i] * I.Iuv);
@@ -836,17 +963,123 @@ __device__ __forceinline__ void kf_apply(const Innov& I, float u, float v, float
     df_add(p[4], lo.phi, fmaf(K0[4], u, K1[4] * v));
     df_wrap_pi(p[4], lo.phi);
     df_add(p[5], lo.th, fmaf(K0[5], u, K1[5] * v));
+}
+
+// Kalman update: K = C H^T S^-1, p += K r, C -= K (H C).
+__device__ __forceinline__ void kf_apply(const Innov& I, float u, float v, float p[6], Lo& lo, float C[21]) {
+    float K0[6], K1[6];
+    kf_gain_state(I, u, v, p, lo, K0, K1);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j) C[sym(i, j)] = C[sym(i, j)] - fmaf(K0[i], I.HCu[j], K1[i] * I.HCv[j]);
 }
 
+// The same update with C in the Joseph form (I - K H) C (I - K H)^T + K V K^T,
+// written C - K G^T - G K^T with G = (H C)^T - K S / 2 (equal to C - K H C
+// for the optimal gain; about 50 more FMAs).  It holds for any gain, so the
+// rounding of K enters C only at second order and C stays positive where an
+// update shrinks a variance by orders of magnitude (the position along a
+// layer after a long or scattered step), where C - K H C can turn a variance
+// negative.  The fit kernels take it; the finder keeps the short form.
+__device__ __forceinline__ void kf_apply_joseph(const Innov& I, float u, float v, float p[6], Lo& lo,
+                                                float C[21]) {
+    float K0[6], K1[6];
+    kf_gain_state(I, u, v, p, lo, K0, K1);
+    float G0[6], G1[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        G0[i] = fmaf(-0.5f * K0[i], I.Suu, fmaf(-0.5f * K1[i], I.Suv, I.HCu[i]));
+        G1[i] = fmaf(-0.5f * K0[i], I.Suv, fmaf(-0.5f * K1[i], I.Svv, I.HCv[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j)
+            C[sym(i, j)] = fmaf(-K0[i], G0[j], fmaf(-K1[i], G1[j], fmaf(-K0[j], G0[i], fmaf(-K1[j], G1[i], C[sym(i, j)]))));
+}
+
+// One measurement row h (variance r) through the square root, Potter's form:
+// phi = S^T h, s = |phi|^2 + r, gain K = S phi / s, and
+// S' = S - (gamma / s) (S phi) phi^T with gamma = 1 / (1 + sqrt(r / s)), so that
+// S' S'^T = C - C h h^T C / s.  Adds the gain times the residual to dp and
+// returns the residual's chi2 contribution.
+template <int K>
+__device__ __forceinline__ float potter_step(float (&S)[6][K], const float ph[K], float r, float res, float dp[6]) {
+    float s = r;
+#pragma unroll
+    for (int j = 0; j < K; ++j) s = fmaf(ph[j], ph[j], s);
+    float Sp[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        float a = 0.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j) a = fmaf(S[i][j], ph[j], a);
+        Sp[i] = a;
+    }
+    const float is = 1.f / s;
+    const float kr = res * is;
+    const float g = is / (1.f + sqrtf(r * is));
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        dp[i] = fmaf(Sp[i], kr, dp[i]);
+        const float gs = -g * Sp[i];
+#pragma unroll
+        for (int j = 0; j < K; ++j) S[i][j] = fmaf(gs, ph[j], S[i][j]);
+    }
+    return res * kr;
+}
+
+// Kalman update with the square root: the residual (u, v) of the hit at the
+// predicted state taken as two scalar measurements (their variances su2, sv2
+// are independent), v's residual moved to the state after the u step.  The
+// state changes as in the joint update and the two chi2 terms add up to
+// r^T S^-1 r (exact algebra); returns that chi2.
+template <int K>
+__device__ __forceinline__ float sqrt_update(int kind, float su2, float sv2, const Frame& f, float u, float v,
+                                             float p[6], Lo& lo, SqrtCov<K>* Q) {
+    float dp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float ph[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) ph[j] = fmaf(-f.sp, Q->S[0][j], f.cp * Q->S[1][j]);
+    float chi2 = potter_step(Q->S, ph, su2, u, dp);
+    const float v2 = v - (kind == 0 ? dp[2] : fmaf(f.cp, dp[0], f.sp * dp[1]));
+#pragma unroll
+    for (int j = 0; j < K; ++j) ph[j] = kind == 0 ? Q->S[2][j] : fmaf(f.cp, Q->S[0][j], f.sp * Q->S[1][j]);
+    chi2 += potter_step(Q->S, ph, sv2, v2, dp);
+    df_add(p[0], lo.x, dp[0]);
+    df_add(p[1], lo.y, dp[1]);
+    df_add(p[2], lo.z, dp[2]);
+    p[3] += dp[3];
+    df_add(p[4], lo.phi, dp[4]);
+    df_wrap_pi(p[4], lo.phi);
+    df_add(p[5], lo.th, dp[5]);
+    return chi2;
+}
+
+// C = S S^T.
+template <int K>
+__device__ __forceinline__ void sqrt_to_cov(const SqrtCov<K>& Q, float C[21]) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            float a = 0.f;
+#pragma unroll
+            for (int m = 0; m < K; ++m) a = fmaf(Q.S[i][m], Q.S[j][m], a);
+            C[sym(i, j)] = a;
+        }
+}
+
 // Seed state at hit 1 from three hits (circle in x-y, line in arc length-z),
-// with a prior covariance whose position part lies in the first layer's surface.
-// Returns false for degenerate hits.  Also returns eta of the estimate.
+// with a prior covariance whose position part lies in the first layer's
+// surface, as its square root (five columns: the position along the surface's
+// two directions, q/pT, phi, theta).  Returns false for degenerate hits.  Also
+// returns eta of the estimate.
+template <int K>
 __device__ __forceinline__ bool seed_state(const LayerDesc& L1, float kb, const float h1[3], const float h2[3],
-                                           const float h3[3], float p[6], float C[21], float& eta) {
+                                           const float h3[3], float p[6], SqrtCov<K>& Q, float& eta) {
+    static_assert(K >= 5, "the prior takes five columns");
     float ax = h2[0] - h1[0], ay = h2[1] - h1[1];
     float bx = h3[0] - h1[0], by = h3[1] - h1[1];
     float cx = h3[0] - h2[0], cy = h3[1] - h2[1];
@@ -868,22 +1101,24 @@ __device__ __forceinline__ bool seed_state(const LayerDesc& L1, float kb, const 
     p[5] = atan2f(1.f, cot);
     eta = asinhf(cot);
 #pragma unroll
-    for (int k = 0; k < 21; ++k) C[k] = 0.f;
-    float s2 = L1.seed_sig2;
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < K; ++j) Q.S[i][j] = 0.f;
+    const float sg = sqrtf(L1.seed_sig2);
     if (L1.kind == 0) {
         float r = sqrtf(fmaf(h1[0], h1[0], h1[1] * h1[1]));
         float sp = h1[1] / r, cp = h1[0] / r;
-        C[sym(0, 0)] = s2 * sp * sp;
-        C[sym(1, 0)] = -s2 * sp * cp;
-        C[sym(1, 1)] = s2 * cp * cp;
-        C[sym(2, 2)] = s2;
+        Q.S[0][0] = -sg * sp;  // along the cylinder's azimuth
+        Q.S[1][0] = sg * cp;
+        Q.S[2][1] = sg;
     } else {
-        C[sym(0, 0)] = s2;
-        C[sym(1, 1)] = s2;
+        Q.S[0][0] = sg;
+        Q.S[1][1] = sg;
     }
-    C[sym(3, 3)] = (0.1f * w) * (0.1f * w) + 1e-4f;
-    C[sym(4, 4)] = 1e-4f;
-    C[sym(5, 5)] = 1e-4f;
+    Q.S[3][2] = sqrtf(fmaf(0.1f * w, 0.1f * w, 1e-4f));
+    Q.S[4][3] = 0.01f;
+    Q.S[5][4] = 0.01f;
+    Q.k = 5;
     return true;
 }
 

@@ -129,10 +129,9 @@ extern "C" int emu_find(const mkf_layer *layers, int nl, float bz, const float *
     for (int t = 0; t < n_seeds; ++t) {
         blockIdx.x = t / 128;
         threadIdx.x = t % 128;
-        if (phys == 2)
-            seed_kernel<true>(A);
-        else
-            seed_kernel<false>(A);
+        if (phys == 2) seed_kernel<2>(A);
+        else if (phys == 1) seed_kernel<1>(A);
+        else seed_kernel<0>(A);
     }
     blockDim.x = 32;
     std::vector<unsigned char> smem(find_smem_bytes(nl, N, 32));

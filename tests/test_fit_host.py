@@ -4,6 +4,7 @@ multiple scattering -- against the oracle, with the FP32 tolerances of the GPU
 parity tests."""
 import ctypes as C
 import os
+import re
 import shutil
 import subprocess
 import tempfile
@@ -28,12 +29,9 @@ def lib():
     src = open(os.path.join(CSRC, "mkf_fit.cu")).read()
     a = src.index("namespace {")
     b = src.index("}  // namespace") + len("}  // namespace")
-    body = src[a:b].replace("template <bool kBackward, int kPhys>\n__global__ void __launch_bounds__(128, kPhys == 2 ? 4 : 8) "
-                            "fit_kernel(const __grid_constant__ FitArgs A)",
-                            "template <bool kBackward, int kPhys>\nvoid fit_kernel(const FitArgs &A)")
-    body = body.replace("template <int kPhys>\n__global__ void __launch_bounds__(128, 4) "
-                        "smooth_kernel(const __grid_constant__ FitArgs A)",
-                        "template <int kPhys>\nvoid smooth_kernel(const FitArgs &A)")
+    # the kernels as plain host functions (launch bounds and grid constants dropped)
+    body = re.sub(r"__global__ void __launch_bounds__\([^)]*\) (fit|smooth)_kernel\(const __grid_constant__ FitArgs A\)",
+                  r"void \1_kernel(const FitArgs &A)", src[a:b])
     assert "void fit_kernel(const FitArgs &A)" in body and "void smooth_kernel(const FitArgs &A)" in body
     d = tempfile.mkdtemp()
     with open(os.path.join(d, "fit_dev.inc"), "w") as f:
