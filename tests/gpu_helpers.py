@@ -24,7 +24,7 @@ PAR_SIGMA_FRAC = 1e-2
 # up to 1.5e-3 max(chi2, ndf) over ~2e4 tracks of the parity cases (98 % of
 # every case below 0.72e-3).
 CHI2_REL = 1e-3
-CHI2_MAX = 2.0  # per track, in units of CHI2_REL
+CHI2_MAX = 1.0  # per track, in units of CHI2_REL
 
 
 def wrap(a):

@@ -18,7 +18,7 @@ import pytest
 
 import oracle as O
 from synth import make_batch
-from tests.gpu_helpers import compare
+from tests.gpu_helpers import chi2_errors, compare
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -90,6 +90,21 @@ def test_emulated_finder_matches_oracle(emu_so, cfg, event, tracks, noise, n_bes
                  n_best=n_best, max_out=len(b.layers) + 3)
     out = run_emu(emu_so, cfg, event, tracks, noise, n_best, 1)
     compare(out, ref)
+
+
+def test_emulated_seed_phase_precision(emu_so):
+    """2000 find20 seeds of an event no other test uses, one of whose chi2
+    the seed kernel got 12.5e-3 of max(chi2, ndf) wrong with the seed-hit
+    filter's covariance in FP32 entries: with its square root every track
+    agrees to half the parity bar."""
+    b = make_batch("find20", [30006], n_tracks=2000)
+    ref = O.find(O.geometry_as_loaded(b), b.xyz.astype(np.float64), b.layer, b.event_offsets, b.seed_hits, b.seed_event,
+                 n_best=10, max_out=len(b.layers) + 3)
+    out = run_emu(emu_so, "find20", 30006, 2000, None, 10, 1)
+    compare(out, ref)
+    ok = (out["hits"] == ref["hits"]).all(axis=0) & (ref["status"] & O.ST_BADSEED == 0)
+    assert ok.sum() > 1950
+    assert chi2_errors(out["chi2"][ok], ref["chi2"][ok], 2 * ref["n_hits"][ok] - 5).max() <= 1.0
 
 
 @pytest.mark.parametrize("n_best,eloss", [(1, 0.0), (10, 0.0), (10, 0.1)])

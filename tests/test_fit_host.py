@@ -14,7 +14,7 @@ import pytest
 
 import oracle as O
 from synth import make_batch
-from tests.gpu_helpers import chi2_ok, par_errors
+from tests.gpu_helpers import chi2_errors, chi2_ok, par_errors
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -112,6 +112,23 @@ def test_fit_kernel_on_host(lib, cfg, material, eloss, alpha):
     okb = ok & (refb["status"] == 0)
     assert par_errors(outb["par"][:, okb], refb["par"][:, okb], refb["cov"][:, okb]).max() <= 1.0
     assert chi2_ok(outb["chi2"][okb], refb["chi2"][okb], refb["ndf"][okb])
+
+
+def test_fit_kernel_on_host_seed_phase_precision(lib):
+    """8000 find20 tracks of events no other test uses, four of whose chi2
+    came out 2.1e-3 to 12.5e-3 of max(chi2, ndf) off with the seed-hit filter's
+    covariance in FP32 entries (the transported seed prior shrinks by up to six
+    orders of magnitude over the three hits): with its square root every track
+    agrees to half the parity bar."""
+    errs = []
+    for ev in (30006, 30007, 30008, 30009):
+        b = make_batch("find20", [ev])
+        out = _run(lib, b, b.track_hits)
+        ref = O.fit(O.geometry_as_loaded(b), b.xyz.astype(np.float64), b.layer, b.track_hits)
+        ok = (ref["status"] == 0) & (out["status"] == 0)
+        assert (out["status"] == ref["status"]).all() and ok.sum() > 1950
+        errs.append(chi2_errors(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok]))
+    assert np.concatenate(errs).max() <= 1.0
 
 
 def test_fit_kernel_on_host_with_material_map(lib):

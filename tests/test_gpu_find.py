@@ -40,6 +40,21 @@ def test_find_parity_small(n_best):
 
 # widths that leave lanes of a warp without a seed (3: ten seeds and two idle
 # lanes, 7: four seeds and four idle lanes) as well as the ones that divide 32
+def test_find_seed_phase_precision():
+    """8000 find20 seeds of events no other test uses, among them the ones
+    whose chi2 the FP32 seed-hit filter got wrong by 2e-3 to 5e-2 of
+    max(chi2, ndf) (the covariance entries of the transported seed prior
+    rounded to FP32): with the seed-hit covariance as a square root every
+    track agrees to half the parity bar."""
+    b = make_batch("find20", [30006, 30007, 30008, 30009])
+    out = run_gpu(b, 10)
+    ref = run_oracle(b, 10)
+    compare(out, ref)
+    ok = ((out["hits"] == ref["hits"]).all(axis=0)) & (ref["status"] & O.ST_BADSEED == 0)
+    err = chi2_errors(out["chi2"][ok], ref["chi2"][ok], 2 * ref["n_hits"][ok] - 5)
+    assert ok.sum() > 7900 and err.max() <= 1.0, (ok.sum(), err.max())
+
+
 @pytest.mark.parametrize("n_best", [1, 3, 4, 7, 16])
 def test_find_parity_other_widths(n_best):
     b = make_batch("find20", [22, 23], n_tracks=200)
