@@ -14,15 +14,14 @@ PAR_FLOOR = np.array([1e-4, 1e-4, 1e-4, 1e-6, 1e-5, 1e-5])
 # a few metres) reaches microns while the state is known only to millimetres.
 # At a measured layer sigma is tens of microns, so the floors still decide.
 PAR_SIGMA_FRAC = 1e-2
-# chi2, per track: |chi2_gpu - chi2_oracle| <= 2e-3 max(chi2, ndf).
+# chi2, per track: |chi2_gpu - chi2_oracle| <= 1e-3 max(chi2, ndf).
 # The FP32 rounding of a residual is a fixed fraction of the hit resolution, so
 # its effect on chi2 scales with the number of measurements, not with chi2 itself
 # (which can be ~0 by chance).  The kernels compiled in FP64 agree with the
 # oracle to 1e-7 of this bar, so what remains is FP32 rounding spread over the
-# whole filter (propagation, gain, covariance update); it is largest on forward
-# tracks through five disks, where the covariance is most strongly correlated:
-# up to 1.5e-3 max(chi2, ndf) over ~2e4 tracks of the parity cases (98 % of
-# every case below 0.72e-3).
+# filter; with the seed hits' covariance as a square root (the prior shrinks by
+# up to six orders of magnitude there) it is at most 0.87e-3 max(chi2, ndf) over
+# the parity cases (98 % of every case below 0.31e-3).
 CHI2_REL = 1e-3
 CHI2_MAX = 1.0  # per track, in units of CHI2_REL
 
