@@ -25,13 +25,13 @@ def test_fit_parity(cfg, tracks):
     assert e.max() <= 1.0, e.max(axis=1)
     c = chi2_errors(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
     assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok]), (np.quantile(c, 0.98), c.max())
-    # covariance diagonal: relative 5e-2 (variances of q/pT and theta lose up to
-    # ~2e-2 to the FP32 conditioning of the filtered covariance, whose prior
-    # shrinks by ~1e4 over the track; 5e-2 on a variance is 2.5 % on sigma)
+    # covariance diagonal: relative 1e-3 (the prior shrinks by up to six orders
+    # of magnitude over the seed hits, which the square-root form carries; up to
+    # 2.3e-4 measured, 2e-2 with the covariance in FP32 entries through them)
     for i, k in enumerate((0, 2, 5, 9, 14, 20)):
         scale = np.maximum(np.abs(ref["cov"][k, ok]), 1e-9 * np.abs(ref["cov"][:, ok]).max(axis=0))
         r = np.abs(out["cov"][k, ok] - ref["cov"][k, ok]) / scale
-        assert r.max() < 5e-2, (k, r.max())
+        assert r.max() < 1e-3, (k, r.max())
 
 
 def test_fit_given_seed_states_and_ragged_lists():
@@ -105,10 +105,13 @@ def test_fit_backward_parity(cfg, tracks, inflate):
     assert e.max() <= 1.0, e.max(axis=1)
     c = chi2_errors(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
     assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok]), (np.quantile(c, 0.98), c.max())
+    # the start inflated 1e4 shrinks by as much over the first hits (9.5e-3
+    # measured there, up to 2.4e-4 at inflation 1-100)
+    bar = 2e-2 if inflate > 100.0 else 1e-3
     for k in (0, 2, 5, 9, 14, 20):
         scale = np.maximum(np.abs(ref["cov"][k, ok]), 1e-9 * np.abs(ref["cov"][:, ok]).max(axis=0))
         r = np.abs(out["cov"][k, ok] - ref["cov"][k, ok]) / scale
-        assert r.max() < 5e-2, (k, r.max())
+        assert r.max() < bar, (k, r.max())
 
 
 def test_fit_backward_ragged_lists_and_errors():
@@ -155,16 +158,17 @@ def test_fit_with_material_parity(cfg, material, eloss):
     assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
     # covariance diagonal: with scattering noise the FP32 filter's covariance
     # loses more to conditioning (each update shrinks a prior widened by the
-    # noise) than without it: 99 % of the tracks within 5e-2 relative, every
-    # track crossing its last layer steeply within 1.5e-1 (steep_crossing); x
-    # and y against the transverse position variance (on a cylinder one of them
-    # is nearly radial, with a variance close to zero)
+    # noise) than without it: 99 % of the tracks within 5e-3 relative on each
+    # variance, every track crossing its last layer steeply within 3e-2
+    # (steep_crossing; measured 2.2e-3 and 1.3e-2); x and y against the
+    # transverse position variance (on a cylinder one of them is nearly
+    # radial, with a variance close to zero)
     pos = ref["cov"][0, ok] + ref["cov"][2, ok]
     steep = steep_crossing(b, last_hits(b)[ok])
     for k in (0, 2, 5, 9, 14, 20):
         floor = 1e-2 * pos if k in (0, 2) else 1e-9 * np.abs(ref["cov"][:, ok]).max(axis=0)
         r = np.abs(out["cov"][k, ok] - ref["cov"][k, ok]) / np.maximum(np.abs(ref["cov"][k, ok]), floor)
-        assert np.quantile(r, 0.99) < 5e-2 and r[steep].max() < 1.5e-1, (k, np.quantile(r, 0.99), r[steep].max())
+        assert np.quantile(r, 0.99) < 5e-3 and r[steep].max() < 3e-2, (k, np.quantile(r, 0.99), r[steep].max())
     outb, refb, f = _backward_pair(b, b.track_hits, 100.0, ctx)
     okb = (refb["status"] == 0) & (f["status"] == 0)
     assert (outb["status"] == refb["status"]).all()
@@ -187,12 +191,12 @@ def test_fit_in_parameterised_field_parity(cfg, alpha):
     ok = ref["status"] == 0
     assert par_errors(out["par"][:, ok], ref["par"][:, ok], ref["cov"][:, ok]).max() <= 1.0
     assert chi2_ok(out["chi2"][ok], ref["chi2"][ok], ref["ndf"][ok])
+    # covariance diagonal without material: every track within 1e-3 (5.8e-5 measured)
     pos = ref["cov"][0, ok] + ref["cov"][2, ok]
-    steep = steep_crossing(b, last_hits(b)[ok])
     for k in (0, 2, 5, 9, 14, 20):
         floor = 1e-2 * pos if k in (0, 2) else 1e-9 * np.abs(ref["cov"][:, ok]).max(axis=0)
         r = np.abs(out["cov"][k, ok] - ref["cov"][k, ok]) / np.maximum(np.abs(ref["cov"][k, ok]), floor)
-        assert np.quantile(r, 0.99) < 5e-2 and r[steep].max() < 1.5e-1, (k, np.quantile(r, 0.99), r[steep].max())
+        assert r.max() < 1e-3, (k, r.max())
     outb, refb, f = _backward_pair(b, b.track_hits, 100.0, ctx)
     okb = (refb["status"] == 0) & (f["status"] == 0)
     assert (outb["status"] == refb["status"]).all()
