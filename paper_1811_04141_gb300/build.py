@@ -15,12 +15,16 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmkf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-# The finder and the fit divide and take square roots with the approximate forms
-# (division within 2 ulp, no IEEE slow paths): their code shrinks and they run
-# 7-11 % faster, while their differences from the FP64 oracle keep the same
-# distribution (they are set by the FP32 state and residual rounding, not by
-# these operations).
-_APPROX = ["-prec-div=false", "-prec-sqrt=false"]
+# The finder and the fit are compiled with fast math: division and square root
+# in the approximate forms (within 2 ulp, no IEEE slow paths; 7-11 % faster),
+# denormals flushed to zero (no value they carry comes near 1e-38) and logf as
+# the hardware approximation (the scattering angle's logarithm, relative error
+# ~1e-6 of a term that is 4 % of the angle).  Their differences from the FP64
+# oracle keep the same distribution: they are set by the FP32 state and residual
+# rounding, not by these operations.  Flushing denormals made the finder 2 %
+# faster on the 512-event workload and the whole set 4 %, with bit-identical
+# hit lists and chi2 there.
+_APPROX = ["--use_fast_math"]
 FILE_FLAGS = {"mkf_find.cu": _APPROX, "mkf_fit.cu": _APPROX}
 
 
