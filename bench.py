@@ -550,10 +550,10 @@ def physics_leg(dev, n_events: int = 5, per_event: int = 10000, reps: int = 10):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one mkf_find call
 # (seed_kernel, the order's scan and scatter, find_kernel) per candidate-layer it
 # processes, from a one-pass ncu capture of the current kernels on 96 of the 512
-# uneven dense events (the whole workload exceeds the capture size rule): 617.6 MB
+# uneven dense events (the whole workload exceeds the capture size rule): 618.4 MB
 # for 46.5 M candidate-layers (the finder's ncu summary under profiles/); the traffic
 # (hit records, seed records, outputs) grows with the candidate-layers processed.
-FIND_DRAM_BYTES_PER_CAND_LAYER = 13.28
+FIND_DRAM_BYTES_PER_CAND_LAYER = 13.30
 
 
 def _carve(arena, specs):
